@@ -1,0 +1,340 @@
+"""FP64 CPU oracle for the RBSOG force evaluation (arXiv:2205.13824).
+
+TEST INFRASTRUCTURE ONLY.  This package is the judge the CUDA path is
+compared with: only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it.  It shares no code with the
+product package ``paper_2205_13824_gb300`` and never imports it.
+
+The arithmetic lives in ``rbsog_oracle.c`` (plain C, FP64, OpenMP over
+independent outer loops); this module compiles it on first use and exposes
+numpy-level wrappers.  Every wrapper names the passage of the paper it follows
+in the C source.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rbsog_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liborcl.so")
+_lock = threading.Lock()
+_lib = None
+
+_d = C.c_double
+_i32 = C.c_int32
+_i64 = C.c_int64
+_u64 = C.c_uint64
+_pd = C.POINTER(C.c_double)
+_pi32 = C.POINTER(C.c_int32)
+
+
+class OrcSys(C.Structure):
+    _fields_ = [("L", _d * 3), ("M", _i32), ("omega", _pd), ("s", _pd), ("rc", _d),
+                ("lB", _d), ("wca_sigma", _d), ("wca_eps", _d)]
+
+
+class OrcEnergies(C.Structure):
+    _fields_ = [("U_near", _d), ("U_far", _d), ("U_self", _d), ("U_wca", _d), ("K", _d), ("T", _d)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liborcl.so`` (gcc, -O2, OpenMP,
+    no FP contraction so x86 and Arm hosts agree bit for bit)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                              os.path.getmtime(os.path.join(_HERE, "rbsog_oracle.h")))):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_sog_coeffs.argtypes = [_d, _d, _i32, _pd, _pd]
+            for fn in ("orc_sog_F", "orc_sog_dF"):
+                getattr(L, fn).argtypes = [_pd, _pd, _i32, _d]
+                getattr(L, fn).restype = _d
+            L.orc_sog_omega0.argtypes = [_d, _d, _i32, _d]
+            L.orc_sog_omega0.restype = _d
+            L.orc_sog_solve.argtypes = [_d, _d, _i32, _pd, _pd]
+            L.orc_sog_solve.restype = C.c_int
+            L.orc_bsa.argtypes = [_d, _d, _d]
+            L.orc_bsa.restype = _d
+            L.orc_ftilde.argtypes = [_pd, _pd, _i32, _d]
+            L.orc_ftilde.restype = _d
+            L.orc_H.argtypes = [_d, _d, C.c_int]
+            L.orc_H.restype = _d
+            L.orc_S.argtypes = [_pd, _pd, _i32, _pd]
+            L.orc_S.restype = _d
+            L.orc_proposal_q1.argtypes = [_i32, _d, _d]
+            L.orc_proposal_q1.restype = _d
+            L.orc_philox4x64_10.argtypes = [C.POINTER(_u64), C.POINTER(_u64), C.POINTER(_u64)]
+            L.orc_mh_chain.argtypes = [_pd, _pd, _i32, _pd, _u64, _u64, _i64, _pi32]
+            L.orc_mh_chain.restype = _i64
+            L.orc_kseq.argtypes = [_pd, _pd, _i32, _pd, _u64, _i64, _i64, _pi32]
+            L.orc_kseq.restype = _i64
+            L.orc_wrap.argtypes = [_i64, _pd, _pd]
+            L.orc_cell_list.argtypes = [_i64, _pd, _pd, _d, _pi32, _pi32, _pi32, _pi32]
+            L.orc_cell_list.restype = C.c_int
+            near = [_i64, _pd, _pd, C.POINTER(OrcSys), _pd, _pd, _pd, _pi32]
+            L.orc_near_direct.argtypes = near
+            L.orc_near_cells.argtypes = near
+            L.orc_near_cells.restype = C.c_int
+            L.orc_far_exact.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), _d, _pd, _pd]
+            L.orc_far_exact.restype = _i64
+            L.orc_rho.argtypes = [_i64, _pd, _pd, _pd, _i32, _pi32, _pd]
+            L.orc_far_rb.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _pd, _pd, _pd]
+            L.orc_self_energy.argtypes = [_i64, _pd, C.POINTER(OrcSys)]
+            L.orc_self_energy.restype = _d
+            L.orc_forces.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _pd,
+                                     C.POINTER(OrcEnergies)]
+            L.orc_forces.restype = C.c_int
+            L.orc_md.argtypes = [_i64, _pd, _pd, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _i64,
+                                 _d, _d, _d, _d, C.c_int, C.POINTER(OrcEnergies)]
+            L.orc_md.restype = C.c_int
+            L.orc_num_threads.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a, ct=_pd):
+    return a.ctypes.data_as(ct)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32a(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ---------------------------------------------------------------- SOG (Sec. 2)
+
+class SOG:
+    """Sum-of-Gaussians far kernel F_M(r) = sum_{l=0}^{M} w_l exp(-r^2/s_l^2)
+    (Eqs. 2.6-2.7) with the C0/C1-tuned narrowest weight w_0 (Eq. 2.9)."""
+
+    def __init__(self, b: float, sigma: float, omega0: float, M: int):
+        self.b, self.sigma, self.omega0, self.M = float(b), float(sigma), float(omega0), int(M)
+        self.omega = np.zeros(M + 1)
+        self.s = np.zeros(M + 1)
+        lib().orc_sog_coeffs(self.b, self.sigma, self.M, _p(self.omega), _p(self.s))
+        self.omega_bsa0 = float(self.omega[0])
+        self.omega[0] = self.omega0
+
+    @classmethod
+    def solve(cls, b: float, rc: float, M: int) -> "SOG":
+        sig, w0 = _d(), _d()
+        rc_ = lib().orc_sog_solve(float(b), float(rc), int(M), C.byref(sig), C.byref(w0))
+        if rc_ != 0:
+            raise ValueError("no C0/C1 root for these (b, r_c, M)")
+        return cls(b, sig.value, w0.value, M)
+
+    def F(self, r):
+        return np.array([lib().orc_sog_F(_p(self.omega), _p(self.s), self.M, float(x))
+                         for x in np.atleast_1d(r)])
+
+    def dF(self, r):
+        return np.array([lib().orc_sog_dF(_p(self.omega), _p(self.s), self.M, float(x))
+                         for x in np.atleast_1d(r)])
+
+    def ftilde(self, k2):
+        return np.array([lib().orc_ftilde(_p(self.omega), _p(self.s), self.M, float(x))
+                         for x in np.atleast_1d(k2)])
+
+    def S(self, L):
+        L = _f64(L)
+        return lib().orc_S(_p(self.omega), _p(self.s), self.M, _p(L))
+
+
+def sog_omega0(b, sigma, M, rc):
+    return lib().orc_sog_omega0(float(b), float(sigma), int(M), float(rc))
+
+
+def bsa(b, sigma, r):
+    return lib().orc_bsa(float(b), float(sigma), float(r))
+
+
+def H(s, L, dual=-1):
+    return lib().orc_H(float(s), float(L), int(dual))
+
+
+def proposal_q1(m, s0, Ld):
+    return lib().orc_proposal_q1(int(m), float(s0), float(Ld))
+
+
+# ----------------------------------------------------------- sampler (Sec. 3.3)
+
+def philox4x64_10(ctr, key):
+    c = (_u64 * 4)(*[int(v) & (2**64 - 1) for v in ctr])
+    k = (_u64 * 2)(*[int(v) & (2**64 - 1) for v in key])
+    o = (_u64 * 4)()
+    lib().orc_philox4x64_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def mh_chain(sog: SOG, L, seed: int, chain: int, length: int):
+    L = _f64(L)
+    out = np.zeros((length, 3), dtype=np.int32)
+    it = lib().orc_mh_chain(_p(sog.omega), _p(sog.s), sog.M, _p(L), int(seed), int(chain),
+                            int(length), _p(out, _pi32))
+    if it < 0:
+        raise RuntimeError("MH chain failed to start")
+    return out, int(it)
+
+
+def kseq(sog: SOG, L, seed: int, n_chains: int, chain_len: int):
+    """Frequency sequence of Algorithm 1 from n_chains independent chains."""
+    L = _f64(L)
+    out = np.zeros((n_chains * chain_len, 3), dtype=np.int32)
+    it = lib().orc_kseq(_p(sog.omega), _p(sog.s), sog.M, _p(L), int(seed), int(n_chains),
+                        int(chain_len), _p(out, _pi32))
+    if it < 0:
+        raise RuntimeError("MH chain failed to start")
+    return out
+
+
+# ------------------------------------------------------------ forces (Sec. 3)
+
+class System:
+    """Box, SOG kernel, cutoff and pair parameters for the force routines."""
+
+    def __init__(self, L, sog: SOG, rc: float, lB: float = 1.0, wca_sigma: float = 0.0,
+                 wca_eps: float = 0.0):
+        self.L = _f64(L)
+        self.sog = sog
+        self.rc, self.lB = float(rc), float(lB)
+        self.c = OrcSys((_d * 3)(*self.L), sog.M, _p(sog.omega), _p(sog.s), self.rc, self.lB,
+                        float(wca_sigma), float(wca_eps))
+
+    @property
+    def V(self):
+        return float(np.prod(self.L))
+
+    def S(self):
+        return self.sog.S(self.L)
+
+
+def wrap(x, L):
+    x = _f64(x).copy()
+    L = _f64(L)
+    lib().orc_wrap(x.shape[0], _p(x), _p(L))
+    return x
+
+
+def cell_list(x, L, rc):
+    x = _f64(x)
+    L = _f64(L)
+    n = x.shape[0]
+    nc = np.zeros(3, dtype=np.int32)
+    ncmax = int(np.prod(np.maximum(np.floor(L / rc), 1)))
+    cell_of = np.zeros(n, dtype=np.int32)
+    start = np.zeros(ncmax + 1, dtype=np.int32)
+    perm = np.zeros(n, dtype=np.int32)
+    if lib().orc_cell_list(n, _p(x), _p(L), float(rc), _p(nc, _pi32), _p(cell_of, _pi32),
+                           _p(start, _pi32), _p(perm, _pi32)) != 0:
+        raise ValueError("fewer than 3 cells per side")
+    return nc, cell_of, start, perm
+
+
+def near(sys_: System, q, x, method="cells"):
+    q, x = _f64(q), _f64(x)
+    n = x.shape[0]
+    f = np.zeros((n, 3))
+    un, uw = _d(), _d()
+    nbr = np.zeros(n, dtype=np.int32)
+    if method == "direct":
+        lib().orc_near_direct(n, _p(q), _p(x), C.byref(sys_.c), _p(f), C.byref(un), C.byref(uw),
+                              _p(nbr, _pi32))
+    else:
+        if lib().orc_near_cells(n, _p(q), _p(x), C.byref(sys_.c), _p(f), C.byref(un),
+                                C.byref(uw), _p(nbr, _pi32)) != 0:
+            raise ValueError("fewer than 3 cells per side")
+    return f, un.value, uw.value, nbr
+
+
+def far_exact(sys_: System, q, x, tol=1e-16):
+    q, x = _f64(q), _f64(x)
+    f = np.zeros((x.shape[0], 3))
+    U = _d()
+    lib().orc_far_exact(x.shape[0], _p(q), _p(x), C.byref(sys_.c), float(tol), _p(f), C.byref(U))
+    return f, U.value
+
+
+def rho(q, x, L, m):
+    q, x, L, m = _f64(q), _f64(x), _f64(L), _i32a(m)
+    out = np.zeros((m.shape[0], 2))
+    lib().orc_rho(x.shape[0], _p(q), _p(x), _p(L), m.shape[0], _p(m, _pi32), _p(out))
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def far_rb(sys_: System, q, x, S, m):
+    q, x, m = _f64(q), _f64(x), _i32a(m)
+    f = np.zeros((x.shape[0], 3))
+    U = _d()
+    r = np.zeros((m.shape[0], 2))
+    lib().orc_far_rb(x.shape[0], _p(q), _p(x), C.byref(sys_.c), float(S), m.shape[0],
+                     _p(m, _pi32), _p(f), C.byref(U), _p(r))
+    return f, U.value, r[:, 0] + 1j * r[:, 1]
+
+
+def self_energy(sys_: System, q):
+    q = _f64(q)
+    return lib().orc_self_energy(q.shape[0], _p(q), C.byref(sys_.c))
+
+
+def forces(sys_: System, q, x, S=0.0, m=None):
+    """Total force and energies; m = None uses the exact far sum."""
+    q, x = _f64(q), _f64(x)
+    n = x.shape[0]
+    f = np.zeros((n, 3))
+    e = OrcEnergies()
+    if m is None:
+        rc_ = lib().orc_forces(n, _p(q), _p(x), C.byref(sys_.c), 0.0, 0, None, _p(f), C.byref(e))
+    else:
+        m = _i32a(m)
+        rc_ = lib().orc_forces(n, _p(q), _p(x), C.byref(sys_.c), float(S), m.shape[0],
+                               _p(m, _pi32), _p(f), C.byref(e))
+    if rc_ != 0:
+        raise ValueError("fewer than 3 cells per side")
+    return f, e.as_dict()
+
+
+def md(sys_: System, q, x, v, S, P, kseq_, nsteps, dt, mass=1.0, T0=1.0, tau=0.0, f=None):
+    """Velocity-Verlet run of Algorithm 1; returns (x, v, f, per-step energies).
+    P = 0 uses the exact far sum (kseq_ ignored)."""
+    q = _f64(q)
+    x = _f64(x).copy()
+    v = _f64(v).copy()
+    n = x.shape[0]
+    have = f is not None
+    f = _f64(f).copy() if have else np.zeros((n, 3))
+    es = (OrcEnergies * max(int(nsteps), 1))()
+    ks = _i32a(kseq_ if kseq_ is not None else np.zeros((1, 3)))
+    rc_ = lib().orc_md(n, _p(q), _p(x), _p(v), _p(f), C.byref(sys_.c), float(S), int(P),
+                       _p(ks, _pi32), int(nsteps), float(dt), float(mass), float(T0), float(tau),
+                       int(have), es)
+    if rc_ != 0:
+        raise ValueError("fewer than 3 cells per side")
+    return x, v, f, [es[t].as_dict() for t in range(int(nsteps))]
+
+
+def num_threads():
+    return int(lib().orc_num_threads())

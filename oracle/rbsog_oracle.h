@@ -1,0 +1,100 @@
+/*
+ * FP64 CPU oracle for the random batch sum-of-Gaussians (RBSOG) force
+ * evaluation and velocity-Verlet step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the judge the CUDA path is
+ * compared against.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark load it; the product library never links, calls or
+ * includes anything here, and nothing here includes the product's headers.
+ *
+ * Every function follows the paper's formulas in their plain form (no
+ * blocking, no fused kernels, no precision tricks).  Where the printed
+ * formula is wrong or ambiguous, the reading taken is stated at the
+ * function.  Parity status per function:
+ *   - all functions declared here are pinned by tests under -m "not gpu"
+ *     (closed forms, Table 1, Ewald, Madelung, finite differences,
+ *     invariants, brute force, chi-square).
+ */
+#ifndef RBSOG_ORACLE_H
+#define RBSOG_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* System description shared by the force routines of the oracle. */
+typedef struct {
+    double L[3];          /* periodic box edges                               */
+    int32_t M;            /* last Gaussian index; the SOG has M+1 terms       */
+    const double *omega;  /* [M+1] Gaussian weights omega_l                   */
+    const double *s;      /* [M+1] Gaussian widths s_l                        */
+    double rc;            /* near-field cutoff r_c                            */
+    double lB;            /* Coulomb prefactor (Bjerrum length x kT)          */
+    double wca_sigma;     /* WCA sigma; 0 disables the soft repulsion         */
+    double wca_eps;       /* WCA epsilon                                      */
+} orc_sys;
+
+/* Energies of one force evaluation; every Coulomb term already carries lB. */
+typedef struct {
+    double U_near;   /* (1/2) sum_ij q_i q_j N(r_ij), r_ij < r_c              */
+    double U_far;    /* U*_F: exact Fourier sum or its random-batch estimate  */
+    double U_self;   /* (1/2) F_M(0) sum_i q_i^2                              */
+    double U_wca;    /* soft-repulsion energy                                 */
+    double K;        /* kinetic energy (only filled by the MD driver)         */
+    double T;        /* instantaneous temperature 2K/(3N-3)                   */
+} orc_energies;
+
+/* ---- sum-of-Gaussians decomposition (Sec. 2, Eqs. 2.5-2.11) ------------- */
+void   orc_sog_coeffs(double b, double sigma, int32_t M, double *omega, double *s);
+double orc_sog_F(const double *omega, const double *s, int32_t M, double r);
+double orc_sog_dF(const double *omega, const double *s, int32_t M, double r);
+double orc_sog_omega0(double b, double sigma, int32_t M, double rc);
+int    orc_sog_solve(double b, double rc, int32_t M, double *sigma, double *omega0);
+double orc_bsa(double b, double sigma, double r);
+
+/* ---- Fourier side (Eqs. 3.4-3.5, 3.16-3.22) ----------------------------- */
+double orc_ftilde(const double *omega, const double *s, int32_t M, double k2);
+double orc_H(double s, double L, int dual);
+double orc_S(const double *omega, const double *s, int32_t M, const double L[3]);
+double orc_proposal_q1(int32_t m, double s0, double Ld);
+
+/* ---- counter-based generator and the Metropolis-Hastings sampler -------- */
+void    orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+int64_t orc_mh_chain(const double *omega, const double *s, int32_t M, const double L[3],
+                     uint64_t seed, uint64_t chain, int64_t len, int32_t *m_out);
+int64_t orc_kseq(const double *omega, const double *s, int32_t M, const double L[3],
+                 uint64_t seed, int64_t n_chains, int64_t chain_len, int32_t *m_out);
+
+/* ---- cell list and near field (Sec. 3.1, Eq. 3.9 first line) ------------ */
+void orc_wrap(int64_t n, double *x, const double L[3]);
+int  orc_cell_list(int64_t n, const double *x, const double L[3], double rc,
+                   int32_t *ncell, int32_t *cell_of, int32_t *cell_start, int32_t *perm);
+void orc_near_direct(int64_t n, const double *q, const double *x, const orc_sys *sys,
+                     double *f, double *U_near, double *U_wca, int32_t *nbr);
+int  orc_near_cells(int64_t n, const double *q, const double *x, const orc_sys *sys,
+                    double *f, double *U_near, double *U_wca, int32_t *nbr);
+
+/* ---- far field (Eq. 3.9 second line; Eq. 3.24) ------------------------- */
+int64_t orc_far_exact(int64_t n, const double *q, const double *x, const orc_sys *sys,
+                      double tol, double *f, double *U_star);
+void orc_rho(int64_t n, const double *q, const double *x, const double L[3],
+             int32_t P, const int32_t *m, double *rho);
+void orc_far_rb(int64_t n, const double *q, const double *x, const orc_sys *sys,
+                double S, int32_t P, const int32_t *m, double *f, double *U_rb, double *rho);
+double orc_self_energy(int64_t n, const double *q, const orc_sys *sys);
+
+/* ---- total force and the MD driver (Algorithm 1) ------------------------ */
+int  orc_forces(int64_t n, const double *q, const double *x, const orc_sys *sys,
+                double S, int32_t P, const int32_t *m, double *f, orc_energies *e);
+int  orc_md(int64_t n, const double *q, double *x, double *v, double *f,
+            const orc_sys *sys, double S, int32_t P, const int32_t *kseq,
+            int64_t nsteps, double dt, double mass, double T0, double tau,
+            int have_force, orc_energies *e_steps);
+
+int  orc_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
