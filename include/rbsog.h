@@ -1,0 +1,180 @@
+/*
+ * rbsog.h -- C ABI of the GB300 (sm_103a) random batch sum-of-Gaussians
+ * (RBSOG) force evaluation and velocity-Verlet integrator.
+ *
+ * Method: Liang, Xu, Xu, Zhao, "Random batch sum-of-Gaussians method for
+ * molecular dynamics simulations of particle systems" (arXiv:2205.13824).
+ * Section and equation numbers below refer to that paper.
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an rbsog_status; nothing throws or aborts across the
+ *     ABI.  On failure rbsog_last_error() describes the cause.
+ *   - Arrays of particle vectors are row-major [n][3] doubles in the caller's
+ *     particle order.  Pointers may be host memory (pageable or pinned) or
+ *     device memory of the context's device: copies use cudaMemcpyDefault.
+ *   - The caller owns every buffer it passes; the library copies what it
+ *     needs and never frees or retains caller memory after the call returns.
+ *   - Work is enqueued on the CUDA stream given to rbsog_create (0 = the
+ *     legacy default stream).  Internally the context runs on its own stream
+ *     and orders itself after / before the caller's stream with events.
+ *     Calls that return host values (energies, state into host memory,
+ *     statuses of device checks) synchronise with that work.
+ *   - Units are the caller's; all Coulomb terms are multiplied by
+ *     coulomb_prefactor (Bjerrum length x kT in reduced units).
+ */
+#ifndef RBSOG_H
+#define RBSOG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbsog_ctx rbsog_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    RBSOG_OK = 0,
+    RBSOG_EINVAL = 1,   /* invalid argument or parameter set                 */
+    RBSOG_ENOMEM = 2,   /* device or host allocation failed                  */
+    RBSOG_ECUDA = 3,    /* a CUDA runtime call failed                        */
+    RBSOG_ESTATE = 4,   /* call out of order (e.g. step before set_state)    */
+    RBSOG_ENUMERIC = 5, /* non-finite force found on the device              */
+    RBSOG_ETIMEOUT = 6  /* a bounded device wait gave up                     */
+} rbsog_status;
+
+typedef enum {
+    RBSOG_FP64 = 0,  /* plain FP64 everywhere: the comparator path           */
+    RBSOG_FP32C = 1  /* 32-bit fixed-point positions, FP32 pair and sincos
+                        arithmetic, compensated FP32 rho(k) partials; FP64
+                        for the cross-block rho combine, energies and the
+                        integrator's state                                  */
+} rbsog_precision;
+
+/* Parameters of one system (Sec. 2 and 3; Algorithm 1). */
+typedef struct {
+    double L[3];              /* periodic cuboid edges L_x, L_y, L_z (Sec. 2)                */
+    double b;                 /* SOG base b > 1 (Eq. 2.5)                                     */
+    double sigma;             /* SOG width sigma; <= 0: solve sigma and omega0 jointly from
+                                 the C0/C1 conditions at r_c (Eqs. 2.10-2.11)                 */
+    double omega0;            /* narrowest weight; <= 0 with sigma > 0: C0 value of Eq. 2.11   */
+    int32_t M;                /* last Gaussian index, M+1 terms (Eq. 2.8), 0 <= M < 128       */
+    double r_c;               /* near cutoff (Eq. 2.7); floor(L_d / r_c) >= 3, r_c < L_d / 2 */
+    int32_t P;                /* frequencies per step, the batch size of Eq. 3.24, >= 1      */
+    double coulomb_prefactor; /* multiplies every Coulomb term                                */
+    double wca_sigma;         /* soft repulsion 4e[(s/r)^12-(s/r)^6]+e for r < 2^(1/6) s;
+                                 0 disables it                                               */
+    double wca_eps;
+    double dt;                /* velocity-Verlet step                                         */
+    double mass;              /* particle mass (all particles)                                */
+    double T_target;          /* Berendsen target temperature (k_B = 1)                        */
+    double tau_T;             /* Berendsen time constant; <= 0: NVE                            */
+    uint64_t seed;            /* key of the counter-based generator of the sampler            */
+    int64_t n_ksets;          /* k-sets to pre-sample (Algorithm 1 line 2); one is consumed
+                                 per force evaluation; >= 1                                   */
+    int32_t chain_len;        /* samples per Metropolis-Hastings chain; 0: 256                  */
+    int32_t precision;        /* rbsog_precision                                               */
+} rbsog_params;
+
+/* Energies of the last force evaluation (Eqs. 3.1, 3.6-3.8) and kinetic state. */
+typedef struct {
+    double U_near; /* (1/2) sum q_i q_j N(r_ij) over pairs within r_c                   */
+    double U_far;  /* random-batch estimate (pi^{3/2} S / (2 P V)) sum_eta |rho(k_eta)|^2 */
+    double U_self; /* (1/2) F_M(0) sum q_i^2                                              */
+    double U_wca;  /* soft repulsion                                                      */
+    double K;      /* kinetic energy after the last completed step                        */
+    double T;      /* 2K / (3N - 3)                                                       */
+} rbsog_energies;
+
+/* Solved SOG decomposition (Eqs. 2.8-2.11) and the normaliser S (Eq. 3.16). */
+typedef struct {
+    double sigma, omega0, S;
+    int32_t M;
+    int32_t ncell[3];         /* cell grid of the near-field cell list                      */
+    int64_t n_chains;         /* sampler chains; chain c fills sequence entries
+                                 [c * chain_len, (c + 1) * chain_len)                       */
+    int32_t chain_len;
+} rbsog_info;
+
+/* Create a context for n >= 2 particles on CUDA device `device`; `stream`
+ * is a cudaStream_t (or NULL for the legacy default stream).  *out is set
+ * to NULL on failure. */
+rbsog_status rbsog_create(rbsog_ctx **out, int64_t n, int device, void *stream);
+
+/* Validate p, solve the SOG parameters if asked (Eqs. 2.10-2.11, host FP64),
+ * compute S (Eq. 3.16), and pre-sample the frequency sequence of
+ * Algorithm 1 on the device (independent Metropolis-Hastings chains,
+ * Sec. 3.3).  Rejects (RBSOG_EINVAL): b <= 1, sigma/omega0 invalid, M outside
+ * [0, 127], P < 1, n_ksets < 1, r_c <= 0, r_c >= L_d / 2, fewer than 3 cells
+ * per side, mass <= 0, an unknown precision.  Resets the k-set cursor. */
+rbsog_status rbsog_set_params(rbsog_ctx *ctx, const rbsog_params *p);
+
+/* Parameters as solved by the last rbsog_set_params.  omega and s (length
+ * M+1, host) may be NULL. */
+rbsog_status rbsog_get_info(const rbsog_ctx *ctx, rbsog_info *info, double *omega, double *s);
+
+/* Load charges q[n], positions x[n][3] (folded into the box) and
+ * velocities v[n][3] (NULL: zero).  Rejects a non-neutral charge vector,
+ * |sum q| > 1e-12 sum |q| (the method assumes neutrality, Sec. 2).
+ * Invalidates the stored forces: the next step first evaluates them. */
+rbsog_status rbsog_set_state(rbsog_ctx *ctx, const double *q, const double *x, const double *v);
+
+/* One force evaluation F = F_N + F*_F (+ WCA) at the current positions
+ * (Eq. 3.9 first line, Eq. 3.24).  m_kset: P integer frequency vectors
+ * m[P][3] (k = 2 pi m / L) in host or device memory, or NULL to take the
+ * next k-set of the pre-sampled sequence (advancing the cursor).  f_out
+ * ([n][3], host or device) and e_out (host) may be NULL.  The forces are
+ * also kept as the context's current forces. */
+rbsog_status rbsog_compute_forces(rbsog_ctx *ctx, const int32_t *m_kset, double *f_out,
+                                  rbsog_energies *e_out);
+
+/* Advance nsteps velocity-Verlet steps of Algorithm 1, each consuming the
+ * next k-set; with tau_T > 0 velocities are rescaled by
+ * sqrt(1 + dt/tau_T (T_target/T - 1)) after the second half kick.  Enqueued
+ * asynchronously (replayed from a CUDA graph of one step when profiling is
+ * off).  Returns RBSOG_EINVAL if the sequence would run out of k-sets. */
+rbsog_status rbsog_step(rbsog_ctx *ctx, int64_t nsteps);
+
+/* Copy the current state out (any pointer may be NULL; host or device):
+ * x[n][3] folded positions, v[n][3], f[n][3] current forces, *step the
+ * number of completed steps.  Synchronises and reports RBSOG_ENUMERIC if a
+ * non-finite force was produced since the last check. */
+rbsog_status rbsog_get_state(rbsog_ctx *ctx, double *x, double *v, double *f, int64_t *step);
+
+/* Energies of the last force evaluation and the kinetic energy (host). */
+rbsog_status rbsog_get_energies(rbsog_ctx *ctx, rbsog_energies *e);
+
+/* Copy k-sets [set0, set0 + nsets) of the pre-sampled sequence as
+ * m[nsets * P][3] int32 (host or device). */
+rbsog_status rbsog_get_kseq(rbsog_ctx *ctx, int64_t set0, int64_t nsets, int32_t *m_out);
+
+/* Structure factors rho(k) = sum_j q_j e^{i k . r_j} (Eq. 3.4) at the current
+ * positions for P integer vectors m[P][3] (host or device); rho_out is
+ * [P][2] (Re, Im) doubles, host or device.  Uses the same sweep and combine
+ * kernels as the force path. */
+rbsog_status rbsog_rho(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *rho_out);
+
+/* Cell list of the current positions (the near-field traversal structure):
+ * cell_start[ncell + 1] offsets, perm[n] particle index in cell order
+ * (increasing index within a cell), nbr[n] number of partners within r_c
+ * per particle (caller order).  Any pointer may be NULL. */
+rbsog_status rbsog_get_cells(rbsog_ctx *ctx, int32_t *cell_start, int32_t *perm, int32_t *nbr);
+
+/* Kernel-level timing: when on, launches run eagerly with a CUDA event pair
+ * around each kernel; rbsog_get_profile returns, per kernel name, the launch
+ * count and the summed device time in ms since profiling was switched on.
+ * names: array of `cap` char[32] slots. Returns the number of kernels. */
+rbsog_status rbsog_set_profiling(rbsog_ctx *ctx, int on);
+rbsog_status rbsog_get_profile(rbsog_ctx *ctx, int32_t cap, char (*names)[32], int64_t *launches,
+                               double *ms, int32_t *count);
+
+/* Description of the last error on this context (never NULL). */
+const char *rbsog_last_error(const rbsog_ctx *ctx);
+
+/* Release all device and host resources of the context (NULL is a no-op). */
+rbsog_status rbsog_destroy(rbsog_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBSOG_H */

@@ -100,6 +100,9 @@ def lib():
             L.orc_far_exact.restype = _i64
             L.orc_rho.argtypes = [_i64, _pd, _pd, _pd, _i32, _pi32, _pd]
             L.orc_far_rb.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _pd, _pd, _pd]
+            L.orc_forces_sample.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _i64,
+                                            C.POINTER(_i64), _pd]
+            L.orc_forces_sample.restype = C.c_int
             L.orc_self_energy.argtypes = [_i64, _pd, C.POINTER(OrcSys)]
             L.orc_self_energy.restype = _d
             L.orc_forces.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _pd,
@@ -129,7 +132,7 @@ def _i32a(a):
 
 class SOG:
     """Sum-of-Gaussians far kernel F_M(r) = sum_{l=0}^{M} w_l exp(-r^2/s_l^2)
-    (Eqs. 2.6-2.7) with the C0/C1-tuned narrowest weight w_0 (Eq. 2.9)."""
+    (Eqs. 2.8-2.9) with the C0/C1-tuned narrowest weight w_0 (Eq. 2.11)."""
 
     def __init__(self, b: float, sigma: float, omega0: float, M: int):
         self.b, self.sigma, self.omega0, self.M = float(b), float(sigma), float(omega0), int(M)
@@ -293,6 +296,17 @@ def far_rb(sys_: System, q, x, S, m):
     lib().orc_far_rb(x.shape[0], _p(q), _p(x), C.byref(sys_.c), float(S), m.shape[0],
                      _p(m, _pi32), _p(f), C.byref(U), _p(r))
     return f, U.value, r[:, 0] + 1j * r[:, 1]
+
+
+def forces_sample(sys_: System, q, x, S, m, idx):
+    """Random-batch total force on the particles idx only (rho over all)."""
+    q, x, m = _f64(q), _f64(x), _i32a(m)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    f = np.zeros((len(idx), 3))
+    if lib().orc_forces_sample(x.shape[0], _p(q), _p(x), C.byref(sys_.c), float(S), m.shape[0],
+                               _p(m, _pi32), len(idx), _p(idx, C.POINTER(_i64)), _p(f)) != 0:
+        raise ValueError("fewer than 3 cells per side")
+    return f
 
 
 def self_energy(sys_: System, q):

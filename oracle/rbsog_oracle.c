@@ -647,6 +647,67 @@ void orc_far_rb(int64_t n, const double *q, const double *x, const orc_sys *sys,
     free(rho);
 }
 
+/* Total force on a subset of particles only (idx[0..ns)), for checks at sizes
+ * where the O(N) sweep over all particles is affordable but N per-particle
+ * force sums are not.  Near field: minimum-image scan over the 27 cells
+ * around each sampled particle; far field: Eq. 3.24 with rho from all
+ * particles.  f is [ns][3]. */
+int orc_forces_sample(int64_t n, const double *q, const double *x, const orc_sys *sys, double S,
+                      int32_t P, const int32_t *m, int64_t ns, const int64_t *idx, double *f) {
+    int32_t nc3[3];
+    int32_t *cell_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t ncmax = 1;
+    for (int d = 0; d < 3; ++d) {
+        int64_t c = (int64_t)floor(sys->L[d] / sys->rc);
+        ncmax *= c > 0 ? c : 1;
+    }
+    int32_t *start = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ncmax + 1));
+    if (orc_cell_list(n, x, sys->L, sys->rc, nc3, cell_of, start, perm) != 0) {
+        free(cell_of); free(perm); free(start);
+        return -1;
+    }
+    const double V = sys->L[0] * sys->L[1] * sys->L[2];
+    const double c = pow(M_PI, 1.5) * S / ((double)P * V);
+    double *rho = (double *)malloc(sizeof(double) * 2 * (size_t)(P > 0 ? P : 1));
+    orc_rho(n, q, x, sys->L, P, m, rho);
+    const double rc2 = sys->rc * sys->rc;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < ns; ++t) {
+        const int64_t i = idx[t];
+        int32_t ci = cell_of[i];
+        int32_t cx = ci % nc3[0], cy = (ci / nc3[0]) % nc3[1], cz = ci / (nc3[0] * nc3[1]);
+        double fi[3] = {0.0, 0.0, 0.0}, un = 0.0, uw = 0.0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int32_t o = (((cz + dz + nc3[2]) % nc3[2]) * nc3[1] + (cy + dy + nc3[1]) % nc3[1]) * nc3[0] +
+                                (cx + dx + nc3[0]) % nc3[0];
+                    for (int32_t u = start[o]; u < start[o + 1]; ++u) {
+                        int32_t j = perm[u];
+                        if (j == i) continue;
+                        double d[3];
+                        double r2 = min_image(x + 3 * i, x + 3 * j, sys->L, d);
+                        if (r2 < rc2) near_pair(sys, q[i], q[j], d, r2, fi, &un, &uw);
+                    }
+                }
+        double ff[3] = {0.0, 0.0, 0.0};
+        for (int32_t e = 0; e < P; ++e) {
+            double k[3];
+            for (int d = 0; d < 3; ++d) k[d] = 2.0 * M_PI * (double)m[3 * e + d] / sys->L[d];
+            double th = k[0] * x[3 * i] + k[1] * x[3 * i + 1] + k[2] * x[3 * i + 2];
+            double im = cos(th) * rho[2 * e + 1] - sin(th) * rho[2 * e];
+            ff[0] += k[0] * im;
+            ff[1] += k[1] * im;
+            ff[2] += k[2] * im;
+        }
+        double g = -sys->lB * q[i] * c;
+        for (int d = 0; d < 3; ++d) f[3 * t + d] = fi[d] + g * ff[d];
+    }
+    free(rho); free(cell_of); free(perm); free(start);
+    return 0;
+}
+
 /* Gaussian self energy, (1/2) F_M(0) sum_i q_i^2 = (1/2)(sum_l w_l) sum_i q_i^2
  * (Eq. 3.8; the closed form printed there holds for the unmodified w_0). */
 double orc_self_energy(int64_t n, const double *q, const orc_sys *sys) {

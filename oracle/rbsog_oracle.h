@@ -83,6 +83,8 @@ void orc_rho(int64_t n, const double *q, const double *x, const double L[3],
 void orc_far_rb(int64_t n, const double *q, const double *x, const orc_sys *sys,
                 double S, int32_t P, const int32_t *m, double *f, double *U_rb, double *rho);
 double orc_self_energy(int64_t n, const double *q, const orc_sys *sys);
+int orc_forces_sample(int64_t n, const double *q, const double *x, const orc_sys *sys, double S,
+                      int32_t P, const int32_t *m, int64_t ns, const int64_t *idx, double *f);
 
 /* ---- total force and the MD driver (Algorithm 1) ------------------------ */
 int  orc_forces(int64_t n, const double *q, const double *x, const orc_sys *sys,

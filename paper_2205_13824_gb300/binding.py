@@ -1,0 +1,206 @@
+"""ctypes binding of librbsog (include/rbsog.h): argument marshalling only.
+
+Every ``rbsog_*`` function here has the name and argument order of the C
+entry point; it converts torch tensors / numpy arrays to raw pointers and
+raises ``RBSOGError`` on a non-zero status.  No arithmetic of the method
+happens in Python: if the shared library is missing the import fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librbsog.so")
+
+RBSOG_FP64 = 0
+RBSOG_FP32C = 1
+STATUS = {0: "RBSOG_OK", 1: "RBSOG_EINVAL", 2: "RBSOG_ENOMEM", 3: "RBSOG_ECUDA",
+          4: "RBSOG_ESTATE", 5: "RBSOG_ENUMERIC", 6: "RBSOG_ETIMEOUT"}
+
+# Every symbol include/rbsog.h declares.
+EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_state",
+           "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_get_energies",
+           "rbsog_get_kseq", "rbsog_rho", "rbsog_get_cells", "rbsog_set_profiling",
+           "rbsog_get_profile", "rbsog_last_error", "rbsog_destroy")
+
+
+class RBSOGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rbsog_params(C.Structure):
+    _fields_ = [("L", C.c_double * 3), ("b", C.c_double), ("sigma", C.c_double),
+                ("omega0", C.c_double), ("M", C.c_int32), ("r_c", C.c_double), ("P", C.c_int32),
+                ("coulomb_prefactor", C.c_double), ("wca_sigma", C.c_double),
+                ("wca_eps", C.c_double), ("dt", C.c_double), ("mass", C.c_double),
+                ("T_target", C.c_double), ("tau_T", C.c_double), ("seed", C.c_uint64),
+                ("n_ksets", C.c_int64), ("chain_len", C.c_int32), ("precision", C.c_int32)]
+
+
+class rbsog_energies(C.Structure):
+    _fields_ = [("U_near", C.c_double), ("U_far", C.c_double), ("U_self", C.c_double),
+                ("U_wca", C.c_double), ("K", C.c_double), ("T", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class rbsog_info(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("omega0", C.c_double), ("S", C.c_double),
+                ("M", C.c_int32), ("ncell", C.c_int32 * 3), ("n_chains", C.c_int64),
+                ("chain_len", C.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    st = C.c_int
+    sig = {
+        "rbsog_create": [C.POINTER(P), C.c_int64, C.c_int, P],
+        "rbsog_set_params": [P, C.POINTER(rbsog_params)],
+        "rbsog_get_info": [P, C.POINTER(rbsog_info), P, P],
+        "rbsog_set_state": [P, P, P, P],
+        "rbsog_compute_forces": [P, P, P, C.POINTER(rbsog_energies)],
+        "rbsog_step": [P, C.c_int64],
+        "rbsog_get_state": [P, P, P, P, C.POINTER(C.c_int64)],
+        "rbsog_get_energies": [P, C.POINTER(rbsog_energies)],
+        "rbsog_get_kseq": [P, C.c_int64, C.c_int64, P],
+        "rbsog_rho": [P, P, C.c_int32, P],
+        "rbsog_get_cells": [P, P, P, P],
+        "rbsog_set_profiling": [P, C.c_int],
+        "rbsog_get_profile": [P, C.c_int32, P, P, P, C.POINTER(C.c_int32)],
+        "rbsog_destroy": [P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = st
+    lib.rbsog_last_error.argtypes = [P]
+    lib.rbsog_last_error.restype = C.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _ptr(a):
+    """Raw address of a torch tensor, numpy array or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _check(ctx, status):
+    if status != 0:
+        msg = _lib.rbsog_last_error(ctx)
+        raise RBSOGError(status, msg.decode() if msg else "")
+
+
+def rbsog_create(n: int, device: int = 0, stream: int | None = None):
+    ctx = C.c_void_p()
+    s = _lib.rbsog_create(C.byref(ctx), int(n), int(device), stream)
+    if s != 0:
+        raise RBSOGError(s, "rbsog_create failed")
+    return ctx
+
+
+def rbsog_set_params(ctx, p: rbsog_params):
+    _check(ctx, _lib.rbsog_set_params(ctx, C.byref(p)))
+
+
+def rbsog_get_info(ctx, M: int | None = None):
+    info = rbsog_info()
+    om = s = None
+    if M is not None:
+        om = np.zeros(M + 1)
+        s = np.zeros(M + 1)
+    _check(ctx, _lib.rbsog_get_info(ctx, C.byref(info), _ptr(om), _ptr(s)))
+    return info, om, s
+
+
+def rbsog_set_state(ctx, q, x, v=None):
+    _check(ctx, _lib.rbsog_set_state(ctx, _ptr(q), _ptr(x), _ptr(v)))
+
+
+def rbsog_compute_forces(ctx, m_kset=None, f_out=None, want_energies=True):
+    e = rbsog_energies() if want_energies else None
+    _check(ctx, _lib.rbsog_compute_forces(ctx, _ptr(m_kset), _ptr(f_out),
+                                          C.byref(e) if e is not None else None))
+    return e.as_dict() if e is not None else None
+
+
+def rbsog_step(ctx, nsteps: int):
+    _check(ctx, _lib.rbsog_step(ctx, int(nsteps)))
+
+
+def rbsog_get_state(ctx, x=None, v=None, f=None):
+    step = C.c_int64()
+    _check(ctx, _lib.rbsog_get_state(ctx, _ptr(x), _ptr(v), _ptr(f), C.byref(step)))
+    return step.value
+
+
+def rbsog_get_energies(ctx):
+    e = rbsog_energies()
+    _check(ctx, _lib.rbsog_get_energies(ctx, C.byref(e)))
+    return e.as_dict()
+
+
+def rbsog_get_kseq(ctx, set0: int, nsets: int, m_out):
+    _check(ctx, _lib.rbsog_get_kseq(ctx, int(set0), int(nsets), _ptr(m_out)))
+
+
+def rbsog_rho(ctx, m, rho_out):
+    P = int(m.shape[0])
+    _check(ctx, _lib.rbsog_rho(ctx, _ptr(m), P, _ptr(rho_out)))
+
+
+def rbsog_get_cells(ctx, cell_start=None, perm=None, nbr=None):
+    _check(ctx, _lib.rbsog_get_cells(ctx, _ptr(cell_start), _ptr(perm), _ptr(nbr)))
+
+
+def rbsog_set_profiling(ctx, on: bool):
+    _check(ctx, _lib.rbsog_set_profiling(ctx, 1 if on else 0))
+
+
+def rbsog_get_profile(ctx, cap: int = 64):
+    names = (C.c_char * 32 * cap)()
+    launches = np.zeros(cap, dtype=np.int64)
+    ms = np.zeros(cap, dtype=np.float64)
+    cnt = C.c_int32()
+    _check(ctx, _lib.rbsog_get_profile(ctx, cap, C.cast(names, C.c_void_p), _ptr(launches),
+                                       _ptr(ms), C.byref(cnt)))
+    out = {}
+    for i in range(min(cnt.value, cap)):
+        out[bytes(names[i]).split(b"\0")[0].decode()] = (int(launches[i]), float(ms[i]))
+    return out
+
+
+def rbsog_last_error(ctx) -> str:
+    m = _lib.rbsog_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def rbsog_destroy(ctx):
+    _check(None, _lib.rbsog_destroy(ctx))

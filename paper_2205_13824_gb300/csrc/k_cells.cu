@@ -1,0 +1,154 @@
+// Device cell list for the near field: a counting sort of particles into
+// cells of side >= r_c.  Four launches:
+//   bin      one thread per particle: cell id (FP64 floor(x / h), the same
+//            decision as any IEEE evaluation) and an arrival slot from an
+//            integer atomic on the cell's counter;
+//   scan     one block, warp-shuffle exclusive scan of the counters into cell
+//            start offsets (and the counters are cleared for the next build);
+//   scatter  one thread per particle: perm_raw[start + slot] = i;
+//   order    one warp per cell: ranks the cell's members by particle index
+//            (so the order inside a cell, and everything summed in that
+//            order, is deterministic) and gathers the particle data into
+//            cell order -- FP64 (x, y, z, q) or, for the FP32C path, 32-bit
+//            fixed-point positions X_d = floor(x_d / L_d * 2^32) with an FP32
+//            charge.
+#include "rbsog_kernels.cuh"
+
+namespace rbsog {
+namespace {
+
+__global__ void __launch_bounds__(256) k_bin(int64_t n, const double4_32a *__restrict__ posq, BoxDev box,
+                                             int32_t *__restrict__ cell_of, int32_t *__restrict__ slot,
+                                             int32_t *__restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double4_32a p = posq[i];
+    const double xs[3] = {p.x, p.y, p.z};
+    int c3[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int c = (int)floor(xs[d] / box.h[d]);
+        c = c >= box.nc[d] ? box.nc[d] - 1 : c;
+        c = c < 0 ? 0 : c;
+        c3[d] = c;
+    }
+    const int cell = (c3[2] * box.nc[1] + c3[1]) * box.nc[0] + c3[0];
+    cell_of[i] = cell;
+    slot[i] = atomicAdd(&count[cell], 1);
+}
+
+// Exclusive scan of count[0..ncell) into start[0..ncell], single block of
+// 1024 threads: each thread owns a contiguous chunk, chunk sums are scanned
+// with warp shuffles, then every chunk is written out.  Clears count.
+__global__ void __launch_bounds__(1024) k_scan(int ncell, int32_t *__restrict__ count,
+                                               int32_t *__restrict__ start) {
+    __shared__ int warp_tot[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int chunk = (ncell + blockDim.x - 1) / blockDim.x;
+    const int b = tid * chunk, e = min(b + chunk, ncell);
+    int local = 0;
+    for (int j = b; j < e; ++j) local += count[j];
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        warp_tot[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    int run = incl - local + (wid > 0 ? warp_tot[wid - 1] : 0);
+    for (int j = b; j < e; ++j) {
+        const int cj = count[j];
+        start[j] = run;
+        run += cj;
+        count[j] = 0;
+    }
+    if (tid == blockDim.x - 1) start[ncell] = warp_tot[31];
+}
+
+__global__ void __launch_bounds__(256) k_scatter(int64_t n, const int32_t *__restrict__ cell_of,
+                                                 const int32_t *__restrict__ slot,
+                                                 const int32_t *__restrict__ start,
+                                                 int32_t *__restrict__ perm_raw) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    perm_raw[start[cell_of[i]] + slot[i]] = (int32_t)i;
+}
+
+__device__ __forceinline__ uint32_t to_fixed32(double x, double L) {
+    const double t = x / L * 4294967296.0;
+    const double c = t < 0.0 ? 0.0 : (t > 4294967295.0 ? 4294967295.0 : t);
+    return (uint32_t)__double2ull_rz(c);
+}
+
+// One warp per cell: rank = number of members with a smaller particle index.
+__global__ void __launch_bounds__(256) k_order_gather(int ncell, const int32_t *__restrict__ start,
+                                                      const int32_t *__restrict__ perm_raw,
+                                                      int32_t *__restrict__ perm,
+                                                      const double4_32a *__restrict__ posq, BoxDev box,
+                                                      int precision, double4_32a *__restrict__ sp64,
+                                                      uint4 *__restrict__ sp32) {
+    const int lane = threadIdx.x & 31;
+    const int cell = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (cell >= ncell) return;
+    const int b = start[cell], e = start[cell + 1], cnt = e - b;
+    for (int t = lane; t < cnt; t += 32) {
+        const int idx = perm_raw[b + t];
+        int rank = 0;
+        for (int u = 0; u < cnt; ++u) rank += (perm_raw[b + u] < idx) ? 1 : 0;
+        const int s = b + rank;
+        perm[s] = idx;
+        const double4_32a p = posq[idx];
+        if (precision == 0) {
+            sp64[s] = p;
+        } else {
+            uint4 o;
+            o.x = to_fixed32(p.x, box.L[0]);
+            o.y = to_fixed32(p.y, box.L[1]);
+            o.z = to_fixed32(p.z, box.L[2]);
+            o.w = __float_as_uint((float)p.w);
+            sp32[s] = o;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_build_cells(int64_t n, const double4_32a *posq, const BoxDev &box,
+                               const CellBuffers &cb, int precision, double4_32a *sp64, uint4 *sp32,
+                               int32_t *err_flag, cudaStream_t st, const Prof *prof) {
+    (void)err_flag;
+    const int t = 256;
+    const unsigned nb = (unsigned)((n + t - 1) / t);
+    {
+        ProfScope ps(prof, "cell_bin");
+        k_bin<<<nb, t, 0, st>>>(n, posq, box, cb.cell_of, cb.slot, cb.count);
+    }
+    {
+        ProfScope ps(prof, "cell_scan");
+        k_scan<<<1, 1024, 0, st>>>(box.ncell, cb.count, cb.start);
+    }
+    {
+        ProfScope ps(prof, "cell_scatter");
+        k_scatter<<<nb, t, 0, st>>>(n, cb.cell_of, cb.slot, cb.start, cb.perm_raw);
+    }
+    {
+        ProfScope ps(prof, "cell_order_gather");
+        const unsigned blocks = (unsigned)(((int64_t)box.ncell * 32 + t - 1) / t);
+        k_order_gather<<<blocks, t, 0, st>>>(box.ncell, cb.start, cb.perm_raw, cb.perm, posq, box,
+                                             precision, sp64, sp32);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rbsog

@@ -1,0 +1,237 @@
+// Velocity-Verlet integration (Algorithm 1, line 4) with the Berendsen
+// rescale, fixed-order energy reductions, and layout conversions between
+// the caller's [n][3] arrays and the internal 32-byte particle records.
+// All state updates are FP64 and memory-bound: one thread per particle,
+// coalesced 32-byte loads and stores.
+#include "rbsog_kernels.cuh"
+
+namespace rbsog {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double fold(double x, double L) {
+    double v = x - L * floor(x / L);
+    return v >= L ? 0.0 : v;
+}
+
+// v += dt/2 F/m ; x += dt v ; x folded into [0, L).
+__global__ void __launch_bounds__(kThreads) k_kick_drift(MdArgs a, double4_32a *__restrict__ posq,
+                                                         double4_32a *__restrict__ vel,
+                                                         const double4_32a *__restrict__ force) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= a.n) return;
+    const double4_32a f = force[i];
+    double4_32a v = vel[i];
+    double4_32a p = posq[i];
+    const double h = 0.5 * a.dt * a.inv_mass;
+    v.x += h * f.x;
+    v.y += h * f.y;
+    v.z += h * f.z;
+    p.x = fold(p.x + a.dt * v.x, a.L[0]);
+    p.y = fold(p.y + a.dt * v.y, a.L[1]);
+    p.z = fold(p.z + a.dt * v.z, a.L[2]);
+    vel[i] = v;
+    posq[i] = p;
+}
+
+// v += dt/2 F/m and the block's kinetic energy sum (fixed order).
+__global__ void __launch_bounds__(kThreads) k_kick(MdArgs a, double4_32a *__restrict__ vel,
+                                                   const double4_32a *__restrict__ force,
+                                                   double *__restrict__ kpart) {
+    __shared__ double s_red[kThreads / 32];
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    double ke = 0.0;
+    if (i < a.n) {
+        const double4_32a f = force[i];
+        double4_32a v = vel[i];
+        const double h = 0.5 * a.dt * a.inv_mass;
+        v.x += h * f.x;
+        v.y += h * f.y;
+        v.z += h * f.z;
+        vel[i] = v;
+        ke = 0.5 * a.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ke += __shfl_down_sync(0xffffffffu, ke, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = ke;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += s_red[w];
+        kpart[blockIdx.x] = t;
+    }
+}
+
+// Single block: fixed-order sums of the near-energy partials, |rho|^2 and
+// the kinetic partials; Berendsen factor; k-set cursor and step counter.
+__global__ void __launch_bounds__(1024) k_finalize(MdArgs a, const double2 *__restrict__ epart,
+                                                   const double2 *__restrict__ rho,
+                                                   const double *__restrict__ kpart, int with_kinetic,
+                                                   double *__restrict__ energy, int64_t *cursor,
+                                                   int64_t advance, int64_t *step_counter) {
+    __shared__ double s_red[4][32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double un = 0.0, uw = 0.0, r2 = 0.0, ke = 0.0;
+    for (int j = tid; j < a.n_epart; j += blockDim.x) {
+        const double2 e = epart[j];
+        un += e.x;
+        uw += e.y;
+    }
+    for (int j = tid; j < a.P; j += blockDim.x) {
+        const double2 r = rho[j];
+        r2 += r.x * r.x + r.y * r.y;
+    }
+    if (with_kinetic)
+        for (int j = tid; j < a.n_kpart; j += blockDim.x) ke += kpart[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        un += __shfl_down_sync(0xffffffffu, un, o);
+        uw += __shfl_down_sync(0xffffffffu, uw, o);
+        r2 += __shfl_down_sync(0xffffffffu, r2, o);
+        ke += __shfl_down_sync(0xffffffffu, ke, o);
+    }
+    if (lane == 0) {
+        s_red[0][wid] = un;
+        s_red[1][wid] = uw;
+        s_red[2][wid] = r2;
+        s_red[3][wid] = ke;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t[4] = {0, 0, 0, 0};
+        const int nw = blockDim.x / 32;
+        for (int q = 0; q < 4; ++q)
+            for (int w = 0; w < nw; ++w) t[q] += s_red[q][w];
+        energy[0] = t[0];
+        energy[1] = a.half_coef_U * t[2];
+        energy[2] = a.U_self;
+        energy[3] = t[1];
+        if (with_kinetic) {
+            double K = t[3];
+            double T = 2.0 * K / (3.0 * (double)a.n - 3.0);
+            double lam = 1.0;
+            if (a.tau > 0.0 && T > 0.0) {
+                lam = sqrt(1.0 + a.dt / a.tau * (a.T0 / T - 1.0));
+                K *= lam * lam;
+                T *= lam * lam;
+            }
+            energy[4] = K;
+            energy[5] = T;
+            energy[6] = lam;
+            if (step_counter) *step_counter += 1;
+        }
+        if (cursor) *cursor += advance;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_rescale(int64_t n, double4_32a *__restrict__ vel,
+                                                      const double *__restrict__ energy) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    const double lam = energy[6];
+    double4_32a v = vel[i];
+    v.x *= lam;
+    v.y *= lam;
+    v.z *= lam;
+    vel[i] = v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_pack(int64_t n, const double *__restrict__ x3,
+                                                   const double *__restrict__ q, double4_32a *__restrict__ out,
+                                                   int wrap, double Lx, double Ly, double Lz) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    double x = x3 ? x3[3 * i] : 0.0, y = x3 ? x3[3 * i + 1] : 0.0, z = x3 ? x3[3 * i + 2] : 0.0;
+    if (wrap) {
+        x = fold(x, Lx);
+        y = fold(y, Ly);
+        z = fold(z, Lz);
+    }
+    out[i] = make_double4_32a(x, y, z, q ? q[i] : 0.0);
+}
+
+__global__ void __launch_bounds__(kThreads) k_unpack(int64_t n, const double4_32a *__restrict__ in,
+                                                     double *__restrict__ x3) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    const double4_32a p = in[i];
+    x3[3 * i] = p.x;
+    x3[3 * i + 1] = p.y;
+    x3[3 * i + 2] = p.z;
+}
+
+__global__ void __launch_bounds__(kThreads) k_unsort(int64_t n, const int32_t *__restrict__ perm,
+                                                     const int32_t *__restrict__ sorted,
+                                                     int32_t *__restrict__ out) {
+    const int64_t s = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (s >= n) return;
+    out[perm[s]] = sorted[s];
+}
+
+__global__ void k_m_to_int4(int32_t P, const int32_t *__restrict__ m3, int4 *__restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    out[k] = make_int4(m3[3 * k], m3[3 * k + 1], m3[3 * k + 2], 0);
+}
+
+inline unsigned nblk(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+int kinetic_num_blocks(int64_t n) { return (int)nblk(n); }
+
+cudaError_t launch_kick_drift(const MdArgs &a, double4_32a *posq, double4_32a *vel, const double4_32a *force,
+                              cudaStream_t st, const Prof *prof) {
+    ProfScope ps(prof, "kick_drift");
+    k_kick_drift<<<nblk(a.n), kThreads, 0, st>>>(a, posq, vel, force);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick(const MdArgs &a, double4_32a *vel, const double4_32a *force, double *kpart,
+                        cudaStream_t st, const Prof *prof) {
+    ProfScope ps(prof, "kick");
+    k_kick<<<nblk(a.n), kThreads, 0, st>>>(a, vel, force, kpart);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const MdArgs &a, const double2 *epart, const double2 *rho,
+                            const double *kpart, int with_kinetic, double *energy,
+                            int64_t *cursor, int64_t advance, int64_t *step_counter,
+                            cudaStream_t st, const Prof *prof) {
+    ProfScope ps(prof, "finalize");
+    k_finalize<<<1, 1024, 0, st>>>(a, epart, rho, kpart, with_kinetic, energy, cursor, advance,
+                                   step_counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rescale(const MdArgs &a, double4_32a *vel, const double *energy, cudaStream_t st,
+                           const Prof *prof) {
+    ProfScope ps(prof, "rescale");
+    k_rescale<<<nblk(a.n), kThreads, 0, st>>>(a.n, vel, energy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(int64_t n, const double *x3, const double *q, double4_32a *out, int wrap,
+                        const double *L, cudaStream_t st) {
+    k_pack<<<nblk(n), kThreads, 0, st>>>(n, x3, q, out, wrap, L[0], L[1], L[2]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(int64_t n, const double4_32a *in, double *x3, cudaStream_t st) {
+    k_unpack<<<nblk(n), kThreads, 0, st>>>(n, in, x3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unsort_i32(int64_t n, const int32_t *perm, const int32_t *sorted, int32_t *out,
+                              cudaStream_t st) {
+    k_unsort<<<nblk(n), kThreads, 0, st>>>(n, perm, sorted, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m_to_int4(int32_t P, const int32_t *m3, int4 *out, cudaStream_t st) {
+    k_m_to_int4<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(P, m3, out);
+    return cudaGetLastError();
+}
+
+}  // namespace rbsog

@@ -1,0 +1,147 @@
+// Frequency sampler of the random batch (Sec. 3.3, Eqs. 3.18-3.22) and the
+// pre-sampled sequence of Algorithm 1 (line 2), run as independent
+// Metropolis-Hastings chains (the paper's parallel sampling, Sec. 3.4), one
+// chain per thread.
+//
+// This translation unit is compiled with -fmad=false: every floating-point
+// expression below rounds after each operation, so that the accept/reject
+// decisions and the rounded proposals are taken in the same FP64 arithmetic
+// as any other IEEE implementation of the same expressions.
+#include "rbsog_kernels.cuh"
+
+namespace rbsog {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 64x64->128-bit products with the published multipliers, key bumped by the
+// published Weyl constants before every round after the first.
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+        const uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+        const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// 53 random bits mapped to [0, 1).
+__device__ __forceinline__ double unit53(uint64_t x) {
+    return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Unnormalised target mass, proportional to F~(k) of Eq. 3.5 at k = 2 pi m / L.
+__device__ double target_mass(const SamplerDev &sp, int mx, int my, int mz) {
+    const int md[3] = {mx, my, mz};
+    double k2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double kd = 2.0 * kPi * (double)md[d] / sp.L[d];
+        k2 += kd * kd;
+    }
+    double acc = 0.0;
+    for (int l = 0; l <= sp.M; ++l)
+        acc += sp.omega[l] * sp.s[l] * sp.s[l] * sp.s[l] * exp(-sp.s[l] * sp.s[l] * k2 / 4.0);
+    return acc;
+}
+
+// Proposal mass of one coordinate: the rounded normal of variance
+// (L_d / (s_0 pi))^2 / 2, i.e. (1/2)[erf((m+1/2) a) - erf((m-1/2) a)] with
+// a = pi s_0 / L_d (Eq. 3.22, without the printed extra 1/2 in the argument).
+__device__ double proposal_mass(int m, double s0, double Ld) {
+    const double a = kPi * s0 / Ld;
+    if (m == 0) return erf(0.5 * a);
+    return 0.5 * (erf(((double)m + 0.5) * a) - erf(((double)m - 0.5) * a));
+}
+
+// Chain c emits chain_len states into kseq[c * chain_len ...].  Iteration j
+// uses the Philox blocks with key (seed, c) and counters (j, 0, 0, 0) (four
+// uniforms -> Box-Muller normals for the proposal) and (j, 1, 0, 0) (the
+// acceptance uniform).  The first non-zero proposal starts the chain; after
+// that each iteration emits the post-decision state.  Zero proposals are
+// rejections (p(0) = 0).
+__global__ void __launch_bounds__(128) k_mh_chain(SamplerDev sp, int4 *__restrict__ kseq,
+                                                  int32_t *__restrict__ err_flag) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= sp.n_chains) return;
+    const double s0 = sp.s[0];
+    double sd[3];
+    for (int d = 0; d < 3; ++d) sd[d] = sp.L[d] / (sqrt(2.0) * kPi * s0);
+    const int64_t len = sp.chain_len;
+    const int64_t cap = 64 * len + 4096;
+    int4 *out = kseq + c * len;
+    int cur[3] = {0, 0, 0};
+    double p_cur = 0.0, q_cur = 0.0;
+    bool have = false;
+    int64_t emitted = 0, j = 0;
+    while (emitted < len) {
+        if (j >= cap) {  // bounded: a chain that cannot start reports and stops
+            atomicOr(err_flag, 2);
+            for (; emitted < len; ++emitted) out[emitted] = make_int4(0, 0, 0, 0);
+            return;
+        }
+        uint64_t ra[4] = {(uint64_t)j, 0, 0, 0};
+        uint64_t rb[4] = {(uint64_t)j, 1, 0, 0};
+        philox4x64_10(ra, sp.seed, (uint64_t)c);
+        philox4x64_10(rb, sp.seed, (uint64_t)c);
+        const double r01 = sqrt(-2.0 * log(1.0 - unit53(ra[0])));
+        const double r23 = sqrt(-2.0 * log(1.0 - unit53(ra[2])));
+        double z[3];
+        z[0] = r01 * cos(2.0 * kPi * unit53(ra[1]));
+        z[1] = r01 * sin(2.0 * kPi * unit53(ra[1]));
+        z[2] = r23 * cos(2.0 * kPi * unit53(ra[3]));
+        int mp[3];
+        for (int d = 0; d < 3; ++d) mp[d] = (int)round(z[d] * sd[d]);
+        const bool zero = (mp[0] == 0 && mp[1] == 0 && mp[2] == 0);
+        ++j;
+        if (!have) {
+            if (zero) continue;
+            cur[0] = mp[0];
+            cur[1] = mp[1];
+            cur[2] = mp[2];
+            p_cur = target_mass(sp, cur[0], cur[1], cur[2]);
+            q_cur = proposal_mass(cur[0], s0, sp.L[0]) * proposal_mass(cur[1], s0, sp.L[1]) *
+                    proposal_mass(cur[2], s0, sp.L[2]);
+            have = true;
+        } else if (!zero) {
+            const double p_new = target_mass(sp, mp[0], mp[1], mp[2]);
+            const double q_new = proposal_mass(mp[0], s0, sp.L[0]) *
+                                 proposal_mass(mp[1], s0, sp.L[1]) *
+                                 proposal_mass(mp[2], s0, sp.L[2]);
+            const double ratio = (p_new * q_cur) / (p_cur * q_new);
+            if (unit53(rb[0]) < ratio) {
+                cur[0] = mp[0];
+                cur[1] = mp[1];
+                cur[2] = mp[2];
+                p_cur = p_new;
+                q_cur = q_new;
+            }
+        }
+        out[emitted] = make_int4(cur[0], cur[1], cur[2], 0);
+        ++emitted;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_mh_sampler(const SamplerDev &sp, int4 *kseq, int32_t *err_flag,
+                              cudaStream_t st, const Prof *prof) {
+    if (sp.n_chains <= 0) return cudaSuccess;
+    ProfScope ps(prof, "mh_sampler");
+    const int threads = 128;
+    const int64_t blocks = (sp.n_chains + threads - 1) / threads;
+    k_mh_chain<<<(unsigned)blocks, threads, 0, st>>>(sp, kseq, err_flag);
+    return cudaGetLastError();
+}
+
+}  // namespace rbsog

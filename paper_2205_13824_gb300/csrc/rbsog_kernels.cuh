@@ -1,0 +1,166 @@
+// Internal declarations shared by the translation units of librbsog: the
+// by-value parameter blocks handed to kernels and the host-side launchers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rbsog {
+
+constexpr int kMaxGauss = 128;   // M + 1 <= kMaxGauss
+constexpr int kMaxTaylor = 16;   // terms of the folded wide-Gaussian series
+
+// Sum-of-Gaussians near kernel in the form the pair kernels evaluate.
+// Gaussians l < n_direct are evaluated with exp; the wide ones (s_l >= 2 r_c)
+// are folded into Taylor series in r^2 about 0 with coefficients
+//   A[n] = sum_{l >= n_direct} w_l s_l^{-2n},
+// so that sum_{wide} w_l e^{-r^2/s_l^2}       = sum_n (-r^2)^n / n! A[n]
+// and     sum_{wide} w_l/s_l^2 e^{-r^2/s_l^2} = sum_n (-r^2)^n / n! A[n+1].
+struct NearSog {
+    int32_t n_direct;
+    int32_t n_taylor;              // number of Taylor terms used (n = 0..n_taylor-1)
+    double omega[kMaxGauss];       // w_l, l < n_direct
+    double inv_s2[kMaxGauss];      // 1 / s_l^2, l < n_direct
+    double tay_f[kMaxTaylor];      // A[n] / n! with sign (-1)^n folded in
+    double tay_g[kMaxTaylor];      // A[n+1] / n! with sign (-1)^n folded in
+    float omega_f[kMaxGauss];
+    float inv_s2_f[kMaxGauss];
+    float tay_f_f[kMaxTaylor];
+    float tay_g_f[kMaxTaylor];
+};
+
+// Box, cell grid and pair constants.
+struct BoxDev {
+    double L[3];
+    double h[3];          // cell sides L_d / nc_d
+    int32_t nc[3];        // cells per side
+    int32_t ncell;
+    double rc2;           // r_c * r_c
+    double lB;            // Coulomb prefactor
+    double wca_s2;        // wca_sigma^2 (0: off)
+    double wca_rc2;       // 2^(1/3) wca_sigma^2
+    double wca_eps;
+    float L_f[3];
+    float fix_scale[3];   // L_d / 2^32: fixed-point unit of the FP32C positions
+};
+
+// Sampler inputs (Sec. 3.3): full SOG (not folded) in FP64.
+struct SamplerDev {
+    int32_t M;
+    double omega[kMaxGauss];
+    double s[kMaxGauss];
+    double L[3];
+    uint64_t seed;
+    int64_t n_chains;
+    int32_t chain_len;
+};
+
+// Per-kernel timing hook: when non-null the launcher brackets the launch
+// with CUDA events through this callback (name, begin/end).
+struct Prof {
+    void (*mark)(void *self, const char *name, int begin);
+    void *self;
+};
+
+struct ProfScope {
+    const Prof *p;
+    const char *name;
+    ProfScope(const Prof *p_, const char *n) : p(p_), name(n) {
+        if (p && p->mark) p->mark(p->self, name, 1);
+    }
+    ~ProfScope() {
+        if (p && p->mark) p->mark(p->self, name, 0);
+    }
+};
+
+// ---- sampler (k_sampler.cu) -------------------------------------------------
+cudaError_t launch_mh_sampler(const SamplerDev &sp, int4 *kseq, int32_t *err_flag,
+                              cudaStream_t st, const Prof *prof);
+
+// ---- cell list (k_cells.cu) ---------------------------------------------------
+struct CellBuffers {
+    int32_t *cell_of;     // [n]   cell id of each particle (caller order)
+    int32_t *slot;        // [n]   arrival slot inside its cell (unordered)
+    int32_t *count;       // [ncell] zeroed after every scan
+    int32_t *start;       // [ncell + 1]
+    int32_t *perm_raw;    // [n]   cell order, unordered inside a cell
+    int32_t *perm;        // [n]   cell order, increasing index inside a cell
+};
+// precision 0: gather FP64 (x, y, z, q) into sp64; 1: 32-bit fixed point
+// positions and FP32 charge into sp32.
+cudaError_t launch_build_cells(int64_t n, const double4_32a *posq, const BoxDev &box,
+                               const CellBuffers &cb, int precision, double4_32a *sp64, uint4 *sp32,
+                               int32_t *err_flag, cudaStream_t st, const Prof *prof);
+
+// ---- near field (k_near.cu) ---------------------------------------------------
+// Forces (sorted order) into fnear; per-block energy partials (U_near, U_wca)
+// into epart[nblocks]; neighbour counts (sorted order) into nbr when non-null.
+int near_num_blocks(const BoxDev &box, int group);
+cudaError_t launch_near(int precision, const BoxDev &box, const NearSog &sog, int group,
+                        const int32_t *start, const double4_32a *sp64, const uint4 *sp32,
+                        double4_32a *fnear, double2 *epart, int32_t *nbr, cudaStream_t st,
+                        const Prof *prof);
+
+// ---- far field (k_far.cu) -----------------------------------------------------
+struct FarArgs {
+    int64_t n;
+    int32_t P;
+    double L[3];
+    double coef;               // -lB * pi^{3/2} S / (P V): multiplies q_i k Im(...)
+    const int4 *kseq;          // pre-sampled sequence (or null)
+    const int64_t *cursor;     // device k-set index (or null)
+    const int4 *m_explicit;    // explicit k-set (overrides kseq when non-null)
+    int32_t tile_p;            // particles per sweep block
+    int32_t n_ptiles;
+};
+int far_num_ptiles(int64_t n, int tile_p);
+cudaError_t launch_rho_sweep(int precision, const FarArgs &a, const double4_32a *sp64,
+                             const uint4 *sp32, double2 *rho_part, cudaStream_t st,
+                             const Prof *prof);
+// Combines partials in FP64 (fixed order) into rho[P] and the per-k scatter
+// table (k vector, prescaled Re/Im rho, integer m).
+cudaError_t launch_rho_combine(int precision, const FarArgs &a, const double2 *rho_part,
+                               double2 *rho, void *ktab, cudaStream_t st, const Prof *prof);
+// Total force (near + far) written to force[perm[s]] in caller order.
+cudaError_t launch_far_scatter(int precision, const FarArgs &a, const double4_32a *sp64,
+                               const uint4 *sp32, const void *ktab, const double4_32a *fnear,
+                               const int32_t *perm, double4_32a *force, int32_t *err_flag,
+                               cudaStream_t st, const Prof *prof);
+size_t ktab_bytes(int precision, int32_t P);
+
+// ---- integrator and reductions (k_md.cu) --------------------------------------
+struct MdArgs {
+    int64_t n;
+    double dt, inv_mass, mass;
+    double L[3];
+    double T0, tau;            // Berendsen (tau <= 0: off)
+    int32_t n_epart;           // near-energy partials
+    int32_t n_kpart;           // kinetic partials
+    int32_t P;
+    double half_coef_U;        // lB * pi^{3/2} S / (2 P V)
+    double U_self;
+};
+// Device energies: [0] U_near [1] U_far [2] U_self [3] U_wca [4] K [5] T [6] lambda
+constexpr int kNumEnergy = 8;
+cudaError_t launch_kick_drift(const MdArgs &a, double4_32a *posq, double4_32a *vel, const double4_32a *force,
+                              cudaStream_t st, const Prof *prof);
+cudaError_t launch_kick(const MdArgs &a, double4_32a *vel, const double4_32a *force, double *kpart,
+                        cudaStream_t st, const Prof *prof);
+// Sum energy partials in fixed order; U_far from rho; T, Berendsen lambda;
+// advance the k-set cursor by `advance`.
+cudaError_t launch_finalize(const MdArgs &a, const double2 *epart, const double2 *rho,
+                            const double *kpart, int with_kinetic, double *energy,
+                            int64_t *cursor, int64_t advance, int64_t *step_counter,
+                            cudaStream_t st, const Prof *prof);
+cudaError_t launch_rescale(const MdArgs &a, double4_32a *vel, const double *energy, cudaStream_t st,
+                           const Prof *prof);
+int kinetic_num_blocks(int64_t n);
+// Layout conversions between caller [n][3] arrays and the internal double4_32a.
+cudaError_t launch_pack(int64_t n, const double *x3, const double *q, double4_32a *out, int wrap,
+                        const double *L, cudaStream_t st);
+cudaError_t launch_unpack(int64_t n, const double4_32a *in, double *x3, cudaStream_t st);
+cudaError_t launch_unsort_i32(int64_t n, const int32_t *perm, const int32_t *sorted,
+                              int32_t *out, cudaStream_t st);
+cudaError_t launch_m_to_int4(int32_t P, const int32_t *m3, int4 *out, cudaStream_t st);
+
+}  // namespace rbsog

@@ -1,0 +1,330 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on
+the same seeded inputs and the same frequency sets.
+
+Bars: integer work bit-exact (sampled sequence, cell list, neighbour
+counts); FP64 forces within 1e-10 RMS relative of the oracle; FP32C forces
+within 1e-4 RMS relative (the precision target), energies reported."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import rbsog_inputs as I
+from tests._util import B_PROD, M_PROD, prod_sog, untruncated_M
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _lib():
+    import paper_2205_13824_gb300 as P
+    return P
+
+
+def rms_rel(a, b):
+    return math.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2))
+
+
+def make(N, L, P, prec="fp64", n_ksets=4, seed=11, chain_len=0, sog=None, wca=True, lB=1.0,
+         tau=0.0, dt=0.001):
+    Pk = _lib()
+    sog = sog or prod_sog(O)
+    p = Pk.make_params(L, P, sigma=sog.sigma, omega0=sog.omega0, M=sog.M, n_ksets=n_ksets,
+                       seed=seed, chain_len=chain_len, precision=prec, lB=lB,
+                       wca_sigma=1.0 if wca else 0.0, wca_eps=1.0 if wca else 0.0, tau_T=tau,
+                       dt=dt)
+    return Pk.RBSOG(N, p, device=0), sog
+
+
+def osys(L, sog, wca=True, lB=1.0):
+    Lv = (L,) * 3 if isinstance(L, (int, float)) else tuple(L)
+    return O.System(Lv, sog, 3.0, lB, 1.0 if wca else 0.0, 1.0 if wca else 0.0)
+
+
+def to_dev(*arrs):
+    d = _dev()
+    return [torch.tensor(a, device=d) for a in arrs]
+
+
+# ------------------------------------------------------------------ sampler
+
+@pytest.mark.parametrize("L,P,nsets,chain", [(12.6, 100, 11, 64), (50.4, 200, 7, 0), (128.0, 500, 5, 256),
+                                             ((10.0, 12.0, 15.0), 37, 9, 50)])
+def test_kseq_bit_exact(L, P, nsets, chain):
+    """The device Metropolis-Hastings chains emit exactly the oracle's
+    sequence (same Philox streams, same FP64 decisions)."""
+    _dev()
+    Lv = (L,) * 3 if isinstance(L, (int, float)) else L
+    N = 1000
+    g, sog = make(N, Lv, P, n_ksets=nsets, seed=20240601, chain_len=chain)
+    info, _, _ = g.info()
+    ks_gpu = g.kseq(0, nsets)
+    ks_orc = O.kseq(sog, Lv, seed=20240601, n_chains=info.n_chains, chain_len=info.chain_len)
+    assert np.array_equal(ks_gpu, ks_orc[: nsets * P])
+    g.close()
+
+
+def test_sog_solve_and_S_match_oracle():
+    _dev()
+    Pk = _lib()
+    for L in (12.6, 128.0):
+        p = Pk.make_params(L, 10, n_ksets=1)      # sigma <= 0: library solves C0/C1
+        g = Pk.RBSOG(1000, p, device=0)
+        info, om, s = g.info()
+        ref = O.SOG.solve(B_PROD, 3.0, untruncated_M(B_PROD))
+        assert info.sigma == pytest.approx(ref.sigma, rel=1e-12)
+        assert info.omega0 == pytest.approx(ref.omega0, rel=1e-12)
+        tr = O.SOG(B_PROD, ref.sigma, ref.omega0, M_PROD)
+        assert np.allclose(om, tr.omega, rtol=1e-12)
+        assert np.allclose(s, tr.s, rtol=1e-14)
+        assert info.S == pytest.approx(tr.S((L, L, L)), rel=1e-12)
+        g.close()
+
+
+# --------------------------------------------------------------- cell list
+
+@pytest.mark.parametrize("N,L", [(1000, 12.6), (4998, 21.5), (64000, 50.4), (2, 9.0), (10, 20.0)])
+def test_cell_list_and_neighbours_bit_exact(N, L):
+    _dev()
+    if N in (2, 10):       # degenerate: a lone pair; a box of mostly empty cells
+        q, x = I.random_neutral(N, L, seed=4, min_dist=0.9)
+        v = np.zeros_like(x)
+    else:
+        q, x, v = I.electrolyte(N, L, seed=3)
+    g, sog = make(N, L, 8)
+    g.set_state(*to_dev(q, x, v))
+    nc, cell_of, start_o, perm_o = O.cell_list(O.wrap(x, (L,) * 3), (L, L, L), 3.0)
+    ncell = int(np.prod(nc))
+    start = np.zeros(ncell + 1, dtype=np.int32)
+    perm = np.zeros(N, dtype=np.int32)
+    nbr = np.zeros(N, dtype=np.int32)
+    _lib().binding.rbsog_get_cells(g.ctx, start, perm, nbr)
+    assert np.array_equal(start, start_o[: ncell + 1])
+    assert np.array_equal(perm, perm_o)
+    if N <= 5000:
+        _, _, _, nbr_o = O.near(osys(L, sog), q, O.wrap(x, (L,) * 3), "direct")
+    else:
+        _, _, _, nbr_o = O.near(osys(L, sog), q, O.wrap(x, (L,) * 3), "cells")
+    assert np.array_equal(nbr, nbr_o)
+    g.close()
+
+
+# ------------------------------------------------------------------- rho(k)
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32c", 2e-6)])
+def test_rho_matches_oracle(prec, tol):
+    _dev()
+    N, L = 4998, 21.5
+    q, x, v = I.electrolyte(N, L, seed=5)
+    g, sog = make(N, L, 8, prec=prec)
+    g.set_state(*to_dev(q, x, v))
+    rng = np.random.default_rng(1)
+    m = rng.integers(-40, 41, size=(77, 3)).astype(np.int32)
+    out = np.zeros((77, 2))
+    _lib().binding.rbsog_rho(g.ctx, m, out)
+    ref = O.rho(q, O.wrap(x, (L,) * 3), (L, L, L), m)
+    err = np.abs(out[:, 0] + 1j * out[:, 1] - ref)
+    assert err.max() <= tol * np.sum(np.abs(q))
+    g.close()
+
+
+# ------------------------------------------------------------------- forces
+
+CASES = [
+    # N, L, P: the 1,000-ion electrolyte; a ragged size (not a multiple of
+    # any tile, P not a multiple of 32); a 64,000-ion box; 3 cells per side
+    (1000, 12.6, 100),
+    (4998, 21.5, 37),
+    (64000, 50.4, 200),
+    (216, 9.0, 64),
+]
+
+
+@pytest.mark.parametrize("N,L,P", CASES)
+def test_forces_fp64_match_oracle(N, L, P):
+    _dev()
+    q, x, v = I.electrolyte(N, L, seed=N)
+    g, sog = make(N, L, P)
+    g.set_state(*to_dev(q, x, v))
+    s = osys(L, sog)
+    m = O.kseq(sog, s.L, seed=99, n_chains=4, chain_len=(P + 3) // 4)[:P]
+    f_gpu = torch.zeros((N, 3), dtype=torch.float64, device=_dev())
+    e = _lib().binding.rbsog_compute_forces(g.ctx, m, f_gpu)
+    xw = O.wrap(x, s.L)
+    if N <= 5000:
+        f_o, e_o = O.forces(s, q, xw, S=s.S(), m=m)
+        assert rms_rel(f_gpu.cpu().numpy(), f_o) < 1e-10
+        for k in ("U_near", "U_far", "U_self", "U_wca"):
+            assert e[k] == pytest.approx(e_o[k], rel=1e-10, abs=1e-10)
+    else:
+        idx = np.random.default_rng(0).choice(N, size=400, replace=False)
+        f_o = O.forces_sample(s, q, xw, s.S(), m, idx)
+        assert rms_rel(f_gpu.cpu().numpy()[idx], f_o) < 1e-10
+    g.close()
+
+
+@pytest.mark.parametrize("N,L,P", CASES)
+def test_forces_fp32c_within_target(N, L, P):
+    _dev()
+    q, x, v = I.electrolyte(N, L, seed=N)
+    g, sog = make(N, L, P, prec="fp32c")
+    g.set_state(*to_dev(q, x, v))
+    s = osys(L, sog)
+    m = O.kseq(sog, s.L, seed=99, n_chains=4, chain_len=(P + 3) // 4)[:P]
+    f_gpu = torch.zeros((N, 3), dtype=torch.float64, device=_dev())
+    e = _lib().binding.rbsog_compute_forces(g.ctx, m, f_gpu)
+    xw = O.wrap(x, s.L)
+    if N <= 5000:
+        f_o, e_o = O.forces(s, q, xw, S=s.S(), m=m)
+        err = rms_rel(f_gpu.cpu().numpy(), f_o)
+        U = e["U_near"] + e["U_far"] - e["U_self"] + e["U_wca"]
+        U_o = e_o["U_near"] + e_o["U_far"] - e_o["U_self"] + e_o["U_wca"]
+        assert abs(U - U_o) <= 1e-5 * abs(U_o)
+    else:
+        idx = np.random.default_rng(0).choice(N, size=400, replace=False)
+        f_o = O.forces_sample(s, q, xw, s.S(), m, idx)
+        err = rms_rel(f_gpu.cpu().numpy()[idx], f_o)
+    print(f"FP32C N={N} P={P}: rms rel force err {err:.3e}")
+    assert err < 1e-4
+    g.close()
+
+
+def test_far_force_sums_to_zero_and_no_nan():
+    """Per k-set the random-batch force has zero sum (Im rho* rho = 0) and
+    the near force obeys Newton 3, so the total force sums to ~0."""
+    _dev()
+    N, L, P = 4998, 21.5, 64
+    q, x, v = I.electrolyte(N, L, seed=9)
+    for prec, tol in (("fp64", 1e-11), ("fp32c", 1e-5)):
+        g, sog = make(N, L, P, prec=prec, n_ksets=3)
+        g.set_state(*to_dev(q, x, v))
+        f = torch.zeros((N, 3), dtype=torch.float64, device=_dev())
+        _lib().binding.rbsog_compute_forces(g.ctx, None, f)
+        fn = f.cpu().numpy()
+        assert np.isfinite(fn).all()
+        assert np.abs(fn.sum(0)).max() <= tol * np.abs(fn).sum(1).mean() * math.sqrt(N)
+        g.close()
+
+
+# ------------------------------------------------------------------- dynamics
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_md_trajectory_matches_oracle(prec):
+    """One force evaluation + 10 velocity-Verlet steps on the 1,000-ion
+    electrolyte with the pre-sampled sequence (Algorithm 1)."""
+    _dev()
+    N, L, P, steps = 1000, 12.6, 100, 10
+    q, x, v = I.electrolyte(N, L, seed=1)
+    g, sog = make(N, L, P, prec=prec, n_ksets=steps + 1, seed=42, chain_len=100)
+    g.set_state(*to_dev(q, x, v))
+    g.step(steps)
+    xg, vg, fg, nstep = g.state()
+    assert nstep == steps
+    info, _, _ = g.info()
+    s = osys(L, sog)
+    ks = O.kseq(sog, s.L, seed=42, n_chains=info.n_chains, chain_len=info.chain_len)
+    xo, vo, fo, es = O.md(s, q, x, v, s.S(), P, ks, steps, 0.001)
+    dx = xg.cpu().numpy() - xo
+    dx -= L * np.rint(dx / L)
+    if prec == "fp64":
+        assert np.abs(dx).max() < 1e-11
+        assert np.abs(vg.cpu().numpy() - vo).max() < 1e-9
+        assert rms_rel(fg.cpu().numpy(), fo) < 1e-10
+        e = g.energies()
+        assert e["K"] == pytest.approx(es[-1]["K"], rel=1e-10)
+        assert e["U_far"] == pytest.approx(es[-1]["U_far"], rel=1e-10)
+    else:
+        assert np.abs(dx).max() < 1e-6
+        assert rms_rel(fg.cpu().numpy(), fo) < 1e-4
+    g.close()
+
+
+def test_berendsen_matches_oracle():
+    _dev()
+    N, L, P, steps = 1000, 12.6, 50, 6
+    q, x, v = I.electrolyte(N, L, seed=2, T=2.0)
+    g, sog = make(N, L, P, n_ksets=steps + 1, seed=5, chain_len=50, tau=0.01)
+    g.set_state(*to_dev(q, x, v))
+    g.step(steps)
+    xg, vg, fg, _ = g.state()
+    info, _, _ = g.info()
+    s = osys(L, sog)
+    ks = O.kseq(sog, s.L, seed=5, n_chains=info.n_chains, chain_len=info.chain_len)
+    xo, vo, fo, es = O.md(s, q, x, v, s.S(), P, ks, steps, 0.001, T0=1.0, tau=0.01)
+    assert np.abs(vg.cpu().numpy() - vo).max() < 1e-9
+    assert g.energies()["T"] == pytest.approx(es[-1]["T"], rel=1e-10)
+    g.close()
+
+
+def test_graph_replay_equals_eager_launches():
+    """The CUDA-graph step and the eager (profiled) step give identical bits."""
+    _dev()
+    N, L, P, steps = 4998, 21.5, 64, 5
+    q, x, v = I.electrolyte(N, L, seed=8)
+    out = []
+    for prof in (False, True):
+        g, _ = make(N, L, P, prec="fp32c", n_ksets=steps + 1, seed=3)
+        _lib().binding.rbsog_set_profiling(g.ctx, prof)
+        g.set_state(*to_dev(q, x, v))
+        g.step(steps)
+        xg, vg, fg, _ = g.state()
+        out.append((xg.cpu().numpy(), vg.cpu().numpy(), fg.cpu().numpy()))
+        if prof:
+            rep = _lib().binding.rbsog_get_profile(g.ctx)
+            assert rep["far_scatter_fp32c"][0] == steps + 1
+        g.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
+def test_runs_are_deterministic():
+    _dev()
+    N, L, P = 4998, 21.5, 64
+    q, x, v = I.electrolyte(N, L, seed=8)
+    res = []
+    for _ in range(2):
+        g, _ = make(N, L, P, prec="fp32c", n_ksets=4, seed=3)
+        g.set_state(*to_dev(q, x, v))
+        g.step(3)
+        res.append(g.state()[2].cpu().numpy())
+        g.close()
+    assert np.array_equal(res[0], res[1])
+
+
+# ------------------------------------------------------------------- errors
+
+def test_invalid_arguments_are_rejected():
+    _dev()
+    Pk = _lib()
+    B = Pk.binding
+    ctx = B.rbsog_create(100, 0, None)
+    bad = [dict(L=5.0), dict(b=1.0), dict(P=0), dict(M=200), dict(precision=7), dict(r_c=7.0, L=12.0)]
+    for kw in bad:
+        args = dict(L=12.6, P=10, n_ksets=1)
+        args.update(kw)
+        with pytest.raises(B.RBSOGError) as ei:
+            B.rbsog_set_params(ctx, Pk.make_params(**args))
+        assert ei.value.status == 1
+    with pytest.raises(B.RBSOGError) as ei:
+        B.rbsog_step(ctx, 1)
+    assert ei.value.status == 4
+    B.rbsog_set_params(ctx, Pk.make_params(12.6, 10, n_ksets=2))
+    q = np.ones(100)
+    x = np.random.default_rng(0).uniform(0, 12.6, (100, 3))
+    with pytest.raises(B.RBSOGError) as ei:
+        B.rbsog_set_state(ctx, q, x, None)                 # not neutral
+    assert ei.value.status == 1
+    q[::2] = -1
+    B.rbsog_set_state(ctx, q, x, None)                     # host pointers work too
+    with pytest.raises(B.RBSOGError) as ei:
+        B.rbsog_step(ctx, 5)                               # only 2 k-sets sampled
+    assert ei.value.status == 1
+    B.rbsog_destroy(ctx)
