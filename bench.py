@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the RBSOG velocity-Verlet step.
+
+Workload (default): the 1,048,576-ion 1:1 electrolyte (L = 128, number
+density 0.5, r_c = 3, P = 500 frequencies per step, SOG b = 1.4878, M = 36),
+FP32C path.  One "step" is the whole hot path: half kick + drift, cell-list
+build, near field, rho(k) sweep and combine, far-field scatter, half kick and
+the fixed-order energy reductions.  Inputs are resident in HBM when the timed
+region starts; the state (~0.2 GB) is larger than L2.
+
+Prints ONE JSON line (rank 0).  With --gpus N > 1 (torchrun, one process per
+GPU) every rank advances its own independent replica (weak scaling, no data
+collective); the timed region is bracketed by barriers and the slowest rank's
+time is used.
+
+--impl reference times the FP64 CPU oracle (the checker the CUDA path is
+validated against) on the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at N=1M (FP32-comp vs FP64 path, same error); p50/p99 job latency"
+N_DEF, L_DEF, P_DEF = 1048576, 128.0, 500
+SM_COUNT = 152
+MUFU_PER_CLK_SM = 16          # MUFU (sin/cos/ex2/rsqrt) results per clock per SM
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=N_DEF)
+    ap.add_argument("--L", type=float, default=L_DEF)
+    ap.add_argument("--P", type=int, default=P_DEF)
+    ap.add_argument("--quick", action="store_true", help="skip the FP64 path, P sweep and CPU baseline")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    return rank, world, local, dist
+
+
+class Clocks:
+    """nvidia-smi sampler of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r[0] for r in rows if r[2] > 200.0] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+def electrolyte_state(N, L, seed):
+    import rbsog_inputs as I
+    return I.electrolyte(N, L, seed=seed)
+
+
+def roofline_for(name, launches, ms_total, N, P, sm_mhz, peaks):
+    """Algorithmic work of one launch over its average CUDA-event duration."""
+    t = ms_total / launches / 1e3
+    f = (sm_mhz or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    if name.startswith(("rho_sweep", "far_scatter")):
+        # one (particle, frequency) term = one sin + one cos on the MUFU pipe
+        achieved = N * P / t / 1e9
+        peak = SM_COUNT * MUFU_PER_CLK_SM / 2 * f / 1e9
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gsincos/s",
+                "frac": achieved / peak, "traffic": None, "kernel": name,
+                "ms_per_launch": t * 1e3, "peak_basis": f"{MUFU_PER_CLK_SM} MUFU/clk/SM x {SM_COUNT} SMs / 2 at "
+                                                         f"{f / 1e6:.0f} MHz (median SM clock in the timed region)"}
+    if name.startswith("near"):
+        # one accepted pair ~ 6 MUFU (rsqrt + 5 narrow Gaussians); count pairs
+        pairs = N * (4.0 / 3.0) * math.pi * 27.0 * 0.5
+        achieved = pairs * 6 / t / 1e9
+        peak = SM_COUNT * MUFU_PER_CLK_SM * f / 1e9
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GMUFU/s",
+                "frac": achieved / peak, "traffic": None, "kernel": name, "ms_per_launch": t * 1e3}
+    bytes_ = N * 64
+    achieved = bytes_ / t / 1e9
+    peak = peaks.get("hbm_gbs", 6686.1)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": name, "ms_per_launch": t * 1e3}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def run_ours(args, rank, world, local, dist):
+    import numpy as np
+    import torch
+
+    import paper_2205_13824_gb300 as Pk
+    B = Pk.binding
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    N, L, P, K, W = args.N, args.L, args.P, args.steps, args.warmup
+    q, x, v = electrolyte_state(N, L, seed=2024 + rank)
+    n_e2e = max(3, min(K, 10))
+    need = W + 2 * K + n_e2e + 8
+    p32 = Pk.make_params(L, P, n_ksets=need, seed=17 + rank, precision="fp32c")
+    g = Pk.RBSOG(N, p32, device=local)
+    tq, tx, tv = (torch.tensor(a, device=dev) for a in (q, x, v))
+    g.set_state(tq, tx, tv)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    g.step(W)                                   # warm-up (builds the step graph)
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = Clocks(local)
+    with clk:
+        barrier()
+        t_wall = time.perf_counter()
+        e0.record(stream)
+        g.step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        barrier()
+    ms = e0.elapsed_time(e1) / K
+    clocks = clk.summary()
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # per-kernel CUDA-event timing over K more steps (eager launches)
+    B.rbsog_set_profiling(g.ctx, True)
+    barrier()
+    e0.record(stream)
+    g.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = e0.elapsed_time(e1) / K
+    prof = B.rbsog_get_profile(g.ctx)
+    B.rbsog_set_profiling(g.ctx, False)
+    launches_per_step = sum(c for c, _ in prof.values()) / K
+
+    # end to end through the C ABI from pinned host buffers: per step the
+    # state (q, x, v, f) goes host->device, one step runs, (x, v, f) comes back
+    hq = torch.tensor(q).pin_memory()
+    xs, vs, fs = (torch.empty((N, 3), dtype=torch.float64).pin_memory() for _ in range(3))
+    B.rbsog_get_state(g.ctx, xs, vs, fs)
+    cur = B.rbsog_get_cursor(g.ctx)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        B.rbsog_set_state(g.ctx, hq, xs, vs)
+        B.rbsog_restore(g.ctx, fs, cur + i, 0)
+        B.rbsog_step(g.ctx, 1)
+        B.rbsog_get_state(g.ctx, xs, vs, fs)
+    t_e2e = (time.perf_counter() - t0) / n_e2e
+    h2d = hq.numel() * 8 + 3 * xs.numel() * 8
+    d2h = 3 * xs.numel() * 8
+    if dist is not None:
+        t = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    g.close()
+
+    extras = {}
+    if not args.quick and rank == 0:
+        extras = run_extras(args, q, x, v, dev)
+
+    peaks = load_peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    roof = roofline_for(top[0], top[1][0], top[1][1], N, P, clocks.get("sm_mhz"), peaks)
+    kernels = {k: {"launches": c, "ms_per_launch": t / c, "share": t / sum(tt for _, tt in prof.values())}
+               for k, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    value = world * N / (ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"1:1 electrolyte N={N} L={L:g} r_c=3 P={P} FP32C", "N": N, "L": L,
+                   "P": P, "r_c": 3.0, "sog": "b=1.48783512395703226 M=36 (Table 1 row 3 at r_c=3)",
+                   "precision": "fp32c", "l2": "inputs larger than L2 (state ~0.2 GB per replica)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single system"},
+        "e2e": {"value": world * N / t_e2e, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(round(launches_per_step * K)),
+        "roofline": roof,
+        "clocks": clocks,
+        "kernels": kernels,
+        "ms_per_step_eager_profiled": ms_prof,
+    }
+    line.update(extras)
+    if rank == 0 and not args.quick:
+        line["cpu_baseline"] = cpu_baseline(N, L, P, q, x, v)
+    return line, rank
+
+
+def run_extras(args, q, x, v, dev):
+    """FP64 comparator path at the same workload, the FP32C-vs-FP64 force
+    error on one shared k-set, and the P sweep of the FP32C path."""
+    import numpy as np
+    import torch
+
+    import paper_2205_13824_gb300 as Pk
+    B = Pk.binding
+    N, L, P = args.N, args.L, args.P
+    out = {}
+    tq, tx, tv = (torch.tensor(a, device=dev) for a in (q, x, v))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    K64 = max(2, min(args.steps, 5))
+    g64 = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=K64 + 4, seed=17, precision="fp64"), device=dev.index)
+    g32 = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=4, seed=17, precision="fp32c"), device=dev.index)
+    g64.set_state(tq, tx, tv)
+    g32.set_state(tq, tx, tv)
+    m = g64.kseq(0, 1)
+    f64 = torch.zeros((N, 3), dtype=torch.float64, device=dev)
+    f32 = torch.zeros_like(f64)
+    B.rbsog_compute_forces(g64.ctx, m, f64)
+    B.rbsog_compute_forces(g32.ctx, m, f32)
+    err = float(torch.sqrt(((f32 - f64) ** 2).sum() / (f64 ** 2).sum()))
+    g32.close()
+    g64.step(1)
+    torch.cuda.synchronize()
+    e0.record(st)
+    g64.step(K64)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / K64
+    g64.close()
+    out["fp64_path"] = {"value": N / (ms64 / 1e3), "unit": "particle-steps/s", "ms_per_step": ms64,
+                        "steps": K64, "dtype": "f64"}
+    out["fp32c_vs_fp64_rms_rel_force_err"] = err
+    sweep = {}
+    for Ps in (100, 500, 2000):
+        if Ps == P:
+            continue
+        g = Pk.RBSOG(N, Pk.make_params(L, Ps, n_ksets=args.steps + 8, seed=19, precision="fp32c"),
+                     device=dev.index)
+        g.set_state(tq, tx, tv)
+        g.step(2)
+        torch.cuda.synchronize()
+        e0.record(st)
+        g.step(args.steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1) / args.steps
+        sweep[str(Ps)] = {"value": N / (ms_s / 1e3), "ms_per_step": ms_s}
+        g.close()
+    out["fp32c_P_sweep"] = sweep
+    return out
+
+
+def cpu_baseline(N, L, P, q, x, v, sample_steps=1):
+    """The FP64 oracle, as it stands, on the host cores: one full
+    velocity-Verlet step (one force evaluation) of the same workload."""
+    import numpy as np
+
+    import oracle as O
+    sog = O.SOG.solve(1.48783512395703226, 3.0, 232)
+    sog = O.SOG(sog.b, sog.sigma, sog.omega0, 36)
+    s = O.System((L, L, L), sog, 3.0, 1.0, 1.0, 1.0)
+    S = s.S()
+    ks = O.kseq(sog, s.L, seed=5, n_chains=8, chain_len=(P * sample_steps + 7) // 8)
+    f0 = np.zeros_like(x)
+    t0 = time.perf_counter()
+    O.md(s, q, x, v, S, P, ks, sample_steps, 0.001, f=f0)
+    dt = time.perf_counter() - t0
+    return {"value": N * sample_steps / dt, "unit": "particle-steps/s", "cores": O.num_threads(),
+            "kind": "oracle", "sample": f"{sample_steps} full step(s) (one FP64 force evaluation each: "
+                                        f"near cells + random-batch far, P={P}) of the N={N} workload",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    """Oracle arm: each step is one full FP64 velocity-Verlet step of the
+    oracle on this workload, on the host cores of rank 0."""
+    import numpy as np
+
+    import oracle as O
+    N, L, P, K, W = args.N, args.L, args.P, args.steps, args.warmup
+    q, x, v = electrolyte_state(N, L, seed=2024)
+    sog = O.SOG.solve(1.48783512395703226, 3.0, 232)
+    sog = O.SOG(sog.b, sog.sigma, sog.omega0, 36)
+    s = O.System((L, L, L), sog, 3.0, 1.0, 1.0, 1.0)
+    S = s.S()
+    ks = O.kseq(sog, s.L, seed=5, n_chains=16, chain_len=(P * (W + K + 1) + 15) // 16)
+    x, v, f, _ = O.md(s, q, x, v, S, P, ks, 0, 0.001)      # initial forces
+    used = 1
+    if W:
+        x, v, f, _ = O.md(s, q, x, v, S, P, ks[used * P:], W, 0.001, f=f)
+        used += W
+    t0 = time.perf_counter()
+    x, v, f, _ = O.md(s, q, x, v, S, P, ks[used * P:], K, 0.001, f=f)
+    dt = time.perf_counter() - t0
+    val = N * K / dt
+    return {"metric": METRIC, "value": val, "unit": "particle-steps/s", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": dt / K * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"1:1 electrolyte N={N} L={L:g} r_c=3 P={P}", "N": N, "L": L, "P": P},
+            "cpu_baseline": {"value": val, "unit": "particle-steps/s", "cores": O.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{K} full FP64 steps of the N={N} workload on the host cores"},
+            "e2e": {"value": val, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    rank, world, local, dist = dist_setup(args)
+    line, rank = run_ours(args, rank, world, local, dist)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -141,6 +141,17 @@ rbsog_status rbsog_step(rbsog_ctx *ctx, int64_t nsteps);
  * non-finite force was produced since the last check. */
 rbsog_status rbsog_get_state(rbsog_ctx *ctx, double *x, double *v, double *f, int64_t *step);
 
+/* Number of k-sets consumed so far (the cursor into the pre-sampled
+ * sequence; host value, no synchronisation). */
+rbsog_status rbsog_get_cursor(const rbsog_ctx *ctx, int64_t *kset_cursor);
+
+/* Resume from a checkpoint: after rbsog_set_state, load the forces f[n][3]
+ * (host or device) that belong to those positions, the k-set cursor and
+ * the step counter, so that the next step continues the run exactly (the
+ * stored forces are used instead of a new force evaluation).  Rejects a
+ * cursor outside [0, n_ksets]. */
+rbsog_status rbsog_restore(rbsog_ctx *ctx, const double *f, int64_t kset_cursor, int64_t step);
+
 /* Energies of the last force evaluation and the kinetic energy (host). */
 rbsog_status rbsog_get_energies(rbsog_ctx *ctx, rbsog_energies *e);
 

@@ -24,6 +24,7 @@ STATUS = {0: "RBSOG_OK", 1: "RBSOG_EINVAL", 2: "RBSOG_ENOMEM", 3: "RBSOG_ECUDA",
 EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_state",
            "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_get_energies",
            "rbsog_get_kseq", "rbsog_rho", "rbsog_get_cells", "rbsog_set_profiling",
+           "rbsog_get_cursor", "rbsog_restore",
            "rbsog_get_profile", "rbsog_last_error", "rbsog_destroy")
 
 
@@ -72,6 +73,8 @@ def _load():
         "rbsog_step": [P, C.c_int64],
         "rbsog_get_state": [P, P, P, P, C.POINTER(C.c_int64)],
         "rbsog_get_energies": [P, C.POINTER(rbsog_energies)],
+        "rbsog_get_cursor": [P, C.POINTER(C.c_int64)],
+        "rbsog_restore": [P, P, C.c_int64, C.c_int64],
         "rbsog_get_kseq": [P, C.c_int64, C.c_int64, P],
         "rbsog_rho": [P, P, C.c_int32, P],
         "rbsog_get_cells": [P, P, P, P],
@@ -159,6 +162,16 @@ def rbsog_get_state(ctx, x=None, v=None, f=None):
     step = C.c_int64()
     _check(ctx, _lib.rbsog_get_state(ctx, _ptr(x), _ptr(v), _ptr(f), C.byref(step)))
     return step.value
+
+
+def rbsog_get_cursor(ctx):
+    c = C.c_int64()
+    _check(ctx, _lib.rbsog_get_cursor(ctx, C.byref(c)))
+    return c.value
+
+
+def rbsog_restore(ctx, f, kset_cursor: int, step: int):
+    _check(ctx, _lib.rbsog_restore(ctx, _ptr(f), int(kset_cursor), int(step)))
 
 
 def rbsog_get_energies(ctx):

@@ -728,6 +728,33 @@ rbsog_status rbsog_get_state(rbsog_ctx *ctx, double *x, double *v, double *f, in
     return leave(ctx);
 }
 
+rbsog_status rbsog_get_cursor(const rbsog_ctx *ctx, int64_t *kset_cursor) {
+    if (!ctx || !kset_cursor) return RBSOG_EINVAL;
+    *kset_cursor = ctx->host_cursor;
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_restore(rbsog_ctx *ctx, const double *f, int64_t kset_cursor, int64_t step) {
+    if (!ctx || !f) return RBSOG_EINVAL;
+    if (!ctx->have_state) return fail(ctx, RBSOG_ESTATE, "set_state must come first");
+    if (kset_cursor < 0 || kset_cursor > ctx->n_sets || step < 0)
+        return fail(ctx, RBSOG_EINVAL, "cursor %lld outside [0, %lld]", (long long)kset_cursor,
+                    (long long)ctx->n_sets);
+    rbsog_status es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    CK(cudaMemcpyAsync(ctx->staging, f, sizeof(double) * 3 * ctx->n, cudaMemcpyDefault, ctx->st));
+    CK(launch_pack(ctx->n, ctx->staging, nullptr, ctx->force, 0, ctx->p.L, ctx->st));
+    *ctx->h_i64 = kset_cursor;
+    CK(cudaMemcpyAsync(ctx->cursor, ctx->h_i64, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    *ctx->h_i64 = step;
+    CK(cudaMemcpyAsync(ctx->step_ctr, ctx->h_i64, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->host_cursor = kset_cursor;
+    ctx->force_valid = true;
+    return leave(ctx);
+}
+
 rbsog_status rbsog_get_energies(rbsog_ctx *ctx, rbsog_energies *e) {
     if (!ctx || !e) return RBSOG_EINVAL;
     rbsog_status es = enter(ctx);

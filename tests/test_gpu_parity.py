@@ -288,6 +288,38 @@ def test_graph_replay_equals_eager_launches():
         assert np.array_equal(a, b)
 
 
+def test_checkpoint_resume_is_bit_exact():
+    """6 steps in one run equal 3 steps, a checkpoint (x, v, f, cursor,
+    step) through host memory, a fresh context and 3 more steps."""
+    _dev()
+    B = _lib().binding
+    N, L, P = 4998, 21.5, 64
+    q, x, v = I.electrolyte(N, L, seed=8)
+    for prec in ("fp64", "fp32c"):
+        g, _ = make(N, L, P, prec=prec, n_ksets=8, seed=3)
+        g.set_state(*to_dev(q, x, v))
+        g.step(6)
+        ref = [a.cpu().numpy() for a in g.state()[:3]]
+        g.close()
+        g, _ = make(N, L, P, prec=prec, n_ksets=8, seed=3)
+        g.set_state(*to_dev(q, x, v))
+        g.step(3)
+        xs, vs, fs = (np.zeros((N, 3)) for _ in range(3))
+        step = B.rbsog_get_state(g.ctx, xs, vs, fs)
+        cur = B.rbsog_get_cursor(g.ctx)
+        assert (step, cur) == (3, 4)
+        g.close()
+        g, _ = make(N, L, P, prec=prec, n_ksets=8, seed=3)
+        B.rbsog_set_state(g.ctx, q, xs, vs)
+        B.rbsog_restore(g.ctx, fs, cur, step)
+        g.step(3)
+        out = [a.cpu().numpy() for a in g.state()[:3]]
+        assert g.state()[3] == 6
+        for a, b in zip(ref, out):
+            assert np.array_equal(a, b)
+        g.close()
+
+
 def test_runs_are_deterministic():
     _dev()
     N, L, P = 4998, 21.5, 64
