@@ -2,14 +2,21 @@
 // -grad of U_N with N(r) = 1/r - F_M(r) of Eq. 2.7), plus the WCA soft
 // repulsion, over the device cell list.
 //
-// Work decomposition: a block owns `group` consecutive cells of one x-row
-// (the "home" cells; in cell order their particles are contiguous).  It
-// stages the 9 neighbouring row segments (x0-1 .. xe, y +-1, z +-1; every
-// segment is one or two contiguous ranges of the cell-ordered arrays) into
-// shared memory with coalesced 16/32-byte loads, then each thread walks the
-// 27 cells around its home particle in shared memory.  Every ordered pair is
-// visited from both ends (no Newton-3 atomics), so forces and the
-// fixed-order energy partials are deterministic.
+// Work decomposition.  A block owns `group` consecutive cells of one x-row
+// (the home cells; in cell order their particles are contiguous) and one
+// thread per home particle.  The block stages the 9 neighbouring row
+// segments (x0-1 .. xe, y +-1, z +-1; each is one or two contiguous ranges
+// of the cell-ordered arrays) into shared memory with coalesced 16/32-byte
+// loads.  Each thread then works in two phases:
+//   test     walk the 27-cell candidate ranges of its particle (9 contiguous
+//            runs in shared memory) with distance tests only, appending the
+//            staged index of every partner within r_c to a private list in
+//            shared memory (thread-minor layout, conflict-free);
+//   compute  evaluate pair force and energy for the listed partners, so the
+//            expensive arithmetic runs without branch divergence.
+// Every ordered pair is visited from both ends (no Newton-3 atomics) and each
+// particle sums its partners in a fixed order, so forces and energies are
+// deterministic.
 //
 // FP64 path: separations d = (x_i - x_j) - L n with the image shift n of the
 // staged cell and r^2 = (dx^2 + dy^2) + dz^2 rounded after every operation,
@@ -27,11 +34,11 @@
 namespace rbsog {
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 128;   // one home particle per thread
 constexpr int kMaxGroup = 16;
 constexpr int kMaxStaged = 9 * (kMaxGroup + 2);
-constexpr int kCap64 = 2048;   // staged particles per chunk, FP64 (64 KiB)
-constexpr int kCap32 = 3072;   // staged particles per chunk, FP32C (48 KiB)
+constexpr int kList32 = 64;     // partner-list entries per thread, FP32C (uint16)
+constexpr int kList64 = 64;     // partner-list entries per thread, FP64 (int32: index | shift code)
 
 __device__ __forceinline__ int wrap_cell(int c, int n, int &shift) {
     shift = 0;
@@ -51,20 +58,118 @@ __device__ __forceinline__ float fixed_offset(uint32_t a, uint32_t o, float scal
     return (float)(int32_t)(a - o) * scale;
 }
 
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <int PREC>
-__global__ void __launch_bounds__(kThreads)
-    k_near(BoxDev box, NearSog sog, int group, int nseg_x, const int32_t *__restrict__ start,
-           const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
-           double4_32a *__restrict__ fnear, double2 *__restrict__ epart, int32_t *__restrict__ nbr) {
+struct NearTypes;
+template <>
+struct NearTypes<0> {
+    using real = double;
+    using staged = double4_32a;
+    using entry = int32_t;
+    static constexpr int kList = kList64;
+};
+template <>
+struct NearTypes<1> {
+    using real = float;
+    using staged = float4;
+    using entry = uint16_t;
+    static constexpr int kList = kList32;
+};
+
+template <int PREC, int ND, int NT>
+struct PairMath;
+
+template <int ND, int NT>
+struct PairMath<1, ND, NT> {
+    // fs = F_M(r) sum, gs = sum w_l/s_l^2 e^{-r^2/s_l^2}; coefficients are
+    // read from the grid-constant parameter block (constant-bank operands
+    // when the counts are compile-time constants)
+    static __device__ __forceinline__ void gauss(const NearSog &s, float r2, float &fs, float &gs) {
+        fs = 0.f;
+        gs = 0.f;
+        const int nd = ND > 0 ? ND : s.n_direct;
+#pragma unroll
+        for (int l = 0; l < (ND > 0 ? ND : kMaxGauss); ++l) {
+            if (l >= nd) break;
+            const float e = ex2_approx(-r2 * s.inv_s2_log2e_f[l]);
+            fs = fmaf(s.omega_f[l], e, fs);
+            gs = fmaf(s.omega_s2_f[l], e, gs);
+        }
+        const int nt = NT > 0 ? NT : s.n_taylor_f;
+        if (nt > 0) {
+            float pf = s.tay_f_f[nt - 1], pg = s.tay_g_f[nt - 1];
+#pragma unroll
+            for (int m = (NT > 0 ? NT : kMaxTaylor) - 2; m >= 0; --m) {
+                if (m > nt - 2) continue;
+                pf = fmaf(pf, r2, s.tay_f_f[m]);
+                pg = fmaf(pg, r2, s.tay_g_f[m]);
+            }
+            fs += pf;
+            gs += pg;
+        }
+    }
+    static __device__ __forceinline__ float inv_sqrt(float r2) { return rsqrtf(r2); }
+};
+
+template <int ND, int NT>
+struct PairMath<0, ND, NT> {
+    static __device__ __forceinline__ void gauss(const NearSog &s, double r2, double &fs, double &gs) {
+        fs = 0.0;
+        gs = 0.0;
+        const int nd = ND > 0 ? ND : s.n_direct;
+#pragma unroll
+        for (int l = 0; l < (ND > 0 ? ND : kMaxGauss); ++l) {
+            if (l >= nd) break;
+            const double e = exp(-r2 * s.inv_s2[l]);
+            fs += s.omega[l] * e;
+            gs += s.omega[l] * s.inv_s2[l] * e;
+        }
+        const int nt = NT > 0 ? NT : s.n_taylor;
+        if (nt > 0) {
+            double pf = s.tay_f[nt - 1], pg = s.tay_g[nt - 1];
+#pragma unroll
+            for (int m = (NT > 0 ? NT : kMaxTaylor) - 2; m >= 0; --m) {
+                if (m > nt - 2) continue;
+                pf = pf * r2 + s.tay_f[m];
+                pg = pg * r2 + s.tay_g[m];
+            }
+            fs += pf;
+            gs += pg;
+        }
+    }
+    static __device__ __forceinline__ double inv_sqrt(double r2) { return 1.0 / sqrt(r2); }
+};
+
+template <class real>
+struct PairConst {
+    real rc2, wrc2, ws2, weps, lB;
+};
+
+template <int PREC, int ND, int NT>
+__global__ void __launch_bounds__(kThreads, 4)
+    k_near(const __grid_constant__ BoxDev box, const __grid_constant__ NearSog sog, int group, int nseg_x,
+           int cap, const int32_t *__restrict__ start, const double4_32a *__restrict__ sp64,
+           const uint4 *__restrict__ sp32, double4_32a *__restrict__ fnear, double2 *__restrict__ epart,
+           int32_t *__restrict__ nbr) {
+    using T = NearTypes<PREC>;
+    using real = typename T::real;
+    using staged = typename T::staged;
+    using entry = typename T::entry;
+    using PM = PairMath<PREC, ND, NT>;
+    constexpr int kList = T::kList;
     __shared__ int s_off[kMaxStaged + 1];
     __shared__ int s_src[kMaxStaged];
     __shared__ int s_shift[kMaxStaged];
     __shared__ int s_hstart[kMaxGroup + 1];
     __shared__ double s_red[2][kThreads / 32];
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    double4_32a *st64 = reinterpret_cast<double4_32a *>(smem_raw);
-    float4 *st32 = reinterpret_cast<float4 *>(smem_raw);
-    const int cap = PREC == 0 ? kCap64 : kCap32;
+    staged *st = reinterpret_cast<staged *>(smem_raw);
+    entry *list = reinterpret_cast<entry *>(smem_raw + sizeof(staged) * (size_t)cap);   // [kList][kThreads]
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
@@ -107,166 +212,162 @@ __global__ void __launch_bounds__(kThreads)
     const int total = s_off[ns];
     const int hb = s_hstart[0], he = s_hstart[nh];
 
-    // FP32C origin: centre of the home segment in fixed point
-    uint32_t ox = 0, oy = 0, oz = 0;
-    if (PREC == 1) {
-        const double cxm = ((double)x0 + 0.5 * nh) * box.h[0] / box.L[0];
-        const double cym = ((double)cy + 0.5) * box.h[1] / box.L[1];
-        const double czm = ((double)cz + 0.5) * box.h[2] / box.L[2];
-        ox = (uint32_t)(uint64_t)(cxm * 4294967296.0);
-        oy = (uint32_t)(uint64_t)(cym * 4294967296.0);
-        oz = (uint32_t)(uint64_t)(czm * 4294967296.0);
+    uint32_t ox = 0, oy = 0, oz = 0;   // FP32C origin: centre of the home segment
+    if constexpr (PREC == 1) {
+        ox = (uint32_t)(uint64_t)(((double)x0 + 0.5 * nh) * box.h[0] / box.L[0] * 4294967296.0);
+        oy = (uint32_t)(uint64_t)(((double)cy + 0.5) * box.h[1] / box.L[1] * 4294967296.0);
+        oz = (uint32_t)(uint64_t)(((double)cz + 0.5) * box.h[2] / box.L[2] * 4294967296.0);
+    }
+    const float fsx = box.fix_scale[0], fsy = box.fix_scale[1], fsz = box.fix_scale[2];
+    PairConst<real> pc;
+    if constexpr (PREC == 0) {
+        pc = PairConst<real>{box.rc2, box.wca_rc2, box.wca_s2, box.wca_eps, box.lB};
+    } else {
+        pc = PairConst<real>{box.rc2_f, box.wca_rc2_f, box.wca_s2_f, box.wca_eps_f, box.lB_f};
     }
 
     double e_near = 0.0, e_wca = 0.0;
-    for (int base = hb; base < he; base += kThreads) {
-        const int hi = base + tid;
+    for (int rb = hb; rb < he; rb += kThreads) {   // rounds of one home particle per thread
+        const int hi = rb + tid;
         const bool active = hi < he;
         int cxr = 0;
-        if (active) {
+        if (active)
             while (cxr + 1 < nh && s_hstart[cxr + 1] <= hi) ++cxr;
-        }
-        double4_32a pi64 = make_double4_32a(0, 0, 0, 0);
-        float4 pi32 = make_float4(0, 0, 0, 0);
+        const int t_self = s_off[4 * w + cxr + 1] + (hi - s_hstart[cxr]);
+        real ix = 0, iy = 0, iz = 0, qi = 0;
         if (active) {
-            if (PREC == 0) {
-                pi64 = sp64[hi];
+            if constexpr (PREC == 0) {
+                const double4_32a p = sp64[hi];
+                ix = p.x; iy = p.y; iz = p.z; qi = p.w;
             } else {
                 const uint4 u = sp32[hi];
-                pi32 = make_float4(fixed_offset(u.x, ox, box.fix_scale[0]),
-                                   fixed_offset(u.y, oy, box.fix_scale[1]),
-                                   fixed_offset(u.z, oz, box.fix_scale[2]), __uint_as_float(u.w));
+                ix = fixed_offset(u.x, ox, fsx);
+                iy = fixed_offset(u.y, oy, fsy);
+                iz = fixed_offset(u.z, oz, fsz);
+                qi = __uint_as_float(u.w);
             }
         }
-        double fx = 0.0, fy = 0.0, fz = 0.0, un = 0.0, uw = 0.0;
-        float gx = 0.f, gy = 0.f, gz = 0.f, vn = 0.f, vw = 0.f;
+        real fx = 0, fy = 0, fz = 0, un = 0, uw = 0;
         int cnt = 0;
         for (int c0 = 0; c0 < total; c0 += cap) {
             const int c1 = min(c0 + cap, total);
             __syncthreads();
-            for (int t = c0 + tid; t < c1; t += kThreads) {
-                int lo = 0, hi2 = ns;   // largest k with s_off[k] <= t
-                while (hi2 - lo > 1) {
-                    const int mid = (lo + hi2) >> 1;
-                    if (s_off[mid] <= t) lo = mid; else hi2 = mid;
-                }
-                const int src = s_src[lo] + (t - s_off[lo]);
-                if (PREC == 0) {
-                    st64[t - c0] = sp64[src];
-                } else {
-                    const uint4 u = sp32[src];
-                    st32[t - c0] = make_float4(fixed_offset(u.x, ox, box.fix_scale[0]),
-                                               fixed_offset(u.y, oy, box.fix_scale[1]),
-                                               fixed_offset(u.z, oz, box.fix_scale[2]),
-                                               __uint_as_float(u.w));
-                }
-            }
-            __syncthreads();
-            if (!active) continue;
+            // stage [c0, c1): per row the cell x0-1, the contiguous block
+            // x0..xe-1 of the row, and the cell xe
             for (int r = 0; r < 9; ++r) {
-                for (int q3 = 0; q3 < 3; ++q3) {
-                    const int k = r * w + cxr + q3;
-                    const int tb = max(s_off[k], c0), te = min(s_off[k + 1], c1);
-                    if (tb >= te) continue;
-                    const int srcb = s_src[k] - s_off[k];
-                    if (PREC == 0) {
-                        const int sh = s_shift[k];
-                        const double lx = box.L[0] * (double)((sh & 3) - 1);
-                        const double ly = box.L[1] * (double)(((sh >> 2) & 3) - 1);
-                        const double lz = box.L[2] * (double)(((sh >> 4) & 3) - 1);
-                        for (int t = tb; t < te; ++t) {
-                            const double4_32a pj = st64[t - c0];
-                            const double dx = __dsub_rn(__dsub_rn(pi64.x, pj.x), lx);
-                            const double dy = __dsub_rn(__dsub_rn(pi64.y, pj.y), ly);
-                            const double dz = __dsub_rn(__dsub_rn(pi64.z, pj.z), lz);
-                            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                                        __dmul_rn(dz, dz));
-                            if (!(r2 < box.rc2) || srcb + t == hi) continue;
-                            ++cnt;
-                            const double inv_r = 1.0 / sqrt(r2);
-                            double fs = 0.0, gs = 0.0;
-                            for (int l = 0; l < sog.n_direct; ++l) {
-                                const double e = exp(-r2 * sog.inv_s2[l]);
-                                fs += sog.omega[l] * e;
-                                gs += sog.omega[l] * sog.inv_s2[l] * e;
-                            }
-                            if (sog.n_taylor > 0) {
-                                double pf = sog.tay_f[sog.n_taylor - 1], pg = sog.tay_g[sog.n_taylor - 1];
-                                for (int m = sog.n_taylor - 2; m >= 0; --m) {
-                                    pf = pf * r2 + sog.tay_f[m];
-                                    pg = pg * r2 + sog.tay_g[m];
-                                }
-                                fs += pf;
-                                gs += pg;
-                            }
-                            const double qq = box.lB * pi64.w * pj.w;
-                            double g = qq * (inv_r * inv_r * inv_r - 2.0 * gs);
-                            un += 0.5 * qq * (inv_r - fs);
-                            if (r2 < box.wca_rc2) {
-                                const double sr2 = box.wca_s2 / r2;
-                                const double sr6 = sr2 * sr2 * sr2;
-                                g += 24.0 * box.wca_eps * (2.0 * sr6 * sr6 - sr6) / r2;
-                                uw += 0.5 * (4.0 * box.wca_eps * (sr6 * sr6 - sr6) + box.wca_eps);
-                            }
-                            fx += g * dx;
-                            fy += g * dy;
-                            fz += g * dz;
-                        }
-                    } else {
-                        const float rc2 = (float)box.rc2;
-                        const float wrc2 = (float)box.wca_rc2;
-                        for (int t = tb; t < te; ++t) {
-                            const float4 pj = st32[t - c0];
-                            const float dx = pi32.x - pj.x, dy = pi32.y - pj.y, dz = pi32.z - pj.z;
-                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                            if (!(r2 < rc2) || srcb + t == hi) continue;
-                            ++cnt;
-                            const float inv_r = rsqrtf(r2);
-                            float fs = 0.f, gs = 0.f;
-                            for (int l = 0; l < sog.n_direct; ++l) {
-                                const float e = __expf(-r2 * sog.inv_s2_f[l]);
-                                fs = fmaf(sog.omega_f[l], e, fs);
-                                gs = fmaf(sog.omega_f[l] * sog.inv_s2_f[l], e, gs);
-                            }
-                            if (sog.n_taylor > 0) {
-                                float pf = sog.tay_f_f[sog.n_taylor - 1], pg = sog.tay_g_f[sog.n_taylor - 1];
-                                for (int m = sog.n_taylor - 2; m >= 0; --m) {
-                                    pf = fmaf(pf, r2, sog.tay_f_f[m]);
-                                    pg = fmaf(pg, r2, sog.tay_g_f[m]);
-                                }
-                                fs += pf;
-                                gs += pg;
-                            }
-                            const float qq = (float)box.lB * pi32.w * pj.w;
-                            float g = qq * (inv_r * inv_r * inv_r - 2.f * gs);
-                            vn = fmaf(0.5f * qq, inv_r - fs, vn);
-                            if (r2 < wrc2) {
-                                const float sr2 = (float)box.wca_s2 / r2;
-                                const float sr6 = sr2 * sr2 * sr2;
-                                const float we = (float)box.wca_eps;
-                                g += 24.f * we * (2.f * sr6 * sr6 - sr6) / r2;
-                                vw += 0.5f * (4.f * we * (sr6 * sr6 - sr6) + we);
-                            }
-                            gx = fmaf(g, dx, gx);
-                            gy = fmaf(g, dy, gy);
-                            gz = fmaf(g, dz, gz);
+                const int k = r * w;
+                const int plo[3] = {s_off[k], s_off[k + 1], s_off[k + w - 1]};
+                const int phi[3] = {s_off[k + 1], s_off[k + w - 1], s_off[k + w]};
+                const int psrc[3] = {s_src[k], s_src[k + 1], s_src[k + w - 1]};
+#pragma unroll
+                for (int pp = 0; pp < 3; ++pp) {
+                    const int a = max(plo[pp], c0), b = min(phi[pp], c1);
+                    for (int t = a + tid; t < b; t += kThreads) {
+                        const int src = psrc[pp] + (t - plo[pp]);
+                        if constexpr (PREC == 0) {
+                            st[t - c0] = sp64[src];
+                        } else {
+                            const uint4 u = sp32[src];
+                            st[t - c0] = make_float4(fixed_offset(u.x, ox, fsx), fixed_offset(u.y, oy, fsy),
+                                                     fixed_offset(u.z, oz, fsz), __uint_as_float(u.w));
                         }
                     }
                 }
             }
+            __syncthreads();
+            if (!active) continue;
+            int n = 0;
+            // pair force and energy for list entries [0, n)
+            auto compute = [&]() {
+                for (int e = 0; e < n; ++e) {
+                    const entry en = list[e * kThreads + tid];
+                    const int t = (int)en & 0xFFFFF;
+                    real dx, dy, dz, r2, qj;
+                    if constexpr (PREC == 0) {
+                        const int code = (int)en >> 20;
+                        const double4_32a pj = st[t];
+                        const double lx = box.L[0] * (double)((code & 3) - 1);
+                        const double ly = box.L[1] * (double)(((code >> 2) & 3) - 1);
+                        const double lz = box.L[2] * (double)(((code >> 4) & 3) - 1);
+                        dx = __dsub_rn(__dsub_rn(ix, pj.x), lx);
+                        dy = __dsub_rn(__dsub_rn(iy, pj.y), ly);
+                        dz = __dsub_rn(__dsub_rn(iz, pj.z), lz);
+                        r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                        qj = pj.w;
+                    } else {
+                        const float4 pj = st[t];
+                        dx = ix - pj.x;
+                        dy = iy - pj.y;
+                        dz = iz - pj.z;
+                        r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        qj = pj.w;
+                    }
+                    const real qq = pc.lB * qi * qj;
+                    real fs, gs;
+                    PM::gauss(sog, r2, fs, gs);
+                    const real inv_r = PM::inv_sqrt(r2);
+                    real g = qq * (inv_r * inv_r * inv_r - (real)2 * gs);
+                    un += (real)0.5 * qq * (inv_r - fs);
+                    if (r2 < pc.wrc2) {
+                        const real sr2 = pc.ws2 / r2;
+                        const real sr6 = sr2 * sr2 * sr2;
+                        g += (real)24 * pc.weps * ((real)2 * sr6 * sr6 - sr6) / r2;
+                        uw += (real)0.5 * ((real)4 * pc.weps * (sr6 * sr6 - sr6) + pc.weps);
+                    }
+                    fx += g * dx;
+                    fy += g * dy;
+                    fz += g * dz;
+                }
+                cnt += n;
+                n = 0;
+            };
+            for (int r = 0; r < 9; ++r) {
+                const int k0 = r * w + cxr;
+                const int lo = max(s_off[k0], c0), hi3 = min(s_off[k0 + 3], c1);
+                int b1 = 0, b2 = 0, code0 = 0, code1 = 0, code2 = 0;
+                if constexpr (PREC == 0) {
+                    b1 = s_off[k0 + 1];
+                    b2 = s_off[k0 + 2];
+                    code0 = s_shift[k0];
+                    code1 = s_shift[k0 + 1];
+                    code2 = s_shift[k0 + 2];
+                }
+                // the list always has room for a whole run of candidates, so
+                // the test loop below never branches into the pair arithmetic
+                for (int tb = lo; tb < hi3; tb += kList) {
+                    const int te = min(tb + kList, hi3);
+                    if (n + (te - tb) > kList) compute();
+#pragma unroll 4
+                    for (int t = tb; t < te; ++t) {
+                        bool ok;
+                        int code = 0;
+                        if constexpr (PREC == 0) {
+                            code = t < b1 ? code0 : (t < b2 ? code1 : code2);
+                            const double4_32a pj = st[t - c0];
+                            const double dx = __dsub_rn(__dsub_rn(ix, pj.x), box.L[0] * (double)((code & 3) - 1));
+                            const double dy = __dsub_rn(__dsub_rn(iy, pj.y), box.L[1] * (double)(((code >> 2) & 3) - 1));
+                            const double dz = __dsub_rn(__dsub_rn(iz, pj.z), box.L[2] * (double)(((code >> 4) & 3) - 1));
+                            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                            ok = r2 < pc.rc2;
+                        } else {
+                            const float4 pj = st[t - c0];
+                            const float dx = ix - pj.x, dy = iy - pj.y, dz = iz - pj.z;
+                            ok = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < pc.rc2;
+                        }
+                        if (ok && t != t_self) {
+                            list[n * kThreads + tid] = (entry)((t - c0) | (code << 20));
+                            ++n;
+                        }
+                    }
+                }
+            }
+            compute();
         }
         if (active) {
-            if (PREC == 1) {
-                fx = gx;
-                fy = gy;
-                fz = gz;
-                un = vn;
-                uw = vw;
-            }
-            fnear[hi] = make_double4_32a(fx, fy, fz, 0.0);
+            fnear[hi] = make_double4_32a((double)fx, (double)fy, (double)fz, 0.0);
             if (nbr) nbr[hi] = cnt;
-            e_near += un;
-            e_wca += uw;
+            e_near += (double)un;
+            e_wca += (double)uw;
         }
     }
     // fixed-order block reduction of the energies
@@ -290,6 +391,11 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+size_t near_smem(int precision, int cap) {
+    if (precision == 0) return sizeof(double4_32a) * (size_t)cap + sizeof(int32_t) * kList64 * kThreads;
+    return sizeof(float4) * (size_t)cap + sizeof(uint16_t) * kList32 * kThreads;
+}
+
 }  // namespace
 
 int near_num_blocks(const BoxDev &box, int group) {
@@ -297,31 +403,30 @@ int near_num_blocks(const BoxDev &box, int group) {
     return nseg_x * box.nc[1] * box.nc[2];
 }
 
-cudaError_t launch_near(int precision, const BoxDev &box, const NearSog &sog, int group,
+cudaError_t launch_near(int precision, const BoxDev &box, const NearSog &sog, int group, int cap,
                         const int32_t *start, const double4_32a *sp64, const uint4 *sp32,
                         double4_32a *fnear, double2 *epart, int32_t *nbr, cudaStream_t st,
                         const Prof *prof) {
-    if (group < 1 || group > kMaxGroup) return cudaErrorInvalidValue;
-    static bool attr_done[2] = {false, false};
+    if (group < 1 || group > kMaxGroup || cap < 32 || cap > (1 << 20)) return cudaErrorInvalidValue;
     const int nseg_x = (box.nc[0] + group - 1) / group;
     const unsigned blocks = (unsigned)(nseg_x * box.nc[1] * box.nc[2]);
-    ProfScope ps(prof, precision == 0 ? "near_fp64" : "near_fp32c");
-    if (precision == 0) {
-        const size_t sm = sizeof(double4_32a) * kCap64;
-        if (!attr_done[0]) {
-            cudaFuncSetAttribute(k_near<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            attr_done[0] = true;
-        }
-        k_near<0><<<blocks, kThreads, sm, st>>>(box, sog, group, nseg_x, start, sp64, sp32, fnear,
-                                               epart, nbr);
+    const size_t sm = near_smem(precision, cap);
+    // specialised (fully unrolled) variants for the production kernel: b = 1.4878...
+    // gives 5 exp Gaussians below 2 r_c and 8 (FP32) / 12 (FP64) Taylor terms
+    // for any r_c; other parameter sets take the runtime-count variant
+    const bool spec = sog.n_direct == 5 && (precision == 1 ? sog.n_taylor_f == 8 : sog.n_taylor == 12);
+    ProfScope ps(prof, precision == 0 ? (spec ? "near_fp64" : "near_fp64_generic")
+                                      : (spec ? "near_fp32c" : "near_fp32c_generic"));
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<blocks, kThreads, sm, st>>>(box, sog, group, nseg_x, cap, start, sp64, sp32, fnear, epart, nbr);
+    };
+    if (precision == 1) {
+        if (spec) go(k_near<1, 5, 8>);
+        else go(k_near<1, 0, 0>);
     } else {
-        const size_t sm = sizeof(float4) * kCap32;
-        if (!attr_done[1]) {
-            cudaFuncSetAttribute(k_near<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            attr_done[1] = true;
-        }
-        k_near<1><<<blocks, kThreads, sm, st>>>(box, sog, group, nseg_x, start, sp64, sp32, fnear,
-                                               epart, nbr);
+        if (spec) go(k_near<0, 5, 12>);
+        else go(k_near<0, 0, 0>);
     }
     return cudaGetLastError();
 }

@@ -45,7 +45,7 @@ struct rbsog_ctx {
     double sigma = 0, omega0 = 0, S = 0, V = 0, coef = 0, half_coef_U = 0, U_self = 0, sum_q2 = 0;
     BoxDev box{};
     NearSog nsog{};
-    int group = 1, tile_p = 2048, n_ptiles = 1, n_epart = 1, n_kpart = 1;
+    int group = 1, near_cap = 1024, tile_p = 2048, n_ptiles = 1, n_epart = 1, n_kpart = 1;
     int64_t n_sets = 0, n_chains = 0;
     int chain_len = 256;
     int64_t host_cursor = 0;  // k-sets consumed, mirrored on the host
@@ -255,7 +255,8 @@ void build_near_sog(rbsog_ctx *c) {
         ns.omega[l] = c->omega[l];
         ns.inv_s2[l] = 1.0 / (c->s[l] * c->s[l]);
         ns.omega_f[l] = (float)ns.omega[l];
-        ns.inv_s2_f[l] = (float)ns.inv_s2[l];
+        ns.omega_s2_f[l] = (float)(ns.omega[l] * ns.inv_s2[l]);
+        ns.inv_s2_log2e_f[l] = (float)(ns.inv_s2[l] * 1.4426950408889634);
     }
     ns.n_taylor = 0;
     if (nd <= M) {
@@ -266,15 +267,21 @@ void build_near_sog(rbsog_ctx *c) {
             for (int l = M; l >= nd; --l) A[n] += c->omega[l] * std::pow(c->s[l], -2.0 * n);
         }
         const double xmax = rc * rc / (c->s[nd] * c->s[nd]);
-        int nt = 1;
-        double fact = 1.0, xp = 1.0;
-        while (nt < kMaxTaylor) {
-            xp *= xmax;
-            fact *= nt;
-            if (xp / fact < 1e-19) break;
-            ++nt;
-        }
+        // smallest number of terms whose first omitted term x^n / n! is below tol
+        auto terms = [xmax](double tol) {
+            int nt = 1;
+            double fact = 1.0, xp = 1.0;
+            while (nt < kMaxTaylor) {
+                xp *= xmax;
+                fact *= nt;
+                if (xp / fact < tol) break;
+                ++nt;
+            }
+            return nt;
+        };
+        const int nt = terms(1e-19);
         ns.n_taylor = nt;
+        ns.n_taylor_f = terms(1e-10);
         double f = 1.0;
         for (int n = 0; n < nt; ++n) {
             if (n > 0) f *= n;
@@ -338,7 +345,7 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const int4 *m_explicit, int32_t *nbr
     const int prec = ctx->p.precision;
     CK(launch_build_cells(ctx->n, ctx->posq, ctx->box, ctx->cb, prec, ctx->sp64, ctx->sp32,
                           ctx->err_flag, ctx->st, pf));
-    CK(launch_near(prec, ctx->box, ctx->nsog, ctx->group, ctx->cb.start, ctx->sp64, ctx->sp32,
+    CK(launch_near(prec, ctx->box, ctx->nsog, ctx->group, ctx->near_cap, ctx->cb.start, ctx->sp64, ctx->sp32,
                    ctx->fnear, ctx->epart, nbr_sorted, ctx->st, pf));
     const FarArgs fa = far_args(ctx, m_explicit, ctx->p.P);
     CK(launch_rho_sweep(prec, fa, ctx->sp64, ctx->sp32, ctx->rho_part, ctx->st, pf));
@@ -498,13 +505,26 @@ rbsog_status rbsog_set_params(rbsog_ctx *ctx, const rbsog_params *pp) {
     b.wca_s2 = p.wca_sigma * p.wca_sigma;
     b.wca_rc2 = p.wca_sigma > 0.0 ? std::pow(2.0, 1.0 / 3.0) * b.wca_s2 : 0.0;
     b.wca_eps = p.wca_eps;
+    b.rc2_f = (float)b.rc2;
+    b.lB_f = (float)b.lB;
+    b.wca_s2_f = (float)b.wca_s2;
+    b.wca_rc2_f = (float)b.wca_rc2;
+    b.wca_eps_f = (float)b.wca_eps;
     build_near_sog(ctx);
 
+    // near field: one thread per home particle, ~110 home particles per block;
+    // the staging chunk covers the mean occupancy of the 9 (group + 2) staged
+    // cells with 30% head-room (denser regions are processed in chunks)
     const double per_cell = (double)ctx->n / (double)ncell;
-    int g = (int)std::lround(100.0 / std::max(per_cell, 1e-3));
+    int g = (int)std::lround(110.0 / std::max(per_cell, 1e-3));
     g = std::max(1, std::min(g, std::min(16, nc[0] - 2)));
     ctx->group = g;
     ctx->n_epart = near_num_blocks(b, g);
+    {
+        const double est = 9.0 * (g + 2) * per_cell * 1.3 + 64.0;
+        const int cap_max = p.precision == RBSOG_FP64 ? 2048 : 4096;
+        ctx->near_cap = std::min(cap_max, std::max(256, ((int)std::ceil(est) + 127) / 128 * 128));
+    }
 
     const int nkt = (p.P + 31) / 32;
     int tp = 2048;
@@ -831,7 +851,7 @@ rbsog_status rbsog_get_cells(rbsog_ctx *ctx, int32_t *cell_start, int32_t *perm,
     CK(launch_build_cells(ctx->n, ctx->posq, ctx->box, ctx->cb, ctx->p.precision, ctx->sp64, ctx->sp32,
                           ctx->err_flag, ctx->st, pf));
     if (nbr) {
-        CK(launch_near(ctx->p.precision, ctx->box, ctx->nsog, ctx->group, ctx->cb.start, ctx->sp64,
+        CK(launch_near(ctx->p.precision, ctx->box, ctx->nsog, ctx->group, ctx->near_cap, ctx->cb.start, ctx->sp64,
                        ctx->sp32, ctx->fnear, ctx->epart, ctx->nbr_sorted, ctx->st, pf));
         CK(launch_unsort_i32(ctx->n, ctx->cb.perm, ctx->nbr_sorted, ctx->i32_tmp, ctx->st));
         CK(cudaMemcpyAsync(nbr, ctx->i32_tmp, sizeof(int32_t) * ctx->n, cudaMemcpyDefault, ctx->st));

@@ -18,13 +18,15 @@ constexpr int kMaxTaylor = 16;   // terms of the folded wide-Gaussian series
 // and     sum_{wide} w_l/s_l^2 e^{-r^2/s_l^2} = sum_n (-r^2)^n / n! A[n+1].
 struct NearSog {
     int32_t n_direct;
-    int32_t n_taylor;              // number of Taylor terms used (n = 0..n_taylor-1)
+    int32_t n_taylor;              // Taylor terms for FP64 (truncation < 1e-19 relative)
+    int32_t n_taylor_f;            // Taylor terms for FP32 (truncation < 1e-10 relative)
     double omega[kMaxGauss];       // w_l, l < n_direct
     double inv_s2[kMaxGauss];      // 1 / s_l^2, l < n_direct
     double tay_f[kMaxTaylor];      // A[n] / n! with sign (-1)^n folded in
     double tay_g[kMaxTaylor];      // A[n+1] / n! with sign (-1)^n folded in
     float omega_f[kMaxGauss];
-    float inv_s2_f[kMaxGauss];
+    float omega_s2_f[kMaxGauss];   // w_l / s_l^2
+    float inv_s2_log2e_f[kMaxGauss];  // log2(e) / s_l^2 (argument of ex2)
     float tay_f_f[kMaxTaylor];
     float tay_g_f[kMaxTaylor];
 };
@@ -42,6 +44,8 @@ struct BoxDev {
     double wca_eps;
     float L_f[3];
     float fix_scale[3];   // L_d / 2^32: fixed-point unit of the FP32C positions
+    // FP32 copies of the pair constants (no double->float conversion in kernels)
+    float rc2_f, lB_f, wca_s2_f, wca_rc2_f, wca_eps_f;
 };
 
 // Sampler inputs (Sec. 3.3): full SOG (not folded) in FP64.
@@ -96,7 +100,8 @@ cudaError_t launch_build_cells(int64_t n, const double4_32a *posq, const BoxDev 
 // Forces (sorted order) into fnear; per-block energy partials (U_near, U_wca)
 // into epart[nblocks]; neighbour counts (sorted order) into nbr when non-null.
 int near_num_blocks(const BoxDev &box, int group);
-cudaError_t launch_near(int precision, const BoxDev &box, const NearSog &sog, int group,
+// cap: staged particles per shared-memory chunk (larger regions are chunked).
+cudaError_t launch_near(int precision, const BoxDev &box, const NearSog &sog, int group, int cap,
                         const int32_t *start, const double4_32a *sp64, const uint4 *sp32,
                         double4_32a *fnear, double2 *epart, int32_t *nbr, cudaStream_t st,
                         const Prof *prof);

@@ -283,6 +283,7 @@ def test_graph_replay_equals_eager_launches():
         if prof:
             rep = _lib().binding.rbsog_get_profile(g.ctx)
             assert rep["far_scatter_fp32c"][0] == steps + 1
+            assert "near_fp32c" in rep       # the production SOG set runs the unrolled variant
         g.close()
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
