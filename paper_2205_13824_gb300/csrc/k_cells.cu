@@ -3,10 +3,11 @@
 //   bin      one thread per particle: cell id (FP64 floor(x / h), the same
 //            decision as any IEEE evaluation) and an arrival slot from an
 //            integer atomic on the cell's counter;
-//   scan     one block, warp-shuffle exclusive scan of the counters into cell
-//            start offsets (and the counters are cleared for the next build);
+//   scan     two launches: per-tile warp-shuffle scans, then tile offsets
+//            (the counters are cleared for the next build);
 //   scatter  one thread per particle: perm_raw[start + slot] = i;
 //   order    one warp per cell: ranks the cell's members by particle index
+//            (indices exchanged by warp shuffles)
 //            (so the order inside a cell, and everything summed in that
 //            order, is deterministic) and gathers the particle data into
 //            cell order -- FP64 (x, y, z, q) or, for the FP32C path, 32-bit
@@ -37,17 +38,30 @@ __global__ void __launch_bounds__(256) k_bin(int64_t n, const double4_32a *__res
     slot[i] = atomicAdd(&count[cell], 1);
 }
 
-// Exclusive scan of count[0..ncell) into start[0..ncell], single block of
-// 1024 threads: each thread owns a contiguous chunk, chunk sums are scanned
-// with warp shuffles, then every chunk is written out.  Clears count.
-__global__ void __launch_bounds__(1024) k_scan(int ncell, int32_t *__restrict__ count,
-                                               int32_t *__restrict__ start) {
-    __shared__ int warp_tot[32];
+// Exclusive scan of count[0..ncell) into start[0..ncell] in two launches:
+//   tile   each block scans a tile of kScanTile counters (8 per thread,
+//          warp-shuffle scan of the thread sums) into start[] and writes the
+//          tile total;
+//   add    each block sums the totals of the tiles before it (fixed order)
+//          and adds that offset to its tile; the counters are cleared for the
+//          next build and start[ncell] receives the grand total.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile(int ncell, const int32_t *__restrict__ count,
+                                                            int32_t *__restrict__ start,
+                                                            int32_t *__restrict__ tile_sum) {
+    __shared__ int warp_tot[kScanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int chunk = (ncell + blockDim.x - 1) / blockDim.x;
-    const int b = tid * chunk, e = min(b + chunk, ncell);
+    const int base = blockIdx.x * kScanTile + tid * kScanPer;
+    int v[kScanPer];
     int local = 0;
-    for (int j = b; j < e; ++j) local += count[j];
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+        v[j] = base + j < ncell ? count[base + j] : 0;
+        local += v[j];
+    }
     int incl = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -56,24 +70,40 @@ __global__ void __launch_bounds__(1024) k_scan(int ncell, int32_t *__restrict__ 
     }
     if (lane == 31) warp_tot[wid] = incl;
     __syncthreads();
-    if (wid == 0) {
-        int w = warp_tot[lane];
+    int woff = 0;
+    for (int w = 0; w < wid; ++w) woff += warp_tot[w];
+    int run = woff + incl - local;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += t;
-        }
-        warp_tot[lane] = w;  // inclusive over warps
+    for (int j = 0; j < kScanPer; ++j) {
+        if (base + j < ncell) start[base + j] = run;
+        run += v[j];
+    }
+    if (tid == kScanThreads - 1) tile_sum[blockIdx.x] = woff + incl;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(int ncell, int ntiles, int32_t *__restrict__ count,
+                                                           int32_t *__restrict__ start,
+                                                           const int32_t *__restrict__ tile_sum) {
+    __shared__ int s_off;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        int acc = 0;
+        for (int t = lane; t < (int)blockIdx.x; t += 32) acc += tile_sum[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_off = acc;
     }
     __syncthreads();
-    int run = incl - local + (wid > 0 ? warp_tot[wid - 1] : 0);
-    for (int j = b; j < e; ++j) {
-        const int cj = count[j];
-        start[j] = run;
-        run += cj;
-        count[j] = 0;
+    const int off = s_off;
+    const int base = blockIdx.x * kScanTile;
+    for (int j = tid; j < kScanTile; j += kScanThreads) {
+        const int c = base + j;
+        if (c < ncell) {
+            start[c] += off;
+            count[c] = 0;
+        }
     }
-    if (tid == blockDim.x - 1) start[ncell] = warp_tot[31];
+    if (blockIdx.x == ntiles - 1 && tid == 0) start[ncell] = off + tile_sum[ntiles - 1];
 }
 
 __global__ void __launch_bounds__(256) k_scatter(int64_t n, const int32_t *__restrict__ cell_of,
@@ -91,7 +121,8 @@ __device__ __forceinline__ uint32_t to_fixed32(double x, double L) {
     return (uint32_t)__double2ull_rz(c);
 }
 
-// One warp per cell: rank = number of members with a smaller particle index.
+// One warp per cell: rank = number of members with a smaller particle index
+// (the members' indices are exchanged by shuffles for cells of up to 32).
 __global__ void __launch_bounds__(256) k_order_gather(int ncell, const int32_t *__restrict__ start,
                                                       const int32_t *__restrict__ perm_raw,
                                                       int32_t *__restrict__ perm,
@@ -102,27 +133,36 @@ __global__ void __launch_bounds__(256) k_order_gather(int ncell, const int32_t *
     const int cell = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (cell >= ncell) return;
     const int b = start[cell], e = start[cell + 1], cnt = e - b;
-    for (int t = lane; t < cnt; t += 32) {
-        const int idx = perm_raw[b + t];
+    for (int t0 = 0; t0 < cnt; t0 += 32) {
+        const int t = t0 + lane;
+        const int idx = t < cnt ? perm_raw[b + t] : 0x7fffffff;
         int rank = 0;
-        for (int u = 0; u < cnt; ++u) rank += (perm_raw[b + u] < idx) ? 1 : 0;
-        const int s = b + rank;
-        perm[s] = idx;
-        const double4_32a p = posq[idx];
-        if (precision == 0) {
-            sp64[s] = p;
+        if (cnt <= 32) {
+            for (int u = 0; u < cnt; ++u) rank += (__shfl_sync(0xffffffffu, idx, u) < idx) ? 1 : 0;
         } else {
-            uint4 o;
-            o.x = to_fixed32(p.x, box.L[0]);
-            o.y = to_fixed32(p.y, box.L[1]);
-            o.z = to_fixed32(p.z, box.L[2]);
-            o.w = __float_as_uint((float)p.w);
-            sp32[s] = o;
+            for (int u = 0; u < cnt; ++u) rank += (perm_raw[b + u] < idx) ? 1 : 0;
+        }
+        if (t < cnt) {
+            const int s = b + rank;
+            perm[s] = idx;
+            const double4_32a p = posq[idx];
+            if (precision == 0) {
+                sp64[s] = p;
+            } else {
+                uint4 o;
+                o.x = to_fixed32(p.x, box.L[0]);
+                o.y = to_fixed32(p.y, box.L[1]);
+                o.z = to_fixed32(p.z, box.L[2]);
+                o.w = __float_as_uint((float)p.w);
+                sp32[s] = o;
+            }
         }
     }
 }
 
 }  // namespace
+
+int cell_scan_tiles(int ncell) { return (ncell + kScanTile - 1) / kScanTile; }
 
 cudaError_t launch_build_cells(int64_t n, const double4_32a *posq, const BoxDev &box,
                                const CellBuffers &cb, int precision, double4_32a *sp64, uint4 *sp32,
@@ -136,7 +176,9 @@ cudaError_t launch_build_cells(int64_t n, const double4_32a *posq, const BoxDev 
     }
     {
         ProfScope ps(prof, "cell_scan");
-        k_scan<<<1, 1024, 0, st>>>(box.ncell, cb.count, cb.start);
+        const int ntiles = (box.ncell + kScanTile - 1) / kScanTile;
+        k_scan_tile<<<ntiles, kScanThreads, 0, st>>>(box.ncell, cb.count, cb.start, cb.tile_sum);
+        k_scan_add<<<ntiles, kScanThreads, 0, st>>>(box.ncell, ntiles, cb.count, cb.start, cb.tile_sum);
     }
     {
         ProfScope ps(prof, "cell_scatter");

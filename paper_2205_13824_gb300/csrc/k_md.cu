@@ -28,9 +28,13 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift(MdArgs a, double4_32a *
     v.x += h * f.x;
     v.y += h * f.y;
     v.z += h * f.z;
-    p.x = fold(p.x + a.dt * v.x, a.L[0]);
-    p.y = fold(p.y + a.dt * v.y, a.L[1]);
-    p.z = fold(p.z + a.dt * v.z, a.L[2]);
+    // fold only coordinates that left the box (the division is FP64-pipe bound)
+    p.x += a.dt * v.x;
+    p.y += a.dt * v.y;
+    p.z += a.dt * v.z;
+    if (p.x < 0.0 || p.x >= a.L[0]) p.x = fold(p.x, a.L[0]);
+    if (p.y < 0.0 || p.y >= a.L[1]) p.y = fold(p.y, a.L[1]);
+    if (p.z < 0.0 || p.z >= a.L[2]) p.z = fold(p.z, a.L[2]);
     vel[i] = v;
     posq[i] = p;
 }

@@ -166,10 +166,11 @@ __global__ void __launch_bounds__(kThreads, 4)
     __shared__ int s_src[kMaxStaged];
     __shared__ int s_shift[kMaxStaged];
     __shared__ int s_hstart[kMaxGroup + 1];
-    __shared__ double s_red[2][kThreads / 32];
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    staged *st = reinterpret_cast<staged *>(smem_raw);
-    entry *list = reinterpret_cast<entry *>(smem_raw + sizeof(staged) * (size_t)cap);   // [kList][kThreads]
+    // disjoint regions: restrict lets the compiler move staged loads across
+    // list stores
+    staged *__restrict__ st = reinterpret_cast<staged *>(smem_raw);
+    entry *__restrict__ list = reinterpret_cast<entry *>(smem_raw + sizeof(staged) * (size_t)cap);   // [kList][kThreads]
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
@@ -227,58 +228,66 @@ __global__ void __launch_bounds__(kThreads, 4)
     }
 
     double e_near = 0.0, e_wca = 0.0;
-    for (int rb = hb; rb < he; rb += kThreads) {   // rounds of one home particle per thread
-        const int hi = rb + tid;
-        const bool active = hi < he;
-        int cxr = 0;
-        if (active)
-            while (cxr + 1 < nh && s_hstart[cxr + 1] <= hi) ++cxr;
-        const int t_self = s_off[4 * w + cxr + 1] + (hi - s_hstart[cxr]);
-        real ix = 0, iy = 0, iz = 0, qi = 0;
-        if (active) {
-            if constexpr (PREC == 0) {
-                const double4_32a p = sp64[hi];
-                ix = p.x; iy = p.y; iz = p.z; qi = p.w;
-            } else {
-                const uint4 u = sp32[hi];
-                ix = fixed_offset(u.x, ox, fsx);
-                iy = fixed_offset(u.y, oy, fsy);
-                iz = fixed_offset(u.z, oz, fsz);
-                qi = __uint_as_float(u.w);
-            }
-        }
-        real fx = 0, fy = 0, fz = 0, un = 0, uw = 0;
-        int cnt = 0;
-        for (int c0 = 0; c0 < total; c0 += cap) {
-            const int c1 = min(c0 + cap, total);
-            __syncthreads();
-            // stage [c0, c1): per row the cell x0-1, the contiguous block
-            // x0..xe-1 of the row, and the cell xe
-            for (int r = 0; r < 9; ++r) {
-                const int k = r * w;
-                const int plo[3] = {s_off[k], s_off[k + 1], s_off[k + w - 1]};
-                const int phi[3] = {s_off[k + 1], s_off[k + w - 1], s_off[k + w]};
-                const int psrc[3] = {s_src[k], s_src[k + 1], s_src[k + w - 1]};
+    // Staging: one chunk [c0, c1) of the staged region at a time (normally the
+    // whole region fits); every warp then works through the home particles in
+    // runs of 32 consecutive particles (one per lane).
+    for (int c0 = 0; c0 < total; c0 += cap) {
+        const int c1 = min(c0 + cap, total);
+        if (c0 > 0) __syncthreads();
+        for (int r = 0; r < 9; ++r) {
+            const int k = r * w;
+            const int plo[3] = {s_off[k], s_off[k + 1], s_off[k + w - 1]};
+            const int phi[3] = {s_off[k + 1], s_off[k + w - 1], s_off[k + w]};
+            const int psrc[3] = {s_src[k], s_src[k + 1], s_src[k + w - 1]};
 #pragma unroll
-                for (int pp = 0; pp < 3; ++pp) {
-                    const int a = max(plo[pp], c0), b = min(phi[pp], c1);
-                    for (int t = a + tid; t < b; t += kThreads) {
-                        const int src = psrc[pp] + (t - plo[pp]);
-                        if constexpr (PREC == 0) {
-                            st[t - c0] = sp64[src];
-                        } else {
-                            const uint4 u = sp32[src];
-                            st[t - c0] = make_float4(fixed_offset(u.x, ox, fsx), fixed_offset(u.y, oy, fsy),
-                                                     fixed_offset(u.z, oz, fsz), __uint_as_float(u.w));
-                        }
+            for (int pp = 0; pp < 3; ++pp) {
+                const int a = max(plo[pp], c0), b = min(phi[pp], c1);
+                for (int t = a + tid; t < b; t += kThreads) {
+                    const int src = psrc[pp] + (t - plo[pp]);
+                    if constexpr (PREC == 0) {
+                        st[t - c0] = sp64[src];
+                    } else {
+                        const uint4 u = sp32[src];
+                        st[t - c0] = make_float4(fixed_offset(u.x, ox, fsx), fixed_offset(u.y, oy, fsy),
+                                                 fixed_offset(u.z, oz, fsz), __uint_as_float(u.w));
                     }
                 }
             }
-            __syncthreads();
-            if (!active) continue;
-            int n = 0;
+        }
+        __syncthreads();
+        for (int rb = hb + 32 * wid; rb < he; rb += kThreads) {
+            const int hi = rb + lane;
+            const bool active = hi < he;
+            int cxr = 0;
+            while (cxr + 1 < nh && s_hstart[cxr + 1] <= (active ? hi : he - 1)) ++cxr;
+            // the warp's lanes cover home cells cx_lo..cx_hi (particles are in
+            // cell order); all lanes walk the union of their stencils, so the
+            // candidate loops have warp-uniform trip counts and every staged
+            // load is a broadcast -- candidates two or more cells away are
+            // farther than h >= r_c and fail the distance test
+            const int cx_lo = __shfl_sync(0xffffffffu, cxr, 0);
+            const int cx_hi = __reduce_max_sync(0xffffffffu, (unsigned)cxr);
+            const int t_self = s_off[4 * w + cxr + 1] + (hi - s_hstart[cxr]);
+            real ix = 0, iy = 0, iz = 0, qi = 0;
+            if (active) {
+                if constexpr (PREC == 0) {
+                    const double4_32a p = sp64[hi];
+                    ix = p.x; iy = p.y; iz = p.z; qi = p.w;
+                } else {
+                    const uint4 u = sp32[hi];
+                    ix = fixed_offset(u.x, ox, fsx);
+                    iy = fixed_offset(u.y, oy, fsy);
+                    iz = fixed_offset(u.z, oz, fsz);
+                    qi = __uint_as_float(u.w);
+                }
+            } else {
+                ix = iy = iz = (real)1e30;   // inactive lanes accept nothing
+            }
+            real fx = 0, fy = 0, fz = 0, un = 0, uw = 0;
+            int cnt = 0, n = 0;
             // pair force and energy for list entries [0, n)
             auto compute = [&]() {
+#pragma unroll 2
                 for (int e = 0; e < n; ++e) {
                     const entry en = list[e * kThreads + tid];
                     const int t = (int)en & 0xFFFFF;
@@ -322,73 +331,67 @@ __global__ void __launch_bounds__(kThreads, 4)
                 n = 0;
             };
             for (int r = 0; r < 9; ++r) {
-                const int k0 = r * w + cxr;
-                const int lo = max(s_off[k0], c0), hi3 = min(s_off[k0 + 3], c1);
-                int b1 = 0, b2 = 0, code0 = 0, code1 = 0, code2 = 0;
-                if constexpr (PREC == 0) {
-                    b1 = s_off[k0 + 1];
-                    b2 = s_off[k0 + 2];
-                    code0 = s_shift[k0];
-                    code1 = s_shift[k0 + 1];
-                    code2 = s_shift[k0 + 2];
-                }
-                // the list always has room for a whole run of candidates, so
-                // the test loop below never branches into the pair arithmetic
+                const int kb = r * w + cx_lo, ke = r * w + cx_hi + 3;   // staged cells [kb, ke)
+                const int lo = max(s_off[kb], c0), hi3 = min(s_off[ke], c1);
                 for (int tb = lo; tb < hi3; tb += kList) {
                     const int te = min(tb + kList, hi3);
-                    if (n + (te - tb) > kList) compute();
-#pragma unroll 4
-                    for (int t = tb; t < te; ++t) {
-                        bool ok;
-                        int code = 0;
-                        if constexpr (PREC == 0) {
-                            code = t < b1 ? code0 : (t < b2 ? code1 : code2);
+                    // the list always has room for a whole run of candidates,
+                    // so the test loop never branches into the pair arithmetic
+                    if (__any_sync(0xffffffffu, n + (te - tb) > kList)) compute();
+                    if constexpr (PREC == 0) {
+                        int kc = kb;
+                        while (s_off[kc + 1] <= tb) ++kc;
+                        for (int t = tb; t < te; ++t) {
+                            while (s_off[kc + 1] <= t) ++kc;
+                            const int code = s_shift[kc];
                             const double4_32a pj = st[t - c0];
                             const double dx = __dsub_rn(__dsub_rn(ix, pj.x), box.L[0] * (double)((code & 3) - 1));
                             const double dy = __dsub_rn(__dsub_rn(iy, pj.y), box.L[1] * (double)(((code >> 2) & 3) - 1));
                             const double dz = __dsub_rn(__dsub_rn(iz, pj.z), box.L[2] * (double)(((code >> 4) & 3) - 1));
                             const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                            ok = r2 < pc.rc2;
-                        } else {
+                            if (r2 < pc.rc2 && t != t_self) {
+                                list[n * kThreads + tid] = (entry)((t - c0) | (code << 20));
+                                ++n;
+                            }
+                        }
+                    } else {
+#pragma unroll 4
+                        for (int t = tb; t < te; ++t) {
                             const float4 pj = st[t - c0];
                             const float dx = ix - pj.x, dy = iy - pj.y, dz = iz - pj.z;
-                            ok = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < pc.rc2;
-                        }
-                        if (ok && t != t_self) {
-                            list[n * kThreads + tid] = (entry)((t - c0) | (code << 20));
-                            ++n;
+                            if (fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < pc.rc2 && t != t_self) {
+                                list[n * kThreads + tid] = (entry)(t - c0);
+                                ++n;
+                            }
                         }
                     }
                 }
             }
             compute();
-        }
-        if (active) {
-            fnear[hi] = make_double4_32a((double)fx, (double)fy, (double)fz, 0.0);
-            if (nbr) nbr[hi] = cnt;
+            if (active) {
+                if (c0 == 0) {
+                    fnear[hi] = make_double4_32a((double)fx, (double)fy, (double)fz, 0.0);
+                    if (nbr) nbr[hi] = cnt;
+                } else {   // later chunks of an oversized region add to the first
+                    double4_32a f = fnear[hi];
+                    f.x += fx;
+                    f.y += fy;
+                    f.z += fz;
+                    fnear[hi] = f;
+                    if (nbr) nbr[hi] += cnt;
+                }
+            }
             e_near += (double)un;
             e_wca += (double)uw;
         }
     }
-    // fixed-order block reduction of the energies
+    // fixed-order warp reduction of the energies, one partial per warp
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         e_near += __shfl_down_sync(0xffffffffu, e_near, o);
         e_wca += __shfl_down_sync(0xffffffffu, e_wca, o);
     }
-    if (lane == 0) {
-        s_red[0][wid] = e_near;
-        s_red[1][wid] = e_wca;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double a = 0.0, b = 0.0;
-        for (int i = 0; i < kThreads / 32; ++i) {
-            a += s_red[0][i];
-            b += s_red[1][i];
-        }
-        epart[blockIdx.x] = make_double2(a, b);
-    }
+    if (lane == 0) epart[(int64_t)blockIdx.x * (kThreads / 32) + wid] = make_double2(e_near, e_wca);
 }
 
 size_t near_smem(int precision, int cap) {
@@ -402,6 +405,8 @@ int near_num_blocks(const BoxDev &box, int group) {
     const int nseg_x = (box.nc[0] + group - 1) / group;
     return nseg_x * box.nc[1] * box.nc[2];
 }
+
+int near_num_partials(const BoxDev &box, int group) { return near_num_blocks(box, group) * (kThreads / 32); }
 
 cudaError_t launch_near(int precision, const BoxDev &box, const NearSog &sog, int group, int cap,
                         const int32_t *start, const double4_32a *sp64, const uint4 *sp32,

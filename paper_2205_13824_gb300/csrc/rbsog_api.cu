@@ -516,12 +516,12 @@ rbsog_status rbsog_set_params(rbsog_ctx *ctx, const rbsog_params *pp) {
     // the staging chunk covers the mean occupancy of the 9 (group + 2) staged
     // cells with 30% head-room (denser regions are processed in chunks)
     const double per_cell = (double)ctx->n / (double)ncell;
-    int g = (int)std::lround(110.0 / std::max(per_cell, 1e-3));
+    int g = (int)std::lround(120.0 / std::max(per_cell, 1e-3));
     g = std::max(1, std::min(g, std::min(16, nc[0] - 2)));
     ctx->group = g;
-    ctx->n_epart = near_num_blocks(b, g);
+    ctx->n_epart = near_num_partials(b, g);
     {
-        const double est = 9.0 * (g + 2) * per_cell * 1.3 + 64.0;
+        const double est = 9.0 * (g + 2) * per_cell * 1.15 + 64.0;
         const int cap_max = p.precision == RBSOG_FP64 ? 2048 : 4096;
         ctx->near_cap = std::min(cap_max, std::max(256, ((int)std::ceil(est) + 127) / 128 * 128));
     }
@@ -545,6 +545,7 @@ rbsog_status rbsog_set_params(rbsog_ctx *ctx, const rbsog_params *pp) {
     CK(dalloc(&ctx->epart, (size_t)ctx->n_epart));
     CK(dalloc(&ctx->cb.count, (size_t)ncell));
     CK(dalloc(&ctx->cb.start, (size_t)ncell + 1));
+    CK(dalloc(&ctx->cb.tile_sum, (size_t)cell_scan_tiles((int)ncell)));
     CK(dalloc(&ctx->m_tmp, (size_t)p.P));
     CK(dalloc(&ctx->m3_tmp, (size_t)p.P * 3));
     ctx->m_tmp_cap = p.P;
@@ -937,6 +938,7 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->cb.slot);
     dfree(&ctx->cb.count);
     dfree(&ctx->cb.start);
+    dfree(&ctx->cb.tile_sum);
     dfree(&ctx->cb.perm_raw);
     dfree(&ctx->cb.perm);
     dfree(&ctx->kpart);

@@ -89,7 +89,9 @@ struct CellBuffers {
     int32_t *start;       // [ncell + 1]
     int32_t *perm_raw;    // [n]   cell order, unordered inside a cell
     int32_t *perm;        // [n]   cell order, increasing index inside a cell
+    int32_t *tile_sum;    // [cell_scan_tiles(ncell)] scan tile totals
 };
+int cell_scan_tiles(int ncell);
 // precision 0: gather FP64 (x, y, z, q) into sp64; 1: 32-bit fixed point
 // positions and FP32 charge into sp32.
 cudaError_t launch_build_cells(int64_t n, const double4_32a *posq, const BoxDev &box,
@@ -100,6 +102,7 @@ cudaError_t launch_build_cells(int64_t n, const double4_32a *posq, const BoxDev 
 // Forces (sorted order) into fnear; per-block energy partials (U_near, U_wca)
 // into epart[nblocks]; neighbour counts (sorted order) into nbr when non-null.
 int near_num_blocks(const BoxDev &box, int group);
+int near_num_partials(const BoxDev &box, int group);   // energy partials written (one per warp)
 // cap: staged particles per shared-memory chunk (larger regions are chunked).
 cudaError_t launch_near(int precision, const BoxDev &box, const NearSog &sog, int group, int cap,
                         const int32_t *start, const double4_32a *sp64, const uint4 *sp32,
