@@ -179,6 +179,34 @@ rbsog_status rbsog_set_profiling(rbsog_ctx *ctx, int on);
 rbsog_status rbsog_get_profile(rbsog_ctx *ctx, int32_t cap, char (*names)[32], int64_t *launches,
                                double *ms, int32_t *count);
 
+/* Allocation-free structure factors.  The paper has no counterpart to this
+ * entry point; it serves callers that cannot allocate device memory where
+ * they need rho(k) -- code inside a region that forbids allocation (for
+ * example work being recorded into a stream capture) or an embedding host
+ * whose allocator must not be re-entered or has a fixed budget.
+ *
+ * Computes rho(k) = sum_j q_j e^{i k . r_j}, k = 2 pi m / L (Eq. 3.4), in
+ * FP64, exactly like rbsog_rho but without a context: q[n], x[n][3] (any
+ * real positions), m[P][3] and rho_out[P][2] (Re, Im) are caller-owned
+ * DEVICE buffers on the current device; L[3] is host memory.  Work is
+ * enqueued on `stream` (cudaStream_t, NULL = legacy default stream); the
+ * call does not synchronise.
+ *
+ * It allocates nothing: its partial sums live in a file-scope device array
+ * of RBSOG_NOALLOC_MAX_P * 64 complex FP64 values (2 MiB) that every GPU
+ * which loads the library holds until the process exits.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress, with
+ * the device current); make that first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (different
+ * streams, or host threads) race and must be ordered by the caller.  Each
+ * call overwrites every partial it reads, so no clearing is needed.
+ *
+ * Returns RBSOG_EINVAL for n < 1, P < 1, P > RBSOG_NOALLOC_MAX_P, a
+ * non-positive box edge or a NULL pointer; RBSOG_ECUDA if a CUDA call fails. */
+#define RBSOG_NOALLOC_MAX_P 2048
+rbsog_status rbsog_rho_noalloc(int64_t n, const double *q, const double *x, const double *L,
+                               const int32_t *m, int32_t P, double *rho_out, void *stream);
+
 /* Description of the last error on this context (never NULL). */
 const char *rbsog_last_error(const rbsog_ctx *ctx);
 

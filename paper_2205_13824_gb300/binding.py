@@ -24,7 +24,7 @@ STATUS = {0: "RBSOG_OK", 1: "RBSOG_EINVAL", 2: "RBSOG_ENOMEM", 3: "RBSOG_ECUDA",
 EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_state",
            "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_get_energies",
            "rbsog_get_kseq", "rbsog_rho", "rbsog_get_cells", "rbsog_set_profiling",
-           "rbsog_get_cursor", "rbsog_restore",
+           "rbsog_get_cursor", "rbsog_restore", "rbsog_rho_noalloc",
            "rbsog_get_profile", "rbsog_last_error", "rbsog_destroy")
 
 
@@ -81,6 +81,7 @@ def _load():
         "rbsog_set_profiling": [P, C.c_int],
         "rbsog_get_profile": [P, C.c_int32, P, P, P, C.POINTER(C.c_int32)],
         "rbsog_destroy": [P],
+        "rbsog_rho_noalloc": [C.c_int64, P, P, C.POINTER(C.c_double), P, C.c_int32, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -208,6 +209,21 @@ def rbsog_get_profile(ctx, cap: int = 64):
     for i in range(min(cnt.value, cap)):
         out[bytes(names[i]).split(b"\0")[0].decode()] = (int(launches[i]), float(ms[i]))
     return out
+
+
+RBSOG_NOALLOC_MAX_P = 2048
+
+
+def rbsog_rho_noalloc(q, x, L, m, rho_out, stream=None):
+    """rho(k) from caller-owned device buffers with no device allocation
+    (see include/rbsog.h); P = m.shape[0] must not exceed RBSOG_NOALLOC_MAX_P."""
+    P = int(m.shape[0])
+    Lc = (C.c_double * 3)(*[float(v) for v in L])
+    s = _lib.rbsog_rho_noalloc(int(x.shape[0]), _ptr(q), _ptr(x), Lc, _ptr(m), P, _ptr(rho_out), stream)
+    if s != 0:
+        why = (f"P={P} exceeds the allocation-free maximum of {RBSOG_NOALLOC_MAX_P}"
+               if P > RBSOG_NOALLOC_MAX_P else "invalid argument or CUDA failure")
+        raise RBSOGError(s, f"rbsog_rho_noalloc: {why}")
 
 
 def rbsog_last_error(ctx) -> str:
