@@ -33,8 +33,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s at N=1M (FP32-comp vs FP64 path, same error); p50/p99 job latency"
 N_DEF, L_DEF, P_DEF = 1048576, 128.0, 500
-SM_COUNT = 152
-MUFU_PER_CLK_SM = 16          # MUFU (sin/cos/ex2/rsqrt) results per clock per SM
 
 
 def parse():
@@ -120,30 +118,65 @@ def electrolyte_state(N, L, seed):
     return I.electrolyte(N, L, seed=seed)
 
 
-def roofline_for(name, launches, ms_total, N, P, sm_mhz, peaks):
-    """Algorithmic work of one launch over its average CUDA-event duration."""
+# ncu summaries (profiles/) holding the DRAM traffic of a kernel at this
+# workload, with the hash of the kernel source they were taken from
+PROFILE_OF = {"near": ("near_fp32c_electrolyte_N1048576.md", "k_near.cu"),
+              "rho_sweep": ("rho_sweep_fp32c_electrolyte_N1048576_P500.md", "k_far.cu"),
+              "far_scatter": ("far_scatter_fp32c_electrolyte_N1048576_P500.md", "k_far.cu")}
+
+
+def profiled_traffic(kernel, N, P):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    summary is for another workload or the kernel source changed since."""
+    import hashlib
+    import re
+    for key, (fname, src) in PROFILE_OF.items():
+        if not kernel.startswith(key):
+            continue
+        if N != N_DEF or (key != "near" and P != P_DEF):
+            return None
+        try:
+            txt = open(os.path.join(ROOT, "profiles", fname)).read()
+            cur = hashlib.sha256(open(os.path.join(ROOT, "paper_2205_13824_gb300", "csrc", src), "rb")
+                                 .read()).hexdigest()[:16]
+        except OSError:
+            return None
+        m = re.search(r"traffic_bytes_per_launch: (\d+)", txt)
+        h = re.search(r"sha256 prefix `([0-9a-f]+)`", txt)
+        if m and h and h.group(1) == cur:
+            return int(m.group(1))
+        return None
+    return None
+
+
+def roofline_for(name, launches, ms_total, N, L, P, rc, meas, hbm_gbs):
+    """Algorithmic work of one launch over its average CUDA-event duration,
+    against the rate measured on this GPU by rbsog_measure_peaks."""
     t = ms_total / launches / 1e3
-    f = (sm_mhz or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    out = {"kernel": name, "ms_per_launch": t * 1e3, "traffic": profiled_traffic(name, N, P)}
     if name.startswith(("rho_sweep", "far_scatter")):
         # one (particle, frequency) term = one sin + one cos on the MUFU pipe
         achieved = N * P / t / 1e9
-        peak = SM_COUNT * MUFU_PER_CLK_SM / 2 * f / 1e9
-        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gsincos/s",
-                "frac": achieved / peak, "traffic": None, "kernel": name,
-                "ms_per_launch": t * 1e3, "peak_basis": f"{MUFU_PER_CLK_SM} MUFU/clk/SM x {SM_COUNT} SMs / 2 at "
-                                                         f"{f / 1e6:.0f} MHz (median SM clock in the timed region)"}
+        peak = meas["mufu_per_s"] / 2 / 1e9
+        out.update(bound="alu", achieved=achieved, peak=peak, unit="Gsincos/s", frac=achieved / peak,
+                   peak_basis="measured MUFU sin+cos rate / 2 (rbsog_measure_peaks)")
+        return out
     if name.startswith("near"):
-        # one accepted pair ~ 6 MUFU (rsqrt + 5 narrow Gaussians); count pairs
-        pairs = N * (4.0 / 3.0) * math.pi * 27.0 * 0.5
-        achieved = pairs * 6 / t / 1e9
-        peak = SM_COUNT * MUFU_PER_CLK_SM * f / 1e9
-        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GMUFU/s",
-                "frac": achieved / peak, "traffic": None, "kernel": name, "ms_per_launch": t * 1e3}
-    bytes_ = N * 64
-    achieved = bytes_ / t / 1e9
-    peak = peaks.get("hbm_gbs", 6686.1)
-    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": name, "ms_per_launch": t * 1e3}
+        # FP32 instruction-equivalents: 8 per candidate distance test over the
+        # 27-cell stencil, 50 per pair inside r_c (MUFU ops counted once)
+        ncell = math.floor(L / rc) ** 3
+        cand = 27.0 * N / ncell
+        pairs = 4.0 / 3.0 * math.pi * rc ** 3 * N / L ** 3
+        ops = N * (8.0 * cand + 50.0 * pairs)
+        achieved = ops / t / 1e12
+        peak = meas["fma32_per_s"] / 1e12
+        out.update(bound="alu", achieved=achieved, peak=peak, unit="Top/s", frac=achieved / peak,
+                   peak_basis="measured FP32 FMA issue rate (rbsog_measure_peaks); work = 8 FP32 ops per "
+                              "candidate test + 50 per pair within r_c")
+        return out
+    achieved = N * 64 / t / 1e9
+    out.update(bound="hbm", achieved=achieved, peak=hbm_gbs, unit="GB/s", frac=achieved / hbm_gbs)
+    return out
 
 
 def load_peaks():
@@ -176,6 +209,7 @@ def run_ours(args, rank, world, local, dist):
             dist.barrier()
         torch.cuda.synchronize()
 
+    meas = B.rbsog_measure_peaks(local)         # roofline denominators on this GPU
     g.step(W)                                   # warm-up (builds the step graph)
     barrier()
     stream = torch.cuda.current_stream()
@@ -236,8 +270,11 @@ def run_ours(args, rank, world, local, dist):
         extras = run_extras(args, q, x, v, dev)
 
     peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6686.1)
     top = max(prof.items(), key=lambda kv: kv[1][1])
-    roof = roofline_for(top[0], top[1][0], top[1][1], N, P, clocks.get("sm_mhz"), peaks)
+    roof = roofline_for(top[0], top[1][0], top[1][1], N, L, P, 3.0, meas, hbm)
+    roof_far = [roofline_for(k, c, t, N, L, P, 3.0, meas, hbm) for k, (c, t) in prof.items()
+                if k.startswith(("rho_sweep", "far_scatter"))]
     kernels = {k: {"launches": c, "ms_per_launch": t / c, "share": t / sum(tt for _, tt in prof.values())}
                for k, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     value = world * N / (ms / 1e3)
@@ -253,6 +290,9 @@ def run_ours(args, rank, world, local, dist):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * K)),
         "roofline": roof,
+        "roofline_far_field": roof_far,
+        "measured_peaks": {"mufu_per_s": meas["mufu_per_s"], "fma32_per_s": meas["fma32_per_s"],
+                           "fma64_per_s": meas["fma64_per_s"], "sm_mhz": meas["sm_mhz"]},
         "clocks": clocks,
         "kernels": kernels,
         "ms_per_step_eager_profiled": ms_prof,

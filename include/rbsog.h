@@ -207,6 +207,13 @@ rbsog_status rbsog_get_profile(rbsog_ctx *ctx, int32_t cap, char (*names)[32], i
 rbsog_status rbsog_rho_noalloc(int64_t n, const double *q, const double *x, const double *L,
                                const int32_t *m, int32_t P, double *rho_out, void *stream);
 
+/* Roofline denominators measured on `device` by short microbenchmarks (not
+ * part of the method): out[0] MUFU sin/cos results per second (each of sin
+ * and cos counts one), out[1] FP32 FMA per second, out[2] FP64 FMA per
+ * second, out[3] SM clock in MHz while they ran, out[4] SM count.  Allocates
+ * 128 bytes of device memory; synchronises. */
+rbsog_status rbsog_measure_peaks(int device, double *out);
+
 /* Description of the last error on this context (never NULL). */
 const char *rbsog_last_error(const rbsog_ctx *ctx);
 

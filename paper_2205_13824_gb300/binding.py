@@ -24,7 +24,7 @@ STATUS = {0: "RBSOG_OK", 1: "RBSOG_EINVAL", 2: "RBSOG_ENOMEM", 3: "RBSOG_ECUDA",
 EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_state",
            "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_get_energies",
            "rbsog_get_kseq", "rbsog_rho", "rbsog_get_cells", "rbsog_set_profiling",
-           "rbsog_get_cursor", "rbsog_restore", "rbsog_rho_noalloc",
+           "rbsog_get_cursor", "rbsog_restore", "rbsog_rho_noalloc", "rbsog_measure_peaks",
            "rbsog_get_profile", "rbsog_last_error", "rbsog_destroy")
 
 
@@ -82,6 +82,7 @@ def _load():
         "rbsog_get_profile": [P, C.c_int32, P, P, P, C.POINTER(C.c_int32)],
         "rbsog_destroy": [P],
         "rbsog_rho_noalloc": [C.c_int64, P, P, C.POINTER(C.c_double), P, C.c_int32, P, P],
+        "rbsog_measure_peaks": [C.c_int, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -224,6 +225,15 @@ def rbsog_rho_noalloc(q, x, L, m, rho_out, stream=None):
         why = (f"P={P} exceeds the allocation-free maximum of {RBSOG_NOALLOC_MAX_P}"
                if P > RBSOG_NOALLOC_MAX_P else "invalid argument or CUDA failure")
         raise RBSOGError(s, f"rbsog_rho_noalloc: {why}")
+
+
+def rbsog_measure_peaks(device: int = 0):
+    out = np.zeros(5)
+    s = _lib.rbsog_measure_peaks(int(device), _ptr(out))
+    if s != 0:
+        raise RBSOGError(s, "rbsog_measure_peaks failed")
+    return {"mufu_per_s": out[0], "fma32_per_s": out[1], "fma64_per_s": out[2], "sm_mhz": out[3],
+            "sm_count": int(out[4])}
 
 
 def rbsog_last_error(ctx) -> str:
