@@ -214,6 +214,39 @@ rbsog_status rbsog_rho_noalloc(int64_t n, const double *q, const double *x, cons
  * 128 bytes of device memory; synchronises. */
 rbsog_status rbsog_measure_peaks(int device, double *out);
 
+/* ---- Batched replicas -----------------------------------------------------
+ * A batch holds n_sys independent systems of uneven size that advance
+ * together: one rbsog_batch_step launches one CUDA graph per step whose
+ * kernels cover every system (work tables map blocks to systems), so small
+ * systems do not each pay for their own launches.  Every system's work is
+ * decomposed exactly as it would be alone, so a system's trajectory is
+ * bit-identical alone and in any batch.  Systems of one batch share b,
+ * sigma, omega0, M, r_c, P and precision; box, charges, Coulomb prefactor,
+ * WCA, dt, mass, thermostat, seed and sequence length are per system.  The
+ * rbsog_ctx functions above operate on system 0 of a batch; a context made
+ * by rbsog_create is a batch of one.  Destroy a batch with rbsog_destroy. */
+typedef struct rbsog_ctx rbsog_batch;
+/* n_per[n_sys] particles per system (each >= 2). */
+rbsog_status rbsog_batch_create(rbsog_batch **out, int32_t n_sys, const int64_t *n_per, int device,
+                                void *stream);
+/* p[n_sys]; the same validation as rbsog_set_params for each system. */
+rbsog_status rbsog_batch_set_params(rbsog_batch *b, const rbsog_params *p);
+/* As rbsog_set_state / rbsog_restore / rbsog_get_state / rbsog_get_energies /
+ * rbsog_get_kseq for system `sys` of the batch.  A system loaded with
+ * set_state receives its initial force evaluation at the next step; the
+ * other systems keep their forces and cursors. */
+rbsog_status rbsog_batch_set_state(rbsog_batch *b, int32_t sys, const double *q, const double *x,
+                                   const double *v);
+rbsog_status rbsog_batch_restore(rbsog_batch *b, int32_t sys, const double *f, int64_t kset_cursor,
+                                 int64_t step);
+rbsog_status rbsog_batch_get_state(rbsog_batch *b, int32_t sys, double *x, double *v, double *f,
+                                   int64_t *step);
+rbsog_status rbsog_batch_get_energies(rbsog_batch *b, int32_t sys, rbsog_energies *e);
+rbsog_status rbsog_batch_get_kseq(rbsog_batch *b, int32_t sys, int64_t set0, int64_t nsets,
+                                  int32_t *m_out);
+/* Advance every system of the batch by nsteps velocity-Verlet steps. */
+rbsog_status rbsog_batch_step(rbsog_batch *b, int64_t nsteps);
+
 /* Description of the last error on this context (never NULL). */
 const char *rbsog_last_error(const rbsog_ctx *ctx);
 

@@ -25,6 +25,8 @@ EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_stat
            "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_get_energies",
            "rbsog_get_kseq", "rbsog_rho", "rbsog_get_cells", "rbsog_set_profiling",
            "rbsog_get_cursor", "rbsog_restore", "rbsog_rho_noalloc", "rbsog_measure_peaks",
+           "rbsog_batch_create", "rbsog_batch_set_params", "rbsog_batch_set_state", "rbsog_batch_restore",
+           "rbsog_batch_get_state", "rbsog_batch_get_energies", "rbsog_batch_get_kseq", "rbsog_batch_step",
            "rbsog_get_profile", "rbsog_last_error", "rbsog_destroy")
 
 
@@ -83,6 +85,14 @@ def _load():
         "rbsog_destroy": [P],
         "rbsog_rho_noalloc": [C.c_int64, P, P, C.POINTER(C.c_double), P, C.c_int32, P, P],
         "rbsog_measure_peaks": [C.c_int, P],
+        "rbsog_batch_create": [C.POINTER(P), C.c_int32, P, C.c_int, P],
+        "rbsog_batch_set_params": [P, P],
+        "rbsog_batch_set_state": [P, C.c_int32, P, P, P],
+        "rbsog_batch_restore": [P, C.c_int32, P, C.c_int64, C.c_int64],
+        "rbsog_batch_get_state": [P, C.c_int32, P, P, P, C.POINTER(C.c_int64)],
+        "rbsog_batch_get_energies": [P, C.c_int32, C.POINTER(rbsog_energies)],
+        "rbsog_batch_get_kseq": [P, C.c_int32, C.c_int64, C.c_int64, P],
+        "rbsog_batch_step": [P, C.c_int64],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -234,6 +244,48 @@ def rbsog_measure_peaks(device: int = 0):
         raise RBSOGError(s, "rbsog_measure_peaks failed")
     return {"mufu_per_s": out[0], "fma32_per_s": out[1], "fma64_per_s": out[2], "sm_mhz": out[3],
             "sm_count": int(out[4])}
+
+
+def rbsog_batch_create(n_per, device: int = 0, stream: int | None = None):
+    arr = np.ascontiguousarray(n_per, dtype=np.int64)
+    ctx = C.c_void_p()
+    s = _lib.rbsog_batch_create(C.byref(ctx), int(arr.shape[0]), _ptr(arr), int(device), stream)
+    if s != 0:
+        raise RBSOGError(s, "rbsog_batch_create failed")
+    return ctx
+
+
+def rbsog_batch_set_params(ctx, params):
+    arr = (rbsog_params * len(params))(*params)
+    _check(ctx, _lib.rbsog_batch_set_params(ctx, C.cast(arr, C.c_void_p)))
+
+
+def rbsog_batch_set_state(ctx, sys: int, q, x, v=None):
+    _check(ctx, _lib.rbsog_batch_set_state(ctx, int(sys), _ptr(q), _ptr(x), _ptr(v)))
+
+
+def rbsog_batch_restore(ctx, sys: int, f, kset_cursor: int, step: int):
+    _check(ctx, _lib.rbsog_batch_restore(ctx, int(sys), _ptr(f), int(kset_cursor), int(step)))
+
+
+def rbsog_batch_get_state(ctx, sys: int, x=None, v=None, f=None):
+    step = C.c_int64()
+    _check(ctx, _lib.rbsog_batch_get_state(ctx, int(sys), _ptr(x), _ptr(v), _ptr(f), C.byref(step)))
+    return step.value
+
+
+def rbsog_batch_get_energies(ctx, sys: int):
+    e = rbsog_energies()
+    _check(ctx, _lib.rbsog_batch_get_energies(ctx, int(sys), C.byref(e)))
+    return e.as_dict()
+
+
+def rbsog_batch_get_kseq(ctx, sys: int, set0: int, nsets: int, m_out):
+    _check(ctx, _lib.rbsog_batch_get_kseq(ctx, int(sys), int(set0), int(nsets), _ptr(m_out)))
+
+
+def rbsog_batch_step(ctx, nsteps: int):
+    _check(ctx, _lib.rbsog_batch_step(ctx, int(nsteps)))
 
 
 def rbsog_last_error(ctx) -> str:

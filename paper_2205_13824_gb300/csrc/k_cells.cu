@@ -18,22 +18,25 @@
 namespace rbsog {
 namespace {
 
-__global__ void __launch_bounds__(256) k_bin(int64_t n, const double4_32a *__restrict__ posq, BoxDev box,
-                                             int32_t *__restrict__ cell_of, int32_t *__restrict__ slot,
-                                             int32_t *__restrict__ count) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__global__ void __launch_bounds__(kParticleBlock) k_bin(BatchView bv, const double4_32a *__restrict__ posq,
+                                                        int32_t *__restrict__ cell_of, int32_t *__restrict__ slot,
+                                                        int32_t *__restrict__ count) {
+    const int2 w = bv.pblk[blockIdx.x];
+    const SysDesc &d = bv.sys[w.x];
+    const int64_t il = (int64_t)w.y * kParticleBlock + threadIdx.x;
+    if (il >= d.n) return;
+    const int64_t i = d.p_off + il;
     const double4_32a p = posq[i];
     const double xs[3] = {p.x, p.y, p.z};
     int c3[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        int c = (int)floor(xs[d] / box.h[d]);
-        c = c >= box.nc[d] ? box.nc[d] - 1 : c;
+    for (int k = 0; k < 3; ++k) {
+        int c = (int)floor(xs[k] / d.box.h[k]);
+        c = c >= d.box.nc[k] ? d.box.nc[k] - 1 : c;
         c = c < 0 ? 0 : c;
-        c3[d] = c;
+        c3[k] = c;
     }
-    const int cell = (c3[2] * box.nc[1] + c3[1]) * box.nc[0] + c3[0];
+    const int cell = (int)d.c_off + (c3[2] * d.box.nc[1] + c3[1]) * d.box.nc[0] + c3[0];
     cell_of[i] = cell;
     slot[i] = atomicAdd(&count[cell], 1);
 }
@@ -123,15 +126,15 @@ __device__ __forceinline__ uint32_t to_fixed32(double x, double L) {
 
 // One warp per cell: rank = number of members with a smaller particle index
 // (the members' indices are exchanged by shuffles for cells of up to 32).
-__global__ void __launch_bounds__(256) k_order_gather(int ncell, const int32_t *__restrict__ start,
+__global__ void __launch_bounds__(256) k_order_gather(BatchView bv, const int32_t *__restrict__ start,
                                                       const int32_t *__restrict__ perm_raw,
                                                       int32_t *__restrict__ perm,
-                                                      const double4_32a *__restrict__ posq, BoxDev box,
-                                                      int precision, double4_32a *__restrict__ sp64,
-                                                      uint4 *__restrict__ sp32) {
+                                                      const double4_32a *__restrict__ posq, int precision,
+                                                      double4_32a *__restrict__ sp64, uint4 *__restrict__ sp32) {
     const int lane = threadIdx.x & 31;
-    const int cell = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (cell >= ncell) return;
+    const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (cell >= bv.ncell_total) return;
+    const BoxDev &box = bv.sys[bv.cell_sys[cell]].box;
     const int b = start[cell], e = start[cell + 1], cnt = e - b;
     for (int t0 = 0; t0 < cnt; t0 += 32) {
         const int t = t0 + lane;
@@ -162,33 +165,32 @@ __global__ void __launch_bounds__(256) k_order_gather(int ncell, const int32_t *
 
 }  // namespace
 
-int cell_scan_tiles(int ncell) { return (ncell + kScanTile - 1) / kScanTile; }
+int cell_scan_tiles(int64_t ncell) { return (int)((ncell + kScanTile - 1) / kScanTile); }
 
-cudaError_t launch_build_cells(int64_t n, const double4_32a *posq, const BoxDev &box,
-                               const CellBuffers &cb, int precision, double4_32a *sp64, uint4 *sp32,
-                               int32_t *err_flag, cudaStream_t st, const Prof *prof) {
-    (void)err_flag;
+cudaError_t launch_build_cells(const BatchView &bv, const double4_32a *posq, const CellBuffers &cb,
+                               int precision, double4_32a *sp64, uint4 *sp32, cudaStream_t st,
+                               const Prof *prof) {
     const int t = 256;
-    const unsigned nb = (unsigned)((n + t - 1) / t);
+    const int ncell = (int)bv.ncell_total;
     {
         ProfScope ps(prof, "cell_bin");
-        k_bin<<<nb, t, 0, st>>>(n, posq, box, cb.cell_of, cb.slot, cb.count);
+        k_bin<<<bv.n_pblk, kParticleBlock, 0, st>>>(bv, posq, cb.cell_of, cb.slot, cb.count);
     }
     {
         ProfScope ps(prof, "cell_scan");
-        const int ntiles = (box.ncell + kScanTile - 1) / kScanTile;
-        k_scan_tile<<<ntiles, kScanThreads, 0, st>>>(box.ncell, cb.count, cb.start, cb.tile_sum);
-        k_scan_add<<<ntiles, kScanThreads, 0, st>>>(box.ncell, ntiles, cb.count, cb.start, cb.tile_sum);
+        const int ntiles = cell_scan_tiles(ncell);
+        k_scan_tile<<<ntiles, kScanThreads, 0, st>>>(ncell, cb.count, cb.start, cb.tile_sum);
+        k_scan_add<<<ntiles, kScanThreads, 0, st>>>(ncell, ntiles, cb.count, cb.start, cb.tile_sum);
     }
     {
         ProfScope ps(prof, "cell_scatter");
-        k_scatter<<<nb, t, 0, st>>>(n, cb.cell_of, cb.slot, cb.start, cb.perm_raw);
+        const unsigned nb = (unsigned)((bv.n_total + t - 1) / t);
+        k_scatter<<<nb, t, 0, st>>>(bv.n_total, cb.cell_of, cb.slot, cb.start, cb.perm_raw);
     }
     {
         ProfScope ps(prof, "cell_order_gather");
-        const unsigned blocks = (unsigned)(((int64_t)box.ncell * 32 + t - 1) / t);
-        k_order_gather<<<blocks, t, 0, st>>>(box.ncell, cb.start, cb.perm_raw, cb.perm, posq, box,
-                                             precision, sp64, sp32);
+        const unsigned blocks = (unsigned)((bv.ncell_total * 32 + t - 1) / t);
+        k_order_gather<<<blocks, t, 0, st>>>(bv, cb.start, cb.perm_raw, cb.perm, posq, precision, sp64, sp32);
     }
     return cudaGetLastError();
 }

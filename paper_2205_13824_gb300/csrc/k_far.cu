@@ -30,7 +30,7 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kSweepThreads = 256;          // 8 warps
 constexpr int kKTile = 32;                  // frequencies per sweep block
-constexpr int kScatterThreads = 256;
+constexpr int kScatterThreads = kParticleBlock;
 constexpr int kKChunk32 = 1024;             // frequencies per staged chunk (FP32C, 32 KiB)
 constexpr int kKChunk64 = 512;              // frequencies per staged chunk (FP64, 32 KiB)
 
@@ -45,10 +45,10 @@ struct KEntry64 {       // 64 bytes
     double cim, mx, my, mz;
 };
 
-__device__ __forceinline__ int4 load_m(const FarArgs &a, int k) {
-    if (a.m_explicit) return a.m_explicit[k];
-    const int64_t set = a.cursor ? *a.cursor : 0;
-    return a.kseq[set * (int64_t)a.P + k];
+// Frequency k of system s's current k-set (explicit set for a batch of one).
+__device__ __forceinline__ int4 load_m(const BatchView &bv, const SysDesc &d, int s, int k) {
+    if (bv.m_explicit) return bv.m_explicit[k];
+    return bv.kseq[d.k_off + bv.cursor[s] * (int64_t)bv.P + k];
 }
 
 // angle in [0, 2 pi) of a phase given in units of 2^-32 turns, rounded to
@@ -69,19 +69,21 @@ __device__ __forceinline__ void two_sum(float &hi, float &lo, float x) {
 
 template <int PREC>
 __global__ void __launch_bounds__(kSweepThreads)
-    k_rho_sweep(FarArgs a, const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
+    k_rho_sweep(BatchView bv, const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
                 double2 *__restrict__ rho_part) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ double s_re[kSweepThreads / 32][kKTile];
     __shared__ double s_im[kSweepThreads / 32][kKTile];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int ptile = blockIdx.x;
+    const int2 work = bv.sblk[blockIdx.x];
+    const SysDesc &d = bv.sys[work.x];
+    const int ptile = work.y;
     const int k = blockIdx.y * kKTile + lane;
-    const int64_t p0 = (int64_t)ptile * a.tile_p;
-    const int np = (int)min((int64_t)a.tile_p, a.n - p0);
+    const int64_t p0 = d.p_off + (int64_t)ptile * d.tile_p;
+    const int np = (int)min((int64_t)d.tile_p, d.p_off + d.n - p0);
 
     int4 m = make_int4(0, 0, 0, 0);
-    if (k < a.P) m = load_m(a, k);
+    if (k < bv.P) m = load_m(bv, d, work.x, k);
 
     const int per_warp = (np + 7) / 8;
     const int jb = wid * per_warp, je = min(jb + per_warp, np);
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(kSweepThreads)
         s_im[wid][lane] = (double)im_hi + (double)im_lo;
     } else {
         double4_32a *sp = reinterpret_cast<double4_32a *>(smem_raw);
-        const double ilx = 1.0 / a.L[0], ily = 1.0 / a.L[1], ilz = 1.0 / a.L[2];
+        const double ilx = 1.0 / d.box.L[0], ily = 1.0 / d.box.L[1], ilz = 1.0 / d.box.L[2];
         for (int j = tid; j < np; j += kSweepThreads) {
             const double4_32a p = sp64[p0 + j];
             sp[j] = make_double4_32a(p.x * ilx, p.y * ily, p.z * ilz, p.w);
@@ -132,26 +134,28 @@ __global__ void __launch_bounds__(kSweepThreads)
         s_im[wid][lane] = im;
     }
     __syncthreads();
-    if (wid == 0 && k < a.P) {
+    if (wid == 0 && k < bv.P) {
         double re = 0.0, im = 0.0;
 #pragma unroll
         for (int w = 0; w < kSweepThreads / 32; ++w) {
             re += s_re[w][lane];
             im += s_im[w][lane];
         }
-        rho_part[(int64_t)k * a.n_ptiles + ptile] = make_double2(re, im);
+        rho_part[d.rp_off + (int64_t)k * d.n_ptiles + ptile] = make_double2(re, im);
     }
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(256) k_rho_combine(FarArgs a, const double2 *__restrict__ rho_part,
+__global__ void __launch_bounds__(256) k_rho_combine(BatchView bv, const double2 *__restrict__ rho_part,
                                                      double2 *__restrict__ rho, void *__restrict__ ktab) {
     const int lane = threadIdx.x & 31;
-    const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (k >= a.P) return;
-    const double2 *row = rho_part + (int64_t)k * a.n_ptiles;
+    const int64_t gk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // system * P + k
+    if (gk >= (int64_t)bv.n_sys * bv.P) return;
+    const int sy = (int)(gk / bv.P), k = (int)(gk % bv.P);
+    const SysDesc &d = bv.sys[sy];
+    const double2 *row = rho_part + d.rp_off + (int64_t)k * d.n_ptiles;
     double re = 0.0, im = 0.0;
-    for (int t = lane; t < a.n_ptiles; t += 32) {
+    for (int t = lane; t < d.n_ptiles; t += 32) {
         const double2 v = row[t];
         re += v.x;
         im += v.y;
@@ -162,55 +166,60 @@ __global__ void __launch_bounds__(256) k_rho_combine(FarArgs a, const double2 *_
         im += __shfl_down_sync(0xffffffffu, im, o);
     }
     if (lane == 0) {
-        rho[k] = make_double2(re, im);
-        const int4 m = load_m(a, k);
-        const double kx = 2.0 * kPi * m.x / a.L[0], ky = 2.0 * kPi * m.y / a.L[1],
-                     kz = 2.0 * kPi * m.z / a.L[2];
+        rho[gk] = make_double2(re, im);
+        const int4 m = load_m(bv, d, sy, k);
+        const double kx = 2.0 * kPi * m.x / d.box.L[0], ky = 2.0 * kPi * m.y / d.box.L[1],
+                     kz = 2.0 * kPi * m.z / d.box.L[2];
+        const double coef = d.coef;
         if (PREC == 1) {
             KEntry32 e;
             e.mx = m.x;
             e.my = m.y;
             e.mz = m.z;
-            e.cre = (float)(a.coef * re);
+            e.cre = (float)(coef * re);
             e.kx = (float)kx;
             e.ky = (float)ky;
             e.kz = (float)kz;
-            e.cim = (float)(a.coef * im);
-            reinterpret_cast<KEntry32 *>(ktab)[k] = e;
+            e.cim = (float)(coef * im);
+            reinterpret_cast<KEntry32 *>(ktab)[gk] = e;
         } else {
             KEntry64 e;
             e.kx = kx;
             e.ky = ky;
             e.kz = kz;
-            e.cre = a.coef * re;
-            e.cim = a.coef * im;
+            e.cre = coef * re;
+            e.cim = coef * im;
             e.mx = m.x;
             e.my = m.y;
             e.mz = m.z;
-            reinterpret_cast<KEntry64 *>(ktab)[k] = e;
+            reinterpret_cast<KEntry64 *>(ktab)[gk] = e;
         }
     }
 }
 
 template <int PREC>
 __global__ void __launch_bounds__(kScatterThreads)
-    k_far_scatter(FarArgs a, const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
-                  const void *__restrict__ ktab, const double4_32a *__restrict__ fnear,
+    k_far_scatter(BatchView bv, const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
+                  const void *__restrict__ ktab_all, const double4_32a *__restrict__ fnear,
                   const int32_t *__restrict__ perm, double4_32a *__restrict__ force,
                   int32_t *__restrict__ err_flag) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int tid = threadIdx.x;
-    const int64_t s = (int64_t)blockIdx.x * kScatterThreads + tid;
-    const bool active = s < a.n;
+    const int2 work = bv.pblk[blockIdx.x];
+    const SysDesc &d = bv.sys[work.x];
+    const int64_t sl = (int64_t)work.y * kScatterThreads + tid;
+    const int64_t s = d.p_off + sl;
+    const bool active = sl < d.n;
+    const int P = bv.P;
     double fx, fy, fz;
     if (PREC == 1) {
         float4 *sk = reinterpret_cast<float4 *>(smem_raw);
-        const float4 *kt = reinterpret_cast<const float4 *>(ktab);
+        const float4 *kt = reinterpret_cast<const float4 *>(ktab_all) + 2 * (int64_t)work.x * P;
         uint4 p = make_uint4(0, 0, 0, 0);
         if (active) p = sp32[s];
         float gx = 0.f, gy = 0.f, gz = 0.f;
-        for (int c0 = 0; c0 < a.P; c0 += kKChunk32) {
-            const int nk = min(kKChunk32, a.P - c0);
+        for (int c0 = 0; c0 < P; c0 += kKChunk32) {
+            const int nk = min(kKChunk32, P - c0);
             __syncthreads();
             for (int t = tid; t < 2 * nk; t += kScatterThreads) sk[t] = kt[2 * c0 + t];
             __syncthreads();
@@ -234,13 +243,13 @@ __global__ void __launch_bounds__(kScatterThreads)
         fz = (double)(q * gz);
     } else {
         double4_32a *sk = reinterpret_cast<double4_32a *>(smem_raw);
-        const double4_32a *kt = reinterpret_cast<const double4_32a *>(ktab);
+        const double4_32a *kt = reinterpret_cast<const double4_32a *>(ktab_all) + 2 * (int64_t)work.x * P;
         double4_32a p = make_double4_32a(0, 0, 0, 0);
         if (active) p = sp64[s];
-        const double ux = p.x / a.L[0], uy = p.y / a.L[1], uz = p.z / a.L[2];
+        const double ux = p.x / d.box.L[0], uy = p.y / d.box.L[1], uz = p.z / d.box.L[2];
         double gx = 0.0, gy = 0.0, gz = 0.0;
-        for (int c0 = 0; c0 < a.P; c0 += kKChunk64) {
-            const int nk = min(kKChunk64, a.P - c0);
+        for (int c0 = 0; c0 < P; c0 += kKChunk64) {
+            const int nk = min(kKChunk64, P - c0);
             __syncthreads();
             for (int t = tid; t < 2 * nk; t += kScatterThreads) sk[t] = kt[2 * c0 + t];
             __syncthreads();
@@ -261,6 +270,7 @@ __global__ void __launch_bounds__(kScatterThreads)
         fz = p.w * gz;
     }
     if (!active) return;
+    if (bv.force_mask && !bv.force_mask[work.x]) return;
     const double4_32a fn = fnear[s];
     const double tx = fx + fn.x, ty = fy + fn.y, tz = fz + fn.z;
     if (!(isfinite(tx) && isfinite(ty) && isfinite(tz))) atomicOr(err_flag, 1);
@@ -269,61 +279,58 @@ __global__ void __launch_bounds__(kScatterThreads)
 
 }  // namespace
 
-int far_num_ptiles(int64_t n, int tile_p) { return (int)((n + tile_p - 1) / tile_p); }
-
-size_t ktab_bytes(int precision, int32_t P) {
-    return (size_t)P * (precision == 1 ? sizeof(KEntry32) : sizeof(KEntry64));
+void far_layout(int64_t n, int32_t P, int &tile_p, int &n_ptiles) {
+    // at least ~3 waves of sweep blocks (152 SMs x 8 resident blocks)
+    const int nkt = (P + kKTile - 1) / kKTile;
+    int tp = 2048;
+    while (tp > 128 && (double)((n + tp - 1) / tp) * nkt < 152.0 * 8 * 3) tp /= 2;
+    tile_p = tp;
+    n_ptiles = (int)((n + tp - 1) / tp);
 }
 
-cudaError_t launch_rho_sweep(int precision, const FarArgs &a, const double4_32a *sp64,
-                             const uint4 *sp32, double2 *rho_part, cudaStream_t st,
-                             const Prof *prof) {
-    static bool attr_done[2] = {false, false};
-    dim3 grid((unsigned)a.n_ptiles, (unsigned)((a.P + kKTile - 1) / kKTile));
+size_t ktab_bytes(int precision, int64_t nk) {
+    return (size_t)nk * (precision == 1 ? sizeof(KEntry32) : sizeof(KEntry64));
+}
+
+cudaError_t launch_rho_sweep(int precision, const BatchView &bv, const double4_32a *sp64, const uint4 *sp32,
+                             double2 *rho_part, cudaStream_t st, const Prof *prof) {
+    dim3 grid((unsigned)bv.n_sblk, (unsigned)((bv.P + kKTile - 1) / kKTile));
     ProfScope ps(prof, precision == 1 ? "rho_sweep_fp32c" : "rho_sweep_fp64");
     if (precision == 1) {
-        const size_t sm = sizeof(uint4) * (size_t)a.tile_p;
-        if (!attr_done[1]) {
-            cudaFuncSetAttribute(k_rho_sweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-            attr_done[1] = true;
-        }
-        k_rho_sweep<1><<<grid, kSweepThreads, sm, st>>>(a, sp64, sp32, rho_part);
+        const size_t sm = sizeof(uint4) * (size_t)bv.max_tile_p;
+        cudaFuncSetAttribute(k_rho_sweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_rho_sweep<1><<<grid, kSweepThreads, sm, st>>>(bv, sp64, sp32, rho_part);
     } else {
-        const size_t sm = sizeof(double4_32a) * (size_t)a.tile_p;
-        if (!attr_done[0]) {
-            cudaFuncSetAttribute(k_rho_sweep<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-            attr_done[0] = true;
-        }
-        k_rho_sweep<0><<<grid, kSweepThreads, sm, st>>>(a, sp64, sp32, rho_part);
+        const size_t sm = sizeof(double4_32a) * (size_t)bv.max_tile_p;
+        cudaFuncSetAttribute(k_rho_sweep<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_rho_sweep<0><<<grid, kSweepThreads, sm, st>>>(bv, sp64, sp32, rho_part);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_rho_combine(int precision, const FarArgs &a, const double2 *rho_part,
-                               double2 *rho, void *ktab, cudaStream_t st, const Prof *prof) {
+cudaError_t launch_rho_combine(int precision, const BatchView &bv, const double2 *rho_part, double2 *rho,
+                               void *ktab, cudaStream_t st, const Prof *prof) {
     ProfScope ps(prof, "rho_combine");
-    const unsigned blocks = (unsigned)(((int64_t)a.P * 32 + 255) / 256);
+    const unsigned blocks = (unsigned)(((int64_t)bv.n_sys * bv.P * 32 + 255) / 256);
     if (precision == 1)
-        k_rho_combine<1><<<blocks, 256, 0, st>>>(a, rho_part, rho, ktab);
+        k_rho_combine<1><<<blocks, 256, 0, st>>>(bv, rho_part, rho, ktab);
     else
-        k_rho_combine<0><<<blocks, 256, 0, st>>>(a, rho_part, rho, ktab);
+        k_rho_combine<0><<<blocks, 256, 0, st>>>(bv, rho_part, rho, ktab);
     return cudaGetLastError();
 }
 
-cudaError_t launch_far_scatter(int precision, const FarArgs &a, const double4_32a *sp64,
-                               const uint4 *sp32, const void *ktab, const double4_32a *fnear,
-                               const int32_t *perm, double4_32a *force, int32_t *err_flag,
-                               cudaStream_t st, const Prof *prof) {
-    const unsigned blocks = (unsigned)((a.n + kScatterThreads - 1) / kScatterThreads);
+cudaError_t launch_far_scatter(int precision, const BatchView &bv, const double4_32a *sp64, const uint4 *sp32,
+                               const void *ktab, const double4_32a *fnear, const int32_t *perm,
+                               double4_32a *force, int32_t *err_flag, cudaStream_t st, const Prof *prof) {
     ProfScope ps(prof, precision == 1 ? "far_scatter_fp32c" : "far_scatter_fp64");
     if (precision == 1) {
         const size_t sm = sizeof(KEntry32) * kKChunk32;
-        k_far_scatter<1><<<blocks, kScatterThreads, sm, st>>>(a, sp64, sp32, ktab, fnear, perm, force,
-                                                              err_flag);
+        k_far_scatter<1><<<bv.n_pblk, kScatterThreads, sm, st>>>(bv, sp64, sp32, ktab, fnear, perm, force,
+                                                                  err_flag);
     } else {
         const size_t sm = sizeof(KEntry64) * kKChunk64;
-        k_far_scatter<0><<<blocks, kScatterThreads, sm, st>>>(a, sp64, sp32, ktab, fnear, perm, force,
-                                                              err_flag);
+        k_far_scatter<0><<<bv.n_pblk, kScatterThreads, sm, st>>>(bv, sp64, sp32, ktab, fnear, perm, force,
+                                                                  err_flag);
     }
     return cudaGetLastError();
 }

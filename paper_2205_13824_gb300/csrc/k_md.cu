@@ -8,7 +8,7 @@
 namespace rbsog {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = kParticleBlock;
 
 __device__ __forceinline__ double fold(double x, double L) {
     double v = x - L * floor(x / L);
@@ -16,11 +16,14 @@ __device__ __forceinline__ double fold(double x, double L) {
 }
 
 // v += dt/2 F/m ; x += dt v ; x folded into [0, L).
-__global__ void __launch_bounds__(kThreads) k_kick_drift(MdArgs a, double4_32a *__restrict__ posq,
+__global__ void __launch_bounds__(kThreads) k_kick_drift(BatchView bv, double4_32a *__restrict__ posq,
                                                          double4_32a *__restrict__ vel,
                                                          const double4_32a *__restrict__ force) {
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= a.n) return;
+    const int2 w = bv.pblk[blockIdx.x];
+    const SysDesc &a = bv.sys[w.x];
+    const int64_t il = (int64_t)w.y * kThreads + threadIdx.x;
+    if (il >= a.n) return;
+    const int64_t i = a.p_off + il;
     const double4_32a f = force[i];
     double4_32a v = vel[i];
     double4_32a p = posq[i];
@@ -32,21 +35,24 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift(MdArgs a, double4_32a *
     p.x += a.dt * v.x;
     p.y += a.dt * v.y;
     p.z += a.dt * v.z;
-    if (p.x < 0.0 || p.x >= a.L[0]) p.x = fold(p.x, a.L[0]);
-    if (p.y < 0.0 || p.y >= a.L[1]) p.y = fold(p.y, a.L[1]);
-    if (p.z < 0.0 || p.z >= a.L[2]) p.z = fold(p.z, a.L[2]);
+    if (p.x < 0.0 || p.x >= a.box.L[0]) p.x = fold(p.x, a.box.L[0]);
+    if (p.y < 0.0 || p.y >= a.box.L[1]) p.y = fold(p.y, a.box.L[1]);
+    if (p.z < 0.0 || p.z >= a.box.L[2]) p.z = fold(p.z, a.box.L[2]);
     vel[i] = v;
     posq[i] = p;
 }
 
 // v += dt/2 F/m and the block's kinetic energy sum (fixed order).
-__global__ void __launch_bounds__(kThreads) k_kick(MdArgs a, double4_32a *__restrict__ vel,
+__global__ void __launch_bounds__(kThreads) k_kick(BatchView bv, double4_32a *__restrict__ vel,
                                                    const double4_32a *__restrict__ force,
                                                    double *__restrict__ kpart) {
     __shared__ double s_red[kThreads / 32];
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int2 w = bv.pblk[blockIdx.x];
+    const SysDesc &a = bv.sys[w.x];
+    const int64_t il = (int64_t)w.y * kThreads + threadIdx.x;
+    const int64_t i = a.p_off + il;
     double ke = 0.0;
-    if (i < a.n) {
+    if (il < a.n) {
         const double4_32a f = force[i];
         double4_32a v = vel[i];
         const double h = 0.5 * a.dt * a.inv_mass;
@@ -63,31 +69,33 @@ __global__ void __launch_bounds__(kThreads) k_kick(MdArgs a, double4_32a *__rest
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) t += s_red[w];
-        kpart[blockIdx.x] = t;
+        kpart[a.kp_off + w.y] = t;
     }
 }
 
-// Single block: fixed-order sums of the near-energy partials, |rho|^2 and
-// the kinetic partials; Berendsen factor; k-set cursor and step counter.
-__global__ void __launch_bounds__(1024) k_finalize(MdArgs a, const double2 *__restrict__ epart,
+// One block per system: fixed-order sums of its near-energy partials, |rho|^2
+// and kinetic partials; Berendsen factor; k-set cursor and step counter.
+__global__ void __launch_bounds__(1024) k_finalize(BatchView bv, const double2 *__restrict__ epart,
                                                    const double2 *__restrict__ rho,
                                                    const double *__restrict__ kpart, int with_kinetic,
-                                                   double *__restrict__ energy, int64_t *cursor,
-                                                   int64_t advance, int64_t *step_counter) {
+                                                   double *__restrict__ energy, int64_t advance) {
     __shared__ double s_red[4][32];
+    const int sy = blockIdx.x;
+    if (bv.force_mask && !bv.force_mask[sy]) return;
+    const SysDesc &a = bv.sys[sy];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     double un = 0.0, uw = 0.0, r2 = 0.0, ke = 0.0;
     for (int j = tid; j < a.n_epart; j += blockDim.x) {
-        const double2 e = epart[j];
+        const double2 e = epart[a.e_off + j];
         un += e.x;
         uw += e.y;
     }
-    for (int j = tid; j < a.P; j += blockDim.x) {
-        const double2 r = rho[j];
+    for (int j = tid; j < bv.P; j += blockDim.x) {
+        const double2 r = rho[(int64_t)sy * bv.P + j];
         r2 += r.x * r.x + r.y * r.y;
     }
     if (with_kinetic)
-        for (int j = tid; j < a.n_kpart; j += blockDim.x) ke += kpart[j];
+        for (int j = tid; j < a.n_kpart; j += blockDim.x) ke += kpart[a.kp_off + j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         un += __shfl_down_sync(0xffffffffu, un, o);
@@ -107,10 +115,11 @@ __global__ void __launch_bounds__(1024) k_finalize(MdArgs a, const double2 *__re
         const int nw = blockDim.x / 32;
         for (int q = 0; q < 4; ++q)
             for (int w = 0; w < nw; ++w) t[q] += s_red[q][w];
-        energy[0] = t[0];
-        energy[1] = a.half_coef_U * t[2];
-        energy[2] = a.U_self;
-        energy[3] = t[1];
+        double *en = energy + (int64_t)sy * kNumEnergy;
+        en[0] = t[0];
+        en[1] = a.half_coef_U * t[2];
+        en[2] = a.U_self;
+        en[3] = t[1];
         if (with_kinetic) {
             double K = t[3];
             double T = 2.0 * K / (3.0 * (double)a.n - 3.0);
@@ -120,20 +129,24 @@ __global__ void __launch_bounds__(1024) k_finalize(MdArgs a, const double2 *__re
                 K *= lam * lam;
                 T *= lam * lam;
             }
-            energy[4] = K;
-            energy[5] = T;
-            energy[6] = lam;
-            if (step_counter) *step_counter += 1;
+            en[4] = K;
+            en[5] = T;
+            en[6] = lam;
+            bv.step[sy] += 1;
         }
-        if (cursor) *cursor += advance;
+        bv.cursor[sy] += advance;
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_rescale(int64_t n, double4_32a *__restrict__ vel,
+__global__ void __launch_bounds__(kThreads) k_rescale(BatchView bv, double4_32a *__restrict__ vel,
                                                       const double *__restrict__ energy) {
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= n) return;
-    const double lam = energy[6];
+    const int2 w = bv.pblk[blockIdx.x];
+    const SysDesc &a = bv.sys[w.x];
+    if (a.tau <= 0.0) return;
+    const int64_t il = (int64_t)w.y * kThreads + threadIdx.x;
+    if (il >= a.n) return;
+    const int64_t i = a.p_off + il;
+    const double lam = energy[(int64_t)w.x * kNumEnergy + 6];
     double4_32a v = vel[i];
     v.x *= lam;
     v.y *= lam;
@@ -165,12 +178,13 @@ __global__ void __launch_bounds__(kThreads) k_unpack(int64_t n, const double4_32
     x3[3 * i + 2] = p.z;
 }
 
-__global__ void __launch_bounds__(kThreads) k_unsort(int64_t n, const int32_t *__restrict__ perm,
+// out[perm[off + s] - off] = sorted[off + s] for one system's range.
+__global__ void __launch_bounds__(kThreads) k_unsort(int64_t n, int64_t off, const int32_t *__restrict__ perm,
                                                      const int32_t *__restrict__ sorted,
                                                      int32_t *__restrict__ out) {
     const int64_t s = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (s >= n) return;
-    out[perm[s]] = sorted[s];
+    out[perm[off + s] - off] = sorted[off + s];
 }
 
 __global__ void k_m_to_int4(int32_t P, const int32_t *__restrict__ m3, int4 *__restrict__ out) {
@@ -183,36 +197,31 @@ inline unsigned nblk(int64_t n) { return (unsigned)((n + kThreads - 1) / kThread
 
 }  // namespace
 
-int kinetic_num_blocks(int64_t n) { return (int)nblk(n); }
-
-cudaError_t launch_kick_drift(const MdArgs &a, double4_32a *posq, double4_32a *vel, const double4_32a *force,
+cudaError_t launch_kick_drift(const BatchView &bv, double4_32a *posq, double4_32a *vel, const double4_32a *force,
                               cudaStream_t st, const Prof *prof) {
     ProfScope ps(prof, "kick_drift");
-    k_kick_drift<<<nblk(a.n), kThreads, 0, st>>>(a, posq, vel, force);
+    k_kick_drift<<<bv.n_pblk, kThreads, 0, st>>>(bv, posq, vel, force);
     return cudaGetLastError();
 }
 
-cudaError_t launch_kick(const MdArgs &a, double4_32a *vel, const double4_32a *force, double *kpart,
+cudaError_t launch_kick(const BatchView &bv, double4_32a *vel, const double4_32a *force, double *kpart,
                         cudaStream_t st, const Prof *prof) {
     ProfScope ps(prof, "kick");
-    k_kick<<<nblk(a.n), kThreads, 0, st>>>(a, vel, force, kpart);
+    k_kick<<<bv.n_pblk, kThreads, 0, st>>>(bv, vel, force, kpart);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const MdArgs &a, const double2 *epart, const double2 *rho,
-                            const double *kpart, int with_kinetic, double *energy,
-                            int64_t *cursor, int64_t advance, int64_t *step_counter,
-                            cudaStream_t st, const Prof *prof) {
+cudaError_t launch_finalize(const BatchView &bv, const double2 *epart, const double2 *rho, const double *kpart,
+                            int with_kinetic, double *energy, int64_t advance, cudaStream_t st, const Prof *prof) {
     ProfScope ps(prof, "finalize");
-    k_finalize<<<1, 1024, 0, st>>>(a, epart, rho, kpart, with_kinetic, energy, cursor, advance,
-                                   step_counter);
+    k_finalize<<<bv.n_sys, 1024, 0, st>>>(bv, epart, rho, kpart, with_kinetic, energy, advance);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rescale(const MdArgs &a, double4_32a *vel, const double *energy, cudaStream_t st,
+cudaError_t launch_rescale(const BatchView &bv, double4_32a *vel, const double *energy, cudaStream_t st,
                            const Prof *prof) {
     ProfScope ps(prof, "rescale");
-    k_rescale<<<nblk(a.n), kThreads, 0, st>>>(a.n, vel, energy);
+    k_rescale<<<bv.n_pblk, kThreads, 0, st>>>(bv, vel, energy);
     return cudaGetLastError();
 }
 
@@ -227,9 +236,9 @@ cudaError_t launch_unpack(int64_t n, const double4_32a *in, double *x3, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_unsort_i32(int64_t n, const int32_t *perm, const int32_t *sorted, int32_t *out,
+cudaError_t launch_unsort_i32(int64_t n, int64_t off, const int32_t *perm, const int32_t *sorted, int32_t *out,
                               cudaStream_t st) {
-    k_unsort<<<nblk(n), kThreads, 0, st>>>(n, perm, sorted, out);
+    k_unsort<<<nblk(n), kThreads, 0, st>>>(n, off, perm, sorted, out);
     return cudaGetLastError();
 }
 

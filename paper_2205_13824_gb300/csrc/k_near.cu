@@ -29,6 +29,9 @@
 // as a Taylor series in r^2 (r^2 / s_l^2 <= 1/4 inside the cutoff), which
 // removes most transcendental work without changing the kernel beyond
 // rounding.
+#include <algorithm>
+#include <cmath>
+
 #include "rbsog_kernels.cuh"
 
 namespace rbsog {
@@ -152,10 +155,9 @@ struct PairConst {
 
 template <int PREC, int ND, int NT>
 __global__ void __launch_bounds__(kThreads, 4)
-    k_near(const __grid_constant__ BoxDev box, const __grid_constant__ NearSog sog, int group, int nseg_x,
-           int cap, const int32_t *__restrict__ start, const double4_32a *__restrict__ sp64,
-           const uint4 *__restrict__ sp32, double4_32a *__restrict__ fnear, double2 *__restrict__ epart,
-           int32_t *__restrict__ nbr) {
+    k_near(const BatchView bv, const __grid_constant__ NearSog sog, const int32_t *__restrict__ start,
+           const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
+           double4_32a *__restrict__ fnear, double2 *__restrict__ epart, int32_t *__restrict__ nbr) {
     using T = NearTypes<PREC>;
     using real = typename T::real;
     using staged = typename T::staged;
@@ -170,11 +172,16 @@ __global__ void __launch_bounds__(kThreads, 4)
     // disjoint regions: restrict lets the compiler move staged loads across
     // list stores
     staged *__restrict__ st = reinterpret_cast<staged *>(smem_raw);
-    entry *__restrict__ list = reinterpret_cast<entry *>(smem_raw + sizeof(staged) * (size_t)cap);   // [kList][kThreads]
+    entry *__restrict__ list = reinterpret_cast<entry *>(smem_raw + sizeof(staged) * (size_t)bv.max_cap);   // [kList][kThreads]
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int2 work = bv.nblk[blockIdx.x];
+    const SysDesc &desc = bv.sys[work.x];
+    const BoxDev &box = desc.box;
+    const int group = desc.group, nseg_x = desc.nseg_x, cap = desc.near_cap;
+    const int64_t coff = desc.c_off;
     const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
-    const int sx = blockIdx.x % nseg_x, row = blockIdx.x / nseg_x;
+    const int sx = work.y % nseg_x, row = work.y / nseg_x;
     const int cy = row % ny, cz = row / ny;
     const int x0 = sx * group, xe = min(x0 + group, nx), nh = xe - x0, w = nh + 2;
     const int ns = 9 * w;
@@ -186,13 +193,13 @@ __global__ void __launch_bounds__(kThreads, 4)
         const int zz = wrap_cell(cz + r / 3 - 1, nz, shz);
         const int yy = wrap_cell(cy + r % 3 - 1, ny, shy);
         const int xx = wrap_cell(x0 - 1 + xi, nx, shx);
-        const int id = (zz * ny + yy) * nx + xx;
+        const int64_t id = coff + (zz * ny + yy) * nx + xx;
         const int b = start[id];
         s_src[k] = b;
         s_off[k + 1] = start[id + 1] - b;   // count for now
         s_shift[k] = (shx + 1) | ((shy + 1) << 2) | ((shz + 1) << 4);
     }
-    if (tid <= nh) s_hstart[tid] = start[(cz * ny + cy) * nx + x0 + tid];
+    if (tid <= nh) s_hstart[tid] = start[coff + (cz * ny + cy) * nx + x0 + tid];
     if (tid == 0) s_off[0] = 0;
     __syncthreads();
     if (wid == 0) {  // inclusive scan of counts into offsets, 32 at a time
@@ -391,7 +398,7 @@ __global__ void __launch_bounds__(kThreads, 4)
         e_near += __shfl_down_sync(0xffffffffu, e_near, o);
         e_wca += __shfl_down_sync(0xffffffffu, e_wca, o);
     }
-    if (lane == 0) epart[(int64_t)blockIdx.x * (kThreads / 32) + wid] = make_double2(e_near, e_wca);
+    if (lane == 0) epart[desc.e_off + work.y * (kThreads / 32) + wid] = make_double2(e_near, e_wca);
 }
 
 size_t near_smem(int precision, int cap) {
@@ -401,21 +408,27 @@ size_t near_smem(int precision, int cap) {
 
 }  // namespace
 
-int near_num_blocks(const BoxDev &box, int group) {
-    const int nseg_x = (box.nc[0] + group - 1) / group;
-    return nseg_x * box.nc[1] * box.nc[2];
+void near_layout(const BoxDev &box, int64_t n, int precision, int &group, int &nseg_x, int &cap, int &nblocks,
+                 int &npartials) {
+    // one warp per 32 home particles and ~120 home particles per block; the
+    // staging chunk covers the mean occupancy of the 9 (group + 2) staged
+    // cells with 15% head-room (denser regions are processed in chunks)
+    const double per_cell = (double)n / (double)box.ncell;
+    int g = (int)std::lround(120.0 / std::max(per_cell, 1e-3));
+    g = std::max(1, std::min(g, std::min(kMaxGroup, box.nc[0] - 2)));
+    group = g;
+    nseg_x = (box.nc[0] + g - 1) / g;
+    nblocks = nseg_x * box.nc[1] * box.nc[2];
+    npartials = nblocks * (kThreads / 32);
+    const double est = 9.0 * (g + 2) * per_cell * 1.15 + 64.0;
+    const int cap_max = precision == 0 ? 2048 : 4096;
+    cap = std::min(cap_max, std::max(256, ((int)std::ceil(est) + 127) / 128 * 128));
 }
 
-int near_num_partials(const BoxDev &box, int group) { return near_num_blocks(box, group) * (kThreads / 32); }
-
-cudaError_t launch_near(int precision, const BoxDev &box, const NearSog &sog, int group, int cap,
-                        const int32_t *start, const double4_32a *sp64, const uint4 *sp32,
-                        double4_32a *fnear, double2 *epart, int32_t *nbr, cudaStream_t st,
-                        const Prof *prof) {
-    if (group < 1 || group > kMaxGroup || cap < 32 || cap > (1 << 20)) return cudaErrorInvalidValue;
-    const int nseg_x = (box.nc[0] + group - 1) / group;
-    const unsigned blocks = (unsigned)(nseg_x * box.nc[1] * box.nc[2]);
-    const size_t sm = near_smem(precision, cap);
+cudaError_t launch_near(int precision, const BatchView &bv, const NearSog &sog, const int32_t *start,
+                        const double4_32a *sp64, const uint4 *sp32, double4_32a *fnear, double2 *epart,
+                        int32_t *nbr, cudaStream_t st, const Prof *prof) {
+    const size_t sm = near_smem(precision, bv.max_cap);
     // specialised (fully unrolled) variants for the production kernel: b = 1.4878...
     // gives 5 exp Gaussians below 2 r_c and 8 (FP32) / 12 (FP64) Taylor terms
     // for any r_c; other parameter sets take the runtime-count variant
@@ -424,7 +437,7 @@ cudaError_t launch_near(int precision, const BoxDev &box, const NearSog &sog, in
                                       : (spec ? "near_fp32c" : "near_fp32c_generic"));
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kern<<<blocks, kThreads, sm, st>>>(box, sog, group, nseg_x, cap, start, sp64, sp32, fnear, epart, nbr);
+        kern<<<bv.n_nblk, kThreads, sm, st>>>(bv, sog, start, sp64, sp32, fnear, epart, nbr);
     };
     if (precision == 1) {
         if (spec) go(k_near<1, 5, 8>);

@@ -1,7 +1,10 @@
-// C ABI of librbsog (declared in include/rbsog.h): context management,
-// parameter set-up on the host (SOG solve, S, cell grid, launch shapes), and
-// the sequencing of the device kernels for one force evaluation and one
-// velocity-Verlet step, replayed from a CUDA graph.
+// C ABI of librbsog (declared in include/rbsog.h).  The engine advances a
+// batch of independent systems laid out back to back in device memory; a
+// single-system context is a batch of one.  Host code here sets up the
+// parameters (SOG solve, S, cell grids, launch layouts, work tables) and
+// sequences the device kernels of one force evaluation and one
+// velocity-Verlet step, which is captured once into a CUDA graph and
+// replayed: one graph launch advances every system of the batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,53 +34,57 @@ struct ProfRec {
 }  // namespace
 
 struct rbsog_ctx {
-    int64_t n = 0;
+    int32_t n_sys = 0;
+    std::vector<int64_t> n_per, p_off;
+    int64_t n_total = 0;
     int device = 0;
     cudaStream_t user = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::string err;
 
-    bool have_params = false, have_state = false, force_valid = false;
-    rbsog_params p{};
-    // solved parameters
+    bool have_params = false;
+    std::vector<char> have_state, force_valid;
+    std::vector<rbsog_params> p;
+    // shared SOG (every system of a batch uses the same b, sigma, omega0, M, r_c)
     std::vector<double> omega, s;
-    double sigma = 0, omega0 = 0, S = 0, V = 0, coef = 0, half_coef_U = 0, U_self = 0, sum_q2 = 0;
-    BoxDev box{};
+    double sigma = 0, omega0 = 0;
     NearSog nsog{};
-    int group = 1, near_cap = 1024, tile_p = 2048, n_ptiles = 1, n_epart = 1, n_kpart = 1;
-    int64_t n_sets = 0, n_chains = 0;
-    int chain_len = 256;
-    int64_t host_cursor = 0;  // k-sets consumed, mirrored on the host
+    int32_t P = 0, precision = 0;
+    std::vector<SysDesc> desc;
+    std::vector<double> S, sum_q2;
+    std::vector<int64_t> n_chains, host_cursor;
+    std::vector<int> chain_len;
+    int64_t ncell_total = 0;
+    int max_cap = 256, max_tile_p = 128;
+    std::vector<int2> pblk, nblk, sblk;
 
-    // device buffers: per-particle (allocated at create)
+    // device buffers
     double4_32a *posq = nullptr, *vel = nullptr, *force = nullptr, *fnear = nullptr, *sp64 = nullptr;
     uint4 *sp32 = nullptr;
-    double *staging = nullptr;        // [n][3]
+    double *staging = nullptr;        // [n_total][3]
     int32_t *nbr_sorted = nullptr, *i32_tmp = nullptr;
     CellBuffers cb{};
     double *kpart = nullptr;
-    // per-parameter-set
     int4 *kseq = nullptr;
     int64_t *cursor = nullptr, *step_ctr = nullptr;
     double2 *rho_part = nullptr, *rho = nullptr, *epart = nullptr;
     void *ktab = nullptr;
-    int32_t *ncell_alloc = nullptr;  // marker of cell arrays size
-    int64_t ncell_cap = 0;
     double *energy = nullptr;
     int32_t *err_flag = nullptr;
     int4 *m_tmp = nullptr;
     int32_t *m3_tmp = nullptr;
-    int32_t m_tmp_cap = 0;
+    SysDesc *d_desc = nullptr;
+    int2 *d_pblk = nullptr, *d_nblk = nullptr, *d_sblk = nullptr;
+    int32_t *d_cell_sys = nullptr;
+    int32_t *d_mask = nullptr;        // [n_sys] systems that need a force evaluation
     // pinned host mirrors
     double *h_energy = nullptr;
     int32_t *h_err = nullptr;
     int64_t *h_i64 = nullptr;
 
-    // graph of one step
     cudaGraphExec_t graph = nullptr;
 
-    // profiling
     bool profiling = false;
     std::vector<ProfRec> prof_open, prof_done;
     std::vector<cudaEvent_t> ev_pool;
@@ -243,17 +250,15 @@ double theta_sum(double s, double L) {
     return h * L / (std::sqrt(kPi) * s);
 }
 
-void build_near_sog(rbsog_ctx *c) {
-    NearSog &ns = c->nsog;
+void build_near_sog(NearSog &ns, const std::vector<double> &omega, const std::vector<double> &s, int M,
+                    double rc) {
     std::memset(&ns, 0, sizeof ns);
-    const int M = c->p.M;
-    const double rc = c->p.r_c;
     int nd = 0;
-    while (nd <= M && c->s[nd] < 2.0 * rc) ++nd;
+    while (nd <= M && s[nd] < 2.0 * rc) ++nd;
     ns.n_direct = nd;
     for (int l = 0; l < nd; ++l) {
-        ns.omega[l] = c->omega[l];
-        ns.inv_s2[l] = 1.0 / (c->s[l] * c->s[l]);
+        ns.omega[l] = omega[l];
+        ns.inv_s2[l] = 1.0 / (s[l] * s[l]);
         ns.omega_f[l] = (float)ns.omega[l];
         ns.omega_s2_f[l] = (float)(ns.omega[l] * ns.inv_s2[l]);
         ns.inv_s2_log2e_f[l] = (float)(ns.inv_s2[l] * 1.4426950408889634);
@@ -264,9 +269,9 @@ void build_near_sog(rbsog_ctx *c) {
         double A[kMaxTaylor + 2];
         for (int n = 0; n < kMaxTaylor + 2; ++n) {
             A[n] = 0.0;
-            for (int l = M; l >= nd; --l) A[n] += c->omega[l] * std::pow(c->s[l], -2.0 * n);
+            for (int l = M; l >= nd; --l) A[n] += omega[l] * std::pow(s[l], -2.0 * n);
         }
-        const double xmax = rc * rc / (c->s[nd] * c->s[nd]);
+        const double xmax = rc * rc / (s[nd] * s[nd]);
         // smallest number of terms whose first omitted term x^n / n! is below tol
         auto terms = [xmax](double tol) {
             int nt = 1;
@@ -307,64 +312,57 @@ rbsog_status leave(rbsog_ctx *ctx) {
     return RBSOG_OK;
 }
 
-FarArgs far_args(rbsog_ctx *c, const int4 *m_explicit, int32_t P) {
-    FarArgs a{};
-    a.n = c->n;
-    a.P = P;
-    for (int d = 0; d < 3; ++d) a.L[d] = c->p.L[d];
-    a.coef = -c->p.coulomb_prefactor * std::pow(kPi, 1.5) * c->S / ((double)P * c->V);
-    a.kseq = c->kseq;
-    a.cursor = c->cursor;
-    a.m_explicit = m_explicit;
-    a.tile_p = c->tile_p;
-    a.n_ptiles = c->n_ptiles;
-    return a;
-}
-
-MdArgs md_args(rbsog_ctx *c) {
-    MdArgs a{};
-    a.n = c->n;
-    a.dt = c->p.dt;
-    a.mass = c->p.mass;
-    a.inv_mass = 1.0 / c->p.mass;
-    for (int d = 0; d < 3; ++d) a.L[d] = c->p.L[d];
-    a.T0 = c->p.T_target;
-    a.tau = c->p.tau_T;
-    a.n_epart = c->n_epart;
-    a.n_kpart = c->n_kpart;
-    a.P = c->p.P;
-    a.half_coef_U = c->p.coulomb_prefactor * std::pow(kPi, 1.5) * c->S / (2.0 * c->p.P * c->V);
-    a.U_self = c->U_self;
-    return a;
+BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
+    BatchView v{};
+    v.sys = c->d_desc;
+    v.n_sys = c->n_sys;
+    v.P = P > 0 ? P : c->P;
+    v.n_total = c->n_total;
+    v.ncell_total = c->ncell_total;
+    v.pblk = c->d_pblk;
+    v.n_pblk = (int32_t)c->pblk.size();
+    v.nblk = c->d_nblk;
+    v.n_nblk = (int32_t)c->nblk.size();
+    v.sblk = c->d_sblk;
+    v.n_sblk = (int32_t)c->sblk.size();
+    v.cell_sys = c->d_cell_sys;
+    v.cursor = c->cursor;
+    v.step = c->step_ctr;
+    v.kseq = c->kseq;
+    v.m_explicit = m_explicit;
+    v.max_cap = c->max_cap;
+    v.max_tile_p = c->max_tile_p;
+    v.force_mask = nullptr;
+    return v;
 }
 
 // Cell list + near field + far field for the current positions; total force
-// into c->force (caller order).  m_explicit: explicit k-set or null.
-rbsog_status enqueue_forces(rbsog_ctx *ctx, const int4 *m_explicit, int32_t *nbr_sorted) {
+// into c->force (caller order).  With a mask, only masked systems take the
+// new forces, energies and k-set.
+rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_sorted) {
     const Prof *pf = prof_of(ctx);
-    const int prec = ctx->p.precision;
-    CK(launch_build_cells(ctx->n, ctx->posq, ctx->box, ctx->cb, prec, ctx->sp64, ctx->sp32,
+    const int prec = ctx->precision;
+    CK(launch_build_cells(bv, ctx->posq, ctx->cb, prec, ctx->sp64, ctx->sp32, ctx->st, pf));
+    CK(launch_near(prec, bv, ctx->nsog, ctx->cb.start, ctx->sp64, ctx->sp32, ctx->fnear, ctx->epart, nbr_sorted,
+                   ctx->st, pf));
+    CK(launch_rho_sweep(prec, bv, ctx->sp64, ctx->sp32, ctx->rho_part, ctx->st, pf));
+    CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
+    CK(launch_far_scatter(prec, bv, ctx->sp64, ctx->sp32, ctx->ktab, ctx->fnear, ctx->cb.perm, ctx->force,
                           ctx->err_flag, ctx->st, pf));
-    CK(launch_near(prec, ctx->box, ctx->nsog, ctx->group, ctx->near_cap, ctx->cb.start, ctx->sp64, ctx->sp32,
-                   ctx->fnear, ctx->epart, nbr_sorted, ctx->st, pf));
-    const FarArgs fa = far_args(ctx, m_explicit, ctx->p.P);
-    CK(launch_rho_sweep(prec, fa, ctx->sp64, ctx->sp32, ctx->rho_part, ctx->st, pf));
-    CK(launch_rho_combine(prec, fa, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
-    CK(launch_far_scatter(prec, fa, ctx->sp64, ctx->sp32, ctx->ktab, ctx->fnear, ctx->cb.perm,
-                          ctx->force, ctx->err_flag, ctx->st, pf));
     return RBSOG_OK;
 }
 
 rbsog_status enqueue_step(rbsog_ctx *ctx) {
     const Prof *pf = prof_of(ctx);
-    const MdArgs ma = md_args(ctx);
-    CK(launch_kick_drift(ma, ctx->posq, ctx->vel, ctx->force, ctx->st, pf));
-    rbsog_status s = enqueue_forces(ctx, nullptr, nullptr);
+    const BatchView bv = view(ctx);
+    CK(launch_kick_drift(bv, ctx->posq, ctx->vel, ctx->force, ctx->st, pf));
+    rbsog_status s = enqueue_forces(ctx, bv, nullptr);
     if (s != RBSOG_OK) return s;
-    CK(launch_kick(ma, ctx->vel, ctx->force, ctx->kpart, ctx->st, pf));
-    CK(launch_finalize(ma, ctx->epart, ctx->rho, ctx->kpart, 1, ctx->energy, ctx->cursor, 1,
-                       ctx->step_ctr, ctx->st, pf));
-    if (ctx->p.tau_T > 0.0) CK(launch_rescale(ma, ctx->vel, ctx->energy, ctx->st, pf));
+    CK(launch_kick(bv, ctx->vel, ctx->force, ctx->kpart, ctx->st, pf));
+    CK(launch_finalize(bv, ctx->epart, ctx->rho, ctx->kpart, 1, ctx->energy, 1, ctx->st, pf));
+    bool thermo = false;
+    for (auto &pp : ctx->p) thermo = thermo || pp.tau_T > 0.0;
+    if (thermo) CK(launch_rescale(bv, ctx->vel, ctx->energy, ctx->st, pf));
     return RBSOG_OK;
 }
 
@@ -386,17 +384,76 @@ rbsog_status check_flags(rbsog_ctx *ctx) {
     return RBSOG_OK;
 }
 
+rbsog_status upload_desc(rbsog_ctx *ctx) {
+    CK(cudaMemcpyAsync(ctx->d_desc, ctx->desc.data(), sizeof(SysDesc) * ctx->n_sys, cudaMemcpyHostToDevice,
+                       ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return RBSOG_OK;
+}
+
+double self_energy(const rbsog_ctx *c, int s) {
+    double wsum = 0.0;
+    for (size_t l = 0; l < c->omega.size(); ++l) wsum += c->omega[l];
+    return 0.5 * wsum * c->sum_q2[s] * c->p[s].coulomb_prefactor;
+}
+
+// Systems without valid forces get an initial force evaluation (and consume
+// one k-set); the others keep theirs.
+rbsog_status initial_forces(rbsog_ctx *ctx) {
+    std::vector<int32_t> mask(ctx->n_sys, 0);
+    bool any = false;
+    for (int s = 0; s < ctx->n_sys; ++s)
+        if (!ctx->force_valid[s]) {
+            mask[s] = 1;
+            any = true;
+        }
+    if (!any) return RBSOG_OK;
+    CK(cudaMemcpyAsync(ctx->d_mask, mask.data(), sizeof(int32_t) * ctx->n_sys, cudaMemcpyHostToDevice, ctx->st));
+    BatchView bv = view(ctx);
+    bv.force_mask = ctx->d_mask;
+    rbsog_status es = enqueue_forces(ctx, bv, nullptr);
+    if (es != RBSOG_OK) return es;
+    CK(launch_finalize(bv, ctx->epart, ctx->rho, ctx->kpart, 0, ctx->energy, 1, ctx->st, prof_of(ctx)));
+    CK(cudaStreamSynchronize(ctx->st));   // the host mask buffer is reused
+    for (int s = 0; s < ctx->n_sys; ++s)
+        if (mask[s]) {
+            ctx->host_cursor[s] += 1;
+            ctx->force_valid[s] = 1;
+        }
+    return RBSOG_OK;
+}
+
+rbsog_status check_sys(rbsog_ctx *ctx, int32_t sys) {
+    if (sys < 0 || sys >= ctx->n_sys) return fail(ctx, RBSOG_EINVAL, "system %d outside [0, %d)", sys, ctx->n_sys);
+    return RBSOG_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
-rbsog_status rbsog_create(rbsog_ctx **out, int64_t n, int device, void *stream) {
-    if (!out) return RBSOG_EINVAL;
+rbsog_status rbsog_batch_create(rbsog_batch **out, int32_t n_sys, const int64_t *n_per, int device, void *stream) {
+    if (!out || !n_per || n_sys < 1) return RBSOG_EINVAL;
     *out = nullptr;
-    if (n < 2 || n > (int64_t)INT32_MAX / 2) return RBSOG_EINVAL;
+    int64_t total = 0;
+    for (int s = 0; s < n_sys; ++s) {
+        if (n_per[s] < 2) return RBSOG_EINVAL;
+        total += n_per[s];
+    }
+    if (total > (int64_t)INT32_MAX / 2) return RBSOG_EINVAL;
     rbsog_ctx *ctx = new (std::nothrow) rbsog_ctx();
     if (!ctx) return RBSOG_ENOMEM;
-    ctx->n = n;
+    ctx->n_sys = n_sys;
+    ctx->n_per.assign(n_per, n_per + n_sys);
+    ctx->p_off.resize(n_sys);
+    for (int s = 0; s < n_sys; ++s) {
+        ctx->p_off[s] = ctx->n_total;
+        ctx->n_total += n_per[s];
+    }
+    ctx->have_state.assign(n_sys, 0);
+    ctx->force_valid.assign(n_sys, 0);
+    ctx->sum_q2.assign(n_sys, 0.0);
+    ctx->host_cursor.assign(n_sys, 0);
     ctx->device = device;
     ctx->user = (cudaStream_t)stream;
     ctx->prof_hook.mark = prof_mark;
@@ -410,16 +467,18 @@ rbsog_status rbsog_create(rbsog_ctx **out, int64_t n, int device, void *stream) 
     if (cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess)
         return bail(RBSOG_ECUDA);
+    const int64_t n = ctx->n_total;
     bool ok = dalloc(&ctx->posq, n) == cudaSuccess && dalloc(&ctx->vel, n) == cudaSuccess &&
               dalloc(&ctx->force, n) == cudaSuccess && dalloc(&ctx->fnear, n) == cudaSuccess &&
               dalloc(&ctx->sp64, n) == cudaSuccess && dalloc(&ctx->sp32, n) == cudaSuccess &&
               dalloc(&ctx->staging, 3 * n) == cudaSuccess && dalloc(&ctx->nbr_sorted, n) == cudaSuccess &&
               dalloc(&ctx->i32_tmp, n) == cudaSuccess && dalloc(&ctx->cb.cell_of, n) == cudaSuccess &&
               dalloc(&ctx->cb.slot, n) == cudaSuccess && dalloc(&ctx->cb.perm_raw, n) == cudaSuccess &&
-              dalloc(&ctx->cb.perm, n) == cudaSuccess &&
-              dalloc(&ctx->kpart, (size_t)kinetic_num_blocks(n)) == cudaSuccess &&
-              dalloc(&ctx->cursor, 1) == cudaSuccess && dalloc(&ctx->step_ctr, 1) == cudaSuccess &&
-              dalloc(&ctx->energy, kNumEnergy) == cudaSuccess && dalloc(&ctx->err_flag, 1) == cudaSuccess;
+              dalloc(&ctx->cb.perm, n) == cudaSuccess && dalloc(&ctx->cursor, n_sys) == cudaSuccess &&
+              dalloc(&ctx->step_ctr, n_sys) == cudaSuccess &&
+              dalloc(&ctx->energy, (size_t)kNumEnergy * n_sys) == cudaSuccess &&
+              dalloc(&ctx->err_flag, 1) == cudaSuccess && dalloc(&ctx->d_desc, n_sys) == cudaSuccess &&
+              dalloc(&ctx->d_mask, n_sys) == cudaSuccess;
     if (!ok) return bail(RBSOG_ENOMEM);
     if (cudaMallocHost((void **)&ctx->h_energy, sizeof(double) * kNumEnergy) != cudaSuccess ||
         cudaMallocHost((void **)&ctx->h_err, sizeof(int32_t)) != cudaSuccess ||
@@ -427,176 +486,237 @@ rbsog_status rbsog_create(rbsog_ctx **out, int64_t n, int device, void *stream) 
         return bail(RBSOG_ENOMEM);
     cudaMemsetAsync(ctx->vel, 0, sizeof(double4_32a) * n, ctx->st);
     cudaMemsetAsync(ctx->force, 0, sizeof(double4_32a) * n, ctx->st);
-    cudaMemsetAsync(ctx->energy, 0, sizeof(double) * kNumEnergy, ctx->st);
+    cudaMemsetAsync(ctx->posq, 0, sizeof(double4_32a) * n, ctx->st);
+    cudaMemsetAsync(ctx->energy, 0, sizeof(double) * kNumEnergy * n_sys, ctx->st);
     cudaMemsetAsync(ctx->err_flag, 0, sizeof(int32_t), ctx->st);
-    cudaMemsetAsync(ctx->cursor, 0, sizeof(int64_t), ctx->st);
-    cudaMemsetAsync(ctx->step_ctr, 0, sizeof(int64_t), ctx->st);
+    cudaMemsetAsync(ctx->cursor, 0, sizeof(int64_t) * n_sys, ctx->st);
+    cudaMemsetAsync(ctx->step_ctr, 0, sizeof(int64_t) * n_sys, ctx->st);
     if (cudaStreamSynchronize(ctx->st) != cudaSuccess) return bail(RBSOG_ECUDA);
-    ctx->n_kpart = kinetic_num_blocks(n);
     *out = ctx;
     return RBSOG_OK;
 }
 
-rbsog_status rbsog_set_params(rbsog_ctx *ctx, const rbsog_params *pp) {
-    if (!ctx || !pp) return RBSOG_EINVAL;
-    rbsog_params p = *pp;
-    if (!(p.b > 1.0)) return fail(ctx, RBSOG_EINVAL, "b must be > 1");
-    if (p.M < 0 || p.M >= kMaxGauss) return fail(ctx, RBSOG_EINVAL, "M must be in [0, %d]", kMaxGauss - 1);
-    if (p.P < 1) return fail(ctx, RBSOG_EINVAL, "P must be >= 1");
-    if (p.n_ksets < 1) return fail(ctx, RBSOG_EINVAL, "n_ksets must be >= 1");
-    if (!(p.r_c > 0.0)) return fail(ctx, RBSOG_EINVAL, "r_c must be > 0");
-    if (!(p.mass > 0.0)) return fail(ctx, RBSOG_EINVAL, "mass must be > 0");
-    if (p.precision != RBSOG_FP64 && p.precision != RBSOG_FP32C)
-        return fail(ctx, RBSOG_EINVAL, "unknown precision %d", p.precision);
-    if (p.chain_len < 0) return fail(ctx, RBSOG_EINVAL, "chain_len must be >= 0");
-    if (p.wca_sigma < 0.0) return fail(ctx, RBSOG_EINVAL, "wca_sigma must be >= 0");
-    int nc[3];
-    for (int d = 0; d < 3; ++d) {
-        if (!(p.L[d] > 0.0)) return fail(ctx, RBSOG_EINVAL, "box edges must be > 0");
-        if (!(p.r_c < 0.5 * p.L[d])) return fail(ctx, RBSOG_EINVAL, "r_c must be < L/2");
-        nc[d] = (int)std::floor(p.L[d] / p.r_c);
-        if (nc[d] < 3) return fail(ctx, RBSOG_EINVAL, "need at least 3 cells per side (L/r_c >= 3)");
+rbsog_status rbsog_create(rbsog_ctx **out, int64_t n, int device, void *stream) {
+    if (n < 2 || n > (int64_t)INT32_MAX / 2) {
+        if (out) *out = nullptr;
+        return RBSOG_EINVAL;
     }
-    const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
-    if (ncell > (int64_t)INT32_MAX / 2) return fail(ctx, RBSOG_EINVAL, "cell grid too large");
+    return rbsog_batch_create(out, 1, &n, device, stream);
+}
 
-    // --- SOG (Eqs. 2.9-2.11)
-    double sigma = p.sigma, w0 = p.omega0;
+rbsog_status rbsog_batch_set_params(rbsog_batch *ctx, const rbsog_params *pp) {
+    if (!ctx || !pp) return RBSOG_EINVAL;
+    const int ns = ctx->n_sys;
+    std::vector<rbsog_params> p(pp, pp + ns);
+    std::vector<BoxDev> box(ns);
+    for (int s = 0; s < ns; ++s) {
+        const rbsog_params &q = p[s];
+        if (!(q.b > 1.0)) return fail(ctx, RBSOG_EINVAL, "system %d: b must be > 1", s);
+        if (q.M < 0 || q.M >= kMaxGauss) return fail(ctx, RBSOG_EINVAL, "system %d: M must be in [0, %d]", s, kMaxGauss - 1);
+        if (q.P < 1) return fail(ctx, RBSOG_EINVAL, "system %d: P must be >= 1", s);
+        if (q.n_ksets < 1) return fail(ctx, RBSOG_EINVAL, "system %d: n_ksets must be >= 1", s);
+        if (!(q.r_c > 0.0)) return fail(ctx, RBSOG_EINVAL, "system %d: r_c must be > 0", s);
+        if (!(q.mass > 0.0)) return fail(ctx, RBSOG_EINVAL, "system %d: mass must be > 0", s);
+        if (q.precision != RBSOG_FP64 && q.precision != RBSOG_FP32C)
+            return fail(ctx, RBSOG_EINVAL, "system %d: unknown precision %d", s, q.precision);
+        if (q.chain_len < 0) return fail(ctx, RBSOG_EINVAL, "system %d: chain_len must be >= 0", s);
+        if (q.wca_sigma < 0.0) return fail(ctx, RBSOG_EINVAL, "system %d: wca_sigma must be >= 0", s);
+        if (s > 0 && (q.b != p[0].b || q.sigma != p[0].sigma || q.omega0 != p[0].omega0 || q.M != p[0].M ||
+                      q.r_c != p[0].r_c || q.P != p[0].P || q.precision != p[0].precision))
+            return fail(ctx, RBSOG_EINVAL, "system %d: b, sigma, omega0, M, r_c, P and precision must be the same "
+                                           "for every system of a batch", s);
+        BoxDev &b = box[s];
+        std::memset(&b, 0, sizeof b);
+        int64_t ncell = 1;
+        for (int d = 0; d < 3; ++d) {
+            if (!(q.L[d] > 0.0)) return fail(ctx, RBSOG_EINVAL, "system %d: box edges must be > 0", s);
+            if (!(q.r_c < 0.5 * q.L[d])) return fail(ctx, RBSOG_EINVAL, "system %d: r_c must be < L/2", s);
+            b.nc[d] = (int)std::floor(q.L[d] / q.r_c);
+            if (b.nc[d] < 3) return fail(ctx, RBSOG_EINVAL, "system %d: need at least 3 cells per side (L/r_c >= 3)", s);
+            ncell *= b.nc[d];
+            b.L[d] = q.L[d];
+            b.h[d] = q.L[d] / (double)b.nc[d];
+            b.L_f[d] = (float)q.L[d];
+            b.fix_scale[d] = (float)(q.L[d] / 4294967296.0);
+        }
+        if (ncell > (int64_t)INT32_MAX / 4) return fail(ctx, RBSOG_EINVAL, "system %d: cell grid too large", s);
+        b.ncell = (int32_t)ncell;
+        b.rc2 = q.r_c * q.r_c;
+        b.lB = q.coulomb_prefactor;
+        b.wca_s2 = q.wca_sigma * q.wca_sigma;
+        b.wca_rc2 = q.wca_sigma > 0.0 ? std::pow(2.0, 1.0 / 3.0) * b.wca_s2 : 0.0;
+        b.wca_eps = q.wca_eps;
+        b.rc2_f = (float)b.rc2;
+        b.lB_f = (float)b.lB;
+        b.wca_s2_f = (float)b.wca_s2;
+        b.wca_rc2_f = (float)b.wca_rc2;
+        b.wca_eps_f = (float)b.wca_eps;
+    }
+
+    // --- SOG (Eqs. 2.9-2.11), shared by the batch
+    double sigma = p[0].sigma, w0 = p[0].omega0;
     if (!(sigma > 0.0)) {
-        if (!solve_sigma(p.b, p.r_c, sigma, w0))
-            return fail(ctx, RBSOG_EINVAL, "no C0/C1 root for b=%g r_c=%g", p.b, p.r_c);
+        if (!solve_sigma(p[0].b, p[0].r_c, sigma, w0))
+            return fail(ctx, RBSOG_EINVAL, "no C0/C1 root for b=%g r_c=%g", p[0].b, p[0].r_c);
     } else if (!(w0 > 0.0)) {
-        w0 = c0_weight(p.b, sigma, p.r_c);
+        w0 = c0_weight(p[0].b, sigma, p[0].r_c);
     }
     if (!(w0 > 0.0) || !std::isfinite(w0)) return fail(ctx, RBSOG_EINVAL, "invalid omega0");
-    std::vector<double> w, s;
-    bsa_coeffs(p.b, sigma, p.M, w, s);
+    std::vector<double> w, sv;
+    bsa_coeffs(p[0].b, sigma, p[0].M, w, sv);
     w[0] = w0;
-    double S = 0.0;
-    for (int l = p.M; l >= 0; --l) {
-        const double prod = theta_sum(s[l], p.L[0]) * theta_sum(s[l], p.L[1]) * theta_sum(s[l], p.L[2]);
-        S += w[l] * s[l] * s[l] * s[l] * (prod - 1.0);
-    }
 
     drop_graph(ctx);
     ctx->p = p;
     ctx->omega = w;
-    ctx->s = s;
+    ctx->s = sv;
     ctx->sigma = sigma;
     ctx->omega0 = w0;
-    ctx->S = S;
-    ctx->V = p.L[0] * p.L[1] * p.L[2];
-    double wsum = 0.0;
-    for (int l = 0; l <= p.M; ++l) wsum += w[l];
-    ctx->U_self = 0.5 * wsum * ctx->sum_q2 * p.coulomb_prefactor;
+    ctx->P = p[0].P;
+    ctx->precision = p[0].precision;
+    build_near_sog(ctx->nsog, w, sv, p[0].M, p[0].r_c);
 
-    BoxDev &b = ctx->box;
-    std::memset(&b, 0, sizeof b);
-    for (int d = 0; d < 3; ++d) {
-        b.L[d] = p.L[d];
-        b.nc[d] = nc[d];
-        b.h[d] = p.L[d] / (double)nc[d];
-        b.L_f[d] = (float)p.L[d];
-        b.fix_scale[d] = (float)(p.L[d] / 4294967296.0);
+    // --- per-system layout
+    ctx->desc.assign(ns, SysDesc{});
+    ctx->S.assign(ns, 0.0);
+    ctx->n_chains.assign(ns, 0);
+    ctx->chain_len.assign(ns, 256);
+    ctx->pblk.clear();
+    ctx->nblk.clear();
+    ctx->sblk.clear();
+    std::vector<int32_t> cell_sys;
+    int64_t c_off = 0, e_off = 0, rp_off = 0, k_off = 0, kp_off = 0;
+    ctx->max_cap = 256;
+    ctx->max_tile_p = 128;
+    for (int s = 0; s < ns; ++s) {
+        const rbsog_params &q = p[s];
+        SysDesc &d = ctx->desc[s];
+        d.box = box[s];
+        d.p_off = ctx->p_off[s];
+        d.n = ctx->n_per[s];
+        d.c_off = c_off;
+        int nblocks = 0, npart = 0;
+        near_layout(d.box, d.n, ctx->precision, d.group, d.nseg_x, d.near_cap, nblocks, npart);
+        d.e_off = (int32_t)e_off;
+        d.n_epart = npart;
+        far_layout(d.n, ctx->P, d.tile_p, d.n_ptiles);
+        d.rp_off = rp_off;
+        d.k_off = k_off;
+        d.n_sets = q.n_ksets;
+        d.n_kpart = (int32_t)((d.n + kParticleBlock - 1) / kParticleBlock);
+        d.kp_off = (int32_t)kp_off;
+        double Ssum = 0.0;
+        for (int l = q.M; l >= 0; --l) {
+            const double prod = theta_sum(sv[l], q.L[0]) * theta_sum(sv[l], q.L[1]) * theta_sum(sv[l], q.L[2]);
+            Ssum += w[l] * sv[l] * sv[l] * sv[l] * (prod - 1.0);
+        }
+        ctx->S[s] = Ssum;
+        const double V = q.L[0] * q.L[1] * q.L[2];
+        d.coef = -q.coulomb_prefactor * std::pow(kPi, 1.5) * Ssum / ((double)ctx->P * V);
+        d.half_coef_U = q.coulomb_prefactor * std::pow(kPi, 1.5) * Ssum / (2.0 * ctx->P * V);
+        d.dt = q.dt;
+        d.mass = q.mass;
+        d.inv_mass = 1.0 / q.mass;
+        d.T0 = q.T_target;
+        d.tau = q.tau_T;
+        ctx->chain_len[s] = q.chain_len > 0 ? q.chain_len : 256;
+        const int64_t total = q.n_ksets * (int64_t)ctx->P;
+        ctx->n_chains[s] = (total + ctx->chain_len[s] - 1) / ctx->chain_len[s];
+        for (int64_t b = 0; b < d.n_kpart; ++b) ctx->pblk.push_back(make_int2(s, (int)b));
+        for (int b = 0; b < nblocks; ++b) ctx->nblk.push_back(make_int2(s, b));
+        for (int b = 0; b < d.n_ptiles; ++b) ctx->sblk.push_back(make_int2(s, b));
+        cell_sys.insert(cell_sys.end(), (size_t)d.box.ncell, s);
+        ctx->max_cap = std::max(ctx->max_cap, d.near_cap);
+        ctx->max_tile_p = std::max(ctx->max_tile_p, d.tile_p);
+        c_off += d.box.ncell;
+        e_off += npart;
+        rp_off += (int64_t)ctx->P * d.n_ptiles;
+        k_off += ctx->n_chains[s] * ctx->chain_len[s];
+        kp_off += d.n_kpart;
     }
-    b.ncell = (int32_t)ncell;
-    b.rc2 = p.r_c * p.r_c;
-    b.lB = p.coulomb_prefactor;
-    b.wca_s2 = p.wca_sigma * p.wca_sigma;
-    b.wca_rc2 = p.wca_sigma > 0.0 ? std::pow(2.0, 1.0 / 3.0) * b.wca_s2 : 0.0;
-    b.wca_eps = p.wca_eps;
-    b.rc2_f = (float)b.rc2;
-    b.lB_f = (float)b.lB;
-    b.wca_s2_f = (float)b.wca_s2;
-    b.wca_rc2_f = (float)b.wca_rc2;
-    b.wca_eps_f = (float)b.wca_eps;
-    build_near_sog(ctx);
-
-    // near field: one thread per home particle, ~110 home particles per block;
-    // the staging chunk covers the mean occupancy of the 9 (group + 2) staged
-    // cells with 30% head-room (denser regions are processed in chunks)
-    const double per_cell = (double)ctx->n / (double)ncell;
-    int g = (int)std::lround(120.0 / std::max(per_cell, 1e-3));
-    g = std::max(1, std::min(g, std::min(16, nc[0] - 2)));
-    ctx->group = g;
-    ctx->n_epart = near_num_partials(b, g);
-    {
-        const double est = 9.0 * (g + 2) * per_cell * 1.15 + 64.0;
-        const int cap_max = p.precision == RBSOG_FP64 ? 2048 : 4096;
-        ctx->near_cap = std::min(cap_max, std::max(256, ((int)std::ceil(est) + 127) / 128 * 128));
-    }
-
-    const int nkt = (p.P + 31) / 32;
-    int tp = 2048;
-    while (tp > 128 && (double)((ctx->n + tp - 1) / tp) * nkt < 152.0 * 8 * 3) tp /= 2;
-    ctx->tile_p = tp;
-    ctx->n_ptiles = far_num_ptiles(ctx->n, tp);
-
-    ctx->chain_len = p.chain_len > 0 ? p.chain_len : 256;
-    ctx->n_sets = p.n_ksets;
-    const int64_t total = p.n_ksets * (int64_t)p.P;
-    ctx->n_chains = (total + ctx->chain_len - 1) / ctx->chain_len;
+    for (int s = 0; s < ns; ++s) ctx->desc[s].U_self = self_energy(ctx, s);
+    ctx->ncell_total = c_off;
+    if (c_off > (int64_t)INT32_MAX / 2) return fail(ctx, RBSOG_EINVAL, "cell grids of the batch too large");
 
     CK(cudaSetDevice(ctx->device));
-    CK(dalloc(&ctx->kseq, (size_t)(ctx->n_chains * ctx->chain_len)));
-    CK(dalloc(&ctx->rho_part, (size_t)p.P * ctx->n_ptiles));
-    CK(dalloc(&ctx->rho, (size_t)p.P));
-    CK(dalloc((unsigned char **)&ctx->ktab, ktab_bytes(p.precision, p.P)));
-    CK(dalloc(&ctx->epart, (size_t)ctx->n_epart));
-    CK(dalloc(&ctx->cb.count, (size_t)ncell));
-    CK(dalloc(&ctx->cb.start, (size_t)ncell + 1));
-    CK(dalloc(&ctx->cb.tile_sum, (size_t)cell_scan_tiles((int)ncell)));
-    CK(dalloc(&ctx->m_tmp, (size_t)p.P));
-    CK(dalloc(&ctx->m3_tmp, (size_t)p.P * 3));
-    ctx->m_tmp_cap = p.P;
+    CK(dalloc(&ctx->kseq, (size_t)k_off));
+    CK(dalloc(&ctx->rho_part, (size_t)rp_off));
+    CK(dalloc(&ctx->rho, (size_t)ns * ctx->P));
+    CK(dalloc((unsigned char **)&ctx->ktab, ktab_bytes(ctx->precision, (int64_t)ns * ctx->P)));
+    CK(dalloc(&ctx->epart, (size_t)e_off));
+    CK(dalloc(&ctx->kpart, (size_t)kp_off));
+    CK(dalloc(&ctx->cb.count, (size_t)c_off));
+    CK(dalloc(&ctx->cb.start, (size_t)c_off + 1));
+    CK(dalloc(&ctx->cb.tile_sum, (size_t)cell_scan_tiles(c_off)));
+    CK(dalloc(&ctx->m_tmp, (size_t)ctx->P));
+    CK(dalloc(&ctx->m3_tmp, (size_t)ctx->P * 3));
+    CK(dalloc(&ctx->d_pblk, ctx->pblk.size()));
+    CK(dalloc(&ctx->d_nblk, ctx->nblk.size()));
+    CK(dalloc(&ctx->d_sblk, ctx->sblk.size()));
+    CK(dalloc(&ctx->d_cell_sys, cell_sys.size()));
     rbsog_status es = enter(ctx);
     if (es != RBSOG_OK) return es;
-    CK(cudaMemsetAsync(ctx->cb.count, 0, sizeof(int32_t) * ncell, ctx->st));
-    CK(cudaMemsetAsync(ctx->cursor, 0, sizeof(int64_t), ctx->st));
-    CK(cudaMemsetAsync(ctx->step_ctr, 0, sizeof(int64_t), ctx->st));
+    CK(cudaMemcpyAsync(ctx->d_pblk, ctx->pblk.data(), sizeof(int2) * ctx->pblk.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->d_nblk, ctx->nblk.data(), sizeof(int2) * ctx->nblk.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->d_sblk, ctx->sblk.data(), sizeof(int2) * ctx->sblk.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->d_cell_sys, cell_sys.data(), sizeof(int32_t) * cell_sys.size(), cudaMemcpyHostToDevice,
+                       ctx->st));
+    CK(cudaMemsetAsync(ctx->cb.count, 0, sizeof(int32_t) * c_off, ctx->st));
+    CK(cudaMemsetAsync(ctx->cursor, 0, sizeof(int64_t) * ns, ctx->st));
+    CK(cudaMemsetAsync(ctx->step_ctr, 0, sizeof(int64_t) * ns, ctx->st));
     CK(cudaMemsetAsync(ctx->err_flag, 0, sizeof(int32_t), ctx->st));
-    ctx->host_cursor = 0;
+    es = upload_desc(ctx);
+    if (es != RBSOG_OK) return es;
+    std::fill(ctx->host_cursor.begin(), ctx->host_cursor.end(), 0);
+    std::fill(ctx->force_valid.begin(), ctx->force_valid.end(), 0);
 
-    SamplerDev sp{};
-    sp.M = p.M;
-    for (int l = 0; l <= p.M; ++l) {
-        sp.omega[l] = w[l];
-        sp.s[l] = s[l];
+    for (int s = 0; s < ns; ++s) {
+        SamplerDev sp{};
+        sp.M = p[s].M;
+        for (int l = 0; l <= p[s].M; ++l) {
+            sp.omega[l] = w[l];
+            sp.s[l] = sv[l];
+        }
+        for (int d = 0; d < 3; ++d) sp.L[d] = p[s].L[d];
+        sp.seed = p[s].seed;
+        sp.n_chains = ctx->n_chains[s];
+        sp.chain_len = ctx->chain_len[s];
+        CK(launch_mh_sampler(sp, ctx->kseq + ctx->desc[s].k_off, ctx->err_flag, ctx->st, prof_of(ctx)));
     }
-    for (int d = 0; d < 3; ++d) sp.L[d] = p.L[d];
-    sp.seed = p.seed;
-    sp.n_chains = ctx->n_chains;
-    sp.chain_len = ctx->chain_len;
-    CK(launch_mh_sampler(sp, ctx->kseq, ctx->err_flag, ctx->st, prof_of(ctx)));
     rbsog_status fs = check_flags(ctx);
     if (fs != RBSOG_OK) return fs;
     ctx->have_params = true;
-    ctx->force_valid = false;
     return leave(ctx);
 }
+
+rbsog_status rbsog_set_params(rbsog_ctx *ctx, const rbsog_params *p) { return rbsog_batch_set_params(ctx, p); }
 
 rbsog_status rbsog_get_info(const rbsog_ctx *ctx, rbsog_info *info, double *omega, double *s) {
     if (!ctx || !info) return RBSOG_EINVAL;
     if (!ctx->have_params) return RBSOG_ESTATE;
     info->sigma = ctx->sigma;
     info->omega0 = ctx->omega0;
-    info->S = ctx->S;
-    info->M = ctx->p.M;
-    for (int d = 0; d < 3; ++d) info->ncell[d] = ctx->box.nc[d];
-    info->n_chains = ctx->n_chains;
-    info->chain_len = ctx->chain_len;
-    if (omega) std::memcpy(omega, ctx->omega.data(), sizeof(double) * (ctx->p.M + 1));
-    if (s) std::memcpy(s, ctx->s.data(), sizeof(double) * (ctx->p.M + 1));
+    info->S = ctx->S[0];
+    info->M = ctx->p[0].M;
+    for (int d = 0; d < 3; ++d) info->ncell[d] = ctx->desc[0].box.nc[d];
+    info->n_chains = ctx->n_chains[0];
+    info->chain_len = ctx->chain_len[0];
+    if (omega) std::memcpy(omega, ctx->omega.data(), sizeof(double) * (ctx->p[0].M + 1));
+    if (s) std::memcpy(s, ctx->s.data(), sizeof(double) * (ctx->p[0].M + 1));
     return RBSOG_OK;
 }
 
-rbsog_status rbsog_set_state(rbsog_ctx *ctx, const double *q, const double *x, const double *v) {
+rbsog_status rbsog_batch_set_state(rbsog_batch *ctx, int32_t sys, const double *q, const double *x,
+                                   const double *v) {
     if (!ctx || !q || !x) return RBSOG_EINVAL;
     if (!ctx->have_params) return fail(ctx, RBSOG_ESTATE, "set_params must come first");
-    rbsog_status es = enter(ctx);
+    rbsog_status es = check_sys(ctx, sys);
     if (es != RBSOG_OK) return es;
-    std::vector<double> hq((size_t)ctx->n);
-    CK(cudaMemcpyAsync(hq.data(), q, sizeof(double) * ctx->n, cudaMemcpyDefault, ctx->st));
+    es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    const int64_t n = ctx->n_per[sys], off = ctx->p_off[sys];
+    std::vector<double> hq((size_t)n);
+    CK(cudaMemcpyAsync(hq.data(), q, sizeof(double) * n, cudaMemcpyDefault, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     double sq = 0.0, sa = 0.0, s2 = 0.0;
     for (double qi : hq) {
@@ -606,54 +726,66 @@ rbsog_status rbsog_set_state(rbsog_ctx *ctx, const double *q, const double *x, c
         s2 += qi * qi;
     }
     if (std::fabs(sq) > 1e-12 * sa) return fail(ctx, RBSOG_EINVAL, "charges are not neutral (sum %.3e)", sq);
-    ctx->sum_q2 = s2;
-    double wsum = 0.0;
-    for (int l = 0; l <= ctx->p.M; ++l) wsum += ctx->omega[l];
-    ctx->U_self = 0.5 * wsum * s2 * ctx->p.coulomb_prefactor;
-
+    ctx->sum_q2[sys] = s2;
+    ctx->desc[sys].U_self = self_energy(ctx, sys);
+    es = upload_desc(ctx);
+    if (es != RBSOG_OK) return es;
     double *qd = nullptr;
-    CK(cudaMallocAsync((void **)&qd, sizeof(double) * ctx->n, ctx->st));
-    CK(cudaMemcpyAsync(qd, q, sizeof(double) * ctx->n, cudaMemcpyDefault, ctx->st));
-    CK(cudaMemcpyAsync(ctx->staging, x, sizeof(double) * 3 * ctx->n, cudaMemcpyDefault, ctx->st));
-    CK(launch_pack(ctx->n, ctx->staging, qd, ctx->posq, 1, ctx->p.L, ctx->st));
+    CK(cudaMallocAsync((void **)&qd, sizeof(double) * n, ctx->st));
+    CK(cudaMemcpyAsync(qd, q, sizeof(double) * n, cudaMemcpyDefault, ctx->st));
+    CK(cudaMemcpyAsync(ctx->staging, x, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
+    CK(launch_pack(n, ctx->staging, qd, ctx->posq + off, 1, ctx->p[sys].L, ctx->st));
     if (v) {
-        CK(cudaMemcpyAsync(ctx->staging, v, sizeof(double) * 3 * ctx->n, cudaMemcpyDefault, ctx->st));
-        CK(launch_pack(ctx->n, ctx->staging, nullptr, ctx->vel, 0, ctx->p.L, ctx->st));
+        CK(cudaMemcpyAsync(ctx->staging, v, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
+        CK(launch_pack(n, ctx->staging, nullptr, ctx->vel + off, 0, ctx->p[sys].L, ctx->st));
     } else {
-        CK(cudaMemsetAsync(ctx->vel, 0, sizeof(double4_32a) * ctx->n, ctx->st));
+        CK(cudaMemsetAsync(ctx->vel + off, 0, sizeof(double4_32a) * n, ctx->st));
     }
     CK(cudaFreeAsync(qd, ctx->st));
-    CK(cudaMemsetAsync(ctx->step_ctr, 0, sizeof(int64_t), ctx->st));
+    CK(cudaMemsetAsync(ctx->step_ctr + sys, 0, sizeof(int64_t), ctx->st));
     drop_graph(ctx);
-    ctx->have_state = true;
-    ctx->force_valid = false;
+    ctx->have_state[sys] = 1;
+    ctx->force_valid[sys] = 0;
     return leave(ctx);
 }
 
-rbsog_status rbsog_compute_forces(rbsog_ctx *ctx, const int32_t *m_kset, double *f_out,
-                                  rbsog_energies *e_out) {
+rbsog_status rbsog_set_state(rbsog_ctx *ctx, const double *q, const double *x, const double *v) {
+    return rbsog_batch_set_state(ctx, 0, q, x, v);
+}
+
+static bool all_state(const rbsog_ctx *ctx) {
+    for (char c : ctx->have_state)
+        if (!c) return false;
+    return true;
+}
+
+rbsog_status rbsog_compute_forces(rbsog_ctx *ctx, const int32_t *m_kset, double *f_out, rbsog_energies *e_out) {
     if (!ctx) return RBSOG_EINVAL;
-    if (!ctx->have_params || !ctx->have_state) return fail(ctx, RBSOG_ESTATE, "params and state required");
-    if (!m_kset && ctx->host_cursor >= ctx->n_sets)
-        return fail(ctx, RBSOG_EINVAL, "pre-sampled k-sequence exhausted");
+    if (!ctx->have_params || !all_state(ctx)) return fail(ctx, RBSOG_ESTATE, "params and state required");
+    if (m_kset && ctx->n_sys != 1) return fail(ctx, RBSOG_EINVAL, "an explicit k-set needs a single system");
+    if (!m_kset)
+        for (int s = 0; s < ctx->n_sys; ++s)
+            if (ctx->host_cursor[s] >= ctx->desc[s].n_sets)
+                return fail(ctx, RBSOG_EINVAL, "pre-sampled k-sequence exhausted");
     rbsog_status es = enter(ctx);
     if (es != RBSOG_OK) return es;
     const int4 *mex = nullptr;
     if (m_kset) {
-        CK(cudaMemcpyAsync(ctx->m3_tmp, m_kset, sizeof(int32_t) * 3 * ctx->p.P, cudaMemcpyDefault, ctx->st));
-        CK(launch_m_to_int4(ctx->p.P, ctx->m3_tmp, ctx->m_tmp, ctx->st));
+        CK(cudaMemcpyAsync(ctx->m3_tmp, m_kset, sizeof(int32_t) * 3 * ctx->P, cudaMemcpyDefault, ctx->st));
+        CK(launch_m_to_int4(ctx->P, ctx->m3_tmp, ctx->m_tmp, ctx->st));
         mex = ctx->m_tmp;
     }
-    es = enqueue_forces(ctx, mex, nullptr);
+    const BatchView bv = view(ctx, mex);
+    es = enqueue_forces(ctx, bv, nullptr);
     if (es != RBSOG_OK) return es;
-    const MdArgs ma = md_args(ctx);
-    CK(launch_finalize(ma, ctx->epart, ctx->rho, ctx->kpart, 0, ctx->energy, ctx->cursor,
-                       m_kset ? 0 : 1, nullptr, ctx->st, prof_of(ctx)));
-    if (!m_kset) ctx->host_cursor += 1;
-    ctx->force_valid = true;
+    CK(launch_finalize(bv, ctx->epart, ctx->rho, ctx->kpart, 0, ctx->energy, m_kset ? 0 : 1, ctx->st,
+                       prof_of(ctx)));
+    if (!m_kset)
+        for (auto &c : ctx->host_cursor) c += 1;
+    std::fill(ctx->force_valid.begin(), ctx->force_valid.end(), 1);
     if (f_out) {
-        CK(launch_unpack(ctx->n, ctx->force, ctx->staging, ctx->st));
-        CK(cudaMemcpyAsync(f_out, ctx->staging, sizeof(double) * 3 * ctx->n, cudaMemcpyDefault, ctx->st));
+        CK(launch_unpack(ctx->n_per[0], ctx->force, ctx->staging, ctx->st));
+        CK(cudaMemcpyAsync(f_out, ctx->staging, sizeof(double) * 3 * ctx->n_per[0], cudaMemcpyDefault, ctx->st));
     }
     if (e_out || f_out) {
         es = check_flags(ctx);
@@ -672,26 +804,23 @@ rbsog_status rbsog_compute_forces(rbsog_ctx *ctx, const int32_t *m_kset, double 
     return leave(ctx);
 }
 
-rbsog_status rbsog_step(rbsog_ctx *ctx, int64_t nsteps) {
+rbsog_status rbsog_batch_step(rbsog_batch *ctx, int64_t nsteps) {
     if (!ctx) return RBSOG_EINVAL;
     if (nsteps < 0) return fail(ctx, RBSOG_EINVAL, "nsteps must be >= 0");
-    if (!ctx->have_params || !ctx->have_state) return fail(ctx, RBSOG_ESTATE, "params and state required");
-    const int64_t need = nsteps + (ctx->force_valid ? 0 : 1);
-    if (ctx->host_cursor + need > ctx->n_sets)
-        return fail(ctx, RBSOG_EINVAL, "pre-sampled k-sequence too short (%lld sets left, %lld needed)",
-                    (long long)(ctx->n_sets - ctx->host_cursor), (long long)need);
-    if (nsteps == 0 && ctx->force_valid) return RBSOG_OK;
+    if (!ctx->have_params || !all_state(ctx)) return fail(ctx, RBSOG_ESTATE, "params and state required");
+    bool all_valid = true;
+    for (int s = 0; s < ctx->n_sys; ++s) {
+        const int64_t need = nsteps + (ctx->force_valid[s] ? 0 : 1);
+        all_valid = all_valid && ctx->force_valid[s];
+        if (ctx->host_cursor[s] + need > ctx->desc[s].n_sets)
+            return fail(ctx, RBSOG_EINVAL, "system %d: pre-sampled k-sequence too short (%lld sets left, %lld needed)",
+                        s, (long long)(ctx->desc[s].n_sets - ctx->host_cursor[s]), (long long)need);
+    }
+    if (nsteps == 0 && all_valid) return RBSOG_OK;
     rbsog_status es = enter(ctx);
     if (es != RBSOG_OK) return es;
-    if (!ctx->force_valid) {
-        es = enqueue_forces(ctx, nullptr, nullptr);
-        if (es != RBSOG_OK) return es;
-        const MdArgs ma = md_args(ctx);
-        CK(launch_finalize(ma, ctx->epart, ctx->rho, ctx->kpart, 0, ctx->energy, ctx->cursor, 1,
-                           nullptr, ctx->st, prof_of(ctx)));
-        ctx->host_cursor += 1;
-        ctx->force_valid = true;
-    }
+    es = initial_forces(ctx);
+    if (es != RBSOG_OK) return es;
     if (ctx->profiling) {
         for (int64_t t = 0; t < nsteps; ++t) {
             es = enqueue_step(ctx);
@@ -714,33 +843,31 @@ rbsog_status rbsog_step(rbsog_ctx *ctx, int64_t nsteps) {
         }
         for (int64_t t = 0; t < nsteps; ++t) CK(cudaGraphLaunch(ctx->graph, ctx->st));
     }
-    ctx->host_cursor += nsteps;
+    for (auto &c : ctx->host_cursor) c += nsteps;
     return leave(ctx);
 }
 
-rbsog_status rbsog_get_state(rbsog_ctx *ctx, double *x, double *v, double *f, int64_t *step) {
+rbsog_status rbsog_step(rbsog_ctx *ctx, int64_t nsteps) { return rbsog_batch_step(ctx, nsteps); }
+
+rbsog_status rbsog_batch_get_state(rbsog_batch *ctx, int32_t sys, double *x, double *v, double *f, int64_t *step) {
     if (!ctx) return RBSOG_EINVAL;
-    if (!ctx->have_state) return fail(ctx, RBSOG_ESTATE, "no state");
-    rbsog_status es = enter(ctx);
+    rbsog_status es = check_sys(ctx, sys);
     if (es != RBSOG_OK) return es;
-    const size_t bytes = sizeof(double) * 3 * ctx->n;
-    if (x) {
-        CK(launch_unpack(ctx->n, ctx->posq, ctx->staging, ctx->st));
-        CK(cudaMemcpyAsync(x, ctx->staging, bytes, cudaMemcpyDefault, ctx->st));
-        CK(cudaStreamSynchronize(ctx->st));
-    }
-    if (v) {
-        CK(launch_unpack(ctx->n, ctx->vel, ctx->staging, ctx->st));
-        CK(cudaMemcpyAsync(v, ctx->staging, bytes, cudaMemcpyDefault, ctx->st));
-        CK(cudaStreamSynchronize(ctx->st));
-    }
-    if (f) {
-        CK(launch_unpack(ctx->n, ctx->force, ctx->staging, ctx->st));
-        CK(cudaMemcpyAsync(f, ctx->staging, bytes, cudaMemcpyDefault, ctx->st));
+    if (!ctx->have_state[sys]) return fail(ctx, RBSOG_ESTATE, "no state");
+    es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    const int64_t n = ctx->n_per[sys], off = ctx->p_off[sys];
+    const size_t bytes = sizeof(double) * 3 * n;
+    const double4_32a *src[3] = {ctx->posq + off, ctx->vel + off, ctx->force + off};
+    double *dst[3] = {x, v, f};
+    for (int k = 0; k < 3; ++k) {
+        if (!dst[k]) continue;
+        CK(launch_unpack(n, src[k], ctx->staging, ctx->st));
+        CK(cudaMemcpyAsync(dst[k], ctx->staging, bytes, cudaMemcpyDefault, ctx->st));
         CK(cudaStreamSynchronize(ctx->st));
     }
     if (step) {
-        CK(cudaMemcpyAsync(ctx->h_i64, ctx->step_ctr, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(ctx->h_i64, ctx->step_ctr + sys, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaStreamSynchronize(ctx->st));
         *step = *ctx->h_i64;
     }
@@ -749,38 +876,52 @@ rbsog_status rbsog_get_state(rbsog_ctx *ctx, double *x, double *v, double *f, in
     return leave(ctx);
 }
 
+rbsog_status rbsog_get_state(rbsog_ctx *ctx, double *x, double *v, double *f, int64_t *step) {
+    return rbsog_batch_get_state(ctx, 0, x, v, f, step);
+}
+
 rbsog_status rbsog_get_cursor(const rbsog_ctx *ctx, int64_t *kset_cursor) {
     if (!ctx || !kset_cursor) return RBSOG_EINVAL;
-    *kset_cursor = ctx->host_cursor;
+    *kset_cursor = ctx->host_cursor[0];
     return RBSOG_OK;
 }
 
-rbsog_status rbsog_restore(rbsog_ctx *ctx, const double *f, int64_t kset_cursor, int64_t step) {
+rbsog_status rbsog_batch_restore(rbsog_batch *ctx, int32_t sys, const double *f, int64_t kset_cursor, int64_t step) {
     if (!ctx || !f) return RBSOG_EINVAL;
-    if (!ctx->have_state) return fail(ctx, RBSOG_ESTATE, "set_state must come first");
-    if (kset_cursor < 0 || kset_cursor > ctx->n_sets || step < 0)
-        return fail(ctx, RBSOG_EINVAL, "cursor %lld outside [0, %lld]", (long long)kset_cursor,
-                    (long long)ctx->n_sets);
-    rbsog_status es = enter(ctx);
+    rbsog_status es = check_sys(ctx, sys);
     if (es != RBSOG_OK) return es;
-    CK(cudaMemcpyAsync(ctx->staging, f, sizeof(double) * 3 * ctx->n, cudaMemcpyDefault, ctx->st));
-    CK(launch_pack(ctx->n, ctx->staging, nullptr, ctx->force, 0, ctx->p.L, ctx->st));
+    if (!ctx->have_state[sys]) return fail(ctx, RBSOG_ESTATE, "set_state must come first");
+    if (kset_cursor < 0 || kset_cursor > ctx->desc[sys].n_sets || step < 0)
+        return fail(ctx, RBSOG_EINVAL, "cursor %lld outside [0, %lld]", (long long)kset_cursor,
+                    (long long)ctx->desc[sys].n_sets);
+    es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    const int64_t n = ctx->n_per[sys], off = ctx->p_off[sys];
+    CK(cudaMemcpyAsync(ctx->staging, f, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
+    CK(launch_pack(n, ctx->staging, nullptr, ctx->force + off, 0, ctx->p[sys].L, ctx->st));
     *ctx->h_i64 = kset_cursor;
-    CK(cudaMemcpyAsync(ctx->cursor, ctx->h_i64, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->cursor + sys, ctx->h_i64, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     *ctx->h_i64 = step;
-    CK(cudaMemcpyAsync(ctx->step_ctr, ctx->h_i64, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->step_ctr + sys, ctx->h_i64, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    ctx->host_cursor = kset_cursor;
-    ctx->force_valid = true;
+    ctx->host_cursor[sys] = kset_cursor;
+    ctx->force_valid[sys] = 1;
     return leave(ctx);
 }
 
-rbsog_status rbsog_get_energies(rbsog_ctx *ctx, rbsog_energies *e) {
+rbsog_status rbsog_restore(rbsog_ctx *ctx, const double *f, int64_t kset_cursor, int64_t step) {
+    return rbsog_batch_restore(ctx, 0, f, kset_cursor, step);
+}
+
+rbsog_status rbsog_batch_get_energies(rbsog_batch *ctx, int32_t sys, rbsog_energies *e) {
     if (!ctx || !e) return RBSOG_EINVAL;
-    rbsog_status es = enter(ctx);
+    rbsog_status es = check_sys(ctx, sys);
     if (es != RBSOG_OK) return es;
-    CK(cudaMemcpyAsync(ctx->h_energy, ctx->energy, sizeof(double) * kNumEnergy, cudaMemcpyDeviceToHost, ctx->st));
+    es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    CK(cudaMemcpyAsync(ctx->h_energy, ctx->energy + (int64_t)sys * kNumEnergy, sizeof(double) * kNumEnergy,
+                       cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     e->U_near = ctx->h_energy[0];
     e->U_far = ctx->h_energy[1];
@@ -791,15 +932,20 @@ rbsog_status rbsog_get_energies(rbsog_ctx *ctx, rbsog_energies *e) {
     return leave(ctx);
 }
 
-rbsog_status rbsog_get_kseq(rbsog_ctx *ctx, int64_t set0, int64_t nsets, int32_t *m_out) {
+rbsog_status rbsog_get_energies(rbsog_ctx *ctx, rbsog_energies *e) { return rbsog_batch_get_energies(ctx, 0, e); }
+
+rbsog_status rbsog_batch_get_kseq(rbsog_batch *ctx, int32_t sys, int64_t set0, int64_t nsets, int32_t *m_out) {
     if (!ctx || !m_out || set0 < 0 || nsets < 0) return RBSOG_EINVAL;
     if (!ctx->have_params) return fail(ctx, RBSOG_ESTATE, "no params");
-    if (set0 + nsets > ctx->n_sets) return fail(ctx, RBSOG_EINVAL, "k-set range beyond the sequence");
-    const int64_t cnt = nsets * ctx->p.P;
-    std::vector<int4> tmp((size_t)cnt);
-    rbsog_status es = enter(ctx);
+    rbsog_status es = check_sys(ctx, sys);
     if (es != RBSOG_OK) return es;
-    CK(cudaMemcpyAsync(tmp.data(), ctx->kseq + set0 * ctx->p.P, sizeof(int4) * cnt, cudaMemcpyDeviceToHost, ctx->st));
+    if (set0 + nsets > ctx->desc[sys].n_sets) return fail(ctx, RBSOG_EINVAL, "k-set range beyond the sequence");
+    const int64_t cnt = nsets * ctx->P;
+    std::vector<int4> tmp((size_t)cnt);
+    es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    CK(cudaMemcpyAsync(tmp.data(), ctx->kseq + ctx->desc[sys].k_off + set0 * ctx->P, sizeof(int4) * cnt,
+                       cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     std::vector<int32_t> m3((size_t)cnt * 3);
     for (int64_t i = 0; i < cnt; ++i) {
@@ -812,9 +958,14 @@ rbsog_status rbsog_get_kseq(rbsog_ctx *ctx, int64_t set0, int64_t nsets, int32_t
     return leave(ctx);
 }
 
+rbsog_status rbsog_get_kseq(rbsog_ctx *ctx, int64_t set0, int64_t nsets, int32_t *m_out) {
+    return rbsog_batch_get_kseq(ctx, 0, set0, nsets, m_out);
+}
+
 rbsog_status rbsog_rho(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *rho_out) {
     if (!ctx || !m || !rho_out || P < 1) return RBSOG_EINVAL;
-    if (!ctx->have_params || !ctx->have_state) return fail(ctx, RBSOG_ESTATE, "params and state required");
+    if (ctx->n_sys != 1) return fail(ctx, RBSOG_EINVAL, "rbsog_rho needs a single system");
+    if (!ctx->have_params || !all_state(ctx)) return fail(ctx, RBSOG_ESTATE, "params and state required");
     rbsog_status es = enter(ctx);
     if (es != RBSOG_OK) return es;
     int32_t *m3 = nullptr;
@@ -823,16 +974,15 @@ rbsog_status rbsog_rho(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *rho_
     void *kt = nullptr;
     CK(cudaMallocAsync((void **)&m3, sizeof(int32_t) * 3 * P, ctx->st));
     CK(cudaMallocAsync((void **)&m4, sizeof(int4) * P, ctx->st));
-    CK(cudaMallocAsync((void **)&part, sizeof(double2) * (size_t)P * ctx->n_ptiles, ctx->st));
+    CK(cudaMallocAsync((void **)&part, sizeof(double2) * (size_t)P * ctx->desc[0].n_ptiles, ctx->st));
     CK(cudaMallocAsync((void **)&rho, sizeof(double2) * P, ctx->st));
-    CK(cudaMallocAsync(&kt, ktab_bytes(ctx->p.precision, P), ctx->st));
+    CK(cudaMallocAsync(&kt, ktab_bytes(ctx->precision, P), ctx->st));
     CK(cudaMemcpyAsync(m3, m, sizeof(int32_t) * 3 * P, cudaMemcpyDefault, ctx->st));
     CK(launch_m_to_int4(P, m3, m4, ctx->st));
-    CK(launch_build_cells(ctx->n, ctx->posq, ctx->box, ctx->cb, ctx->p.precision, ctx->sp64, ctx->sp32,
-                          ctx->err_flag, ctx->st, prof_of(ctx)));
-    const FarArgs fa = far_args(ctx, m4, P);
-    CK(launch_rho_sweep(ctx->p.precision, fa, ctx->sp64, ctx->sp32, part, ctx->st, prof_of(ctx)));
-    CK(launch_rho_combine(ctx->p.precision, fa, part, rho, kt, ctx->st, prof_of(ctx)));
+    const BatchView bv = view(ctx, m4, P);
+    CK(launch_build_cells(bv, ctx->posq, ctx->cb, ctx->precision, ctx->sp64, ctx->sp32, ctx->st, prof_of(ctx)));
+    CK(launch_rho_sweep(ctx->precision, bv, ctx->sp64, ctx->sp32, part, ctx->st, prof_of(ctx)));
+    CK(launch_rho_combine(ctx->precision, bv, part, rho, kt, ctx->st, prof_of(ctx)));
     CK(cudaMemcpyAsync(rho_out, rho, sizeof(double2) * P, cudaMemcpyDefault, ctx->st));
     CK(cudaFreeAsync(m3, ctx->st));
     CK(cudaFreeAsync(m4, ctx->st));
@@ -845,21 +995,23 @@ rbsog_status rbsog_rho(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *rho_
 
 rbsog_status rbsog_get_cells(rbsog_ctx *ctx, int32_t *cell_start, int32_t *perm, int32_t *nbr) {
     if (!ctx) return RBSOG_EINVAL;
-    if (!ctx->have_params || !ctx->have_state) return fail(ctx, RBSOG_ESTATE, "params and state required");
+    if (ctx->n_sys != 1) return fail(ctx, RBSOG_EINVAL, "rbsog_get_cells needs a single system");
+    if (!ctx->have_params || !all_state(ctx)) return fail(ctx, RBSOG_ESTATE, "params and state required");
     rbsog_status es = enter(ctx);
     if (es != RBSOG_OK) return es;
     const Prof *pf = prof_of(ctx);
-    CK(launch_build_cells(ctx->n, ctx->posq, ctx->box, ctx->cb, ctx->p.precision, ctx->sp64, ctx->sp32,
-                          ctx->err_flag, ctx->st, pf));
+    const BatchView bv = view(ctx);
+    CK(launch_build_cells(bv, ctx->posq, ctx->cb, ctx->precision, ctx->sp64, ctx->sp32, ctx->st, pf));
     if (nbr) {
-        CK(launch_near(ctx->p.precision, ctx->box, ctx->nsog, ctx->group, ctx->near_cap, ctx->cb.start, ctx->sp64,
-                       ctx->sp32, ctx->fnear, ctx->epart, ctx->nbr_sorted, ctx->st, pf));
-        CK(launch_unsort_i32(ctx->n, ctx->cb.perm, ctx->nbr_sorted, ctx->i32_tmp, ctx->st));
-        CK(cudaMemcpyAsync(nbr, ctx->i32_tmp, sizeof(int32_t) * ctx->n, cudaMemcpyDefault, ctx->st));
+        CK(launch_near(ctx->precision, bv, ctx->nsog, ctx->cb.start, ctx->sp64, ctx->sp32, ctx->fnear, ctx->epart,
+                       ctx->nbr_sorted, ctx->st, pf));
+        CK(launch_unsort_i32(ctx->n_total, 0, ctx->cb.perm, ctx->nbr_sorted, ctx->i32_tmp, ctx->st));
+        CK(cudaMemcpyAsync(nbr, ctx->i32_tmp, sizeof(int32_t) * ctx->n_total, cudaMemcpyDefault, ctx->st));
     }
     if (cell_start)
-        CK(cudaMemcpyAsync(cell_start, ctx->cb.start, sizeof(int32_t) * (ctx->box.ncell + 1), cudaMemcpyDefault, ctx->st));
-    if (perm) CK(cudaMemcpyAsync(perm, ctx->cb.perm, sizeof(int32_t) * ctx->n, cudaMemcpyDefault, ctx->st));
+        CK(cudaMemcpyAsync(cell_start, ctx->cb.start, sizeof(int32_t) * (ctx->ncell_total + 1), cudaMemcpyDefault,
+                           ctx->st));
+    if (perm) CK(cudaMemcpyAsync(perm, ctx->cb.perm, sizeof(int32_t) * ctx->n_total, cudaMemcpyDefault, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return leave(ctx);
 }
@@ -878,8 +1030,8 @@ rbsog_status rbsog_set_profiling(rbsog_ctx *ctx, int on) {
     return RBSOG_OK;
 }
 
-rbsog_status rbsog_get_profile(rbsog_ctx *ctx, int32_t cap, char (*names)[32], int64_t *launches,
-                               double *ms, int32_t *count) {
+rbsog_status rbsog_get_profile(rbsog_ctx *ctx, int32_t cap, char (*names)[32], int64_t *launches, double *ms,
+                               int32_t *count) {
     if (!ctx || !count) return RBSOG_EINVAL;
     CK(cudaSetDevice(ctx->device));
     CK(cudaStreamSynchronize(ctx->st));
@@ -953,6 +1105,12 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->err_flag);
     dfree(&ctx->m_tmp);
     dfree(&ctx->m3_tmp);
+    dfree(&ctx->d_desc);
+    dfree(&ctx->d_pblk);
+    dfree(&ctx->d_nblk);
+    dfree(&ctx->d_sblk);
+    dfree(&ctx->d_cell_sys);
+    dfree(&ctx->d_mask);
     if (ctx->h_energy) cudaFreeHost(ctx->h_energy);
     if (ctx->h_err) cudaFreeHost(ctx->h_err);
     if (ctx->h_i64) cudaFreeHost(ctx->h_i64);

@@ -81,9 +81,56 @@ struct ProfScope {
 cudaError_t launch_mh_sampler(const SamplerDev &sp, int4 *kseq, int32_t *err_flag,
                               cudaStream_t st, const Prof *prof);
 
+// ---- batch layout -------------------------------------------------------------
+// Every kernel works on a batch of independent systems laid out back to back
+// (particles, cells, k-sequences, partial sums).  A single system is a batch
+// of one.  Each system's work is decomposed exactly as it would be alone, so
+// its results do not depend on the other systems in the batch.
+struct SysDesc {
+    BoxDev box;
+    int64_t p_off, n;          // first particle (global index), particle count
+    int64_t c_off;             // first cell (global index)
+    int32_t group, nseg_x;     // near field: home cells per block, segments per x-row
+    int32_t near_cap;          // near field: staged particles per shared-memory chunk
+    int32_t e_off, n_epart;    // near-energy partials (one per warp)
+    int32_t tile_p, n_ptiles;  // rho sweep: particles per tile, tiles
+    int64_t rp_off;            // first rho partial (double2 units)
+    int64_t k_off;             // first int4 of this system's k-sequence
+    int64_t n_sets;            // k-sets sampled
+    int32_t kp_off, n_kpart;   // kinetic partials (one per particle block)
+    double coef;               // -lB pi^{3/2} S / (P V): multiplies q_i k Im(...)
+    double half_coef_U;        // lB pi^{3/2} S / (2 P V)
+    double U_self;
+    double dt, inv_mass, mass, T0, tau;
+};
+
+// Work tables map a launch's blocks to (system, local block).
+struct BatchView {
+    const SysDesc *sys;        // [n_sys], device
+    int32_t n_sys;
+    int32_t P;                 // frequencies per step, the same for every system
+    int64_t n_total, ncell_total;
+    const int2 *pblk;          // blocks of kParticleBlock particles
+    int32_t n_pblk;
+    const int2 *nblk;          // near-field blocks
+    int32_t n_nblk;
+    const int2 *sblk;          // rho-sweep particle tiles
+    int32_t n_sblk;
+    const int32_t *cell_sys;   // [ncell_total] system of each cell
+    int64_t *cursor;           // [n_sys] k-sets consumed
+    int64_t *step;             // [n_sys] completed steps
+    const int4 *kseq;          // concatenated k-sequences
+    const int4 *m_explicit;    // explicit k-set for a batch of one, or null
+    const int32_t *force_mask; // [n_sys]: only systems with a non-zero entry take the new
+                               // forces, energies and k-set (null: all systems)
+    int32_t max_cap;           // largest near staging chunk of the batch
+    int32_t max_tile_p;        // largest rho-sweep tile of the batch
+};
+constexpr int kParticleBlock = 256;
+
 // ---- cell list (k_cells.cu) ---------------------------------------------------
 struct CellBuffers {
-    int32_t *cell_of;     // [n]   cell id of each particle (caller order)
+    int32_t *cell_of;     // [n]   cell id of each particle (global)
     int32_t *slot;        // [n]   arrival slot inside its cell (unordered)
     int32_t *count;       // [ncell] zeroed after every scan
     int32_t *start;       // [ncell + 1]
@@ -91,83 +138,58 @@ struct CellBuffers {
     int32_t *perm;        // [n]   cell order, increasing index inside a cell
     int32_t *tile_sum;    // [cell_scan_tiles(ncell)] scan tile totals
 };
-int cell_scan_tiles(int ncell);
+int cell_scan_tiles(int64_t ncell);
 // precision 0: gather FP64 (x, y, z, q) into sp64; 1: 32-bit fixed point
 // positions and FP32 charge into sp32.
-cudaError_t launch_build_cells(int64_t n, const double4_32a *posq, const BoxDev &box,
-                               const CellBuffers &cb, int precision, double4_32a *sp64, uint4 *sp32,
-                               int32_t *err_flag, cudaStream_t st, const Prof *prof);
+cudaError_t launch_build_cells(const BatchView &bv, const double4_32a *posq, const CellBuffers &cb,
+                               int precision, double4_32a *sp64, uint4 *sp32, cudaStream_t st,
+                               const Prof *prof);
 
 // ---- near field (k_near.cu) ---------------------------------------------------
-// Forces (sorted order) into fnear; per-block energy partials (U_near, U_wca)
-// into epart[nblocks]; neighbour counts (sorted order) into nbr when non-null.
-int near_num_blocks(const BoxDev &box, int group);
-int near_num_partials(const BoxDev &box, int group);   // energy partials written (one per warp)
-// cap: staged particles per shared-memory chunk (larger regions are chunked).
-cudaError_t launch_near(int precision, const BoxDev &box, const NearSog &sog, int group, int cap,
-                        const int32_t *start, const double4_32a *sp64, const uint4 *sp32,
-                        double4_32a *fnear, double2 *epart, int32_t *nbr, cudaStream_t st,
-                        const Prof *prof);
+// Forces (cell order) into fnear; energy partials (U_near, U_wca), one per
+// warp, into epart; neighbour counts (cell order) into nbr when non-null.
+void near_layout(const BoxDev &box, int64_t n, int precision, int &group, int &nseg_x, int &cap,
+                 int &nblocks, int &npartials);
+cudaError_t launch_near(int precision, const BatchView &bv, const NearSog &sog, const int32_t *start,
+                        const double4_32a *sp64, const uint4 *sp32, double4_32a *fnear, double2 *epart,
+                        int32_t *nbr, cudaStream_t st, const Prof *prof);
 
 // ---- far field (k_far.cu) -----------------------------------------------------
-struct FarArgs {
-    int64_t n;
-    int32_t P;
-    double L[3];
-    double coef;               // -lB * pi^{3/2} S / (P V): multiplies q_i k Im(...)
-    const int4 *kseq;          // pre-sampled sequence (or null)
-    const int64_t *cursor;     // device k-set index (or null)
-    const int4 *m_explicit;    // explicit k-set (overrides kseq when non-null)
-    int32_t tile_p;            // particles per sweep block
-    int32_t n_ptiles;
-};
-int far_num_ptiles(int64_t n, int tile_p);
-cudaError_t launch_rho_sweep(int precision, const FarArgs &a, const double4_32a *sp64,
-                             const uint4 *sp32, double2 *rho_part, cudaStream_t st,
-                             const Prof *prof);
-// Combines partials in FP64 (fixed order) into rho[P] and the per-k scatter
-// table (k vector, prescaled Re/Im rho, integer m).
-cudaError_t launch_rho_combine(int precision, const FarArgs &a, const double2 *rho_part,
-                               double2 *rho, void *ktab, cudaStream_t st, const Prof *prof);
+void far_layout(int64_t n, int32_t P, int &tile_p, int &n_ptiles);
+cudaError_t launch_rho_sweep(int precision, const BatchView &bv, const double4_32a *sp64,
+                             const uint4 *sp32, double2 *rho_part, cudaStream_t st, const Prof *prof);
+// Combines partials in FP64 (fixed order) into rho[n_sys * P] and the per-k
+// scatter table (k vector, prescaled Re/Im rho, integer m).
+cudaError_t launch_rho_combine(int precision, const BatchView &bv, const double2 *rho_part, double2 *rho,
+                               void *ktab, cudaStream_t st, const Prof *prof);
 // Total force (near + far) written to force[perm[s]] in caller order.
-cudaError_t launch_far_scatter(int precision, const FarArgs &a, const double4_32a *sp64,
+cudaError_t launch_far_scatter(int precision, const BatchView &bv, const double4_32a *sp64,
                                const uint4 *sp32, const void *ktab, const double4_32a *fnear,
-                               const int32_t *perm, double4_32a *force, int32_t *err_flag,
-                               cudaStream_t st, const Prof *prof);
-size_t ktab_bytes(int precision, int32_t P);
+                               const int32_t *perm, double4_32a *force, int32_t *err_flag, cudaStream_t st,
+                               const Prof *prof);
+size_t ktab_bytes(int precision, int64_t nk);
 
 // ---- integrator and reductions (k_md.cu) --------------------------------------
-struct MdArgs {
-    int64_t n;
-    double dt, inv_mass, mass;
-    double L[3];
-    double T0, tau;            // Berendsen (tau <= 0: off)
-    int32_t n_epart;           // near-energy partials
-    int32_t n_kpart;           // kinetic partials
-    int32_t P;
-    double half_coef_U;        // lB * pi^{3/2} S / (2 P V)
-    double U_self;
-};
-// Device energies: [0] U_near [1] U_far [2] U_self [3] U_wca [4] K [5] T [6] lambda
+// Device energies per system, 8 doubles: [0] U_near [1] U_far [2] U_self
+// [3] U_wca [4] K [5] T [6] lambda
 constexpr int kNumEnergy = 8;
-cudaError_t launch_kick_drift(const MdArgs &a, double4_32a *posq, double4_32a *vel, const double4_32a *force,
-                              cudaStream_t st, const Prof *prof);
-cudaError_t launch_kick(const MdArgs &a, double4_32a *vel, const double4_32a *force, double *kpart,
+cudaError_t launch_kick_drift(const BatchView &bv, double4_32a *posq, double4_32a *vel,
+                              const double4_32a *force, cudaStream_t st, const Prof *prof);
+cudaError_t launch_kick(const BatchView &bv, double4_32a *vel, const double4_32a *force, double *kpart,
                         cudaStream_t st, const Prof *prof);
-// Sum energy partials in fixed order; U_far from rho; T, Berendsen lambda;
-// advance the k-set cursor by `advance`.
-cudaError_t launch_finalize(const MdArgs &a, const double2 *epart, const double2 *rho,
-                            const double *kpart, int with_kinetic, double *energy,
-                            int64_t *cursor, int64_t advance, int64_t *step_counter,
-                            cudaStream_t st, const Prof *prof);
-cudaError_t launch_rescale(const MdArgs &a, double4_32a *vel, const double *energy, cudaStream_t st,
+// One block per system: sums energy partials in fixed order, U_far from rho,
+// T and the Berendsen factor; advances each cursor by `advance` and, with
+// kinetic terms, each step counter by one.
+cudaError_t launch_finalize(const BatchView &bv, const double2 *epart, const double2 *rho, const double *kpart,
+                            int with_kinetic, double *energy, int64_t advance, cudaStream_t st,
+                            const Prof *prof);
+cudaError_t launch_rescale(const BatchView &bv, double4_32a *vel, const double *energy, cudaStream_t st,
                            const Prof *prof);
-int kinetic_num_blocks(int64_t n);
 // Layout conversions between caller [n][3] arrays and the internal double4_32a.
 cudaError_t launch_pack(int64_t n, const double *x3, const double *q, double4_32a *out, int wrap,
                         const double *L, cudaStream_t st);
 cudaError_t launch_unpack(int64_t n, const double4_32a *in, double *x3, cudaStream_t st);
-cudaError_t launch_unsort_i32(int64_t n, const int32_t *perm, const int32_t *sorted,
+cudaError_t launch_unsort_i32(int64_t n, int64_t off, const int32_t *perm, const int32_t *sorted,
                               int32_t *out, cudaStream_t st);
 cudaError_t launch_m_to_int4(int32_t P, const int32_t *m3, int4 *out, cudaStream_t st);
 

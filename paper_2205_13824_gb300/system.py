@@ -89,3 +89,51 @@ class RBSOG:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Independent systems of uneven size advanced together: one CUDA graph
+    launch per step covers every system (see rbsog_batch_* in rbsog.h)."""
+
+    def __init__(self, n_per, params, device: int = 0, stream=None):
+        import torch
+        self.n_per = [int(n) for n in n_per]
+        self.device = int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        self.ctx = B.rbsog_batch_create(self.n_per, self.device, stream)
+        self.params = list(params)
+        B.rbsog_batch_set_params(self.ctx, self.params)
+
+    def set_state(self, sys, q, x, v=None):
+        B.rbsog_batch_set_state(self.ctx, sys, q, x, v)
+
+    def restore(self, sys, f, kset_cursor, step):
+        B.rbsog_batch_restore(self.ctx, sys, f, kset_cursor, step)
+
+    def step(self, nsteps: int):
+        B.rbsog_batch_step(self.ctx, nsteps)
+
+    def state(self, sys):
+        import torch
+        n = self.n_per[sys]
+        dev = f"cuda:{self.device}"
+        x = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        v = torch.empty_like(x)
+        f = torch.empty_like(x)
+        step = B.rbsog_batch_get_state(self.ctx, sys, x, v, f)
+        return x, v, f, step
+
+    def energies(self, sys):
+        return B.rbsog_batch_get_energies(self.ctx, sys)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            B.rbsog_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
