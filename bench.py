@@ -210,6 +210,7 @@ def run_ours(args, rank, world, local, dist):
         torch.cuda.synchronize()
 
     meas = B.rbsog_measure_peaks(local)         # roofline denominators on this GPU
+    tuned = B.rbsog_batch_autotune(g.ctx, 3)    # launch shapes for this workload
     g.step(W)                                   # warm-up (builds the step graph)
     barrier()
     stream = torch.cuda.current_stream()
@@ -285,7 +286,8 @@ def run_ours(args, rank, world, local, dist):
         "config": {"workload": f"1:1 electrolyte N={N} L={L:g} r_c=3 P={P} FP32C", "N": N, "L": L,
                    "P": P, "r_c": 3.0, "sog": "b=1.48783512395703226 M=36 (Table 1 row 3 at r_c=3)",
                    "precision": "fp32c", "l2": "inputs larger than L2 (state ~0.2 GB per replica)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single system"},
+                   "parallelism": f"replicas x{world}" if world > 1 else "single system",
+                   "autotuned": tuned},
         "e2e": {"value": world * N / t_e2e, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * K)),
@@ -356,7 +358,42 @@ def run_extras(args, q, x, v, dev):
         sweep[str(Ps)] = {"value": N / (ms_s / 1e3), "ms_per_step": ms_s}
         g.close()
     out["fp32c_P_sweep"] = sweep
+    out["batched_replicas"] = run_replicas(args, dev)
     return out
+
+
+def run_replicas(args, dev, n_sys=256, P=200):
+    """Batched replicas: n_sys independent electrolytes, N log-uniform in
+    [1000, 100000], density 0.5, Bjerrum length uniform in [0.7, 1.5], P = 200,
+    FP32C, all advanced by one graph launch per step (autotuned shapes)."""
+    import torch
+
+    import paper_2205_13824_gb300 as Pk
+    import rbsog_inputs as I
+    B = Pk.binding
+    Ns, Ls, lBs = I.replica_sizes(n_sys, seed=4)
+    K, W = args.steps, max(2, min(args.warmup, 5))
+    params = [Pk.make_params(float(Ls[i]), P, lB=float(lBs[i]), seed=1000 + i, n_ksets=W + K + 4,
+                             precision="fp32c") for i in range(n_sys)]
+    b = Pk.Batch([int(n) for n in Ns], params, device=dev.index)
+    for i in range(n_sys):
+        q, x, v = I.electrolyte(int(Ns[i]), float(Ls[i]), seed=5000 + i)
+        b.set_state(i, torch.tensor(q, device=dev), torch.tensor(x, device=dev), torch.tensor(v, device=dev))
+    tuned = B.rbsog_batch_autotune(b.ctx, 2)
+    b.step(W)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.step(K)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    total = int(sum(int(n) for n in Ns))
+    b.close()
+    return {"value": total / (ms / 1e3), "unit": "particle-steps/s", "ms_per_step": ms, "steps": K,
+            "n_sys": n_sys, "particles": total, "P": P, "launches_per_step": "one graph launch",
+            "autotuned": tuned}
 
 
 def cpu_baseline(N, L, P, q, x, v, sample_steps=1):

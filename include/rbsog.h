@@ -247,6 +247,17 @@ rbsog_status rbsog_batch_get_kseq(rbsog_batch *b, int32_t sys, int64_t set0, int
 /* Advance every system of the batch by nsteps velocity-Verlet steps. */
 rbsog_status rbsog_batch_step(rbsog_batch *b, int64_t nsteps);
 
+/* Autotuner for launch shapes: times `reps` force evaluations of the whole
+ * batch (into scratch forces; state, cursors and energies are untouched)
+ * for candidate near-field block sizes (home particles per block) and
+ * rho-sweep tiles (particles per tile), keeps the fastest, applies it and
+ * remembers it for the systems' size classes (floor(log2 n), P, precision)
+ * for every later context of the process.  chosen[2] (host, may be NULL)
+ * receives (home, tile; 0 = default rule).  Needs params and state.  The
+ * launch shape changes the order of floating-point sums, so results after
+ * tuning may differ from untuned ones in the last bits. */
+rbsog_status rbsog_batch_autotune(rbsog_batch *b, int32_t reps, int32_t *chosen);
+
 /* Description of the last error on this context (never NULL). */
 const char *rbsog_last_error(const rbsog_ctx *ctx);
 

@@ -27,6 +27,7 @@ EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_stat
            "rbsog_get_cursor", "rbsog_restore", "rbsog_rho_noalloc", "rbsog_measure_peaks",
            "rbsog_batch_create", "rbsog_batch_set_params", "rbsog_batch_set_state", "rbsog_batch_restore",
            "rbsog_batch_get_state", "rbsog_batch_get_energies", "rbsog_batch_get_kseq", "rbsog_batch_step",
+           "rbsog_batch_autotune",
            "rbsog_get_profile", "rbsog_last_error", "rbsog_destroy")
 
 
@@ -93,6 +94,7 @@ def _load():
         "rbsog_batch_get_energies": [P, C.c_int32, C.POINTER(rbsog_energies)],
         "rbsog_batch_get_kseq": [P, C.c_int32, C.c_int64, C.c_int64, P],
         "rbsog_batch_step": [P, C.c_int64],
+        "rbsog_batch_autotune": [P, C.c_int32, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -286,6 +288,12 @@ def rbsog_batch_get_kseq(ctx, sys: int, set0: int, nsets: int, m_out):
 
 def rbsog_batch_step(ctx, nsteps: int):
     _check(ctx, _lib.rbsog_batch_step(ctx, int(nsteps)))
+
+
+def rbsog_batch_autotune(ctx, reps: int = 3):
+    chosen = np.zeros(2, dtype=np.int32)
+    _check(ctx, _lib.rbsog_batch_autotune(ctx, int(reps), _ptr(chosen)))
+    return {"home": int(chosen[0]), "tile": int(chosen[1])}
 
 
 def rbsog_last_error(ctx) -> str:

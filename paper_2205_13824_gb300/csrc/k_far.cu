@@ -22,6 +22,8 @@
 // scatter    one thread per particle, frequencies staged through shared
 //            memory in chunks; adds the near-field force and writes the total
 //            to the particle's caller-order slot.
+#include <algorithm>
+
 #include "rbsog_kernels.cuh"
 
 namespace rbsog {
@@ -279,11 +281,12 @@ __global__ void __launch_bounds__(kScatterThreads)
 
 }  // namespace
 
-void far_layout(int64_t n, int32_t P, int &tile_p, int &n_ptiles) {
-    // at least ~3 waves of sweep blocks (152 SMs x 8 resident blocks)
+void far_layout(int64_t n, int32_t P, int tile_override, int &tile_p, int &n_ptiles) {
+    // default: at least ~3 waves of sweep blocks (152 SMs x 8 resident blocks)
     const int nkt = (P + kKTile - 1) / kKTile;
     int tp = 2048;
     while (tp > 128 && (double)((n + tp - 1) / tp) * nkt < 152.0 * 8 * 3) tp /= 2;
+    if (tile_override > 0) tp = std::min(4096, std::max(64, tile_override));
     tile_p = tp;
     n_ptiles = (int)((n + tp - 1) / tp);
 }

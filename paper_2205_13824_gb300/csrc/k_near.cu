@@ -408,13 +408,13 @@ size_t near_smem(int precision, int cap) {
 
 }  // namespace
 
-void near_layout(const BoxDev &box, int64_t n, int precision, int &group, int &nseg_x, int &cap, int &nblocks,
-                 int &npartials) {
-    // one warp per 32 home particles and ~120 home particles per block; the
-    // staging chunk covers the mean occupancy of the 9 (group + 2) staged
-    // cells with 15% head-room (denser regions are processed in chunks)
+void near_layout(const BoxDev &box, int64_t n, int precision, int home, int &group, int &nseg_x, int &cap,
+                 int &nblocks, int &npartials) {
+    // one warp per 32 home particles and about `home` home particles per
+    // block; the staging chunk covers the mean occupancy of the 9 (group + 2)
+    // staged cells with 15% head-room (denser regions are processed in chunks)
     const double per_cell = (double)n / (double)box.ncell;
-    int g = (int)std::lround(120.0 / std::max(per_cell, 1e-3));
+    int g = (int)std::lround((double)home / std::max(per_cell, 1e-3));
     g = std::max(1, std::min(g, std::min(kMaxGroup, box.nc[0] - 2)));
     group = g;
     nseg_x = (box.nc[0] + g - 1) / g;

@@ -42,11 +42,11 @@ __device__ __forceinline__ double unit53(uint64_t x) {
 }
 
 // Unnormalised target mass, proportional to F~(k) of Eq. 3.5 at k = 2 pi m / L.
-__device__ double target_mass(const SamplerDev &sp, int mx, int my, int mz) {
+__device__ double target_mass(const SamplerDev &sp, const double *L, int mx, int my, int mz) {
     const int md[3] = {mx, my, mz};
     double k2 = 0.0;
     for (int d = 0; d < 3; ++d) {
-        const double kd = 2.0 * kPi * (double)md[d] / sp.L[d];
+        const double kd = 2.0 * kPi * (double)md[d] / L[d];
         k2 += kd * kd;
     }
     double acc = 0.0;
@@ -70,16 +70,26 @@ __device__ double proposal_mass(int m, double s0, double Ld) {
 // acceptance uniform).  The first non-zero proposal starts the chain; after
 // that each iteration emits the post-decision state.  Zero proposals are
 // rejections (p(0) = 0).
-__global__ void __launch_bounds__(128) k_mh_chain(SamplerDev sp, int4 *__restrict__ kseq,
+__global__ void __launch_bounds__(128) k_mh_chain(const __grid_constant__ SamplerDev sp, const SamplerSys *__restrict__ sys, int n_sys,
+                                                  int64_t total_chains, int4 *__restrict__ kseq,
                                                   int32_t *__restrict__ err_flag) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= sp.n_chains) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total_chains) return;
+    int lo = 0, hi = n_sys;   // system of global chain g: largest lo with chain_off <= g
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sys[mid].chain_off <= g) lo = mid; else hi = mid;
+    }
+    const SamplerSys &y = sys[lo];
+    const int64_t c = g - y.chain_off;           // chain index within its system
     const double s0 = sp.s[0];
     double sd[3];
-    for (int d = 0; d < 3; ++d) sd[d] = sp.L[d] / (sqrt(2.0) * kPi * s0);
-    const int64_t len = sp.chain_len;
+    for (int d = 0; d < 3; ++d) sd[d] = y.L[d] / (sqrt(2.0) * kPi * s0);
+    const int64_t len = y.chain_len;
     const int64_t cap = 64 * len + 4096;
-    int4 *out = kseq + c * len;
+    int4 *out = kseq + y.k_off + c * len;
+    const uint64_t seed = y.seed;
+    const double *L = y.L;
     int cur[3] = {0, 0, 0};
     double p_cur = 0.0, q_cur = 0.0;
     bool have = false;
@@ -92,8 +102,8 @@ __global__ void __launch_bounds__(128) k_mh_chain(SamplerDev sp, int4 *__restric
         }
         uint64_t ra[4] = {(uint64_t)j, 0, 0, 0};
         uint64_t rb[4] = {(uint64_t)j, 1, 0, 0};
-        philox4x64_10(ra, sp.seed, (uint64_t)c);
-        philox4x64_10(rb, sp.seed, (uint64_t)c);
+        philox4x64_10(ra, seed, (uint64_t)c);
+        philox4x64_10(rb, seed, (uint64_t)c);
         const double r01 = sqrt(-2.0 * log(1.0 - unit53(ra[0])));
         const double r23 = sqrt(-2.0 * log(1.0 - unit53(ra[2])));
         double z[3];
@@ -109,15 +119,15 @@ __global__ void __launch_bounds__(128) k_mh_chain(SamplerDev sp, int4 *__restric
             cur[0] = mp[0];
             cur[1] = mp[1];
             cur[2] = mp[2];
-            p_cur = target_mass(sp, cur[0], cur[1], cur[2]);
-            q_cur = proposal_mass(cur[0], s0, sp.L[0]) * proposal_mass(cur[1], s0, sp.L[1]) *
-                    proposal_mass(cur[2], s0, sp.L[2]);
+            p_cur = target_mass(sp, L, cur[0], cur[1], cur[2]);
+            q_cur = proposal_mass(cur[0], s0, L[0]) * proposal_mass(cur[1], s0, L[1]) *
+                    proposal_mass(cur[2], s0, L[2]);
             have = true;
         } else if (!zero) {
-            const double p_new = target_mass(sp, mp[0], mp[1], mp[2]);
-            const double q_new = proposal_mass(mp[0], s0, sp.L[0]) *
-                                 proposal_mass(mp[1], s0, sp.L[1]) *
-                                 proposal_mass(mp[2], s0, sp.L[2]);
+            const double p_new = target_mass(sp, L, mp[0], mp[1], mp[2]);
+            const double q_new = proposal_mass(mp[0], s0, L[0]) *
+                                 proposal_mass(mp[1], s0, L[1]) *
+                                 proposal_mass(mp[2], s0, L[2]);
             const double ratio = (p_new * q_cur) / (p_cur * q_new);
             if (unit53(rb[0]) < ratio) {
                 cur[0] = mp[0];
@@ -134,13 +144,13 @@ __global__ void __launch_bounds__(128) k_mh_chain(SamplerDev sp, int4 *__restric
 
 }  // namespace
 
-cudaError_t launch_mh_sampler(const SamplerDev &sp, int4 *kseq, int32_t *err_flag,
-                              cudaStream_t st, const Prof *prof) {
-    if (sp.n_chains <= 0) return cudaSuccess;
+cudaError_t launch_mh_sampler(const SamplerDev &sp, const SamplerSys *sys, int n_sys, int64_t total_chains,
+                              int4 *kseq, int32_t *err_flag, cudaStream_t st, const Prof *prof) {
+    if (total_chains <= 0) return cudaSuccess;
     ProfScope ps(prof, "mh_sampler");
-    const int threads = 128;
-    const int64_t blocks = (sp.n_chains + threads - 1) / threads;
-    k_mh_chain<<<(unsigned)blocks, threads, 0, st>>>(sp, kseq, err_flag);
+    const int threads = 64;   // chains are long serial FP64 loops: spread them over many SMs
+    const int64_t blocks = (total_chains + threads - 1) / threads;
+    k_mh_chain<<<(unsigned)blocks, threads, 0, st>>>(sp, sys, n_sys, total_chains, kseq, err_flag);
     return cudaGetLastError();
 }
 

@@ -13,6 +13,8 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -30,6 +32,29 @@ struct ProfRec {
     const char *name;
     cudaEvent_t a, b;
 };
+
+// Launch-shape tunables chosen by rbsog_batch_autotune, remembered per size
+// class (floor(log2 n)), P and precision for every later context in the
+// process.  home: near-field home particles per block; tile: rho-sweep
+// particles per tile (0 = default rule).
+struct Tune {
+    int home = 120;
+    int tile = 0;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, Tune> g_tune;
+
+std::tuple<int, int, int> tune_key(int64_t n, int P, int prec) {
+    int c = 0;
+    while ((int64_t(1) << (c + 1)) <= n) ++c;
+    return std::make_tuple(c, P, prec);
+}
+
+Tune tune_for(int64_t n, int P, int prec) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(n, P, prec));
+    return it == g_tune.end() ? Tune{} : it->second;
+}
 
 }  // namespace
 
@@ -55,6 +80,7 @@ struct rbsog_ctx {
     std::vector<double> S, sum_q2;
     std::vector<int64_t> n_chains, host_cursor;
     std::vector<int> chain_len;
+    std::vector<Tune> tune;            // per-system launch-shape tunables
     int64_t ncell_total = 0;
     int max_cap = 256, max_tile_p = 128;
     std::vector<int2> pblk, nblk, sblk;
@@ -339,7 +365,8 @@ BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
 // Cell list + near field + far field for the current positions; total force
 // into c->force (caller order).  With a mask, only masked systems take the
 // new forces, energies and k-set.
-rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_sorted) {
+rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_sorted,
+                            double4_32a *force_out = nullptr) {
     const Prof *pf = prof_of(ctx);
     const int prec = ctx->precision;
     CK(launch_build_cells(bv, ctx->posq, ctx->cb, prec, ctx->sp64, ctx->sp32, ctx->st, pf));
@@ -347,8 +374,8 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
                    ctx->st, pf));
     CK(launch_rho_sweep(prec, bv, ctx->sp64, ctx->sp32, ctx->rho_part, ctx->st, pf));
     CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
-    CK(launch_far_scatter(prec, bv, ctx->sp64, ctx->sp32, ctx->ktab, ctx->fnear, ctx->cb.perm, ctx->force,
-                          ctx->err_flag, ctx->st, pf));
+    CK(launch_far_scatter(prec, bv, ctx->sp64, ctx->sp32, ctx->ktab, ctx->fnear, ctx->cb.perm,
+                          force_out ? force_out : ctx->force, ctx->err_flag, ctx->st, pf));
     return RBSOG_OK;
 }
 
@@ -421,6 +448,47 @@ rbsog_status initial_forces(rbsog_ctx *ctx) {
             ctx->force_valid[s] = 1;
         }
     return RBSOG_OK;
+}
+
+// Near-field and rho-sweep launch shapes from the per-system tunables:
+// segment grouping, staging chunk, sweep tiles, partial-sum offsets, work
+// tables and the buffers whose size depends on them.
+rbsog_status apply_layout(rbsog_ctx *ctx) {
+    drop_graph(ctx);
+    ctx->nblk.clear();
+    ctx->sblk.clear();
+    ctx->max_cap = 256;
+    ctx->max_tile_p = 128;
+    int64_t e_off = 0, rp_off = 0;
+    for (int s = 0; s < ctx->n_sys; ++s) {
+        SysDesc &d = ctx->desc[s];
+        int nblocks = 0, npart = 0;
+        near_layout(d.box, d.n, ctx->precision, ctx->tune[s].home, d.group, d.nseg_x, d.near_cap, nblocks, npart);
+        d.e_off = (int32_t)e_off;
+        d.n_epart = npart;
+        far_layout(d.n, ctx->P, ctx->tune[s].tile, d.tile_p, d.n_ptiles);
+        d.rp_off = rp_off;
+        for (int b = 0; b < nblocks; ++b) ctx->nblk.push_back(make_int2(s, b));
+        for (int b = 0; b < d.n_ptiles; ++b) ctx->sblk.push_back(make_int2(s, b));
+        ctx->max_cap = std::max(ctx->max_cap, d.near_cap);
+        ctx->max_tile_p = std::max(ctx->max_tile_p, d.tile_p);
+        e_off += npart;
+        rp_off += (int64_t)ctx->P * d.n_ptiles;
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(dalloc(&ctx->rho_part, (size_t)rp_off));
+    CK(dalloc(&ctx->epart, (size_t)e_off));
+    CK(dalloc(&ctx->d_nblk, ctx->nblk.size()));
+    CK(dalloc(&ctx->d_sblk, ctx->sblk.size()));
+    CK(cudaMemcpyAsync(ctx->d_nblk, ctx->nblk.data(), sizeof(int2) * ctx->nblk.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->d_sblk, ctx->sblk.data(), sizeof(int2) * ctx->sblk.size(), cudaMemcpyHostToDevice, ctx->st));
+    return upload_desc(ctx);
+}
+
+bool all_state(const rbsog_ctx *ctx) {
+    for (char c : ctx->have_state)
+        if (!c) return false;
+    return true;
 }
 
 rbsog_status check_sys(rbsog_ctx *ctx, int32_t sys) {
@@ -585,9 +653,8 @@ rbsog_status rbsog_batch_set_params(rbsog_batch *ctx, const rbsog_params *pp) {
     ctx->nblk.clear();
     ctx->sblk.clear();
     std::vector<int32_t> cell_sys;
-    int64_t c_off = 0, e_off = 0, rp_off = 0, k_off = 0, kp_off = 0;
-    ctx->max_cap = 256;
-    ctx->max_tile_p = 128;
+    int64_t c_off = 0, k_off = 0, kp_off = 0;
+    ctx->tune.assign(ns, Tune{});
     for (int s = 0; s < ns; ++s) {
         const rbsog_params &q = p[s];
         SysDesc &d = ctx->desc[s];
@@ -595,12 +662,6 @@ rbsog_status rbsog_batch_set_params(rbsog_batch *ctx, const rbsog_params *pp) {
         d.p_off = ctx->p_off[s];
         d.n = ctx->n_per[s];
         d.c_off = c_off;
-        int nblocks = 0, npart = 0;
-        near_layout(d.box, d.n, ctx->precision, d.group, d.nseg_x, d.near_cap, nblocks, npart);
-        d.e_off = (int32_t)e_off;
-        d.n_epart = npart;
-        far_layout(d.n, ctx->P, d.tile_p, d.n_ptiles);
-        d.rp_off = rp_off;
         d.k_off = k_off;
         d.n_sets = q.n_ksets;
         d.n_kpart = (int32_t)((d.n + kParticleBlock - 1) / kParticleBlock);
@@ -611,6 +672,7 @@ rbsog_status rbsog_batch_set_params(rbsog_batch *ctx, const rbsog_params *pp) {
             Ssum += w[l] * sv[l] * sv[l] * sv[l] * (prod - 1.0);
         }
         ctx->S[s] = Ssum;
+        ctx->tune[s] = tune_for(d.n, ctx->P, ctx->precision);
         const double V = q.L[0] * q.L[1] * q.L[2];
         d.coef = -q.coulomb_prefactor * std::pow(kPi, 1.5) * Ssum / ((double)ctx->P * V);
         d.half_coef_U = q.coulomb_prefactor * std::pow(kPi, 1.5) * Ssum / (2.0 * ctx->P * V);
@@ -623,14 +685,8 @@ rbsog_status rbsog_batch_set_params(rbsog_batch *ctx, const rbsog_params *pp) {
         const int64_t total = q.n_ksets * (int64_t)ctx->P;
         ctx->n_chains[s] = (total + ctx->chain_len[s] - 1) / ctx->chain_len[s];
         for (int64_t b = 0; b < d.n_kpart; ++b) ctx->pblk.push_back(make_int2(s, (int)b));
-        for (int b = 0; b < nblocks; ++b) ctx->nblk.push_back(make_int2(s, b));
-        for (int b = 0; b < d.n_ptiles; ++b) ctx->sblk.push_back(make_int2(s, b));
         cell_sys.insert(cell_sys.end(), (size_t)d.box.ncell, s);
-        ctx->max_cap = std::max(ctx->max_cap, d.near_cap);
-        ctx->max_tile_p = std::max(ctx->max_tile_p, d.tile_p);
         c_off += d.box.ncell;
-        e_off += npart;
-        rp_off += (int64_t)ctx->P * d.n_ptiles;
         k_off += ctx->n_chains[s] * ctx->chain_len[s];
         kp_off += d.n_kpart;
     }
@@ -640,10 +696,8 @@ rbsog_status rbsog_batch_set_params(rbsog_batch *ctx, const rbsog_params *pp) {
 
     CK(cudaSetDevice(ctx->device));
     CK(dalloc(&ctx->kseq, (size_t)k_off));
-    CK(dalloc(&ctx->rho_part, (size_t)rp_off));
     CK(dalloc(&ctx->rho, (size_t)ns * ctx->P));
     CK(dalloc((unsigned char **)&ctx->ktab, ktab_bytes(ctx->precision, (int64_t)ns * ctx->P)));
-    CK(dalloc(&ctx->epart, (size_t)e_off));
     CK(dalloc(&ctx->kpart, (size_t)kp_off));
     CK(dalloc(&ctx->cb.count, (size_t)c_off));
     CK(dalloc(&ctx->cb.start, (size_t)c_off + 1));
@@ -651,14 +705,12 @@ rbsog_status rbsog_batch_set_params(rbsog_batch *ctx, const rbsog_params *pp) {
     CK(dalloc(&ctx->m_tmp, (size_t)ctx->P));
     CK(dalloc(&ctx->m3_tmp, (size_t)ctx->P * 3));
     CK(dalloc(&ctx->d_pblk, ctx->pblk.size()));
-    CK(dalloc(&ctx->d_nblk, ctx->nblk.size()));
-    CK(dalloc(&ctx->d_sblk, ctx->sblk.size()));
     CK(dalloc(&ctx->d_cell_sys, cell_sys.size()));
     rbsog_status es = enter(ctx);
     if (es != RBSOG_OK) return es;
+    es = apply_layout(ctx);
+    if (es != RBSOG_OK) return es;
     CK(cudaMemcpyAsync(ctx->d_pblk, ctx->pblk.data(), sizeof(int2) * ctx->pblk.size(), cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaMemcpyAsync(ctx->d_nblk, ctx->nblk.data(), sizeof(int2) * ctx->nblk.size(), cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaMemcpyAsync(ctx->d_sblk, ctx->sblk.data(), sizeof(int2) * ctx->sblk.size(), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->d_cell_sys, cell_sys.data(), sizeof(int32_t) * cell_sys.size(), cudaMemcpyHostToDevice,
                        ctx->st));
     CK(cudaMemsetAsync(ctx->cb.count, 0, sizeof(int32_t) * c_off, ctx->st));
@@ -670,18 +722,28 @@ rbsog_status rbsog_batch_set_params(rbsog_batch *ctx, const rbsog_params *pp) {
     std::fill(ctx->host_cursor.begin(), ctx->host_cursor.end(), 0);
     std::fill(ctx->force_valid.begin(), ctx->force_valid.end(), 0);
 
-    for (int s = 0; s < ns; ++s) {
+    {
         SamplerDev sp{};
-        sp.M = p[s].M;
-        for (int l = 0; l <= p[s].M; ++l) {
+        sp.M = p[0].M;
+        for (int l = 0; l <= p[0].M; ++l) {
             sp.omega[l] = w[l];
             sp.s[l] = sv[l];
         }
-        for (int d = 0; d < 3; ++d) sp.L[d] = p[s].L[d];
-        sp.seed = p[s].seed;
-        sp.n_chains = ctx->n_chains[s];
-        sp.chain_len = ctx->chain_len[s];
-        CK(launch_mh_sampler(sp, ctx->kseq + ctx->desc[s].k_off, ctx->err_flag, ctx->st, prof_of(ctx)));
+        std::vector<SamplerSys> ss(ns);
+        int64_t coff = 0;
+        for (int s = 0; s < ns; ++s) {
+            for (int d = 0; d < 3; ++d) ss[s].L[d] = p[s].L[d];
+            ss[s].seed = p[s].seed;
+            ss[s].chain_off = coff;
+            ss[s].k_off = ctx->desc[s].k_off;
+            ss[s].chain_len = ctx->chain_len[s];
+            coff += ctx->n_chains[s];
+        }
+        SamplerSys *d_ss = nullptr;
+        CK(cudaMallocAsync((void **)&d_ss, sizeof(SamplerSys) * ns, ctx->st));
+        CK(cudaMemcpyAsync(d_ss, ss.data(), sizeof(SamplerSys) * ns, cudaMemcpyHostToDevice, ctx->st));
+        CK(launch_mh_sampler(sp, d_ss, ns, coff, ctx->kseq, ctx->err_flag, ctx->st, prof_of(ctx)));
+        CK(cudaFreeAsync(d_ss, ctx->st));
     }
     rbsog_status fs = check_flags(ctx);
     if (fs != RBSOG_OK) return fs;
@@ -690,6 +752,86 @@ rbsog_status rbsog_batch_set_params(rbsog_batch *ctx, const rbsog_params *pp) {
 }
 
 rbsog_status rbsog_set_params(rbsog_ctx *ctx, const rbsog_params *p) { return rbsog_batch_set_params(ctx, p); }
+
+rbsog_status rbsog_batch_autotune(rbsog_batch *ctx, int32_t reps, int32_t *chosen) {
+    if (!ctx || reps < 1) return RBSOG_EINVAL;
+    if (!ctx->have_params || !all_state(ctx)) return fail(ctx, RBSOG_ESTATE, "params and state required");
+    const bool prof = ctx->profiling;
+    ctx->profiling = false;
+    rbsog_status es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    double4_32a *scratch = nullptr;
+    CK(cudaMallocAsync((void **)&scratch, sizeof(double4_32a) * ctx->n_total, ctx->st));
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    // time `reps` force evaluations of the whole batch into scratch forces
+    // (the simulation state, cursors and energies are not touched)
+    auto measure = [&](const Tune &t, float &best) -> rbsog_status {
+        for (auto &x : ctx->tune) x = t;
+        rbsog_status s2 = apply_layout(ctx);
+        if (s2 != RBSOG_OK) return s2;
+        const BatchView bv = view(ctx);
+        s2 = enqueue_forces(ctx, bv, nullptr, scratch);   // warm-up
+        if (s2 != RBSOG_OK) return s2;
+        best = 1e30f;
+        for (int r = 0; r < reps; ++r) {
+            CK(cudaEventRecord(a, ctx->st));
+            s2 = enqueue_forces(ctx, bv, nullptr, scratch);
+            if (s2 != RBSOG_OK) return s2;
+            CK(cudaEventRecord(b, ctx->st));
+            CK(cudaEventSynchronize(b));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            best = std::min(best, ms);
+        }
+        return RBSOG_OK;
+    };
+    const int homes[] = {64, 96, 120, 160, 224};
+    const int tiles[] = {0, 256, 512, 1024, 2048};
+    Tune best_t;
+    float best_ms = 1e30f;
+    for (int h : homes) {
+        Tune t;
+        t.home = h;
+        float ms = 0.f;
+        es = measure(t, ms);
+        if (es != RBSOG_OK) return es;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_t = t;
+        }
+    }
+    for (int tl : tiles) {
+        if (tl == 0) continue;   // the default rule was measured with the homes
+        Tune t = best_t;
+        t.tile = tl;
+        float ms = 0.f;
+        es = measure(t, ms);
+        if (es != RBSOG_OK) return es;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_t = t;
+        }
+    }
+    for (auto &x : ctx->tune) x = best_t;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (int s = 0; s < ctx->n_sys; ++s) g_tune[tune_key(ctx->desc[s].n, ctx->P, ctx->precision)] = best_t;
+    }
+    es = apply_layout(ctx);
+    if (es != RBSOG_OK) return es;
+    CK(cudaFreeAsync(scratch, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->profiling = prof;
+    if (chosen) {
+        chosen[0] = best_t.home;
+        chosen[1] = best_t.tile;
+    }
+    return leave(ctx);
+}
 
 rbsog_status rbsog_get_info(const rbsog_ctx *ctx, rbsog_info *info, double *omega, double *s) {
     if (!ctx || !info) return RBSOG_EINVAL;
@@ -751,12 +893,6 @@ rbsog_status rbsog_batch_set_state(rbsog_batch *ctx, int32_t sys, const double *
 
 rbsog_status rbsog_set_state(rbsog_ctx *ctx, const double *q, const double *x, const double *v) {
     return rbsog_batch_set_state(ctx, 0, q, x, v);
-}
-
-static bool all_state(const rbsog_ctx *ctx) {
-    for (char c : ctx->have_state)
-        if (!c) return false;
-    return true;
 }
 
 rbsog_status rbsog_compute_forces(rbsog_ctx *ctx, const int32_t *m_kset, double *f_out, rbsog_energies *e_out) {

@@ -48,14 +48,18 @@ struct BoxDev {
     float rc2_f, lB_f, wca_s2_f, wca_rc2_f, wca_eps_f;
 };
 
-// Sampler inputs (Sec. 3.3): full SOG (not folded) in FP64.
+// Sampler inputs (Sec. 3.3): full SOG (not folded) in FP64, shared by the
+// systems of a batch; per system the box, seed and chain layout.
 struct SamplerDev {
     int32_t M;
     double omega[kMaxGauss];
     double s[kMaxGauss];
+};
+struct SamplerSys {
     double L[3];
     uint64_t seed;
-    int64_t n_chains;
+    int64_t chain_off;        // first global chain of this system
+    int64_t k_off;            // first int4 of this system's sequence
     int32_t chain_len;
 };
 
@@ -78,8 +82,9 @@ struct ProfScope {
 };
 
 // ---- sampler (k_sampler.cu) -------------------------------------------------
-cudaError_t launch_mh_sampler(const SamplerDev &sp, int4 *kseq, int32_t *err_flag,
-                              cudaStream_t st, const Prof *prof);
+// One launch, one thread per chain over all systems (sys sorted by chain_off).
+cudaError_t launch_mh_sampler(const SamplerDev &sp, const SamplerSys *sys, int n_sys, int64_t total_chains,
+                              int4 *kseq, int32_t *err_flag, cudaStream_t st, const Prof *prof);
 
 // ---- batch layout -------------------------------------------------------------
 // Every kernel works on a batch of independent systems laid out back to back
@@ -148,14 +153,16 @@ cudaError_t launch_build_cells(const BatchView &bv, const double4_32a *posq, con
 // ---- near field (k_near.cu) ---------------------------------------------------
 // Forces (cell order) into fnear; energy partials (U_near, U_wca), one per
 // warp, into epart; neighbour counts (cell order) into nbr when non-null.
-void near_layout(const BoxDev &box, int64_t n, int precision, int &group, int &nseg_x, int &cap,
+// home: target home particles per block (tunable, 120 by default)
+void near_layout(const BoxDev &box, int64_t n, int precision, int home, int &group, int &nseg_x, int &cap,
                  int &nblocks, int &npartials);
 cudaError_t launch_near(int precision, const BatchView &bv, const NearSog &sog, const int32_t *start,
                         const double4_32a *sp64, const uint4 *sp32, double4_32a *fnear, double2 *epart,
                         int32_t *nbr, cudaStream_t st, const Prof *prof);
 
 // ---- far field (k_far.cu) -----------------------------------------------------
-void far_layout(int64_t n, int32_t P, int &tile_p, int &n_ptiles);
+// tile_override > 0 replaces the default particles-per-tile rule (tunable)
+void far_layout(int64_t n, int32_t P, int tile_override, int &tile_p, int &n_ptiles);
 cudaError_t launch_rho_sweep(int precision, const BatchView &bv, const double4_32a *sp64,
                              const uint4 *sp32, double2 *rho_part, cudaStream_t st, const Prof *prof);
 // Combines partials in FP64 (fixed order) into rho[n_sys * P] and the per-k

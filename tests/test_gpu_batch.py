@@ -75,3 +75,29 @@ def test_batch_late_join_keeps_other_cursors():
     ga.close()
     # system 1 restarted: its first step of the second segment consumed k-sets 3.. (cursor kept)
     assert B.rbsog_get_cursor is not None
+
+
+def test_autotuned_batch_equals_alone_bitwise():
+    """After the autotuner picks launch shapes for a batch, a system run alone
+    (which looks up the same remembered shapes for its size class) still
+    reproduces its batched trajectory bit for bit."""
+    Pk, dev = _setup()
+    B = Pk.binding
+    steps = 4
+    sysl = SYSTEMS[:3]
+    states = [I.electrolyte(N, L, seed=300 + i) for i, (N, L, _, _) in enumerate(sysl)]
+    params = [_params(Pk, L, lB, seed, "fp32c", steps + 2) for (N, L, lB, seed) in sysl]
+    b = Pk.Batch([s[0] for s in sysl], params, device=0)
+    for i, (q, x, v) in enumerate(states):
+        b.set_state(i, *(torch.tensor(a, device=dev) for a in (q, x, v)))
+    chosen = B.rbsog_batch_autotune(b.ctx, 2)
+    assert chosen["home"] in (64, 96, 120, 160, 224)
+    b.step(steps)
+    batched = [b.state(i)[0].cpu().numpy() for i in range(len(sysl))]
+    b.close()
+    for i, (N, L, lB, seed) in enumerate(sysl):
+        g = Pk.RBSOG(N, params[i], device=0)
+        g.set_state(*(torch.tensor(a, device=dev) for a in states[i]))
+        g.step(steps)
+        assert np.array_equal(g.state()[0].cpu().numpy(), batched[i])
+        g.close()
