@@ -111,6 +111,9 @@ def lib():
             L.orc_md.argtypes = [_i64, _pd, _pd, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _i64,
                                  _d, _d, _d, _d, C.c_int, C.POINTER(OrcEnergies)]
             L.orc_md.restype = C.c_int
+            L.orc_rdf_counts.argtypes = [_i64, _pd, _pd, _d, _i32, C.POINTER(_u64)]
+            L.orc_rdf_counts.restype = C.c_int
+            L.orc_rdf_g.argtypes = [C.POINTER(_u64), _i32, _d, _i64, _i64, _pd]
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -348,6 +351,20 @@ def md(sys_: System, q, x, v, S, P, kseq_, nsteps, dt, mass=1.0, T0=1.0, tau=0.0
     if rc_ != 0:
         raise ValueError("fewer than 3 cells per side")
     return x, v, f, [es[t].as_dict() for t in range(int(nsteps))]
+
+
+def rdf(q, x, L, nbins):
+    """Appendix A: pair-distance histograms by sign pair (rows ++, +-, --) on
+    [0, L/2) and the g(r) estimate; returns (counts[3, nbins] uint64,
+    g[3, nbins], bin edges[nbins + 1])."""
+    q, x = _f64(q), _f64(x)
+    counts = np.zeros((3, nbins), dtype=np.uint64)
+    if lib().orc_rdf_counts(x.shape[0], _p(q), _p(x), float(L), int(nbins), _p(counts, C.POINTER(_u64))):
+        raise ValueError("nbins must be a power of two in [16, 4096] and L > 0")
+    g = np.zeros((3, nbins))
+    lib().orc_rdf_g(_p(counts, C.POINTER(_u64)), int(nbins), float(L), int((q > 0).sum()), int((q < 0).sum()),
+                    _p(g))
+    return counts, g, np.arange(nbins + 1) * (float(L) / (2 * nbins))
 
 
 def num_threads():

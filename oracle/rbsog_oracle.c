@@ -25,7 +25,10 @@
  *   proposal     q(m) = (1/2)[erf((m+1/2) pi s_0/L) - erf((m-1/2) pi s_0/L)] (Sec. 3.3
  *                prints an extra factor 1/2 inside erf for m != 0);
  *   self energy  (1/2) F_M(0) sum q^2 with the modified omega_0;
- *   m = 0        a zero proposal is a rejection (the chain repeats its state).
+ *   m = 0        a zero proposal is a rejection (the chain repeats its state);
+ *   RDF          Appendix A per sign pair, rho = number density of the second
+ *                species (N^2, not N(N-1), normalisation), distances measured on
+ *                positions quantised to L 2^-32 per axis (cubic box).
  */
 #include "rbsog_oracle.h"
 
@@ -779,4 +782,95 @@ int orc_md(int64_t n, const double *q, double *x, double *v, double *f,
         if (e_steps) e_steps[t] = e;
     }
     return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Radial distribution functions (Appendix A).
+ *
+ * g(r) = (1/(N rho)) sum_i sum_{j != i} <delta(r_ij - r)> / (4 pi r^2), taken
+ * per pair of charge signs (++, +-, --) with rho the number density of the
+ * second species, and estimated by a histogram of the minimum-image pair
+ * distances on [0, L/2) in nbins equal bins (cubic box of edge L).
+ *
+ * Distances are measured on positions quantised to L 2^-32 per axis:
+ * X = floor(frac(x / L) 2^32) mod 2^32.  On that lattice the minimum-image
+ * difference is an exact integer d in [-2^31, 2^31), the squared distance an
+ * exact integer R = dx^2 + dy^2 + dz^2 (units (L 2^-32)^2), r < L/2 means
+ * R < 2^62, and the bin of width 2^31/nbins lattice units is
+ * floor(isqrt(R) / (2^31/nbins)): every bin decision is exact integer
+ * arithmetic, so any correct implementation gives the same counts.
+ * ------------------------------------------------------------------------ */
+static uint32_t rdf_quantise(double x, double L) {
+    double t = x / L;
+    t = t - floor(t);
+    const double v = floor(t * 4294967296.0);
+    return (uint32_t)((uint64_t)v & 0xffffffffu);
+}
+
+/* floor(sqrt(R)) for R < 2^62, exact */
+static uint64_t rdf_isqrt(uint64_t R) {
+    uint64_t s = (uint64_t)sqrt((double)R);
+    while (s * s > R) --s;
+    while ((s + 1) * (s + 1) <= R) ++s;
+    return s;
+}
+
+int orc_rdf_counts(int64_t n, const double *q, const double *x, double L, int32_t nbins, uint64_t *counts) {
+    if (nbins < 16 || nbins > 4096 || (nbins & (nbins - 1)) || !(L > 0.0)) return -1;
+    const uint64_t width = (uint64_t)2147483648u / (uint64_t)nbins;   /* lattice units per bin */
+    uint32_t *X = malloc(sizeof(uint32_t) * 3 * (size_t)(n > 0 ? n : 1));
+    int *sp = malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        for (int d = 0; d < 3; ++d) X[3 * i + d] = rdf_quantise(x[3 * i + d], L);
+        sp[i] = q[i] > 0.0 ? 0 : (q[i] < 0.0 ? 1 : -1);   /* sign species; neutral sites are skipped */
+    }
+    memset(counts, 0, sizeof(uint64_t) * 3 * (size_t)nbins);
+    int nt = orc_num_threads();
+    uint64_t *part = calloc((size_t)nt * 3 * (size_t)nbins, sizeof(uint64_t));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+#ifdef _OPENMP
+        uint64_t *h = part + (size_t)omp_get_thread_num() * 3 * (size_t)nbins;
+#else
+        uint64_t *h = part;
+#endif
+        if (sp[i] < 0) continue;
+        for (int64_t j = i + 1; j < n; ++j) {
+            if (sp[j] < 0) continue;
+            uint64_t R = 0;
+            for (int d = 0; d < 3; ++d) {
+                int64_t dd = (int64_t)X[3 * i + d] - (int64_t)X[3 * j + d];
+                if (dd >= 2147483648LL) dd -= 4294967296LL;
+                if (dd < -2147483648LL) dd += 4294967296LL;
+                R += (uint64_t)(dd * dd);
+            }
+            if (R >= ((uint64_t)1 << 62)) continue;              /* r >= L/2 */
+            const int64_t bin = (int64_t)(rdf_isqrt(R) / width);
+            h[(sp[i] + sp[j]) * nbins + bin] += 1;               /* 0: ++, 1: +-, 2: -- */
+        }
+    }
+    for (int t = 0; t < nt; ++t)
+        for (int64_t k = 0; k < 3 * (int64_t)nbins; ++k) counts[k] += part[(size_t)t * 3 * nbins + k];
+    free(part);
+    free(sp);
+    free(X);
+    return 0;
+}
+
+/* Histogram estimate of Appendix A's g(r) for bin k (r in [k dr, (k+1) dr),
+ * dr = L / (2 nbins)): the expected number of ordered pairs in the shell is
+ * N_a (N_b / V) * shell volume, with shell volume (4 pi / 3)((k+1)^3 - k^3) dr^3;
+ * like pairs are counted once per unordered pair, so twice as ordered pairs. */
+void orc_rdf_g(const uint64_t *counts, int32_t nbins, double L, int64_t n_pos, int64_t n_neg, double *g) {
+    const double V = L * L * L;
+    const double dr = L / (2.0 * nbins);
+    const double na[3] = {(double)n_pos, (double)n_pos, (double)n_neg};
+    const double nb[3] = {(double)n_pos, (double)n_neg, (double)n_neg};
+    const double mult[3] = {2.0, 1.0, 2.0};
+    for (int t = 0; t < 3; ++t)
+        for (int32_t k = 0; k < nbins; ++k) {
+            const double shell = 4.0 * M_PI / 3.0 * (pow(k + 1.0, 3) - pow((double)k, 3)) * dr * dr * dr;
+            const double expect = na[t] * nb[t] / V * shell;
+            g[t * nbins + k] = expect > 0.0 ? mult[t] * (double)counts[t * nbins + k] / expect : 0.0;
+        }
 }

@@ -94,6 +94,10 @@ int  orc_md(int64_t n, const double *q, double *x, double *v, double *f,
             int64_t nsteps, double dt, double mass, double T0, double tau,
             int have_force, orc_energies *e_steps);
 
+/* ---- radial distribution functions (Appendix A) ----------------------- */
+int  orc_rdf_counts(int64_t n, const double *q, const double *x, double L, int32_t nbins, uint64_t *counts);
+void orc_rdf_g(const uint64_t *counts, int32_t nbins, double L, int64_t n_pos, int64_t n_neg, double *g);
+
 int  orc_num_threads(void);
 
 #ifdef __cplusplus
