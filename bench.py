@@ -359,6 +359,62 @@ def run_extras(args, q, x, v, dev):
         g.close()
     out["fp32c_P_sweep"] = sweep
     out["batched_replicas"] = run_replicas(args, dev)
+    out["serving"] = run_serving(dev)
+    return out
+
+
+def serve_trace(Pk, trace, states, P, max_jobs, quantum):
+    """Replay a job trace in real time through one server: jobs are
+    submitted when their arrival time has passed; latency = completion -
+    arrival (wall clock)."""
+    srv = Pk.Server(max_jobs=max_jobs, mem_budget_bytes=64 << 30, quantum=quantum)
+    lat, pending = [], {}
+    nxt = 0
+    t0 = time.perf_counter()
+    while nxt < len(trace) or pending:
+        now = time.perf_counter() - t0
+        while nxt < len(trace) and trace[nxt]["t"] <= now:
+            j = trace[nxt]
+            p = Pk.make_params(j["L"], P, seed=j["seed"], n_ksets=j["steps"] + 1, precision="fp32c")
+            pending[srv.submit(p, *states[nxt], nsteps=j["steps"])] = j["t"]
+            nxt += 1
+        if not pending:
+            time.sleep(max(0.0, trace[nxt]["t"] - now))
+            continue
+        _, _, retired = srv.advance()
+        if retired:
+            done = time.perf_counter() - t0
+            for jid in list(pending):
+                if srv.result(jid)[0] == 2:
+                    lat.append(done - pending.pop(jid))
+                    srv.release(jid)
+    span = time.perf_counter() - t0
+    srv.close()
+    return lat, span
+
+
+def run_serving(dev, n_jobs=48, rate=20.0, P=100):
+    """Continuous batching under a Poisson job trace (rbsog_inputs.job_trace:
+    N log-uniform in [500, 50000], 100-1000 steps, density 0.5, FP32C,
+    P = 100), against the same trace served one job at a time."""
+    import numpy as np
+
+    import paper_2205_13824_gb300 as Pk
+    import rbsog_inputs as I
+    trace = I.job_trace(n_jobs, seed=11, rate=rate, n_min=500, n_max=50000, steps_min=100, steps_max=1000)
+    states = [I.electrolyte(j["N"], j["L"], seed=j["seed"] % 100000) for j in trace]
+    work = sum(j["N"] * j["steps"] for j in trace)
+    # warm the server path once (graph instantiation, allocator) on a short job
+    serve_trace(Pk, [dict(trace[0], t=0.0, steps=5)], states[:1], P, 4, 5)
+    out = {"jobs": n_jobs, "arrival_rate_per_s": rate, "P": P,
+           "offered_particle_steps_per_s": work / trace[-1]["t"]}
+    for name, mj, quantum in (("continuous_batching", 64, 25), ("one_at_a_time", 1, 25)):
+        lat, span = serve_trace(Pk, trace, states, P, mj, quantum)
+        lat = np.sort(np.array(lat))
+        out[name] = {"max_jobs": mj, "quantum_steps": quantum, "makespan_s": span,
+                     "served_particle_steps_per_s": work / span,
+                     "latency_p50_s": float(np.percentile(lat, 50)),
+                     "latency_p99_s": float(np.percentile(lat, 99)), "completed": int(lat.size)}
     return out
 
 

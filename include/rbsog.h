@@ -258,6 +258,40 @@ rbsog_status rbsog_batch_step(rbsog_batch *b, int64_t nsteps);
  * tuning may differ from untuned ones in the last bits. */
 rbsog_status rbsog_batch_autotune(rbsog_batch *b, int32_t reps, int32_t *chosen);
 
+/* ---- Serving engine ---------------------------------------------------------
+ * Continuous batching of MD jobs (each: n particles, parameters, initial
+ * state, a step count).  Jobs wait in a FIFO queue and are admitted while a
+ * job slot is free and their estimated device-memory footprint fits the
+ * budget; admitted jobs advance together as one batch (one graph launch per
+ * step).  A job that has done its steps is frozen on the device and retired
+ * (state copied to host) at the end of the quantum; admissions and
+ * retirements rebuild the batch at the next quantum, moving the running
+ * jobs' state device to device.  Each job's trajectory is the one it would
+ * follow alone (same parameters and seed).  All jobs of a server share b,
+ * sigma, omega0, M, r_c, P and precision.  Host memory for inputs is copied
+ * at submit; results stay on the host until released. */
+typedef struct rbsog_server rbsog_server;
+/* max_jobs >= 1 slots, mem_budget_bytes > 0, quantum >= 1 steps per advance. */
+rbsog_status rbsog_server_create(rbsog_server **out, int32_t max_jobs, int64_t mem_budget_bytes,
+                                 int32_t quantum, int device, void *stream);
+/* Queue a job: q[n], x[n][3], v[n][3] (NULL: zero) in host memory; the
+ * sequence length is set to nsteps + 1.  RBSOG_ENOMEM if the job alone
+ * exceeds the budget. */
+rbsog_status rbsog_server_submit(rbsog_server *s, int64_t n, const rbsog_params *p, const double *q,
+                                 const double *x, const double *v, int64_t nsteps, int64_t *job_id);
+/* Admit what fits, rebuild the batch if its membership changed, advance it
+ * by up to `quantum` steps and retire finished jobs (synchronises). */
+rbsog_status rbsog_server_advance(rbsog_server *s, int32_t *n_active, int32_t *n_waiting,
+                                  int32_t *n_retired);
+/* status: 0 waiting, 1 running, 2 done (then x, v, f [n][3], energies and the
+ * steps done are copied out to host pointers, any of which may be NULL). */
+rbsog_status rbsog_server_result(rbsog_server *s, int64_t job_id, int32_t *status, double *x, double *v,
+                                 double *f, rbsog_energies *e, int64_t *steps_done);
+/* Free a finished job's host results. */
+rbsog_status rbsog_server_release(rbsog_server *s, int64_t job_id);
+const char *rbsog_server_last_error(const rbsog_server *s);
+rbsog_status rbsog_server_destroy(rbsog_server *s);
+
 /* Description of the last error on this context (never NULL). */
 const char *rbsog_last_error(const rbsog_ctx *ctx);
 

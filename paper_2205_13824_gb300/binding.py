@@ -28,6 +28,8 @@ EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_stat
            "rbsog_batch_create", "rbsog_batch_set_params", "rbsog_batch_set_state", "rbsog_batch_restore",
            "rbsog_batch_get_state", "rbsog_batch_get_energies", "rbsog_batch_get_kseq", "rbsog_batch_step",
            "rbsog_batch_autotune",
+           "rbsog_server_create", "rbsog_server_submit", "rbsog_server_advance", "rbsog_server_result",
+           "rbsog_server_release", "rbsog_server_last_error", "rbsog_server_destroy",
            "rbsog_get_profile", "rbsog_last_error", "rbsog_destroy")
 
 
@@ -95,6 +97,14 @@ def _load():
         "rbsog_batch_get_kseq": [P, C.c_int32, C.c_int64, C.c_int64, P],
         "rbsog_batch_step": [P, C.c_int64],
         "rbsog_batch_autotune": [P, C.c_int32, P],
+        "rbsog_server_create": [C.POINTER(P), C.c_int32, C.c_int64, C.c_int32, C.c_int, P],
+        "rbsog_server_submit": [P, C.c_int64, C.POINTER(rbsog_params), P, P, P, C.c_int64,
+                                C.POINTER(C.c_int64)],
+        "rbsog_server_advance": [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+        "rbsog_server_result": [P, C.c_int64, C.POINTER(C.c_int32), P, P, P, C.POINTER(rbsog_energies),
+                                C.POINTER(C.c_int64)],
+        "rbsog_server_release": [P, C.c_int64],
+        "rbsog_server_destroy": [P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -102,6 +112,8 @@ def _load():
         f.restype = st
     lib.rbsog_last_error.argtypes = [P]
     lib.rbsog_last_error.restype = C.c_char_p
+    lib.rbsog_server_last_error.argtypes = [P]
+    lib.rbsog_server_last_error.restype = C.c_char_p
     return lib
 
 
@@ -294,6 +306,67 @@ def rbsog_batch_autotune(ctx, reps: int = 3):
     chosen = np.zeros(2, dtype=np.int32)
     _check(ctx, _lib.rbsog_batch_autotune(ctx, int(reps), _ptr(chosen)))
     return {"home": int(chosen[0]), "tile": int(chosen[1])}
+
+
+def _check_server(s, status):
+    if status != 0:
+        msg = _lib.rbsog_server_last_error(s)
+        raise RBSOGError(status, msg.decode() if msg else "")
+
+
+def rbsog_server_create(max_jobs: int, mem_budget_bytes: int, quantum: int, device: int = 0,
+                        stream: int | None = None):
+    s = C.c_void_p()
+    st = _lib.rbsog_server_create(C.byref(s), int(max_jobs), int(mem_budget_bytes), int(quantum),
+                                  int(device), stream)
+    if st != 0:
+        raise RBSOGError(st, "rbsog_server_create failed")
+    return s
+
+
+def rbsog_server_submit(s, p: rbsog_params, q, x, v, nsteps: int) -> int:
+    """q, x, v: host numpy arrays (float64, C-contiguous); v may be None."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+    jid = C.c_int64()
+    _check_server(s, _lib.rbsog_server_submit(s, int(q.shape[0]), C.byref(p), _ptr(q), _ptr(x), _ptr(v),
+                                              int(nsteps), C.byref(jid)))
+    return jid.value
+
+
+def rbsog_server_advance(s):
+    a, w, r = C.c_int32(), C.c_int32(), C.c_int32()
+    _check_server(s, _lib.rbsog_server_advance(s, C.byref(a), C.byref(w), C.byref(r)))
+    return a.value, w.value, r.value
+
+
+def rbsog_server_result(s, job_id: int, n: int):
+    """(status, x, v, f, energies, steps_done); arrays only once status == 2."""
+    st = C.c_int32()
+    steps = C.c_int64()
+    e = rbsog_energies()
+    x = np.empty((n, 3))
+    v = np.empty((n, 3))
+    f = np.empty((n, 3))
+    _check_server(s, _lib.rbsog_server_result(s, int(job_id), C.byref(st), _ptr(x), _ptr(v), _ptr(f),
+                                              C.byref(e), C.byref(steps)))
+    if st.value != 2:
+        return st.value, None, None, None, None, 0
+    return st.value, x, v, f, e.as_dict(), steps.value
+
+
+def rbsog_server_release(s, job_id: int):
+    _check_server(s, _lib.rbsog_server_release(s, int(job_id)))
+
+
+def rbsog_server_last_error(s) -> str:
+    m = _lib.rbsog_server_last_error(s)
+    return m.decode() if m else ""
+
+
+def rbsog_server_destroy(s):
+    _check_server(None, _lib.rbsog_server_destroy(s))
 
 
 def rbsog_last_error(ctx) -> str:

@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kSweepThreads)
     __shared__ double s_im[kSweepThreads / 32][kKTile];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int2 work = bv.sblk[blockIdx.x];
+    if (bv.remaining && bv.remaining[work.x] == 0) return;   // frozen system: whole block leaves
     const SysDesc &d = bv.sys[work.x];
     const int ptile = work.y;
     const int k = blockIdx.y * kKTile + lane;
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(256) k_rho_combine(BatchView bv, const double2
     const int64_t gk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // system * P + k
     if (gk >= (int64_t)bv.n_sys * bv.P) return;
     const int sy = (int)(gk / bv.P), k = (int)(gk % bv.P);
+    if (bv.remaining && bv.remaining[sy] == 0) return;
     const SysDesc &d = bv.sys[sy];
     const double2 *row = rho_part + d.rp_off + (int64_t)k * d.n_ptiles;
     double re = 0.0, im = 0.0;
@@ -208,6 +210,7 @@ __global__ void __launch_bounds__(kScatterThreads)
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int tid = threadIdx.x;
     const int2 work = bv.pblk[blockIdx.x];
+    if (bv.remaining && bv.remaining[work.x] == 0) return;   // frozen system: whole block leaves
     const SysDesc &d = bv.sys[work.x];
     const int64_t sl = (int64_t)work.y * kScatterThreads + tid;
     const int64_t s = d.p_off + sl;

@@ -20,6 +20,7 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift(BatchView bv, double4_3
                                                          double4_32a *__restrict__ vel,
                                                          const double4_32a *__restrict__ force) {
     const int2 w = bv.pblk[blockIdx.x];
+    if (bv.remaining && bv.remaining[w.x] == 0) return;
     const SysDesc &a = bv.sys[w.x];
     const int64_t il = (int64_t)w.y * kThreads + threadIdx.x;
     if (il >= a.n) return;
@@ -48,6 +49,7 @@ __global__ void __launch_bounds__(kThreads) k_kick(BatchView bv, double4_32a *__
                                                    double *__restrict__ kpart) {
     __shared__ double s_red[kThreads / 32];
     const int2 w = bv.pblk[blockIdx.x];
+    if (bv.remaining && bv.remaining[w.x] == 0) return;
     const SysDesc &a = bv.sys[w.x];
     const int64_t il = (int64_t)w.y * kThreads + threadIdx.x;
     const int64_t i = a.p_off + il;
@@ -82,6 +84,7 @@ __global__ void __launch_bounds__(1024) k_finalize(BatchView bv, const double2 *
     __shared__ double s_red[4][32];
     const int sy = blockIdx.x;
     if (bv.force_mask && !bv.force_mask[sy]) return;
+    if (bv.remaining && bv.remaining[sy] == 0) return;
     const SysDesc &a = bv.sys[sy];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     double un = 0.0, uw = 0.0, r2 = 0.0, ke = 0.0;
@@ -141,6 +144,7 @@ __global__ void __launch_bounds__(1024) k_finalize(BatchView bv, const double2 *
 __global__ void __launch_bounds__(kThreads) k_rescale(BatchView bv, double4_32a *__restrict__ vel,
                                                       const double *__restrict__ energy) {
     const int2 w = bv.pblk[blockIdx.x];
+    if (bv.remaining && bv.remaining[w.x] == 0) return;
     const SysDesc &a = bv.sys[w.x];
     if (a.tau <= 0.0) return;
     const int64_t il = (int64_t)w.y * kThreads + threadIdx.x;
@@ -187,6 +191,11 @@ __global__ void __launch_bounds__(kThreads) k_unsort(int64_t n, int64_t off, con
     out[perm[off + s] - off] = sorted[off + s];
 }
 
+__global__ void k_step_done(int32_t n_sys, int64_t *__restrict__ remaining) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n_sys && remaining[s] > 0) remaining[s] -= 1;
+}
+
 __global__ void k_m_to_int4(int32_t P, const int32_t *__restrict__ m3, int4 *__restrict__ out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= P) return;
@@ -222,6 +231,13 @@ cudaError_t launch_rescale(const BatchView &bv, double4_32a *vel, const double *
                            const Prof *prof) {
     ProfScope ps(prof, "rescale");
     k_rescale<<<bv.n_pblk, kThreads, 0, st>>>(bv, vel, energy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_done(const BatchView &bv, cudaStream_t st, const Prof *prof) {
+    if (!bv.remaining) return cudaSuccess;
+    ProfScope ps(prof, "step_done");
+    k_step_done<<<(unsigned)((bv.n_sys + 127) / 128), 128, 0, st>>>(bv.n_sys, bv.remaining);
     return cudaGetLastError();
 }
 

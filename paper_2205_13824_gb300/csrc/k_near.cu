@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(kThreads, 4)
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int2 work = bv.nblk[blockIdx.x];
+    if (bv.remaining && bv.remaining[work.x] == 0) return;   // frozen system: whole block leaves
     const SysDesc &desc = bv.sys[work.x];
     const BoxDev &box = desc.box;
     const int group = desc.group, nseg_x = desc.nseg_x, cap = desc.near_cap;

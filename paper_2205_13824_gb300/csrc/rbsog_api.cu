@@ -104,6 +104,11 @@ struct rbsog_ctx {
     int2 *d_pblk = nullptr, *d_nblk = nullptr, *d_sblk = nullptr;
     int32_t *d_cell_sys = nullptr;
     int32_t *d_mask = nullptr;        // [n_sys] systems that need a force evaluation
+    // per-system step budgets (used by the serving engine): a system whose
+    // budget reaches 0 is frozen by every step kernel
+    bool use_budget = false;
+    int64_t *d_remaining = nullptr;
+    std::vector<int64_t> remaining_host;
     // pinned host mirrors
     double *h_energy = nullptr;
     int32_t *h_err = nullptr;
@@ -359,6 +364,7 @@ BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
     v.max_cap = c->max_cap;
     v.max_tile_p = c->max_tile_p;
     v.force_mask = nullptr;
+    v.remaining = c->use_budget ? c->d_remaining : nullptr;
     return v;
 }
 
@@ -390,6 +396,7 @@ rbsog_status enqueue_step(rbsog_ctx *ctx) {
     bool thermo = false;
     for (auto &pp : ctx->p) thermo = thermo || pp.tau_T > 0.0;
     if (thermo) CK(launch_rescale(bv, ctx->vel, ctx->energy, ctx->st, pf));
+    CK(launch_step_done(bv, ctx->st, pf));
     return RBSOG_OK;
 }
 
@@ -572,7 +579,12 @@ rbsog_status rbsog_create(rbsog_ctx **out, int64_t n, int device, void *stream) 
     return rbsog_batch_create(out, 1, &n, device, stream);
 }
 
-rbsog_status rbsog_batch_set_params(rbsog_batch *ctx, const rbsog_params *pp) {
+}  // extern "C"
+
+namespace {
+// sample_mask (may be null): systems whose k-sequence is sampled here; the
+// others receive theirs by copy (serving engine rebuilds).
+rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::vector<char> *sample_mask) {
     if (!ctx || !pp) return RBSOG_EINVAL;
     const int ns = ctx->n_sys;
     std::vector<rbsog_params> p(pp, pp + ns);
@@ -729,26 +741,38 @@ rbsog_status rbsog_batch_set_params(rbsog_batch *ctx, const rbsog_params *pp) {
             sp.omega[l] = w[l];
             sp.s[l] = sv[l];
         }
-        std::vector<SamplerSys> ss(ns);
+        std::vector<SamplerSys> ss;
         int64_t coff = 0;
         for (int s = 0; s < ns; ++s) {
-            for (int d = 0; d < 3; ++d) ss[s].L[d] = p[s].L[d];
-            ss[s].seed = p[s].seed;
-            ss[s].chain_off = coff;
-            ss[s].k_off = ctx->desc[s].k_off;
-            ss[s].chain_len = ctx->chain_len[s];
+            if (sample_mask && !(*sample_mask)[s]) continue;
+            SamplerSys y{};
+            for (int d = 0; d < 3; ++d) y.L[d] = p[s].L[d];
+            y.seed = p[s].seed;
+            y.chain_off = coff;
+            y.k_off = ctx->desc[s].k_off;
+            y.chain_len = ctx->chain_len[s];
             coff += ctx->n_chains[s];
+            ss.push_back(y);
         }
-        SamplerSys *d_ss = nullptr;
-        CK(cudaMallocAsync((void **)&d_ss, sizeof(SamplerSys) * ns, ctx->st));
-        CK(cudaMemcpyAsync(d_ss, ss.data(), sizeof(SamplerSys) * ns, cudaMemcpyHostToDevice, ctx->st));
-        CK(launch_mh_sampler(sp, d_ss, ns, coff, ctx->kseq, ctx->err_flag, ctx->st, prof_of(ctx)));
-        CK(cudaFreeAsync(d_ss, ctx->st));
+        if (!ss.empty()) {
+            SamplerSys *d_ss = nullptr;
+            CK(cudaMallocAsync((void **)&d_ss, sizeof(SamplerSys) * ss.size(), ctx->st));
+            CK(cudaMemcpyAsync(d_ss, ss.data(), sizeof(SamplerSys) * ss.size(), cudaMemcpyHostToDevice, ctx->st));
+            CK(launch_mh_sampler(sp, d_ss, (int)ss.size(), coff, ctx->kseq, ctx->err_flag, ctx->st, prof_of(ctx)));
+            CK(cudaFreeAsync(d_ss, ctx->st));
+        }
     }
     rbsog_status fs = check_flags(ctx);
     if (fs != RBSOG_OK) return fs;
     ctx->have_params = true;
     return leave(ctx);
+}
+}  // namespace
+
+extern "C" {
+
+rbsog_status rbsog_batch_set_params(rbsog_batch *ctx, const rbsog_params *pp) {
+    return set_params_impl(ctx, pp, nullptr);
 }
 
 rbsog_status rbsog_set_params(rbsog_ctx *ctx, const rbsog_params *p) { return rbsog_batch_set_params(ctx, p); }
@@ -946,7 +970,8 @@ rbsog_status rbsog_batch_step(rbsog_batch *ctx, int64_t nsteps) {
     if (!ctx->have_params || !all_state(ctx)) return fail(ctx, RBSOG_ESTATE, "params and state required");
     bool all_valid = true;
     for (int s = 0; s < ctx->n_sys; ++s) {
-        const int64_t need = nsteps + (ctx->force_valid[s] ? 0 : 1);
+        const int64_t run = ctx->use_budget ? std::min(nsteps, ctx->remaining_host[s]) : nsteps;
+        const int64_t need = run + (ctx->force_valid[s] ? 0 : 1);
         all_valid = all_valid && ctx->force_valid[s];
         if (ctx->host_cursor[s] + need > ctx->desc[s].n_sets)
             return fail(ctx, RBSOG_EINVAL, "system %d: pre-sampled k-sequence too short (%lld sets left, %lld needed)",
@@ -979,7 +1004,11 @@ rbsog_status rbsog_batch_step(rbsog_batch *ctx, int64_t nsteps) {
         }
         for (int64_t t = 0; t < nsteps; ++t) CK(cudaGraphLaunch(ctx->graph, ctx->st));
     }
-    for (auto &c : ctx->host_cursor) c += nsteps;
+    for (int s = 0; s < ctx->n_sys; ++s) {
+        const int64_t run = ctx->use_budget ? std::min(nsteps, ctx->remaining_host[s]) : nsteps;
+        ctx->host_cursor[s] += run;
+        if (ctx->use_budget) ctx->remaining_host[s] -= run;
+    }
     return leave(ctx);
 }
 
@@ -1247,6 +1276,7 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->d_sblk);
     dfree(&ctx->d_cell_sys);
     dfree(&ctx->d_mask);
+    dfree(&ctx->d_remaining);
     if (ctx->h_energy) cudaFreeHost(ctx->h_energy);
     if (ctx->h_err) cudaFreeHost(ctx->h_err);
     if (ctx->h_i64) cudaFreeHost(ctx->h_i64);
@@ -1254,6 +1284,290 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     if (ctx->st) cudaStreamDestroy(ctx->st);
     delete ctx;
+    return RBSOG_OK;
+}
+
+}  // extern "C"
+
+// ---- serving engine -------------------------------------------------------------
+// Continuous batching of MD jobs: jobs wait in a FIFO queue, are admitted
+// while a job slot is free and their device-memory footprint fits the budget,
+// and advance together as one batch (one graph launch per step).  A job whose
+// step budget is used up is frozen on the device and retired at the end of
+// the quantum; admissions and retirements rebuild the batch at the next
+// quantum, moving running jobs' state, forces, cursors and k-sequences
+// device-to-device so that no running job is re-sampled or perturbed.
+namespace {
+
+struct Job {
+    int64_t id = 0, n = 0, nsteps = 0, footprint = 0;
+    rbsog_params p{};
+    std::vector<double> q, x, v;           // inputs until admission
+    std::vector<double> xo, vo, fo;        // results after retirement
+    rbsog_energies e{};
+    int32_t status = 0;                    // 0 waiting, 1 running, 2 done
+    int64_t steps_done = 0;
+};
+
+}  // namespace
+
+struct rbsog_server {
+    int device = 0;
+    cudaStream_t user = nullptr;
+    int32_t max_jobs = 64, quantum = 50;
+    int64_t budget = 0, used = 0;
+    std::map<int64_t, Job> jobs;
+    std::vector<int64_t> waiting;     // FIFO
+    std::vector<int64_t> active;      // system order of the current batch
+    rbsog_ctx *batch = nullptr;
+    bool dirty = false;               // retirements since the last rebuild
+    int64_t next_id = 1;
+    std::string err;
+};
+
+namespace {
+
+int64_t footprint_bytes(const Job &j) {
+    // state, cell-ordered copies, cell arrays and staging per particle; the
+    // k-sequence; cells and partial sums
+    int64_t ncell = 1;
+    for (int d = 0; d < 3; ++d) ncell *= (int64_t)std::floor(j.p.L[d] / j.p.r_c);
+    return j.n * 256 + (j.nsteps + 1) * (int64_t)j.p.P * 16 + ncell * 16 + (int64_t)j.p.P * 4096;
+}
+
+rbsog_status srv_fail(rbsog_server *s, rbsog_status st, const std::string &m) {
+    s->err = m;
+    return st;
+}
+
+#define CK_S(srv, call)                                                                 \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) return srv_fail(srv, RBSOG_ECUDA, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Build a batch of `keep` (running, state moved from the old batch) followed
+// by `add` (new, loaded from host); destroy the old batch.
+rbsog_status rebuild(rbsog_server *sv, const std::vector<int64_t> &keep, const std::vector<int64_t> &add) {
+    std::vector<int64_t> order(keep);
+    order.insert(order.end(), add.begin(), add.end());
+    rbsog_ctx *old = sv->batch;
+    if (order.empty()) {
+        if (old) rbsog_destroy(old);
+        sv->batch = nullptr;
+        sv->active.clear();
+        return RBSOG_OK;
+    }
+    std::vector<int64_t> n_per;
+    std::vector<rbsog_params> ps;
+    std::vector<char> sample;
+    for (size_t k = 0; k < order.size(); ++k) {
+        const Job &j = sv->jobs[order[k]];
+        n_per.push_back(j.n);
+        ps.push_back(j.p);
+        sample.push_back(k < keep.size() ? 0 : 1);
+    }
+    rbsog_ctx *nb = nullptr;
+    rbsog_status st = rbsog_batch_create(&nb, (int32_t)order.size(), n_per.data(), sv->device, sv->user);
+    if (st != RBSOG_OK) return srv_fail(sv, st, "batch create failed");
+    rbsog_ctx *ctx = nb;
+    st = set_params_impl(nb, ps.data(), &sample);
+    if (st != RBSOG_OK) {
+        std::string m = nb->err;
+        rbsog_destroy(nb);
+        return srv_fail(sv, st, "set_params: " + m);
+    }
+    nb->use_budget = true;
+    nb->remaining_host.assign(order.size(), 0);
+    CK(dalloc(&nb->d_remaining, order.size()));
+    st = enter(nb);
+    if (st != RBSOG_OK) return st;
+    // running jobs: everything moves device to device
+    std::map<int64_t, int> old_index;
+    for (size_t k = 0; k < sv->active.size(); ++k) old_index[sv->active[k]] = (int)k;
+    if (old) CK(cudaStreamSynchronize(old->st));
+    for (size_t k = 0; k < keep.size(); ++k) {
+        const int o = old_index.at(keep[k]);
+        const SysDesc &od = old->desc[o];
+        const SysDesc &ndsc = nb->desc[k];
+        const int64_t n = od.n;
+        CK(cudaMemcpyAsync(nb->kseq + ndsc.k_off, old->kseq + od.k_off,
+                           sizeof(int4) * old->n_chains[o] * old->chain_len[o], cudaMemcpyDeviceToDevice, nb->st));
+        CK(cudaMemcpyAsync(nb->posq + ndsc.p_off, old->posq + od.p_off, sizeof(double4_32a) * n,
+                           cudaMemcpyDeviceToDevice, nb->st));
+        CK(cudaMemcpyAsync(nb->vel + ndsc.p_off, old->vel + od.p_off, sizeof(double4_32a) * n,
+                           cudaMemcpyDeviceToDevice, nb->st));
+        CK(cudaMemcpyAsync(nb->force + ndsc.p_off, old->force + od.p_off, sizeof(double4_32a) * n,
+                           cudaMemcpyDeviceToDevice, nb->st));
+        CK(cudaMemcpyAsync(nb->cursor + k, old->cursor + o, sizeof(int64_t), cudaMemcpyDeviceToDevice, nb->st));
+        CK(cudaMemcpyAsync(nb->step_ctr + k, old->step_ctr + o, sizeof(int64_t), cudaMemcpyDeviceToDevice, nb->st));
+        CK(cudaMemcpyAsync(nb->energy + k * kNumEnergy, old->energy + (int64_t)o * kNumEnergy,
+                           sizeof(double) * kNumEnergy, cudaMemcpyDeviceToDevice, nb->st));
+        nb->have_state[k] = 1;
+        nb->force_valid[k] = old->force_valid[o];
+        nb->host_cursor[k] = old->host_cursor[o];
+        nb->sum_q2[k] = old->sum_q2[o];
+        nb->desc[k].U_self = self_energy(nb, (int)k);
+        nb->remaining_host[k] = old->remaining_host[o];
+    }
+    st = upload_desc(nb);
+    if (st != RBSOG_OK) return st;
+    CK(cudaMemcpyAsync(nb->d_remaining, nb->remaining_host.data(), sizeof(int64_t) * keep.size(),
+                       cudaMemcpyHostToDevice, nb->st));
+    CK(cudaStreamSynchronize(nb->st));
+    st = leave(nb);
+    if (st != RBSOG_OK) return st;
+    // new jobs: loaded from host; their first step starts with a force evaluation
+    for (size_t k = keep.size(); k < order.size(); ++k) {
+        Job &j = sv->jobs[order[k]];
+        st = rbsog_batch_set_state(nb, (int32_t)k, j.q.data(), j.x.data(), j.v.data());
+        if (st != RBSOG_OK) {
+            std::string m = nb->err;
+            rbsog_destroy(nb);
+            return srv_fail(sv, st, "set_state: " + m);
+        }
+        nb->remaining_host[k] = j.nsteps;
+        *nb->h_i64 = j.nsteps;
+        CK(cudaMemcpyAsync(nb->d_remaining + k, nb->h_i64, sizeof(int64_t), cudaMemcpyHostToDevice, nb->st));
+        CK(cudaStreamSynchronize(nb->st));
+        j.status = 1;
+        std::vector<double>().swap(j.q);
+        std::vector<double>().swap(j.x);
+        std::vector<double>().swap(j.v);
+    }
+    if (old) rbsog_destroy(old);
+    sv->batch = nb;
+    sv->active = order;
+    return RBSOG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rbsog_status rbsog_server_create(rbsog_server **out, int32_t max_jobs, int64_t mem_budget_bytes, int32_t quantum,
+                                 int device, void *stream) {
+    if (!out || max_jobs < 1 || mem_budget_bytes <= 0 || quantum < 1) return RBSOG_EINVAL;
+    rbsog_server *s = new (std::nothrow) rbsog_server();
+    if (!s) return RBSOG_ENOMEM;
+    s->max_jobs = max_jobs;
+    s->budget = mem_budget_bytes;
+    s->quantum = quantum;
+    s->device = device;
+    s->user = (cudaStream_t)stream;
+    *out = s;
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_server_submit(rbsog_server *s, int64_t n, const rbsog_params *p, const double *q,
+                                 const double *x, const double *v, int64_t nsteps, int64_t *job_id) {
+    if (!s || !p || !q || !x || n < 2 || nsteps < 1) return RBSOG_EINVAL;
+    Job j;
+    j.id = s->next_id++;
+    j.n = n;
+    j.nsteps = nsteps;
+    j.p = *p;
+    j.p.n_ksets = nsteps + 1;
+    j.q.assign(q, q + n);
+    j.x.assign(x, x + 3 * n);
+    if (v) j.v.assign(v, v + 3 * n);
+    else j.v.assign(3 * n, 0.0);
+    j.footprint = footprint_bytes(j);
+    if (j.footprint > s->budget) return srv_fail(s, RBSOG_ENOMEM, "job larger than the memory budget");
+    if (job_id) *job_id = j.id;
+    s->waiting.push_back(j.id);
+    s->jobs[j.id] = std::move(j);
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_server_advance(rbsog_server *s, int32_t *n_active, int32_t *n_waiting, int32_t *n_retired) {
+    if (!s) return RBSOG_EINVAL;
+    int32_t retired = 0;
+    // admission: FIFO, by free slots and memory budget
+    std::vector<int64_t> add;
+    while (!s->waiting.empty()) {
+        const int64_t id = s->waiting.front();
+        const Job &j = s->jobs[id];
+        if ((int64_t)(s->active.size() + add.size()) >= s->max_jobs || s->used + j.footprint > s->budget) break;
+        s->used += j.footprint;
+        add.push_back(id);
+        s->waiting.erase(s->waiting.begin());
+    }
+    if (!add.empty() || s->dirty) {
+        std::vector<int64_t> keep;
+        for (int64_t id : s->active)
+            if (s->jobs[id].status == 1) keep.push_back(id);
+        rbsog_status st = rebuild(s, keep, add);
+        if (st != RBSOG_OK) return st;
+        s->dirty = false;
+    }
+    rbsog_ctx *b = s->batch;
+    if (b) {
+        int64_t q = 0;
+        for (int64_t r : b->remaining_host) q = std::max(q, r);
+        q = std::min<int64_t>(q, s->quantum);
+        if (q > 0) {
+            rbsog_status st = rbsog_batch_step(b, q);
+            if (st != RBSOG_OK) return srv_fail(s, st, "step: " + b->err);
+            CK_S(s, cudaStreamSynchronize(b->st));
+        }
+        // retire finished jobs
+        for (size_t k = 0; k < s->active.size(); ++k) {
+            Job &j = s->jobs[s->active[k]];
+            if (j.status != 1 || b->remaining_host[k] != 0) continue;
+            j.xo.resize(3 * j.n);
+            j.vo.resize(3 * j.n);
+            j.fo.resize(3 * j.n);
+            rbsog_status st = rbsog_batch_get_state(b, (int32_t)k, j.xo.data(), j.vo.data(), j.fo.data(),
+                                                    &j.steps_done);
+            if (st != RBSOG_OK) return srv_fail(s, st, "get_state: " + b->err);
+            st = rbsog_batch_get_energies(b, (int32_t)k, &j.e);
+            if (st != RBSOG_OK) return srv_fail(s, st, "energies: " + b->err);
+            j.status = 2;
+            s->used -= j.footprint;
+            s->dirty = true;
+            ++retired;
+        }
+    }
+    int32_t act = 0;
+    for (int64_t id : s->active)
+        if (s->jobs[id].status == 1) ++act;
+    if (n_active) *n_active = act;
+    if (n_waiting) *n_waiting = (int32_t)s->waiting.size();
+    if (n_retired) *n_retired = retired;
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_server_result(rbsog_server *s, int64_t job_id, int32_t *status, double *x, double *v,
+                                 double *f, rbsog_energies *e, int64_t *steps_done) {
+    if (!s) return RBSOG_EINVAL;
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return srv_fail(s, RBSOG_EINVAL, "unknown job");
+    const Job &j = it->second;
+    if (status) *status = j.status;
+    if (j.status != 2) return RBSOG_OK;
+    if (x) std::memcpy(x, j.xo.data(), sizeof(double) * 3 * j.n);
+    if (v) std::memcpy(v, j.vo.data(), sizeof(double) * 3 * j.n);
+    if (f) std::memcpy(f, j.fo.data(), sizeof(double) * 3 * j.n);
+    if (e) *e = j.e;
+    if (steps_done) *steps_done = j.steps_done;
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_server_release(rbsog_server *s, int64_t job_id) {
+    if (!s) return RBSOG_EINVAL;
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end() || it->second.status != 2) return srv_fail(s, RBSOG_EINVAL, "job not finished");
+    s->jobs.erase(it);
+    return RBSOG_OK;
+}
+
+const char *rbsog_server_last_error(const rbsog_server *s) { return s ? s->err.c_str() : "null server"; }
+
+rbsog_status rbsog_server_destroy(rbsog_server *s) {
+    if (!s) return RBSOG_OK;
+    if (s->batch) rbsog_destroy(s->batch);
+    delete s;
     return RBSOG_OK;
 }
 

@@ -128,6 +128,8 @@ struct BatchView {
     const int4 *m_explicit;    // explicit k-set for a batch of one, or null
     const int32_t *force_mask; // [n_sys]: only systems with a non-zero entry take the new
                                // forces, energies and k-set (null: all systems)
+    int64_t *remaining;        // [n_sys] steps left per system; a system at 0 is frozen
+                               // (skipped by every step kernel); null: no budgets
     int32_t max_cap;           // largest near staging chunk of the batch
     int32_t max_tile_p;        // largest rho-sweep tile of the batch
 };
@@ -192,6 +194,8 @@ cudaError_t launch_finalize(const BatchView &bv, const double2 *epart, const dou
                             const Prof *prof);
 cudaError_t launch_rescale(const BatchView &bv, double4_32a *vel, const double *energy, cudaStream_t st,
                            const Prof *prof);
+// With step budgets: one step of every unfrozen system is done.
+cudaError_t launch_step_done(const BatchView &bv, cudaStream_t st, const Prof *prof);
 // Layout conversions between caller [n][3] arrays and the internal double4_32a.
 cudaError_t launch_pack(int64_t n, const double *x3, const double *q, double4_32a *out, int wrap,
                         const double *L, cudaStream_t st);

@@ -137,3 +137,44 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous batching of MD jobs (see rbsog_server_* in rbsog.h): jobs are
+    queued with submit(), admitted while a slot is free and their memory
+    footprint fits, advanced together by advance(), and retired when done."""
+
+    def __init__(self, max_jobs=64, mem_budget_bytes=64 << 30, quantum=50, device: int = 0, stream=None):
+        import torch
+        self.device = int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        self.s = B.rbsog_server_create(max_jobs, mem_budget_bytes, quantum, self.device, stream)
+        self.n_of = {}
+
+    def submit(self, params, q, x, v=None, nsteps=1) -> int:
+        jid = B.rbsog_server_submit(self.s, params, q, x, v, nsteps)
+        self.n_of[jid] = len(q)
+        return jid
+
+    def advance(self):
+        """(active, waiting, retired this call)."""
+        return B.rbsog_server_advance(self.s)
+
+    def result(self, jid):
+        return B.rbsog_server_result(self.s, jid, self.n_of[jid])
+
+    def release(self, jid):
+        B.rbsog_server_release(self.s, jid)
+        self.n_of.pop(jid, None)
+
+    def close(self):
+        if getattr(self, "s", None) is not None:
+            B.rbsog_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
