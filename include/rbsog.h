@@ -258,6 +258,20 @@ rbsog_status rbsog_batch_step(rbsog_batch *b, int64_t nsteps);
  * tuning may differ from untuned ones in the last bits. */
 rbsog_status rbsog_batch_autotune(rbsog_batch *b, int32_t reps, int32_t *chosen);
 
+/* Radial distribution functions (Appendix A) of the current positions of
+ * system `sys` (rbsog_rdf: of the single system), cubic box only.  Pairs at
+ * minimum-image distance r < L/2 are counted once per unordered pair in
+ * counts[3][nbins] by charge-sign pair (row 0: ++, 1: +-, 2: --; neutral
+ * sites are skipped), bin k holding k dr <= r < (k+1) dr, dr = L/(2 nbins).
+ * g[3][nbins] receives the estimate of g(r) = (1/(N_a rho_b)) sum_{i in a}
+ * sum_{j in b, j != i} delta(r_ij - r)/(4 pi r^2), rho_b = N_b / V.
+ * Distances are measured on positions quantised to L 2^-32 per axis, so the
+ * counts are exact integers independent of rounding.  nbins: a power of two
+ * in [16, 4096].  counts and g may be host or device pointers or NULL.
+ * Synchronises.  Cost O(N^2 / 2) pair visits. */
+rbsog_status rbsog_batch_rdf(rbsog_batch *ctx, int32_t sys, int32_t nbins, uint64_t *counts, double *g);
+rbsog_status rbsog_rdf(rbsog_ctx *ctx, int32_t nbins, uint64_t *counts, double *g);
+
 /* ---- Serving engine ---------------------------------------------------------
  * Continuous batching of MD jobs (each: n particles, parameters, initial
  * state, a step count).  Jobs wait in a FIFO queue and are admitted while a

@@ -27,7 +27,7 @@ EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_stat
            "rbsog_get_cursor", "rbsog_restore", "rbsog_rho_noalloc", "rbsog_measure_peaks",
            "rbsog_batch_create", "rbsog_batch_set_params", "rbsog_batch_set_state", "rbsog_batch_restore",
            "rbsog_batch_get_state", "rbsog_batch_get_energies", "rbsog_batch_get_kseq", "rbsog_batch_step",
-           "rbsog_batch_autotune",
+           "rbsog_batch_autotune", "rbsog_batch_rdf", "rbsog_rdf",
            "rbsog_server_create", "rbsog_server_submit", "rbsog_server_advance", "rbsog_server_result",
            "rbsog_server_release", "rbsog_server_last_error", "rbsog_server_destroy",
            "rbsog_get_profile", "rbsog_last_error", "rbsog_destroy")
@@ -97,6 +97,8 @@ def _load():
         "rbsog_batch_get_kseq": [P, C.c_int32, C.c_int64, C.c_int64, P],
         "rbsog_batch_step": [P, C.c_int64],
         "rbsog_batch_autotune": [P, C.c_int32, P],
+        "rbsog_batch_rdf": [P, C.c_int32, C.c_int32, P, P],
+        "rbsog_rdf": [P, C.c_int32, P, P],
         "rbsog_server_create": [C.POINTER(P), C.c_int32, C.c_int64, C.c_int32, C.c_int, P],
         "rbsog_server_submit": [P, C.c_int64, C.POINTER(rbsog_params), P, P, P, C.c_int64,
                                 C.POINTER(C.c_int64)],
@@ -306,6 +308,21 @@ def rbsog_batch_autotune(ctx, reps: int = 3):
     chosen = np.zeros(2, dtype=np.int32)
     _check(ctx, _lib.rbsog_batch_autotune(ctx, int(reps), _ptr(chosen)))
     return {"home": int(chosen[0]), "tile": int(chosen[1])}
+
+
+def rbsog_batch_rdf(ctx, sys: int, nbins: int, counts=None, g=None):
+    """Appendix A pair histograms counts[3, nbins] (uint64; rows ++, +-, --)
+    and g[3, nbins] of system `sys`; allocates host numpy arrays if omitted."""
+    if counts is None:
+        counts = np.zeros((3, nbins), dtype=np.uint64)
+    if g is None:
+        g = np.zeros((3, nbins))
+    _check(ctx, _lib.rbsog_batch_rdf(ctx, int(sys), int(nbins), _ptr(counts), _ptr(g)))
+    return counts, g
+
+
+def rbsog_rdf(ctx, nbins: int, counts=None, g=None):
+    return rbsog_batch_rdf(ctx, 0, nbins, counts, g)
 
 
 def _check_server(s, status):

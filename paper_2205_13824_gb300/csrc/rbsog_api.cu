@@ -1181,6 +1181,38 @@ rbsog_status rbsog_get_cells(rbsog_ctx *ctx, int32_t *cell_start, int32_t *perm,
     return leave(ctx);
 }
 
+rbsog_status rbsog_batch_rdf(rbsog_batch *ctx, int32_t sys, int32_t nbins, uint64_t *counts, double *g) {
+    if (!ctx) return RBSOG_EINVAL;
+    rbsog_status es = check_sys(ctx, sys);
+    if (es != RBSOG_OK) return es;
+    if (!ctx->have_params || !ctx->have_state[sys]) return fail(ctx, RBSOG_ESTATE, "params and state required");
+    if (nbins < 16 || nbins > 4096 || (nbins & (nbins - 1)))
+        return fail(ctx, RBSOG_EINVAL, "nbins must be a power of two in [16, 4096]");
+    const double *L = ctx->p[sys].L;
+    if (L[0] != L[1] || L[0] != L[2]) return fail(ctx, RBSOG_EINVAL, "the RDF needs a cubic box");
+    es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    const int64_t n = ctx->n_per[sys];
+    unsigned long long *d_counts = nullptr;
+    double *d_g = nullptr;
+    const size_t nc = 3 * (size_t)nbins;
+    CK(cudaMallocAsync((void **)&d_counts, sizeof(unsigned long long) * (nc + 2), ctx->st));
+    CK(cudaMallocAsync((void **)&d_g, sizeof(double) * nc, ctx->st));
+    // the staging buffer (24 bytes per particle) holds the packed uint4 sites
+    CK(launch_rdf(n, ctx->posq + ctx->p_off[sys], L[0], nbins, reinterpret_cast<uint4 *>(ctx->staging), d_counts,
+                  d_counts + nc, d_g, ctx->st, prof_of(ctx)));
+    if (counts) CK(cudaMemcpyAsync(counts, d_counts, sizeof(uint64_t) * nc, cudaMemcpyDefault, ctx->st));
+    if (g) CK(cudaMemcpyAsync(g, d_g, sizeof(double) * nc, cudaMemcpyDefault, ctx->st));
+    CK(cudaFreeAsync(d_counts, ctx->st));
+    CK(cudaFreeAsync(d_g, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return leave(ctx);
+}
+
+rbsog_status rbsog_rdf(rbsog_ctx *ctx, int32_t nbins, uint64_t *counts, double *g) {
+    return rbsog_batch_rdf(ctx, 0, nbins, counts, g);
+}
+
 rbsog_status rbsog_set_profiling(rbsog_ctx *ctx, int on) {
     if (!ctx) return RBSOG_EINVAL;
     CK(cudaSetDevice(ctx->device));

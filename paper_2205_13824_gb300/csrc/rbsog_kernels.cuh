@@ -204,4 +204,15 @@ cudaError_t launch_unsort_i32(int64_t n, int64_t off, const int32_t *perm, const
                               int32_t *out, cudaStream_t st);
 cudaError_t launch_m_to_int4(int32_t P, const int32_t *m3, int4 *out, cudaStream_t st);
 
+// ---- radial distribution functions (k_rdf.cu) --------------------------------
+// Sign-pair histograms counts[3][nbins] (++, +-, --) of minimum-image pair
+// distances on [0, L/2) for n particles posq[0..n) of a cubic box of edge L,
+// nbins a power of two in [16, 4096]; nspec[2] receives the numbers of
+// positive and negative sites; g[3][nbins] (optional) the Appendix A estimate.
+// pt is scratch of n uint4.
+cudaError_t launch_rdf(int64_t n, const double4_32a *posq, double L, int32_t nbins, uint4 *pt,
+                       unsigned long long *counts, unsigned long long *nspec, double *g, cudaStream_t st,
+                       const Prof *prof);
+
 }  // namespace rbsog
+

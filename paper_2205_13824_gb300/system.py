@@ -73,6 +73,10 @@ class RBSOG:
     def energies(self):
         return B.rbsog_get_energies(self.ctx)
 
+    def rdf(self, nbins: int = 256):
+        """(counts[3, nbins], g[3, nbins]) by sign pair ++, +-, -- on [0, L/2)."""
+        return B.rbsog_rdf(self.ctx, nbins)
+
     def kseq(self, set0: int, nsets: int):
         import numpy as np
         out = np.zeros((nsets * self.params.P, 3), dtype=np.int32)
@@ -126,6 +130,9 @@ class Batch:
 
     def energies(self, sys):
         return B.rbsog_batch_get_energies(self.ctx, sys)
+
+    def rdf(self, sys, nbins: int = 256):
+        return B.rbsog_batch_rdf(self.ctx, sys, nbins)
 
     def close(self):
         if getattr(self, "ctx", None) is not None:
