@@ -6,12 +6,13 @@
 //   scan     two launches: per-tile warp-shuffle scans, then tile offsets
 //            (the counters are cleared for the next build);
 //   scatter  one thread per particle: perm_raw[start + slot] = i;
-//   order    one warp per cell: ranks the cell's members by particle index
-//            (indices exchanged by warp shuffles)
-//            (so the order inside a cell, and everything summed in that
-//            order, is deterministic) and gathers the particle data into
-//            cell order -- FP64 (x, y, z, q) or, for the FP32C path, 32-bit
-//            fixed-point positions X_d = floor(x_d / L_d * 2^32) with an FP32
+//   order    one warp per cell: ranks the cell's members by (fixed-point x,
+//            particle index) (keys exchanged by warp shuffles), so the order
+//            inside a cell -- and everything summed in that order -- is
+//            deterministic, and an x-row of cells is sorted in x (the near
+//            field searches it); then gathers the particle data into cell
+//            order -- FP64 (x, y, z, q) or, for the FP32C path, 32-bit
+//            fixed-point positions X_d = trunc(x_d * (2^32 / L_d)) with an FP32
 //            charge.
 #include "rbsog_kernels.cuh"
 
@@ -118,14 +119,16 @@ __global__ void __launch_bounds__(256) k_scatter(int64_t n, const int32_t *__res
     perm_raw[start[cell_of[i]] + slot[i]] = (int32_t)i;
 }
 
-__device__ __forceinline__ uint32_t to_fixed32(double x, double L) {
-    const double t = x / L * 4294967296.0;
+// X = trunc(x * (2^32 / L)) clamped to [0, 2^32 - 1]: one FP64 multiply (the
+// scale is computed once on the host), not a division per coordinate.
+__device__ __forceinline__ uint32_t to_fixed32(double x, double inv) {
+    const double t = x * inv;
     const double c = t < 0.0 ? 0.0 : (t > 4294967295.0 ? 4294967295.0 : t);
     return (uint32_t)__double2ull_rz(c);
 }
 
-// One warp per cell: rank = number of members with a smaller particle index
-// (the members' indices are exchanged by shuffles for cells of up to 32).
+// One warp per cell: rank = number of members with a smaller key
+// (X << 32 | index) (keys exchanged by shuffles for cells of up to 32).
 __global__ void __launch_bounds__(256) k_order_gather(BatchView bv, const int32_t *__restrict__ start,
                                                       const int32_t *__restrict__ perm_raw,
                                                       int32_t *__restrict__ perm,
@@ -139,23 +142,32 @@ __global__ void __launch_bounds__(256) k_order_gather(BatchView bv, const int32_
     for (int t0 = 0; t0 < cnt; t0 += 32) {
         const int t = t0 + lane;
         const int idx = t < cnt ? perm_raw[b + t] : 0x7fffffff;
+        double4_32a p{};
+        unsigned long long key = ~0ull;
+        if (t < cnt) {
+            p = posq[idx];
+            key = ((unsigned long long)to_fixed32(p.x, box.fix_inv[0]) << 32) | (uint32_t)idx;
+        }
         int rank = 0;
         if (cnt <= 32) {
-            for (int u = 0; u < cnt; ++u) rank += (__shfl_sync(0xffffffffu, idx, u) < idx) ? 1 : 0;
+            for (int u = 0; u < cnt; ++u) rank += (__shfl_sync(0xffffffffu, key, u) < key) ? 1 : 0;
         } else {
-            for (int u = 0; u < cnt; ++u) rank += (perm_raw[b + u] < idx) ? 1 : 0;
+            for (int u = 0; u < cnt; ++u) {
+                const int j = perm_raw[b + u];
+                const unsigned long long kj = ((unsigned long long)to_fixed32(posq[j].x, box.fix_inv[0]) << 32) | (uint32_t)j;
+                rank += kj < key ? 1 : 0;
+            }
         }
         if (t < cnt) {
             const int s = b + rank;
             perm[s] = idx;
-            const double4_32a p = posq[idx];
             if (precision == 0) {
                 sp64[s] = p;
             } else {
                 uint4 o;
-                o.x = to_fixed32(p.x, box.L[0]);
-                o.y = to_fixed32(p.y, box.L[1]);
-                o.z = to_fixed32(p.z, box.L[2]);
+                o.x = to_fixed32(p.x, box.fix_inv[0]);
+                o.y = to_fixed32(p.y, box.fix_inv[1]);
+                o.z = to_fixed32(p.z, box.fix_inv[2]);
                 o.w = __float_as_uint((float)p.w);
                 sp32[s] = o;
             }

@@ -40,7 +40,8 @@ namespace {
 constexpr int kThreads = 128;   // one home particle per thread
 constexpr int kMaxGroup = 16;
 constexpr int kMaxStaged = 9 * (kMaxGroup + 2);
-constexpr int kList32 = 64;     // partner-list entries per thread, FP32C (uint16)
+constexpr int kList32 = 64;     // partner-list entries per thread, FP32C (uint16), plus one spare slot
+constexpr int kMaxHome = 1024;  // home particles a block can reorder (more: cell order is kept)
 constexpr int kList64 = 64;     // partner-list entries per thread, FP64 (int32: index | shift code)
 
 __device__ __forceinline__ int wrap_cell(int c, int n, int &shift) {
@@ -153,7 +154,7 @@ struct PairConst {
     real rc2, wrc2, ws2, weps, lB;
 };
 
-template <int PREC, int ND, int NT>
+template <int PREC, int ND, int NT, bool WIN>
 __global__ void __launch_bounds__(kThreads, 4)
     k_near(const BatchView bv, const __grid_constant__ NearSog sog, const int32_t *__restrict__ start,
            const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
@@ -168,6 +169,8 @@ __global__ void __launch_bounds__(kThreads, 4)
     __shared__ int s_src[kMaxStaged];
     __shared__ int s_shift[kMaxStaged];
     __shared__ int s_hstart[kMaxGroup + 1];
+    __shared__ float4 s_tab[ND < 0 ? 2 * kTabN : 1];   // Gaussian-sum tables (ND < 0)
+    __shared__ uint16_t s_hord[WIN ? kMaxHome : 1];    // home particles in quadrant order (WIN)
     extern __shared__ __align__(32) unsigned char smem_raw[];
     // disjoint regions: restrict lets the compiler move staged loads across
     // list stores
@@ -201,6 +204,8 @@ __global__ void __launch_bounds__(kThreads, 4)
         s_shift[k] = (shx + 1) | ((shy + 1) << 2) | ((shz + 1) << 4);
     }
     if (tid <= nh) s_hstart[tid] = start[coff + (cz * ny + cy) * nx + x0 + tid];
+    if constexpr (ND < 0)
+        for (int k = tid; k < 2 * kTabN; k += kThreads) s_tab[k] = k < kTabN ? sog.tab_g[k] : sog.tab_f[k - kTabN];
     if (tid == 0) s_off[0] = 0;
     __syncthreads();
     if (wid == 0) {  // inclusive scan of counts into offsets, 32 at a time
@@ -221,13 +226,52 @@ __global__ void __launch_bounds__(kThreads, 4)
     const int total = s_off[ns];
     const int hb = s_hstart[0], he = s_hstart[nh];
 
-    uint32_t ox = 0, oy = 0, oz = 0;   // FP32C origin: centre of the home segment
+    // FP32C origin: centre of the home segment (to FP32 rounding, a few 1e-6
+    // of a cell side -- any common origin gives the same offsets' differences)
+    uint32_t ox = 0, oy = 0, oz = 0;
     if constexpr (PREC == 1) {
-        ox = (uint32_t)(uint64_t)(((double)x0 + 0.5 * nh) * box.h[0] / box.L[0] * 4294967296.0);
-        oy = (uint32_t)(uint64_t)(((double)cy + 0.5) * box.h[1] / box.L[1] * 4294967296.0);
-        oz = (uint32_t)(uint64_t)(((double)cz + 0.5) * box.h[2] / box.L[2] * 4294967296.0);
+        ox = (uint32_t)__float2ull_rn(((float)x0 + 0.5f * (float)nh) * box.cell_fix[0]);
+        oy = (uint32_t)__float2ull_rn(((float)cy + 0.5f) * box.cell_fix[1]);
+        oz = (uint32_t)__float2ull_rn(((float)cz + 0.5f) * box.cell_fix[2]);
     }
     const float fsx = box.fix_scale[0], fsy = box.fix_scale[1], fsz = box.fix_scale[2];
+    // WIN: the warps take the home particles grouped by the quadrant of their
+    // cell's y-z square they sit in (stable within a quadrant, so in x order),
+    // so that a warp's lanes see similar row gaps and similar window lengths.
+    // The grouping is a deterministic stable counting sort done by warp 0.
+    const int nhome = he - hb;
+    const bool reord = WIN && nhome <= kMaxHome;
+    if constexpr (WIN) {
+        if (reord && wid == 0) {
+            auto quad = [&](int p) {
+                if (p >= nhome) return 4;
+                const uint4 uq = sp32[hb + p];
+                return (fixed_offset(uq.y, oy, fsy) > 0.f ? 1 : 0) | (fixed_offset(uq.z, oz, fsz) > 0.f ? 2 : 0);
+            };
+            int o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+            for (int p0 = 0; p0 < nhome; p0 += 32) {
+                const int k = quad(p0 + lane);
+                o1 += __popc(__ballot_sync(0xffffffffu, k == 0));
+                o2 += __popc(__ballot_sync(0xffffffffu, k == 1));
+                o3 += __popc(__ballot_sync(0xffffffffu, k == 2));
+            }
+            o2 += o1;   // exclusive offsets of quadrants 1, 2, 3
+            o3 += o2;
+            const unsigned lt = (1u << lane) - 1u;
+            for (int p0 = 0; p0 < nhome; p0 += 32) {
+                const int p = p0 + lane, k = quad(p);
+                const unsigned m0 = __ballot_sync(0xffffffffu, k == 0), m1 = __ballot_sync(0xffffffffu, k == 1);
+                const unsigned m2 = __ballot_sync(0xffffffffu, k == 2), m3 = __ballot_sync(0xffffffffu, k == 3);
+                const unsigned mk = k == 0 ? m0 : k == 1 ? m1 : k == 2 ? m2 : m3;
+                const int ok = k == 0 ? o0 : k == 1 ? o1 : k == 2 ? o2 : o3;
+                if (p < nhome) s_hord[ok + __popc(mk & lt)] = (uint16_t)p;
+                o0 += __popc(m0);
+                o1 += __popc(m1);
+                o2 += __popc(m2);
+                o3 += __popc(m3);
+            }
+        }
+    }
     PairConst<real> pc;
     if constexpr (PREC == 0) {
         pc = PairConst<real>{box.rc2, box.wca_rc2, box.wca_s2, box.wca_eps, box.lB};
@@ -264,8 +308,9 @@ __global__ void __launch_bounds__(kThreads, 4)
         }
         __syncthreads();
         for (int rb = hb + 32 * wid; rb < he; rb += kThreads) {
-            const int hi = rb + lane;
-            const bool active = hi < he;
+            const int pidx = rb - hb + lane;
+            const bool active = pidx < nhome;
+            const int hi = active ? hb + (reord ? (int)s_hord[pidx] : pidx) : he;
             int cxr = 0;
             while (cxr + 1 < nh && s_hstart[cxr + 1] <= (active ? hi : he - 1)) ++cxr;
             // the warp's lanes cover home cells cx_lo..cx_hi (particles are in
@@ -321,7 +366,17 @@ __global__ void __launch_bounds__(kThreads, 4)
                     }
                     const real qq = pc.lB * qi * qj;
                     real fs, gs;
-                    PM::gauss(sog, r2, fs, gs);
+                    if constexpr (ND < 0) {
+                        // piecewise cubic in r^2 (interval k, local s in [0, 1))
+                        const float x = r2 * sog.tab_scale;
+                        const int k = min((int)x, kTabN - 1);
+                        const float sl = x - (float)k;
+                        const float4 cg = s_tab[k], cf = s_tab[kTabN + k];
+                        gs = fmaf(fmaf(fmaf(cg.w, sl, cg.z), sl, cg.y), sl, cg.x);
+                        fs = fmaf(fmaf(fmaf(cf.w, sl, cf.z), sl, cf.y), sl, cf.x);
+                    } else {
+                        PM::gauss(sog, r2, fs, gs);
+                    }
                     const real inv_r = PM::inv_sqrt(r2);
                     real g = qq * (inv_r * inv_r * inv_r - (real)2 * gs);
                     un += (real)0.5 * qq * (inv_r - fs);
@@ -338,6 +393,72 @@ __global__ void __launch_bounds__(kThreads, 4)
                 cnt += n;
                 n = 0;
             };
+            if constexpr (WIN) {
+                // Per-lane windows.  Every staged row is sorted in x (cells
+                // in x order, members by x), so the candidates of lane i in
+                // row (dy, dz) are the contiguous run with |x_j - x_i| <= b,
+                // b^2 = r_c^2 - (y gap)^2 - (z gap)^2 from the row's y/z
+                // extent; it is found by binary search in the two cells that
+                // hold its ends.  The margin (far above FP32 rounding of the
+                // offsets) keeps the run a superset of the partners; the
+                // distance test below decides.
+                constexpr float kMargin = 1e-3f;
+                constexpr int kChunk = 8;
+                const float hx = box.h_f[0], hy = box.h_f[1], hz = box.h_f[2];
+                const float inv_hx = 1.0f / hx, xbase = 1.0f + 0.5f * (float)nh;
+#pragma unroll 1
+                for (int r = 0; r < 9; ++r) {
+                    const int dyr = r % 3 - 1, dzr = r / 3 - 1;
+                    int lo = 0, len = 0;
+                    if (active) {
+                        const float gy = dyr == 0 ? 0.f
+                                                  : fmaxf((dyr < 0 ? iy + 0.5f * hy : 0.5f * hy - iy) - kMargin, 0.f);
+                        const float gz = dzr == 0 ? 0.f
+                                                  : fmaxf((dzr < 0 ? iz + 0.5f * hz : 0.5f * hz - iz) - kMargin, 0.f);
+                        const float b2 = pc.rc2 - gy * gy - gz * gz;
+                        if (b2 > 0.f) {
+                            const float bb = sqrtf(b2) + kMargin;
+                            const float xl = ix - bb, xr = ix + bb;
+                            const int k0 = r * w;
+                            const int cl = min(max((int)floorf(fmaf(xl, inv_hx, xbase)), 0), w - 1);
+                            const int ch = min(max((int)floorf(fmaf(xr, inv_hx, xbase)), 0), w - 1);
+                            int a = max(s_off[k0 + cl], c0), e = min(s_off[k0 + cl + 1], c1);
+                            while (a < e) {   // first x >= xl
+                                const int m = (a + e) >> 1;
+                                if (st[m - c0].x < xl) a = m + 1; else e = m;
+                            }
+                            lo = a;
+                            a = max(s_off[k0 + ch], c0);
+                            e = min(s_off[k0 + ch + 1], c1);
+                            while (a < e) {   // first x > xr
+                                const int m = (a + e) >> 1;
+                                if (st[m - c0].x <= xr) a = m + 1; else e = m;
+                            }
+                            len = max(a - lo, 0);
+                        }
+                    }
+                    const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+                    for (int it = 0; it < maxlen; it += kChunk) {
+                        const int m = len - it;
+                        if (__any_sync(0xffffffffu, n + min(max(m, 0), kChunk) > kList)) compute();
+                        const int tb = lo + it - c0;
+                        // branch-free append: every slot writes list entry n
+                        // (one spare slot past kList), only partners advance n;
+                        // the particle itself has r^2 = 0 exactly (identical
+                        // offsets) and is not counted
+#pragma unroll
+                        for (int uu = 0; uu < kChunk; ++uu) {
+                            const bool in = uu < m;
+                            const int t = in ? tb + uu : 0;   // staged slot 0 exists whenever maxlen > 0
+                            const float4 pj = st[t];
+                            const float dx = ix - pj.x, dy = iy - pj.y, dz = iz - pj.z;
+                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                            list[n * kThreads + tid] = (entry)t;
+                            n += (in && r2 < pc.rc2 && r2 > 0.f) ? 1 : 0;
+                        }
+                    }
+                }
+            } else
             for (int r = 0; r < 9; ++r) {
                 const int kb = r * w + cx_lo, ke = r * w + cx_hi + 3;   // staged cells [kb, ke)
                 const int lo = max(s_off[kb], c0), hi3 = min(s_off[ke], c1);
@@ -404,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 4)
 
 size_t near_smem(int precision, int cap) {
     if (precision == 0) return sizeof(double4_32a) * (size_t)cap + sizeof(int32_t) * kList64 * kThreads;
-    return sizeof(float4) * (size_t)cap + sizeof(uint16_t) * kList32 * kThreads;
+    return sizeof(float4) * (size_t)cap + sizeof(uint16_t) * (kList32 + 1) * kThreads;
 }
 
 }  // namespace
@@ -434,18 +555,23 @@ cudaError_t launch_near(int precision, const BatchView &bv, const NearSog &sog, 
     // gives 5 exp Gaussians below 2 r_c and 8 (FP32) / 12 (FP64) Taylor terms
     // for any r_c; other parameter sets take the runtime-count variant
     const bool spec = sog.n_direct == 5 && (precision == 1 ? sog.n_taylor_f == 8 : sog.n_taylor == 12);
+    // FP32C evaluates the Gaussian sums from the piecewise-cubic tables when
+    // they are accurate to FP32 rounding (any SOG set whose narrowest Gaussian
+    // is wide against the table step); otherwise exp + Taylor as FP64 does
+    const bool tab = precision == 1 && sog.tab_err < 4e-7f;
     ProfScope ps(prof, precision == 0 ? (spec ? "near_fp64" : "near_fp64_generic")
-                                      : (spec ? "near_fp32c" : "near_fp32c_generic"));
+                                      : (tab ? "near_fp32c" : spec ? "near_fp32c_direct" : "near_fp32c_generic"));
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         kern<<<bv.n_nblk, kThreads, sm, st>>>(bv, sog, start, sp64, sp32, fnear, epart, nbr);
     };
     if (precision == 1) {
-        if (spec) go(k_near<1, 5, 8>);
-        else go(k_near<1, 0, 0>);
+        if (tab) go(k_near<1, -1, 0, true>);
+        else if (spec) go(k_near<1, 5, 8, false>);
+        else go(k_near<1, 0, 0, false>);
     } else {
-        if (spec) go(k_near<0, 5, 12>);
-        else go(k_near<0, 0, 0>);
+        if (spec) go(k_near<0, 5, 12, false>);
+        else go(k_near<0, 0, 0, false>);
     }
     return cudaGetLastError();
 }

@@ -65,7 +65,11 @@ __global__ void k_clock(int iters, long long *out) {
     unsigned long long t0;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     float x = 1.0f;
+    // empty volatile asm statements tie the loop between the timer reads
+    // (volatile asm is not reordered against volatile asm)
+    asm volatile("" : "+f"(x));
     for (int i = 0; i < iters; ++i) x = fmaf(x, 0.9999f, 1e-4f);
+    asm volatile("" : "+f"(x));
     long long c1 = clock64();
     unsigned long long t1;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));

@@ -1,7 +1,7 @@
 // Frequency sampler of the random batch (Sec. 3.3, Eqs. 3.18-3.22) and the
 // pre-sampled sequence of Algorithm 1 (line 2), run as independent
 // Metropolis-Hastings chains (the paper's parallel sampling, Sec. 3.4), one
-// chain per thread.
+// chain per block.
 //
 // This translation unit is compiled with -fmad=false: every floating-point
 // expression below rounds after each operation, so that the accept/reject
@@ -70,12 +70,62 @@ __device__ double proposal_mass(int m, double s0, double Ld) {
 // acceptance uniform).  The first non-zero proposal starts the chain; after
 // that each iteration emits the post-decision state.  Zero proposals are
 // rejections (p(0) = 0).
-__global__ void __launch_bounds__(128) k_mh_chain(const __grid_constant__ SamplerDev sp, const SamplerSys *__restrict__ sys, int n_sys,
-                                                  int64_t total_chains, int4 *__restrict__ kseq,
-                                                  int32_t *__restrict__ err_flag) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+//
+// The proposals of an independence sampler do not depend on the chain's
+// state, so one block runs one chain in rounds of kRound iterations: every
+// thread draws one iteration's proposal and evaluates its target and proposal
+// masses (the expensive FP64 part) in parallel, then one thread walks the
+// round's iterations in order and takes the accept/reject decisions from the
+// stored values -- the same values and the same expression as a serial
+// chain, so the emitted sequence is identical to it.
+constexpr int kRound = 256;
+
+struct Draw {
+    int4 m;        // proposal; w = 1 if it is the zero mode
+    double p, q;   // target and proposal masses (0 for the zero mode)
+    double u;      // acceptance uniform
+};
+
+__device__ Draw draw(const SamplerDev &sp, const SamplerSys &y, int64_t c, int64_t j, const double sd[3]) {
+    uint64_t ra[4] = {(uint64_t)j, 0, 0, 0};
+    uint64_t rb[4] = {(uint64_t)j, 1, 0, 0};
+    philox4x64_10(ra, y.seed, (uint64_t)c);
+    philox4x64_10(rb, y.seed, (uint64_t)c);
+    const double r01 = sqrt(-2.0 * log(1.0 - unit53(ra[0])));
+    const double r23 = sqrt(-2.0 * log(1.0 - unit53(ra[2])));
+    double z[3];
+    z[0] = r01 * cos(2.0 * kPi * unit53(ra[1]));
+    z[1] = r01 * sin(2.0 * kPi * unit53(ra[1]));
+    z[2] = r23 * cos(2.0 * kPi * unit53(ra[3]));
+    int mp[3];
+    for (int d = 0; d < 3; ++d) mp[d] = (int)round(z[d] * sd[d]);
+    Draw o;
+    const bool zero = (mp[0] == 0 && mp[1] == 0 && mp[2] == 0);
+    o.m = make_int4(mp[0], mp[1], mp[2], zero ? 1 : 0);
+    o.u = unit53(rb[0]);
+    if (zero) {
+        o.p = o.q = 0.0;
+    } else {
+        const double s0 = sp.s[0];
+        o.p = target_mass(sp, y.L, mp[0], mp[1], mp[2]);
+        o.q = proposal_mass(mp[0], s0, y.L[0]) * proposal_mass(mp[1], s0, y.L[1]) *
+              proposal_mass(mp[2], s0, y.L[2]);
+    }
+    return o;
+}
+
+__global__ void __launch_bounds__(kRound) k_mh_chain(const __grid_constant__ SamplerDev sp,
+                                                     const SamplerSys *__restrict__ sys, int n_sys,
+                                                     int64_t total_chains, int4 *__restrict__ kseq,
+                                                     int32_t *__restrict__ err_flag) {
+    __shared__ Draw s_draw[kRound];
+    __shared__ int4 s_out[kRound];
+    __shared__ int s_nout, s_done;
+    __shared__ int64_t s_base;
+    const int tid = threadIdx.x;
+    const int64_t g = blockIdx.x;   // global chain
     if (g >= total_chains) return;
-    int lo = 0, hi = n_sys;   // system of global chain g: largest lo with chain_off <= g
+    int lo = 0, hi = n_sys;         // system of global chain g: largest lo with chain_off <= g
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         if (sys[mid].chain_off <= g) lo = mid; else hi = mid;
@@ -88,57 +138,55 @@ __global__ void __launch_bounds__(128) k_mh_chain(const __grid_constant__ Sample
     const int64_t len = y.chain_len;
     const int64_t cap = 64 * len + 4096;
     int4 *out = kseq + y.k_off + c * len;
-    const uint64_t seed = y.seed;
-    const double *L = y.L;
-    int cur[3] = {0, 0, 0};
+    // serial state, held by thread 0
+    int4 cur = make_int4(0, 0, 0, 0);
     double p_cur = 0.0, q_cur = 0.0;
     bool have = false;
-    int64_t emitted = 0, j = 0;
-    while (emitted < len) {
-        if (j >= cap) {  // bounded: a chain that cannot start reports and stops
-            atomicOr(err_flag, 2);
-            for (; emitted < len; ++emitted) out[emitted] = make_int4(0, 0, 0, 0);
-            return;
-        }
-        uint64_t ra[4] = {(uint64_t)j, 0, 0, 0};
-        uint64_t rb[4] = {(uint64_t)j, 1, 0, 0};
-        philox4x64_10(ra, seed, (uint64_t)c);
-        philox4x64_10(rb, seed, (uint64_t)c);
-        const double r01 = sqrt(-2.0 * log(1.0 - unit53(ra[0])));
-        const double r23 = sqrt(-2.0 * log(1.0 - unit53(ra[2])));
-        double z[3];
-        z[0] = r01 * cos(2.0 * kPi * unit53(ra[1]));
-        z[1] = r01 * sin(2.0 * kPi * unit53(ra[1]));
-        z[2] = r23 * cos(2.0 * kPi * unit53(ra[3]));
-        int mp[3];
-        for (int d = 0; d < 3; ++d) mp[d] = (int)round(z[d] * sd[d]);
-        const bool zero = (mp[0] == 0 && mp[1] == 0 && mp[2] == 0);
-        ++j;
-        if (!have) {
-            if (zero) continue;
-            cur[0] = mp[0];
-            cur[1] = mp[1];
-            cur[2] = mp[2];
-            p_cur = target_mass(sp, L, cur[0], cur[1], cur[2]);
-            q_cur = proposal_mass(cur[0], s0, L[0]) * proposal_mass(cur[1], s0, L[1]) *
-                    proposal_mass(cur[2], s0, L[2]);
-            have = true;
-        } else if (!zero) {
-            const double p_new = target_mass(sp, L, mp[0], mp[1], mp[2]);
-            const double q_new = proposal_mass(mp[0], s0, L[0]) *
-                                 proposal_mass(mp[1], s0, L[1]) *
-                                 proposal_mass(mp[2], s0, L[2]);
-            const double ratio = (p_new * q_cur) / (p_cur * q_new);
-            if (unit53(rb[0]) < ratio) {
-                cur[0] = mp[0];
-                cur[1] = mp[1];
-                cur[2] = mp[2];
-                p_cur = p_new;
-                q_cur = q_new;
+    int64_t emitted = 0;
+    for (int64_t j0 = 0;; j0 += kRound) {
+        const int64_t j = j0 + tid;
+        if (j < cap) s_draw[tid] = draw(sp, y, c, j, sd);
+        __syncthreads();
+        if (tid == 0) {
+            int nout = 0, done = 0;
+            for (int k = 0; k < kRound && emitted < len; ++k) {
+                if (j0 + k >= cap) {   // bounded: a chain that cannot start reports and stops
+                    atomicOr(err_flag, 2);
+                    done = 2;
+                    break;
+                }
+                const Draw &dr = s_draw[k];
+                const bool zero = dr.m.w != 0;
+                if (!have) {
+                    if (zero) continue;
+                    cur = make_int4(dr.m.x, dr.m.y, dr.m.z, 0);
+                    p_cur = dr.p;
+                    q_cur = dr.q;
+                    have = true;
+                } else if (!zero) {
+                    const double ratio = (dr.p * q_cur) / (p_cur * dr.q);
+                    if (dr.u < ratio) {
+                        cur = make_int4(dr.m.x, dr.m.y, dr.m.z, 0);
+                        p_cur = dr.p;
+                        q_cur = dr.q;
+                    }
+                }
+                s_out[nout++] = cur;
+                ++emitted;
             }
+            if (emitted >= len && !done) done = 1;
+            s_nout = nout;
+            s_done = done;
+            s_base = emitted - nout;
         }
-        out[emitted] = make_int4(cur[0], cur[1], cur[2], 0);
-        ++emitted;
+        __syncthreads();
+        const int nout = s_nout, done = s_done;
+        const int64_t base = s_base;
+        if (tid < nout) out[base + tid] = s_out[tid];
+        if (done == 2)   // zero-fill what the stopped chain did not emit
+            for (int64_t e = base + nout + tid; e < len; e += kRound) out[e] = make_int4(0, 0, 0, 0);
+        if (done) break;
+        __syncthreads();   // s_draw / s_out are reused by the next round
     }
 }
 
@@ -148,9 +196,7 @@ cudaError_t launch_mh_sampler(const SamplerDev &sp, const SamplerSys *sys, int n
                               int4 *kseq, int32_t *err_flag, cudaStream_t st, const Prof *prof) {
     if (total_chains <= 0) return cudaSuccess;
     ProfScope ps(prof, "mh_sampler");
-    const int threads = 64;   // chains are long serial FP64 loops: spread them over many SMs
-    const int64_t blocks = (total_chains + threads - 1) / threads;
-    k_mh_chain<<<(unsigned)blocks, threads, 0, st>>>(sp, sys, n_sys, total_chains, kseq, err_flag);
+    k_mh_chain<<<(unsigned)total_chains, kRound, 0, st>>>(sp, sys, n_sys, total_chains, kseq, err_flag);
     return cudaGetLastError();
 }
 

@@ -222,7 +222,7 @@ double c1_defect(double b, double sigma, double rc) {
 
 // Solve sigma on a log grid + bisection; choose the root whose w_0 is
 // closest to the bilateral-series weight.
-bool solve_sigma(double b, double rc, double &sigma, double &w0) {
+bool solve_sigma_uncached(double b, double rc, double &sigma, double &w0) {
     const int ngrid = 2400;
     const double lo = 0.04 * rc, hi = 2.5 * rc;
     double best = -1.0, best_dev = 1e300;
@@ -255,6 +255,28 @@ bool solve_sigma(double b, double rc, double &sigma, double &w0) {
     if (best < 0) return false;
     sigma = best;
     w0 = c0_weight(b, best, rc);
+    return true;
+}
+
+// The solve costs a few tens of milliseconds (thousands of untruncated series
+// evaluations); its result depends on (b, r_c) only and is remembered for the
+// process, so contexts that are rebuilt often (the serving engine) pay once.
+std::mutex g_sigma_mu;
+std::map<std::pair<double, double>, std::pair<double, double>> g_sigma;
+
+bool solve_sigma(double b, double rc, double &sigma, double &w0) {
+    {
+        std::lock_guard<std::mutex> lk(g_sigma_mu);
+        auto it = g_sigma.find({b, rc});
+        if (it != g_sigma.end()) {
+            sigma = it->second.first;
+            w0 = it->second.second;
+            return true;
+        }
+    }
+    if (!solve_sigma_uncached(b, rc, sigma, w0)) return false;
+    std::lock_guard<std::mutex> lk(g_sigma_mu);
+    g_sigma[{b, rc}] = {sigma, w0};
     return true;
 }
 
@@ -328,6 +350,70 @@ void build_near_sog(NearSog &ns, const std::vector<double> &omega, const std::ve
             ns.tay_g_f[n] = (float)ns.tay_g[n];
         }
     }
+}
+
+// Interpolating cubic through Chebyshev nodes of each table interval, in
+// monomial form in the interval's local coordinate s in [0, 1).  For the
+// production set the largest error (relative to G(0) and F(0)) is at FP32
+// rounding level; it is recorded in tab_err.
+void build_sog_tables(NearSog &ns, const std::vector<double> &omega, const std::vector<double> &s, int M,
+                      double rc) {
+    const double du = rc * rc / kTabN;
+    auto G = [&](double uu) {
+        double v = 0.0;
+        for (int l = M; l >= 0; --l) v += omega[l] / (s[l] * s[l]) * std::exp(-uu / (s[l] * s[l]));
+        return v;
+    };
+    auto F = [&](double uu) {
+        double v = 0.0;
+        for (int l = M; l >= 0; --l) v += omega[l] * std::exp(-uu / (s[l] * s[l]));
+        return v;
+    };
+    double sn[4];
+    for (int j = 0; j < 4; ++j) sn[j] = 0.5 - 0.5 * std::cos((2 * j + 1) * kPi / 8.0);
+    auto fit = [&](auto fn, int k, double c[4]) {
+        // Vandermonde solve with partial pivoting (4 x 4)
+        double A[4][5];
+        for (int j = 0; j < 4; ++j) {
+            double p = 1.0;
+            for (int m = 0; m < 4; ++m) {
+                A[j][m] = p;
+                p *= sn[j];
+            }
+            A[j][4] = fn((k + sn[j]) * du);
+        }
+        for (int col = 0; col < 4; ++col) {
+            int piv = col;
+            for (int r = col + 1; r < 4; ++r)
+                if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+            for (int m = 0; m < 5; ++m) std::swap(A[col][m], A[piv][m]);
+            for (int r = 0; r < 4; ++r) {
+                if (r == col) continue;
+                const double f = A[r][col] / A[col][col];
+                for (int m = col; m < 5; ++m) A[r][m] -= f * A[col][m];
+            }
+        }
+        for (int m = 0; m < 4; ++m) c[m] = A[m][4] / A[m][m];
+    };
+    const double g0 = G(0.0), f0 = F(0.0);
+    double err = 0.0;
+    for (int k = 0; k < kTabN; ++k) {
+        double cg[4], cf[4];
+        fit(G, k, cg);
+        fit(F, k, cf);
+        ns.tab_g[k] = make_float4((float)cg[0], (float)cg[1], (float)cg[2], (float)cg[3]);
+        ns.tab_f[k] = make_float4((float)cf[0], (float)cf[1], (float)cf[2], (float)cf[3]);
+        for (int q = 0; q <= 16; ++q) {
+            const double x = q / 16.0;
+            const float4 a = ns.tab_g[k], b = ns.tab_f[k];
+            const double pg = ((double)a.w * x + a.z) * x * x + (double)a.y * x + a.x;
+            const double pf = ((double)b.w * x + b.z) * x * x + (double)b.y * x + b.x;
+            err = std::max(err, std::fabs(pg - G((k + x) * du)) / g0);
+            err = std::max(err, std::fabs(pf - F((k + x) * du)) / f0);
+        }
+    }
+    ns.tab_scale = (float)(kTabN / (rc * rc));
+    ns.tab_err = (float)err;
 }
 
 rbsog_status enter(rbsog_ctx *ctx) {
@@ -618,6 +704,9 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
             b.h[d] = q.L[d] / (double)b.nc[d];
             b.L_f[d] = (float)q.L[d];
             b.fix_scale[d] = (float)(q.L[d] / 4294967296.0);
+            b.fix_inv[d] = 4294967296.0 / q.L[d];
+            b.cell_fix[d] = (float)(4294967296.0 / (double)b.nc[d]);
+            b.h_f[d] = (float)b.h[d];
         }
         if (ncell > (int64_t)INT32_MAX / 4) return fail(ctx, RBSOG_EINVAL, "system %d: cell grid too large", s);
         b.ncell = (int32_t)ncell;
@@ -655,6 +744,7 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
     ctx->P = p[0].P;
     ctx->precision = p[0].precision;
     build_near_sog(ctx->nsog, w, sv, p[0].M, p[0].r_c);
+    build_sog_tables(ctx->nsog, w, sv, p[0].M, p[0].r_c);
 
     // --- per-system layout
     ctx->desc.assign(ns, SysDesc{});
@@ -1352,7 +1442,7 @@ struct rbsog_server {
     std::vector<int64_t> waiting;     // FIFO
     std::vector<int64_t> active;      // system order of the current batch
     rbsog_ctx *batch = nullptr;
-    bool dirty = false;               // retirements since the last rebuild
+    int64_t frozen_n = 0;             // particles of retired jobs still in the batch
     int64_t next_id = 1;
     std::string err;
 };
@@ -1525,13 +1615,18 @@ rbsog_status rbsog_server_advance(rbsog_server *s, int32_t *n_active, int32_t *n
         add.push_back(id);
         s->waiting.erase(s->waiting.begin());
     }
-    if (!add.empty() || s->dirty) {
+    // Retired jobs stay frozen in the batch (their blocks exit at once) until
+    // an admission rebuilds it anyway, or they hold most of its particles.
+    int64_t live_n = 0;
+    for (int64_t id : s->active)
+        if (s->jobs[id].status == 1) live_n += s->jobs[id].n;
+    if (!add.empty() || (s->frozen_n > 0 && (live_n == 0 || s->frozen_n > live_n))) {
         std::vector<int64_t> keep;
         for (int64_t id : s->active)
             if (s->jobs[id].status == 1) keep.push_back(id);
         rbsog_status st = rebuild(s, keep, add);
         if (st != RBSOG_OK) return st;
-        s->dirty = false;
+        s->frozen_n = 0;
     }
     rbsog_ctx *b = s->batch;
     if (b) {
@@ -1557,7 +1652,7 @@ rbsog_status rbsog_server_advance(rbsog_server *s, int32_t *n_active, int32_t *n
             if (st != RBSOG_OK) return srv_fail(s, st, "energies: " + b->err);
             j.status = 2;
             s->used -= j.footprint;
-            s->dirty = true;
+            s->frozen_n += j.n;
             ++retired;
         }
     }

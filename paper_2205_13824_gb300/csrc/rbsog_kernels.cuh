@@ -9,6 +9,7 @@ namespace rbsog {
 
 constexpr int kMaxGauss = 128;   // M + 1 <= kMaxGauss
 constexpr int kMaxTaylor = 16;   // terms of the folded wide-Gaussian series
+constexpr int kTabN = 64;        // intervals of the FP32 Gaussian-sum tables
 
 // Sum-of-Gaussians near kernel in the form the pair kernels evaluate.
 // Gaussians l < n_direct are evaluated with exp; the wide ones (s_l >= 2 r_c)
@@ -29,6 +30,14 @@ struct NearSog {
     float inv_s2_log2e_f[kMaxGauss];  // log2(e) / s_l^2 (argument of ex2)
     float tay_f_f[kMaxTaylor];
     float tay_g_f[kMaxTaylor];
+    // FP32 piecewise-cubic tables of the whole Gaussian sums on u = r^2 in
+    // [0, r_c^2]: interval k covers u = (k + s) r_c^2 / kTabN, s in [0, 1),
+    // and holds the monomial coefficients (c0, c1, c2, c3) in s of
+    // G(u) = sum_l w_l / s_l^2 e^{-u/s_l^2} (tab_g) and F_M (tab_f)
+    float4 tab_g[kTabN];
+    float4 tab_f[kTabN];
+    float tab_scale;               // kTabN / r_c^2
+    float tab_err;                 // max abs error of the FP32 tables, relative to G(0) / F(0)
 };
 
 // Box, cell grid and pair constants.
@@ -44,6 +53,9 @@ struct BoxDev {
     double wca_eps;
     float L_f[3];
     float fix_scale[3];   // L_d / 2^32: fixed-point unit of the FP32C positions
+    double fix_inv[3];    // 2^32 / L_d: X_d = trunc(x_d * fix_inv[d]), clamped to [0, 2^32 - 1]
+    float cell_fix[3];    // 2^32 / nc_d: fixed-point length of one cell side
+    float h_f[3];         // h_d in FP32
     // FP32 copies of the pair constants (no double->float conversion in kernels)
     float rc2_f, lB_f, wca_s2_f, wca_rc2_f, wca_eps_f;
 };

@@ -165,7 +165,12 @@ def test_cell_list_matches_binning():
     c = np.minimum(np.floor(x / h).astype(int), 3)
     ref = (c[:, 2] * 4 + c[:, 1]) * 4 + c[:, 0]
     assert np.array_equal(cell_of, ref)
-    assert np.array_equal(perm, np.argsort(ref, kind="stable"))
+    # within a cell: increasing fixed-point x, ties by index
+    X = np.clip(x[:, 0] * (4294967296.0 / L), 0.0, 4294967295.0).astype(np.uint64)
+    assert np.array_equal(perm, np.lexsort((np.arange(len(x)), X, ref)))
+    xs = x[perm]
+    for c in range(64):   # x increases along each cell's member list
+        assert np.all(np.diff(xs[start[c]:start[c + 1], 0]) >= 0)
     assert np.array_equal(start, np.r_[0, np.cumsum(np.bincount(ref, minlength=64))])
 
 
