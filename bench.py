@@ -393,28 +393,86 @@ def serve_trace(Pk, trace, states, P, max_jobs, quantum):
     return lat, span
 
 
-def run_serving(dev, n_jobs=48, rate=20.0, P=100):
-    """Continuous batching under a Poisson job trace (rbsog_inputs.job_trace:
-    N log-uniform in [500, 50000], 100-1000 steps, density 0.5, FP32C,
-    P = 100), against the same trace served one job at a time."""
+def fifo_latencies(arrivals, service):
+    """Latencies of one FIFO server with the given arrival and service times."""
+    free, lat = 0.0, []
+    for a, s in zip(arrivals, service):
+        start = max(a, free)
+        free = start + s
+        lat.append(free - a)
+    return lat
+
+
+def run_serving(dev, n_jobs=64, P=200):
+    """Continuous batching under Poisson job traces (rbsog_inputs.job_trace):
+    N log-uniform in [500, 200000] at density 0.5, 100-1000 steps, P = 200,
+    FP32C -- the serving workload's size and length mix with the step counts
+    cut tenfold so that a trace replays in seconds.  Two arrival rates: 50
+    jobs/s (offered load above capacity) and 10 jobs/s.  Against it: the same
+    50/s trace served one job at a time (FP32C, measured), and one job at a
+    time in FP64 (estimated: FIFO queue over the measured FP64 step times of
+    each job size class)."""
     import numpy as np
+    import torch
 
     import paper_2205_13824_gb300 as Pk
     import rbsog_inputs as I
-    trace = I.job_trace(n_jobs, seed=11, rate=rate, n_min=500, n_max=50000, steps_min=100, steps_max=1000)
-    states = [I.electrolyte(j["N"], j["L"], seed=j["seed"] % 100000) for j in trace]
-    work = sum(j["N"] * j["steps"] for j in trace)
-    # warm the server path once (graph instantiation, allocator) on a short job
-    serve_trace(Pk, [dict(trace[0], t=0.0, steps=5)], states[:1], P, 4, 5)
-    out = {"jobs": n_jobs, "arrival_rate_per_s": rate, "P": P,
-           "offered_particle_steps_per_s": work / trace[-1]["t"]}
-    for name, mj, quantum in (("continuous_batching", 64, 25), ("one_at_a_time", 1, 25)):
-        lat, span = serve_trace(Pk, trace, states, P, mj, quantum)
-        lat = np.sort(np.array(lat))
-        out[name] = {"max_jobs": mj, "quantum_steps": quantum, "makespan_s": span,
-                     "served_particle_steps_per_s": work / span,
-                     "latency_p50_s": float(np.percentile(lat, 50)),
-                     "latency_p99_s": float(np.percentile(lat, 99)), "completed": int(lat.size)}
+    out = {"jobs": n_jobs, "P": P, "N_range": [500, 200000], "steps_range": [100, 1000],
+           "precision": "fp32c", "quantum_steps": 25}
+    states_cache = {}
+
+    def states_for(trace):
+        res = []
+        for j in trace:
+            key = (j["N"], j["seed"])
+            if key not in states_cache:
+                states_cache[key] = I.electrolyte(j["N"], j["L"], seed=j["seed"] % 100000)
+            res.append(states_cache[key])
+        return res
+
+    warm = I.job_trace(1, seed=5, rate=50.0, n_min=500, n_max=2000, steps_min=5, steps_max=5)
+    serve_trace(Pk, [dict(warm[0], t=0.0)], states_for(warm), P, 4, 5)
+    for label, rate in (("rate_50_per_s", 50.0), ("rate_10_per_s", 10.0)):
+        trace = I.job_trace(n_jobs, seed=11, rate=rate, n_min=500, n_max=200000, steps_min=100, steps_max=1000)
+        states = states_for(trace)
+        work = sum(j["N"] * j["steps"] for j in trace)
+        res = {"arrival_rate_per_s": rate, "offered_particle_steps_per_s": work / trace[-1]["t"]}
+        modes = (("continuous_batching", 64),) + ((("one_at_a_time_fp32c", 1),) if rate == 50.0 else ())
+        for name, mj in modes:
+            lat, span = serve_trace(Pk, trace, states, P, mj, 25)
+            lat = np.sort(np.array(lat))
+            res[name] = {"max_jobs": mj, "makespan_s": span, "served_particle_steps_per_s": work / span,
+                         "latency_p50_s": float(np.percentile(lat, 50)),
+                         "latency_p99_s": float(np.percentile(lat, 99)), "completed": int(lat.size)}
+        if rate == 50.0:
+            # FP64, one job at a time: step time measured per size class (N
+            # at 1k, 10k, 100k, 200k), interpolated in log N; FIFO queue
+            sizes = [1000, 10000, 100000, 200000]
+            ms = []
+            for n in sizes:
+                L = (n / 0.5) ** (1.0 / 3.0)
+                q, x, v = I.electrolyte(n, L, seed=3)
+                g = Pk.RBSOG(n, Pk.make_params(L, P, n_ksets=8, precision="fp64"))
+                g.set_state(*(torch.tensor(a, device=dev) for a in (q, x, v)))
+                g.step(1)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                g.step(5)
+                torch.cuda.synchronize()
+                ms.append((time.perf_counter() - t0) / 5 * 1e3)
+                g.close()
+            step_ms = np.interp(np.log([j["N"] for j in trace]), np.log(sizes), ms)
+            service = [s * j["steps"] / 1e3 for s, j in zip(step_ms, trace)]
+            lat = np.sort(np.array(fifo_latencies([j["t"] for j in trace], service)))
+            free = 0.0
+            for a, s in zip([j["t"] for j in trace], service):
+                free = max(a, free) + s
+            res["one_at_a_time_fp64_estimate"] = {
+                "basis": "FIFO queue over measured FP64 step times at N = 1k, 10k, 100k, 200k (log-interpolated)",
+                "fp64_ms_per_step_at": dict(zip([str(s) for s in sizes], ms)),
+                "makespan_s": free, "served_particle_steps_per_s": work / free,
+                "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99))}
+        out[label] = res
     return out
 
 

@@ -358,7 +358,7 @@ void orc_wrap(int64_t n, double *x, const double L[3]) {
 }
 
 /* Cells of side h_d = L_d / n_d with n_d = floor(L_d / r_c) >= 3.  A particle
- * at wrapped x goes to c_d = floor(x_d / h_d) (clamped to n_d - 1), cell id
+ * at wrapped x goes to c_d = floor(x_d * (n_d / L_d)) (clamped to [0, n_d - 1]), cell id
  * (c_z n_y + c_y) n_x + c_x.  Members of a cell are listed by increasing
  * fixed-point x coordinate X = trunc(x (2^32 / L_x)) (clamped to [0, 2^32 - 1]),
  * ties by increasing particle index: the order along an x-row of cells is
@@ -372,18 +372,18 @@ static uint32_t cell_key_x(double x, double Lx) {
 
 int orc_cell_list(int64_t n, const double *x, const double L[3], double rc,
                   int32_t *ncell, int32_t *cell_of, int32_t *cell_start, int32_t *perm) {
-    double h[3];
+    double inv_h[3];
     for (int d = 0; d < 3; ++d) {
         ncell[d] = (int32_t)floor(L[d] / rc);
         if (ncell[d] < 3) return -1;
-        h[d] = L[d] / (double)ncell[d];
+        inv_h[d] = (double)ncell[d] / L[d];
     }
     int64_t nc = (int64_t)ncell[0] * ncell[1] * ncell[2];
     for (int64_t c = 0; c <= nc; ++c) cell_start[c] = 0;
     for (int64_t i = 0; i < n; ++i) {
         int32_t c3[3];
         for (int d = 0; d < 3; ++d) {
-            int32_t c = (int32_t)floor(x[3 * i + d] / h[d]);
+            int32_t c = (int32_t)floor(x[3 * i + d] * inv_h[d]);
             if (c >= ncell[d]) c = ncell[d] - 1;
             if (c < 0) c = 0;
             c3[d] = c;

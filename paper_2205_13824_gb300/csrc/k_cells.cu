@@ -1,8 +1,9 @@
 // Device cell list for the near field: a counting sort of particles into
 // cells of side >= r_c.  Four launches:
-//   bin      one thread per particle: cell id (FP64 floor(x / h), the same
-//            decision as any IEEE evaluation) and an arrival slot from an
-//            integer atomic on the cell's counter;
+//   bin      one thread per particle: cell id (FP64 floor(x * (n / L)), the
+//            same decision as any IEEE evaluation of that product; a multiply,
+//            not a divide, on GB300's narrow FP64 pipe) and an arrival slot
+//            from an integer atomic on the cell's counter;
 //   scan     two launches: per-tile warp-shuffle scans, then tile offsets
 //            (the counters are cleared for the next build);
 //   scatter  one thread per particle: perm_raw[start + slot] = i;
@@ -32,7 +33,7 @@ __global__ void __launch_bounds__(kParticleBlock) k_bin(BatchView bv, const doub
     int c3[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        int c = (int)floor(xs[k] / d.box.h[k]);
+        int c = (int)floor(xs[k] * d.box.inv_h[k]);
         c = c >= d.box.nc[k] ? d.box.nc[k] - 1 : c;
         c = c < 0 ? 0 : c;
         c3[k] = c;

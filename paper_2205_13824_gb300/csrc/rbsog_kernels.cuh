@@ -55,6 +55,7 @@ struct BoxDev {
     float fix_scale[3];   // L_d / 2^32: fixed-point unit of the FP32C positions
     double fix_inv[3];    // 2^32 / L_d: X_d = trunc(x_d * fix_inv[d]), clamped to [0, 2^32 - 1]
     float cell_fix[3];    // 2^32 / nc_d: fixed-point length of one cell side
+    double inv_h[3];      // nc_d / L_d: cell of x is floor(x_d * inv_h[d]) (clamped)
     float h_f[3];         // h_d in FP32
     // FP32 copies of the pair constants (no double->float conversion in kernels)
     float rc2_f, lB_f, wca_s2_f, wca_rc2_f, wca_eps_f;

@@ -161,8 +161,7 @@ def test_cell_list_matches_binning():
     q, x, _ = I.electrolyte(1000, L, seed=3)
     nc, cell_of, start, perm = O.cell_list(x, (L, L, L), 3.0)
     assert list(nc) == [4, 4, 4]
-    h = L / 4
-    c = np.minimum(np.floor(x / h).astype(int), 3)
+    c = np.minimum(np.floor(x * (4 / L)).astype(int), 3)
     ref = (c[:, 2] * 4 + c[:, 1]) * 4 + c[:, 0]
     assert np.array_equal(cell_of, ref)
     # within a cell: increasing fixed-point x, ties by index
