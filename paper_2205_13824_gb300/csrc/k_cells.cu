@@ -1,5 +1,5 @@
 // Device cell list for the near field: a counting sort of particles into
-// cells of side >= r_c.  Four launches:
+// cells of side >= r_c.  Launches:
 //   bin      one thread per particle: cell id (FP64 floor(x * (n / L)), the
 //            same decision as any IEEE evaluation of that product; a multiply,
 //            not a divide, on GB300's narrow FP64 pipe) and an arrival slot
@@ -7,11 +7,11 @@
 //   scan     two launches: per-tile warp-shuffle scans, then tile offsets
 //            (the counters are cleared for the next build);
 //   scatter  one thread per particle: perm_raw[start + slot] = i;
-//   order    one warp per cell: ranks the cell's members by (fixed-point x,
-//            particle index) (keys exchanged by warp shuffles), so the order
-//            inside a cell -- and everything summed in that order -- is
+//   order    two passes of one thread per particle: ranks each cell's
+//            members by (fixed-point x, particle index), so the order inside
+//            a cell -- and everything summed in that order -- is
 //            deterministic, and an x-row of cells is sorted in x (the near
-//            field searches it); then gathers the particle data into cell
+//            field searches it); then moves the particle data into cell
 //            order -- FP64 (x, y, z, q) or, for the FP32C path, 32-bit
 //            fixed-point positions X_d = trunc(x_d * (2^32 / L_d)) with an FP32
 //            charge.
@@ -128,52 +128,57 @@ __device__ __forceinline__ uint32_t to_fixed32(double x, double inv) {
     return (uint32_t)__double2ull_rz(c);
 }
 
-// One warp per cell: rank = number of members with a smaller key
-// (X << 32 | index) (keys exchanged by shuffles for cells of up to 32).
-__global__ void __launch_bounds__(256) k_order_gather(BatchView bv, const int32_t *__restrict__ start,
-                                                      const int32_t *__restrict__ perm_raw,
-                                                      int32_t *__restrict__ perm,
-                                                      const double4_32a *__restrict__ posq, int precision,
-                                                      double4_32a *__restrict__ sp64, uint4 *__restrict__ sp32) {
-    const int lane = threadIdx.x & 31;
-    const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (cell >= bv.ncell_total) return;
-    const BoxDev &box = bv.sys[bv.cell_sys[cell]].box;
-    const int b = start[cell], e = start[cell + 1], cnt = e - b;
-    for (int t0 = 0; t0 < cnt; t0 += 32) {
-        const int t = t0 + lane;
-        const int idx = t < cnt ? perm_raw[b + t] : 0x7fffffff;
-        double4_32a p{};
-        unsigned long long key = ~0ull;
-        if (t < cnt) {
-            p = posq[idx];
-            key = ((unsigned long long)to_fixed32(p.x, box.fix_inv[0]) << 32) | (uint32_t)idx;
-        }
-        int rank = 0;
-        if (cnt <= 32) {
-            for (int u = 0; u < cnt; ++u) rank += (__shfl_sync(0xffffffffu, key, u) < key) ? 1 : 0;
-        } else {
-            for (int u = 0; u < cnt; ++u) {
-                const int j = perm_raw[b + u];
-                const unsigned long long kj = ((unsigned long long)to_fixed32(posq[j].x, box.fix_inv[0]) << 32) | (uint32_t)j;
-                rank += kj < key ? 1 : 0;
-            }
-        }
-        if (t < cnt) {
-            const int s = b + rank;
-            perm[s] = idx;
-            if (precision == 0) {
-                sp64[s] = p;
-            } else {
-                uint4 o;
-                o.x = to_fixed32(p.x, box.fix_inv[0]);
-                o.y = to_fixed32(p.y, box.fix_inv[1]);
-                o.z = to_fixed32(p.z, box.fix_inv[2]);
-                o.w = __float_as_uint((float)p.w);
-                sp32[s] = o;
-            }
-        }
+// Order inside a cell, in two passes of one thread per particle:
+//   keys    perm_raw slot s holds particle i: key[s] = (X << 32) | i with the
+//           fixed-point x coordinate X, and pack[s] = the particle in the
+//           gathered format (FP64 (x, y, z, q), or fixed-point X, Y, Z with
+//           the FP32 charge);
+//   rank    slot s of cell c goes to start[c] + (number of members of c with a
+//           smaller key): the members' keys are read from the cached key
+//           array (the threads of a cell read the same addresses).
+__global__ void __launch_bounds__(256) k_cell_keys(BatchView bv, const int32_t *__restrict__ perm_raw,
+                                                   const int32_t *__restrict__ cell_of,
+                                                   const double4_32a *__restrict__ posq, int precision,
+                                                   unsigned long long *__restrict__ key,
+                                                   double4_32a *__restrict__ pack) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= bv.n_total) return;
+    const int idx = perm_raw[s];
+    const BoxDev &box = bv.sys[bv.cell_sys[cell_of[idx]]].box;
+    const double4_32a p = posq[idx];
+    const uint32_t X = to_fixed32(p.x, box.fix_inv[0]);
+    key[s] = ((unsigned long long)X << 32) | (uint32_t)idx;
+    if (precision == 0) {
+        pack[s] = p;
+    } else {
+        uint4 o;
+        o.x = X;
+        o.y = to_fixed32(p.y, box.fix_inv[1]);
+        o.z = to_fixed32(p.z, box.fix_inv[2]);
+        o.w = __float_as_uint((float)p.w);
+        reinterpret_cast<uint4 *>(pack)[s] = o;
     }
+}
+
+__global__ void __launch_bounds__(256) k_cell_rank(int64_t n, const int32_t *__restrict__ perm_raw,
+                                                   const int32_t *__restrict__ cell_of,
+                                                   const int32_t *__restrict__ start,
+                                                   const unsigned long long *__restrict__ key,
+                                                   const double4_32a *__restrict__ pack, int precision,
+                                                   int32_t *__restrict__ perm, double4_32a *__restrict__ sp64,
+                                                   uint4 *__restrict__ sp32) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int idx = perm_raw[s];
+    const int c = cell_of[idx];
+    const int b = start[c], e = start[c + 1];
+    const unsigned long long k = key[s];
+    int rank = 0;
+    for (int u = b; u < e; ++u) rank += key[u] < k ? 1 : 0;
+    const int d = b + rank;
+    perm[d] = idx;
+    if (precision == 0) sp64[d] = pack[s];
+    else sp32[d] = reinterpret_cast<const uint4 *>(pack)[s];
 }
 
 }  // namespace
@@ -202,8 +207,10 @@ cudaError_t launch_build_cells(const BatchView &bv, const double4_32a *posq, con
     }
     {
         ProfScope ps(prof, "cell_order_gather");
-        const unsigned blocks = (unsigned)((bv.ncell_total * 32 + t - 1) / t);
-        k_order_gather<<<blocks, t, 0, st>>>(bv, cb.start, cb.perm_raw, cb.perm, posq, precision, sp64, sp32);
+        const unsigned nb = (unsigned)((bv.n_total + t - 1) / t);
+        k_cell_keys<<<nb, t, 0, st>>>(bv, cb.perm_raw, cb.cell_of, posq, precision, cb.key, cb.pack);
+        k_cell_rank<<<nb, t, 0, st>>>(bv.n_total, cb.perm_raw, cb.cell_of, cb.start, cb.key, cb.pack, precision,
+                                      cb.perm, sp64, sp32);
     }
     return cudaGetLastError();
 }

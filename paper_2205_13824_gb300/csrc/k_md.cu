@@ -88,17 +88,40 @@ __global__ void __launch_bounds__(1024) k_finalize(BatchView bv, const double2 *
     const SysDesc &a = bv.sys[sy];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     double un = 0.0, uw = 0.0, r2 = 0.0, ke = 0.0;
-    for (int j = tid; j < a.n_epart; j += blockDim.x) {
-        const double2 e = epart[a.e_off + j];
-        un += e.x;
-        uw += e.y;
+    // each thread sums j = tid, tid + B, tid + 2B, ... in that order; the
+    // loads of eight terms are issued before their adds
+    const int B = blockDim.x;
+    for (int j0 = tid; j0 < a.n_epart; j0 += 8 * B) {
+        double2 e[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = j0 + u * B;
+            e[u] = j < a.n_epart ? epart[a.e_off + j] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (j0 + u * B < a.n_epart) {
+                un += e[u].x;
+                uw += e[u].y;
+            }
+        }
     }
     for (int j = tid; j < bv.P; j += blockDim.x) {
         const double2 r = rho[(int64_t)sy * bv.P + j];
         r2 += r.x * r.x + r.y * r.y;
     }
     if (with_kinetic)
-        for (int j = tid; j < a.n_kpart; j += blockDim.x) ke += kpart[a.kp_off + j];
+        for (int j0 = tid; j0 < a.n_kpart; j0 += 8 * B) {
+            double k8[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u * B;
+                k8[u] = j < a.n_kpart ? kpart[a.kp_off + j] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (j0 + u * B < a.n_kpart) ke += k8[u];
+        }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         un += __shfl_down_sync(0xffffffffu, un, o);

@@ -40,7 +40,7 @@ namespace {
 constexpr int kThreads = 128;   // one home particle per thread
 constexpr int kMaxGroup = 16;
 constexpr int kMaxStaged = 9 * (kMaxGroup + 2);
-constexpr int kList32 = 64;     // partner-list entries per thread, FP32C (uint16), plus one spare slot
+constexpr int kList32 = 32;     // partner-list entries per thread, FP32C (uint16), plus one spare slot
 constexpr int kMaxHome = 1024;  // home particles a block can reorder (more: cell order is kept)
 constexpr int kList64 = 64;     // partner-list entries per thread, FP64 (int32: index | shift code)
 
@@ -154,8 +154,10 @@ struct PairConst {
     real rc2, wrc2, ws2, weps, lB;
 };
 
+// FP32C: 6 resident blocks per SM (at most 85 registers), measured faster
+// than 4-5 with the shorter partner list; FP64 keeps 4 (no spills)
 template <int PREC, int ND, int NT, bool WIN>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, PREC == 1 ? 6 : 4)
     k_near(const BatchView bv, const __grid_constant__ NearSog sog, const int32_t *__restrict__ start,
            const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
            double4_32a *__restrict__ fnear, double2 *__restrict__ epart, int32_t *__restrict__ nbr) {
@@ -514,13 +516,26 @@ __global__ void __launch_bounds__(kThreads, 4)
             e_wca += (double)uw;
         }
     }
-    // fixed-order warp reduction of the energies, one partial per warp
+    // fixed-order reduction of the energies: warp shuffles, then the warps in
+    // order -- one partial per block (the per-system sum of the partials runs
+    // on one SM, where FP64 adds are scarce on this GPU)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         e_near += __shfl_down_sync(0xffffffffu, e_near, o);
         e_wca += __shfl_down_sync(0xffffffffu, e_wca, o);
     }
-    if (lane == 0) epart[desc.e_off + work.y * (kThreads / 32) + wid] = make_double2(e_near, e_wca);
+    __shared__ double2 s_ew[kThreads / 32];
+    if (lane == 0) s_ew[wid] = make_double2(e_near, e_wca);
+    __syncthreads();
+    if (tid == 0) {
+        double2 t = s_ew[0];
+#pragma unroll
+        for (int w2 = 1; w2 < kThreads / 32; ++w2) {
+            t.x += s_ew[w2].x;
+            t.y += s_ew[w2].y;
+        }
+        epart[desc.e_off + work.y] = t;
+    }
 }
 
 size_t near_smem(int precision, int cap) {
@@ -541,7 +556,7 @@ void near_layout(const BoxDev &box, int64_t n, int precision, int home, int &gro
     group = g;
     nseg_x = (box.nc[0] + g - 1) / g;
     nblocks = nseg_x * box.nc[1] * box.nc[2];
-    npartials = nblocks * (kThreads / 32);
+    npartials = nblocks;
     const double est = 9.0 * (g + 2) * per_cell * 1.15 + 64.0;
     const int cap_max = precision == 0 ? 2048 : 4096;
     cap = std::min(cap_max, std::max(256, ((int)std::ceil(est) + 127) / 128 * 128));

@@ -635,7 +635,8 @@ rbsog_status rbsog_batch_create(rbsog_batch **out, int32_t n_sys, const int64_t 
               dalloc(&ctx->staging, 3 * n) == cudaSuccess && dalloc(&ctx->nbr_sorted, n) == cudaSuccess &&
               dalloc(&ctx->i32_tmp, n) == cudaSuccess && dalloc(&ctx->cb.cell_of, n) == cudaSuccess &&
               dalloc(&ctx->cb.slot, n) == cudaSuccess && dalloc(&ctx->cb.perm_raw, n) == cudaSuccess &&
-              dalloc(&ctx->cb.perm, n) == cudaSuccess && dalloc(&ctx->cursor, n_sys) == cudaSuccess &&
+              dalloc(&ctx->cb.perm, n) == cudaSuccess && dalloc(&ctx->cb.key, n) == cudaSuccess &&
+              dalloc(&ctx->cb.pack, n) == cudaSuccess && dalloc(&ctx->cursor, n_sys) == cudaSuccess &&
               dalloc(&ctx->step_ctr, n_sys) == cudaSuccess &&
               dalloc(&ctx->energy, (size_t)kNumEnergy * n_sys) == cudaSuccess &&
               dalloc(&ctx->err_flag, 1) == cudaSuccess && dalloc(&ctx->d_desc, n_sys) == cudaSuccess &&
@@ -1381,6 +1382,8 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->cb.tile_sum);
     dfree(&ctx->cb.perm_raw);
     dfree(&ctx->cb.perm);
+    dfree(&ctx->cb.key);
+    dfree(&ctx->cb.pack);
     dfree(&ctx->kpart);
     dfree(&ctx->kseq);
     dfree(&ctx->cursor);

@@ -110,7 +110,7 @@ struct SysDesc {
     int64_t c_off;             // first cell (global index)
     int32_t group, nseg_x;     // near field: home cells per block, segments per x-row
     int32_t near_cap;          // near field: staged particles per shared-memory chunk
-    int32_t e_off, n_epart;    // near-energy partials (one per warp)
+    int32_t e_off, n_epart;    // near-energy partials (one per near-field block)
     int32_t tile_p, n_ptiles;  // rho sweep: particles per tile, tiles
     int64_t rp_off;            // first rho partial (double2 units)
     int64_t k_off;             // first int4 of this system's k-sequence
@@ -157,6 +157,8 @@ struct CellBuffers {
     int32_t *perm_raw;    // [n]   cell order, unordered inside a cell
     int32_t *perm;        // [n]   cell order, increasing index inside a cell
     int32_t *tile_sum;    // [cell_scan_tiles(ncell)] scan tile totals
+    unsigned long long *key;   // [n] in perm_raw order: (fixed-point x << 32) | index
+    double4_32a *pack;         // [n] in perm_raw order: particle data in the gathered format
 };
 int cell_scan_tiles(int64_t ncell);
 // precision 0: gather FP64 (x, y, z, q) into sp64; 1: 32-bit fixed point
