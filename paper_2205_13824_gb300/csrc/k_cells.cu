@@ -22,7 +22,8 @@ namespace {
 
 __global__ void __launch_bounds__(kParticleBlock) k_bin(BatchView bv, const double4_32a *__restrict__ posq,
                                                         int32_t *__restrict__ cell_of, int32_t *__restrict__ slot,
-                                                        int32_t *__restrict__ count) {
+                                                        int32_t *__restrict__ count, const int32_t *__restrict__ gate) {
+    if (gate && !*gate) return;
     const int2 w = bv.pblk[blockIdx.x];
     const SysDesc &d = bv.sys[w.x];
     const int64_t il = (int64_t)w.y * kParticleBlock + threadIdx.x;
@@ -56,7 +57,9 @@ constexpr int kScanTile = kScanThreads * kScanPer;
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_tile(int ncell, const int32_t *__restrict__ count,
                                                             int32_t *__restrict__ start,
-                                                            int32_t *__restrict__ tile_sum) {
+                                                            int32_t *__restrict__ tile_sum,
+                                                            const int32_t *__restrict__ gate) {
+    if (gate && !*gate) return;
     __shared__ int warp_tot[kScanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int base = blockIdx.x * kScanTile + tid * kScanPer;
@@ -88,7 +91,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tile(int ncell, const int
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_add(int ncell, int ntiles, int32_t *__restrict__ count,
                                                            int32_t *__restrict__ start,
-                                                           const int32_t *__restrict__ tile_sum) {
+                                                           const int32_t *__restrict__ tile_sum,
+                                                           const int32_t *__restrict__ gate) {
+    if (gate && !*gate) return;
     __shared__ int s_off;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid < 32) {
@@ -114,7 +119,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(int ncell, int ntiles
 __global__ void __launch_bounds__(256) k_scatter(int64_t n, const int32_t *__restrict__ cell_of,
                                                  const int32_t *__restrict__ slot,
                                                  const int32_t *__restrict__ start,
-                                                 int32_t *__restrict__ perm_raw) {
+                                                 int32_t *__restrict__ perm_raw, const int32_t *__restrict__ gate) {
+    if (gate && !*gate) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     perm_raw[start[cell_of[i]] + slot[i]] = (int32_t)i;
@@ -122,11 +128,7 @@ __global__ void __launch_bounds__(256) k_scatter(int64_t n, const int32_t *__res
 
 // X = trunc(x * (2^32 / L)) clamped to [0, 2^32 - 1]: one FP64 multiply (the
 // scale is computed once on the host), not a division per coordinate.
-__device__ __forceinline__ uint32_t to_fixed32(double x, double inv) {
-    const double t = x * inv;
-    const double c = t < 0.0 ? 0.0 : (t > 4294967295.0 ? 4294967295.0 : t);
-    return (uint32_t)__double2ull_rz(c);
-}
+__device__ __forceinline__ uint32_t to_fixed32(double x, double inv) { return fixed32(x, inv); }
 
 // Order inside a cell, in two passes of one thread per particle:
 //   keys    perm_raw slot s holds particle i: key[s] = (X << 32) | i with the
@@ -140,7 +142,9 @@ __global__ void __launch_bounds__(256) k_cell_keys(BatchView bv, const int32_t *
                                                    const int32_t *__restrict__ cell_of,
                                                    const double4_32a *__restrict__ posq, int precision,
                                                    unsigned long long *__restrict__ key,
-                                                   double4_32a *__restrict__ pack) {
+                                                   double4_32a *__restrict__ pack,
+                                                   const int32_t *__restrict__ gate) {
+    if (gate && !*gate) return;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= bv.n_total) return;
     const int idx = perm_raw[s];
@@ -166,7 +170,8 @@ __global__ void __launch_bounds__(256) k_cell_rank(int64_t n, const int32_t *__r
                                                    const unsigned long long *__restrict__ key,
                                                    const double4_32a *__restrict__ pack, int precision,
                                                    int32_t *__restrict__ perm, double4_32a *__restrict__ sp64,
-                                                   uint4 *__restrict__ sp32) {
+                                                   uint4 *__restrict__ sp32, const int32_t *__restrict__ gate) {
+    if (gate && !*gate) return;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int idx = perm_raw[s];
@@ -187,30 +192,30 @@ int cell_scan_tiles(int64_t ncell) { return (int)((ncell + kScanTile - 1) / kSca
 
 cudaError_t launch_build_cells(const BatchView &bv, const double4_32a *posq, const CellBuffers &cb,
                                int precision, double4_32a *sp64, uint4 *sp32, cudaStream_t st,
-                               const Prof *prof) {
+                               const Prof *prof, const int32_t *gate) {
     const int t = 256;
     const int ncell = (int)bv.ncell_total;
     {
         ProfScope ps(prof, "cell_bin");
-        k_bin<<<bv.n_pblk, kParticleBlock, 0, st>>>(bv, posq, cb.cell_of, cb.slot, cb.count);
+        k_bin<<<bv.n_pblk, kParticleBlock, 0, st>>>(bv, posq, cb.cell_of, cb.slot, cb.count, gate);
     }
     {
         ProfScope ps(prof, "cell_scan");
         const int ntiles = cell_scan_tiles(ncell);
-        k_scan_tile<<<ntiles, kScanThreads, 0, st>>>(ncell, cb.count, cb.start, cb.tile_sum);
-        k_scan_add<<<ntiles, kScanThreads, 0, st>>>(ncell, ntiles, cb.count, cb.start, cb.tile_sum);
+        k_scan_tile<<<ntiles, kScanThreads, 0, st>>>(ncell, cb.count, cb.start, cb.tile_sum, gate);
+        k_scan_add<<<ntiles, kScanThreads, 0, st>>>(ncell, ntiles, cb.count, cb.start, cb.tile_sum, gate);
     }
     {
         ProfScope ps(prof, "cell_scatter");
         const unsigned nb = (unsigned)((bv.n_total + t - 1) / t);
-        k_scatter<<<nb, t, 0, st>>>(bv.n_total, cb.cell_of, cb.slot, cb.start, cb.perm_raw);
+        k_scatter<<<nb, t, 0, st>>>(bv.n_total, cb.cell_of, cb.slot, cb.start, cb.perm_raw, gate);
     }
     {
         ProfScope ps(prof, "cell_order_gather");
         const unsigned nb = (unsigned)((bv.n_total + t - 1) / t);
-        k_cell_keys<<<nb, t, 0, st>>>(bv, cb.perm_raw, cb.cell_of, posq, precision, cb.key, cb.pack);
+        k_cell_keys<<<nb, t, 0, st>>>(bv, cb.perm_raw, cb.cell_of, posq, precision, cb.key, cb.pack, gate);
         k_cell_rank<<<nb, t, 0, st>>>(bv.n_total, cb.perm_raw, cb.cell_of, cb.start, cb.key, cb.pack, precision,
-                                      cb.perm, sp64, sp32);
+                                      cb.perm, sp64, sp32, gate);
     }
     return cudaGetLastError();
 }

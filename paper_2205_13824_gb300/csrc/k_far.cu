@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kScatterThreads)
     k_far_scatter(BatchView bv, const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
                   const void *__restrict__ ktab_all, const double4_32a *__restrict__ fnear,
                   const int32_t *__restrict__ perm, double4_32a *__restrict__ force,
-                  int32_t *__restrict__ err_flag) {
+                  int32_t *__restrict__ err_flag, double2 *__restrict__ epart) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int tid = threadIdx.x;
     const int2 work = bv.pblk[blockIdx.x];
@@ -274,12 +274,39 @@ __global__ void __launch_bounds__(kScatterThreads)
         fy = p.w * gy;
         fz = p.w * gz;
     }
+    if (bv.force_mask && !bv.force_mask[work.x]) return;   // whole block
+    double4_32a fn = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    if (active) fn = fnear[s];
+    if (!perm) {
+        // caller order (neighbour-list path): the block's near energies, two
+        // floats per particle in fn.w, summed in fixed order (warps, then
+        // the warps in order) into one partial per particle block
+        double en = 0.0, ew = 0.0;
+        if (active) {
+            en = (double)__int_as_float(__double2hiint(fn.w));
+            ew = (double)__int_as_float(__double2loint(fn.w));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            en += __shfl_down_sync(0xffffffffu, en, o);
+            ew += __shfl_down_sync(0xffffffffu, ew, o);
+        }
+        __shared__ double2 s_e[kScatterThreads / 32];
+        if ((tid & 31) == 0) s_e[tid >> 5] = make_double2(en, ew);
+        __syncthreads();
+        if (tid == 0) {
+            double2 t = s_e[0];
+            for (int w2 = 1; w2 < kScatterThreads / 32; ++w2) {
+                t.x += s_e[w2].x;
+                t.y += s_e[w2].y;
+            }
+            epart[d.e_off + work.y] = t;
+        }
+    }
     if (!active) return;
-    if (bv.force_mask && !bv.force_mask[work.x]) return;
-    const double4_32a fn = fnear[s];
     const double tx = fx + fn.x, ty = fy + fn.y, tz = fz + fn.z;
     if (!(isfinite(tx) && isfinite(ty) && isfinite(tz))) atomicOr(err_flag, 1);
-    force[perm[s]] = make_double4_32a(tx, ty, tz, 0.0);
+    force[perm ? perm[s] : s] = make_double4_32a(tx, ty, tz, 0.0);
 }
 
 }  // namespace
@@ -327,16 +354,17 @@ cudaError_t launch_rho_combine(int precision, const BatchView &bv, const double2
 
 cudaError_t launch_far_scatter(int precision, const BatchView &bv, const double4_32a *sp64, const uint4 *sp32,
                                const void *ktab, const double4_32a *fnear, const int32_t *perm,
-                               double4_32a *force, int32_t *err_flag, cudaStream_t st, const Prof *prof) {
+                               double4_32a *force, int32_t *err_flag, cudaStream_t st, const Prof *prof,
+                               double2 *epart) {
     ProfScope ps(prof, precision == 1 ? "far_scatter_fp32c" : "far_scatter_fp64");
     if (precision == 1) {
         const size_t sm = sizeof(KEntry32) * kKChunk32;
         k_far_scatter<1><<<bv.n_pblk, kScatterThreads, sm, st>>>(bv, sp64, sp32, ktab, fnear, perm, force,
-                                                                  err_flag);
+                                                                  err_flag, epart);
     } else {
         const size_t sm = sizeof(KEntry64) * kKChunk64;
         k_far_scatter<0><<<bv.n_pblk, kScatterThreads, sm, st>>>(bv, sp64, sp32, ktab, fnear, perm, force,
-                                                                  err_flag);
+                                                                  err_flag, epart);
     }
     return cudaGetLastError();
 }

@@ -18,7 +18,9 @@ __device__ __forceinline__ double fold(double x, double L) {
 // v += dt/2 F/m ; x += dt v ; x folded into [0, L).
 __global__ void __launch_bounds__(kThreads) k_kick_drift(BatchView bv, double4_32a *__restrict__ posq,
                                                          double4_32a *__restrict__ vel,
-                                                         const double4_32a *__restrict__ force) {
+                                                         const double4_32a *__restrict__ force,
+                                                         uint4 *__restrict__ sp32c, const uint4 *__restrict__ xref,
+                                                         int32_t *__restrict__ rebuild) {
     const int2 w = bv.pblk[blockIdx.x];
     if (bv.remaining && bv.remaining[w.x] == 0) return;
     const SysDesc &a = bv.sys[w.x];
@@ -41,6 +43,7 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift(BatchView bv, double4_3
     if (p.z < 0.0 || p.z >= a.box.L[2]) p.z = fold(p.z, a.box.L[2]);
     vel[i] = v;
     posq[i] = p;
+    if (sp32c) fixed_pack_check(a, w.x, bv.n_sys, p, i, sp32c, xref, rebuild);
 }
 
 // v += dt/2 F/m and the block's kinetic energy sum (fixed order).
@@ -70,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_kick(BatchView bv, double4_32a *__
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) t += s_red[w];
+        for (int q = 0; q < kThreads / 32; ++q) t += s_red[q];
         kpart[a.kp_off + w.y] = t;
     }
 }
@@ -230,9 +233,9 @@ inline unsigned nblk(int64_t n) { return (unsigned)((n + kThreads - 1) / kThread
 }  // namespace
 
 cudaError_t launch_kick_drift(const BatchView &bv, double4_32a *posq, double4_32a *vel, const double4_32a *force,
-                              cudaStream_t st, const Prof *prof) {
+                              cudaStream_t st, const Prof *prof, uint4 *sp32c, const uint4 *xref, int32_t *rebuild) {
     ProfScope ps(prof, "kick_drift");
-    k_kick_drift<<<bv.n_pblk, kThreads, 0, st>>>(bv, posq, vel, force);
+    k_kick_drift<<<bv.n_pblk, kThreads, 0, st>>>(bv, posq, vel, force, sp32c, xref, rebuild);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,361 @@
+// Near field of the FP32C path with neighbour lists (Eq. 3.9, first line,
+// read as -grad of U_N with N(r) = 1/r - F_M(r), plus WCA).
+//
+// Every particle keeps the list of the particles within r_l = r_c + skin of
+// it when the list was built.  While no particle of the system has moved by
+// more than skin/2 since then, every pair inside r_c is on the lists, so the
+// per-step force only has to test the listed candidates (about (r_l/r_c)^3
+// times the pairs) instead of a cell stencil.  The displacement test runs in
+// the kick-drift kernel on the fixed-point positions; a system whose
+// particles moved too far gets its cell list and neighbour lists rebuilt
+// inside the same step (the rebuild kernels are gated by a device flag per
+// system, so the captured step graph needs no host decision).
+//
+// Determinism: a system's rebuild decisions depend only on its own
+// positions, and a list's order only on the cell list built from them, so a
+// system's forces are the same bits alone or in any batch.  Pair terms are
+// summed in list order; a run restarted from a checkpoint builds fresh lists
+// at the restart step and so agrees with the continuous run to FP32 rounding
+// of those sums.  Energies are summed per particle and then over blocks of
+// particles in caller order.
+//
+// Kernels:
+//   fix_pack    fixed-point caller-order positions (and the displacement
+//               test) for force evaluations that do not follow a kick-drift;
+//   list_build  per near-field block (home x-row segment of cells, 9 staged
+//               row segments as in the cell-stencil kernel): binary-searched
+//               x-windows of r_l in the x-sorted rows, candidates appended
+//               to an ELL list (slot-major, particle-minor);
+//   near_list   one thread per particle in the cell order of the last build:
+//               listed partners, fixed-point differences (the 32-bit wrap is
+//               the minimum image), r^2 < r_c^2, Gaussian sums from the FP32
+//               tables; force and the two energies per particle;
+//   list_clear  resets the rebuild flags after a build.
+#include <climits>
+#include <cmath>
+
+#include "rbsog_kernels.cuh"
+
+namespace rbsog {
+namespace {
+
+constexpr int kBuildThreads = 128;
+constexpr int kMaxGroupB = 16;
+constexpr int kMaxStagedB = 9 * (kMaxGroupB + 2);
+constexpr int kNearThreads = kParticleBlock;
+
+__device__ __forceinline__ int wrap_cell_b(int c, int n) {
+    return c < 0 ? c + n : (c >= n ? c - n : c);
+}
+
+__device__ __forceinline__ float offset_f(uint32_t a, uint32_t o, float scale) {
+    return (float)(int32_t)(a - o) * scale;
+}
+
+__global__ void __launch_bounds__(kParticleBlock) k_fix_pack(BatchView bv, const double4_32a *__restrict__ posq,
+                                                             uint4 *__restrict__ sp32c,
+                                                             const uint4 *__restrict__ xref,
+                                                             int32_t *__restrict__ rebuild) {
+    const int2 w = bv.pblk[blockIdx.x];
+    const SysDesc &d = bv.sys[w.x];
+    const int64_t il = (int64_t)w.y * kParticleBlock + threadIdx.x;
+    if (il >= d.n) return;
+    const int64_t i = d.p_off + il;
+    fixed_pack_check(d, w.x, bv.n_sys, posq[i], i, sp32c, xref, rebuild);
+}
+
+// Neighbour lists of the home particles of one near-field block.
+__global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv, const int32_t *__restrict__ start,
+                                                              const uint4 *__restrict__ sp32,
+                                                              const int32_t *__restrict__ perm,
+                                                              const int32_t *__restrict__ rebuild,
+                                                              int32_t *__restrict__ nbr_list,
+                                                              int32_t *__restrict__ nbr_cnt,
+                                                              int32_t *__restrict__ list_perm,
+                                                              uint4 *__restrict__ xref,
+                                                              int32_t *__restrict__ err_flag) {
+    __shared__ int s_off[kMaxStagedB + 1];
+    __shared__ int s_src[kMaxStagedB];
+    __shared__ int s_hstart[kMaxGroupB + 1];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int2 work = bv.nblk[blockIdx.x];
+    if (!rebuild[work.x]) return;                              // this system keeps its lists
+    if (bv.remaining && bv.remaining[work.x] == 0) return;
+    const SysDesc &desc = bv.sys[work.x];
+    const BoxDev &box = desc.box;
+    const int group = desc.group, nseg_x = desc.nseg_x, cap = desc.near_cap;
+    const int lcap = bv.list_cap;
+    float4 *__restrict__ st = reinterpret_cast<float4 *>(smem_raw);                       // [cap]
+    int *__restrict__ st_id = reinterpret_cast<int *>(smem_raw + sizeof(float4) * cap);   // [cap]
+    const int64_t coff = desc.c_off;
+    const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
+    const int sx = work.y % nseg_x, row = work.y / nseg_x;
+    const int cy = row % ny, cz = row / ny;
+    const int x0 = sx * group, xe = min(x0 + group, nx), nh = xe - x0, w = nh + 2;
+    const int ns = 9 * w;
+    for (int k = tid; k < ns; k += kBuildThreads) {
+        const int r = k / w, xi = k % w;
+        const int zz = wrap_cell_b(cz + r / 3 - 1, nz);
+        const int yy = wrap_cell_b(cy + r % 3 - 1, ny);
+        const int xx = wrap_cell_b(x0 - 1 + xi, nx);
+        const int64_t id = coff + (zz * ny + yy) * nx + xx;
+        const int b = start[id];
+        s_src[k] = b;
+        s_off[k + 1] = start[id + 1] - b;
+    }
+    if (tid <= nh) s_hstart[tid] = start[coff + (cz * ny + cy) * nx + x0 + tid];
+    if (tid == 0) s_off[0] = 0;
+    __syncthreads();
+    if (wid == 0) {
+        int carry = 0;
+        for (int base = 0; base < ns; base += 32) {
+            const int k = base + lane;
+            int v = k < ns ? s_off[k + 1] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            if (k < ns) s_off[k + 1] = v + carry;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+    const int total = s_off[ns];
+    const int hb = s_hstart[0], he = s_hstart[nh];
+    const uint32_t ox = (uint32_t)__float2ull_rn(((float)x0 + 0.5f * (float)nh) * box.cell_fix[0]);
+    const uint32_t oy = (uint32_t)__float2ull_rn(((float)cy + 0.5f) * box.cell_fix[1]);
+    const uint32_t oz = (uint32_t)__float2ull_rn(((float)cz + 0.5f) * box.cell_fix[2]);
+    const float fsx = box.fix_scale[0], fsy = box.fix_scale[1], fsz = box.fix_scale[2];
+    const float hx = box.h_f[0], hy = box.h_f[1], hz = box.h_f[2];
+    const float inv_hx = 1.0f / hx, xbase = 1.0f + 0.5f * (float)nh;
+    const float rl2 = box.rl2_f;
+    constexpr float kMargin = 1e-3f;
+
+    for (int rb = hb; rb < he; rb += kBuildThreads) {   // rounds of home particles
+        const int hi = rb + tid;
+        const bool active = hi < he;
+        float ix = 1e30f, iy = 1e30f, iz = 1e30f;
+        if (active) {
+            const uint4 u = sp32[hi];
+            ix = offset_f(u.x, ox, fsx);
+            iy = offset_f(u.y, oy, fsy);
+            iz = offset_f(u.z, oz, fsz);
+        }
+        int cnt = 0;
+        bool over = false;
+        for (int c0 = 0; c0 < total; c0 += cap) {
+            const int c1 = min(c0 + cap, total);
+            __syncthreads();
+            for (int r = 0; r < 9; ++r) {
+                const int k = r * w;
+                const int plo[3] = {s_off[k], s_off[k + 1], s_off[k + w - 1]};
+                const int phi[3] = {s_off[k + 1], s_off[k + w - 1], s_off[k + w]};
+                const int psrc[3] = {s_src[k], s_src[k + 1], s_src[k + w - 1]};
+                for (int pp = 0; pp < 3; ++pp) {
+                    const int a = max(plo[pp], c0), b = min(phi[pp], c1);
+                    for (int t = a + tid; t < b; t += kBuildThreads) {
+                        const int src = psrc[pp] + (t - plo[pp]);
+                        const uint4 u = sp32[src];
+                        st[t - c0] = make_float4(offset_f(u.x, ox, fsx), offset_f(u.y, oy, fsy),
+                                                 offset_f(u.z, oz, fsz), 0.f);
+                        st_id[t - c0] = perm[src];
+                    }
+                }
+            }
+            __syncthreads();
+            if (!active) continue;
+            for (int r = 0; r < 9; ++r) {
+                const int dyr = r % 3 - 1, dzr = r / 3 - 1;
+                const float gy = dyr == 0 ? 0.f : fmaxf((dyr < 0 ? iy + 0.5f * hy : 0.5f * hy - iy) - kMargin, 0.f);
+                const float gz = dzr == 0 ? 0.f : fmaxf((dzr < 0 ? iz + 0.5f * hz : 0.5f * hz - iz) - kMargin, 0.f);
+                const float b2 = rl2 - gy * gy - gz * gz;
+                if (!(b2 > 0.f)) continue;
+                const float bb = sqrtf(b2) + kMargin;
+                const float xl = ix - bb, xr = ix + bb;
+                const int k0 = r * w;
+                const int cl = min(max((int)floorf(fmaf(xl, inv_hx, xbase)), 0), w - 1);
+                const int ch = min(max((int)floorf(fmaf(xr, inv_hx, xbase)), 0), w - 1);
+                int a = max(s_off[k0 + cl], c0), e = min(s_off[k0 + cl + 1], c1);
+                while (a < e) {
+                    const int m = (a + e) >> 1;
+                    if (st[m - c0].x < xl) a = m + 1; else e = m;
+                }
+                const int lo = a;
+                a = max(s_off[k0 + ch], c0);
+                e = min(s_off[k0 + ch + 1], c1);
+                while (a < e) {
+                    const int m = (a + e) >> 1;
+                    if (st[m - c0].x <= xr) a = m + 1; else e = m;
+                }
+                for (int t = lo; t < a; ++t) {
+                    const float4 pj = st[t - c0];
+                    const float dx = ix - pj.x, dy = iy - pj.y, dz = iz - pj.z;
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    if (r2 < rl2 && r2 > 0.f) {
+                        if (cnt < lcap) nbr_list[(int64_t)cnt * bv.n_total + hi] = st_id[t - c0];
+                        else over = true;
+                        ++cnt;
+                    }
+                }
+            }
+        }
+        if (active) {
+            if (over) {
+                atomicOr(err_flag, 4);
+                cnt = lcap;
+            }
+            nbr_cnt[hi] = cnt;
+            const int ci = perm[hi];
+            list_perm[hi] = ci;
+            xref[ci] = sp32[hi];
+        }
+    }
+}
+
+// Pair force and energies from the neighbour lists, one thread per particle
+// (cell order of the last build); results in caller order.
+__global__ void __launch_bounds__(kNearThreads) k_near_list(const BatchView bv,
+                                                            const __grid_constant__ NearSog sog,
+                                                            const uint4 *__restrict__ sp32c,
+                                                            const int32_t *__restrict__ nbr_list,
+                                                            const int32_t *__restrict__ nbr_cnt,
+                                                            const int32_t *__restrict__ list_perm,
+                                                            double4_32a *__restrict__ fnear,
+                                                            int32_t *__restrict__ nbr) {
+    __shared__ float4 s_tab[2 * kTabN];
+    const int2 w = bv.pblk[blockIdx.x];
+    if (bv.remaining && bv.remaining[w.x] == 0) return;
+    for (int k = threadIdx.x; k < 2 * kTabN; k += kNearThreads) s_tab[k] = k < kTabN ? sog.tab_g[k] : sog.tab_f[k - kTabN];
+    __syncthreads();
+    const SysDesc &d = bv.sys[w.x];
+    const int64_t sl = (int64_t)w.y * kParticleBlock + threadIdx.x;
+    if (sl >= d.n) return;
+    const BoxDev &box = d.box;
+    const int64_t s = d.p_off + sl;
+    const int i = list_perm[s];
+    const uint4 pi = sp32c[i];
+    const float qi = box.lB_f * __uint_as_float(pi.w);
+    const float fsx = box.fix_scale[0], fsy = box.fix_scale[1], fsz = box.fix_scale[2];
+    const float rc2 = box.rc2_f, wrc2 = box.wca_rc2_f, ws2 = box.wca_s2_f, weps = box.wca_eps_f;
+    const float tscale = sog.tab_scale;
+    const int cnt = min(nbr_cnt[s], bv.list_cap);
+    const int64_t stride = bv.n_total;
+    float fx = 0.f, fy = 0.f, fz = 0.f, un = 0.f, uw = 0.f;
+    int acc = 0;
+    int jn = cnt > 0 ? nbr_list[s] : 0;
+    for (int k = 0; k < cnt; ++k) {
+        const int j = jn;
+        if (k + 1 < cnt) jn = nbr_list[(int64_t)(k + 1) * stride + s];   // next index in flight
+        const uint4 pj = sp32c[j];
+        const float dx = offset_f(pi.x, pj.x, fsx), dy = offset_f(pi.y, pj.y, fsy), dz = offset_f(pi.z, pj.z, fsz);
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        if (r2 < rc2) {
+            ++acc;
+            const float qq = qi * __uint_as_float(pj.w);
+            const float x = r2 * tscale;
+            const int kt = min((int)x, kTabN - 1);
+            const float sx = x - (float)kt;
+            const float4 cg = s_tab[kt], cf = s_tab[kTabN + kt];
+            const float gs = fmaf(fmaf(fmaf(cg.w, sx, cg.z), sx, cg.y), sx, cg.x);
+            const float fs = fmaf(fmaf(fmaf(cf.w, sx, cf.z), sx, cf.y), sx, cf.x);
+            const float inv_r = rsqrtf(r2);
+            float g = qq * (inv_r * inv_r * inv_r - 2.0f * gs);
+            un += 0.5f * qq * (inv_r - fs);
+            if (r2 < wrc2) {
+                const float sr2 = ws2 / r2;
+                const float sr6 = sr2 * sr2 * sr2;
+                g += 24.0f * weps * (2.0f * sr6 * sr6 - sr6) / r2;
+                uw += 0.5f * (4.0f * weps * (sr6 * sr6 - sr6) + weps);
+            }
+            fx = fmaf(g, dx, fx);
+            fy = fmaf(g, dy, fy);
+            fz = fmaf(g, dz, fz);
+        }
+    }
+    // the two energies travel in the w slot as a pair of floats
+    fnear[i] = make_double4_32a((double)fx, (double)fy, (double)fz,
+                                __hiloint2double(__float_as_int(un), __float_as_int(uw)));
+    if (nbr) nbr[i] = acc;
+}
+
+// One running system's lists, reference positions and flag moved from one
+// batch layout (particles at old_off, ELL stride old_total) to another; a
+// list longer than the new capacity flags the system for a rebuild instead.
+__global__ void __launch_bounds__(256) k_list_move(int64_t n, int64_t old_off, int64_t new_off, int64_t old_total,
+                                                   int64_t new_total, int new_cap, const int32_t *__restrict__ old_list,
+                                                   const int32_t *__restrict__ old_cnt,
+                                                   const int32_t *__restrict__ old_perm,
+                                                   const uint4 *__restrict__ old_xref, int32_t *__restrict__ new_list,
+                                                   int32_t *__restrict__ new_cnt, int32_t *__restrict__ new_perm,
+                                                   uint4 *__restrict__ new_xref, int32_t *__restrict__ new_flag) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int cnt = old_cnt[old_off + s];
+    new_xref[new_off + s] = old_xref[old_off + s];
+    if (cnt > new_cap) {
+        new_cnt[new_off + s] = 0;
+        new_perm[new_off + s] = (int32_t)(new_off + s);
+        *new_flag = 1;
+        return;
+    }
+    const int64_t shift = new_off - old_off;
+    new_cnt[new_off + s] = cnt;
+    new_perm[new_off + s] = (int32_t)(old_perm[old_off + s] + shift);
+    for (int k = 0; k < cnt; ++k)
+        new_list[(int64_t)k * new_total + new_off + s] = (int32_t)(old_list[(int64_t)k * old_total + old_off + s] + shift);
+}
+
+__global__ void k_list_clear(int n_sys, int32_t *__restrict__ rebuild) {
+    for (int s = threadIdx.x; s <= n_sys; s += blockDim.x) rebuild[s] = 0;
+}
+
+}  // namespace
+
+size_t list_build_smem(int cap, int list_cap) {
+    (void)list_cap;
+    return (sizeof(float4) + sizeof(int)) * (size_t)cap;
+}
+
+cudaError_t launch_fix_pack(const BatchView &bv, const double4_32a *posq, uint4 *sp32c, const uint4 *xref,
+                            int32_t *rebuild, cudaStream_t st, const Prof *prof) {
+    ProfScope ps(prof, "fix_pack");
+    k_fix_pack<<<bv.n_pblk, kParticleBlock, 0, st>>>(bv, posq, sp32c, xref, rebuild);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_list_build(const BatchView &bv, const int32_t *start, const uint4 *sp32, const int32_t *perm,
+                              const int32_t *rebuild, int32_t *nbr_list, int32_t *nbr_cnt, int32_t *list_perm,
+                              uint4 *xref, int32_t *err_flag, cudaStream_t st, const Prof *prof) {
+    ProfScope ps(prof, "list_build");
+    const size_t sm = list_build_smem(bv.max_cap, bv.list_cap);
+    cudaError_t e = cudaFuncSetAttribute(k_list_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_list_build<<<bv.n_nblk, kBuildThreads, sm, st>>>(bv, start, sp32, perm, rebuild, nbr_list, nbr_cnt, list_perm,
+                                                       xref, err_flag);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_list_clear<<<1, 64, 0, st>>>(bv.n_sys, const_cast<int32_t *>(rebuild));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_list_move(int64_t n, int64_t old_off, int64_t new_off, int64_t old_total, int64_t new_total,
+                             int new_cap, const int32_t *old_list, const int32_t *old_cnt, const int32_t *old_perm,
+                             const uint4 *old_xref, int32_t *new_list, int32_t *new_cnt, int32_t *new_perm,
+                             uint4 *new_xref, int32_t *new_flag, cudaStream_t st) {
+    k_list_move<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, old_off, new_off, old_total, new_total, new_cap,
+                                                             old_list, old_cnt, old_perm, old_xref, new_list,
+                                                             new_cnt, new_perm, new_xref, new_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near_list(const BatchView &bv, const NearSog &sog, const uint4 *sp32c, const int32_t *nbr_list,
+                             const int32_t *nbr_cnt, const int32_t *list_perm, double4_32a *fnear, int32_t *nbr,
+                             cudaStream_t st, const Prof *prof) {
+    ProfScope ps(prof, "near_fp32c");
+    k_near_list<<<bv.n_pblk, kNearThreads, 0, st>>>(bv, sog, sp32c, nbr_list, nbr_cnt, list_perm, fnear, nbr);
+    return cudaGetLastError();
+}
+
+}  // namespace rbsog

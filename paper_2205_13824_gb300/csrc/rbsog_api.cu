@@ -109,6 +109,13 @@ struct rbsog_ctx {
     bool use_budget = false;
     int64_t *d_remaining = nullptr;
     std::vector<int64_t> remaining_host;
+    // FP32C neighbour lists (Verlet lists with a skin): on when every system's
+    // box holds at least 3 cells of side r_c + skin per side
+    bool use_list = false;
+    double skin = 0.0;
+    int32_t list_cap = 0;
+    uint4 *sp32c = nullptr, *xref = nullptr;
+    int32_t *nbr_list = nullptr, *nbr_cnt = nullptr, *list_perm = nullptr, *d_rebuild = nullptr;
     // pinned host mirrors
     double *h_energy = nullptr;
     int32_t *h_err = nullptr;
@@ -451,6 +458,7 @@ BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
     v.max_tile_p = c->max_tile_p;
     v.force_mask = nullptr;
     v.remaining = c->use_budget ? c->d_remaining : nullptr;
+    v.list_cap = c->use_list ? c->list_cap : 0;
     return v;
 }
 
@@ -458,9 +466,26 @@ BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
 // into c->force (caller order).  With a mask, only masked systems take the
 // new forces, energies and k-set.
 rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_sorted,
-                            double4_32a *force_out = nullptr) {
+                            double4_32a *force_out = nullptr, bool packed = false) {
     const Prof *pf = prof_of(ctx);
     const int prec = ctx->precision;
+    if (ctx->use_list && !nbr_sorted) {
+        // neighbour lists: caller-order fixed-point positions (written by the
+        // kick-drift in a step), cell list and lists of the flagged systems,
+        // listed pairs, far field in caller order
+        if (!packed) CK(launch_fix_pack(bv, ctx->posq, ctx->sp32c, ctx->xref, ctx->d_rebuild, ctx->st, pf));
+        CK(launch_build_cells(bv, ctx->posq, ctx->cb, prec, ctx->sp64, ctx->sp32, ctx->st, pf,
+                              ctx->d_rebuild + ctx->n_sys));
+        CK(launch_list_build(bv, ctx->cb.start, ctx->sp32, ctx->cb.perm, ctx->d_rebuild, ctx->nbr_list, ctx->nbr_cnt,
+                             ctx->list_perm, ctx->xref, ctx->err_flag, ctx->st, pf));
+        CK(launch_near_list(bv, ctx->nsog, ctx->sp32c, ctx->nbr_list, ctx->nbr_cnt, ctx->list_perm, ctx->fnear,
+                            nullptr, ctx->st, pf));
+        CK(launch_rho_sweep(prec, bv, ctx->sp64, ctx->sp32c, ctx->rho_part, ctx->st, pf));
+        CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
+        CK(launch_far_scatter(prec, bv, ctx->sp64, ctx->sp32c, ctx->ktab, ctx->fnear, nullptr,
+                              force_out ? force_out : ctx->force, ctx->err_flag, ctx->st, pf, ctx->epart));
+        return RBSOG_OK;
+    }
     CK(launch_build_cells(bv, ctx->posq, ctx->cb, prec, ctx->sp64, ctx->sp32, ctx->st, pf));
     CK(launch_near(prec, bv, ctx->nsog, ctx->cb.start, ctx->sp64, ctx->sp32, ctx->fnear, ctx->epart, nbr_sorted,
                    ctx->st, pf));
@@ -474,8 +499,11 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
 rbsog_status enqueue_step(rbsog_ctx *ctx) {
     const Prof *pf = prof_of(ctx);
     const BatchView bv = view(ctx);
-    CK(launch_kick_drift(bv, ctx->posq, ctx->vel, ctx->force, ctx->st, pf));
-    rbsog_status s = enqueue_forces(ctx, bv, nullptr);
+    if (ctx->use_list)
+        CK(launch_kick_drift(bv, ctx->posq, ctx->vel, ctx->force, ctx->st, pf, ctx->sp32c, ctx->xref, ctx->d_rebuild));
+    else
+        CK(launch_kick_drift(bv, ctx->posq, ctx->vel, ctx->force, ctx->st, pf));
+    rbsog_status s = enqueue_forces(ctx, bv, nullptr, nullptr, ctx->use_list);
     if (s != RBSOG_OK) return s;
     CK(launch_kick(bv, ctx->vel, ctx->force, ctx->kpart, ctx->st, pf));
     CK(launch_finalize(bv, ctx->epart, ctx->rho, ctx->kpart, 1, ctx->energy, 1, ctx->st, pf));
@@ -499,6 +527,9 @@ rbsog_status check_flags(rbsog_ctx *ctx) {
         CK(cudaMemsetAsync(ctx->err_flag, 0, sizeof(int32_t), ctx->st));
         if (f & 1) return fail(ctx, RBSOG_ENUMERIC, "non-finite force produced on the device");
         if (f & 2) return fail(ctx, RBSOG_ETIMEOUT, "a sampler chain hit its iteration cap");
+        if (f & 4)
+            return fail(ctx, RBSOG_ENUMERIC, "a neighbour list exceeded its capacity (local density far above the "
+                                             "system's mean)");
         return fail(ctx, RBSOG_ECUDA, "device error flag %d", f);
     }
     return RBSOG_OK;
@@ -507,6 +538,17 @@ rbsog_status check_flags(rbsog_ctx *ctx) {
 rbsog_status upload_desc(rbsog_ctx *ctx) {
     CK(cudaMemcpyAsync(ctx->d_desc, ctx->desc.data(), sizeof(SysDesc) * ctx->n_sys, cudaMemcpyHostToDevice,
                        ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return RBSOG_OK;
+}
+
+// New positions for system s: its neighbour lists are rebuilt before they
+// are used next.
+rbsog_status flag_rebuild(rbsog_ctx *ctx, int s) {
+    if (!ctx->use_list) return RBSOG_OK;
+    static const int32_t one = 1;
+    CK(cudaMemcpyAsync(ctx->d_rebuild + s, &one, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->d_rebuild + ctx->n_sys, &one, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return RBSOG_OK;
 }
@@ -556,9 +598,18 @@ rbsog_status apply_layout(rbsog_ctx *ctx) {
     for (int s = 0; s < ctx->n_sys; ++s) {
         SysDesc &d = ctx->desc[s];
         int nblocks = 0, npart = 0;
-        near_layout(d.box, d.n, ctx->precision, ctx->tune[s].home, d.group, d.nseg_x, d.near_cap, nblocks, npart);
+        // with neighbour lists the cell-row blocks only build lists: about
+        // 112 home particles fill the builder's 128 threads in one round
+        const int home = ctx->use_list ? 112 : ctx->tune[s].home;
+        near_layout(d.box, d.n, ctx->precision, home, d.group, d.nseg_x, d.near_cap, nblocks, npart);
         d.e_off = (int32_t)e_off;
         d.n_epart = npart;
+        if (ctx->use_list) {
+            // energies come per particle block (the cell-stencil kernel, which
+            // rbsog_get_cells still runs, writes one per near block: room for both)
+            d.n_epart = d.n_kpart;
+            npart = std::max(npart, d.n_kpart);
+        }
         far_layout(d.n, ctx->P, ctx->tune[s].tile, d.tile_p, d.n_ptiles);
         d.rp_off = rp_off;
         for (int b = 0; b < nblocks; ++b) ctx->nblk.push_back(make_int2(s, b));
@@ -676,6 +727,26 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
     const int ns = ctx->n_sys;
     std::vector<rbsog_params> p(pp, pp + ns);
     std::vector<BoxDev> box(ns);
+    // FP32C uses neighbour lists with a skin of r_c / 10 when every box holds
+    // at least 3 cells of side r_c + skin per side (else the cell stencil)
+    const double skin = 0.1 * p[0].r_c;
+    bool lists = p[0].precision == RBSOG_FP32C && p[0].r_c > 0.0;
+    for (int s = 0; s < ns && lists; ++s)
+        for (int d = 0; d < 3; ++d)
+            if (!(p[s].L[d] > 0.0) || std::floor(p[s].L[d] / (p[s].r_c + skin)) < 3.0) lists = false;
+    // slots per particle: 1.5 x the mean count within r_c + skin at the
+    // densest system of the batch, plus 48; the builder keeps them per
+    // thread in shared memory, which bounds them (denser: cell stencil)
+    int32_t list_cap = 0;
+    if (lists) {
+        double rho_max = 0.0;
+        for (int s = 0; s < ns; ++s)
+            rho_max = std::max(rho_max, (double)ctx->n_per[s] / (p[s].L[0] * p[s].L[1] * p[s].L[2]));
+        const double rl = p[0].r_c + skin;
+        const double mean = 4.0 / 3.0 * kPi * rl * rl * rl * rho_max;
+        list_cap = (((int)(1.5 * mean) + 48) + 7) / 8 * 8;
+        if (list_cap > 280) lists = false;
+    }
     for (int s = 0; s < ns; ++s) {
         const rbsog_params &q = p[s];
         if (!(q.b > 1.0)) return fail(ctx, RBSOG_EINVAL, "system %d: b must be > 1", s);
@@ -698,8 +769,9 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         for (int d = 0; d < 3; ++d) {
             if (!(q.L[d] > 0.0)) return fail(ctx, RBSOG_EINVAL, "system %d: box edges must be > 0", s);
             if (!(q.r_c < 0.5 * q.L[d])) return fail(ctx, RBSOG_EINVAL, "system %d: r_c must be < L/2", s);
-            b.nc[d] = (int)std::floor(q.L[d] / q.r_c);
-            if (b.nc[d] < 3) return fail(ctx, RBSOG_EINVAL, "system %d: need at least 3 cells per side (L/r_c >= 3)", s);
+            if (std::floor(q.L[d] / q.r_c) < 3.0)
+                return fail(ctx, RBSOG_EINVAL, "system %d: need at least 3 cells per side (L/r_c >= 3)", s);
+            b.nc[d] = (int)std::floor(q.L[d] / (lists ? q.r_c + skin : q.r_c));
             ncell *= b.nc[d];
             b.L[d] = q.L[d];
             b.h[d] = q.L[d] / (double)b.nc[d];
@@ -722,6 +794,9 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         b.wca_s2_f = (float)b.wca_s2;
         b.wca_rc2_f = (float)b.wca_rc2;
         b.wca_eps_f = (float)b.wca_eps;
+        const double rl = q.r_c + skin;
+        b.rl2_f = (float)(rl * rl * (1.0 + 1e-5));
+        b.disp2_f = (float)(0.25 * skin * skin * (1.0 - 1e-4));
     }
 
     // --- SOG (Eqs. 2.9-2.11), shared by the batch
@@ -810,6 +885,23 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
     CK(dalloc(&ctx->m3_tmp, (size_t)ctx->P * 3));
     CK(dalloc(&ctx->d_pblk, ctx->pblk.size()));
     CK(dalloc(&ctx->d_cell_sys, cell_sys.size()));
+    ctx->use_list = lists;
+    ctx->skin = lists ? skin : 0.0;
+    ctx->list_cap = lists ? list_cap : 0;
+    if (lists) {
+        const size_t n = (size_t)ctx->n_total;
+        CK(dalloc(&ctx->sp32c, n));
+        CK(dalloc(&ctx->xref, n));
+        CK(dalloc(&ctx->nbr_cnt, n));
+        CK(dalloc(&ctx->list_perm, n));
+        CK(dalloc(&ctx->nbr_list, n * (size_t)ctx->list_cap));
+        CK(dalloc(&ctx->d_rebuild, (size_t)ns + 1));
+        CK(cudaMemset(ctx->xref, 0, sizeof(uint4) * n));
+        CK(cudaMemset(ctx->nbr_cnt, 0, sizeof(int32_t) * n));
+        CK(cudaMemset(ctx->list_perm, 0, sizeof(int32_t) * n));
+        std::vector<int32_t> ones((size_t)ns + 1, 1);
+        CK(cudaMemcpy(ctx->d_rebuild, ones.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice));
+    }
     rbsog_status es = enter(ctx);
     if (es != RBSOG_OK) return es;
     es = apply_layout(ctx);
@@ -908,6 +1000,7 @@ rbsog_status rbsog_batch_autotune(rbsog_batch *ctx, int32_t reps, int32_t *chose
     Tune best_t;
     float best_ms = 1e30f;
     for (int h : homes) {
+        if (ctx->use_list && h != homes[0]) break;   // the block size only shapes the list builder
         Tune t;
         t.home = h;
         float ms = 0.f;
@@ -1001,6 +1094,8 @@ rbsog_status rbsog_batch_set_state(rbsog_batch *ctx, int32_t sys, const double *
     }
     CK(cudaFreeAsync(qd, ctx->st));
     CK(cudaMemsetAsync(ctx->step_ctr + sys, 0, sizeof(int64_t), ctx->st));
+    es = flag_rebuild(ctx, sys);
+    if (es != RBSOG_OK) return es;
     drop_graph(ctx);
     ctx->have_state[sys] = 1;
     ctx->force_valid[sys] = 0;
@@ -1383,6 +1478,12 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->cb.perm_raw);
     dfree(&ctx->cb.perm);
     dfree(&ctx->cb.key);
+    dfree(&ctx->sp32c);
+    dfree(&ctx->xref);
+    dfree(&ctx->nbr_cnt);
+    dfree(&ctx->list_perm);
+    dfree(&ctx->nbr_list);
+    dfree(&ctx->d_rebuild);
     dfree(&ctx->cb.pack);
     dfree(&ctx->kpart);
     dfree(&ctx->kseq);
@@ -1529,6 +1630,16 @@ rbsog_status rebuild(rbsog_server *sv, const std::vector<int64_t> &keep, const s
         CK(cudaMemcpyAsync(nb->step_ctr + k, old->step_ctr + o, sizeof(int64_t), cudaMemcpyDeviceToDevice, nb->st));
         CK(cudaMemcpyAsync(nb->energy + k * kNumEnergy, old->energy + (int64_t)o * kNumEnergy,
                            sizeof(double) * kNumEnergy, cudaMemcpyDeviceToDevice, nb->st));
+        if (nb->use_list && old->use_list) {
+            // the running system keeps its neighbour lists, reference
+            // positions and rebuild flag: its trajectory is the one it
+            // follows alone
+            CK(cudaMemcpyAsync(nb->d_rebuild + k, old->d_rebuild + o, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                               nb->st));
+            CK(launch_list_move(n, od.p_off, ndsc.p_off, old->n_total, nb->n_total, nb->list_cap, old->nbr_list,
+                                old->nbr_cnt, old->list_perm, old->xref, nb->nbr_list, nb->nbr_cnt, nb->list_perm,
+                                nb->xref, nb->d_rebuild + k, nb->st));
+        }
         nb->have_state[k] = 1;
         nb->force_valid[k] = old->force_valid[o];
         nb->host_cursor[k] = old->host_cursor[o];

@@ -55,6 +55,8 @@ struct BoxDev {
     float fix_scale[3];   // L_d / 2^32: fixed-point unit of the FP32C positions
     double fix_inv[3];    // 2^32 / L_d: X_d = trunc(x_d * fix_inv[d]), clamped to [0, 2^32 - 1]
     float cell_fix[3];    // 2^32 / nc_d: fixed-point length of one cell side
+    float rl2_f;          // neighbour lists: (r_c + skin)^2, with a margin above FP32 rounding
+    float disp2_f;        // neighbour lists: (skin / 2)^2, with a margin below it
     double inv_h[3];      // nc_d / L_d: cell of x is floor(x_d * inv_h[d]) (clamped)
     float h_f[3];         // h_d in FP32
     // FP32 copies of the pair constants (no double->float conversion in kernels)
@@ -145,8 +147,41 @@ struct BatchView {
                                // (skipped by every step kernel); null: no budgets
     int32_t max_cap;           // largest near staging chunk of the batch
     int32_t max_tile_p;        // largest rho-sweep tile of the batch
+    int32_t list_cap;          // neighbour-list slots per particle (0: no lists)
 };
 constexpr int kParticleBlock = 256;
+
+// X = trunc(x * (2^32 / L)) clamped to [0, 2^32 - 1]: the fixed-point
+// coordinate of the FP32C path (one FP64 multiply; the scale comes from the
+// host).
+__device__ __forceinline__ uint32_t fixed32(double x, double inv) {
+    const double t = x * inv;
+    const double c = t < 0.0 ? 0.0 : (t > 4294967295.0 ? 4294967295.0 : t);
+    return (uint32_t)__double2ull_rz(c);
+}
+
+// Caller-order fixed-point position (x, y, z, FP32 charge) of particle i for
+// the neighbour-list path, and the test of its displacement since the last
+// list build: a particle of system `sys` that moved more than skin / 2 sets
+// rebuild[sys] and rebuild[n_sys] (any system).
+__device__ __forceinline__ void fixed_pack_check(const SysDesc &d, int sys, int n_sys, const double4_32a &p,
+                                                 int64_t i, uint4 *__restrict__ sp32c,
+                                                 const uint4 *__restrict__ xref, int32_t *__restrict__ rebuild) {
+    uint4 o;
+    o.x = fixed32(p.x, d.box.fix_inv[0]);
+    o.y = fixed32(p.y, d.box.fix_inv[1]);
+    o.z = fixed32(p.z, d.box.fix_inv[2]);
+    o.w = __float_as_uint((float)p.w);
+    sp32c[i] = o;
+    const uint4 r = xref[i];
+    const float dx = (float)(int32_t)(o.x - r.x) * d.box.fix_scale[0];
+    const float dy = (float)(int32_t)(o.y - r.y) * d.box.fix_scale[1];
+    const float dz = (float)(int32_t)(o.z - r.z) * d.box.fix_scale[2];
+    if (fmaf(dz, dz, fmaf(dy, dy, dx * dx)) > d.box.disp2_f && !rebuild[sys]) {
+        rebuild[sys] = 1;
+        rebuild[n_sys] = 1;
+    }
+}
 
 // ---- cell list (k_cells.cu) ---------------------------------------------------
 struct CellBuffers {
@@ -163,9 +198,11 @@ struct CellBuffers {
 int cell_scan_tiles(int64_t ncell);
 // precision 0: gather FP64 (x, y, z, q) into sp64; 1: 32-bit fixed point
 // positions and FP32 charge into sp32.
+// gate (device flag, may be null): when non-null and zero, every kernel of
+// the build returns at once (the neighbour-list path rebuilds only on demand).
 cudaError_t launch_build_cells(const BatchView &bv, const double4_32a *posq, const CellBuffers &cb,
                                int precision, double4_32a *sp64, uint4 *sp32, cudaStream_t st,
-                               const Prof *prof);
+                               const Prof *prof, const int32_t *gate = nullptr);
 
 // ---- near field (k_near.cu) ---------------------------------------------------
 // Forces (cell order) into fnear; energy partials (U_near, U_wca), one per
@@ -177,6 +214,31 @@ cudaError_t launch_near(int precision, const BatchView &bv, const NearSog &sog, 
                         const double4_32a *sp64, const uint4 *sp32, double4_32a *fnear, double2 *epart,
                         int32_t *nbr, cudaStream_t st, const Prof *prof);
 
+// ---- neighbour lists (k_verlet.cu), FP32C ------------------------------------
+// Lists: ELL, nbr_list[slot * n_total + s] for the particle at cell-order
+// position s of the last build (list_perm[s] its caller index), nbr_cnt[s]
+// entries sorted by caller index; xref[i] the fixed-point position of caller
+// particle i at that build; rebuild[n_sys + 1] flags (per system, any).
+size_t list_build_smem(int cap, int list_cap);
+cudaError_t launch_fix_pack(const BatchView &bv, const double4_32a *posq, uint4 *sp32c, const uint4 *xref,
+                            int32_t *rebuild, cudaStream_t st, const Prof *prof);
+// Rebuilds the lists of flagged systems from the cell list (cell-order sp32,
+// perm) and clears the flags.  err_flag bit 4: a list exceeded list_cap.
+cudaError_t launch_list_build(const BatchView &bv, const int32_t *start, const uint4 *sp32, const int32_t *perm,
+                              const int32_t *rebuild, int32_t *nbr_list, int32_t *nbr_cnt, int32_t *list_perm,
+                              uint4 *xref, int32_t *err_flag, cudaStream_t st, const Prof *prof);
+// Moves one running system's lists between batch layouts (serving engine).
+cudaError_t launch_list_move(int64_t n, int64_t old_off, int64_t new_off, int64_t old_total, int64_t new_total,
+                             int new_cap, const int32_t *old_list, const int32_t *old_cnt, const int32_t *old_perm,
+                             const uint4 *old_xref, int32_t *new_list, int32_t *new_cnt, int32_t *new_perm,
+                             uint4 *new_xref, int32_t *new_flag, cudaStream_t st);
+// Near-field force (caller order) with both energies packed in fnear[i].w as
+// two floats (U_near high word, U_wca low word); accepted pairs into nbr[i]
+// when non-null.
+cudaError_t launch_near_list(const BatchView &bv, const NearSog &sog, const uint4 *sp32c, const int32_t *nbr_list,
+                             const int32_t *nbr_cnt, const int32_t *list_perm, double4_32a *fnear, int32_t *nbr,
+                             cudaStream_t st, const Prof *prof);
+
 // ---- far field (k_far.cu) -----------------------------------------------------
 // tile_override > 0 replaces the default particles-per-tile rule (tunable)
 void far_layout(int64_t n, int32_t P, int tile_override, int &tile_p, int &n_ptiles);
@@ -186,19 +248,25 @@ cudaError_t launch_rho_sweep(int precision, const BatchView &bv, const double4_3
 // scatter table (k vector, prescaled Re/Im rho, integer m).
 cudaError_t launch_rho_combine(int precision, const BatchView &bv, const double2 *rho_part, double2 *rho,
                                void *ktab, cudaStream_t st, const Prof *prof);
-// Total force (near + far) written to force[perm[s]] in caller order.
+// Total force (near + far) written to force[perm[s]] in caller order.  With
+// perm null the particles are already in caller order (neighbour-list path):
+// force[s] = fnear[s] + far, and the per-particle energies packed in
+// fnear[s].w are summed per particle block into epart[e_off + block].
 cudaError_t launch_far_scatter(int precision, const BatchView &bv, const double4_32a *sp64,
                                const uint4 *sp32, const void *ktab, const double4_32a *fnear,
                                const int32_t *perm, double4_32a *force, int32_t *err_flag, cudaStream_t st,
-                               const Prof *prof);
+                               const Prof *prof, double2 *epart = nullptr);
 size_t ktab_bytes(int precision, int64_t nk);
 
 // ---- integrator and reductions (k_md.cu) --------------------------------------
 // Device energies per system, 8 doubles: [0] U_near [1] U_far [2] U_self
 // [3] U_wca [4] K [5] T [6] lambda
 constexpr int kNumEnergy = 8;
+// With sp32c non-null (neighbour-list path) it also writes the fixed-point
+// caller-order positions and runs the displacement test (fixed_pack_check).
 cudaError_t launch_kick_drift(const BatchView &bv, double4_32a *posq, double4_32a *vel,
-                              const double4_32a *force, cudaStream_t st, const Prof *prof);
+                              const double4_32a *force, cudaStream_t st, const Prof *prof,
+                              uint4 *sp32c = nullptr, const uint4 *xref = nullptr, int32_t *rebuild = nullptr);
 cudaError_t launch_kick(const BatchView &bv, double4_32a *vel, const double4_32a *force, double *kpart,
                         cudaStream_t st, const Prof *prof);
 // One block per system: sums energy partials in fixed order, U_far from rho,
