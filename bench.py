@@ -120,7 +120,7 @@ def electrolyte_state(N, L, seed):
 
 # ncu summaries (profiles/) holding the DRAM traffic of a kernel at this
 # workload, with the hash of the kernel source they were taken from
-PROFILE_OF = {"near": ("near_fp32c_electrolyte_N1048576.md", "k_near.cu"),
+PROFILE_OF = {"near": ("near_fp32c_lists_electrolyte_N1048576.md", "k_verlet.cu"),
               "rho_sweep": ("rho_sweep_fp32c_electrolyte_N1048576_P500.md", "k_far.cu"),
               "far_scatter": ("far_scatter_fp32c_electrolyte_N1048576_P500.md", "k_far.cu")}
 
@@ -149,7 +149,7 @@ def profiled_traffic(kernel, N, P):
     return None
 
 
-def roofline_for(name, launches, ms_total, N, L, P, rc, meas, hbm_gbs):
+def roofline_for(name, launches, ms_total, N, L, P, rc, meas, hbm_gbs, lists=False):
     """Algorithmic work of one launch over its average CUDA-event duration,
     against the rate measured on this GPU by rbsog_measure_peaks."""
     t = ms_total / launches / 1e3
@@ -162,17 +162,23 @@ def roofline_for(name, launches, ms_total, N, L, P, rc, meas, hbm_gbs):
                    peak_basis="measured MUFU sin+cos rate / 2 (rbsog_measure_peaks)")
         return out
     if name.startswith("near"):
-        # FP32 instruction-equivalents: 8 per candidate distance test over the
-        # 27-cell stencil, 50 per pair inside r_c (MUFU ops counted once)
-        ncell = math.floor(L / rc) ** 3
-        cand = 27.0 * N / ncell
+        # FP32 instruction-equivalents: 8 per candidate distance test, 50 per
+        # pair inside r_c (MUFU ops counted once).  Candidates: the particles
+        # within r_c + skin of the neighbour-list method (skin = r_c / 10), or
+        # the 27-cell stencil when the step runs without lists
         pairs = 4.0 / 3.0 * math.pi * rc ** 3 * N / L ** 3
+        if lists:
+            cand = 4.0 / 3.0 * math.pi * (1.1 * rc) ** 3 * N / L ** 3
+            basis = "candidate test within r_c + skin"
+        else:
+            cand = 27.0 * N / math.floor(L / rc) ** 3
+            basis = "candidate test over the 27-cell stencil"
         ops = N * (8.0 * cand + 50.0 * pairs)
         achieved = ops / t / 1e12
         peak = meas["fma32_per_s"] / 1e12
         out.update(bound="alu", achieved=achieved, peak=peak, unit="Top/s", frac=achieved / peak,
                    peak_basis="measured FP32 FMA issue rate (rbsog_measure_peaks); work = 8 FP32 ops per "
-                              "candidate test + 50 per pair within r_c")
+                              + basis + " + 50 per pair within r_c")
         return out
     achieved = N * 64 / t / 1e9
     out.update(bound="hbm", achieved=achieved, peak=hbm_gbs, unit="GB/s", frac=achieved / hbm_gbs)
@@ -272,10 +278,13 @@ def run_ours(args, rank, world, local, dist):
 
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6686.1)
+    lists = "list_build" in prof
     top = max(prof.items(), key=lambda kv: kv[1][1])
-    roof = roofline_for(top[0], top[1][0], top[1][1], N, L, P, 3.0, meas, hbm)
+    roof = roofline_for(top[0], top[1][0], top[1][1], N, L, P, 3.0, meas, hbm, lists)
     roof_far = [roofline_for(k, c, t, N, L, P, 3.0, meas, hbm) for k, (c, t) in prof.items()
                 if k.startswith(("rho_sweep", "far_scatter"))]
+    roof_near = [roofline_for(k, c, t, N, L, P, 3.0, meas, hbm, lists) for k, (c, t) in prof.items()
+                 if k.startswith("near")]
     kernels = {k: {"launches": c, "ms_per_launch": t / c, "share": t / sum(tt for _, tt in prof.values())}
                for k, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     value = world * N / (ms / 1e3)
@@ -293,6 +302,9 @@ def run_ours(args, rank, world, local, dist):
         "gpu_launches": int(round(launches_per_step * K)),
         "roofline": roof,
         "roofline_far_field": roof_far,
+        "roofline_near_field": roof_near,
+        "near_field_method": "neighbour lists, skin r_c/10, rebuilt on a displacement test" if lists
+                             else "cell stencil",
         "measured_peaks": {"mufu_per_s": meas["mufu_per_s"], "fma32_per_s": meas["fma32_per_s"],
                            "fma64_per_s": meas["fma64_per_s"], "sm_mhz": meas["sm_mhz"]},
         "clocks": clocks,

@@ -279,12 +279,13 @@ __global__ void __launch_bounds__(kScatterThreads)
     if (active) fn = fnear[s];
     if (!perm) {
         // caller order (neighbour-list path): the block's near energies, two
-        // floats per particle in fn.w, summed in fixed order (warps, then
-        // the warps in order) into one partial per particle block
-        double en = 0.0, ew = 0.0;
+        // floats per particle in fn.w, summed in fixed order (an FP32 tree
+        // per warp -- FP64 adds are scarce on this GPU -- then the warps in
+        // FP64, in order) into one partial per particle block
+        float en = 0.f, ew = 0.f;
         if (active) {
-            en = (double)__int_as_float(__double2hiint(fn.w));
-            ew = (double)__int_as_float(__double2loint(fn.w));
+            en = __int_as_float(__double2hiint(fn.w));
+            ew = __int_as_float(__double2loint(fn.w));
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(kScatterThreads)
             ew += __shfl_down_sync(0xffffffffu, ew, o);
         }
         __shared__ double2 s_e[kScatterThreads / 32];
-        if ((tid & 31) == 0) s_e[tid >> 5] = make_double2(en, ew);
+        if ((tid & 31) == 0) s_e[tid >> 5] = make_double2((double)en, (double)ew);
         __syncthreads();
         if (tid == 0) {
             double2 t = s_e[0];

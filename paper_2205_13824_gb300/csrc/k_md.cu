@@ -267,6 +267,31 @@ cudaError_t launch_step_done(const BatchView &bv, cudaStream_t st, const Prof *p
     return cudaGetLastError();
 }
 
+// Per block of 256 charges: (sum q, sum |q|, sum q^2) in FP64, the threads'
+// terms combined in a fixed tree order.
+__global__ void __launch_bounds__(256) k_charge_sums(int64_t n, const double *__restrict__ q,
+                                                     double *__restrict__ part) {
+    __shared__ double s[3][256];
+    const int tid = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * 256 + tid;
+    const double v = i < n ? q[i] : 0.0;
+    s[0][tid] = v;
+    s[1][tid] = fabs(v);
+    s[2][tid] = v * v;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (tid < h)
+            for (int c = 0; c < 3; ++c) s[c][tid] += s[c][tid + h];
+        __syncthreads();
+    }
+    if (tid < 3) part[3 * blockIdx.x + tid] = s[tid][0];
+}
+
+cudaError_t launch_charge_sums(int64_t n, const double *q, double *part, cudaStream_t st) {
+    k_charge_sums<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, q, part);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack(int64_t n, const double *x3, const double *q, double4_32a *out, int wrap,
                         const double *L, cudaStream_t st) {
     k_pack<<<nblk(n), kThreads, 0, st>>>(n, x3, q, out, wrap, L[0], L[1], L[2]);

@@ -88,7 +88,9 @@ struct rbsog_ctx {
     // device buffers
     double4_32a *posq = nullptr, *vel = nullptr, *force = nullptr, *fnear = nullptr, *sp64 = nullptr;
     uint4 *sp32 = nullptr;
-    double *staging = nullptr;        // [n_total][3]
+    double *staging = nullptr;        // [10 n_total]: three [n][3] regions and one [n]
+    double *qpart = nullptr;          // [3 ceil(n_total / 256)] charge sums per block
+    double *h_qpart = nullptr;        // pinned mirror of qpart
     int32_t *nbr_sorted = nullptr, *i32_tmp = nullptr;
     CellBuffers cb{};
     double *kpart = nullptr;
@@ -542,17 +544,6 @@ rbsog_status upload_desc(rbsog_ctx *ctx) {
     return RBSOG_OK;
 }
 
-// New positions for system s: its neighbour lists are rebuilt before they
-// are used next.
-rbsog_status flag_rebuild(rbsog_ctx *ctx, int s) {
-    if (!ctx->use_list) return RBSOG_OK;
-    static const int32_t one = 1;
-    CK(cudaMemcpyAsync(ctx->d_rebuild + s, &one, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaMemcpyAsync(ctx->d_rebuild + ctx->n_sys, &one, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
-    return RBSOG_OK;
-}
-
 double self_energy(const rbsog_ctx *c, int s) {
     double wsum = 0.0;
     for (size_t l = 0; l < c->omega.size(); ++l) wsum += c->omega[l];
@@ -683,7 +674,8 @@ rbsog_status rbsog_batch_create(rbsog_batch **out, int32_t n_sys, const int64_t 
     bool ok = dalloc(&ctx->posq, n) == cudaSuccess && dalloc(&ctx->vel, n) == cudaSuccess &&
               dalloc(&ctx->force, n) == cudaSuccess && dalloc(&ctx->fnear, n) == cudaSuccess &&
               dalloc(&ctx->sp64, n) == cudaSuccess && dalloc(&ctx->sp32, n) == cudaSuccess &&
-              dalloc(&ctx->staging, 3 * n) == cudaSuccess && dalloc(&ctx->nbr_sorted, n) == cudaSuccess &&
+              dalloc(&ctx->staging, 10 * n) == cudaSuccess &&
+              dalloc(&ctx->qpart, 3 * ((n + 255) / 256)) == cudaSuccess && dalloc(&ctx->nbr_sorted, n) == cudaSuccess &&
               dalloc(&ctx->i32_tmp, n) == cudaSuccess && dalloc(&ctx->cb.cell_of, n) == cudaSuccess &&
               dalloc(&ctx->cb.slot, n) == cudaSuccess && dalloc(&ctx->cb.perm_raw, n) == cudaSuccess &&
               dalloc(&ctx->cb.perm, n) == cudaSuccess && dalloc(&ctx->cb.key, n) == cudaSuccess &&
@@ -695,7 +687,8 @@ rbsog_status rbsog_batch_create(rbsog_batch **out, int32_t n_sys, const int64_t 
     if (!ok) return bail(RBSOG_ENOMEM);
     if (cudaMallocHost((void **)&ctx->h_energy, sizeof(double) * kNumEnergy) != cudaSuccess ||
         cudaMallocHost((void **)&ctx->h_err, sizeof(int32_t)) != cudaSuccess ||
-        cudaMallocHost((void **)&ctx->h_i64, sizeof(int64_t)) != cudaSuccess)
+        cudaMallocHost((void **)&ctx->h_i64, 4 * sizeof(int64_t)) != cudaSuccess ||
+        cudaMallocHost((void **)&ctx->h_qpart, sizeof(double) * 3 * ((n + 255) / 256)) != cudaSuccess)
         return bail(RBSOG_ENOMEM);
     cudaMemsetAsync(ctx->vel, 0, sizeof(double4_32a) * n, ctx->st);
     cudaMemsetAsync(ctx->force, 0, sizeof(double4_32a) * n, ctx->st);
@@ -1066,37 +1059,37 @@ rbsog_status rbsog_batch_set_state(rbsog_batch *ctx, int32_t sys, const double *
     es = enter(ctx);
     if (es != RBSOG_OK) return es;
     const int64_t n = ctx->n_per[sys], off = ctx->p_off[sys];
-    std::vector<double> hq((size_t)n);
-    CK(cudaMemcpyAsync(hq.data(), q, sizeof(double) * n, cudaMemcpyDefault, ctx->st));
+    // inputs (host or device) land in the staging regions; the charge sums
+    // for the neutrality check and the self energy are block sums on the
+    // device, added on the host in block order
+    double *sx = ctx->staging, *sv = ctx->staging + 3 * n, *sq = ctx->staging + 9 * n;
+    CK(cudaMemcpyAsync(sq, q, sizeof(double) * n, cudaMemcpyDefault, ctx->st));
+    CK(cudaMemcpyAsync(sx, x, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
+    if (v) CK(cudaMemcpyAsync(sv, v, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
+    const int64_t nb = (n + 255) / 256;
+    CK(launch_charge_sums(n, sq, ctx->qpart, ctx->st));
+    CK(cudaMemcpyAsync(ctx->h_qpart, ctx->qpart, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    double sq = 0.0, sa = 0.0, s2 = 0.0;
-    for (double qi : hq) {
-        if (!std::isfinite(qi)) return fail(ctx, RBSOG_EINVAL, "non-finite charge");
-        sq += qi;
-        sa += std::fabs(qi);
-        s2 += qi * qi;
+    double qs = 0.0, qa = 0.0, q2 = 0.0;
+    for (int64_t b = 0; b < nb; ++b) {
+        qs += ctx->h_qpart[3 * b];
+        qa += ctx->h_qpart[3 * b + 1];
+        q2 += ctx->h_qpart[3 * b + 2];
     }
-    if (std::fabs(sq) > 1e-12 * sa) return fail(ctx, RBSOG_EINVAL, "charges are not neutral (sum %.3e)", sq);
-    ctx->sum_q2[sys] = s2;
+    if (!std::isfinite(qa)) return fail(ctx, RBSOG_EINVAL, "non-finite charge");
+    if (std::fabs(qs) > 1e-12 * qa) return fail(ctx, RBSOG_EINVAL, "charges are not neutral (sum %.3e)", qs);
+    ctx->sum_q2[sys] = q2;
     ctx->desc[sys].U_self = self_energy(ctx, sys);
-    es = upload_desc(ctx);
-    if (es != RBSOG_OK) return es;
-    double *qd = nullptr;
-    CK(cudaMallocAsync((void **)&qd, sizeof(double) * n, ctx->st));
-    CK(cudaMemcpyAsync(qd, q, sizeof(double) * n, cudaMemcpyDefault, ctx->st));
-    CK(cudaMemcpyAsync(ctx->staging, x, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
-    CK(launch_pack(n, ctx->staging, qd, ctx->posq + off, 1, ctx->p[sys].L, ctx->st));
-    if (v) {
-        CK(cudaMemcpyAsync(ctx->staging, v, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
-        CK(launch_pack(n, ctx->staging, nullptr, ctx->vel + off, 0, ctx->p[sys].L, ctx->st));
-    } else {
-        CK(cudaMemsetAsync(ctx->vel + off, 0, sizeof(double4_32a) * n, ctx->st));
-    }
-    CK(cudaFreeAsync(qd, ctx->st));
+    CK(cudaMemcpyAsync(&ctx->d_desc[sys].U_self, &ctx->desc[sys].U_self, sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->st));
+    CK(launch_pack(n, sx, sq, ctx->posq + off, 1, ctx->p[sys].L, ctx->st));
+    if (v) CK(launch_pack(n, sv, nullptr, ctx->vel + off, 0, ctx->p[sys].L, ctx->st));
+    else CK(cudaMemsetAsync(ctx->vel + off, 0, sizeof(double4_32a) * n, ctx->st));
     CK(cudaMemsetAsync(ctx->step_ctr + sys, 0, sizeof(int64_t), ctx->st));
-    es = flag_rebuild(ctx, sys);
-    if (es != RBSOG_OK) return es;
-    drop_graph(ctx);
+    CK(cudaStreamSynchronize(ctx->st));   // the caller may reuse its buffers
+    // neighbour lists stay valid while every particle is within skin/2 of
+    // its position at the last build: the displacement test of the next
+    // force evaluation decides, for new positions as for integrated ones
     ctx->have_state[sys] = 1;
     ctx->force_valid[sys] = 0;
     return leave(ctx);
@@ -1214,9 +1207,9 @@ rbsog_status rbsog_batch_get_state(rbsog_batch *ctx, int32_t sys, double *x, dou
     double *dst[3] = {x, v, f};
     for (int k = 0; k < 3; ++k) {
         if (!dst[k]) continue;
-        CK(launch_unpack(n, src[k], ctx->staging, ctx->st));
-        CK(cudaMemcpyAsync(dst[k], ctx->staging, bytes, cudaMemcpyDefault, ctx->st));
-        CK(cudaStreamSynchronize(ctx->st));
+        double *reg = ctx->staging + 3 * n * k;
+        CK(launch_unpack(n, src[k], reg, ctx->st));
+        CK(cudaMemcpyAsync(dst[k], reg, bytes, cudaMemcpyDefault, ctx->st));
     }
     if (step) {
         CK(cudaMemcpyAsync(ctx->h_i64, ctx->step_ctr + sys, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->st));
@@ -1468,6 +1461,9 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->sp64);
     dfree(&ctx->sp32);
     dfree(&ctx->staging);
+    dfree(&ctx->qpart);
+    if (ctx->h_qpart) cudaFreeHost(ctx->h_qpart);
+    ctx->h_qpart = nullptr;
     dfree(&ctx->nbr_sorted);
     dfree(&ctx->i32_tmp);
     dfree(&ctx->cb.cell_of);

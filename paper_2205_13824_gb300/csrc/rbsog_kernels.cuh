@@ -279,6 +279,8 @@ cudaError_t launch_rescale(const BatchView &bv, double4_32a *vel, const double *
                            const Prof *prof);
 // With step budgets: one step of every unfrozen system is done.
 cudaError_t launch_step_done(const BatchView &bv, cudaStream_t st, const Prof *prof);
+// Charge sums per block of 256: part[3 b + (0, 1, 2)] = (sum q, sum |q|, sum q^2).
+cudaError_t launch_charge_sums(int64_t n, const double *q, double *part, cudaStream_t st);
 // Layout conversions between caller [n][3] arrays and the internal double4_32a.
 cudaError_t launch_pack(int64_t n, const double *x3, const double *q, double4_32a *out, int wrap,
                         const double *L, cudaStream_t st);
