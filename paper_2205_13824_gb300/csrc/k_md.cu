@@ -67,8 +67,17 @@ __global__ void __launch_bounds__(kThreads) k_kick(BatchView bv, double4_32a *__
         vel[i] = v;
         ke = 0.5 * a.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
     }
+    if (bv.precision == 1) {
+        // FP32C: the warp's terms in an FP32 tree (FP64 adds are scarce on
+        // this GPU), the warps in FP64
+        float kf = (float)ke;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ke += __shfl_down_sync(0xffffffffu, ke, o);
+        for (int o = 16; o > 0; o >>= 1) kf += __shfl_down_sync(0xffffffffu, kf, o);
+        ke = (double)kf;
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ke += __shfl_down_sync(0xffffffffu, ke, o);
+    }
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = ke;
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -244,11 +244,9 @@ __global__ void __launch_bounds__(kNearThreads) k_near_list(const BatchView bv,
     const int64_t stride = bv.n_total;
     float fx = 0.f, fy = 0.f, fz = 0.f, un = 0.f, uw = 0.f;
     int acc = 0;
-    int jn = cnt > 0 ? nbr_list[s] : 0;
-    for (int k = 0; k < cnt; ++k) {
-        const int j = jn;
-        if (k + 1 < cnt) jn = nbr_list[(int64_t)(k + 1) * stride + s];   // next index in flight
-        const uint4 pj = sp32c[j];
+    // candidates in groups of four: four list words, then four positions,
+    // are in flight together (the loads, not the arithmetic, set the pace)
+    auto pair = [&](const uint4 &pj) {
         const float dx = offset_f(pi.x, pj.x, fsx), dy = offset_f(pi.y, pj.y, fsy), dz = offset_f(pi.z, pj.z, fsz);
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         if (r2 < rc2) {
@@ -273,7 +271,19 @@ __global__ void __launch_bounds__(kNearThreads) k_near_list(const BatchView bv,
             fy = fmaf(g, dy, fy);
             fz = fmaf(g, dz, fz);
         }
+    };
+    const int32_t *lp = nbr_list + s;
+    int k = 0;
+    for (; k + 4 <= cnt; k += 4) {
+        const int j0 = lp[(int64_t)k * stride], j1 = lp[(int64_t)(k + 1) * stride];
+        const int j2 = lp[(int64_t)(k + 2) * stride], j3 = lp[(int64_t)(k + 3) * stride];
+        const uint4 p0 = sp32c[j0], p1 = sp32c[j1], p2 = sp32c[j2], p3 = sp32c[j3];
+        pair(p0);
+        pair(p1);
+        pair(p2);
+        pair(p3);
     }
+    for (; k < cnt; ++k) pair(sp32c[lp[(int64_t)k * stride]]);
     // the two energies travel in the w slot as a pair of floats
     fnear[i] = make_double4_32a((double)fx, (double)fy, (double)fz,
                                 __hiloint2double(__float_as_int(un), __float_as_int(uw)));

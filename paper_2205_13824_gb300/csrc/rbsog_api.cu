@@ -461,6 +461,7 @@ BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
     v.force_mask = nullptr;
     v.remaining = c->use_budget ? c->d_remaining : nullptr;
     v.list_cap = c->use_list ? c->list_cap : 0;
+    v.precision = c->precision;
     return v;
 }
 

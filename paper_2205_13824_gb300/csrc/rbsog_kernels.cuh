@@ -148,6 +148,7 @@ struct BatchView {
     int32_t max_cap;           // largest near staging chunk of the batch
     int32_t max_tile_p;        // largest rho-sweep tile of the batch
     int32_t list_cap;          // neighbour-list slots per particle (0: no lists)
+    int32_t precision;         // 0 FP64, 1 FP32C
 };
 constexpr int kParticleBlock = 256;
 
@@ -155,9 +156,9 @@ constexpr int kParticleBlock = 256;
 // coordinate of the FP32C path (one FP64 multiply; the scale comes from the
 // host).
 __device__ __forceinline__ uint32_t fixed32(double x, double inv) {
-    const double t = x * inv;
-    const double c = t < 0.0 ? 0.0 : (t > 4294967295.0 ? 4294967295.0 : t);
-    return (uint32_t)__double2ull_rz(c);
+    // the round-toward-zero conversion to a 32-bit unsigned integer clamps
+    // to [0, 2^32 - 1] (PTX cvt semantics), which is the clamp above
+    return __double2uint_rz(x * inv);
 }
 
 // Caller-order fixed-point position (x, y, z, FP32 charge) of particle i for
