@@ -298,10 +298,16 @@ rbsog_status rbsog_server_submit(rbsog_server *s, int64_t n, const rbsog_params 
 rbsog_status rbsog_server_advance(rbsog_server *s, int32_t *n_active, int32_t *n_waiting,
                                   int32_t *n_retired);
 /* status: 0 waiting, 1 running, 2 done (then x, v, f [n][3], energies and the
- * steps done are copied out to host pointers, any of which may be NULL). */
+ * steps done are copied out to host pointers, any of which may be NULL),
+ * 3 cancelled. */
 rbsog_status rbsog_server_result(rbsog_server *s, int64_t job_id, int32_t *status, double *x, double *v,
                                  double *f, rbsog_energies *e, int64_t *steps_done);
-/* Free a finished job's host results. */
+/* Cancel a job: a waiting job leaves the queue; a running job is frozen at
+ * once (no further steps) and leaves the batch at the next rebuild.  Its
+ * status becomes 3; it frees its slot and memory budget.  RBSOG_EINVAL for
+ * an unknown, finished or already cancelled job. */
+rbsog_status rbsog_server_cancel(rbsog_server *s, int64_t job_id);
+/* Free a finished or cancelled job's host data. */
 rbsog_status rbsog_server_release(rbsog_server *s, int64_t job_id);
 const char *rbsog_server_last_error(const rbsog_server *s);
 rbsog_status rbsog_server_destroy(rbsog_server *s);

@@ -29,7 +29,7 @@ EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_stat
            "rbsog_batch_get_state", "rbsog_batch_get_energies", "rbsog_batch_get_kseq", "rbsog_batch_step",
            "rbsog_batch_autotune", "rbsog_batch_rdf", "rbsog_rdf",
            "rbsog_server_create", "rbsog_server_submit", "rbsog_server_advance", "rbsog_server_result",
-           "rbsog_server_release", "rbsog_server_last_error", "rbsog_server_destroy",
+           "rbsog_server_release", "rbsog_server_cancel", "rbsog_server_last_error", "rbsog_server_destroy",
            "rbsog_get_profile", "rbsog_last_error", "rbsog_destroy")
 
 
@@ -106,6 +106,7 @@ def _load():
         "rbsog_server_result": [P, C.c_int64, C.POINTER(C.c_int32), P, P, P, C.POINTER(rbsog_energies),
                                 C.POINTER(C.c_int64)],
         "rbsog_server_release": [P, C.c_int64],
+        "rbsog_server_cancel": [P, C.c_int64],
         "rbsog_server_destroy": [P],
     }
     for name, args in sig.items():
@@ -371,6 +372,10 @@ def rbsog_server_result(s, job_id: int, n: int):
     if st.value != 2:
         return st.value, None, None, None, None, 0
     return st.value, x, v, f, e.as_dict(), steps.value
+
+
+def rbsog_server_cancel(s, job_id: int):
+    _check_server(s, _lib.rbsog_server_cancel(s, int(job_id)))
 
 
 def rbsog_server_release(s, job_id: int):

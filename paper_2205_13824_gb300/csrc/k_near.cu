@@ -436,7 +436,10 @@ __global__ void __launch_bounds__(kThreads, PREC == 1 ? 6 : 4)
                                 const int m = (a + e) >> 1;
                                 if (st[m - c0].x <= xr) a = m + 1; else e = m;
                             }
-                            len = max(a - lo, 0);
+                            // a cell range that lies wholly after the staged
+                            // chunk leaves its bound at or past c1: the run is
+                            // clamped to the chunk (and is empty there)
+                            len = max(min(a, c1) - min(lo, c1), 0);
                         }
                     }
                     const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);

@@ -31,7 +31,6 @@
 //               the minimum image), r^2 < r_c^2, Gaussian sums from the FP32
 //               tables; force and the two energies per particle;
 //   list_clear  resets the rebuild flags after a build.
-#include <climits>
 #include <cmath>
 
 #include "rbsog_kernels.cuh"
@@ -182,13 +181,16 @@ __global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv
                     const int m = (a + e) >> 1;
                     if (st[m - c0].x < xl) a = m + 1; else e = m;
                 }
-                const int lo = a;
+                // a cell range that lies wholly after the staged chunk leaves
+                // its bound at or past c1: the run is clamped to the chunk
+                const int lo = min(a, c1);
                 a = max(s_off[k0 + ch], c0);
                 e = min(s_off[k0 + ch + 1], c1);
                 while (a < e) {
                     const int m = (a + e) >> 1;
                     if (st[m - c0].x <= xr) a = m + 1; else e = m;
                 }
+                a = min(a, c1);
                 for (int t = lo; t < a; ++t) {
                     const float4 pj = st[t - c0];
                     const float dx = ix - pj.x, dy = iy - pj.y, dz = iz - pj.z;
@@ -303,6 +305,7 @@ __global__ void __launch_bounds__(256) k_list_move(int64_t n, int64_t old_off, i
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int cnt = old_cnt[old_off + s];
+    const int64_t shift = new_off - old_off;
     new_xref[new_off + s] = old_xref[old_off + s];
     if (cnt > new_cap) {
         new_cnt[new_off + s] = 0;
@@ -310,7 +313,6 @@ __global__ void __launch_bounds__(256) k_list_move(int64_t n, int64_t old_off, i
         *new_flag = 1;
         return;
     }
-    const int64_t shift = new_off - old_off;
     new_cnt[new_off + s] = cnt;
     new_perm[new_off + s] = (int32_t)(old_perm[old_off + s] + shift);
     for (int k = 0; k < cnt; ++k)

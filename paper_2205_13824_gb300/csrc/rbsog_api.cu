@@ -1793,10 +1793,40 @@ rbsog_status rbsog_server_result(rbsog_server *s, int64_t job_id, int32_t *statu
     return RBSOG_OK;
 }
 
+rbsog_status rbsog_server_cancel(rbsog_server *s, int64_t job_id) {
+    if (!s) return RBSOG_EINVAL;
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return srv_fail(s, RBSOG_EINVAL, "unknown job");
+    Job &j = it->second;
+    if (j.status == 0) {
+        s->waiting.erase(std::find(s->waiting.begin(), s->waiting.end(), job_id));
+    } else if (j.status == 1) {
+        // freeze the running system at once (its kernels' blocks leave); it
+        // leaves the batch at the next rebuild like a finished job
+        rbsog_ctx *b = s->batch;
+        const auto pos = std::find(s->active.begin(), s->active.end(), job_id);
+        const int k = (int)(pos - s->active.begin());
+        CK_S(s, cudaSetDevice(b->device));
+        CK_S(s, cudaStreamSynchronize(b->st));
+        CK_S(s, cudaMemsetAsync(b->d_remaining + k, 0, sizeof(int64_t), b->st));
+        CK_S(s, cudaStreamSynchronize(b->st));
+        b->remaining_host[k] = 0;
+        s->used -= j.footprint;
+        s->frozen_n += j.n;
+    } else {
+        return srv_fail(s, RBSOG_EINVAL, "job already finished or cancelled");
+    }
+    j.status = 3;
+    std::vector<double>().swap(j.q);
+    std::vector<double>().swap(j.x);
+    std::vector<double>().swap(j.v);
+    return RBSOG_OK;
+}
+
 rbsog_status rbsog_server_release(rbsog_server *s, int64_t job_id) {
     if (!s) return RBSOG_EINVAL;
     auto it = s->jobs.find(job_id);
-    if (it == s->jobs.end() || it->second.status != 2) return srv_fail(s, RBSOG_EINVAL, "job not finished");
+    if (it == s->jobs.end() || it->second.status < 2) return srv_fail(s, RBSOG_EINVAL, "job not finished");
     s->jobs.erase(it);
     return RBSOG_OK;
 }

@@ -171,6 +171,9 @@ class Server:
     def result(self, jid):
         return B.rbsog_server_result(self.s, jid, self.n_of[jid])
 
+    def cancel(self, jid):
+        B.rbsog_server_cancel(self.s, jid)
+
     def release(self, jid):
         B.rbsog_server_release(self.s, jid)
         self.n_of.pop(jid, None)

@@ -278,6 +278,28 @@ def test_fp32c_neighbour_lists_over_rebuilds():
         g.close()
 
 
+def test_neighbour_list_overflow_is_reported():
+    """A cluster far denser than the box's mean density overflows the
+    neighbour-list capacity (sized from the mean): the force evaluation fails
+    with RBSOG_ENUMERIC instead of dropping pairs."""
+    _dev()
+    B = _lib().binding
+    L = 20.0
+    # 1000 particles on a lattice of spacing 0.8 in one corner (density ~2),
+    # 512 on a lattice of spacing 1.2 elsewhere: mean density 0.19
+    dense = np.stack(np.meshgrid(*[np.arange(10)] * 3, indexing="ij"), -1).reshape(-1, 3) * 0.8 + 1.0
+    sparse = np.stack(np.meshgrid(*[np.arange(8)] * 3, indexing="ij"), -1).reshape(-1, 3) * 1.2 + 10.3
+    x = np.concatenate([dense, sparse]).astype(np.float64)
+    N = x.shape[0]
+    q = np.where(np.arange(N) % 2 == 0, 1.0, -1.0)
+    g, _ = make(N, L, 32, prec="fp32c", n_ksets=2, seed=1)
+    g.set_state(*to_dev(q, x))
+    f = torch.zeros((N, 3), dtype=torch.float64, device=_dev())
+    with pytest.raises(B.RBSOGError, match="neighbour list"):
+        B.rbsog_compute_forces(g.ctx, None, f)
+    g.close()
+
+
 def test_berendsen_matches_oracle():
     _dev()
     N, L, P, steps = 1000, 12.6, 50, 6

@@ -117,3 +117,33 @@ def test_server_rejects_invalid_jobs():
     assert srv.result(jid)[0] == 2
     srv.release(jid)
     srv.close()
+
+
+def test_server_cancel_waiting_and_running():
+    """Cancelling a waiting job drops it from the queue; cancelling a running
+    job freezes it at once; the other jobs still finish with their alone
+    trajectories."""
+    Pk, dev = _setup()
+    B = Pk.binding
+    jobs = [JOBS[0], JOBS[2], JOBS[4]]
+    states = [I.electrolyte(j[0], j[1], seed=700 + i) for i, j in enumerate(jobs)]
+    params = [_params(Pk, j[1], j[2], j[3], "fp32c", j[4]) for j in jobs]
+    srv = Pk.Server(max_jobs=2, mem_budget_bytes=8 << 30, quantum=2, device=0)
+    ids = [srv.submit(params[i], *states[i], nsteps=jobs[i][4]) for i in range(3)]
+    act, wait, _ = srv.advance()             # jobs 0 and 1 run, job 2 waits
+    assert (act, wait) == (2, 1)
+    srv.cancel(ids[2])                        # waiting
+    srv.cancel(ids[1])                        # running
+    assert srv.result(ids[1])[0] == 3 and srv.result(ids[2])[0] == 3
+    with pytest.raises(B.RBSOGError):
+        srv.cancel(ids[1])
+    for _ in range(50):
+        act, wait, _ = srv.advance()
+        if act == 0 and wait == 0:
+            break
+    st, x, *_ = srv.result(ids[0])
+    assert st == 2
+    assert np.array_equal(x, _alone(Pk, dev, jobs[0], params[0], states[0])[0])
+    for jid in ids:
+        srv.release(jid)
+    srv.close()
