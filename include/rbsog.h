@@ -39,7 +39,8 @@ typedef enum {
     RBSOG_ENOMEM = 2,   /* device or host allocation failed                  */
     RBSOG_ECUDA = 3,    /* a CUDA runtime call failed                        */
     RBSOG_ESTATE = 4,   /* call out of order (e.g. step before set_state)    */
-    RBSOG_ENUMERIC = 5, /* non-finite force found on the device              */
+    RBSOG_ENUMERIC = 5, /* non-finite force found on the device, or a
+                           neighbour list exceeded its capacity              */
     RBSOG_ETIMEOUT = 6  /* a bounded device wait gave up                     */
 } rbsog_status;
 
@@ -48,7 +49,11 @@ typedef enum {
     RBSOG_FP32C = 1  /* 32-bit fixed-point positions, FP32 pair and sincos
                         arithmetic, compensated FP32 rho(k) partials; FP64
                         for the cross-block rho combine, energies and the
-                        integrator's state                                  */
+                        integrator's state.  Near field on neighbour lists
+                        with a skin of r_c / 10, rebuilt on the device when a
+                        particle has moved more than half the skin (boxes with
+                        fewer than 3 cells of side 1.1 r_c per side: the cell
+                        stencil every step)                                 */
 } rbsog_precision;
 
 /* Parameters of one system (Sec. 2 and 3; Algorithm 1). */
@@ -114,9 +119,12 @@ rbsog_status rbsog_set_params(rbsog_ctx *ctx, const rbsog_params *p);
 rbsog_status rbsog_get_info(const rbsog_ctx *ctx, rbsog_info *info, double *omega, double *s);
 
 /* Load charges q[n], positions x[n][3] (folded into the box) and
- * velocities v[n][3] (NULL: zero).  Rejects a non-neutral charge vector,
- * |sum q| > 1e-12 sum |q| (the method assumes neutrality, Sec. 2).
- * Invalidates the stored forces: the next step first evaluates them. */
+ * velocities v[n][3] (NULL: zero), host or device.  Rejects a non-neutral
+ * charge vector, |sum q| > 1e-12 sum |q| (the method assumes neutrality,
+ * Sec. 2).  Invalidates the stored forces: the next step first evaluates
+ * them.  FP32C neighbour lists are kept: the next force evaluation's
+ * displacement test rebuilds them if any particle moved more than half the
+ * skin since they were built.  Synchronises. */
 rbsog_status rbsog_set_state(rbsog_ctx *ctx, const double *q, const double *x, const double *v);
 
 /* One force evaluation F = F_N + F*_F (+ WCA) at the current positions
@@ -129,7 +137,9 @@ rbsog_status rbsog_compute_forces(rbsog_ctx *ctx, const int32_t *m_kset, double 
                                   rbsog_energies *e_out);
 
 /* Advance nsteps velocity-Verlet steps of Algorithm 1, each consuming the
- * next k-set; with tau_T > 0 velocities are rescaled by
+ * next k-set (RBSOG_ENUMERIC at the next synchronising call if a force was
+ * non-finite or a neighbour list overflowed); with tau_T > 0 velocities are
+ * rescaled by
  * sqrt(1 + dt/tau_T (T_target/T - 1)) after the second half kick.  Enqueued
  * asynchronously (replayed from a CUDA graph of one step when profiling is
  * off).  Returns RBSOG_EINVAL if the sequence would run out of k-sets. */
@@ -167,8 +177,10 @@ rbsog_status rbsog_rho(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *rho_
 
 /* Cell list of the current positions (the near-field traversal structure):
  * cell_start[ncell + 1] offsets, perm[n] particle index in cell order
- * (increasing index within a cell), nbr[n] number of partners within r_c
- * per particle (caller order).  Any pointer may be NULL. */
+ * (within a cell by increasing fixed-point x = trunc(x (2^32 / L_x)), then
+ * index), nbr[n] number of partners within r_c per particle (caller order).
+ * Cells have side >= r_c (FP64) or >= 1.1 r_c (FP32C with neighbour lists).
+ * Any pointer may be NULL. */
 rbsog_status rbsog_get_cells(rbsog_ctx *ctx, int32_t *cell_start, int32_t *perm, int32_t *nbr);
 
 /* Kernel-level timing: when on, launches run eagerly with a CUDA event pair

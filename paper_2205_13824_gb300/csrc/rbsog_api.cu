@@ -545,6 +545,21 @@ rbsog_status upload_desc(rbsog_ctx *ctx) {
     return RBSOG_OK;
 }
 
+// A caller buffer that kernels can read or write in place: device or
+// managed memory.  Host memory (pinned or not) goes through the staging
+// buffer with a bulk copy: measured faster than kernels reading pinned host
+// memory over the host link.
+template <class T>
+T *kernel_view(T *p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the error of an unknown pointer
+        return nullptr;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+    return nullptr;
+}
+
 double self_energy(const rbsog_ctx *c, int s) {
     double wsum = 0.0;
     for (size_t l = 0; l < c->omega.size(); ++l) wsum += c->omega[l];
@@ -1063,10 +1078,20 @@ rbsog_status rbsog_batch_set_state(rbsog_batch *ctx, int32_t sys, const double *
     // inputs (host or device) land in the staging regions; the charge sums
     // for the neutrality check and the self energy are block sums on the
     // device, added on the host in block order
-    double *sx = ctx->staging, *sv = ctx->staging + 3 * n, *sq = ctx->staging + 9 * n;
-    CK(cudaMemcpyAsync(sq, q, sizeof(double) * n, cudaMemcpyDefault, ctx->st));
-    CK(cudaMemcpyAsync(sx, x, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
-    if (v) CK(cudaMemcpyAsync(sv, v, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
+    // (read in place when the caller's memory is device-accessible)
+    const double *sx = kernel_view(x), *sv = v ? kernel_view(v) : nullptr, *sq = kernel_view(q);
+    if (!sq) {
+        CK(cudaMemcpyAsync(ctx->staging + 9 * n, q, sizeof(double) * n, cudaMemcpyDefault, ctx->st));
+        sq = ctx->staging + 9 * n;
+    }
+    if (!sx) {
+        CK(cudaMemcpyAsync(ctx->staging, x, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
+        sx = ctx->staging;
+    }
+    if (v && !sv) {
+        CK(cudaMemcpyAsync(ctx->staging + 3 * n, v, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
+        sv = ctx->staging + 3 * n;
+    }
     const int64_t nb = (n + 255) / 256;
     CK(launch_charge_sums(n, sq, ctx->qpart, ctx->st));
     CK(cudaMemcpyAsync(ctx->h_qpart, ctx->qpart, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, ctx->st));
@@ -1208,6 +1233,11 @@ rbsog_status rbsog_batch_get_state(rbsog_batch *ctx, int32_t sys, double *x, dou
     double *dst[3] = {x, v, f};
     for (int k = 0; k < 3; ++k) {
         if (!dst[k]) continue;
+        double *direct = kernel_view(dst[k]);
+        if (direct) {   // written in place (device or pinned host memory)
+            CK(launch_unpack(n, src[k], direct, ctx->st));
+            continue;
+        }
         double *reg = ctx->staging + 3 * n * k;
         CK(launch_unpack(n, src[k], reg, ctx->st));
         CK(cudaMemcpyAsync(dst[k], reg, bytes, cudaMemcpyDefault, ctx->st));
@@ -1243,13 +1273,16 @@ rbsog_status rbsog_batch_restore(rbsog_batch *ctx, int32_t sys, const double *f,
     es = enter(ctx);
     if (es != RBSOG_OK) return es;
     const int64_t n = ctx->n_per[sys], off = ctx->p_off[sys];
-    CK(cudaMemcpyAsync(ctx->staging, f, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
-    CK(launch_pack(n, ctx->staging, nullptr, ctx->force + off, 0, ctx->p[sys].L, ctx->st));
-    *ctx->h_i64 = kset_cursor;
+    const double *sf = kernel_view(f);
+    if (!sf) {
+        CK(cudaMemcpyAsync(ctx->staging, f, sizeof(double) * 3 * n, cudaMemcpyDefault, ctx->st));
+        sf = ctx->staging;
+    }
+    CK(launch_pack(n, sf, nullptr, ctx->force + off, 0, ctx->p[sys].L, ctx->st));
+    ctx->h_i64[0] = kset_cursor;
+    ctx->h_i64[1] = step;
     CK(cudaMemcpyAsync(ctx->cursor + sys, ctx->h_i64, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
-    *ctx->h_i64 = step;
-    CK(cudaMemcpyAsync(ctx->step_ctr + sys, ctx->h_i64, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->step_ctr + sys, ctx->h_i64 + 1, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     ctx->host_cursor[sys] = kset_cursor;
     ctx->force_valid[sys] = 1;
