@@ -319,11 +319,22 @@ __global__ void __launch_bounds__(256) k_list_move(int64_t n, int64_t old_off, i
         new_list[(int64_t)k * new_total + new_off + s] = (int32_t)(old_list[(int64_t)k * old_total + old_off + s] + shift);
 }
 
+// Inside a captured step: the rebuild branch becomes a conditional graph
+// node whose condition is the 'any system' flag of the displacement test.
+__global__ void k_rebuild_condition(cudaGraphConditionalHandle h, const int32_t *__restrict__ any) {
+    cudaGraphSetConditional(h, *any ? 1u : 0u);
+}
+
 __global__ void k_list_clear(int n_sys, int32_t *__restrict__ rebuild) {
     for (int s = threadIdx.x; s <= n_sys; s += blockDim.x) rebuild[s] = 0;
 }
 
 }  // namespace
+
+cudaError_t launch_rebuild_condition(cudaGraphConditionalHandle h, const int32_t *any, cudaStream_t st) {
+    k_rebuild_condition<<<1, 1, 0, st>>>(h, any);
+    return cudaGetLastError();
+}
 
 size_t list_build_smem(int cap, int list_cap) {
     (void)list_cap;

@@ -124,6 +124,8 @@ struct rbsog_ctx {
     int64_t *h_i64 = nullptr;
 
     cudaGraphExec_t graph = nullptr;
+    bool capturing = false;           // enqueue_step is being captured into the step graph
+    cudaStream_t side = nullptr;      // captures the bodies of conditional graph nodes
 
     bool profiling = false;
     std::vector<ProfRec> prof_open, prof_done;
@@ -477,10 +479,44 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
         // kick-drift in a step), cell list and lists of the flagged systems,
         // listed pairs, far field in caller order
         if (!packed) CK(launch_fix_pack(bv, ctx->posq, ctx->sp32c, ctx->xref, ctx->d_rebuild, ctx->st, pf));
-        CK(launch_build_cells(bv, ctx->posq, ctx->cb, prec, ctx->sp64, ctx->sp32, ctx->st, pf,
-                              ctx->d_rebuild + ctx->n_sys));
-        CK(launch_list_build(bv, ctx->cb.start, ctx->sp32, ctx->cb.perm, ctx->d_rebuild, ctx->nbr_list, ctx->nbr_cnt,
-                             ctx->list_perm, ctx->xref, ctx->err_flag, ctx->st, pf));
+        auto rebuild = [&](cudaStream_t s2) -> rbsog_status {
+            CK(launch_build_cells(bv, ctx->posq, ctx->cb, prec, ctx->sp64, ctx->sp32, s2, pf,
+                                  ctx->d_rebuild + ctx->n_sys));
+            CK(launch_list_build(bv, ctx->cb.start, ctx->sp32, ctx->cb.perm, ctx->d_rebuild, ctx->nbr_list,
+                                 ctx->nbr_cnt, ctx->list_perm, ctx->xref, ctx->err_flag, s2, pf));
+            return RBSOG_OK;
+        };
+        if (ctx->capturing) {
+            // captured step: the rebuild kernels form the body of a
+            // conditional node, so steps without a rebuild launch none of them
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t g = nullptr;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t nd = 0;
+            CK(cudaStreamGetCaptureInfo(ctx->st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+            cudaGraphConditionalHandle h;
+            CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+            CK(launch_rebuild_condition(h, ctx->d_rebuild + ctx->n_sys, ctx->st));
+            CK(cudaStreamGetCaptureInfo(ctx->st, &cs, nullptr, &g, &deps, nullptr, &nd));
+            cudaGraphNodeParams np{};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeIf;
+            np.conditional.size = 1;
+            cudaGraphNode_t cn;
+            CK(cudaGraphAddNode(&cn, g, deps, nullptr, nd, &np));
+            CK(cudaStreamBeginCaptureToGraph(ctx->side, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+            rbsog_status rs = rebuild(ctx->side);
+            cudaGraph_t body = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(ctx->side, &body);
+            if (rs != RBSOG_OK) return rs;
+            CK(ce);
+            CK(cudaStreamUpdateCaptureDependencies(ctx->st, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+        } else {
+            rbsog_status rs = rebuild(ctx->st);
+            if (rs != RBSOG_OK) return rs;
+        }
         CK(launch_near_list(bv, ctx->nsog, ctx->sp32c, ctx->nbr_list, ctx->nbr_cnt, ctx->list_perm, ctx->fnear,
                             nullptr, ctx->st, pf));
         CK(launch_rho_sweep(prec, bv, ctx->sp64, ctx->sp32c, ctx->rho_part, ctx->st, pf));
@@ -683,6 +719,7 @@ rbsog_status rbsog_batch_create(rbsog_batch **out, int32_t n_sys, const int64_t 
     };
     if (cudaSetDevice(device) != cudaSuccess) return bail(RBSOG_ECUDA);
     if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess) return bail(RBSOG_ECUDA);
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess) return bail(RBSOG_ECUDA);
     if (cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess)
         return bail(RBSOG_ECUDA);
@@ -1197,7 +1234,9 @@ rbsog_status rbsog_batch_step(rbsog_batch *ctx, int64_t nsteps) {
         if (!ctx->graph) {
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+            ctx->capturing = true;
             es = enqueue_step(ctx);
+            ctx->capturing = false;
             cudaError_t ce = cudaStreamEndCapture(ctx->st, &g);
             if (es != RBSOG_OK) {
                 if (g) cudaGraphDestroy(g);
@@ -1540,6 +1579,7 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     if (ctx->st) cudaStreamDestroy(ctx->st);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     delete ctx;
     return RBSOG_OK;
 }

@@ -228,6 +228,9 @@ cudaError_t launch_fix_pack(const BatchView &bv, const double4_32a *posq, uint4 
 cudaError_t launch_list_build(const BatchView &bv, const int32_t *start, const uint4 *sp32, const int32_t *perm,
                               const int32_t *rebuild, int32_t *nbr_list, int32_t *nbr_cnt, int32_t *list_perm,
                               uint4 *xref, int32_t *err_flag, cudaStream_t st, const Prof *prof);
+// Sets the condition of a conditional graph node to the 'any system needs a
+// rebuild' flag (captured steps).
+cudaError_t launch_rebuild_condition(cudaGraphConditionalHandle h, const int32_t *any, cudaStream_t st);
 // Moves one running system's lists between batch layouts (serving engine).
 cudaError_t launch_list_move(int64_t n, int64_t old_off, int64_t new_off, int64_t old_total, int64_t new_total,
                              int new_cap, const int32_t *old_list, const int32_t *old_cnt, const int32_t *old_perm,
