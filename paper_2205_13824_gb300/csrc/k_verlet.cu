@@ -25,7 +25,8 @@
 //   list_build  per near-field block (home x-row segment of cells, 9 staged
 //               row segments as in the cell-stencil kernel): binary-searched
 //               x-windows of r_l in the x-sorted rows, candidates appended
-//               to an ELL list (slot-major, particle-minor);
+//               to a sliced list (groups of 32 particles, slot-major inside a
+//               group);
 //   near_list   one thread per particle in the cell order of the last build:
 //               listed partners, fixed-point differences (the 32-bit wrap is
 //               the minimum image), r^2 < r_c^2, Gaussian sums from the FP32
@@ -45,6 +46,14 @@ constexpr int kNearThreads = kParticleBlock;
 
 __device__ __forceinline__ int wrap_cell_b(int c, int n) {
     return c < 0 ? c + n : (c >= n ? c - n : c);
+}
+
+// Sliced list layout: particles in groups of 32 (cell-order positions s),
+// each group's slots contiguous, slot k of the group's 32 particles in one
+// 128-byte run: a warp reads one run per slot, and a group's entries stay in
+// one compact region for the builder's scattered appends.
+__device__ __forceinline__ int64_t slot_index(int64_t s, int k, int cap) {
+    return ((s >> 5) * cap + k) * 32 + (s & 31);
 }
 
 __device__ __forceinline__ float offset_f(uint32_t a, uint32_t o, float scale) {
@@ -196,7 +205,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv
                     const float dx = ix - pj.x, dy = iy - pj.y, dz = iz - pj.z;
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     if (r2 < rl2 && r2 > 0.f) {
-                        if (cnt < lcap) nbr_list[(int64_t)cnt * bv.n_total + hi] = st_id[t - c0];
+                        if (cnt < lcap) nbr_list[slot_index(hi, cnt, lcap)] = st_id[t - c0];
                         else over = true;
                         ++cnt;
                     }
@@ -243,7 +252,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_list(const BatchView bv,
     const float rc2 = box.rc2_f, wrc2 = box.wca_rc2_f, ws2 = box.wca_s2_f, weps = box.wca_eps_f;
     const float tscale = sog.tab_scale;
     const int cnt = min(nbr_cnt[s], bv.list_cap);
-    const int64_t stride = bv.n_total;
+    constexpr int64_t stride = 32;
     float fx = 0.f, fy = 0.f, fz = 0.f, un = 0.f, uw = 0.f;
     int acc = 0;
     // candidates in groups of four: four list words, then four positions,
@@ -274,7 +283,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_list(const BatchView bv,
             fz = fmaf(g, dz, fz);
         }
     };
-    const int32_t *lp = nbr_list + s;
+    const int32_t *lp = nbr_list + slot_index(s, 0, bv.list_cap);
     int k = 0;
     for (; k + 4 <= cnt; k += 4) {
         const int j0 = lp[(int64_t)k * stride], j1 = lp[(int64_t)(k + 1) * stride];
@@ -293,10 +302,10 @@ __global__ void __launch_bounds__(kNearThreads) k_near_list(const BatchView bv,
 }
 
 // One running system's lists, reference positions and flag moved from one
-// batch layout (particles at old_off, ELL stride old_total) to another; a
+// batch layout (particles at old_off, lists of old_cap slots) to another; a
 // list longer than the new capacity flags the system for a rebuild instead.
-__global__ void __launch_bounds__(256) k_list_move(int64_t n, int64_t old_off, int64_t new_off, int64_t old_total,
-                                                   int64_t new_total, int new_cap, const int32_t *__restrict__ old_list,
+__global__ void __launch_bounds__(256) k_list_move(int64_t n, int64_t old_off, int64_t new_off, int old_cap,
+                                                   int new_cap, const int32_t *__restrict__ old_list,
                                                    const int32_t *__restrict__ old_cnt,
                                                    const int32_t *__restrict__ old_perm,
                                                    const uint4 *__restrict__ old_xref, int32_t *__restrict__ new_list,
@@ -316,7 +325,8 @@ __global__ void __launch_bounds__(256) k_list_move(int64_t n, int64_t old_off, i
     new_cnt[new_off + s] = cnt;
     new_perm[new_off + s] = (int32_t)(old_perm[old_off + s] + shift);
     for (int k = 0; k < cnt; ++k)
-        new_list[(int64_t)k * new_total + new_off + s] = (int32_t)(old_list[(int64_t)k * old_total + old_off + s] + shift);
+        new_list[slot_index(new_off + s, k, new_cap)] =
+            (int32_t)(old_list[slot_index(old_off + s, k, old_cap)] + shift);
 }
 
 // Inside a captured step: the rebuild branch becomes a conditional graph
@@ -363,11 +373,11 @@ cudaError_t launch_list_build(const BatchView &bv, const int32_t *start, const u
     return cudaGetLastError();
 }
 
-cudaError_t launch_list_move(int64_t n, int64_t old_off, int64_t new_off, int64_t old_total, int64_t new_total,
-                             int new_cap, const int32_t *old_list, const int32_t *old_cnt, const int32_t *old_perm,
+cudaError_t launch_list_move(int64_t n, int64_t old_off, int64_t new_off, int old_cap, int new_cap,
+                             const int32_t *old_list, const int32_t *old_cnt, const int32_t *old_perm,
                              const uint4 *old_xref, int32_t *new_list, int32_t *new_cnt, int32_t *new_perm,
                              uint4 *new_xref, int32_t *new_flag, cudaStream_t st) {
-    k_list_move<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, old_off, new_off, old_total, new_total, new_cap,
+    k_list_move<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, old_off, new_off, old_cap, new_cap,
                                                              old_list, old_cnt, old_perm, old_xref, new_list,
                                                              new_cnt, new_perm, new_xref, new_flag);
     return cudaGetLastError();

@@ -940,7 +940,7 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         CK(dalloc(&ctx->xref, n));
         CK(dalloc(&ctx->nbr_cnt, n));
         CK(dalloc(&ctx->list_perm, n));
-        CK(dalloc(&ctx->nbr_list, n * (size_t)ctx->list_cap));
+        CK(dalloc(&ctx->nbr_list, (n + 31) / 32 * 32 * (size_t)ctx->list_cap));
         CK(dalloc(&ctx->d_rebuild, (size_t)ns + 1));
         CK(cudaMemset(ctx->xref, 0, sizeof(uint4) * n));
         CK(cudaMemset(ctx->nbr_cnt, 0, sizeof(int32_t) * n));
@@ -1706,7 +1706,7 @@ rbsog_status rebuild(rbsog_server *sv, const std::vector<int64_t> &keep, const s
             // follows alone
             CK(cudaMemcpyAsync(nb->d_rebuild + k, old->d_rebuild + o, sizeof(int32_t), cudaMemcpyDeviceToDevice,
                                nb->st));
-            CK(launch_list_move(n, od.p_off, ndsc.p_off, old->n_total, nb->n_total, nb->list_cap, old->nbr_list,
+            CK(launch_list_move(n, od.p_off, ndsc.p_off, old->list_cap, nb->list_cap, old->nbr_list,
                                 old->nbr_cnt, old->list_perm, old->xref, nb->nbr_list, nb->nbr_cnt, nb->list_perm,
                                 nb->xref, nb->d_rebuild + k, nb->st));
         }

@@ -216,9 +216,9 @@ cudaError_t launch_near(int precision, const BatchView &bv, const NearSog &sog, 
                         int32_t *nbr, cudaStream_t st, const Prof *prof);
 
 // ---- neighbour lists (k_verlet.cu), FP32C ------------------------------------
-// Lists: ELL, nbr_list[slot * n_total + s] for the particle at cell-order
-// position s of the last build (list_perm[s] its caller index), nbr_cnt[s]
-// entries sorted by caller index; xref[i] the fixed-point position of caller
+// Lists: sliced by groups of 32 cell-order positions s of the last build
+// (list_perm[s] the caller index): slot k of s at ((s / 32) cap + k) 32 +
+// s % 32, nbr_cnt[s] entries; xref[i] the fixed-point position of caller
 // particle i at that build; rebuild[n_sys + 1] flags (per system, any).
 size_t list_build_smem(int cap, int list_cap);
 cudaError_t launch_fix_pack(const BatchView &bv, const double4_32a *posq, uint4 *sp32c, const uint4 *xref,
@@ -232,8 +232,8 @@ cudaError_t launch_list_build(const BatchView &bv, const int32_t *start, const u
 // rebuild' flag (captured steps).
 cudaError_t launch_rebuild_condition(cudaGraphConditionalHandle h, const int32_t *any, cudaStream_t st);
 // Moves one running system's lists between batch layouts (serving engine).
-cudaError_t launch_list_move(int64_t n, int64_t old_off, int64_t new_off, int64_t old_total, int64_t new_total,
-                             int new_cap, const int32_t *old_list, const int32_t *old_cnt, const int32_t *old_perm,
+cudaError_t launch_list_move(int64_t n, int64_t old_off, int64_t new_off, int old_cap, int new_cap,
+                             const int32_t *old_list, const int32_t *old_cnt, const int32_t *old_perm,
                              const uint4 *old_xref, int32_t *new_list, int32_t *new_cnt, int32_t *new_perm,
                              uint4 *new_xref, int32_t *new_flag, cudaStream_t st);
 // Near-field force (caller order) with both energies packed in fnear[i].w as
