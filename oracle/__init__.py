@@ -1,7 +1,7 @@
 """FP64 CPU oracle for the RBSOG force evaluation (arXiv:2205.13824).
 
-TEST INFRASTRUCTURE ONLY.  This package is the judge the CUDA path is
-compared with: only ``tests/``, ``__graft_entry__.smoke()`` and the
+TEST INFRASTRUCTURE ONLY.  This package is the reference the CUDA path is
+checked against: only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import it.  It shares no code with the
 product package ``paper_2205_13824_gb300`` and never imports it.
 

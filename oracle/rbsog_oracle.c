@@ -2,7 +2,7 @@
  * FP64 CPU oracle for the random batch sum-of-Gaussians (RBSOG) method of
  * Liang, Xu, Xu and Zhao (arXiv:2205.13824).
  *
- * TEST INFRASTRUCTURE ONLY: the judge that the CUDA path is compared with.
+ * TEST INFRASTRUCTURE ONLY: the reference that the CUDA path is checked against.
  * Only tests, the smoke check and the benchmark's CPU-baseline leg load this
  * library.  It shares no code with the product library (no headers, no
  * helpers, no generated tables).

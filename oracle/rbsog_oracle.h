@@ -2,8 +2,8 @@
  * FP64 CPU oracle for the random batch sum-of-Gaussians (RBSOG) force
  * evaluation and velocity-Verlet step.
  *
- * TEST INFRASTRUCTURE ONLY.  This library is the judge the CUDA path is
- * compared against.  Only the test suite, the smoke check and the CPU-baseline
+ * TEST INFRASTRUCTURE ONLY.  This library is the reference the CUDA path is
+ * checked against.  Only the test suite, the smoke check and the CPU-baseline
  * leg of the benchmark load it; the product library never links, calls or
  * includes anything here, and nothing here includes the product's headers.
  *
