@@ -3,9 +3,11 @@
 // sign of -grad U*_F:
 //   F*_i = -(lB pi^{3/2} S / (P V)) q_i sum_eta k_eta Im(e^{-i k_eta . r_i} rho(k_eta)).
 //
-// rho sweep  grid (particle tiles) x (k tiles of 32).  A block stages its
-//            particle tile in shared memory with coalesced 16/32-byte loads;
-//            lane l of every warp owns frequency k_l of the tile and each warp
+// rho sweep  grid (particle tiles) x (k tiles: 64 in FP32C, 32 in FP64).  A
+//            block stages its particle tile in shared memory with coalesced
+//            16/32-byte loads; lane l of every warp owns frequency k_l of the
+//            tile (FP32C: k_l and k_{l+32}, whose FP32 work runs as packed
+//            f32x2 operations on one broadcast particle load) and each warp
 //            sweeps a slice of the tile, reading the particle by a broadcast
 //            shared-memory load.  No atomics: each block writes one partial
 //            per frequency.
@@ -19,9 +21,13 @@
 // combine    one warp per frequency sums the block partials in FP64 in a
 //            fixed order and writes rho(k) plus the scatter table entry
 //            (k vector, coef Re rho, coef Im rho, m).
-// scatter    one thread per particle, frequencies staged through shared
-//            memory in chunks; adds the near-field force and writes the total
-//            to the particle's caller-order slot.
+// scatter    frequencies staged through shared memory in chunks; adds the
+//            near-field force and writes the total to the particle's
+//            caller-order slot.  FP64: one thread per particle.  FP32C: two
+//            particles per thread (l and l + 128 of a 256-particle block), so
+//            each staged frequency is read once for both and the FP32 work
+//            of the two runs as packed f32x2 operations, which keeps the
+//            instruction issue below the sin/cos unit's time per term.
 #include <algorithm>
 
 #include "rbsog_kernels.cuh"
@@ -31,16 +37,19 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kSweepThreads = 256;          // 8 warps
-constexpr int kKTile = 32;                  // frequencies per sweep block
+constexpr int kKTile = 32;                  // frequencies per sweep block (FP64)
+constexpr int kKTile32 = 64;                // frequencies per sweep block (FP32C), two per lane
 constexpr int kScatterThreads = kParticleBlock;
-constexpr int kKChunk32 = 1024;             // frequencies per staged chunk (FP32C, 32 KiB)
+constexpr int kScatter32Threads = kParticleBlock / 2;   // two particles per thread
+constexpr int kKChunk32 = 512;              // frequencies per staged chunk (FP32C, 16 KiB)
 constexpr int kKChunk64 = 512;              // frequencies per staged chunk (FP64, 32 KiB)
+constexpr float kTwoPiF = 6.28318530717958647f;
 
 struct KEntry32 {       // 32 bytes, two 16-byte broadcast loads
     int32_t mx, my, mz;
-    float cre;
+    float ncre;         // -coef Re rho
     float kx, ky, kz;
-    float cim;
+    float cim;          // coef Im rho
 };
 struct KEntry64 {       // 64 bytes
     double kx, ky, kz, cre;
@@ -53,13 +62,15 @@ __device__ __forceinline__ int4 load_m(const BatchView &bv, const SysDesc &d, in
     return bv.kseq[d.k_off + bv.cursor[s] * (int64_t)bv.P + k];
 }
 
-// angle in [0, 2 pi) of a phase given in units of 2^-32 turns, rounded to
-// 24 bits of turns without an int->float conversion instruction
-__device__ __forceinline__ float turns_to_rad(uint32_t ph) {
+// 1 + t in [1, 2) for a phase given as t = ph 2^-32 turns, t rounded to 23
+// bits, built without an int->float conversion instruction; the angle in
+// [0, 2 pi) is then (1 + t) 2 pi - 2 pi, one FMA
+__device__ __forceinline__ float one_plus_turns(uint32_t ph) {
     const uint32_t r = (ph + 256u) >> 9;                       // 23-bit turns, rounded
-    const float f = __uint_as_float(0x3F800000u | r);          // 1 + turns
-    return fmaf(f, 6.28318530717958647f, -6.28318530717958647f);
+    return __uint_as_float(0x3F800000u | r);                   // 1 + turns, exact
 }
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 __device__ __forceinline__ void two_sum(float &hi, float &lo, float x) {
     const float s = hi + x;
@@ -74,47 +85,57 @@ __global__ void __launch_bounds__(kSweepThreads)
     k_rho_sweep(BatchView bv, const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
                 double2 *__restrict__ rho_part) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    __shared__ double s_re[kSweepThreads / 32][kKTile];
-    __shared__ double s_im[kSweepThreads / 32][kKTile];
+    __shared__ double s_re[kSweepThreads / 32][kKTile32];
+    __shared__ double s_im[kSweepThreads / 32][kKTile32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int2 work = bv.sblk[blockIdx.x];
     if (bv.remaining && bv.remaining[work.x] == 0) return;   // frozen system: whole block leaves
     const SysDesc &d = bv.sys[work.x];
     const int ptile = work.y;
-    const int k = blockIdx.y * kKTile + lane;
+    const int ktile = PREC == 1 ? kKTile32 : kKTile;
+    const int k0 = blockIdx.y * ktile;
     const int64_t p0 = d.p_off + (int64_t)ptile * d.tile_p;
     const int np = (int)min((int64_t)d.tile_p, d.p_off + d.n - p0);
-
-    int4 m = make_int4(0, 0, 0, 0);
-    if (k < bv.P) m = load_m(bv, d, work.x, k);
 
     const int per_warp = (np + 7) / 8;
     const int jb = wid * per_warp, je = min(jb + per_warp, np);
     if (PREC == 1) {
+        int4 ma = make_int4(0, 0, 0, 0), mb = ma;
+        if (k0 + lane < bv.P) ma = load_m(bv, d, work.x, k0 + lane);
+        if (k0 + lane + 32 < bv.P) mb = load_m(bv, d, work.x, k0 + lane + 32);
         uint4 *sp = reinterpret_cast<uint4 *>(smem_raw);
         for (int j = tid; j < np; j += kSweepThreads) sp[j] = sp32[p0 + j];
         __syncthreads();
-        const uint32_t mx = (uint32_t)m.x, my = (uint32_t)m.y, mz = (uint32_t)m.z;
-        float re_hi = 0.f, re_lo = 0.f, im_hi = 0.f, im_lo = 0.f;
+        const float2 two_pi = f2(kTwoPiF, kTwoPiF), m_two_pi = f2(-kTwoPiF, -kTwoPiF);
+        float2 re_hi = f2(0.f, 0.f), re_lo = re_hi, im_hi = re_hi, im_lo = re_hi;
         for (int j0 = jb; j0 < je; j0 += 32) {
             const int j1 = min(j0 + 32, je);
-            float cr = 0.f, ci = 0.f;
+            float2 cr = f2(0.f, 0.f), ci = cr;
 #pragma unroll 4
             for (int j = j0; j < j1; ++j) {
                 const uint4 p = sp[j];
-                const uint32_t ph = mx * p.x + my * p.y + mz * p.z;
-                float s, c;
-                __sincosf(turns_to_rad(ph), &s, &c);
+                const uint32_t ph_a = (uint32_t)ma.x * p.x + (uint32_t)ma.y * p.y + (uint32_t)ma.z * p.z;
+                const uint32_t ph_b = (uint32_t)mb.x * p.x + (uint32_t)mb.y * p.y + (uint32_t)mb.z * p.z;
+                const float2 ang = __ffma2_rn(f2(one_plus_turns(ph_a), one_plus_turns(ph_b)), two_pi, m_two_pi);
+                float s_a, c_a, s_b, c_b;
+                __sincosf(ang.x, &s_a, &c_a);
+                __sincosf(ang.y, &s_b, &c_b);
                 const float q = __uint_as_float(p.w);
-                cr = fmaf(q, c, cr);
-                ci = fmaf(q, s, ci);
+                cr = __ffma2_rn(f2(q, q), f2(c_a, c_b), cr);
+                ci = __ffma2_rn(f2(q, q), f2(s_a, s_b), ci);
             }
-            two_sum(re_hi, re_lo, cr);
-            two_sum(im_hi, im_lo, ci);
+            two_sum(re_hi.x, re_lo.x, cr.x);
+            two_sum(re_hi.y, re_lo.y, cr.y);
+            two_sum(im_hi.x, im_lo.x, ci.x);
+            two_sum(im_hi.y, im_lo.y, ci.y);
         }
-        s_re[wid][lane] = (double)re_hi + (double)re_lo;
-        s_im[wid][lane] = (double)im_hi + (double)im_lo;
+        s_re[wid][lane] = (double)re_hi.x + (double)re_lo.x;
+        s_im[wid][lane] = (double)im_hi.x + (double)im_lo.x;
+        s_re[wid][lane + 32] = (double)re_hi.y + (double)re_lo.y;
+        s_im[wid][lane + 32] = (double)im_hi.y + (double)im_lo.y;
     } else {
+        int4 m = make_int4(0, 0, 0, 0);
+        if (k0 + lane < bv.P) m = load_m(bv, d, work.x, k0 + lane);
         double4_32a *sp = reinterpret_cast<double4_32a *>(smem_raw);
         const double ilx = 1.0 / d.box.L[0], ily = 1.0 / d.box.L[1], ilz = 1.0 / d.box.L[2];
         for (int j = tid; j < np; j += kSweepThreads) {
@@ -137,14 +158,18 @@ __global__ void __launch_bounds__(kSweepThreads)
         s_im[wid][lane] = im;
     }
     __syncthreads();
-    if (wid == 0 && k < bv.P) {
-        double re = 0.0, im = 0.0;
+    // warp c sums column c (frequency k0 + c) over the 8 warps, in order
+    if (tid < ktile) {
+        const int k = k0 + tid;
+        if (k < bv.P) {
+            double re = 0.0, im = 0.0;
 #pragma unroll
-        for (int w = 0; w < kSweepThreads / 32; ++w) {
-            re += s_re[w][lane];
-            im += s_im[w][lane];
+            for (int w = 0; w < kSweepThreads / 32; ++w) {
+                re += s_re[w][tid];
+                im += s_im[w][tid];
+            }
+            rho_part[d.rp_off + (int64_t)k * d.n_ptiles + ptile] = make_double2(re, im);
         }
-        rho_part[d.rp_off + (int64_t)k * d.n_ptiles + ptile] = make_double2(re, im);
     }
 }
 
@@ -180,7 +205,7 @@ __global__ void __launch_bounds__(256) k_rho_combine(BatchView bv, const double2
             e.mx = m.x;
             e.my = m.y;
             e.mz = m.z;
-            e.cre = (float)(coef * re);
+            e.ncre = -(float)(coef * re);
             e.kx = (float)kx;
             e.ky = (float)ky;
             e.kz = (float)kz;
@@ -201,13 +226,38 @@ __global__ void __launch_bounds__(256) k_rho_combine(BatchView bv, const double2
     }
 }
 
-template <int PREC>
+// Particle l of a scatter block: far force (already multiplied by q) plus the
+// near-field force, checked and stored in caller order.
+__device__ __forceinline__ void store_total(int64_t s, double fx, double fy, double fz, const double4_32a &fn,
+                                            const int32_t *__restrict__ perm, double4_32a *__restrict__ force,
+                                            int32_t *__restrict__ err_flag) {
+    const double tx = fx + fn.x, ty = fy + fn.y, tz = fz + fn.z;
+    if (!(isfinite(tx) && isfinite(ty) && isfinite(tz))) atomicOr(err_flag, 1);
+    force[perm ? perm[s] : s] = make_double4_32a(tx, ty, tz, 0.0);
+}
+
+// The two near energies of a particle packed in fn.w (neighbour-list path),
+// summed over a warp's 32 particles by an FP32 tree.
+__device__ __forceinline__ float2 warp_energy(bool active, const double4_32a &fn) {
+    float en = 0.f, ew = 0.f;
+    if (active) {
+        en = __int_as_float(__double2hiint(fn.w));
+        ew = __int_as_float(__double2loint(fn.w));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        en += __shfl_down_sync(0xffffffffu, en, o);
+        ew += __shfl_down_sync(0xffffffffu, ew, o);
+    }
+    return f2(en, ew);
+}
+
 __global__ void __launch_bounds__(kScatterThreads)
-    k_far_scatter(BatchView bv, const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
-                  const void *__restrict__ ktab_all, const double4_32a *__restrict__ fnear,
-                  const int32_t *__restrict__ perm, double4_32a *__restrict__ force,
-                  int32_t *__restrict__ err_flag, double2 *__restrict__ epart) {
+    k_far_scatter64(BatchView bv, const double4_32a *__restrict__ sp64, const void *__restrict__ ktab_all,
+                    const double4_32a *__restrict__ fnear, const int32_t *__restrict__ perm,
+                    double4_32a *__restrict__ force, int32_t *__restrict__ err_flag, double2 *__restrict__ epart) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
+    __shared__ double2 s_e[kScatterThreads / 32];
     const int tid = threadIdx.x;
     const int2 work = bv.pblk[blockIdx.x];
     if (bv.remaining && bv.remaining[work.x] == 0) return;   // frozen system: whole block leaves
@@ -216,84 +266,37 @@ __global__ void __launch_bounds__(kScatterThreads)
     const int64_t s = d.p_off + sl;
     const bool active = sl < d.n;
     const int P = bv.P;
-    double fx, fy, fz;
-    if (PREC == 1) {
-        float4 *sk = reinterpret_cast<float4 *>(smem_raw);
-        const float4 *kt = reinterpret_cast<const float4 *>(ktab_all) + 2 * (int64_t)work.x * P;
-        uint4 p = make_uint4(0, 0, 0, 0);
-        if (active) p = sp32[s];
-        float gx = 0.f, gy = 0.f, gz = 0.f;
-        for (int c0 = 0; c0 < P; c0 += kKChunk32) {
-            const int nk = min(kKChunk32, P - c0);
-            __syncthreads();
-            for (int t = tid; t < 2 * nk; t += kScatterThreads) sk[t] = kt[2 * c0 + t];
-            __syncthreads();
-#pragma unroll 4
-            for (int e = 0; e < nk; ++e) {
-                const float4 e0 = sk[2 * e], e1 = sk[2 * e + 1];
-                const uint32_t ph = (uint32_t)__float_as_int(e0.x) * p.x +
-                                    (uint32_t)__float_as_int(e0.y) * p.y +
-                                    (uint32_t)__float_as_int(e0.z) * p.z;
-                float sn, cs;
-                __sincosf(turns_to_rad(ph), &sn, &cs);
-                const float im = fmaf(cs, e1.w, -sn * e0.w);
-                gx = fmaf(e1.x, im, gx);
-                gy = fmaf(e1.y, im, gy);
-                gz = fmaf(e1.z, im, gz);
-            }
+    double4_32a *sk = reinterpret_cast<double4_32a *>(smem_raw);
+    const double4_32a *kt = reinterpret_cast<const double4_32a *>(ktab_all) + 2 * (int64_t)work.x * P;
+    double4_32a p = make_double4_32a(0, 0, 0, 0);
+    if (active) p = sp64[s];
+    const double ux = p.x / d.box.L[0], uy = p.y / d.box.L[1], uz = p.z / d.box.L[2];
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int c0 = 0; c0 < P; c0 += kKChunk64) {
+        const int nk = min(kKChunk64, P - c0);
+        __syncthreads();
+        for (int t = tid; t < 2 * nk; t += kScatterThreads) sk[t] = kt[2 * c0 + t];
+        __syncthreads();
+        for (int e = 0; e < nk; ++e) {
+            const double4_32a e0 = sk[2 * e], e1 = sk[2 * e + 1];
+            double t = fma(e1.y, ux, fma(e1.z, uy, e1.w * uz));
+            t -= rint(t);
+            double sn, cs;
+            sincospi(2.0 * t, &sn, &cs);
+            const double im = cs * e1.x - sn * e0.w;
+            gx = fma(e0.x, im, gx);
+            gy = fma(e0.y, im, gy);
+            gz = fma(e0.z, im, gz);
         }
-        const float q = __uint_as_float(p.w);
-        fx = (double)(q * gx);
-        fy = (double)(q * gy);
-        fz = (double)(q * gz);
-    } else {
-        double4_32a *sk = reinterpret_cast<double4_32a *>(smem_raw);
-        const double4_32a *kt = reinterpret_cast<const double4_32a *>(ktab_all) + 2 * (int64_t)work.x * P;
-        double4_32a p = make_double4_32a(0, 0, 0, 0);
-        if (active) p = sp64[s];
-        const double ux = p.x / d.box.L[0], uy = p.y / d.box.L[1], uz = p.z / d.box.L[2];
-        double gx = 0.0, gy = 0.0, gz = 0.0;
-        for (int c0 = 0; c0 < P; c0 += kKChunk64) {
-            const int nk = min(kKChunk64, P - c0);
-            __syncthreads();
-            for (int t = tid; t < 2 * nk; t += kScatterThreads) sk[t] = kt[2 * c0 + t];
-            __syncthreads();
-            for (int e = 0; e < nk; ++e) {
-                const double4_32a e0 = sk[2 * e], e1 = sk[2 * e + 1];
-                double t = fma(e1.y, ux, fma(e1.z, uy, e1.w * uz));
-                t -= rint(t);
-                double sn, cs;
-                sincospi(2.0 * t, &sn, &cs);
-                const double im = cs * e1.x - sn * e0.w;
-                gx = fma(e0.x, im, gx);
-                gy = fma(e0.y, im, gy);
-                gz = fma(e0.z, im, gz);
-            }
-        }
-        fx = p.w * gx;
-        fy = p.w * gy;
-        fz = p.w * gz;
     }
     if (bv.force_mask && !bv.force_mask[work.x]) return;   // whole block
     double4_32a fn = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     if (active) fn = fnear[s];
     if (!perm) {
-        // caller order (neighbour-list path): the block's near energies, two
-        // floats per particle in fn.w, summed in fixed order (an FP32 tree
-        // per warp -- FP64 adds are scarce on this GPU -- then the warps in
-        // FP64, in order) into one partial per particle block
-        float en = 0.f, ew = 0.f;
-        if (active) {
-            en = __int_as_float(__double2hiint(fn.w));
-            ew = __int_as_float(__double2loint(fn.w));
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            en += __shfl_down_sync(0xffffffffu, en, o);
-            ew += __shfl_down_sync(0xffffffffu, ew, o);
-        }
-        __shared__ double2 s_e[kScatterThreads / 32];
-        if ((tid & 31) == 0) s_e[tid >> 5] = make_double2((double)en, (double)ew);
+        // caller order: one energy partial per particle block (warp trees in
+        // FP32, then the warps in FP64, in order)
+        const float2 e = warp_energy(active, fn);
+        if ((tid & 31) == 0) s_e[tid >> 5] = make_double2((double)e.x, (double)e.y);
         __syncthreads();
         if (tid == 0) {
             double2 t = s_e[0];
@@ -304,17 +307,93 @@ __global__ void __launch_bounds__(kScatterThreads)
             epart[d.e_off + work.y] = t;
         }
     }
-    if (!active) return;
-    const double tx = fx + fn.x, ty = fy + fn.y, tz = fz + fn.z;
-    if (!(isfinite(tx) && isfinite(ty) && isfinite(tz))) atomicOr(err_flag, 1);
-    force[perm ? perm[s] : s] = make_double4_32a(tx, ty, tz, 0.0);
+    if (active) store_total(s, p.w * gx, p.w * gy, p.w * gz, fn, perm, force, err_flag);
+}
+
+// FP32C: thread t of a block owns particles l = t and l = t + 128 of the
+// block's 256.  Per frequency both phases are exact 32-bit fixed-point dot
+// products; angle, the imaginary part and the three accumulations of the two
+// particles run as f32x2 operations (each lane of such an operation rounds
+// like the scalar one, so a particle's force is the same as when one thread
+// handles it alone).
+__global__ void __launch_bounds__(kScatter32Threads, 9)
+    k_far_scatter32(BatchView bv, const uint4 *__restrict__ sp32, const float4 *__restrict__ ktab_all,
+                    const double4_32a *__restrict__ fnear, const int32_t *__restrict__ perm,
+                    double4_32a *__restrict__ force, int32_t *__restrict__ err_flag, double2 *__restrict__ epart) {
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    __shared__ double2 s_e[kParticleBlock / 32];
+    float4 *sk = reinterpret_cast<float4 *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int2 work = bv.pblk[blockIdx.x];
+    if (bv.remaining && bv.remaining[work.x] == 0) return;   // frozen system: whole block leaves
+    const SysDesc &d = bv.sys[work.x];
+    const int P = bv.P;
+    const int64_t la = (int64_t)work.y * kParticleBlock + tid, lb = la + kScatter32Threads;
+    const bool act_a = la < d.n, act_b = lb < d.n;
+    const int64_t sa = d.p_off + la, sb = d.p_off + lb;
+    uint4 pa = make_uint4(0, 0, 0, 0), pb = pa;
+    if (act_a) pa = sp32[sa];
+    if (act_b) pb = sp32[sb];
+    const float4 *kt = ktab_all + 2 * (int64_t)work.x * P;
+    const float2 two_pi = f2(kTwoPiF, kTwoPiF), m_two_pi = f2(-kTwoPiF, -kTwoPiF);
+    float2 gx = f2(0.f, 0.f), gy = gx, gz = gx;
+    for (int c0 = 0; c0 < P; c0 += kKChunk32) {
+        const int nk = min(kKChunk32, P - c0);
+        __syncthreads();
+        for (int t = tid; t < 2 * nk; t += kScatter32Threads) sk[t] = kt[2 * c0 + t];
+        __syncthreads();
+#pragma unroll 4
+        for (int e = 0; e < nk; ++e) {
+            const float4 e0 = sk[2 * e], e1 = sk[2 * e + 1];
+            const uint32_t mx = __float_as_uint(e0.x), my = __float_as_uint(e0.y), mz = __float_as_uint(e0.z);
+            const uint32_t ph_a = mx * pa.x + my * pa.y + mz * pa.z;
+            const uint32_t ph_b = mx * pb.x + my * pb.y + mz * pb.z;
+            const float2 ang = __ffma2_rn(f2(one_plus_turns(ph_a), one_plus_turns(ph_b)), two_pi, m_two_pi);
+            float sn_a, cs_a, sn_b, cs_b;
+            __sincosf(ang.x, &sn_a, &cs_a);
+            __sincosf(ang.y, &sn_b, &cs_b);
+            // Im(e^{-i k.r} rho) times coef: cos * coef Im - sin * coef Re
+            const float2 im = __ffma2_rn(f2(cs_a, cs_b), f2(e1.w, e1.w), __fmul2_rn(f2(sn_a, sn_b), f2(e0.w, e0.w)));
+            gx = __ffma2_rn(f2(e1.x, e1.x), im, gx);
+            gy = __ffma2_rn(f2(e1.y, e1.y), im, gy);
+            gz = __ffma2_rn(f2(e1.z, e1.z), im, gz);
+        }
+    }
+    if (bv.force_mask && !bv.force_mask[work.x]) return;   // whole block
+    double4_32a fa = make_double4_32a(0.0, 0.0, 0.0, 0.0), fb = fa;
+    if (act_a) fa = fnear[sa];
+    if (act_b) fb = fnear[sb];
+    if (!perm) {
+        // caller order: one energy partial per 256-particle block, an FP32
+        // tree per 32 particles, then the eight trees in FP64 in particle
+        // order (warp w holds particles 32w.. and 128 + 32w..)
+        const float2 e_a = warp_energy(act_a, fa), e_b = warp_energy(act_b, fb);
+        const int w = tid >> 5;
+        if ((tid & 31) == 0) {
+            s_e[w] = make_double2((double)e_a.x, (double)e_a.y);
+            s_e[w + kScatter32Threads / 32] = make_double2((double)e_b.x, (double)e_b.y);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double2 t = s_e[0];
+            for (int w2 = 1; w2 < kParticleBlock / 32; ++w2) {
+                t.x += s_e[w2].x;
+                t.y += s_e[w2].y;
+            }
+            epart[d.e_off + work.y] = t;
+        }
+    }
+    const float qa = __uint_as_float(pa.w), qb = __uint_as_float(pb.w);
+    if (act_a) store_total(sa, (double)(qa * gx.x), (double)(qa * gy.x), (double)(qa * gz.x), fa, perm, force, err_flag);
+    if (act_b) store_total(sb, (double)(qb * gx.y), (double)(qb * gy.y), (double)(qb * gz.y), fb, perm, force, err_flag);
 }
 
 }  // namespace
 
-void far_layout(int64_t n, int32_t P, int tile_override, int &tile_p, int &n_ptiles) {
+void far_layout(int64_t n, int32_t P, int precision, int tile_override, int &tile_p, int &n_ptiles) {
     // default: at least ~3 waves of sweep blocks (152 SMs x 8 resident blocks)
-    const int nkt = (P + kKTile - 1) / kKTile;
+    const int kt = precision == 1 ? kKTile32 : kKTile;
+    const int nkt = (P + kt - 1) / kt;
     int tp = 2048;
     while (tp > 128 && (double)((n + tp - 1) / tp) * nkt < 152.0 * 8 * 3) tp /= 2;
     if (tile_override > 0) tp = std::min(4096, std::max(64, tile_override));
@@ -328,7 +407,8 @@ size_t ktab_bytes(int precision, int64_t nk) {
 
 cudaError_t launch_rho_sweep(int precision, const BatchView &bv, const double4_32a *sp64, const uint4 *sp32,
                              double2 *rho_part, cudaStream_t st, const Prof *prof) {
-    dim3 grid((unsigned)bv.n_sblk, (unsigned)((bv.P + kKTile - 1) / kKTile));
+    const int kt = precision == 1 ? kKTile32 : kKTile;
+    dim3 grid((unsigned)bv.n_sblk, (unsigned)((bv.P + kt - 1) / kt));
     ProfScope ps(prof, precision == 1 ? "rho_sweep_fp32c" : "rho_sweep_fp64");
     if (precision == 1) {
         const size_t sm = sizeof(uint4) * (size_t)bv.max_tile_p;
@@ -360,12 +440,12 @@ cudaError_t launch_far_scatter(int precision, const BatchView &bv, const double4
     ProfScope ps(prof, precision == 1 ? "far_scatter_fp32c" : "far_scatter_fp64");
     if (precision == 1) {
         const size_t sm = sizeof(KEntry32) * kKChunk32;
-        k_far_scatter<1><<<bv.n_pblk, kScatterThreads, sm, st>>>(bv, sp64, sp32, ktab, fnear, perm, force,
-                                                                  err_flag, epart);
+        k_far_scatter32<<<bv.n_pblk, kScatter32Threads, sm, st>>>(bv, sp32, static_cast<const float4 *>(ktab),
+                                                                   fnear, perm, force, err_flag, epart);
     } else {
         const size_t sm = sizeof(KEntry64) * kKChunk64;
-        k_far_scatter<0><<<bv.n_pblk, kScatterThreads, sm, st>>>(bv, sp64, sp32, ktab, fnear, perm, force,
-                                                                  err_flag, epart);
+        k_far_scatter64<<<bv.n_pblk, kScatterThreads, sm, st>>>(bv, sp64, ktab, fnear, perm, force, err_flag,
+                                                                 epart);
     }
     return cudaGetLastError();
 }

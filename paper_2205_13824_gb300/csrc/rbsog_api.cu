@@ -653,7 +653,7 @@ rbsog_status apply_layout(rbsog_ctx *ctx) {
             d.n_epart = d.n_kpart;
             npart = std::max(npart, d.n_kpart);
         }
-        far_layout(d.n, ctx->P, ctx->tune[s].tile, d.tile_p, d.n_ptiles);
+        far_layout(d.n, ctx->P, ctx->precision, ctx->tune[s].tile, d.tile_p, d.n_ptiles);
         d.rp_off = rp_off;
         for (int b = 0; b < nblocks; ++b) ctx->nblk.push_back(make_int2(s, b));
         for (int b = 0; b < d.n_ptiles; ++b) ctx->sblk.push_back(make_int2(s, b));

@@ -245,7 +245,7 @@ cudaError_t launch_near_list(const BatchView &bv, const NearSog &sog, const uint
 
 // ---- far field (k_far.cu) -----------------------------------------------------
 // tile_override > 0 replaces the default particles-per-tile rule (tunable)
-void far_layout(int64_t n, int32_t P, int tile_override, int &tile_p, int &n_ptiles);
+void far_layout(int64_t n, int32_t P, int precision, int tile_override, int &tile_p, int &n_ptiles);
 cudaError_t launch_rho_sweep(int precision, const BatchView &bv, const double4_32a *sp64,
                              const uint4 *sp32, double2 *rho_part, cudaStream_t st, const Prof *prof);
 // Combines partials in FP64 (fixed order) into rho[n_sys * P] and the per-k

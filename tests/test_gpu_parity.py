@@ -317,11 +317,14 @@ def test_berendsen_matches_oracle():
     g.close()
 
 
-def test_graph_replay_equals_eager_launches():
-    """The CUDA-graph step and the eager (profiled) step give identical bits."""
+@pytest.mark.parametrize("steps,T", [(5, 1.0), (60, 4.0)])
+def test_graph_replay_equals_eager_launches(steps, T):
+    """The CUDA-graph step and the eager (profiled) step give identical bits;
+    the longer, hotter run moves particles past half the skin, so the
+    captured step's conditional rebuild node fires inside the graph."""
     _dev()
-    N, L, P, steps = 4998, 21.5, 64, 5
-    q, x, v = I.electrolyte(N, L, seed=8)
+    N, L, P = 4998, 21.5, 64
+    q, x, v = I.electrolyte(N, L, seed=8, T=T)
     out = []
     for prof in (False, True):
         g, _ = make(N, L, P, prec="fp32c", n_ksets=steps + 1, seed=3)
@@ -333,10 +336,14 @@ def test_graph_replay_equals_eager_launches():
         if prof:
             rep = _lib().binding.rbsog_get_profile(g.ctx)
             assert rep["far_scatter_fp32c"][0] == steps + 1
-            assert "near_fp32c" in rep       # the production SOG set runs the unrolled variant
+            assert "near_fp32c" in rep and "list_build" in rep
         g.close()
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+    if steps == 60:                # a particle moved past skin/2 = r_c/20: lists were rebuilt in the graph
+        d = out[0][0] - x
+        d -= L * np.round(d / L)
+        assert np.sqrt((d ** 2).sum(1)).max() > 3.0 / 20
 
 
 def test_checkpoint_resume_is_bit_exact():
