@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift(BatchView bv, double4_3
     if (p.z < 0.0 || p.z >= a.box.L[2]) p.z = fold(p.z, a.box.L[2]);
     vel[i] = v;
     posq[i] = p;
-    if (sp32c) fixed_pack_check(a, w.x, bv.n_sys, p, i, sp32c, xref, rebuild);
+    if (sp32c) fixed_pack_check(a, w.x, bv.n_sys, p, i, sp32c, xref, rebuild, bv.lpos, bv.linv);
 }
 
 // v += dt/2 F/m and the block's kinetic energy sum (fixed order).

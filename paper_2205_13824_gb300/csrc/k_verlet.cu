@@ -29,8 +29,8 @@
 //               group);
 //   near_list   one thread per particle in the cell order of the last build:
 //               listed partners, fixed-point differences (the 32-bit wrap is
-//               the minimum image), r^2 < r_c^2, Gaussian sums from the FP32
-//               tables; force and the two energies per particle;
+//               the minimum image), r^2 < r_c^2, Gaussian sums from one
+//               combined FP32 table; force and the two energies per particle;
 //   list_clear  resets the rebuild flags after a build.
 #include <cmath>
 
@@ -43,6 +43,7 @@ constexpr int kBuildThreads = 128;
 constexpr int kMaxGroupB = 16;
 constexpr int kMaxStagedB = 9 * (kMaxGroupB + 2);
 constexpr int kNearThreads = kParticleBlock;
+constexpr int kTabCopies = 8;                  // shared-memory copies of the tables (bank groups)
 
 __device__ __forceinline__ int wrap_cell_b(int c, int n) {
     return c < 0 ? c + n : (c >= n ? c - n : c);
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(kParticleBlock) k_fix_pack(BatchView bv, const
     const int64_t il = (int64_t)w.y * kParticleBlock + threadIdx.x;
     if (il >= d.n) return;
     const int64_t i = d.p_off + il;
-    fixed_pack_check(d, w.x, bv.n_sys, posq[i], i, sp32c, xref, rebuild);
+    fixed_pack_check(d, w.x, bv.n_sys, posq[i], i, sp32c, xref, rebuild, bv.lpos, bv.linv);
 }
 
 // Neighbour lists of the home particles of one near-field block.
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv
                         const uint4 u = sp32[src];
                         st[t - c0] = make_float4(offset_f(u.x, ox, fsx), offset_f(u.y, oy, fsy),
                                                  offset_f(u.z, oz, fsz), 0.f);
-                        st_id[t - c0] = perm[src];
+                        st_id[t - c0] = src;
                     }
                 }
             }
@@ -219,63 +220,75 @@ __global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv
             }
             nbr_cnt[hi] = cnt;
             const int ci = perm[hi];
+            const uint4 u = sp32[hi];
             list_perm[hi] = ci;
-            xref[ci] = sp32[hi];
+            bv.linv[ci] = hi;
+            bv.lpos[hi] = u;
+            xref[ci] = u;
         }
     }
 }
 
 // Pair force and energies from the neighbour lists, one thread per particle
-// (cell order of the last build); results in caller order.
-__global__ void __launch_bounds__(kNearThreads) k_near_list(const BatchView bv,
-                                                            const __grid_constant__ NearSog sog,
-                                                            const uint4 *__restrict__ sp32c,
+// (cell order of the last build); results in caller order.  Positions are
+// read in that cell order (lpos): the thread's own position is a coalesced
+// load and its partners' lie in the few cell rows around it.
+// G and F come from one combined table (one 16-byte entry per pair, see
+// NearSog), held in shared memory in 8 copies, copy c of entry k at 8 k + c:
+// lane l reads copy l % 8, so the 8 lanes of each quarter warp fetch their
+// entries from 8 different bank groups whatever the entries are (one
+// shared-memory wavefront per quarter warp).
+__global__ void __launch_bounds__(kNearThreads, 5) k_near_list(const BatchView bv, const float ltab_scale,
+                                                            const float ltab_h, const float4 *__restrict__ ltab,
                                                             const int32_t *__restrict__ nbr_list,
                                                             const int32_t *__restrict__ nbr_cnt,
                                                             const int32_t *__restrict__ list_perm,
-                                                            double4_32a *__restrict__ fnear,
-                                                            int32_t *__restrict__ nbr) {
-    __shared__ float4 s_tab[2 * kTabN];
+                                                            double4_32a *__restrict__ fnear) {
+    __shared__ float4 s_tab[kLTabN * kTabCopies];
     const int2 w = bv.pblk[blockIdx.x];
     if (bv.remaining && bv.remaining[w.x] == 0) return;
-    for (int k = threadIdx.x; k < 2 * kTabN; k += kNearThreads) s_tab[k] = k < kTabN ? sog.tab_g[k] : sog.tab_f[k - kTabN];
+    // consecutive threads fill consecutive 16-byte slots (no bank conflicts)
+    for (int t = threadIdx.x; t < kLTabN * kTabCopies; t += kNearThreads) s_tab[t] = ltab[t / kTabCopies];
     __syncthreads();
+    const float4 *__restrict__ tab = s_tab + (threadIdx.x & (kTabCopies - 1));
     const SysDesc &d = bv.sys[w.x];
     const int64_t sl = (int64_t)w.y * kParticleBlock + threadIdx.x;
     if (sl >= d.n) return;
     const BoxDev &box = d.box;
     const int64_t s = d.p_off + sl;
-    const int i = list_perm[s];
-    const uint4 pi = sp32c[i];
+    const uint4 *__restrict__ lpos = bv.lpos;
+    const uint4 pi = lpos[s];
     const float qi = box.lB_f * __uint_as_float(pi.w);
     const float fsx = box.fix_scale[0], fsy = box.fix_scale[1], fsz = box.fix_scale[2];
     const float rc2 = box.rc2_f, wrc2 = box.wca_rc2_f, ws2 = box.wca_s2_f, weps = box.wca_eps_f;
-    const float tscale = sog.tab_scale;
+    const float tscale = ltab_scale, mh = -ltab_h;
     const int cnt = min(nbr_cnt[s], bv.list_cap);
     constexpr int64_t stride = 32;
     float fx = 0.f, fy = 0.f, fz = 0.f, un = 0.f, uw = 0.f;
-    int acc = 0;
     // candidates in groups of four: four list words, then four positions,
     // are in flight together (the loads, not the arithmetic, set the pace)
     auto pair = [&](const uint4 &pj) {
         const float dx = offset_f(pi.x, pj.x, fsx), dy = offset_f(pi.y, pj.y, fsy), dz = offset_f(pi.z, pj.z, fsz);
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         if (r2 < rc2) {
-            ++acc;
             const float qq = qi * __uint_as_float(pj.w);
             const float x = r2 * tscale;
-            const int kt = min((int)x, kTabN - 1);
+            const int kt = min((int)x, kLTabN - 1);
             const float sx = x - (float)kt;
-            const float4 cg = s_tab[kt], cf = s_tab[kTabN + kt];
-            const float gs = fmaf(fmaf(fmaf(cg.w, sx, cg.z), sx, cg.y), sx, cg.x);
-            const float fs = fmaf(fmaf(fmaf(cf.w, sx, cf.z), sx, cf.y), sx, cf.x);
+            const float4 e = tab[kt * kTabCopies];      // (g0, g1, g2, F at the interval start)
+            const float gs = fmaf(fmaf(e.z, sx, e.y), sx, e.x);
+            const float gi = fmaf(fmaf(e.z * (1.0f / 3.0f), sx, 0.5f * e.y), sx, e.x);   // (1/s) int_0^s G
+            const float fs = fmaf(mh * sx, gi, e.w);
             const float inv_r = rsqrtf(r2);
-            float g = qq * (inv_r * inv_r * inv_r - 2.0f * gs);
+            const float inv_r2 = inv_r * inv_r;
+            float g = qq * (inv_r2 * inv_r - 2.0f * gs);
             un += 0.5f * qq * (inv_r - fs);
             if (r2 < wrc2) {
-                const float sr2 = ws2 / r2;
+                // WCA from 1/r^2 (no divisions: this branch runs for some
+                // lane of most warps, so its length is paid by all lanes)
+                const float sr2 = ws2 * inv_r2;
                 const float sr6 = sr2 * sr2 * sr2;
-                g += 24.0f * weps * (2.0f * sr6 * sr6 - sr6) / r2;
+                g += 24.0f * weps * (2.0f * sr6 * sr6 - sr6) * inv_r2;
                 uw += 0.5f * (4.0f * weps * (sr6 * sr6 - sr6) + weps);
             }
             fx = fmaf(g, dx, fx);
@@ -285,20 +298,29 @@ __global__ void __launch_bounds__(kNearThreads) k_near_list(const BatchView bv,
     };
     const int32_t *lp = nbr_list + slot_index(s, 0, bv.list_cap);
     int k = 0;
-    for (; k + 4 <= cnt; k += 4) {
-        const int j0 = lp[(int64_t)k * stride], j1 = lp[(int64_t)(k + 1) * stride];
-        const int j2 = lp[(int64_t)(k + 2) * stride], j3 = lp[(int64_t)(k + 3) * stride];
-        const uint4 p0 = sp32c[j0], p1 = sp32c[j1], p2 = sp32c[j2], p3 = sp32c[j3];
-        pair(p0);
-        pair(p1);
-        pair(p2);
-        pair(p3);
+    if (cnt >= 4) {
+        // the next group's four list words (streamed from DRAM) are loaded
+        // before this group's pairs are evaluated, so their latency overlaps
+        // the arithmetic; only the position gathers (L1/L2) stay exposed
+        int j0 = lp[0], j1 = lp[stride], j2 = lp[2 * stride], j3 = lp[3 * stride];
+        for (; k + 4 <= cnt; k += 4) {
+            const uint4 p0 = lpos[j0], p1 = lpos[j1], p2 = lpos[j2], p3 = lpos[j3];
+            if (k + 8 <= cnt) {
+                j0 = lp[(int64_t)(k + 4) * stride];
+                j1 = lp[(int64_t)(k + 5) * stride];
+                j2 = lp[(int64_t)(k + 6) * stride];
+                j3 = lp[(int64_t)(k + 7) * stride];
+            }
+            pair(p0);
+            pair(p1);
+            pair(p2);
+            pair(p3);
+        }
     }
-    for (; k < cnt; ++k) pair(sp32c[lp[(int64_t)k * stride]]);
+    for (; k < cnt; ++k) pair(lpos[lp[(int64_t)k * stride]]);
     // the two energies travel in the w slot as a pair of floats
-    fnear[i] = make_double4_32a((double)fx, (double)fy, (double)fz,
-                                __hiloint2double(__float_as_int(un), __float_as_int(uw)));
-    if (nbr) nbr[i] = acc;
+    fnear[list_perm[s]] = make_double4_32a((double)fx, (double)fy, (double)fz,
+                                           __hiloint2double(__float_as_int(un), __float_as_int(uw)));
 }
 
 // One running system's lists, reference positions and flag moved from one
@@ -308,14 +330,17 @@ __global__ void __launch_bounds__(256) k_list_move(int64_t n, int64_t old_off, i
                                                    int new_cap, const int32_t *__restrict__ old_list,
                                                    const int32_t *__restrict__ old_cnt,
                                                    const int32_t *__restrict__ old_perm,
-                                                   const uint4 *__restrict__ old_xref, int32_t *__restrict__ new_list,
+                                                   const uint4 *__restrict__ old_xref,
+                                                   const int32_t *__restrict__ old_linv, int32_t *__restrict__ new_list,
                                                    int32_t *__restrict__ new_cnt, int32_t *__restrict__ new_perm,
-                                                   uint4 *__restrict__ new_xref, int32_t *__restrict__ new_flag) {
+                                                   uint4 *__restrict__ new_xref, int32_t *__restrict__ new_linv,
+                                                   int32_t *__restrict__ new_flag) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int cnt = old_cnt[old_off + s];
     const int64_t shift = new_off - old_off;
     new_xref[new_off + s] = old_xref[old_off + s];
+    new_linv[new_off + s] = (int32_t)(old_linv[old_off + s] + shift);
     if (cnt > new_cap) {
         new_cnt[new_off + s] = 0;
         new_perm[new_off + s] = (int32_t)(new_off + s);
@@ -375,19 +400,22 @@ cudaError_t launch_list_build(const BatchView &bv, const int32_t *start, const u
 
 cudaError_t launch_list_move(int64_t n, int64_t old_off, int64_t new_off, int old_cap, int new_cap,
                              const int32_t *old_list, const int32_t *old_cnt, const int32_t *old_perm,
-                             const uint4 *old_xref, int32_t *new_list, int32_t *new_cnt, int32_t *new_perm,
-                             uint4 *new_xref, int32_t *new_flag, cudaStream_t st) {
+                             const uint4 *old_xref, const int32_t *old_linv, int32_t *new_list,
+                             int32_t *new_cnt, int32_t *new_perm, uint4 *new_xref, int32_t *new_linv,
+                             int32_t *new_flag, cudaStream_t st) {
     k_list_move<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, old_off, new_off, old_cap, new_cap,
-                                                             old_list, old_cnt, old_perm, old_xref, new_list,
-                                                             new_cnt, new_perm, new_xref, new_flag);
+                                                             old_list, old_cnt, old_perm, old_xref, old_linv,
+                                                             new_list, new_cnt, new_perm, new_xref, new_linv,
+                                                             new_flag);
     return cudaGetLastError();
 }
 
-cudaError_t launch_near_list(const BatchView &bv, const NearSog &sog, const uint4 *sp32c, const int32_t *nbr_list,
-                             const int32_t *nbr_cnt, const int32_t *list_perm, double4_32a *fnear, int32_t *nbr,
-                             cudaStream_t st, const Prof *prof) {
+cudaError_t launch_near_list(const BatchView &bv, const NearSog &sog, const float4 *ltab, const int32_t *nbr_list,
+                             const int32_t *nbr_cnt, const int32_t *list_perm, double4_32a *fnear, cudaStream_t st,
+                             const Prof *prof) {
     ProfScope ps(prof, "near_fp32c");
-    k_near_list<<<bv.n_pblk, kNearThreads, 0, st>>>(bv, sog, sp32c, nbr_list, nbr_cnt, list_perm, fnear, nbr);
+    k_near_list<<<bv.n_pblk, kNearThreads, 0, st>>>(bv, sog.ltab_scale, sog.ltab_h, ltab, nbr_list, nbr_cnt,
+                                                    list_perm, fnear);
     return cudaGetLastError();
 }
 

@@ -116,7 +116,10 @@ struct rbsog_ctx {
     bool use_list = false;
     double skin = 0.0;
     int32_t list_cap = 0;
-    uint4 *sp32c = nullptr, *xref = nullptr;
+    uint4 *sp32c = nullptr, *xref = nullptr, *lpos = nullptr;
+    int32_t *linv = nullptr;
+    float4 *d_ltab = nullptr;            // combined G/F table of the list path [kLTabN]
+    std::vector<float4> h_ltab;
     int32_t *nbr_list = nullptr, *nbr_cnt = nullptr, *list_perm = nullptr, *d_rebuild = nullptr;
     // pinned host mirrors
     double *h_energy = nullptr;
@@ -427,6 +430,57 @@ void build_sog_tables(NearSog &ns, const std::vector<double> &omega, const std::
     ns.tab_err = (float)err;
 }
 
+constexpr double kListTabTol = 2e-6;   // largest accepted error of the list path's table
+
+// Combined table of the neighbour-list path: G interpolated by a quadratic
+// through the 3 Chebyshev nodes of each interval, F at each interval start
+// (F between starts follows from dF/du = -G).  Returns the largest error of
+// the FP32 entries for G and F over 33 points per interval, relative to
+// G(0) and F(0).
+double build_list_table(NearSog &ns, std::vector<float4> &tab, const std::vector<double> &omega,
+                        const std::vector<double> &s, int M, double rc) {
+    const double h = rc * rc / kLTabN;
+    auto G = [&](double uu) {
+        double v = 0.0;
+        for (int l = M; l >= 0; --l) v += omega[l] / (s[l] * s[l]) * std::exp(-uu / (s[l] * s[l]));
+        return v;
+    };
+    auto F = [&](double uu) {
+        double v = 0.0;
+        for (int l = M; l >= 0; --l) v += omega[l] * std::exp(-uu / (s[l] * s[l]));
+        return v;
+    };
+    double sn[3];
+    for (int j = 0; j < 3; ++j) sn[j] = 0.5 - 0.5 * std::cos((2 * j + 1) * kPi / 6.0);
+    const double g0 = G(0.0), f0 = F(0.0);
+    double err = 0.0;
+    tab.assign(kLTabN, float4{});
+    for (int k = 0; k < kLTabN; ++k) {
+        // Lagrange form through the nodes, expanded to monomials in s
+        double c[3] = {0.0, 0.0, 0.0};
+        for (int j = 0; j < 3; ++j) {
+            const double a = sn[(j + 1) % 3], b = sn[(j + 2) % 3];
+            const double wgt = G((k + sn[j]) * h) / ((sn[j] - a) * (sn[j] - b));
+            c[0] += wgt * a * b;
+            c[1] -= wgt * (a + b);
+            c[2] += wgt;
+        }
+        const float4 e = make_float4((float)c[0], (float)c[1], (float)c[2], (float)F(k * h));
+        tab[k] = e;
+        for (int q = 0; q <= 32; ++q) {
+            const double x = q / 32.0;
+            const double pg = ((double)e.z * x + e.y) * x + e.x;
+            const double pf = (double)e.w - h * x * (((double)e.z / 3.0 * x + 0.5 * e.y) * x + e.x);
+            err = std::max(err, std::fabs(pg - G((k + x) * h)) / g0);
+            err = std::max(err, std::fabs(pf - F((k + x) * h)) / f0);
+        }
+    }
+    ns.ltab_scale = (float)(kLTabN / (rc * rc));
+    ns.ltab_h = (float)h;
+    ns.ltab_err = (float)err;
+    return err;
+}
+
 rbsog_status enter(rbsog_ctx *ctx) {
     CK(cudaSetDevice(ctx->device));
     CK(cudaEventRecord(ctx->ev_in, ctx->user));
@@ -464,6 +518,8 @@ BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
     v.remaining = c->use_budget ? c->d_remaining : nullptr;
     v.list_cap = c->use_list ? c->list_cap : 0;
     v.precision = c->precision;
+    v.lpos = c->use_list ? c->lpos : nullptr;
+    v.linv = c->use_list ? c->linv : nullptr;
     return v;
 }
 
@@ -517,8 +573,8 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
             rbsog_status rs = rebuild(ctx->st);
             if (rs != RBSOG_OK) return rs;
         }
-        CK(launch_near_list(bv, ctx->nsog, ctx->sp32c, ctx->nbr_list, ctx->nbr_cnt, ctx->list_perm, ctx->fnear,
-                            nullptr, ctx->st, pf));
+        CK(launch_near_list(bv, ctx->nsog, ctx->d_ltab, ctx->nbr_list, ctx->nbr_cnt, ctx->list_perm, ctx->fnear,
+                            ctx->st, pf));
         CK(launch_rho_sweep(prec, bv, ctx->sp64, ctx->sp32c, ctx->rho_part, ctx->st, pf));
         CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
         CK(launch_far_scatter(prec, bv, ctx->sp64, ctx->sp32c, ctx->ktab, ctx->fnear, nullptr,
@@ -793,6 +849,26 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         list_cap = (((int)(1.5 * mean) + 48) + 7) / 8 * 8;
         if (list_cap > 280) lists = false;
     }
+    // the list path takes G and F from its combined table only: it needs
+    // that table at FP32 rounding level (else the cell stencil, which falls
+    // back to exp + Taylor sums when its own tables are not accurate enough)
+    if (lists) {
+        double sg = p[0].sigma, ww0 = p[0].omega0;
+        bool ok = p[0].b > 1.0 && p[0].M >= 0 && p[0].M < kMaxGauss && p[0].r_c > 0.0;
+        if (ok && !(sg > 0.0)) ok = solve_sigma(p[0].b, p[0].r_c, sg, ww0);
+        else if (ok && !(ww0 > 0.0)) ww0 = c0_weight(p[0].b, sg, p[0].r_c);
+        if (ok && ww0 > 0.0 && std::isfinite(ww0)) {
+            std::vector<double> w, sv;
+            bsa_coeffs(p[0].b, sg, p[0].M, w, sv);
+            w[0] = ww0;
+            NearSog tmp{};
+            std::vector<float4> t;
+            ok = build_list_table(tmp, t, w, sv, p[0].M, p[0].r_c) < kListTabTol;
+        } else {
+            ok = false;
+        }
+        if (!ok) lists = false;
+    }
     for (int s = 0; s < ns; ++s) {
         const rbsog_params &q = p[s];
         if (!(q.b > 1.0)) return fail(ctx, RBSOG_EINVAL, "system %d: b must be > 1", s);
@@ -868,6 +944,7 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
     ctx->precision = p[0].precision;
     build_near_sog(ctx->nsog, w, sv, p[0].M, p[0].r_c);
     build_sog_tables(ctx->nsog, w, sv, p[0].M, p[0].r_c);
+    build_list_table(ctx->nsog, ctx->h_ltab, w, sv, p[0].M, p[0].r_c);
 
     // --- per-system layout
     ctx->desc.assign(ns, SysDesc{});
@@ -940,11 +1017,20 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         CK(dalloc(&ctx->xref, n));
         CK(dalloc(&ctx->nbr_cnt, n));
         CK(dalloc(&ctx->list_perm, n));
+        CK(dalloc(&ctx->lpos, n));
+        CK(dalloc(&ctx->linv, n));
+        CK(dalloc(&ctx->d_ltab, (size_t)kLTabN));
+        CK(cudaMemcpy(ctx->d_ltab, ctx->h_ltab.data(), sizeof(float4) * kLTabN, cudaMemcpyHostToDevice));
         CK(dalloc(&ctx->nbr_list, (n + 31) / 32 * 32 * (size_t)ctx->list_cap));
         CK(dalloc(&ctx->d_rebuild, (size_t)ns + 1));
         CK(cudaMemset(ctx->xref, 0, sizeof(uint4) * n));
         CK(cudaMemset(ctx->nbr_cnt, 0, sizeof(int32_t) * n));
         CK(cudaMemset(ctx->list_perm, 0, sizeof(int32_t) * n));
+        // every position write before the first build goes through linv:
+        // start from the identity so that it stays inside the array
+        std::vector<int32_t> ident(n);
+        for (size_t q = 0; q < n; ++q) ident[q] = (int32_t)q;
+        CK(cudaMemcpy(ctx->linv, ident.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
         std::vector<int32_t> ones((size_t)ns + 1, 1);
         CK(cudaMemcpy(ctx->d_rebuild, ones.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice));
     }
@@ -1551,6 +1637,9 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->xref);
     dfree(&ctx->nbr_cnt);
     dfree(&ctx->list_perm);
+    dfree(&ctx->lpos);
+    dfree(&ctx->linv);
+    dfree(&ctx->d_ltab);
     dfree(&ctx->nbr_list);
     dfree(&ctx->d_rebuild);
     dfree(&ctx->cb.pack);
@@ -1707,8 +1796,8 @@ rbsog_status rebuild(rbsog_server *sv, const std::vector<int64_t> &keep, const s
             CK(cudaMemcpyAsync(nb->d_rebuild + k, old->d_rebuild + o, sizeof(int32_t), cudaMemcpyDeviceToDevice,
                                nb->st));
             CK(launch_list_move(n, od.p_off, ndsc.p_off, old->list_cap, nb->list_cap, old->nbr_list,
-                                old->nbr_cnt, old->list_perm, old->xref, nb->nbr_list, nb->nbr_cnt, nb->list_perm,
-                                nb->xref, nb->d_rebuild + k, nb->st));
+                                old->nbr_cnt, old->list_perm, old->xref, old->linv, nb->nbr_list, nb->nbr_cnt,
+                                nb->list_perm, nb->xref, nb->linv, nb->d_rebuild + k, nb->st));
         }
         nb->have_state[k] = 1;
         nb->force_valid[k] = old->force_valid[o];

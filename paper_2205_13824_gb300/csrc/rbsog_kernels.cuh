@@ -10,6 +10,7 @@ namespace rbsog {
 constexpr int kMaxGauss = 128;   // M + 1 <= kMaxGauss
 constexpr int kMaxTaylor = 16;   // terms of the folded wide-Gaussian series
 constexpr int kTabN = 64;        // intervals of the FP32 Gaussian-sum tables
+constexpr int kLTabN = 128;      // intervals of the neighbour-list path's combined table
 
 // Sum-of-Gaussians near kernel in the form the pair kernels evaluate.
 // Gaussians l < n_direct are evaluated with exp; the wide ones (s_l >= 2 r_c)
@@ -38,6 +39,14 @@ struct NearSog {
     float4 tab_f[kTabN];
     float tab_scale;               // kTabN / r_c^2
     float tab_err;                 // max abs error of the FP32 tables, relative to G(0) / F(0)
+    // Combined table of the neighbour-list path (one 16-byte entry per
+    // interval, held on the device): interval k of kLTabN covers
+    // u = (k + s) h, h = r_c^2 / kLTabN, and holds (g0, g1, g2, F(k h)) with
+    // G(u) ~ g0 + g1 s + g2 s^2 and, since dF/du = -G,
+    // F(u) ~ F(k h) - h (g0 s + g1 s^2 / 2 + g2 s^3 / 3).
+    float ltab_scale;              // kLTabN / r_c^2
+    float ltab_h;                  // r_c^2 / kLTabN
+    float ltab_err;                // max abs error of G and F from it, relative to G(0) / F(0)
 };
 
 // Box, cell grid and pair constants.
@@ -149,6 +158,9 @@ struct BatchView {
     int32_t max_tile_p;        // largest rho-sweep tile of the batch
     int32_t list_cap;          // neighbour-list slots per particle (0: no lists)
     int32_t precision;         // 0 FP64, 1 FP32C
+    uint4 *lpos;               // [n_total] fixed-point positions in the cell order of the
+                               // last list build (neighbour-list path; null otherwise)
+    int32_t *linv;             // [n_total] cell-order slot of caller particle i at that build
 };
 constexpr int kParticleBlock = 256;
 
@@ -167,13 +179,15 @@ __device__ __forceinline__ uint32_t fixed32(double x, double inv) {
 // rebuild[sys] and rebuild[n_sys] (any system).
 __device__ __forceinline__ void fixed_pack_check(const SysDesc &d, int sys, int n_sys, const double4_32a &p,
                                                  int64_t i, uint4 *__restrict__ sp32c,
-                                                 const uint4 *__restrict__ xref, int32_t *__restrict__ rebuild) {
+                                                 const uint4 *__restrict__ xref, int32_t *__restrict__ rebuild,
+                                                 uint4 *__restrict__ lpos, const int32_t *__restrict__ linv) {
     uint4 o;
     o.x = fixed32(p.x, d.box.fix_inv[0]);
     o.y = fixed32(p.y, d.box.fix_inv[1]);
     o.z = fixed32(p.z, d.box.fix_inv[2]);
     o.w = __float_as_uint((float)p.w);
     sp32c[i] = o;
+    if (lpos) lpos[linv[i]] = o;
     const uint4 r = xref[i];
     const float dx = (float)(int32_t)(o.x - r.x) * d.box.fix_scale[0];
     const float dy = (float)(int32_t)(o.y - r.y) * d.box.fix_scale[1];
@@ -217,9 +231,12 @@ cudaError_t launch_near(int precision, const BatchView &bv, const NearSog &sog, 
 
 // ---- neighbour lists (k_verlet.cu), FP32C ------------------------------------
 // Lists: sliced by groups of 32 cell-order positions s of the last build
-// (list_perm[s] the caller index): slot k of s at ((s / 32) cap + k) 32 +
-// s % 32, nbr_cnt[s] entries; xref[i] the fixed-point position of caller
-// particle i at that build; rebuild[n_sys + 1] flags (per system, any).
+// (list_perm[s] the caller index, linv its inverse): slot k of s at
+// ((s / 32) cap + k) 32 + s % 32, nbr_cnt[s] entries, each the cell-order
+// position of a partner; lpos[s] the current fixed-point position of the
+// particle at s (written by the builder, then by every kick-drift through
+// linv); xref[i] the fixed-point position of caller particle i at that
+// build; rebuild[n_sys + 1] flags (per system, any).
 size_t list_build_smem(int cap, int list_cap);
 cudaError_t launch_fix_pack(const BatchView &bv, const double4_32a *posq, uint4 *sp32c, const uint4 *xref,
                             int32_t *rebuild, cudaStream_t st, const Prof *prof);
@@ -234,14 +251,14 @@ cudaError_t launch_rebuild_condition(cudaGraphConditionalHandle h, const int32_t
 // Moves one running system's lists between batch layouts (serving engine).
 cudaError_t launch_list_move(int64_t n, int64_t old_off, int64_t new_off, int old_cap, int new_cap,
                              const int32_t *old_list, const int32_t *old_cnt, const int32_t *old_perm,
-                             const uint4 *old_xref, int32_t *new_list, int32_t *new_cnt, int32_t *new_perm,
-                             uint4 *new_xref, int32_t *new_flag, cudaStream_t st);
+                             const uint4 *old_xref, const int32_t *old_linv, int32_t *new_list,
+                             int32_t *new_cnt, int32_t *new_perm, uint4 *new_xref, int32_t *new_linv,
+                             int32_t *new_flag, cudaStream_t st);
 // Near-field force (caller order) with both energies packed in fnear[i].w as
-// two floats (U_near high word, U_wca low word); accepted pairs into nbr[i]
-// when non-null.
-cudaError_t launch_near_list(const BatchView &bv, const NearSog &sog, const uint4 *sp32c, const int32_t *nbr_list,
-                             const int32_t *nbr_cnt, const int32_t *list_perm, double4_32a *fnear, int32_t *nbr,
-                             cudaStream_t st, const Prof *prof);
+// two floats (U_near high word, U_wca low word).
+cudaError_t launch_near_list(const BatchView &bv, const NearSog &sog, const float4 *ltab, const int32_t *nbr_list,
+                             const int32_t *nbr_cnt, const int32_t *list_perm, double4_32a *fnear, cudaStream_t st,
+                             const Prof *prof);
 
 // ---- far field (k_far.cu) -----------------------------------------------------
 // tile_override > 0 replaces the default particles-per-tile rule (tunable)
