@@ -237,7 +237,10 @@ def run_ours(args, rank, world, local, dist):
             dist.barrier()
         torch.cuda.synchronize()
 
-    meas = B.rbsog_measure_peaks(local)         # roofline denominators on this GPU
+    # roofline denominators on this GPU: the best of three runs, so that a
+    # run slowed by a clock dip does not lower the peak
+    runs = [B.rbsog_measure_peaks(local) for _ in range(3)]
+    meas = {k: max(r[k] for r in runs) for k in runs[0]}
     tuned = B.rbsog_batch_autotune(g.ctx, 3)    # launch shapes for this workload
     g.step(W)                                   # warm-up (builds the step graph)
     barrier()

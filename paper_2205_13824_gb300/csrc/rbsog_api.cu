@@ -1359,7 +1359,7 @@ rbsog_status rbsog_batch_get_state(rbsog_batch *ctx, int32_t sys, double *x, dou
     for (int k = 0; k < 3; ++k) {
         if (!dst[k]) continue;
         double *direct = kernel_view(dst[k]);
-        if (direct) {   // written in place (device or pinned host memory)
+        if (direct) {   // written in place (device or managed memory)
             CK(launch_unpack(n, src[k], direct, ctx->st));
             continue;
         }
