@@ -273,18 +273,16 @@ def run_ours(args, rank, world, local, dist):
     launches_per_step = sum(c for c, _ in prof.values()) / K
 
     # end to end through the C ABI from pinned host buffers: per step the
-    # state (q, x, v, f) goes host->device, one step runs, (x, v, f) comes back
+    # state (q, x, v, f) goes host->device, one step runs, (x, v, f) comes
+    # back, in one rbsog_step_io call (the state lives in host memory)
     hq = torch.tensor(q).pin_memory()
     xs, vs, fs = (torch.empty((N, 3), dtype=torch.float64).pin_memory() for _ in range(3))
-    B.rbsog_get_state(g.ctx, xs, vs, fs)
+    step0 = B.rbsog_get_state(g.ctx, xs, vs, fs)
     cur = B.rbsog_get_cursor(g.ctx)
     barrier()
     t0 = time.perf_counter()
     for i in range(n_e2e):
-        B.rbsog_set_state(g.ctx, hq, xs, vs)
-        B.rbsog_restore(g.ctx, fs, cur + i, 0)
-        B.rbsog_step(g.ctx, 1)
-        B.rbsog_get_state(g.ctx, xs, vs, fs)
+        B.rbsog_step_io(g.ctx, hq, xs, vs, fs, cur + i, step0 + i, 1, xs, vs, fs)
     t_e2e = (time.perf_counter() - t0) / n_e2e
     h2d = hq.numel() * 8 + 3 * xs.numel() * 8
     d2h = 3 * xs.numel() * 8

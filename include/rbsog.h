@@ -162,6 +162,24 @@ rbsog_status rbsog_get_cursor(const rbsog_ctx *ctx, int64_t *kset_cursor);
  * cursor outside [0, n_ksets]. */
 rbsog_status rbsog_restore(rbsog_ctx *ctx, const double *f, int64_t kset_cursor, int64_t step);
 
+/* Steps for a caller that keeps the state in its own memory: the same
+ * result, bit for bit, as rbsog_set_state(q, x, v), rbsog_restore(f,
+ * kset_cursor, step) (or no restore when f is NULL: the forces of x are then
+ * computed first, consuming one k-set), rbsog_step(nsteps) and
+ * rbsog_get_state(x_out, v_out, f_out), i.e. nsteps velocity-Verlet steps of
+ * Algorithm 1 from the given state.  One call, one synchronisation at the
+ * end; the last step's new positions are copied out while the rest of that
+ * step (forces, second half kick) runs.  q[n], x, v, f, x_out, v_out,
+ * f_out ([n][3] FP64) may be host or device memory; outputs may be NULL and
+ * may alias the inputs.  Single-system contexts only (RBSOG_EINVAL for a
+ * batch of several systems or a serving batch); RBSOG_EINVAL for
+ * non-neutral charges, nsteps < 1, a negative cursor or step, or a
+ * k-sequence too short for the steps; RBSOG_ENUMERIC as rbsog_get_state.
+ * On return the outputs are written. */
+rbsog_status rbsog_step_io(rbsog_ctx *ctx, const double *q, const double *x, const double *v, const double *f,
+                           int64_t kset_cursor, int64_t step, int64_t nsteps, double *x_out, double *v_out,
+                           double *f_out);
+
 /* Energies of the last force evaluation and the kinetic energy (host). */
 rbsog_status rbsog_get_energies(rbsog_ctx *ctx, rbsog_energies *e);
 

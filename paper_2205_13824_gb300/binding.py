@@ -24,7 +24,7 @@ STATUS = {0: "RBSOG_OK", 1: "RBSOG_EINVAL", 2: "RBSOG_ENOMEM", 3: "RBSOG_ECUDA",
 EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_state",
            "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_get_energies",
            "rbsog_get_kseq", "rbsog_rho", "rbsog_get_cells", "rbsog_set_profiling",
-           "rbsog_get_cursor", "rbsog_restore", "rbsog_rho_noalloc", "rbsog_measure_peaks",
+           "rbsog_get_cursor", "rbsog_restore", "rbsog_step_io", "rbsog_rho_noalloc", "rbsog_measure_peaks",
            "rbsog_batch_create", "rbsog_batch_set_params", "rbsog_batch_set_state", "rbsog_batch_restore",
            "rbsog_batch_get_state", "rbsog_batch_get_energies", "rbsog_batch_get_kseq", "rbsog_batch_step",
            "rbsog_batch_autotune", "rbsog_batch_rdf", "rbsog_rdf",
@@ -80,6 +80,7 @@ def _load():
         "rbsog_get_energies": [P, C.POINTER(rbsog_energies)],
         "rbsog_get_cursor": [P, C.POINTER(C.c_int64)],
         "rbsog_restore": [P, P, C.c_int64, C.c_int64],
+        "rbsog_step_io": [P, P, P, P, P, C.c_int64, C.c_int64, C.c_int64, P, P, P],
         "rbsog_get_kseq": [P, C.c_int64, C.c_int64, P],
         "rbsog_rho": [P, P, C.c_int32, P],
         "rbsog_get_cells": [P, P, P, P],
@@ -201,6 +202,12 @@ def rbsog_get_cursor(ctx):
 
 def rbsog_restore(ctx, f, kset_cursor: int, step: int):
     _check(ctx, _lib.rbsog_restore(ctx, _ptr(f), int(kset_cursor), int(step)))
+
+
+def rbsog_step_io(ctx, q, x, v, f, kset_cursor: int, step: int, nsteps: int, x_out=None, v_out=None,
+                  f_out=None):
+    _check(ctx, _lib.rbsog_step_io(ctx, _ptr(q), _ptr(x), _ptr(v), _ptr(f), int(kset_cursor), int(step),
+                                   int(nsteps), _ptr(x_out), _ptr(v_out), _ptr(f_out)))
 
 
 def rbsog_get_energies(ctx):

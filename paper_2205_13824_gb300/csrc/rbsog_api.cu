@@ -66,6 +66,9 @@ struct rbsog_ctx {
     cudaStream_t user = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_q = nullptr, ev_x = nullptr, ev_io = nullptr;   // rbsog_step_io
+    cudaStream_t io = nullptr;                                     // rbsog_step_io downloads
+    cudaGraphExec_t graph_tail = nullptr;   // a step without its kick-drift (rbsog_step_io)
     std::string err;
 
     bool have_params = false;
@@ -591,13 +594,23 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
     return RBSOG_OK;
 }
 
-rbsog_status enqueue_step(rbsog_ctx *ctx) {
+// A step is the kick-drift followed by the tail (forces, second kick,
+// energies, thermostat, step counters); rbsog_step_io launches the two parts
+// separately for its last step so that the positions can be copied out while
+// the tail runs.
+rbsog_status enqueue_kick_drift(rbsog_ctx *ctx) {
     const Prof *pf = prof_of(ctx);
     const BatchView bv = view(ctx);
     if (ctx->use_list)
         CK(launch_kick_drift(bv, ctx->posq, ctx->vel, ctx->force, ctx->st, pf, ctx->sp32c, ctx->xref, ctx->d_rebuild));
     else
         CK(launch_kick_drift(bv, ctx->posq, ctx->vel, ctx->force, ctx->st, pf));
+    return RBSOG_OK;
+}
+
+rbsog_status enqueue_step_tail(rbsog_ctx *ctx) {
+    const Prof *pf = prof_of(ctx);
+    const BatchView bv = view(ctx);
     rbsog_status s = enqueue_forces(ctx, bv, nullptr, nullptr, ctx->use_list);
     if (s != RBSOG_OK) return s;
     CK(launch_kick(bv, ctx->vel, ctx->force, ctx->kpart, ctx->st, pf));
@@ -609,9 +622,37 @@ rbsog_status enqueue_step(rbsog_ctx *ctx) {
     return RBSOG_OK;
 }
 
+rbsog_status enqueue_step(rbsog_ctx *ctx) {
+    rbsog_status s = enqueue_kick_drift(ctx);
+    if (s != RBSOG_OK) return s;
+    return enqueue_step_tail(ctx);
+}
+
 void drop_graph(rbsog_ctx *c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph_tail) cudaGraphExecDestroy(c->graph_tail);
     c->graph = nullptr;
+    c->graph_tail = nullptr;
+}
+
+// Captures a whole step (tail = false) or its tail into *out (once).
+rbsog_status capture_step(rbsog_ctx *ctx, bool tail, cudaGraphExec_t *out) {
+    if (*out) return RBSOG_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    rbsog_status es = tail ? enqueue_step_tail(ctx) : enqueue_step(ctx);
+    ctx->capturing = false;
+    cudaError_t ce = cudaStreamEndCapture(ctx->st, &g);
+    if (es != RBSOG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return es;
+    }
+    if (ce != cudaSuccess) return fail(ctx, RBSOG_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return fail(ctx, RBSOG_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    return RBSOG_OK;
 }
 
 rbsog_status check_flags(rbsog_ctx *ctx) {
@@ -776,6 +817,11 @@ rbsog_status rbsog_batch_create(rbsog_batch **out, int32_t n_sys, const int64_t 
     if (cudaSetDevice(device) != cudaSuccess) return bail(RBSOG_ECUDA);
     if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess) return bail(RBSOG_ECUDA);
     if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess) return bail(RBSOG_ECUDA);
+    if (cudaStreamCreateWithFlags(&ctx->io, cudaStreamNonBlocking) != cudaSuccess) return bail(RBSOG_ECUDA);
+    if (cudaEventCreateWithFlags(&ctx->ev_q, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_x, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_io, cudaEventDisableTiming) != cudaSuccess)
+        return bail(RBSOG_ECUDA);
     if (cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess)
         return bail(RBSOG_ECUDA);
@@ -1317,22 +1363,8 @@ rbsog_status rbsog_batch_step(rbsog_batch *ctx, int64_t nsteps) {
             if (es != RBSOG_OK) return es;
         }
     } else if (nsteps > 0) {
-        if (!ctx->graph) {
-            cudaGraph_t g = nullptr;
-            CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
-            ctx->capturing = true;
-            es = enqueue_step(ctx);
-            ctx->capturing = false;
-            cudaError_t ce = cudaStreamEndCapture(ctx->st, &g);
-            if (es != RBSOG_OK) {
-                if (g) cudaGraphDestroy(g);
-                return es;
-            }
-            if (ce != cudaSuccess) return fail(ctx, RBSOG_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
-            ce = cudaGraphInstantiate(&ctx->graph, g, 0);
-            cudaGraphDestroy(g);
-            if (ce != cudaSuccess) return fail(ctx, RBSOG_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
-        }
+        es = capture_step(ctx, false, &ctx->graph);
+        if (es != RBSOG_OK) return es;
         for (int64_t t = 0; t < nsteps; ++t) CK(cudaGraphLaunch(ctx->graph, ctx->st));
     }
     for (int s = 0; s < ctx->n_sys; ++s) {
@@ -1344,6 +1376,118 @@ rbsog_status rbsog_batch_step(rbsog_batch *ctx, int64_t nsteps) {
 }
 
 rbsog_status rbsog_step(rbsog_ctx *ctx, int64_t nsteps) { return rbsog_batch_step(ctx, nsteps); }
+
+rbsog_status rbsog_step_io(rbsog_ctx *ctx, const double *q, const double *x, const double *v, const double *f,
+                           int64_t kset_cursor, int64_t step, int64_t nsteps, double *x_out, double *v_out,
+                           double *f_out) {
+    if (!ctx || !q || !x || !v) return RBSOG_EINVAL;
+    if (ctx->n_sys != 1) return fail(ctx, RBSOG_EINVAL, "rbsog_step_io needs a single system");
+    if (!ctx->have_params) return fail(ctx, RBSOG_ESTATE, "set_params must come first");
+    if (ctx->use_budget) return fail(ctx, RBSOG_EINVAL, "rbsog_step_io does not run step budgets");
+    if (nsteps < 1 || step < 0 || kset_cursor < 0) return fail(ctx, RBSOG_EINVAL, "need nsteps >= 1, step >= 0, "
+                                                                                  "cursor >= 0");
+    const int64_t need = nsteps + (f ? 0 : 1);
+    if (kset_cursor + need > ctx->desc[0].n_sets)
+        return fail(ctx, RBSOG_EINVAL, "pre-sampled k-sequence too short (%lld sets from the cursor, %lld needed)",
+                    (long long)(ctx->desc[0].n_sets - std::min(kset_cursor, ctx->desc[0].n_sets)), (long long)need);
+    rbsog_status es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    const int64_t n = ctx->n_per[0];
+    const size_t bytes3 = sizeof(double) * 3 * n;
+    // the charges first: their sums (neutrality check, self energy) are
+    // added on the host while the other inputs are still being copied
+    const double *sq = kernel_view(q);
+    if (!sq) {
+        CK(cudaMemcpyAsync(ctx->staging + 9 * n, q, sizeof(double) * n, cudaMemcpyDefault, ctx->st));
+        sq = ctx->staging + 9 * n;
+    }
+    const int64_t nb = (n + 255) / 256;
+    CK(launch_charge_sums(n, sq, ctx->qpart, ctx->st));
+    CK(cudaMemcpyAsync(ctx->h_qpart, ctx->qpart, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaEventRecord(ctx->ev_q, ctx->st));
+    const double *in[3] = {x, v, f};
+    const double *sin[3] = {nullptr, nullptr, nullptr};
+    for (int k = 0; k < 3; ++k) {
+        if (!in[k]) continue;
+        sin[k] = kernel_view(in[k]);
+        if (!sin[k]) {
+            CK(cudaMemcpyAsync(ctx->staging + 3 * n * k, in[k], bytes3, cudaMemcpyDefault, ctx->st));
+            sin[k] = ctx->staging + 3 * n * k;
+        }
+    }
+    CK(cudaEventSynchronize(ctx->ev_q));
+    double qs = 0.0, qa = 0.0, q2 = 0.0;
+    for (int64_t b = 0; b < nb; ++b) {
+        qs += ctx->h_qpart[3 * b];
+        qa += ctx->h_qpart[3 * b + 1];
+        q2 += ctx->h_qpart[3 * b + 2];
+    }
+    if (!std::isfinite(qa) || std::fabs(qs) > 1e-12 * qa) {
+        CK(cudaStreamSynchronize(ctx->st));   // the caller may reuse its buffers
+        if (!std::isfinite(qa)) return fail(ctx, RBSOG_EINVAL, "non-finite charge");
+        return fail(ctx, RBSOG_EINVAL, "charges are not neutral (sum %.3e)", qs);
+    }
+    ctx->sum_q2[0] = q2;
+    ctx->desc[0].U_self = self_energy(ctx, 0);
+    std::memcpy(&ctx->h_i64[2], &ctx->desc[0].U_self, sizeof(double));
+    ctx->h_i64[0] = kset_cursor;
+    ctx->h_i64[1] = step;
+    CK(cudaMemcpyAsync(&ctx->d_desc[0].U_self, &ctx->h_i64[2], sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->cursor, ctx->h_i64, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->step_ctr, ctx->h_i64 + 1, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->st));
+    CK(launch_pack(n, sin[0], sq, ctx->posq, 1, ctx->p[0].L, ctx->st));
+    CK(launch_pack(n, sin[1], nullptr, ctx->vel, 0, ctx->p[0].L, ctx->st));
+    if (f) CK(launch_pack(n, sin[2], nullptr, ctx->force, 0, ctx->p[0].L, ctx->st));
+    ctx->have_state[0] = 1;
+    ctx->host_cursor[0] = kset_cursor;
+    ctx->force_valid[0] = f ? 1 : 0;
+    es = initial_forces(ctx);
+    if (es != RBSOG_OK) return es;
+    // all steps but the last one whole; the last one as kick-drift, then its
+    // tail while the new positions are copied out on the io stream
+    if (ctx->profiling) {
+        for (int64_t t = 0; t + 1 < nsteps; ++t) {
+            es = enqueue_step(ctx);
+            if (es != RBSOG_OK) return es;
+        }
+    } else if (nsteps > 1) {
+        es = capture_step(ctx, false, &ctx->graph);
+        if (es != RBSOG_OK) return es;
+        for (int64_t t = 0; t + 1 < nsteps; ++t) CK(cudaGraphLaunch(ctx->graph, ctx->st));
+    }
+    es = enqueue_kick_drift(ctx);
+    if (es != RBSOG_OK) return es;
+    double *out[3] = {x_out, v_out, f_out};
+    const double4_32a *src[3] = {ctx->posq, ctx->vel, ctx->force};
+    CK(cudaEventRecord(ctx->ev_x, ctx->st));
+    CK(cudaStreamWaitEvent(ctx->io, ctx->ev_x, 0));
+    if (x_out) {
+        double *direct = kernel_view(x_out);
+        CK(launch_unpack(n, src[0], direct ? direct : ctx->staging, ctx->io));
+        if (!direct) CK(cudaMemcpyAsync(x_out, ctx->staging, bytes3, cudaMemcpyDefault, ctx->io));
+    }
+    CK(cudaEventRecord(ctx->ev_io, ctx->io));
+    if (ctx->profiling) {
+        es = enqueue_step_tail(ctx);
+        if (es != RBSOG_OK) return es;
+    } else {
+        es = capture_step(ctx, true, &ctx->graph_tail);
+        if (es != RBSOG_OK) return es;
+        CK(cudaGraphLaunch(ctx->graph_tail, ctx->st));
+    }
+    for (int k = 1; k < 3; ++k) {
+        if (!out[k]) continue;
+        double *direct = kernel_view(out[k]);
+        double *reg = ctx->staging + 3 * n * k;
+        CK(launch_unpack(n, src[k], direct ? direct : reg, ctx->st));
+        if (!direct) CK(cudaMemcpyAsync(out[k], reg, bytes3, cudaMemcpyDefault, ctx->st));
+    }
+    CK(cudaStreamWaitEvent(ctx->st, ctx->ev_io, 0));
+    ctx->host_cursor[0] += nsteps;
+    es = check_flags(ctx);   // synchronises: the outputs are in place on return
+    if (es != RBSOG_OK) return es;
+    return leave(ctx);
+}
 
 rbsog_status rbsog_batch_get_state(rbsog_batch *ctx, int32_t sys, double *x, double *v, double *f, int64_t *step) {
     if (!ctx) return RBSOG_EINVAL;
@@ -1667,8 +1811,12 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     if (ctx->h_i64) cudaFreeHost(ctx->h_i64);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    if (ctx->ev_q) cudaEventDestroy(ctx->ev_q);
+    if (ctx->ev_x) cudaEventDestroy(ctx->ev_x);
+    if (ctx->ev_io) cudaEventDestroy(ctx->ev_io);
     if (ctx->st) cudaStreamDestroy(ctx->st);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->io) cudaStreamDestroy(ctx->io);
     delete ctx;
     return RBSOG_OK;
 }

@@ -428,3 +428,61 @@ def test_invalid_arguments_are_rejected():
         B.rbsog_step(ctx, 5)                               # only 2 k-sets sampled
     assert ei.value.status == 1
     B.rbsog_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+@pytest.mark.parametrize("nsteps,with_f,where", [(1, True, "pinned"), (3, True, "device"), (2, False, "pinned")])
+def test_step_io_equals_the_composed_calls(prec, nsteps, with_f, where):
+    """rbsog_step_io (state in, steps, state out in one call) gives the bits
+    of rbsog_set_state + rbsog_restore + rbsog_step + rbsog_get_state, from a
+    mid-run checkpoint (with forces) or from positions alone."""
+    _dev()
+    import torch
+    B = _lib().binding
+    N, L, P = 4998, 21.5, 64
+    q, x, v = I.electrolyte(N, L, seed=12)
+    if with_f:
+        g, _ = make(N, L, P, prec=prec, n_ksets=12, seed=3)
+        g.set_state(*to_dev(q, x, v))
+        g.step(4)
+        x, v, f = (a.cpu().numpy() for a in g.state()[:3])
+        cur, step = B.rbsog_get_cursor(g.ctx), 4
+        g.close()
+    else:
+        f, cur, step = None, 0, 0
+
+    def buf(a):
+        t = torch.tensor(a) if a is not None else None
+        if t is None:
+            return None
+        return t.pin_memory() if where == "pinned" else t.cuda()
+
+    ref, _ = make(N, L, P, prec=prec, n_ksets=12, seed=3)
+    B.rbsog_set_state(ref.ctx, q, x, v)
+    if with_f:
+        B.rbsog_restore(ref.ctx, f, cur, step)
+    B.rbsog_step(ref.ctx, nsteps)
+    xr, vr, fr = (np.zeros((N, 3)) for _ in range(3))
+    sr = B.rbsog_get_state(ref.ctx, xr, vr, fr)
+    er = B.rbsog_get_energies(ref.ctx)
+    ref.close()
+
+    g, _ = make(N, L, P, prec=prec, n_ksets=12, seed=3)
+    xo, vo, fo = (buf(np.zeros((N, 3))) for _ in range(3))
+    B.rbsog_step_io(g.ctx, buf(q), buf(x), buf(v), buf(f), cur, step, nsteps, xo, vo, fo)
+    torch.cuda.synchronize()
+    for a, b in ((xr, xo), (vr, vo), (fr, fo)):
+        assert np.array_equal(a, b.cpu().numpy())
+    xs = np.zeros((N, 3))
+    assert B.rbsog_get_state(g.ctx, xs) == sr
+    assert np.array_equal(xs, xr)
+    assert B.rbsog_get_energies(g.ctx) == er
+    # the same buffers in and out (the bench's end-to-end loop)
+    xb, vb, fb = buf(xr), buf(vr), buf(fr)
+    B.rbsog_step_io(g.ctx, buf(q), xb, vb, fb, B.rbsog_get_cursor(g.ctx), sr, 1, xb, vb, fb)
+    assert np.all(np.isfinite(xb.cpu().numpy()))
+    with pytest.raises(B.RBSOGError):
+        B.rbsog_step_io(g.ctx, buf(q), xb, vb, fb, 0, 0, 0, xb, vb, fb)   # nsteps < 1
+    with pytest.raises(B.RBSOGError):
+        B.rbsog_step_io(g.ctx, buf(q), xb, vb, fb, 12, 0, 1, xb, vb, fb)  # no k-set left
+    g.close()
