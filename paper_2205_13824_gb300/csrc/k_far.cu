@@ -18,9 +18,9 @@
 //            FP32 pair per thread.
 //            FP64: phase t = m . (x / L) in FP64, reduced by t - rint(t),
 //            cos/sin via sincospi.
-// combine    one warp per frequency sums the block partials in FP64 in a
-//            fixed order and writes rho(k) plus the scatter table entry
-//            (k vector, coef Re rho, coef Im rho, m).
+// combine    one 128-thread block per frequency sums the block partials in
+//            FP64 in a fixed order and writes rho(k) plus the scatter table
+//            entry (k vector, coef Re rho, coef Im rho, m).
 // scatter    frequencies staged through shared memory in chunks; adds the
 //            near-field force and writes the total to the particle's
 //            caller-order slot.  FP64: one thread per particle.  FP32C: two
@@ -39,6 +39,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kSweepThreads = 256;          // 8 warps
 constexpr int kKTile = 32;                  // frequencies per sweep block (FP64)
 constexpr int kKTile32 = 64;                // frequencies per sweep block (FP32C), two per lane
+constexpr int kCombineThreads = 128;        // one combine block per frequency
 constexpr int kScatterThreads = kParticleBlock;
 constexpr int kScatter32Threads = kParticleBlock / 2;   // two particles per thread
 constexpr int kKChunk32 = 512;              // frequencies per staged chunk (FP32C, 16 KiB)
@@ -174,27 +175,48 @@ __global__ void __launch_bounds__(kSweepThreads)
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(256) k_rho_combine(BatchView bv, const double2 *__restrict__ rho_part,
-                                                     double2 *__restrict__ rho, void *__restrict__ ktab) {
-    const int lane = threadIdx.x & 31;
-    const int64_t gk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // system * P + k
-    if (gk >= (int64_t)bv.n_sys * bv.P) return;
+__global__ void __launch_bounds__(kCombineThreads) k_rho_combine(BatchView bv, const double2 *__restrict__ rho_part,
+                                                                 double2 *__restrict__ rho, void *__restrict__ ktab) {
+    __shared__ double2 s_w[kCombineThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t gk = blockIdx.x;   // system * P + k: one block per frequency
     const int sy = (int)(gk / bv.P), k = (int)(gk % bv.P);
     if (bv.remaining && bv.remaining[sy] == 0) return;
     const SysDesc &d = bv.sys[sy];
     const double2 *row = rho_part + d.rp_off + (int64_t)k * d.n_ptiles;
+    // thread t sums tiles t, t + 128, ... in order; then the warps' trees,
+    // then the 4 warps in order
     double re = 0.0, im = 0.0;
-    for (int t = lane; t < d.n_ptiles; t += 32) {
-        const double2 v = row[t];
-        re += v.x;
-        im += v.y;
+    for (int t0 = threadIdx.x; t0 < d.n_ptiles; t0 += 8 * kCombineThreads) {
+        double2 v[8];   // eight loads in flight, then the adds in order
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int t = t0 + u * kCombineThreads;
+            v[u] = t < d.n_ptiles ? row[t] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (t0 + u * kCombineThreads < d.n_ptiles) {
+                re += v[u].x;
+                im += v[u].y;
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         re += __shfl_down_sync(0xffffffffu, re, o);
         im += __shfl_down_sync(0xffffffffu, im, o);
     }
-    if (lane == 0) {
+    if (lane == 0) s_w[wid] = make_double2(re, im);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        re = s_w[0].x;
+        im = s_w[0].y;
+#pragma unroll
+        for (int w2 = 1; w2 < kCombineThreads / 32; ++w2) {
+            re += s_w[w2].x;
+            im += s_w[w2].y;
+        }
         rho[gk] = make_double2(re, im);
         const int4 m = load_m(bv, d, sy, k);
         const double kx = 2.0 * kPi * m.x / d.box.L[0], ky = 2.0 * kPi * m.y / d.box.L[1],
@@ -425,11 +447,11 @@ cudaError_t launch_rho_sweep(int precision, const BatchView &bv, const double4_3
 cudaError_t launch_rho_combine(int precision, const BatchView &bv, const double2 *rho_part, double2 *rho,
                                void *ktab, cudaStream_t st, const Prof *prof) {
     ProfScope ps(prof, "rho_combine");
-    const unsigned blocks = (unsigned)(((int64_t)bv.n_sys * bv.P * 32 + 255) / 256);
+    const unsigned blocks = (unsigned)((int64_t)bv.n_sys * bv.P);
     if (precision == 1)
-        k_rho_combine<1><<<blocks, 256, 0, st>>>(bv, rho_part, rho, ktab);
+        k_rho_combine<1><<<blocks, kCombineThreads, 0, st>>>(bv, rho_part, rho, ktab);
     else
-        k_rho_combine<0><<<blocks, 256, 0, st>>>(bv, rho_part, rho, ktab);
+        k_rho_combine<0><<<blocks, kCombineThreads, 0, st>>>(bv, rho_part, rho, ktab);
     return cudaGetLastError();
 }
 

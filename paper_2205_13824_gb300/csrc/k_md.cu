@@ -9,10 +9,20 @@ namespace rbsog {
 namespace {
 
 constexpr int kThreads = kParticleBlock;
+constexpr int kFinThreads = 256;
 
 __device__ __forceinline__ double fold(double x, double L) {
     double v = x - L * floor(x / L);
     return v >= L ? 0.0 : v;
+}
+
+// x < 0 or x >= L (L > 0) decided on the bit patterns with integer compares
+// (the order of non-negative doubles is that of their bits): the same
+// outcome as the FP64 compares, which are scarce on this GPU; -0.0 stays,
+// NaN folds to NaN either way.
+__device__ __forceinline__ bool outside(double x, long long Lbits) {
+    const long long b = __double_as_longlong(x);
+    return b >= Lbits || (b < 0 && b != (long long)0x8000000000000000ull);
 }
 
 // v += dt/2 F/m ; x += dt v ; x folded into [0, L).
@@ -30,7 +40,7 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift(BatchView bv, double4_3
     const double4_32a f = force[i];
     double4_32a v = vel[i];
     double4_32a p = posq[i];
-    const double h = 0.5 * a.dt * a.inv_mass;
+    const double h = a.half_dt_inv_mass;
     v.x += h * f.x;
     v.y += h * f.y;
     v.z += h * f.z;
@@ -38,9 +48,9 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift(BatchView bv, double4_3
     p.x += a.dt * v.x;
     p.y += a.dt * v.y;
     p.z += a.dt * v.z;
-    if (p.x < 0.0 || p.x >= a.box.L[0]) p.x = fold(p.x, a.box.L[0]);
-    if (p.y < 0.0 || p.y >= a.box.L[1]) p.y = fold(p.y, a.box.L[1]);
-    if (p.z < 0.0 || p.z >= a.box.L[2]) p.z = fold(p.z, a.box.L[2]);
+    if (outside(p.x, __double_as_longlong(a.box.L[0]))) p.x = fold(p.x, a.box.L[0]);
+    if (outside(p.y, __double_as_longlong(a.box.L[1]))) p.y = fold(p.y, a.box.L[1]);
+    if (outside(p.z, __double_as_longlong(a.box.L[2]))) p.z = fold(p.z, a.box.L[2]);
     vel[i] = v;
     posq[i] = p;
     if (sp32c) fixed_pack_check(a, w.x, bv.n_sys, p, i, sp32c, xref, rebuild, bv.lpos, bv.linv);
@@ -57,20 +67,23 @@ __global__ void __launch_bounds__(kThreads) k_kick(BatchView bv, double4_32a *__
     const int64_t il = (int64_t)w.y * kThreads + threadIdx.x;
     const int64_t i = a.p_off + il;
     double ke = 0.0;
+    float kf = 0.f;
     if (il < a.n) {
         const double4_32a f = force[i];
         double4_32a v = vel[i];
-        const double h = 0.5 * a.dt * a.inv_mass;
+        const double h = a.half_dt_inv_mass;
         v.x += h * f.x;
         v.y += h * f.y;
         v.z += h * f.z;
         vel[i] = v;
-        ke = 0.5 * a.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
+        if (bv.precision == 1)   // FP32C: |v|^2 in FP64, the rest in FP32
+            kf = (float)fma(v.z, v.z, fma(v.y, v.y, v.x * v.x)) * a.half_mass_f;
+        else
+            ke = 0.5 * a.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
     }
     if (bv.precision == 1) {
         // FP32C: the warp's terms in an FP32 tree (FP64 adds are scarce on
         // this GPU), the warps in FP64
-        float kf = (float)ke;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) kf += __shfl_down_sync(0xffffffffu, kf, o);
         ke = (double)kf;
@@ -87,53 +100,44 @@ __global__ void __launch_bounds__(kThreads) k_kick(BatchView bv, double4_32a *__
     }
 }
 
-// One block per system: fixed-order sums of its near-energy partials, |rho|^2
-// and kinetic partials; Berendsen factor; k-set cursor and step counter.
-__global__ void __launch_bounds__(1024) k_finalize(BatchView bv, const double2 *__restrict__ epart,
-                                                   const double2 *__restrict__ rho,
-                                                   const double *__restrict__ kpart, int with_kinetic,
-                                                   double *__restrict__ energy, int64_t advance) {
-    __shared__ double s_red[4][32];
-    const int sy = blockIdx.x;
+// kFinChunks blocks per system, each summing one chunk of the near-energy
+// partials, |rho(k)|^2 and kinetic partials in fixed order (thread t takes
+// the chunk's entries t, t + 256, ...; then the warps' trees; then the warps
+// in order); the last block of the system to finish adds the chunk sums in
+// chunk order and writes the energies, T, the Berendsen factor, the cursor
+// and the step counter.  No block waits for another.
+__global__ void __launch_bounds__(kFinThreads) k_finalize(BatchView bv, const double2 *__restrict__ epart,
+                                                          const double2 *__restrict__ rho,
+                                                          const double *__restrict__ kpart, int with_kinetic,
+                                                          double *__restrict__ energy, int64_t advance) {
+    __shared__ double s_red[4][kFinThreads / 32];
+    __shared__ bool s_last;
+    const int sy = blockIdx.x / kFinChunks, c = blockIdx.x % kFinChunks;
     if (bv.force_mask && !bv.force_mask[sy]) return;
     if (bv.remaining && bv.remaining[sy] == 0) return;
     const SysDesc &a = bv.sys[sy];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    auto chunk = [c](int len, int &lo, int &hi) {
+        lo = (int)((int64_t)len * c / kFinChunks);
+        hi = (int)((int64_t)len * (c + 1) / kFinChunks);
+    };
     double un = 0.0, uw = 0.0, r2 = 0.0, ke = 0.0;
-    // each thread sums j = tid, tid + B, tid + 2B, ... in that order; the
-    // loads of eight terms are issued before their adds
-    const int B = blockDim.x;
-    for (int j0 = tid; j0 < a.n_epart; j0 += 8 * B) {
-        double2 e[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int j = j0 + u * B;
-            e[u] = j < a.n_epart ? epart[a.e_off + j] : make_double2(0.0, 0.0);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            if (j0 + u * B < a.n_epart) {
-                un += e[u].x;
-                uw += e[u].y;
-            }
-        }
+    int lo, hi;
+    chunk(a.n_epart, lo, hi);
+    for (int j = lo + tid; j < hi; j += kFinThreads) {
+        const double2 e = epart[a.e_off + j];
+        un += e.x;
+        uw += e.y;
     }
-    for (int j = tid; j < bv.P; j += blockDim.x) {
+    chunk(bv.P, lo, hi);
+    for (int j = lo + tid; j < hi; j += kFinThreads) {
         const double2 r = rho[(int64_t)sy * bv.P + j];
         r2 += r.x * r.x + r.y * r.y;
     }
-    if (with_kinetic)
-        for (int j0 = tid; j0 < a.n_kpart; j0 += 8 * B) {
-            double k8[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = j0 + u * B;
-                k8[u] = j < a.n_kpart ? kpart[a.kp_off + j] : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (j0 + u * B < a.n_kpart) ke += k8[u];
-        }
+    if (with_kinetic) {
+        chunk(a.n_kpart, lo, hi);
+        for (int j = lo + tid; j < hi; j += kFinThreads) ke += kpart[a.kp_off + j];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         un += __shfl_down_sync(0xffffffffu, un, o);
@@ -150,30 +154,44 @@ __global__ void __launch_bounds__(1024) k_finalize(BatchView bv, const double2 *
     __syncthreads();
     if (tid == 0) {
         double t[4] = {0, 0, 0, 0};
-        const int nw = blockDim.x / 32;
         for (int q = 0; q < 4; ++q)
-            for (int w = 0; w < nw; ++w) t[q] += s_red[q][w];
-        double *en = energy + (int64_t)sy * kNumEnergy;
-        en[0] = t[0];
-        en[1] = a.half_coef_U * t[2];
-        en[2] = a.U_self;
-        en[3] = t[1];
-        if (with_kinetic) {
-            double K = t[3];
-            double T = 2.0 * K / (3.0 * (double)a.n - 3.0);
-            double lam = 1.0;
-            if (a.tau > 0.0 && T > 0.0) {
-                lam = sqrt(1.0 + a.dt / a.tau * (a.T0 / T - 1.0));
-                K *= lam * lam;
-                T *= lam * lam;
-            }
-            en[4] = K;
-            en[5] = T;
-            en[6] = lam;
-            bv.step[sy] += 1;
-        }
-        bv.cursor[sy] += advance;
+            for (int w = 0; w < kFinThreads / 32; ++w) t[q] += s_red[q][w];
+        bv.fin_part[sy * kFinChunks + c] = make_double4_32a(t[0], t[1], t[2], t[3]);
+        __threadfence();   // the chunk sum is visible before the count says so
+        s_last = atomicAdd(&bv.fin_count[sy], 1u) == kFinChunks - 1;
     }
+    __syncthreads();
+    if (!s_last || tid != 0) return;
+    __threadfence();
+    double t[4] = {0, 0, 0, 0};
+    for (int q = 0; q < kFinChunks; ++q) {
+        const double *v = reinterpret_cast<const double *>(bv.fin_part + sy * kFinChunks + q);
+        t[0] += __ldcg(v);        // L2: written by other blocks of this launch
+        t[1] += __ldcg(v + 1);
+        t[2] += __ldcg(v + 2);
+        t[3] += __ldcg(v + 3);
+    }
+    bv.fin_count[sy] = 0;   // ready for the next launch
+    double *en = energy + (int64_t)sy * kNumEnergy;
+    en[0] = t[0];
+    en[1] = a.half_coef_U * t[2];
+    en[2] = a.U_self;
+    en[3] = t[1];
+    if (with_kinetic) {
+        double K = t[3];
+        double T = 2.0 * K / (3.0 * (double)a.n - 3.0);
+        double lam = 1.0;
+        if (a.tau > 0.0 && T > 0.0) {
+            lam = sqrt(1.0 + a.dt / a.tau * (a.T0 / T - 1.0));
+            K *= lam * lam;
+            T *= lam * lam;
+        }
+        en[4] = K;
+        en[5] = T;
+        en[6] = lam;
+        bv.step[sy] += 1;
+    }
+    bv.cursor[sy] += advance;
 }
 
 __global__ void __launch_bounds__(kThreads) k_rescale(BatchView bv, double4_32a *__restrict__ vel,
@@ -258,7 +276,8 @@ cudaError_t launch_kick(const BatchView &bv, double4_32a *vel, const double4_32a
 cudaError_t launch_finalize(const BatchView &bv, const double2 *epart, const double2 *rho, const double *kpart,
                             int with_kinetic, double *energy, int64_t advance, cudaStream_t st, const Prof *prof) {
     ProfScope ps(prof, "finalize");
-    k_finalize<<<bv.n_sys, 1024, 0, st>>>(bv, epart, rho, kpart, with_kinetic, energy, advance);
+    k_finalize<<<bv.n_sys * kFinChunks, kFinThreads, 0, st>>>(bv, epart, rho, kpart, with_kinetic, energy,
+                                                               advance);
     return cudaGetLastError();
 }
 

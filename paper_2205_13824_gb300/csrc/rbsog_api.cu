@@ -109,6 +109,8 @@ struct rbsog_ctx {
     int2 *d_pblk = nullptr, *d_nblk = nullptr, *d_sblk = nullptr;
     int32_t *d_cell_sys = nullptr;
     int32_t *d_mask = nullptr;        // [n_sys] systems that need a force evaluation
+    double4_32a *fin_part = nullptr;  // [n_sys * kFinChunks] finalize chunk sums
+    unsigned int *fin_count = nullptr;   // [n_sys] finalize chunks done
     // per-system step budgets (used by the serving engine): a system whose
     // budget reaches 0 is frozen by every step kernel
     bool use_budget = false;
@@ -521,6 +523,8 @@ BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
     v.remaining = c->use_budget ? c->d_remaining : nullptr;
     v.list_cap = c->use_list ? c->list_cap : 0;
     v.precision = c->precision;
+    v.fin_part = c->fin_part;
+    v.fin_count = c->fin_count;
     v.lpos = c->use_list ? c->lpos : nullptr;
     v.linv = c->use_list ? c->linv : nullptr;
     return v;
@@ -838,7 +842,10 @@ rbsog_status rbsog_batch_create(rbsog_batch **out, int32_t n_sys, const int64_t 
               dalloc(&ctx->step_ctr, n_sys) == cudaSuccess &&
               dalloc(&ctx->energy, (size_t)kNumEnergy * n_sys) == cudaSuccess &&
               dalloc(&ctx->err_flag, 1) == cudaSuccess && dalloc(&ctx->d_desc, n_sys) == cudaSuccess &&
-              dalloc(&ctx->d_mask, n_sys) == cudaSuccess;
+              dalloc(&ctx->d_mask, n_sys) == cudaSuccess &&
+              dalloc(&ctx->fin_part, (size_t)n_sys * kFinChunks) == cudaSuccess &&
+              dalloc(&ctx->fin_count, n_sys) == cudaSuccess &&
+              cudaMemset(ctx->fin_count, 0, sizeof(unsigned int) * n_sys) == cudaSuccess;
     if (!ok) return bail(RBSOG_ENOMEM);
     if (cudaMallocHost((void **)&ctx->h_energy, sizeof(double) * kNumEnergy) != cudaSuccess ||
         cudaMallocHost((void **)&ctx->h_err, sizeof(int32_t)) != cudaSuccess ||
@@ -1027,6 +1034,8 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         d.dt = q.dt;
         d.mass = q.mass;
         d.inv_mass = 1.0 / q.mass;
+        d.half_dt_inv_mass = 0.5 * q.dt * d.inv_mass;
+        d.half_mass_f = (float)(0.5 * q.mass);
         d.T0 = q.T_target;
         d.tau = q.tau_T;
         ctx->chain_len[s] = q.chain_len > 0 ? q.chain_len : 256;
@@ -1805,6 +1814,8 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->d_sblk);
     dfree(&ctx->d_cell_sys);
     dfree(&ctx->d_mask);
+    dfree(&ctx->fin_part);
+    dfree(&ctx->fin_count);
     dfree(&ctx->d_remaining);
     if (ctx->h_energy) cudaFreeHost(ctx->h_energy);
     if (ctx->h_err) cudaFreeHost(ctx->h_err);

@@ -131,6 +131,8 @@ struct SysDesc {
     double half_coef_U;        // lB pi^{3/2} S / (2 P V)
     double U_self;
     double dt, inv_mass, mass, T0, tau;
+    double half_dt_inv_mass;   // dt / (2 m): the half kick's factor
+    float half_mass_f;         // m / 2 (FP32C kinetic-energy terms)
 };
 
 // Work tables map a launch's blocks to (system, local block).
@@ -161,7 +163,10 @@ struct BatchView {
     uint4 *lpos;               // [n_total] fixed-point positions in the cell order of the
                                // last list build (neighbour-list path; null otherwise)
     int32_t *linv;             // [n_total] cell-order slot of caller particle i at that build
+    double4_32a *fin_part;     // [n_sys * kFinChunks] finalize: per-chunk energy sums
+    unsigned int *fin_count;   // [n_sys] finalize: chunks done (reset by the last one)
 };
+constexpr int kFinChunks = 16;    // blocks per system in the finalize reduction
 constexpr int kParticleBlock = 256;
 
 // X = trunc(x * (2^32 / L)) clamped to [0, 2^32 - 1]: the fixed-point
@@ -290,9 +295,11 @@ cudaError_t launch_kick_drift(const BatchView &bv, double4_32a *posq, double4_32
                               uint4 *sp32c = nullptr, const uint4 *xref = nullptr, int32_t *rebuild = nullptr);
 cudaError_t launch_kick(const BatchView &bv, double4_32a *vel, const double4_32a *force, double *kpart,
                         cudaStream_t st, const Prof *prof);
-// One block per system: sums energy partials in fixed order, U_far from rho,
-// T and the Berendsen factor; advances each cursor by `advance` and, with
-// kinetic terms, each step counter by one.
+// kFinChunks blocks per system sum chunks of the energy partials, |rho|^2
+// and kinetic partials in fixed order; the last block of a system to finish
+// adds the chunk sums in chunk order and writes the energies, T and the
+// Berendsen factor, and advances the cursor by `advance` and, with kinetic
+// terms, the step counter by one.
 cudaError_t launch_finalize(const BatchView &bv, const double2 *epart, const double2 *rho, const double *kpart,
                             int with_kinetic, double *energy, int64_t advance, cudaStream_t st,
                             const Prof *prof);
