@@ -486,3 +486,32 @@ def test_step_io_equals_the_composed_calls(prec, nsteps, with_f, where):
     with pytest.raises(B.RBSOGError):
         B.rbsog_step_io(g.ctx, buf(q), xb, vb, fb, 12, 0, 1, xb, vb, fb)  # no k-set left
     g.close()
+
+
+def test_fp32c_lists_need_an_accurate_combined_table():
+    """The list path takes G and F from one combined table.  An SOG set whose
+    narrowest Gaussian is narrow against the table step (sigma = 0.3) makes
+    that table inaccurate, so such a set runs on the cell stencil (which
+    falls back to exp + Taylor sums by its own check) and still matches the
+    oracle; the production set runs on lists.  The cell grid tells which:
+    side r_c + skin with lists, r_c without."""
+    _dev()
+    B = _lib().binding
+    N, L, P = 4998, 21.5, 64
+    q, x, v = I.electrolyte(N, L, seed=13)
+    narrow = O.SOG(B_PROD, 0.3, 1.0, M_PROD)
+    narrow = O.SOG(B_PROD, 0.3, narrow.omega_bsa0, M_PROD)
+    for sog, nc in ((prod_sog(O), math.floor(L / 3.3)), (narrow, math.floor(L / 3.0))):
+        g, _ = make(N, L, P, prec="fp32c", n_ksets=2, seed=3, sog=sog)
+        g.set_state(*to_dev(q, x, v))
+        info, _, _ = g.info()
+        assert tuple(info.ncell) == (nc,) * 3
+        m = O.kseq(sog, (L,) * 3, seed=7, n_chains=1, chain_len=P)[:P]
+        import torch
+        f = torch.zeros((N, 3), dtype=torch.float64, device="cuda:0")
+        B.rbsog_compute_forces(g.ctx, m, f)
+        s = osys(L, sog)
+        fo, _ = O.forces(s, q, O.wrap(x, s.L), S=s.S(), m=m)
+        err = np.linalg.norm(f.cpu().numpy() - fo) / np.linalg.norm(fo)
+        assert err < 1e-4, (sog.sigma, err)
+        g.close()
