@@ -105,6 +105,8 @@ def lib():
             L.orc_forces_sample.restype = C.c_int
             L.orc_self_energy.argtypes = [_i64, _pd, C.POINTER(OrcSys)]
             L.orc_self_energy.restype = _d
+            L.orc_boundary.argtypes = [_i64, _pd, _pd, _pd, _d, _i32, _pd]
+            L.orc_boundary.restype = _d
             L.orc_forces.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _pd,
                                      C.POINTER(OrcEnergies)]
             L.orc_forces.restype = C.c_int
@@ -315,6 +317,16 @@ def forces_sample(sys_: System, q, x, S, m, idx):
 def self_energy(sys_: System, q):
     q = _f64(q)
     return lib().orc_self_energy(q.shape[0], _p(q), C.byref(sys_.c))
+
+
+def boundary(q, x, L, kind: int, lB: float = 1.0):
+    """Zero-frequency term (Sec. 3.2): kind 1 spherical (Eq. 3.14), 2
+    planar along z (Eq. 3.15), 0 tinfoil.  Returns (U0, force [n, 3])."""
+    q, x = _f64(q), _f64(x)
+    Lv = _f64(np.broadcast_to(np.asarray(L, float), (3,)).copy())
+    f = np.zeros_like(x)
+    U = lib().orc_boundary(q.shape[0], _p(q), _p(x), _p(Lv), float(lB), int(kind), _p(f))
+    return U, f
 
 
 def forces(sys_: System, q, x, S=0.0, m=None):

@@ -741,6 +741,34 @@ double orc_self_energy(int64_t n, const double *q, const orc_sys *sys) {
     return sys->lB * 0.5 * w * q2;
 }
 
+/* Zero-frequency term: the k -> 0 limit of the far field for a neutral
+ * system, U0 = -(pi/V) sum_{i,j} q_i q_j lim (k.r_ij)^2 / k^2 (Eq. 3.13),
+ * averaged over directions (spherical boundary, Eq. 3.14) or taken along z
+ * (planar boundary, Eq. 3.15); both reduce to the dipole moment
+ * M = sum_i q_i r_i.  The force is -grad U0: -(4 pi / 3V) q_i M and
+ * -(4 pi / V) q_i M_z e_z. */
+double orc_boundary(int64_t n, const double *q, const double *x, const double L[3], double lB, int32_t kind,
+                    double *f) {
+    if (kind != 1 && kind != 2) return 0.0;
+    const double V = L[0] * L[1] * L[2];
+    double M[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d) M[d] += q[i] * x[3 * i + d];
+    double U, c[3];
+    if (kind == 1) {
+        U = 2.0 * M_PI / (3.0 * V) * (M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
+        for (int d = 0; d < 3; ++d) c[d] = -4.0 * M_PI / (3.0 * V) * M[d];
+    } else {
+        U = 2.0 * M_PI / V * M[2] * M[2];
+        c[0] = c[1] = 0.0;
+        c[2] = -4.0 * M_PI / V * M[2];
+    }
+    if (f)
+        for (int64_t i = 0; i < n; ++i)
+            for (int d = 0; d < 3; ++d) f[3 * i + d] += lB * q[i] * c[d];
+    return lB * U;
+}
+
 /* Total force F = F_N + F_F (+ WCA) at wrapped positions x.  P > 0: the
  * random-batch far field on the P vectors m; P == 0: the exact far sum.
  * Total potential energy U_near + U_far - U_self + U_wca. */

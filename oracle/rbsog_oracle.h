@@ -83,6 +83,13 @@ void orc_rho(int64_t n, const double *q, const double *x, const double L[3],
 void orc_far_rb(int64_t n, const double *q, const double *x, const orc_sys *sys,
                 double S, int32_t P, const int32_t *m, double *f, double *U_rb, double *rho);
 double orc_self_energy(int64_t n, const double *q, const orc_sys *sys);
+/* Zero-frequency (boundary) term of the far field (Sec. 3.2, "Analysis of
+ * the zero-frequency mode"): kind 0 tinfoil (nothing), 1 spherical infinite
+ * boundary U0 = (2 pi / 3V) |M|^2 (Eq. 3.14), 2 planar infinite boundary
+ * along z U0 = (2 pi / V) M_z^2 (Eq. 3.15), with M = sum_i q_i r_i over the given positions,
+ * times lB.  Adds -dU0/dr_i to f when f is not NULL; returns U0. */
+double orc_boundary(int64_t n, const double *q, const double *x, const double L[3], double lB, int32_t kind,
+                    double *f);
 int orc_forces_sample(int64_t n, const double *q, const double *x, const orc_sys *sys, double S,
                       int32_t P, const int32_t *m, int64_t ns, const int64_t *idx, double *f);
 

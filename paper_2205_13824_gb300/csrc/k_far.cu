@@ -35,7 +35,6 @@
 namespace rbsog {
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
 constexpr int kSweepThreads = 256;          // 8 warps
 constexpr int kKTile = 32;                  // frequencies per sweep block (FP64)
 constexpr int kKTile32 = 64;                // frequencies per sweep block (FP32C), two per lane
@@ -219,8 +218,8 @@ __global__ void __launch_bounds__(kCombineThreads) k_rho_combine(BatchView bv, c
         }
         rho[gk] = make_double2(re, im);
         const int4 m = load_m(bv, d, sy, k);
-        const double kx = 2.0 * kPi * m.x / d.box.L[0], ky = 2.0 * kPi * m.y / d.box.L[1],
-                     kz = 2.0 * kPi * m.z / d.box.L[2];
+        // 2 pi / L from the host: FP64 divisions are slow on this GPU
+        const double kx = d.box.kfac[0] * m.x, ky = d.box.kfac[1] * m.y, kz = d.box.kfac[2] * m.z;
         const double coef = d.coef;
         if (PREC == 1) {
             KEntry32 e;

@@ -955,6 +955,7 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
             b.fix_inv[d] = 4294967296.0 / q.L[d];
             b.cell_fix[d] = (float)(4294967296.0 / (double)b.nc[d]);
             b.inv_h[d] = (double)b.nc[d] / q.L[d];
+            b.kfac[d] = 2.0 * kPi / q.L[d];
             b.h_f[d] = (float)b.h[d];
         }
         if (ncell > (int64_t)INT32_MAX / 4) return fail(ctx, RBSOG_EINVAL, "system %d: cell grid too large", s);

@@ -63,6 +63,7 @@ struct BoxDev {
     float L_f[3];
     float fix_scale[3];   // L_d / 2^32: fixed-point unit of the FP32C positions
     double fix_inv[3];    // 2^32 / L_d: X_d = trunc(x_d * fix_inv[d]), clamped to [0, 2^32 - 1]
+    double kfac[3];       // 2 pi / L_d: k_d = kfac[d] m_d
     float cell_fix[3];    // 2^32 / nc_d: fixed-point length of one cell side
     float rl2_f;          // neighbour lists: (r_c + skin)^2, with a margin above FP32 rounding
     float disp2_f;        // neighbour lists: (skin / 2)^2, with a margin below it
