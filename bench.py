@@ -387,6 +387,28 @@ def run_extras(args, q, x, v, dev):
         sweep[str(Ps)] = {"value": N / (ms_s / 1e3), "ms_per_step": ms_s}
         g.close()
     out["fp32c_P_sweep"] = sweep
+    # the zero-frequency term of a spherical or planar boundary (Sec. 3.2) on
+    # the same workload: step time with it, and its own kernels' time
+    bnd = {}
+    for kind, name in ((1, "spherical"), (2, "planar")):
+        g = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=args.steps + 8, seed=19, precision="fp32c", boundary=kind),
+                     device=dev.index)
+        g.set_state(tq, tx, tv)
+        g.step(2)
+        torch.cuda.synchronize()
+        e0.record(st)
+        g.step(args.steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_b = e0.elapsed_time(e1) / args.steps
+        B.rbsog_set_profiling(g.ctx, True)
+        g.step(3)
+        torch.cuda.synchronize()
+        prof_b = B.rbsog_get_profile(g.ctx)
+        bnd[name] = {"value": N / (ms_b / 1e3), "ms_per_step": ms_b,
+                     "boundary_kernels_ms": prof_b["boundary"][1] / prof_b["boundary"][0]}
+        g.close()
+    out["fp32c_boundary_terms"] = bnd
     out["batched_replicas"] = run_replicas(args, dev)
     out["serving"] = run_serving(dev)
     return out

@@ -79,6 +79,11 @@ typedef struct {
                                  per force evaluation; >= 1                                   */
     int32_t chain_len;        /* samples per Metropolis-Hastings chain; 0: 256                  */
     int32_t precision;        /* rbsog_precision                                               */
+    int32_t boundary;         /* zero-frequency term (Sec. 3.2): 0 tinfoil (no term);
+                                 1 spherical infinite boundary, U0 = (2 pi / 3V) |M|^2
+                                 (Eq. 3.14); 2 planar infinite boundary along z,
+                                 U0 = (2 pi / V) M_z^2 (Eq. 3.15); M = sum_i q_i r_i over the
+                                 positions folded into [0, L); times coulomb_prefactor       */
 } rbsog_params;
 
 /* Energies of the last force evaluation (Eqs. 3.1, 3.6-3.8) and kinetic state. */
@@ -89,6 +94,7 @@ typedef struct {
     double U_wca;  /* soft repulsion                                                      */
     double K;      /* kinetic energy after the last completed step                        */
     double T;      /* 2K / (3N - 3)                                                       */
+    double U_bound; /* zero-frequency (boundary) term; 0 for tinfoil                      */
 } rbsog_energies;
 
 /* Solved SOG decomposition (Eqs. 2.8-2.11) and the normaliser S (Eq. 3.16). */

@@ -45,12 +45,13 @@ class rbsog_params(C.Structure):
                 ("coulomb_prefactor", C.c_double), ("wca_sigma", C.c_double),
                 ("wca_eps", C.c_double), ("dt", C.c_double), ("mass", C.c_double),
                 ("T_target", C.c_double), ("tau_T", C.c_double), ("seed", C.c_uint64),
-                ("n_ksets", C.c_int64), ("chain_len", C.c_int32), ("precision", C.c_int32)]
+                ("n_ksets", C.c_int64), ("chain_len", C.c_int32), ("precision", C.c_int32),
+                ("boundary", C.c_int32)]
 
 
 class rbsog_energies(C.Structure):
     _fields_ = [("U_near", C.c_double), ("U_far", C.c_double), ("U_self", C.c_double),
-                ("U_wca", C.c_double), ("K", C.c_double), ("T", C.c_double)]
+                ("U_wca", C.c_double), ("K", C.c_double), ("T", C.c_double), ("U_bound", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

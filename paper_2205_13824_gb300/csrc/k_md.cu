@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BatchView bv, const do
     }
     bv.fin_count[sy] = 0;   // ready for the next launch
     double *en = energy + (int64_t)sy * kNumEnergy;
+    if (a.boundary == 0) en[7] = 0.0;   // boundary term: written by its own kernel when on
     en[0] = t[0];
     en[1] = a.half_coef_U * t[2];
     en[2] = a.U_self;

@@ -110,6 +110,9 @@ struct rbsog_ctx {
     int32_t *d_cell_sys = nullptr;
     int32_t *d_mask = nullptr;        // [n_sys] systems that need a force evaluation
     double4_32a *fin_part = nullptr;  // [n_sys * kFinChunks] finalize chunk sums
+    double4_32a *dpart = nullptr;     // [particle blocks] dipole-moment partials (boundary terms)
+    double4_32a *dip = nullptr;       // [n_sys] boundary force factor per unit charge
+    bool any_boundary = false;        // some system has a non-tinfoil boundary
     unsigned int *fin_count = nullptr;   // [n_sys] finalize chunks done
     // per-system step budgets (used by the serving engine): a system whose
     // budget reaches 0 is frozen by every step kernel
@@ -586,6 +589,9 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
         CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
         CK(launch_far_scatter(prec, bv, ctx->sp64, ctx->sp32c, ctx->ktab, ctx->fnear, nullptr,
                               force_out ? force_out : ctx->force, ctx->err_flag, ctx->st, pf, ctx->epart));
+        if (ctx->any_boundary)
+            CK(launch_boundary(bv, ctx->posq, ctx->dpart, ctx->dip, ctx->energy, force_out ? force_out : ctx->force,
+                               ctx->st, pf));
         return RBSOG_OK;
     }
     CK(launch_build_cells(bv, ctx->posq, ctx->cb, prec, ctx->sp64, ctx->sp32, ctx->st, pf));
@@ -595,6 +601,9 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
     CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
     CK(launch_far_scatter(prec, bv, ctx->sp64, ctx->sp32, ctx->ktab, ctx->fnear, ctx->cb.perm,
                           force_out ? force_out : ctx->force, ctx->err_flag, ctx->st, pf));
+    if (ctx->any_boundary)
+        CK(launch_boundary(bv, ctx->posq, ctx->dpart, ctx->dip, ctx->energy, force_out ? force_out : ctx->force,
+                           ctx->st, pf));
     return RBSOG_OK;
 }
 
@@ -844,6 +853,7 @@ rbsog_status rbsog_batch_create(rbsog_batch **out, int32_t n_sys, const int64_t 
               dalloc(&ctx->err_flag, 1) == cudaSuccess && dalloc(&ctx->d_desc, n_sys) == cudaSuccess &&
               dalloc(&ctx->d_mask, n_sys) == cudaSuccess &&
               dalloc(&ctx->fin_part, (size_t)n_sys * kFinChunks) == cudaSuccess &&
+              dalloc(&ctx->dip, n_sys) == cudaSuccess &&
               dalloc(&ctx->fin_count, n_sys) == cudaSuccess &&
               cudaMemset(ctx->fin_count, 0, sizeof(unsigned int) * n_sys) == cudaSuccess;
     if (!ok) return bail(RBSOG_ENOMEM);
@@ -930,6 +940,8 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         if (q.n_ksets < 1) return fail(ctx, RBSOG_EINVAL, "system %d: n_ksets must be >= 1", s);
         if (!(q.r_c > 0.0)) return fail(ctx, RBSOG_EINVAL, "system %d: r_c must be > 0", s);
         if (!(q.mass > 0.0)) return fail(ctx, RBSOG_EINVAL, "system %d: mass must be > 0", s);
+        if (q.boundary < 0 || q.boundary > 2)
+            return fail(ctx, RBSOG_EINVAL, "system %d: boundary must be 0 (tinfoil), 1 (spherical) or 2 (planar)", s);
         if (q.precision != RBSOG_FP64 && q.precision != RBSOG_FP32C)
             return fail(ctx, RBSOG_EINVAL, "system %d: unknown precision %d", s, q.precision);
         if (q.chain_len < 0) return fail(ctx, RBSOG_EINVAL, "system %d: chain_len must be >= 0", s);
@@ -990,6 +1002,8 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
 
     drop_graph(ctx);
     ctx->p = p;
+    ctx->any_boundary = false;
+    for (auto &pp : p) ctx->any_boundary = ctx->any_boundary || pp.boundary != 0;
     ctx->omega = w;
     ctx->s = sv;
     ctx->sigma = sigma;
@@ -1036,6 +1050,7 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         d.mass = q.mass;
         d.inv_mass = 1.0 / q.mass;
         d.half_dt_inv_mass = 0.5 * q.dt * d.inv_mass;
+        d.boundary = q.boundary;
         d.half_mass_f = (float)(0.5 * q.mass);
         d.T0 = q.T_target;
         d.tau = q.tau_T;
@@ -1057,6 +1072,7 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
     CK(dalloc(&ctx->rho, (size_t)ns * ctx->P));
     CK(dalloc((unsigned char **)&ctx->ktab, ktab_bytes(ctx->precision, (int64_t)ns * ctx->P)));
     CK(dalloc(&ctx->kpart, (size_t)kp_off));
+    CK(dalloc(&ctx->dpart, (size_t)kp_off));
     CK(dalloc(&ctx->cb.count, (size_t)c_off));
     CK(dalloc(&ctx->cb.start, (size_t)c_off + 1));
     CK(dalloc(&ctx->cb.tile_sum, (size_t)cell_scan_tiles(c_off)));
@@ -1345,6 +1361,7 @@ rbsog_status rbsog_compute_forces(rbsog_ctx *ctx, const int32_t *m_kset, double 
         e_out->U_wca = ctx->h_energy[3];
         e_out->K = ctx->h_energy[4];
         e_out->T = ctx->h_energy[5];
+        e_out->U_bound = ctx->h_energy[7];
     }
     return leave(ctx);
 }
@@ -1585,6 +1602,7 @@ rbsog_status rbsog_batch_get_energies(rbsog_batch *ctx, int32_t sys, rbsog_energ
     e->U_far = ctx->h_energy[1];
     e->U_self = ctx->h_energy[2];
     e->U_wca = ctx->h_energy[3];
+    e->U_bound = ctx->h_energy[7];
     e->K = ctx->h_energy[4];
     e->T = ctx->h_energy[5];
     return leave(ctx);
@@ -1816,6 +1834,8 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->d_cell_sys);
     dfree(&ctx->d_mask);
     dfree(&ctx->fin_part);
+    dfree(&ctx->dpart);
+    dfree(&ctx->dip);
     dfree(&ctx->fin_count);
     dfree(&ctx->d_remaining);
     if (ctx->h_energy) cudaFreeHost(ctx->h_energy);

@@ -133,6 +133,7 @@ struct SysDesc {
     double U_self;
     double dt, inv_mass, mass, T0, tau;
     double half_dt_inv_mass;   // dt / (2 m): the half kick's factor
+    int32_t boundary;          // zero-frequency term: 0 tinfoil, 1 spherical, 2 planar (z)
     float half_mass_f;         // m / 2 (FP32C kinetic-energy terms)
 };
 
@@ -304,6 +305,12 @@ cudaError_t launch_kick(const BatchView &bv, double4_32a *vel, const double4_32a
 cudaError_t launch_finalize(const BatchView &bv, const double2 *epart, const double2 *rho, const double *kpart,
                             int with_kinetic, double *energy, int64_t advance, cudaStream_t st,
                             const Prof *prof);
+// ---- boundary terms (k_boundary.cu) ---------------------------------------------
+// Zero-frequency term of systems with a non-tinfoil boundary: dipole moment
+// from the caller-order positions, U0 into energy[sys * kNumEnergy + 7], the
+// force term added to the caller-order total force.
+cudaError_t launch_boundary(const BatchView &bv, const double4_32a *posq, double4_32a *dpart, double4_32a *dip,
+                            double *energy, double4_32a *force, cudaStream_t st, const Prof *prof);
 cudaError_t launch_rescale(const BatchView &bv, double4_32a *vel, const double *energy, cudaStream_t st,
                            const Prof *prof);
 // With step budgets: one step of every unfrozen system is done.

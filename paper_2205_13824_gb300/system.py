@@ -14,7 +14,7 @@ DEFAULT_M = 36
 
 def make_params(L, P, r_c=3.0, b=DEFAULT_B, sigma=0.0, omega0=0.0, M=DEFAULT_M, lB=1.0,
                 wca_sigma=1.0, wca_eps=1.0, dt=0.001, mass=1.0, T_target=1.0, tau_T=0.0,
-                seed=1, n_ksets=1, chain_len=0, precision="fp64") -> B.rbsog_params:
+                seed=1, n_ksets=1, chain_len=0, precision="fp64", boundary=0) -> B.rbsog_params:
     if isinstance(L, (int, float)):
         L = (float(L),) * 3
     p = B.rbsog_params()
@@ -27,6 +27,8 @@ def make_params(L, P, r_c=3.0, b=DEFAULT_B, sigma=0.0, omega0=0.0, M=DEFAULT_M, 
     p.seed, p.n_ksets, p.chain_len = int(seed), int(n_ksets), int(chain_len)
     p.precision = {"fp64": B.RBSOG_FP64, "fp32c": B.RBSOG_FP32C}[precision] \
         if isinstance(precision, str) else int(precision)
+    p.boundary = {"tinfoil": 0, "spherical": 1, "planar": 2}[boundary] \
+        if isinstance(boundary, str) else int(boundary)
     return p
 
 
