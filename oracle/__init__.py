@@ -38,6 +38,10 @@ class OrcSys(C.Structure):
                 ("lB", _d), ("wca_sigma", _d), ("wca_eps", _d)]
 
 
+class OrcCoreShell(C.Structure):
+    _fields_ = [("r_in", _d), ("Q", _i32), ("b_exp", _i32), ("b_man", _i32)]
+
+
 class OrcEnergies(C.Structure):
     _fields_ = [("U_near", _d), ("U_far", _d), ("U_self", _d), ("U_wca", _d), ("K", _d), ("T", _d)]
 
@@ -105,6 +109,12 @@ def lib():
             L.orc_forces_sample.restype = C.c_int
             L.orc_self_energy.argtypes = [_i64, _pd, C.POINTER(OrcSys)]
             L.orc_self_energy.restype = _d
+            L.orc_coreshell_eval.argtypes = [C.POINTER(OrcSys), C.POINTER(OrcCoreShell), _d, C.POINTER(_d),
+                                             C.POINTER(_d)]
+            L.orc_coreshell_eval.restype = C.c_int
+            L.orc_near_coreshell.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), C.POINTER(OrcCoreShell), _pd,
+                                             C.POINTER(_d), C.POINTER(_d)]
+            L.orc_near_coreshell.restype = C.c_int
             L.orc_boundary.argtypes = [_i64, _pd, _pd, _pd, _d, _i32, _pd]
             L.orc_boundary.restype = _d
             L.orc_forces.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _pd,
@@ -276,6 +286,30 @@ def near(sys_: System, q, x, method="cells"):
                                 C.byref(uw), _p(nbr, _pi32)) != 0:
             raise ValueError("fewer than 3 cells per side")
     return f, un.value, uw.value, nbr
+
+
+def coreshell(r_in: float, Q: int = 10, b_exp: int = 2, b_man: int = 8) -> OrcCoreShell:
+    """Parameters of the core-shell near-field kernel (Sec. 3.4)."""
+    return OrcCoreShell(float(r_in), int(Q), int(b_exp), int(b_man))
+
+
+def coreshell_eval(sys_: System, cs: OrcCoreShell, r2: float):
+    """(g, n): the scheme's force factor and pair energy kernel at r^2."""
+    g, n = _d(), _d()
+    if lib().orc_coreshell_eval(C.byref(sys_.c), C.byref(cs), float(r2), C.byref(g), C.byref(n)) != 0:
+        raise ValueError("r^2 outside [0, r_c^2) or the table does not reach r_c^2")
+    return g.value, n.value
+
+
+def near_coreshell(sys_: System, q, x, cs: OrcCoreShell):
+    """Near field (+ WCA) with the core-shell kernel: (f, U_near, U_wca)."""
+    q, x = _f64(q), _f64(x)
+    f = np.zeros_like(x)
+    un, uw = _d(), _d()
+    if lib().orc_near_coreshell(x.shape[0], _p(q), _p(x), C.byref(sys_.c), C.byref(cs), _p(f), C.byref(un),
+                                C.byref(uw)) != 0:
+        raise ValueError("the core-shell table does not reach r_c^2")
+    return f, un.value, uw.value
 
 
 def far_exact(sys_: System, q, x, tol=1e-16):

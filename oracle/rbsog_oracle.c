@@ -741,6 +741,135 @@ double orc_self_energy(int64_t n, const double *q, const orc_sys *sys) {
     return sys->lB * 0.5 * w * q2;
 }
 
+/* ---- core-shell near-field kernel (Sec. 3.4) ------------------------------
+ * Core, r < r_in (Eqs. 3.25-3.26): with u = r^2,
+ *   sum_l w_l/s_l^2 e^{-u/s_l^2} = sum_{i=1}^{Q} (-1)^{i-1} A_i u^{i-1},
+ *   A_i = sum_l w_l / ((i-1)! s_l^{2i}),
+ * and F_M(u) = sum_{i=0}^{Q} (-1)^i B_i u^i, B_i = sum_l w_l / (i! s_l^{2i})
+ * (the energy's series, the same expansion).  Eq. 3.26 prints A_i without
+ * the alternating sign of the exponential's series; the series needs it.
+ * Shell, r_in <= r < r_c: the FP32 bits of u give the bin (b_exp low
+ * exponent bits, b_man high mantissa bits); each bin holds the exact kernel
+ * at its lower end and the change to its upper end, and the remaining
+ * mantissa bits give the interpolation fraction. */
+static double cs_G(const orc_sys *sys, double u) {
+    double v = 0.0;
+    for (int32_t l = 0; l <= sys->M; ++l) v += sys->omega[l] / (sys->s[l] * sys->s[l]) * exp(-u / (sys->s[l] * sys->s[l]));
+    return v;
+}
+
+static double cs_F(const orc_sys *sys, double u) {
+    double v = 0.0;
+    for (int32_t l = 0; l <= sys->M; ++l) v += sys->omega[l] * exp(-u / (sys->s[l] * sys->s[l]));
+    return v;
+}
+
+static uint32_t f32_bits(float v) {
+    uint32_t b;
+    memcpy(&b, &v, sizeof b);
+    return b;
+}
+
+/* first octave (biased FP32 exponent) of the shell table, or -1 if the
+ * table's octaves do not reach r_c^2 */
+static int cs_first_octave(const orc_sys *sys, const orc_coreshell *cs) {
+    if (cs->r_in <= 0.0 || cs->r_in >= sys->rc || cs->b_exp < 0 || cs->b_exp > 4 || cs->b_man < 0 ||
+        cs->b_man > 20 || cs->Q < 1)
+        return -1;
+    const int e0 = (int)((f32_bits((float)(cs->r_in * cs->r_in)) >> 23) & 0xffu);
+    const int e1 = (int)((f32_bits((float)(sys->rc * sys->rc)) >> 23) & 0xffu);
+    return e1 - e0 < (1 << cs->b_exp) ? e0 : -1;
+}
+
+static void cs_exact(const orc_sys *sys, double u, double *g, double *n) {
+    const double r = sqrt(u);
+    *g = 1.0 / (u * r) - 2.0 * cs_G(sys, u);
+    *n = 1.0 / r - cs_F(sys, u);
+}
+
+int orc_coreshell_eval(const orc_sys *sys, const orc_coreshell *cs, double r2, double *g, double *n) {
+    const int e0 = cs_first_octave(sys, cs);
+    if (e0 < 0 || !(r2 >= 0.0) || r2 >= sys->rc * sys->rc) return -1;
+    if (r2 < cs->r_in * cs->r_in) {
+        const double r = sqrt(r2);
+        double gs = 0.0, fs = 0.0, fact = 1.0;
+        for (int32_t i = 0; i <= cs->Q; ++i) {
+            if (i > 0) fact *= i;                       /* i! */
+            double Bi = 0.0, Ai1 = 0.0;                 /* B_i and A_{i+1} */
+            for (int32_t l = 0; l <= sys->M; ++l) {
+                const double t = pow(sys->s[l] * sys->s[l], -(double)i);
+                Bi += sys->omega[l] * t / fact;
+                Ai1 += sys->omega[l] * t / (sys->s[l] * sys->s[l]) / fact;
+            }
+            const double sg = (i % 2) ? -1.0 : 1.0;
+            const double ui = pow(r2, (double)i);
+            fs += sg * Bi * ui;
+            if (i < cs->Q) gs += sg * Ai1 * ui;         /* A_1 .. A_Q */
+        }
+        *g = 1.0 / (r2 * r) - 2.0 * gs;
+        *n = 1.0 / r - fs;
+        return 0;
+    }
+    /* shell: the bin from the FP32 bits of r^2 */
+    const uint32_t bits = f32_bits((float)r2);
+    const int E = (int)((bits >> 23) & 0xffu);
+    const uint32_t mb = (uint32_t)cs->b_man;
+    const uint32_t mant = bits & 0x7fffffu;
+    const uint32_t m = mant >> (23u - mb);
+    const uint32_t rest = mant & ((1u << (23u - mb)) - 1u);
+    const double frac = (double)rest / (double)(1u << (23u - mb));
+    const double u0 = ldexp(1.0 + (double)m / (double)(1u << mb), E - 127);
+    const double u1 = ldexp(1.0 + (double)(m + 1) / (double)(1u << mb), E - 127);
+    double g0, n0, g1, n1;
+    cs_exact(sys, u0, &g0, &n0);
+    cs_exact(sys, u1, &g1, &n1);
+    *g = g0 + frac * (g1 - g0);
+    *n = n0 + frac * (n1 - n0);
+    (void)e0;
+    return 0;
+}
+
+int orc_near_coreshell(int64_t n, const double *q, const double *x, const orc_sys *sys, const orc_coreshell *cs,
+                       double *f, double *U_near, double *U_wca) {
+    if (cs_first_octave(sys, cs) < 0) return -1;
+    double *un = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *uw = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    const double rc2 = sys->rc * sys->rc;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double fi[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            const double r2 = min_image(x + 3 * i, x + 3 * j, sys->L, d);
+            if (!(r2 < rc2)) continue;
+            double g, nn;
+            orc_coreshell_eval(sys, cs, r2, &g, &nn);
+            const double qq = sys->lB * q[i] * q[j];
+            for (int c = 0; c < 3; ++c) fi[c] += qq * g * d[c];
+            un[i] += 0.5 * qq * nn;
+            if (sys->wca_sigma > 0.0) {
+                const double rcut2 = pow(2.0, 1.0 / 3.0) * sys->wca_sigma * sys->wca_sigma;
+                if (r2 < rcut2) {
+                    const double sr2 = sys->wca_sigma * sys->wca_sigma / r2;
+                    const double sr6 = sr2 * sr2 * sr2;
+                    const double gw = 24.0 * sys->wca_eps * (2.0 * sr6 * sr6 - sr6) / r2;
+                    for (int c = 0; c < 3; ++c) fi[c] += gw * d[c];
+                    uw[i] += 0.5 * (4.0 * sys->wca_eps * (sr6 * sr6 - sr6) + sys->wca_eps);
+                }
+            }
+        }
+        for (int c = 0; c < 3; ++c) f[3 * i + c] = fi[c];
+    }
+    double a = 0.0, b = 0.0;
+    for (int64_t i = 0; i < n; ++i) { a += un[i]; b += uw[i]; }
+    *U_near = a;
+    *U_wca = b;
+    free(un);
+    free(uw);
+    return 0;
+}
+
 /* Zero-frequency term: the k -> 0 limit of the far field for a neutral
  * system, U0 = -(pi/V) sum_{i,j} q_i q_j lim (k.r_ij)^2 / k^2 (Eq. 3.13),
  * averaged over directions (spherical boundary, Eq. 3.14) or taken along z

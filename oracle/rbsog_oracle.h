@@ -35,6 +35,19 @@ typedef struct {
     double wca_eps;       /* WCA epsilon                                      */
 } orc_sys;
 
+/* Core-shell approximation of the near-field kernel (Sec. 3.4): pairs with
+ * r < r_in take the Gaussian sums from a Q-term Taylor series in r^2 (Eqs.
+ * 3.25-3.26, with 1/r and 1/r^3 exact); pairs with r_in <= r < r_c take
+ * the whole kernel from a table indexed by the b_exp low exponent bits and
+ * the b_man high mantissa bits of the FP32 value of r^2, with linear
+ * interpolation inside each bin. */
+typedef struct {
+    double r_in;          /* core radius                                      */
+    int32_t Q;            /* Taylor terms of the core                         */
+    int32_t b_exp;        /* exponent bits of the shell-table index           */
+    int32_t b_man;        /* mantissa bits of the shell-table index           */
+} orc_coreshell;
+
 /* Energies of one force evaluation; every Coulomb term already carries lB. */
 typedef struct {
     double U_near;   /* (1/2) sum_ij q_i q_j N(r_ij), r_ij < r_c              */
@@ -83,6 +96,16 @@ void orc_rho(int64_t n, const double *q, const double *x, const double L[3],
 void orc_far_rb(int64_t n, const double *q, const double *x, const orc_sys *sys,
                 double S, int32_t P, const int32_t *m, double *f, double *U_rb, double *rho);
 double orc_self_energy(int64_t n, const double *q, const orc_sys *sys);
+/* The core-shell kernel at one squared distance: g = force factor
+ * 1/r^3 - 2 sum_l w_l/s_l^2 e^{-r^2/s_l^2} and n = 1/r - F_M(r) as the
+ * scheme approximates them.  Returns -1 when r2 is outside [0, r_c^2) or the
+ * 2^b_exp octaves of the table, starting at the octave of r_in^2, do not
+ * reach r_c^2. */
+int orc_coreshell_eval(const orc_sys *sys, const orc_coreshell *cs, double r2, double *g, double *n);
+/* Near field (+ WCA, exact) with the core-shell kernel; O(N^2) pair scan.
+ * Returns -1 as orc_coreshell_eval for an uncovered table. */
+int orc_near_coreshell(int64_t n, const double *q, const double *x, const orc_sys *sys, const orc_coreshell *cs,
+                       double *f, double *U_near, double *U_wca);
 /* Zero-frequency (boundary) term of the far field (Sec. 3.2, "Analysis of
  * the zero-frequency mode"): kind 0 tinfoil (nothing), 1 spherical infinite
  * boundary U0 = (2 pi / 3V) |M|^2 (Eq. 3.14), 2 planar infinite boundary
