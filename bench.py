@@ -409,6 +409,26 @@ def run_extras(args, q, x, v, dev):
                      "boundary_kernels_ms": prof_b["boundary"][1] / prof_b["boundary"][0]}
         g.close()
     out["fp32c_boundary_terms"] = bnd
+    # the paper's core-shell near-field kernel (Sec. 3.4) in place of the
+    # combined table, r_in = r_c / 3
+    g = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=args.steps + 8, seed=19, precision="fp32c",
+                                   near_kernel="coreshell"), device=dev.index)
+    g.set_state(tq, tx, tv)
+    g.step(2)
+    torch.cuda.synchronize()
+    e0.record(st)
+    g.step(args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_c = e0.elapsed_time(e1) / args.steps
+    B.rbsog_set_profiling(g.ctx, True)
+    g.step(3)
+    torch.cuda.synchronize()
+    prof_c = B.rbsog_get_profile(g.ctx)
+    near_c = prof_c["near_fp32c_coreshell"]
+    out["fp32c_coreshell_near"] = {"value": N / (ms_c / 1e3), "ms_per_step": ms_c,
+                                   "near_ms": near_c[1] / near_c[0]}
+    g.close()
     out["batched_replicas"] = run_replicas(args, dev)
     out["serving"] = run_serving(dev)
     return out

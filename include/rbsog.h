@@ -84,6 +84,15 @@ typedef struct {
                                  (Eq. 3.14); 2 planar infinite boundary along z,
                                  U0 = (2 pi / V) M_z^2 (Eq. 3.15); M = sum_i q_i r_i over the
                                  positions folded into [0, L); times coulomb_prefactor       */
+    int32_t near_kernel;      /* FP32C neighbour-list path only: 0 the combined G/F table
+                                 (default); 1 the paper's core-shell kernel (Sec. 3.4):
+                                 pairs with r < r_in from a 10-term Taylor series of the
+                                 Gaussian sums in r^2 (Eqs. 3.25-3.26), the others from a
+                                 table indexed by the low exponent bits and 8 high mantissa
+                                 bits of the FP32 r^2, linearly interpolated.  RBSOG_EINVAL
+                                 when the system does not run on neighbour lists.            */
+    double r_in;              /* core radius of near_kernel 1; <= 0: r_c / 3; the table covers
+                                 at most 8 octaves of r^2 from r_in^2 up to r_c^2           */
 } rbsog_params;
 
 /* Energies of the last force evaluation (Eqs. 3.1, 3.6-3.8) and kinetic state. */

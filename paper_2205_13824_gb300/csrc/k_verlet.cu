@@ -238,19 +238,33 @@ __global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv
 // lane l reads copy l % 8, so the 8 lanes of each quarter warp fetch their
 // entries from 8 different bank groups whatever the entries are (one
 // shared-memory wavefront per quarter warp).
-__global__ void __launch_bounds__(kNearThreads, 5) k_near_list(const BatchView bv, const float ltab_scale,
+//
+// CORESHELL: the paper's core-shell kernel (Sec. 3.4) instead of the combined
+// table: pairs with r^2 < r_in^2 take G and F from their Taylor series in r^2
+// (Eqs. 3.25-3.26, coefficients with the series' signs in cs), 1/r and
+// 1/r^3 exact; the others take the whole kernel (force factor and pair
+// energy) from a table indexed by the low exponent bits and 8 high mantissa
+// bits of the FP32 r^2, linearly interpolated by the remaining 15 mantissa
+// bits (entries: value at the bin start and change over the bin).
+template <bool CORESHELL>
+__global__ void __launch_bounds__(kNearThreads, CORESHELL ? 4 : 5) k_near_list(const BatchView bv, const float ltab_scale,
                                                             const float ltab_h, const float4 *__restrict__ ltab,
+                                                            const __grid_constant__ CoreShellDev cs,
                                                             const int32_t *__restrict__ nbr_list,
                                                             const int32_t *__restrict__ nbr_cnt,
                                                             const int32_t *__restrict__ list_perm,
                                                             double4_32a *__restrict__ fnear) {
-    __shared__ float4 s_tab[kLTabN * kTabCopies];
+    extern __shared__ __align__(16) float4 s_tab[];
     const int2 w = bv.pblk[blockIdx.x];
     if (bv.remaining && bv.remaining[w.x] == 0) return;
     // consecutive threads fill consecutive 16-byte slots (no bank conflicts)
-    for (int t = threadIdx.x; t < kLTabN * kTabCopies; t += kNearThreads) s_tab[t] = ltab[t / kTabCopies];
+    if (CORESHELL) {
+        for (int t = threadIdx.x; t < cs.n_tab; t += kNearThreads) s_tab[t] = ltab[t];
+    } else {
+        for (int t = threadIdx.x; t < kLTabN * kTabCopies; t += kNearThreads) s_tab[t] = ltab[t / kTabCopies];
+    }
     __syncthreads();
-    const float4 *__restrict__ tab = s_tab + (threadIdx.x & (kTabCopies - 1));
+    const float4 *__restrict__ tab = CORESHELL ? s_tab : s_tab + (threadIdx.x & (kTabCopies - 1));
     const SysDesc &d = bv.sys[w.x];
     const int64_t sl = (int64_t)w.y * kParticleBlock + threadIdx.x;
     if (sl >= d.n) return;
@@ -272,17 +286,42 @@ __global__ void __launch_bounds__(kNearThreads, 5) k_near_list(const BatchView b
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         if (r2 < rc2) {
             const float qq = qi * __uint_as_float(pj.w);
-            const float x = r2 * tscale;
-            const int kt = min((int)x, kLTabN - 1);
-            const float sx = x - (float)kt;
-            const float4 e = tab[kt * kTabCopies];      // (g0, g1, g2, F at the interval start)
-            const float gs = fmaf(fmaf(e.z, sx, e.y), sx, e.x);
-            const float gi = fmaf(fmaf(e.z * (1.0f / 3.0f), sx, 0.5f * e.y), sx, e.x);   // (1/s) int_0^s G
-            const float fs = fmaf(mh * sx, gi, e.w);
-            const float inv_r = rsqrtf(r2);
-            const float inv_r2 = inv_r * inv_r;
-            float g = qq * (inv_r2 * inv_r - 2.0f * gs);
-            un += 0.5f * qq * (inv_r - fs);
+            float g, inv_r2;
+            if (CORESHELL) {
+                if (r2 < cs.rin2) {
+                    float gs = cs.a[kCsQ - 1], fs = cs.b[kCsQ];
+#pragma unroll
+                    for (int i = kCsQ - 2; i >= 0; --i) gs = fmaf(gs, r2, cs.a[i]);
+#pragma unroll
+                    for (int i = kCsQ - 1; i >= 0; --i) fs = fmaf(fs, r2, cs.b[i]);
+                    const float inv_r = rsqrtf(r2);
+                    inv_r2 = inv_r * inv_r;
+                    g = qq * (inv_r2 * inv_r - 2.0f * gs);
+                    un += 0.5f * qq * (inv_r - fs);
+                } else {
+                    const uint32_t bits = __float_as_uint(r2);
+                    const int idx = (int)((((bits >> 23) & cs.emask) << kCsManBits) |
+                                          ((bits >> (23 - kCsManBits)) & ((1u << kCsManBits) - 1u)));
+                    const float fr = (float)(bits & ((1u << (23 - kCsManBits)) - 1u)) *
+                                     (1.0f / (float)(1u << (23 - kCsManBits)));
+                    const float4 e = tab[idx];                 // (g0, dg, n0, dn) of the bin
+                    g = qq * fmaf(fr, e.y, e.x);
+                    un += 0.5f * qq * fmaf(fr, e.w, e.z);
+                    inv_r2 = r2 < wrc2 ? __frcp_rn(r2) : 0.f;
+                }
+            } else {
+                const float x = r2 * tscale;
+                const int kt = min((int)x, kLTabN - 1);
+                const float sx = x - (float)kt;
+                const float4 e = tab[kt * kTabCopies];      // (g0, g1, g2, F at the interval start)
+                const float gs = fmaf(fmaf(e.z, sx, e.y), sx, e.x);
+                const float gi = fmaf(fmaf(e.z * (1.0f / 3.0f), sx, 0.5f * e.y), sx, e.x);   // (1/s) int_0^s G
+                const float fs = fmaf(mh * sx, gi, e.w);
+                const float inv_r = rsqrtf(r2);
+                inv_r2 = inv_r * inv_r;
+                g = qq * (inv_r2 * inv_r - 2.0f * gs);
+                un += 0.5f * qq * (inv_r - fs);
+            }
             if (r2 < wrc2) {
                 // WCA from 1/r^2 (no divisions: this branch runs for some
                 // lane of most warps, so its length is paid by all lanes)
@@ -412,10 +451,20 @@ cudaError_t launch_list_move(int64_t n, int64_t old_off, int64_t new_off, int ol
 
 cudaError_t launch_near_list(const BatchView &bv, const NearSog &sog, const float4 *ltab, const int32_t *nbr_list,
                              const int32_t *nbr_cnt, const int32_t *list_perm, double4_32a *fnear, cudaStream_t st,
-                             const Prof *prof) {
+                             const Prof *prof, const CoreShellDev *cs, const float4 *cstab) {
+    if (cs) {
+        ProfScope ps(prof, "near_fp32c_coreshell");
+        const size_t sm = sizeof(float4) * (size_t)cs->n_tab;
+        cudaError_t e = cudaFuncSetAttribute(k_near_list<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_near_list<true><<<bv.n_pblk, kNearThreads, sm, st>>>(bv, 0.f, 0.f, cstab, *cs, nbr_list, nbr_cnt,
+                                                               list_perm, fnear);
+        return cudaGetLastError();
+    }
     ProfScope ps(prof, "near_fp32c");
-    k_near_list<<<bv.n_pblk, kNearThreads, 0, st>>>(bv, sog.ltab_scale, sog.ltab_h, ltab, nbr_list, nbr_cnt,
-                                                    list_perm, fnear);
+    const CoreShellDev none{};
+    k_near_list<false><<<bv.n_pblk, kNearThreads, sizeof(float4) * kLTabN * kTabCopies, st>>>(
+        bv, sog.ltab_scale, sog.ltab_h, ltab, none, nbr_list, nbr_cnt, list_perm, fnear);
     return cudaGetLastError();
 }
 

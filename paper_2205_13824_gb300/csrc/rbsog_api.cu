@@ -127,6 +127,9 @@ struct rbsog_ctx {
     uint4 *sp32c = nullptr, *xref = nullptr, *lpos = nullptr;
     int32_t *linv = nullptr;
     float4 *d_ltab = nullptr;            // combined G/F table of the list path [kLTabN]
+    bool use_cs = false;                 // the list path runs the core-shell kernel
+    CoreShellDev cs{};
+    float4 *d_cstab = nullptr;           // its shell table [cs.n_tab]
     std::vector<float4> h_ltab;
     int32_t *nbr_list = nullptr, *nbr_cnt = nullptr, *list_perm = nullptr, *d_rebuild = nullptr;
     // pinned host mirrors
@@ -489,6 +492,66 @@ double build_list_table(NearSog &ns, std::vector<float4> &tab, const std::vector
     return err;
 }
 
+// Core-shell kernel of the list path (Sec. 3.4): Taylor coefficients of the
+// core (signs of the series folded in) and the shell table over the 2^b_exp
+// octaves of r^2 from the octave of r_in^2 (b_exp the smallest of 1..3 that
+// reaches r_c^2).  Each bin holds the exact kernel (force factor
+// u^{-3/2} - 2 G(u), pair energy u^{-1/2} - F_M(u)) at its lower end and the
+// change to its upper end.  False when 8 octaves do not reach r_c^2.
+bool build_coreshell(CoreShellDev &cs, std::vector<float4> &tab, const std::vector<double> &omega,
+                     const std::vector<double> &s, int M, double rc, double r_in) {
+    auto fbits = [](float v) {
+        uint32_t b;
+        std::memcpy(&b, &v, sizeof b);
+        return b;
+    };
+    const int e0 = (int)((fbits((float)(r_in * r_in)) >> 23) & 0xffu);
+    const int e1 = (int)((fbits((float)(rc * rc)) >> 23) & 0xffu);
+    int be = 1;
+    while (be <= 3 && e1 - e0 >= (1 << be)) ++be;
+    if (be > 3) return false;
+    std::memset(&cs, 0, sizeof cs);
+    double fact = 1.0;
+    for (int i = 0; i <= kCsQ; ++i) {
+        if (i > 0) fact *= i;
+        double A = 0.0, Bc = 0.0;          // A_{i+1} and B_i
+        for (int l = 0; l <= M; ++l) {
+            const double t = std::pow(s[l] * s[l], -(double)i) / fact;
+            Bc += omega[l] * t;
+            A += omega[l] * t / (s[l] * s[l]);
+        }
+        const double sg = (i % 2) ? -1.0 : 1.0;
+        if (i < kCsQ) cs.a[i] = (float)(sg * A);
+        cs.b[i] = (float)(sg * Bc);
+    }
+    cs.rin2 = (float)(r_in * r_in);
+    cs.emask = (1u << be) - 1u;
+    cs.n_tab = 1 << (be + kCsManBits);
+    tab.assign((size_t)cs.n_tab, float4{});
+    auto kern = [&](double u, double &g, double &n) {
+        double G = 0.0, F = 0.0;
+        for (int l = M; l >= 0; --l) {
+            const double e = std::exp(-u / (s[l] * s[l]));
+            G += omega[l] / (s[l] * s[l]) * e;
+            F += omega[l] * e;
+        }
+        g = std::pow(u, -1.5) - 2.0 * G;
+        n = 1.0 / std::sqrt(u) - F;
+    };
+    const int nm = 1 << kCsManBits;
+    for (int E = e0; E < e0 + (1 << be); ++E)
+        for (int m = 0; m < nm; ++m) {
+            const double u0 = std::ldexp(1.0 + (double)m / nm, E - 127);
+            const double u1 = std::ldexp(1.0 + (double)(m + 1) / nm, E - 127);
+            double g0, n0, g1, n1;
+            kern(u0, g0, n0);
+            kern(u1, g1, n1);
+            tab[(size_t)(((uint32_t)E & cs.emask) << kCsManBits) | (size_t)m] =
+                make_float4((float)g0, (float)(g1 - g0), (float)n0, (float)(n1 - n0));
+        }
+    return true;
+}
+
 rbsog_status enter(rbsog_ctx *ctx) {
     CK(cudaSetDevice(ctx->device));
     CK(cudaEventRecord(ctx->ev_in, ctx->user));
@@ -584,7 +647,7 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
             if (rs != RBSOG_OK) return rs;
         }
         CK(launch_near_list(bv, ctx->nsog, ctx->d_ltab, ctx->nbr_list, ctx->nbr_cnt, ctx->list_perm, ctx->fnear,
-                            ctx->st, pf));
+                            ctx->st, pf, ctx->use_cs ? &ctx->cs : nullptr, ctx->d_cstab));
         CK(launch_rho_sweep(prec, bv, ctx->sp64, ctx->sp32c, ctx->rho_part, ctx->st, pf));
         CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
         CK(launch_far_scatter(prec, bv, ctx->sp64, ctx->sp32c, ctx->ktab, ctx->fnear, nullptr,
@@ -940,6 +1003,10 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         if (q.n_ksets < 1) return fail(ctx, RBSOG_EINVAL, "system %d: n_ksets must be >= 1", s);
         if (!(q.r_c > 0.0)) return fail(ctx, RBSOG_EINVAL, "system %d: r_c must be > 0", s);
         if (!(q.mass > 0.0)) return fail(ctx, RBSOG_EINVAL, "system %d: mass must be > 0", s);
+        if (q.near_kernel < 0 || q.near_kernel > 1)
+            return fail(ctx, RBSOG_EINVAL, "system %d: near_kernel must be 0 (table) or 1 (core-shell)", s);
+        if (s > 0 && (q.near_kernel != p[0].near_kernel || q.r_in != p[0].r_in))
+            return fail(ctx, RBSOG_EINVAL, "system %d: near_kernel and r_in must be the same for every system", s);
         if (q.boundary < 0 || q.boundary > 2)
             return fail(ctx, RBSOG_EINVAL, "system %d: boundary must be 0 (tinfoil), 1 (spherical) or 2 (planar)", s);
         if (q.precision != RBSOG_FP64 && q.precision != RBSOG_FP32C)
@@ -999,6 +1066,15 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
     std::vector<double> w, sv;
     bsa_coeffs(p[0].b, sigma, p[0].M, w, sv);
     w[0] = w0;
+    std::vector<float4> cstab;
+    CoreShellDev cs_new{};
+    if (p[0].near_kernel == 1) {
+        if (!lists) return fail(ctx, RBSOG_EINVAL, "the core-shell kernel runs on the FP32C neighbour-list path only");
+        const double rin = p[0].r_in > 0.0 ? p[0].r_in : p[0].r_c / 3.0;
+        if (!(rin < p[0].r_c)) return fail(ctx, RBSOG_EINVAL, "r_in must be below r_c");
+        if (!build_coreshell(cs_new, cstab, w, sv, p[0].M, p[0].r_c, rin))
+            return fail(ctx, RBSOG_EINVAL, "the core-shell table cannot reach r_c^2 from r_in^2 in 8 octaves");
+    }
 
     drop_graph(ctx);
     ctx->p = p;
@@ -1013,6 +1089,8 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
     build_near_sog(ctx->nsog, w, sv, p[0].M, p[0].r_c);
     build_sog_tables(ctx->nsog, w, sv, p[0].M, p[0].r_c);
     build_list_table(ctx->nsog, ctx->h_ltab, w, sv, p[0].M, p[0].r_c);
+    ctx->cs = cs_new;
+    ctx->use_cs = p[0].near_kernel == 1;
 
     // --- per-system layout
     ctx->desc.assign(ns, SysDesc{});
@@ -1093,6 +1171,10 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         CK(dalloc(&ctx->linv, n));
         CK(dalloc(&ctx->d_ltab, (size_t)kLTabN));
         CK(cudaMemcpy(ctx->d_ltab, ctx->h_ltab.data(), sizeof(float4) * kLTabN, cudaMemcpyHostToDevice));
+        if (ctx->use_cs) {
+            CK(dalloc(&ctx->d_cstab, cstab.size()));
+            CK(cudaMemcpy(ctx->d_cstab, cstab.data(), sizeof(float4) * cstab.size(), cudaMemcpyHostToDevice));
+        }
         CK(dalloc(&ctx->nbr_list, (n + 31) / 32 * 32 * (size_t)ctx->list_cap));
         CK(dalloc(&ctx->d_rebuild, (size_t)ns + 1));
         CK(cudaMemset(ctx->xref, 0, sizeof(uint4) * n));
@@ -1812,6 +1894,7 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->lpos);
     dfree(&ctx->linv);
     dfree(&ctx->d_ltab);
+    dfree(&ctx->d_cstab);
     dfree(&ctx->nbr_list);
     dfree(&ctx->d_rebuild);
     dfree(&ctx->cb.pack);

@@ -263,9 +263,25 @@ cudaError_t launch_list_move(int64_t n, int64_t old_off, int64_t new_off, int ol
                              int32_t *new_flag, cudaStream_t st);
 // Near-field force (caller order) with both energies packed in fnear[i].w as
 // two floats (U_near high word, U_wca low word).
+// Core-shell kernel of the list path (Sec. 3.4): Taylor coefficients of the
+// core with the series' signs folded in (a: G, b: F_M, in powers of r^2),
+// r_in^2, the shell table's exponent-bit mask and length (entries: kernel
+// value at the bin start and its change over the bin, for the force factor
+// and the pair energy).
+constexpr int kCsQ = 10;         // Taylor terms of the core
+constexpr int kCsManBits = 8;    // mantissa bits of the shell-table index
+struct CoreShellDev {
+    float a[kCsQ];               // G(u)   = sum_{i<Q}  a_i u^i
+    float b[kCsQ + 1];           // F_M(u) = sum_{i<=Q} b_i u^i
+    float rin2;
+    uint32_t emask;              // 2^b_exp - 1
+    int32_t n_tab;               // 2^(b_exp + kCsManBits)
+};
+// cs == nullptr: the combined table (ltab); else the core-shell kernel with
+// its table cstab.
 cudaError_t launch_near_list(const BatchView &bv, const NearSog &sog, const float4 *ltab, const int32_t *nbr_list,
                              const int32_t *nbr_cnt, const int32_t *list_perm, double4_32a *fnear, cudaStream_t st,
-                             const Prof *prof);
+                             const Prof *prof, const CoreShellDev *cs = nullptr, const float4 *cstab = nullptr);
 
 // ---- far field (k_far.cu) -----------------------------------------------------
 // tile_override > 0 replaces the default particles-per-tile rule (tunable)

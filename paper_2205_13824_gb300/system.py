@@ -14,7 +14,8 @@ DEFAULT_M = 36
 
 def make_params(L, P, r_c=3.0, b=DEFAULT_B, sigma=0.0, omega0=0.0, M=DEFAULT_M, lB=1.0,
                 wca_sigma=1.0, wca_eps=1.0, dt=0.001, mass=1.0, T_target=1.0, tau_T=0.0,
-                seed=1, n_ksets=1, chain_len=0, precision="fp64", boundary=0) -> B.rbsog_params:
+                seed=1, n_ksets=1, chain_len=0, precision="fp64", boundary=0, near_kernel=0,
+                r_in=0.0) -> B.rbsog_params:
     if isinstance(L, (int, float)):
         L = (float(L),) * 3
     p = B.rbsog_params()
@@ -29,6 +30,9 @@ def make_params(L, P, r_c=3.0, b=DEFAULT_B, sigma=0.0, omega0=0.0, M=DEFAULT_M, 
         if isinstance(precision, str) else int(precision)
     p.boundary = {"tinfoil": 0, "spherical": 1, "planar": 2}[boundary] \
         if isinstance(boundary, str) else int(boundary)
+    p.near_kernel = {"table": 0, "coreshell": 1}[near_kernel] \
+        if isinstance(near_kernel, str) else int(near_kernel)
+    p.r_in = float(r_in)
     return p
 
 

@@ -515,3 +515,41 @@ def test_fp32c_lists_need_an_accurate_combined_table():
         err = np.linalg.norm(f.cpu().numpy() - fo) / np.linalg.norm(fo)
         assert err < 1e-4, (sog.sigma, err)
         g.close()
+
+
+def test_fp32c_coreshell_kernel_matches_the_oracle_scheme():
+    """The paper's core-shell kernel (Sec. 3.4) on the list path: total
+    forces and near energy against the oracle's core-shell near field (same
+    10 Taylor terms, 2 + 8 index bits, r_in) plus its far field, to the FP32C
+    tolerance; the scheme itself stays close to the direct Gaussian sums."""
+    _dev()
+    import torch
+    Pk = _lib()
+    B = Pk.binding
+    N, L, P = 4998, 21.5, 64
+    q, x, v = I.electrolyte(N, L, seed=17)
+    sog = prod_sog(O)
+    p = Pk.make_params(L, P, sigma=sog.sigma, omega0=sog.omega0, M=sog.M, n_ksets=8, seed=3, precision="fp32c",
+                       near_kernel="coreshell", r_in=1.0)
+    g = Pk.RBSOG(N, p, device=0)
+    g.set_state(*to_dev(q, x, v))
+    m = O.kseq(sog, (L,) * 3, seed=9, n_chains=1, chain_len=P)[:P]
+    f = torch.zeros((N, 3), dtype=torch.float64, device="cuda:0")
+    e = B.rbsog_compute_forces(g.ctx, m, f)
+    s = osys(L, sog)
+    xw = O.wrap(x, s.L)
+    fo, eo = O.forces(s, q, xw, S=s.S(), m=m)
+    fnd, und, _, _ = O.near(s, q, xw, method="cells")
+    fnc, unc, _ = O.near_coreshell(s, q, xw, O.coreshell(1.0, Q=10, b_exp=2, b_man=8))
+    f_cs = fo - fnd + fnc
+    err = np.linalg.norm(f.cpu().numpy() - f_cs) / np.linalg.norm(f_cs)
+    assert err < 1e-4, err
+    assert abs(e["U_near"] - unc) <= 1e-5 * N
+    assert np.linalg.norm(fnc - fnd) <= 1e-5 * np.linalg.norm(fnd)    # the scheme vs the direct sums
+    B.rbsog_set_profiling(g.ctx, True)
+    g.step(2)
+    assert "near_fp32c_coreshell" in B.rbsog_get_profile(g.ctx)
+    g.close()
+    bad = Pk.make_params(L, P, n_ksets=2, precision="fp64", near_kernel="coreshell")
+    with pytest.raises(B.RBSOGError):
+        Pk.RBSOG(N, bad, device=0)
