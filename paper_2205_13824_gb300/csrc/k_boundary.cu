@@ -10,8 +10,9 @@
 //
 // part     one block per particle block: the block's q r sums (fixed order:
 //          warp trees, then the warps in order) as one partial;
-// combine  one warp per system: the partials in block order (lane strides,
-//          then a warp tree), U0 into the energy record;
+// combine  one block per system: the partials in fixed order (thread
+//          strides, warp trees, the warps in order), U0 into the energy
+//          record;
 // force    one thread per particle: the term added to its total force.
 // Systems with the tinfoil boundary skip all three.
 #include "rbsog_kernels.cuh"
@@ -62,13 +63,15 @@ __global__ void __launch_bounds__(kThreads) k_dipole_part(BatchView bv, const do
     }
 }
 
-__global__ void __launch_bounds__(32) k_dipole_combine(BatchView bv, const double4_32a *__restrict__ dpart,
-                                                       double4_32a *__restrict__ dip, double *__restrict__ energy) {
-    const int sys = blockIdx.x, lane = threadIdx.x;
+__global__ void __launch_bounds__(kThreads) k_dipole_combine(BatchView bv, const double4_32a *__restrict__ dpart,
+                                                             double4_32a *__restrict__ dip,
+                                                             double *__restrict__ energy) {
+    __shared__ double s_m[3][kThreads / 32];
+    const int sys = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (!boundary_on(bv, sys)) return;
     const SysDesc &a = bv.sys[sys];
     double mx = 0.0, my = 0.0, mz = 0.0;
-    for (int b = lane; b < a.n_kpart; b += 32) {
+    for (int b = tid; b < a.n_kpart; b += kThreads) {
         const double4_32a v = dpart[a.kp_off + b];
         mx += v.x;
         my += v.y;
@@ -81,6 +84,18 @@ __global__ void __launch_bounds__(32) k_dipole_combine(BatchView bv, const doubl
         mz += __shfl_down_sync(0xffffffffu, mz, o);
     }
     if (lane == 0) {
+        s_m[0][wid] = mx;
+        s_m[1][wid] = my;
+        s_m[2][wid] = mz;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mx = my = mz = 0.0;
+        for (int q = 0; q < kThreads / 32; ++q) {
+            mx += s_m[0][q];
+            my += s_m[1][q];
+            mz += s_m[2][q];
+        }
         const double V = a.box.L[0] * a.box.L[1] * a.box.L[2];
         const double pi = 3.14159265358979323846;
         double U, c[3];
@@ -126,7 +141,7 @@ cudaError_t launch_boundary(const BatchView &bv, const double4_32a *posq, double
     k_dipole_part<<<bv.n_pblk, kThreads, 0, st>>>(bv, posq, dpart);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_dipole_combine<<<bv.n_sys, 32, 0, st>>>(bv, dpart, dip, energy);
+    k_dipole_combine<<<bv.n_sys, kThreads, 0, st>>>(bv, dpart, dip, energy);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_dipole_force<<<bv.n_pblk, kThreads, 0, st>>>(bv, posq, dip, force);
