@@ -123,6 +123,10 @@ def lib():
             L.orc_md.argtypes = [_i64, _pd, _pd, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _i64,
                                  _d, _d, _d, _d, C.c_int, C.POINTER(OrcEnergies)]
             L.orc_md.restype = C.c_int
+            L.orc_md_thermo.argtypes = [_i64, _pd, _pd, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _i64,
+                                        _d, _d, _d, _d, C.c_int, C.POINTER(OrcEnergies), _i32, _u64, _i64]
+            L.orc_md_thermo.restype = C.c_int
+            L.orc_langevin_noise.argtypes = [_u64, _i64, _i64, _pd]
             L.orc_rdf_counts.argtypes = [_i64, _pd, _pd, _d, _i32, C.POINTER(_u64)]
             L.orc_rdf_counts.restype = C.c_int
             L.orc_rdf_g.argtypes = [C.POINTER(_u64), _i32, _d, _i64, _i64, _pd]
@@ -380,9 +384,18 @@ def forces(sys_: System, q, x, S=0.0, m=None):
     return f, e.as_dict()
 
 
-def md(sys_: System, q, x, v, S, P, kseq_, nsteps, dt, mass=1.0, T0=1.0, tau=0.0, f=None):
+def langevin_noise(seed: int, t: int, i: int):
+    z = np.zeros(3)
+    lib().orc_langevin_noise(int(seed), int(t), int(i), _p(z))
+    return z
+
+
+def md(sys_: System, q, x, v, S, P, kseq_, nsteps, dt, mass=1.0, T0=1.0, tau=0.0, f=None, thermostat=0,
+       seed=0, step0=0):
     """Velocity-Verlet run of Algorithm 1; returns (x, v, f, per-step energies).
-    P = 0 uses the exact far sum (kseq_ ignored)."""
+    P = 0 uses the exact far sum (kseq_ ignored).  thermostat 1 (tau > 0):
+    Langevin dynamics in the BAOAB splitting with noise keyed by seed and the
+    step counter (starting at step0)."""
     q = _f64(q)
     x = _f64(x).copy()
     v = _f64(v).copy()
@@ -391,9 +404,9 @@ def md(sys_: System, q, x, v, S, P, kseq_, nsteps, dt, mass=1.0, T0=1.0, tau=0.0
     f = _f64(f).copy() if have else np.zeros((n, 3))
     es = (OrcEnergies * max(int(nsteps), 1))()
     ks = _i32a(kseq_ if kseq_ is not None else np.zeros((1, 3)))
-    rc_ = lib().orc_md(n, _p(q), _p(x), _p(v), _p(f), C.byref(sys_.c), float(S), int(P),
-                       _p(ks, _pi32), int(nsteps), float(dt), float(mass), float(T0), float(tau),
-                       int(have), es)
+    rc_ = lib().orc_md_thermo(n, _p(q), _p(x), _p(v), _p(f), C.byref(sys_.c), float(S), int(P),
+                              _p(ks, _pi32), int(nsteps), float(dt), float(mass), float(T0), float(tau),
+                              int(have), es, int(thermostat), int(seed), int(step0))
     if rc_ != 0:
         raise ValueError("fewer than 3 cells per side")
     return x, v, f, [es[t].as_dict() for t in range(int(nsteps))]

@@ -925,10 +925,46 @@ int orc_forces(int64_t n, const double *q, const double *x, const orc_sys *sys,
  * when have_force == 0 the forces at the initial positions are computed
  * first (consuming the first k-set).  x is wrapped after every drift.
  * T = 2K / (3N - 3).  e_steps[t] receives the energies at the end of step t. */
+int orc_md_thermo(int64_t n, const double *q, double *x, double *v, double *f,
+                  const orc_sys *sys, double S, int32_t P, const int32_t *kseq,
+                  int64_t nsteps, double dt, double mass, double T0, double tau,
+                  int have_force, orc_energies *e_steps, int32_t thermostat, uint64_t seed, int64_t step0);
+
+/* Langevin noise of particle i in the step that starts with step counter t:
+ * Philox4x64-10 with key (seed, 2^63 + 1) (the sampler's chain keys are
+ * below 2^63) and counter (t, i, 0, 0); Box-Muller as in the sampler:
+ * (u0, u1) -> (z_x, z_y), (u2, u3) -> z_z. */
+void orc_langevin_noise(uint64_t seed, int64_t t, int64_t i, double z[3]) {
+    const uint64_t key[2] = {seed, 0x8000000000000001ull};
+    const uint64_t ctr[4] = {(uint64_t)t, (uint64_t)i, 0, 0};
+    uint64_t r[4];
+    orc_philox4x64_10(ctr, key, r);
+    const double r01 = sqrt(-2.0 * log(1.0 - u01(r[0])));
+    const double r23 = sqrt(-2.0 * log(1.0 - u01(r[2])));
+    z[0] = r01 * cos(2.0 * M_PI * u01(r[1]));
+    z[1] = r01 * sin(2.0 * M_PI * u01(r[1]));
+    z[2] = r23 * cos(2.0 * M_PI * u01(r[3]));
+}
+
 int orc_md(int64_t n, const double *q, double *x, double *v, double *f,
            const orc_sys *sys, double S, int32_t P, const int32_t *kseq,
            int64_t nsteps, double dt, double mass, double T0, double tau,
            int have_force, orc_energies *e_steps) {
+    return orc_md_thermo(n, q, x, v, f, sys, S, P, kseq, nsteps, dt, mass, T0, tau, have_force, e_steps, 0, 0, 0);
+}
+
+/* As orc_md, with thermostat 1 (tau > 0): Langevin dynamics with friction
+ * 1/tau in the BAOAB splitting, per step: v += dt/2 F/m; x += dt/2 v;
+ * v = c1 v + c2 z with c1 = e^{-dt/tau}, c2 = sqrt((1 - c1^2) T0/m) and z the
+ * noise of orc_langevin_noise for the step counter step0 + t; x += dt/2 v;
+ * forces; v += dt/2 F/m.  The Berendsen rescale is thermostat 0. */
+int orc_md_thermo(int64_t n, const double *q, double *x, double *v, double *f,
+                  const orc_sys *sys, double S, int32_t P, const int32_t *kseq,
+                  int64_t nsteps, double dt, double mass, double T0, double tau,
+                  int have_force, orc_energies *e_steps, int32_t thermostat, uint64_t seed, int64_t step0) {
+    const int langevin = thermostat == 1 && tau > 0.0;
+    const double c1 = langevin ? exp(-dt / tau) : 1.0;
+    const double c2 = langevin ? sqrt((1.0 - c1 * c1) * T0 / mass) : 0.0;
     int64_t used = 0;
     orc_energies e;
     orc_wrap(n, x, sys->L);
@@ -939,7 +975,17 @@ int orc_md(int64_t n, const double *q, double *x, double *v, double *f,
     }
     for (int64_t t = 0; t < nsteps; ++t) {
         for (int64_t i = 0; i < 3 * n; ++i) v[i] += 0.5 * dt * f[i] / mass;
-        for (int64_t i = 0; i < 3 * n; ++i) x[i] += dt * v[i];
+        if (langevin) {
+            for (int64_t i = 0; i < 3 * n; ++i) x[i] += 0.5 * dt * v[i];
+            for (int64_t i = 0; i < n; ++i) {
+                double z[3];
+                orc_langevin_noise(seed, step0 + t, i, z);
+                for (int d = 0; d < 3; ++d) v[3 * i + d] = c1 * v[3 * i + d] + c2 * z[d];
+            }
+            for (int64_t i = 0; i < 3 * n; ++i) x[i] += 0.5 * dt * v[i];
+        } else {
+            for (int64_t i = 0; i < 3 * n; ++i) x[i] += dt * v[i];
+        }
         orc_wrap(n, x, sys->L);
         int rc = orc_forces(n, q, x, sys, S, P, P > 0 ? kseq + 3 * (int64_t)P * used : NULL, f, &e);
         if (rc) return rc;
@@ -948,7 +994,7 @@ int orc_md(int64_t n, const double *q, double *x, double *v, double *f,
         double K = 0.0;
         for (int64_t i = 0; i < 3 * n; ++i) K += 0.5 * mass * v[i] * v[i];
         double T = 2.0 * K / (3.0 * (double)n - 3.0);
-        if (tau > 0.0 && T > 0.0) {
+        if (!langevin && tau > 0.0 && T > 0.0) {
             double lam = sqrt(1.0 + dt / tau * (T0 / T - 1.0));
             for (int64_t i = 0; i < 3 * n; ++i) v[i] *= lam;
             K = 0.0;

@@ -123,6 +123,17 @@ int  orc_md(int64_t n, const double *q, double *x, double *v, double *f,
             const orc_sys *sys, double S, int32_t P, const int32_t *kseq,
             int64_t nsteps, double dt, double mass, double T0, double tau,
             int have_force, orc_energies *e_steps);
+/* As orc_md with a thermostat choice: 0 Berendsen rescale (tau > 0), 1
+ * Langevin dynamics with friction 1/tau in the BAOAB splitting; the noise of
+ * particle i in the step with step counter step0 + t is
+ * orc_langevin_noise(seed, step0 + t, i). */
+int orc_md_thermo(int64_t n, const double *q, double *x, double *v, double *f,
+                  const orc_sys *sys, double S, int32_t P, const int32_t *kseq,
+                  int64_t nsteps, double dt, double mass, double T0, double tau,
+                  int have_force, orc_energies *e_steps, int32_t thermostat, uint64_t seed, int64_t step0);
+/* Three standard normals for the Langevin noise: Philox4x64-10 with key
+ * (seed, 2^63 + 1), counter (t, i, 0, 0), Box-Muller. */
+void orc_langevin_noise(uint64_t seed, int64_t t, int64_t i, double z[3]);
 
 /* ---- radial distribution functions (Appendix A) ----------------------- */
 int  orc_rdf_counts(int64_t n, const double *q, const double *x, double L, int32_t nbins, uint64_t *counts);
