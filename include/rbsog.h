@@ -93,6 +93,14 @@ typedef struct {
                                  when the system does not run on neighbour lists.            */
     double r_in;              /* core radius of near_kernel 1; <= 0: r_c / 3; the table covers
                                  at most 8 octaves of r^2 from r_in^2 up to r_c^2           */
+    int32_t thermostat;       /* with tau_T > 0: 0 Berendsen rescale after the second half
+                                 kick; 1 Langevin dynamics with friction 1/tau_T and bath
+                                 temperature T_target in the BAOAB splitting (v += dt/2 F/m;
+                                 x += dt/2 v; v = c1 v + c2 z, c1 = e^{-dt/tau_T},
+                                 c2 = sqrt((1 - c1^2) T_target/m); x += dt/2 v; forces;
+                                 v += dt/2 F/m).  The noise z of particle i in the step with
+                                 step counter t is Philox4x64-10 (key (seed, 2^63 + 1),
+                                 counter (t, i, 0, 0)) through Box-Muller                   */
 } rbsog_params;
 
 /* Energies of the last force evaluation (Eqs. 3.1, 3.6-3.8) and kinetic state. */

@@ -46,7 +46,8 @@ class rbsog_params(C.Structure):
                 ("wca_eps", C.c_double), ("dt", C.c_double), ("mass", C.c_double),
                 ("T_target", C.c_double), ("tau_T", C.c_double), ("seed", C.c_uint64),
                 ("n_ksets", C.c_int64), ("chain_len", C.c_int32), ("precision", C.c_int32),
-                ("boundary", C.c_int32), ("near_kernel", C.c_int32), ("r_in", C.c_double)]
+                ("boundary", C.c_int32), ("near_kernel", C.c_int32), ("r_in", C.c_double),
+                ("thermostat", C.c_int32)]
 
 
 class rbsog_energies(C.Structure):

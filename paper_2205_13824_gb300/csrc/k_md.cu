@@ -16,6 +16,37 @@ __device__ __forceinline__ double fold(double x, double L) {
     return v >= L ? 0.0 : v;
 }
 
+// Three standard normals for the Langevin step of particle il in the step
+// with step counter t: Philox4x64-10, key (seed, 2^63 + 1) (the sampler's
+// chain keys stay below 2^63), counter (t, il, 0, 0); Box-Muller
+// (u0, u1) -> (z_x, z_y), (u2, u3) -> z_z.  FP64 arithmetic for the FP64
+// path; FP32 for FP32C, where FP64 transcendentals would dominate the step.
+__device__ __forceinline__ void langevin_noise(uint64_t seed, int64_t t, int64_t il, int precision, double z[3]) {
+    uint64_t c[4] = {(uint64_t)t, (uint64_t)il, 0ull, 0ull};
+    philox4x64_10(c, seed, 0x8000000000000001ull);
+    if (precision == 1) {
+        const float u0 = (float)unit53(c[0]), u1 = (float)unit53(c[1]);
+        const float u2 = (float)unit53(c[2]), u3 = (float)unit53(c[3]);
+        const float r01 = sqrtf(-2.0f * logf(1.0f - u0)), r23 = sqrtf(-2.0f * logf(1.0f - u2));
+        float s1, c1, s3, c3;
+        sincospif(2.0f * u1, &s1, &c1);
+        sincospif(2.0f * u3, &s3, &c3);
+        z[0] = r01 * c1;
+        z[1] = r01 * s1;
+        z[2] = r23 * c3;
+        (void)s3;
+    } else {
+        const double r01 = sqrt(-2.0 * log(1.0 - unit53(c[0]))), r23 = sqrt(-2.0 * log(1.0 - unit53(c[2])));
+        double s1, c1, s3, c3;
+        sincospi(2.0 * unit53(c[1]), &s1, &c1);
+        sincospi(2.0 * unit53(c[3]), &s3, &c3);
+        z[0] = r01 * c1;
+        z[1] = r01 * s1;
+        z[2] = r23 * c3;
+        (void)s3;
+    }
+}
+
 // x < 0 or x >= L (L > 0) decided on the bit patterns with integer compares
 // (the order of non-negative doubles is that of their bits): the same
 // outcome as the FP64 compares, which are scarce on this GPU; -0.0 stays,
@@ -44,10 +75,27 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift(BatchView bv, double4_3
     v.x += h * f.x;
     v.y += h * f.y;
     v.z += h * f.z;
+    if (a.thermostat == 1) {
+        // Langevin, BAOAB: half drift, Ornstein-Uhlenbeck velocity update
+        // with this step's noise, half drift
+        const double hd = a.half_dt;
+        p.x += hd * v.x;
+        p.y += hd * v.y;
+        p.z += hd * v.z;
+        double z[3];
+        langevin_noise(a.lv_seed, bv.step[w.x], il, bv.precision, z);
+        v.x = a.lv_c1 * v.x + a.lv_c2 * z[0];
+        v.y = a.lv_c1 * v.y + a.lv_c2 * z[1];
+        v.z = a.lv_c1 * v.z + a.lv_c2 * z[2];
+        p.x += hd * v.x;
+        p.y += hd * v.y;
+        p.z += hd * v.z;
+    } else {
+        p.x += a.dt * v.x;
+        p.y += a.dt * v.y;
+        p.z += a.dt * v.z;
+    }
     // fold only coordinates that left the box (the division is FP64-pipe bound)
-    p.x += a.dt * v.x;
-    p.y += a.dt * v.y;
-    p.z += a.dt * v.z;
     if (outside(p.x, __double_as_longlong(a.box.L[0]))) p.x = fold(p.x, a.box.L[0]);
     if (outside(p.y, __double_as_longlong(a.box.L[1]))) p.y = fold(p.y, a.box.L[1]);
     if (outside(p.z, __double_as_longlong(a.box.L[2]))) p.z = fold(p.z, a.box.L[2]);
@@ -182,7 +230,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BatchView bv, const do
         double K = t[3];
         double T = 2.0 * K / (3.0 * (double)a.n - 3.0);
         double lam = 1.0;
-        if (a.tau > 0.0 && T > 0.0) {
+        if (a.thermostat == 0 && a.tau > 0.0 && T > 0.0) {
             lam = sqrt(1.0 + a.dt / a.tau * (a.T0 / T - 1.0));
             K *= lam * lam;
             T *= lam * lam;

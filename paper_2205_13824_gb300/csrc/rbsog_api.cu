@@ -692,7 +692,7 @@ rbsog_status enqueue_step_tail(rbsog_ctx *ctx) {
     CK(launch_kick(bv, ctx->vel, ctx->force, ctx->kpart, ctx->st, pf));
     CK(launch_finalize(bv, ctx->epart, ctx->rho, ctx->kpart, 1, ctx->energy, 1, ctx->st, pf));
     bool thermo = false;
-    for (auto &pp : ctx->p) thermo = thermo || pp.tau_T > 0.0;
+    for (auto &pp : ctx->p) thermo = thermo || (pp.tau_T > 0.0 && pp.thermostat == 0);
     if (thermo) CK(launch_rescale(bv, ctx->vel, ctx->energy, ctx->st, pf));
     CK(launch_step_done(bv, ctx->st, pf));
     return RBSOG_OK;
@@ -1003,6 +1003,8 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         if (q.n_ksets < 1) return fail(ctx, RBSOG_EINVAL, "system %d: n_ksets must be >= 1", s);
         if (!(q.r_c > 0.0)) return fail(ctx, RBSOG_EINVAL, "system %d: r_c must be > 0", s);
         if (!(q.mass > 0.0)) return fail(ctx, RBSOG_EINVAL, "system %d: mass must be > 0", s);
+        if (q.thermostat < 0 || q.thermostat > 1)
+            return fail(ctx, RBSOG_EINVAL, "system %d: thermostat must be 0 (Berendsen) or 1 (Langevin)", s);
         if (q.near_kernel < 0 || q.near_kernel > 1)
             return fail(ctx, RBSOG_EINVAL, "system %d: near_kernel must be 0 (table) or 1 (core-shell)", s);
         if (s > 0 && (q.near_kernel != p[0].near_kernel || q.r_in != p[0].r_in))
@@ -1129,6 +1131,11 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         d.inv_mass = 1.0 / q.mass;
         d.half_dt_inv_mass = 0.5 * q.dt * d.inv_mass;
         d.boundary = q.boundary;
+        d.thermostat = q.tau_T > 0.0 ? q.thermostat : 0;
+        d.half_dt = 0.5 * q.dt;
+        d.lv_c1 = d.thermostat == 1 ? std::exp(-q.dt / q.tau_T) : 1.0;
+        d.lv_c2 = d.thermostat == 1 ? std::sqrt((1.0 - d.lv_c1 * d.lv_c1) * q.T_target / q.mass) : 0.0;
+        d.lv_seed = q.seed;
         d.half_mass_f = (float)(0.5 * q.mass);
         d.T0 = q.T_target;
         d.tau = q.tau_T;

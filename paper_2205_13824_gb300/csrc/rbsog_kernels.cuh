@@ -134,6 +134,10 @@ struct SysDesc {
     double dt, inv_mass, mass, T0, tau;
     double half_dt_inv_mass;   // dt / (2 m): the half kick's factor
     int32_t boundary;          // zero-frequency term: 0 tinfoil, 1 spherical, 2 planar (z)
+    int32_t thermostat;        // with tau > 0: 0 Berendsen rescale, 1 Langevin (BAOAB)
+    double half_dt;            // dt / 2
+    double lv_c1, lv_c2;       // Langevin: v <- c1 v + c2 z, c1 = e^{-dt/tau}, c2 = sqrt((1 - c1^2) T0 / m)
+    uint64_t lv_seed;          // key of the Langevin noise
     float half_mass_f;         // m / 2 (FP32C kinetic-energy terms)
 };
 
@@ -170,6 +174,34 @@ struct BatchView {
 };
 constexpr int kFinChunks = 16;    // blocks per system in the finalize reduction
 constexpr int kParticleBlock = 256;
+
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 64x64->128-bit products with the published multipliers, key bumped by the
+// published Weyl constants before every round after the first.
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+        const uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+        const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// 53 random bits mapped to [0, 1).
+__device__ __forceinline__ double unit53(uint64_t x) {
+    return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+}
+
 
 // X = trunc(x * (2^32 / L)) clamped to [0, 2^32 - 1]: the fixed-point
 // coordinate of the FP32C path (one FP64 multiply; the scale comes from the

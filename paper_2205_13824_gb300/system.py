@@ -15,7 +15,7 @@ DEFAULT_M = 36
 def make_params(L, P, r_c=3.0, b=DEFAULT_B, sigma=0.0, omega0=0.0, M=DEFAULT_M, lB=1.0,
                 wca_sigma=1.0, wca_eps=1.0, dt=0.001, mass=1.0, T_target=1.0, tau_T=0.0,
                 seed=1, n_ksets=1, chain_len=0, precision="fp64", boundary=0, near_kernel=0,
-                r_in=0.0) -> B.rbsog_params:
+                r_in=0.0, thermostat=0) -> B.rbsog_params:
     if isinstance(L, (int, float)):
         L = (float(L),) * 3
     p = B.rbsog_params()
@@ -33,6 +33,8 @@ def make_params(L, P, r_c=3.0, b=DEFAULT_B, sigma=0.0, omega0=0.0, M=DEFAULT_M, 
     p.near_kernel = {"table": 0, "coreshell": 1}[near_kernel] \
         if isinstance(near_kernel, str) else int(near_kernel)
     p.r_in = float(r_in)
+    p.thermostat = {"berendsen": 0, "langevin": 1}[thermostat] \
+        if isinstance(thermostat, str) else int(thermostat)
     return p
 
 
