@@ -115,6 +115,8 @@ def lib():
             L.orc_near_coreshell.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), C.POINTER(OrcCoreShell), _pd,
                                              C.POINTER(_d), C.POINTER(_d)]
             L.orc_near_coreshell.restype = C.c_int
+            L.orc_virial.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _pd]
+            L.orc_virial.restype = C.c_int
             L.orc_boundary.argtypes = [_i64, _pd, _pd, _pd, _d, _i32, _pd]
             L.orc_boundary.restype = _d
             L.orc_forces.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), _d, _i32, _pi32, _pd,
@@ -355,6 +357,19 @@ def forces_sample(sys_: System, q, x, S, m, idx):
 def self_energy(sys_: System, q):
     q = _f64(q)
     return lib().orc_self_energy(q.shape[0], _p(q), C.byref(sys_.c))
+
+
+def virial(sys_: System, q, x, S=0.0, m=None):
+    """Configurational virial tensor W[3, 3] = -dU/d eps: near (+ WCA) plus
+    the random-batch far estimator on k-set m, or the exact far sum (m None)."""
+    q, x = _f64(q), _f64(x)
+    W = np.zeros(9)
+    if m is None:
+        lib().orc_virial(x.shape[0], _p(q), _p(x), C.byref(sys_.c), float(S), 0, None, _p(W))
+    else:
+        m = _i32a(m)
+        lib().orc_virial(x.shape[0], _p(q), _p(x), C.byref(sys_.c), float(S), m.shape[0], _p(m, _pi32), _p(W))
+    return W.reshape(3, 3)
 
 
 def boundary(q, x, L, kind: int, lB: float = 1.0):

@@ -741,6 +741,88 @@ double orc_self_energy(int64_t n, const double *q, const orc_sys *sys) {
     return sys->lB * 0.5 * w * q2;
 }
 
+/* ---- virial ----------------------------------------------------------------
+ * Configurational virial tensor W_ab = -dU/d eps_ab under the affine map
+ * r -> (1 + eps) r of positions and box (r_c and the SOG fixed): the near
+ * field (+ WCA) gives sum over pairs of r_ij,a F_ij,b; the far energy
+ * (1/2V) sum_k F~(k) |rho(k)|^2, with V -> V (1 + tr eps) and
+ * k -> (1 - eps^T) k at fixed rho, gives
+ * (1/2V) sum_k |rho(k)|^2 [F~(k) delta_ab + 2 k_a k_b dF~/d(k^2)], and
+ * F~ = pi^{3/2} sum_l w_l s_l^3 e^{-s_l^2 k^2/4} so that
+ * 2 dF~/d(k^2) / F~ = -(1/2) T1/T0, T0 = sum_l w_l s_l^3 e^{..}, T1 = sum_l
+ * w_l s_l^5 e^{..}.  The random-batch estimator weights each sampled k by
+ * pi^{3/2} S / (2 P V) |rho|^2 as the energy's (Eq. 3.24), which makes it
+ * unbiased for the exact far virial.  The k-independent self energy adds
+ * nothing.  Row-major W[9], times lB for the Coulomb terms. */
+static void far_virial_add(const orc_sys *sys, const int32_t m[3], double w, double W[9]) {
+    double k[3], k2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        k[d] = 2.0 * M_PI * m[d] / sys->L[d];
+        k2 += k[d] * k[d];
+    }
+    double T0 = 0.0, T1 = 0.0;
+    for (int32_t l = 0; l <= sys->M; ++l) {
+        const double s2 = sys->s[l] * sys->s[l];
+        const double e = sys->omega[l] * s2 * sys->s[l] * exp(-s2 * k2 / 4.0);
+        T0 += e;
+        T1 += e * s2;
+    }
+    const double r = T0 > 0.0 ? T1 / T0 : 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) W[3 * a + b] += w * ((a == b ? 1.0 : 0.0) - 0.5 * r * k[a] * k[b]);
+}
+
+int orc_virial(int64_t n, const double *q, const double *x, const orc_sys *sys, double S, int32_t P,
+               const int32_t *m, double W[9]) {
+    for (int c = 0; c < 9; ++c) W[c] = 0.0;
+    const double rc2 = sys->rc * sys->rc;
+    const double V = sys->L[0] * sys->L[1] * sys->L[2];
+    /* near field and WCA: pairs i < j */
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j) {
+            double d[3];
+            const double r2 = min_image(x + 3 * i, x + 3 * j, sys->L, d);
+            if (!(r2 < rc2)) continue;
+            double fi[3] = {0.0, 0.0, 0.0}, un = 0.0, uw = 0.0;
+            near_pair(sys, q[i], q[j], d, r2, fi, &un, &uw);   /* force on i from j */
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) W[3 * a + b] += d[a] * fi[b];
+        }
+    double Wf[9] = {0};
+    if (P > 0) {
+        double *rho = (double *)malloc(sizeof(double) * 2 * (size_t)P);
+        orc_rho(n, q, x, sys->L, P, m, rho);
+        const double c = pow(M_PI, 1.5) * S / (2.0 * P * V);
+        for (int32_t e = 0; e < P; ++e)
+            far_virial_add(sys, m + 3 * e, c * (rho[2 * e] * rho[2 * e] + rho[2 * e + 1] * rho[2 * e + 1]), Wf);
+        free(rho);
+    } else {
+        /* exact sum over the half space (each k with -k, as orc_far_exact) */
+        const double kcut = 2.0 * sqrt(log(1e16)) / sys->s[0];
+        int32_t mm[3];
+        for (int d = 0; d < 3; ++d) mm[d] = (int32_t)ceil(kcut * sys->L[d] / (2.0 * M_PI));
+        for (int32_t a = 0; a <= mm[0]; ++a)
+            for (int32_t b = -mm[1]; b <= mm[1]; ++b)
+                for (int32_t c = -mm[2]; c <= mm[2]; ++c) {
+                    const int half = (a > 0) || (a == 0 && b > 0) || (a == 0 && b == 0 && c > 0);
+                    if (!half) continue;
+                    const int32_t mk[3] = {a, b, c};
+                    double k2 = 0.0;
+                    for (int d = 0; d < 3; ++d) {
+                        const double kd = 2.0 * M_PI * mk[d] / sys->L[d];
+                        k2 += kd * kd;
+                    }
+                    if (k2 > kcut * kcut) continue;
+                    double rho[2];
+                    orc_rho(n, q, x, sys->L, 1, mk, rho);
+                    const double ft = orc_ftilde(sys->omega, sys->s, sys->M, k2);
+                    far_virial_add(sys, mk, 2.0 * ft * (rho[0] * rho[0] + rho[1] * rho[1]) / (2.0 * V), Wf);
+                }
+    }
+    for (int c = 0; c < 9; ++c) W[c] += sys->lB * Wf[c];
+    return 0;
+}
+
 /* ---- core-shell near-field kernel (Sec. 3.4) ------------------------------
  * Core, r < r_in (Eqs. 3.25-3.26): with u = r^2,
  *   sum_l w_l/s_l^2 e^{-u/s_l^2} = sum_{i=1}^{Q} (-1)^{i-1} A_i u^{i-1},

@@ -102,6 +102,11 @@ double orc_self_energy(int64_t n, const double *q, const orc_sys *sys);
  * 2^b_exp octaves of the table, starting at the octave of r_in^2, do not
  * reach r_c^2. */
 int orc_coreshell_eval(const orc_sys *sys, const orc_coreshell *cs, double r2, double *g, double *n);
+/* Configurational virial tensor W_ab = -dU/d eps_ab (row-major W[9]) of the
+ * near field (+ WCA) and the far field: the random-batch estimator on the
+ * k-set m (P > 0, weights of Eq. 3.24) or the exact Fourier sum (P == 0). */
+int orc_virial(int64_t n, const double *q, const double *x, const orc_sys *sys, double S, int32_t P,
+               const int32_t *m, double W[9]);
 /* Near field (+ WCA, exact) with the core-shell kernel; O(N^2) pair scan.
  * Returns -1 as orc_coreshell_eval for an uncovered table. */
 int orc_near_coreshell(int64_t n, const double *q, const double *x, const orc_sys *sys, const orc_coreshell *cs,
