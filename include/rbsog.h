@@ -260,6 +260,18 @@ rbsog_status rbsog_get_profile(rbsog_ctx *ctx, int32_t cap, char (*names)[32], i
 rbsog_status rbsog_rho_noalloc(int64_t n, const double *q, const double *x, const double *L,
                                const int32_t *m, int32_t P, double *rho_out, void *stream);
 
+/* Configurational virial tensor W_ab = -dU/d eps_ab of the current
+ * positions under the affine map r -> (1 + eps) r of positions and box (r_c
+ * and the SOG fixed): the near field (+ WCA) sum over pairs r_ij,a F_ij,b
+ * in FP64, plus the random-batch estimate of the far field on the k-set
+ * m[P][3] (host or device): each sampled k weighted as in the energy (Eq.
+ * 3.24), pi^{3/2} S / (2 P V) |rho(k)|^2, times
+ * delta_ab + 2 k_a k_b dF~/d(k^2) / F~ (Eq. 3.5), which is unbiased for the
+ * exact far virial.  W_out[9] (host or device) row-major and symmetric; the
+ * pressure is (2K + trace W) / (3V).  Single system; rebuilds the cell list;
+ * synchronises.  The boundary term is not included. */
+rbsog_status rbsog_compute_virial(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *W_out);
+
 /* Roofline denominators measured on `device` by short microbenchmarks (not
  * part of the method): out[0] MUFU sin/cos results per second (each of sin
  * and cos counts one), out[1] FP32 FMA per second, out[2] FP64 FMA per

@@ -24,7 +24,7 @@ STATUS = {0: "RBSOG_OK", 1: "RBSOG_EINVAL", 2: "RBSOG_ENOMEM", 3: "RBSOG_ECUDA",
 EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_state",
            "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_get_energies",
            "rbsog_get_kseq", "rbsog_rho", "rbsog_get_cells", "rbsog_set_profiling",
-           "rbsog_get_cursor", "rbsog_restore", "rbsog_step_io", "rbsog_rho_noalloc", "rbsog_measure_peaks",
+           "rbsog_get_cursor", "rbsog_restore", "rbsog_step_io", "rbsog_compute_virial", "rbsog_rho_noalloc", "rbsog_measure_peaks",
            "rbsog_batch_create", "rbsog_batch_set_params", "rbsog_batch_set_state", "rbsog_batch_restore",
            "rbsog_batch_get_state", "rbsog_batch_get_energies", "rbsog_batch_get_kseq", "rbsog_batch_step",
            "rbsog_batch_autotune", "rbsog_batch_rdf", "rbsog_rdf",
@@ -83,6 +83,7 @@ def _load():
         "rbsog_get_cursor": [P, C.POINTER(C.c_int64)],
         "rbsog_restore": [P, P, C.c_int64, C.c_int64],
         "rbsog_step_io": [P, P, P, P, P, C.c_int64, C.c_int64, C.c_int64, P, P, P],
+        "rbsog_compute_virial": [P, P, C.c_int32, P],
         "rbsog_get_kseq": [P, C.c_int64, C.c_int64, P],
         "rbsog_rho": [P, P, C.c_int32, P],
         "rbsog_get_cells": [P, P, P, P],
@@ -210,6 +211,14 @@ def rbsog_step_io(ctx, q, x, v, f, kset_cursor: int, step: int, nsteps: int, x_o
                   f_out=None):
     _check(ctx, _lib.rbsog_step_io(ctx, _ptr(q), _ptr(x), _ptr(v), _ptr(f), int(kset_cursor), int(step),
                                    int(nsteps), _ptr(x_out), _ptr(v_out), _ptr(f_out)))
+
+
+def rbsog_compute_virial(ctx, m):
+    """Virial tensor [3, 3] of the current positions with the far field on k-set m[P][3]."""
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    W = np.zeros(9)
+    _check(ctx, _lib.rbsog_compute_virial(ctx, _ptr(m), int(m.shape[0]), _ptr(W)))
+    return W.reshape(3, 3)
 
 
 def rbsog_get_energies(ctx):

@@ -1758,6 +1758,46 @@ rbsog_status rbsog_rho(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *rho_
     return leave(ctx);
 }
 
+rbsog_status rbsog_compute_virial(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *W_out) {
+    if (!ctx || !m || !W_out || P < 1) return RBSOG_EINVAL;
+    if (ctx->n_sys != 1) return fail(ctx, RBSOG_EINVAL, "rbsog_compute_virial needs a single system");
+    if (!ctx->have_params || !all_state(ctx)) return fail(ctx, RBSOG_ESTATE, "params and state required");
+    rbsog_status es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    const int64_t n = ctx->n_per[0];
+    const int M = ctx->p[0].M;
+    int32_t *m3 = nullptr;
+    int4 *m4 = nullptr;
+    double2 *part = nullptr, *rho = nullptr;
+    void *kt = nullptr;
+    double *vpart = nullptr, *dW = nullptr, *dom = nullptr, *dsl = nullptr;
+    CK(cudaMallocAsync((void **)&m3, sizeof(int32_t) * 3 * P, ctx->st));
+    CK(cudaMallocAsync((void **)&m4, sizeof(int4) * P, ctx->st));
+    CK(cudaMallocAsync((void **)&part, sizeof(double2) * (size_t)P * ctx->desc[0].n_ptiles, ctx->st));
+    CK(cudaMallocAsync((void **)&rho, sizeof(double2) * P, ctx->st));
+    CK(cudaMallocAsync(&kt, ktab_bytes(ctx->precision, P), ctx->st));
+    CK(cudaMallocAsync((void **)&vpart, sizeof(double) * 6 * (size_t)virial_blocks(n), ctx->st));
+    CK(cudaMallocAsync((void **)&dW, sizeof(double) * 9, ctx->st));
+    CK(cudaMallocAsync((void **)&dom, sizeof(double) * (M + 1), ctx->st));
+    CK(cudaMallocAsync((void **)&dsl, sizeof(double) * (M + 1), ctx->st));
+    CK(cudaMemcpyAsync(m3, m, sizeof(int32_t) * 3 * P, cudaMemcpyDefault, ctx->st));
+    CK(cudaMemcpyAsync(dom, ctx->omega.data(), sizeof(double) * (M + 1), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(dsl, ctx->s.data(), sizeof(double) * (M + 1), cudaMemcpyHostToDevice, ctx->st));
+    CK(launch_m_to_int4(P, m3, m4, ctx->st));
+    const BatchView bv = view(ctx, m4, P);
+    CK(launch_build_cells(bv, ctx->posq, ctx->cb, ctx->precision, ctx->sp64, ctx->sp32, ctx->st, prof_of(ctx)));
+    CK(launch_rho_sweep(ctx->precision, bv, ctx->sp64, ctx->sp32, part, ctx->st, prof_of(ctx)));
+    CK(launch_rho_combine(ctx->precision, bv, part, rho, kt, ctx->st, prof_of(ctx)));
+    CK(launch_virial(ctx->d_desc, n, ctx->nsog, ctx->cb.start, ctx->cb.perm, ctx->cb.cell_of, ctx->posq, vpart, rho,
+                     m3, P, dom, dsl, M, ctx->S[0], dW, ctx->st));
+    CK(cudaMemcpyAsync(W_out, dW, sizeof(double) * 9, cudaMemcpyDefault, ctx->st));
+    for (void *ptr : {(void *)m3, (void *)m4, (void *)part, (void *)rho, kt, (void *)vpart, (void *)dW, (void *)dom,
+                      (void *)dsl})
+        CK(cudaFreeAsync(ptr, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return leave(ctx);
+}
+
 rbsog_status rbsog_get_cells(rbsog_ctx *ctx, int32_t *cell_start, int32_t *perm, int32_t *nbr) {
     if (!ctx) return RBSOG_EINVAL;
     if (ctx->n_sys != 1) return fail(ctx, RBSOG_EINVAL, "rbsog_get_cells needs a single system");

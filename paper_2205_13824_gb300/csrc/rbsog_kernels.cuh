@@ -353,6 +353,17 @@ cudaError_t launch_kick(const BatchView &bv, double4_32a *vel, const double4_32a
 cudaError_t launch_finalize(const BatchView &bv, const double2 *epart, const double2 *rho, const double *kpart,
                             int with_kinetic, double *energy, int64_t advance, cudaStream_t st,
                             const Prof *prof);
+// ---- virial (k_virial.cu) ------------------------------------------------------
+// Configurational virial W[9] (row-major, symmetric) of system 0: near field
+// (+ WCA) from the cell list (start, perm, cell_of) and the FP64 positions,
+// far field from rho[P] of the k-set m3[P][3] and the SOG (omega, sl of
+// M + 1 terms, normaliser S).  part: virial_blocks(n) * 6 doubles of scratch.
+int32_t virial_blocks(int64_t n);
+cudaError_t launch_virial(const SysDesc *sysd, int64_t n, const NearSog &sog, const int32_t *start,
+                          const int32_t *perm, const int32_t *cell_of, const double4_32a *posq, double *part,
+                          const double2 *rho, const int32_t *m3, int32_t P, const double *omega, const double *sl,
+                          int32_t M, double S, double *W, cudaStream_t st);
+
 // ---- boundary terms (k_boundary.cu) ---------------------------------------------
 // Zero-frequency term of systems with a non-tinfoil boundary: dipole moment
 // from the caller-order positions, U0 into energy[sys * kNumEnergy + 7], the
