@@ -43,7 +43,8 @@ class OrcCoreShell(C.Structure):
 
 
 class OrcEnergies(C.Structure):
-    _fields_ = [("U_near", _d), ("U_far", _d), ("U_self", _d), ("U_wca", _d), ("K", _d), ("T", _d)]
+    _fields_ = [("U_near", _d), ("U_far", _d), ("U_self", _d), ("U_wca", _d), ("K", _d), ("T", _d),
+                ("U_th", _d)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

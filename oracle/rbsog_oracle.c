@@ -1035,7 +1035,13 @@ int orc_md(int64_t n, const double *q, double *x, double *v, double *f,
     return orc_md_thermo(n, q, x, v, f, sys, S, P, kseq, nsteps, dt, mass, T0, tau, have_force, e_steps, 0, 0, 0);
 }
 
-/* As orc_md, with thermostat 1 (tau > 0): Langevin dynamics with friction
+/* As orc_md, with thermostat 2 (tau > 0): Nose-Hoover, thermostat mass
+ * Q = g T0 tau^2 (g = 3N - 3), propagated by the symmetric Trotter
+ * splitting; each step is velocity Verlet followed by two thermostat
+ * half-steps (its own end and the next step's start), each: xi += dt/4 G;
+ * v *= e^{-xi dt/2}; eta += dt/2 xi; xi += dt/4 G, with G = (2K - g T0)/Q
+ * at the current K.  U + K + (1/2) Q xi^2 + g T0 eta is conserved.
+ * With thermostat 1 (tau > 0): Langevin dynamics with friction
  * 1/tau in the BAOAB splitting, per step: v += dt/2 F/m; x += dt/2 v;
  * v = c1 v + c2 z with c1 = e^{-dt/tau}, c2 = sqrt((1 - c1^2) T0/m) and z the
  * noise of orc_langevin_noise for the step counter step0 + t; x += dt/2 v;
@@ -1045,6 +1051,10 @@ int orc_md_thermo(int64_t n, const double *q, double *x, double *v, double *f,
                   int64_t nsteps, double dt, double mass, double T0, double tau,
                   int have_force, orc_energies *e_steps, int32_t thermostat, uint64_t seed, int64_t step0) {
     const int langevin = thermostat == 1 && tau > 0.0;
+    const int nh = thermostat == 2 && tau > 0.0;
+    const double g_dof = 3.0 * (double)n - 3.0;
+    const double Qnh = g_dof * T0 * tau * tau;
+    double xi = 0.0, eta = 0.0;
     const double c1 = langevin ? exp(-dt / tau) : 1.0;
     const double c2 = langevin ? sqrt((1.0 - c1 * c1) * T0 / mass) : 0.0;
     int64_t used = 0;
@@ -1076,7 +1086,23 @@ int orc_md_thermo(int64_t n, const double *q, double *x, double *v, double *f,
         double K = 0.0;
         for (int64_t i = 0; i < 3 * n; ++i) K += 0.5 * mass * v[i] * v[i];
         double T = 2.0 * K / (3.0 * (double)n - 3.0);
-        if (!langevin && tau > 0.0 && T > 0.0) {
+        if (nh) {
+            /* two consecutive half-steps of the thermostat (the end of this
+             * step and the start of the next in the symmetric splitting) */
+            for (int h = 0; h < 2; ++h) {
+                xi += 0.25 * dt * (2.0 * K - g_dof * T0) / Qnh;
+                const double sc = exp(-0.5 * dt * xi);
+                for (int64_t i = 0; i < 3 * n; ++i) v[i] *= sc;
+                K *= sc * sc;
+                eta += 0.5 * dt * xi;
+                xi += 0.25 * dt * (2.0 * K - g_dof * T0) / Qnh;
+            }
+            K = 0.0;
+            for (int64_t i = 0; i < 3 * n; ++i) K += 0.5 * mass * v[i] * v[i];
+            T = 2.0 * K / (3.0 * (double)n - 3.0);
+        }
+        e.U_th = nh ? 0.5 * Qnh * xi * xi + g_dof * T0 * eta : 0.0;
+        if (!langevin && !nh && tau > 0.0 && T > 0.0) {
             double lam = sqrt(1.0 + dt / tau * (T0 / T - 1.0));
             for (int64_t i = 0; i < 3 * n; ++i) v[i] *= lam;
             K = 0.0;

@@ -56,6 +56,7 @@ typedef struct {
     double U_wca;    /* soft-repulsion energy                                 */
     double K;        /* kinetic energy (only filled by the MD driver)         */
     double T;        /* instantaneous temperature 2K/(3N-3)                   */
+    double U_th;     /* Nose-Hoover thermostat energy (1/2) Q xi^2 + g T0 eta  */
 } orc_energies;
 
 /* ---- sum-of-Gaussians decomposition (Sec. 2, Eqs. 2.5-2.11) ------------- */
