@@ -100,7 +100,14 @@ typedef struct {
                                  c2 = sqrt((1 - c1^2) T_target/m); x += dt/2 v; forces;
                                  v += dt/2 F/m).  The noise z of particle i in the step with
                                  step counter t is Philox4x64-10 (key (seed, 2^63 + 1),
-                                 counter (t, i, 0, 0)) through Box-Muller                   */
+                                 counter (t, i, 0, 0)) through Box-Muller;
+                                 2 Nose-Hoover with thermostat mass Q = g T_target tau_T^2
+                                 (g = 3N - 3) in the symmetric Trotter splitting: each step
+                                 is velocity Verlet followed by the end half of its
+                                 thermostat update and the start half of the next, each
+                                 xi += dt/4 G; v *= e^{-xi dt/2}; eta += dt/2 xi;
+                                 xi += dt/4 G with G = (2K - g T_target)/Q; set_state
+                                 starts xi = eta = 0; U + K + U_th is conserved            */
 } rbsog_params;
 
 /* Energies of the last force evaluation (Eqs. 3.1, 3.6-3.8) and kinetic state. */
@@ -112,6 +119,7 @@ typedef struct {
     double K;      /* kinetic energy after the last completed step                        */
     double T;      /* 2K / (3N - 3)                                                       */
     double U_bound; /* zero-frequency (boundary) term; 0 for tinfoil                      */
+    double U_th;   /* Nose-Hoover thermostat energy (1/2) Q xi^2 + g T_target eta; 0 otherwise */
 } rbsog_energies;
 
 /* Solved SOG decomposition (Eqs. 2.8-2.11) and the normaliser S (Eq. 3.16). */

@@ -52,7 +52,8 @@ class rbsog_params(C.Structure):
 
 class rbsog_energies(C.Structure):
     _fields_ = [("U_near", C.c_double), ("U_far", C.c_double), ("U_self", C.c_double),
-                ("U_wca", C.c_double), ("K", C.c_double), ("T", C.c_double), ("U_bound", C.c_double)]
+                ("U_wca", C.c_double), ("K", C.c_double), ("T", C.c_double), ("U_bound", C.c_double),
+                ("U_th", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -234,6 +234,26 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BatchView bv, const do
             lam = sqrt(1.0 + a.dt / a.tau * (a.T0 / T - 1.0));
             K *= lam * lam;
             T *= lam * lam;
+        } else if (a.thermostat == 2 && a.tau > 0.0) {
+            // Nose-Hoover: the end half of this step's thermostat update and
+            // the start half of the next one (symmetric Trotter splitting),
+            // each xi += dt/4 G; v *= e^{-xi dt/2}; eta += dt/2 xi;
+            // xi += dt/4 G with G = (2K - g T0) / Q; the velocity factor is
+            // applied by the rescale kernel
+            const double g = 3.0 * (double)a.n - 3.0;
+            double xi = en[8], eta = en[9];
+            for (int h = 0; h < 2; ++h) {
+                xi += 0.25 * a.dt * (2.0 * K - g * a.T0) / a.nh_Q;
+                const double sc = exp(-0.5 * a.dt * xi);
+                lam *= sc;
+                K *= sc * sc;
+                eta += 0.5 * a.dt * xi;
+                xi += 0.25 * a.dt * (2.0 * K - g * a.T0) / a.nh_Q;
+            }
+            T = 2.0 * K / g;
+            en[8] = xi;
+            en[9] = eta;
+            en[10] = 0.5 * a.nh_Q * xi * xi + g * a.T0 * eta;
         }
         en[4] = K;
         en[5] = T;

@@ -692,7 +692,7 @@ rbsog_status enqueue_step_tail(rbsog_ctx *ctx) {
     CK(launch_kick(bv, ctx->vel, ctx->force, ctx->kpart, ctx->st, pf));
     CK(launch_finalize(bv, ctx->epart, ctx->rho, ctx->kpart, 1, ctx->energy, 1, ctx->st, pf));
     bool thermo = false;
-    for (auto &pp : ctx->p) thermo = thermo || (pp.tau_T > 0.0 && pp.thermostat == 0);
+    for (auto &pp : ctx->p) thermo = thermo || (pp.tau_T > 0.0 && pp.thermostat != 1);
     if (thermo) CK(launch_rescale(bv, ctx->vel, ctx->energy, ctx->st, pf));
     CK(launch_step_done(bv, ctx->st, pf));
     return RBSOG_OK;
@@ -1003,8 +1003,9 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         if (q.n_ksets < 1) return fail(ctx, RBSOG_EINVAL, "system %d: n_ksets must be >= 1", s);
         if (!(q.r_c > 0.0)) return fail(ctx, RBSOG_EINVAL, "system %d: r_c must be > 0", s);
         if (!(q.mass > 0.0)) return fail(ctx, RBSOG_EINVAL, "system %d: mass must be > 0", s);
-        if (q.thermostat < 0 || q.thermostat > 1)
-            return fail(ctx, RBSOG_EINVAL, "system %d: thermostat must be 0 (Berendsen) or 1 (Langevin)", s);
+        if (q.thermostat < 0 || q.thermostat > 2)
+            return fail(ctx, RBSOG_EINVAL,
+                        "system %d: thermostat must be 0 (Berendsen), 1 (Langevin) or 2 (Nose-Hoover)", s);
         if (q.near_kernel < 0 || q.near_kernel > 1)
             return fail(ctx, RBSOG_EINVAL, "system %d: near_kernel must be 0 (table) or 1 (core-shell)", s);
         if (s > 0 && (q.near_kernel != p[0].near_kernel || q.r_in != p[0].r_in))
@@ -1137,6 +1138,7 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         d.lv_c2 = d.thermostat == 1 ? std::sqrt((1.0 - d.lv_c1 * d.lv_c1) * q.T_target / q.mass) : 0.0;
         d.lv_seed = q.seed;
         d.half_mass_f = (float)(0.5 * q.mass);
+        d.nh_Q = d.thermostat == 2 ? (3.0 * (double)d.n - 3.0) * q.T_target * q.tau_T * q.tau_T : 0.0;
         d.T0 = q.T_target;
         d.tau = q.tau_T;
         ctx->chain_len[s] = q.chain_len > 0 ? q.chain_len : 256;
@@ -1396,6 +1398,8 @@ rbsog_status rbsog_batch_set_state(rbsog_batch *ctx, int32_t sys, const double *
     if (v) CK(launch_pack(n, sv, nullptr, ctx->vel + off, 0, ctx->p[sys].L, ctx->st));
     else CK(cudaMemsetAsync(ctx->vel + off, 0, sizeof(double4_32a) * n, ctx->st));
     CK(cudaMemsetAsync(ctx->step_ctr + sys, 0, sizeof(int64_t), ctx->st));
+    // a new state starts the Nose-Hoover variables xi, eta and their energy at zero
+    CK(cudaMemsetAsync(ctx->energy + (int64_t)sys * kNumEnergy + 8, 0, sizeof(double) * 3, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));   // the caller may reuse its buffers
     // neighbour lists stay valid while every particle is within skin/2 of
     // its position at the last build: the displacement test of the next
@@ -1451,6 +1455,7 @@ rbsog_status rbsog_compute_forces(rbsog_ctx *ctx, const int32_t *m_kset, double 
         e_out->K = ctx->h_energy[4];
         e_out->T = ctx->h_energy[5];
         e_out->U_bound = ctx->h_energy[7];
+        e_out->U_th = ctx->h_energy[10];
     }
     return leave(ctx);
 }
@@ -1692,6 +1697,7 @@ rbsog_status rbsog_batch_get_energies(rbsog_batch *ctx, int32_t sys, rbsog_energ
     e->U_self = ctx->h_energy[2];
     e->U_wca = ctx->h_energy[3];
     e->U_bound = ctx->h_energy[7];
+    e->U_th = ctx->h_energy[10];
     e->K = ctx->h_energy[4];
     e->T = ctx->h_energy[5];
     return leave(ctx);

@@ -134,11 +134,12 @@ struct SysDesc {
     double dt, inv_mass, mass, T0, tau;
     double half_dt_inv_mass;   // dt / (2 m): the half kick's factor
     int32_t boundary;          // zero-frequency term: 0 tinfoil, 1 spherical, 2 planar (z)
-    int32_t thermostat;        // with tau > 0: 0 Berendsen rescale, 1 Langevin (BAOAB)
+    int32_t thermostat;        // with tau > 0: 0 Berendsen rescale, 1 Langevin (BAOAB), 2 Nose-Hoover
     double half_dt;            // dt / 2
     double lv_c1, lv_c2;       // Langevin: v <- c1 v + c2 z, c1 = e^{-dt/tau}, c2 = sqrt((1 - c1^2) T0 / m)
     uint64_t lv_seed;          // key of the Langevin noise
     float half_mass_f;         // m / 2 (FP32C kinetic-energy terms)
+    double nh_Q;               // Nose-Hoover thermostat mass g T0 tau^2, g = 3N - 3
 };
 
 // Work tables map a launch's blocks to (system, local block).
@@ -335,9 +336,10 @@ cudaError_t launch_far_scatter(int precision, const BatchView &bv, const double4
 size_t ktab_bytes(int precision, int64_t nk);
 
 // ---- integrator and reductions (k_md.cu) --------------------------------------
-// Device energies per system, 8 doubles: [0] U_near [1] U_far [2] U_self
-// [3] U_wca [4] K [5] T [6] lambda
-constexpr int kNumEnergy = 8;
+// Device energies per system, 12 doubles: [0] U_near [1] U_far [2] U_self
+// [3] U_wca [4] K [5] T [6] lambda (velocity factor of the thermostat)
+// [7] U_bound [8] Nose-Hoover xi [9] eta [10] (1/2) Q xi^2 + g T0 eta [11] spare
+constexpr int kNumEnergy = 12;
 // With sp32c non-null (neighbour-list path) it also writes the fixed-point
 // caller-order positions and runs the displacement test (fixed_pack_check).
 cudaError_t launch_kick_drift(const BatchView &bv, double4_32a *posq, double4_32a *vel,

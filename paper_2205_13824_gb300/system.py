@@ -33,7 +33,7 @@ def make_params(L, P, r_c=3.0, b=DEFAULT_B, sigma=0.0, omega0=0.0, M=DEFAULT_M, 
     p.near_kernel = {"table": 0, "coreshell": 1}[near_kernel] \
         if isinstance(near_kernel, str) else int(near_kernel)
     p.r_in = float(r_in)
-    p.thermostat = {"berendsen": 0, "langevin": 1}[thermostat] \
+    p.thermostat = {"berendsen": 0, "langevin": 1, "nose-hoover": 2}[thermostat] \
         if isinstance(thermostat, str) else int(thermostat)
     return p
 
