@@ -133,6 +133,12 @@ def lib():
             L.orc_rdf_counts.argtypes = [_i64, _pd, _pd, _d, _i32, C.POINTER(_u64)]
             L.orc_rdf_counts.restype = C.c_int
             L.orc_rdf_g.argtypes = [C.POINTER(_u64), _i32, _d, _i64, _i64, _pd]
+            L.orc_msd_vacf.argtypes = [_i64, _i64, _pd, _pd, _pd, _i32, _i32, _pd, _pd, C.POINTER(_i64)]
+            L.orc_msd_vacf.restype = C.c_int
+            L.orc_pressure.argtypes = [_i64, _pd, _pd, _pd, _d, C.POINTER(OrcSys), _d, _i32, _pi32, _pd]
+            L.orc_pressure.restype = C.c_int
+            L.orc_green_kubo.argtypes = [_i64, _pd, _d, _d, _d, _i32, _pd, C.POINTER(_d)]
+            L.orc_green_kubo.restype = C.c_int
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -371,6 +377,49 @@ def virial(sys_: System, q, x, S=0.0, m=None):
         m = _i32a(m)
         lib().orc_virial(x.shape[0], _p(q), _p(x), C.byref(sys_.c), float(S), m.shape[0], _p(m, _pi32), _p(W))
     return W.reshape(3, 3)
+
+
+def msd_vacf(x_frames, v_frames, L, n_lags: int, origin_every: int = 1):
+    """Appendix A's MSD and VACF over frames x[f, n, 3] (folded positions)
+    and v[f, n, 3], averaged over particles and the time origins 0,
+    origin_every, ...; returns (msd[n_lags], vacf[n_lags], count[n_lags])."""
+    x, v = _f64(x_frames), _f64(v_frames)
+    Lv = _f64(np.broadcast_to(np.asarray(L, float), (3,)).copy())
+    msd, vacf = np.zeros(n_lags), np.zeros(n_lags)
+    cnt = np.zeros(n_lags, dtype=np.int64)
+    if lib().orc_msd_vacf(x.shape[1], x.shape[0], _p(x), _p(v), _p(Lv), int(n_lags), int(origin_every),
+                          _p(msd), _p(vacf), cnt.ctypes.data_as(C.POINTER(_i64))):
+        raise ValueError("bad sizes")
+    return msd, vacf, cnt
+
+
+def pressure(sys_: System, q, x, v, mass, S, m):
+    """Pressure tensor (1/V) sum (m v v + r f) of Appendix A, the virial part
+    the random-batch estimate on k-set m (or exact for m None)."""
+    q, x, v = _f64(q), _f64(x), _f64(v)
+    Pt = np.zeros(9)
+    if m is None:
+        rc_ = lib().orc_pressure(x.shape[0], _p(q), _p(x), _p(v), float(mass), C.byref(sys_.c), float(S), 0,
+                                 None, _p(Pt))
+    else:
+        m = _i32a(m)
+        rc_ = lib().orc_pressure(x.shape[0], _p(q), _p(x), _p(v), float(mass), C.byref(sys_.c), float(S),
+                                 m.shape[0], _p(m, _pi32), _p(Pt))
+    if rc_:
+        raise ValueError("fewer than 3 cells per side")
+    return Pt.reshape(3, 3)
+
+
+def green_kubo(P_series, dt, V, T, max_lag):
+    """Green-Kubo viscosity of Appendix A from a pressure-tensor series
+    [n, 3, 3]; returns (acf[max_lag] summed over a <= b, C)."""
+    Pt = _f64(np.asarray(P_series, float).reshape(-1, 9))
+    acf = np.zeros(int(max_lag))
+    Cv = _d(0.0)
+    if lib().orc_green_kubo(Pt.shape[0], _p(Pt), float(dt), float(V), float(T), int(max_lag), _p(acf),
+                            C.byref(Cv)):
+        raise ValueError("bad sizes")
+    return acf, Cv.value
 
 
 def boundary(q, x, L, kind: int, lB: float = 1.0):

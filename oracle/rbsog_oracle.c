@@ -1206,3 +1206,85 @@ void orc_rdf_g(const uint64_t *counts, int32_t nbins, double L, int64_t n_pos, i
             g[t * nbins + k] = expect > 0.0 ? mult[t] * (double)counts[t * nbins + k] / expect : 0.0;
         }
 }
+
+/* ---- time-correlation observables (Appendix A) ------------------------- */
+
+static double min_image1(double d, double L) { return d - L * nearbyint(d / L); }
+
+/* Appendix A's MSD and VACF, each origin and lag summed over the particles in
+ * index order; the frames are unwrapped first. */
+int orc_msd_vacf(int64_t n, int64_t n_frames, const double *x, const double *v, const double *L,
+                 int32_t n_lags, int32_t origin_every, double *msd, double *vacf, int64_t *count) {
+    if (n < 1 || n_frames < 1 || n_lags < 1 || origin_every < 1) return -1;
+    double *u = (double *)malloc(sizeof(double) * 3 * n * n_frames);
+    if (!u) return -1;
+    for (int64_t k = 0; k < 3 * n; ++k) u[k] = x[k];
+    for (int64_t f = 1; f < n_frames; ++f)
+        for (int64_t i = 0; i < n; ++i)
+            for (int d = 0; d < 3; ++d) {
+                const int64_t a = (f * n + i) * 3 + d, b = ((f - 1) * n + i) * 3 + d;
+                u[a] = u[b] + min_image1(x[a] - x[b], L[d]);
+            }
+    for (int32_t t = 0; t < n_lags; ++t) {
+        msd[t] = vacf[t] = 0.0;
+        count[t] = 0;
+    }
+    for (int64_t o = 0; o < n_frames; o += origin_every)
+        for (int32_t t = 0; t < n_lags && o + t < n_frames; ++t) {
+            double sm = 0.0, sv = 0.0;
+            for (int64_t i = 0; i < n; ++i)
+                for (int d = 0; d < 3; ++d) {
+                    const int64_t a = ((o + t) * n + i) * 3 + d, b = (o * n + i) * 3 + d;
+                    const double dr = u[a] - u[b];
+                    sm += dr * dr;
+                    sv += v[b] * v[a];
+                }
+            msd[t] += sm;
+            vacf[t] += sv;
+            count[t] += 1;
+        }
+    for (int32_t t = 0; t < n_lags; ++t)
+        if (count[t] > 0) {
+            msd[t] /= (double)count[t] * (double)n;
+            vacf[t] /= (double)count[t] * (double)n;
+        }
+    free(u);
+    return 0;
+}
+
+int orc_pressure(int64_t n, const double *q, const double *x, const double *v, double mass,
+                 const orc_sys *sys, double S, int32_t P, const int32_t *kset, double *Pt) {
+    double W[9];
+    const int rc = orc_virial(n, q, x, sys, S, P, kset, W);
+    if (rc) return rc;
+    const double V = sys->L[0] * sys->L[1] * sys->L[2];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double k = 0.0;
+            for (int64_t i = 0; i < n; ++i) k += mass * v[3 * i + a] * v[3 * i + b];
+            Pt[3 * a + b] = (k + W[3 * a + b]) / V;
+        }
+    return 0;
+}
+
+int orc_green_kubo(int64_t n_samples, const double *Pt, double dt, double V, double T, int32_t max_lag,
+                   double *acf, double *C) {
+    if (n_samples < 2 || max_lag < 2 || max_lag > n_samples || T <= 0.0) return -1;
+    static const int comp[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int32_t t = 0; t < max_lag; ++t) acf[t] = 0.0;
+    for (int c = 0; c < 6; ++c) {
+        const int e = 3 * comp[c][0] + comp[c][1];
+        double mean = 0.0;
+        for (int64_t s = 0; s < n_samples; ++s) mean += Pt[9 * s + e];
+        mean /= (double)n_samples;
+        for (int32_t t = 0; t < max_lag; ++t) {
+            double a = 0.0;
+            for (int64_t o = 0; o + t < n_samples; ++o) a += (Pt[9 * o + e] - mean) * (Pt[9 * (o + t) + e] - mean);
+            acf[t] += a / (double)(n_samples - t);
+        }
+    }
+    double integral = 0.0;
+    for (int32_t t = 0; t + 1 < max_lag; ++t) integral += 0.5 * dt * (acf[t] + acf[t + 1]);
+    *C = V / (6.0 * T) * integral;
+    return 0;
+}

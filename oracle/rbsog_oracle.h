@@ -145,6 +145,31 @@ void orc_langevin_noise(uint64_t seed, int64_t t, int64_t i, double z[3]);
 int  orc_rdf_counts(int64_t n, const double *q, const double *x, double L, int32_t nbins, uint64_t *counts);
 void orc_rdf_g(const uint64_t *counts, int32_t nbins, double L, int64_t n_pos, int64_t n_neg, double *g);
 
+/* ---- time-correlation observables (Appendix A) ------------------------- */
+/* MSD eta(t) = <|r(t0 + t) - r(t0)|^2> and VACF <v(t0) . v(t0 + t)> over the
+ * frames x[f][n][3] (positions folded into [0, L)) and v[f][n][3], f <
+ * n_frames, averaged over the particles and the time origins t0 = 0,
+ * origin_every, 2 origin_every, ... with t0 + t < n_frames; lags t < n_lags in
+ * frames.  Positions are unwrapped by adding the minimum-image displacement
+ * between consecutive frames.  count[t] = origins that reached lag t;
+ * msd[t] = vacf[t] = 0 where count[t] = 0.  Returns -1 on bad sizes. */
+int orc_msd_vacf(int64_t n, int64_t n_frames, const double *x, const double *v, const double *L,
+                 int32_t n_lags, int32_t origin_every, double *msd, double *vacf, int64_t *count);
+
+/* Pressure tensor of Appendix A, P_ab = (1/V) sum_i (m v_ia v_ib + r_ia f_ib),
+ * the second sum read as the configurational virial W_ab of orc_virial. */
+int orc_pressure(int64_t n, const double *q, const double *x, const double *v, double mass,
+                 const orc_sys *sys, double S, int32_t P, const int32_t *kset, double *Pt);
+
+/* Green-Kubo shear viscosity of Appendix A: C = V/(6 T) sum_{a<=b} of the
+ * integral of <dP_ab(t) dP_ab(0)>, dP the fluctuation of the series
+ * Pt[s][9] (row-major tensors, s < n_samples, spacing dt) about its mean,
+ * each autocorrelation averaged over all origins, acf[t] = the sum over the
+ * six components at lag t < max_lag, the integral by the trapezoid rule up
+ * to lag max_lag - 1.  Returns -1 on bad sizes. */
+int orc_green_kubo(int64_t n_samples, const double *Pt, double dt, double V, double T, int32_t max_lag,
+                   double *acf, double *C);
+
 int  orc_num_threads(void);
 
 #ifdef __cplusplus
