@@ -280,6 +280,57 @@ rbsog_status rbsog_rho_noalloc(int64_t n, const double *q, const double *x, cons
  * synchronises.  The boundary term is not included. */
 rbsog_status rbsog_compute_virial(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *W_out);
 
+/* Pressure tensor of Appendix A, P_ab = (1/V) sum_i (m v_ia v_ib + r_ia f_ib),
+ * the second sum read as the configurational virial W_ab of
+ * rbsog_compute_virial on the k-set m[P][3] (host or device), the first from
+ * the current velocities; FP64 fixed-order sums.  P_out[9] (host or device)
+ * row-major.  Single system; synchronises.  RBSOG_EINVAL for a NULL pointer,
+ * P < 1 or a batch of several systems; RBSOG_ESTATE before set_state. */
+rbsog_status rbsog_compute_pressure(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *P_out);
+
+/* Time-correlation observables of Appendix A on the device (single system):
+ * the mean-squared displacement eta_msd(t) = <|r(t0 + t) - r(t0)|^2> and the
+ * velocity autocorrelation <v(t0) . v(t0 + t)>, averaged over the particles
+ * and the time origins t0.  Time is counted in samples: each
+ * rbsog_observe_sample takes the current positions and velocities as the
+ * next frame (enqueued on the context's stream, no synchronisation), so call
+ * it after every rbsog_step(ctx, s) to sample every s steps.  Positions are
+ * unwrapped by adding the minimum-image displacement since the previous
+ * sample (a particle must move less than half a box edge between samples).
+ * Frames 0, origin_every, 2 origin_every, ... are time origins; each sample
+ * adds, for every origin less than n_lags frames back, one FP64 particle sum
+ * (fixed order) to the accumulator of its lag.
+ *
+ * rbsog_observe_start allocates 2 ceil(n_lags / origin_every) origin slots
+ * of 32 bytes per particle plus per-particle unwrapping state, clears the
+ * accumulators and makes the current state the next sample's frame 0; call
+ * it again after rbsog_set_state.  RBSOG_EINVAL for n_lags < 1,
+ * origin_every < 1 or more than 64 origins kept (ceil(n_lags /
+ * origin_every) > 64), or a batch of several systems.
+ * rbsog_observe_result writes msd[n_lags], vacf[n_lags] and count[n_lags]
+ * (origins that reached each lag; 0 gives msd = vacf = 0), each host or
+ * device, any of them NULL to skip; synchronises.  Sample and result return
+ * RBSOG_ESTATE before rbsog_observe_start. */
+rbsog_status rbsog_observe_start(rbsog_ctx *ctx, int32_t n_lags, int32_t origin_every);
+rbsog_status rbsog_observe_sample(rbsog_ctx *ctx);
+rbsog_status rbsog_observe_result(rbsog_ctx *ctx, double *msd, double *vacf, int64_t *count);
+
+/* Green-Kubo shear viscosity of Appendix A from a pressure-tensor series
+ * P_series[n_samples][9] (row-major tensors spaced dt apart, host or
+ * device; e.g. from rbsog_compute_pressure):
+ * C = V / (6 k_B T) sum_{a <= b} of the integral over t of
+ * <dP_ab(t0 + t) dP_ab(t0)>, where dP_ab is the component's fluctuation
+ * about its mean over the series, each autocorrelation averaged over all
+ * origins t0 with t0 + t < n_samples and integrated by the trapezoid rule
+ * over the lags 0 .. max_lag - 1.  acf_out[max_lag] (host or device, NULL to
+ * skip) receives the summed autocorrelation per lag, *C_out (host) the
+ * integral.  Context-free; work on `stream` (cudaStream_t, NULL = legacy
+ * default stream), which the call synchronises.  RBSOG_EINVAL for
+ * n_samples < 2, max_lag outside [2, n_samples], non-positive dt, V or T,
+ * or a NULL P_series or C_out; RBSOG_ECUDA if a CUDA call fails. */
+rbsog_status rbsog_green_kubo(const double *P_series, int64_t n_samples, double dt, double V, double T,
+                              int32_t max_lag, double *acf_out, double *C_out, void *stream);
+
 /* Roofline denominators measured on `device` by short microbenchmarks (not
  * part of the method): out[0] MUFU sin/cos results per second (each of sin
  * and cos counts one), out[1] FP32 FMA per second, out[2] FP64 FMA per

@@ -25,6 +25,8 @@ EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_stat
            "rbsog_compute_forces", "rbsog_step", "rbsog_get_state", "rbsog_get_energies",
            "rbsog_get_kseq", "rbsog_rho", "rbsog_get_cells", "rbsog_set_profiling",
            "rbsog_get_cursor", "rbsog_restore", "rbsog_step_io", "rbsog_compute_virial", "rbsog_rho_noalloc", "rbsog_measure_peaks",
+           "rbsog_compute_pressure", "rbsog_observe_start", "rbsog_observe_sample", "rbsog_observe_result",
+           "rbsog_green_kubo",
            "rbsog_batch_create", "rbsog_batch_set_params", "rbsog_batch_set_state", "rbsog_batch_restore",
            "rbsog_batch_get_state", "rbsog_batch_get_energies", "rbsog_batch_get_kseq", "rbsog_batch_step",
            "rbsog_batch_autotune", "rbsog_batch_rdf", "rbsog_rdf",
@@ -85,6 +87,12 @@ def _load():
         "rbsog_restore": [P, P, C.c_int64, C.c_int64],
         "rbsog_step_io": [P, P, P, P, P, C.c_int64, C.c_int64, C.c_int64, P, P, P],
         "rbsog_compute_virial": [P, P, C.c_int32, P],
+        "rbsog_compute_pressure": [P, P, C.c_int32, P],
+        "rbsog_observe_start": [P, C.c_int32, C.c_int32],
+        "rbsog_observe_sample": [P],
+        "rbsog_observe_result": [P, P, P, P],
+        "rbsog_green_kubo": [P, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int32, P,
+                             C.POINTER(C.c_double), P],
         "rbsog_get_kseq": [P, C.c_int64, C.c_int64, P],
         "rbsog_rho": [P, P, C.c_int32, P],
         "rbsog_get_cells": [P, P, P, P],
@@ -220,6 +228,44 @@ def rbsog_compute_virial(ctx, m):
     W = np.zeros(9)
     _check(ctx, _lib.rbsog_compute_virial(ctx, _ptr(m), int(m.shape[0]), _ptr(W)))
     return W.reshape(3, 3)
+
+
+def rbsog_compute_pressure(ctx, m):
+    """Pressure tensor [3, 3] (kinetic + virial over V), the far field on k-set m[P][3]."""
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    Pt = np.zeros(9)
+    _check(ctx, _lib.rbsog_compute_pressure(ctx, _ptr(m), int(m.shape[0]), _ptr(Pt)))
+    return Pt.reshape(3, 3)
+
+
+def rbsog_observe_start(ctx, n_lags: int, origin_every: int = 1):
+    _check(ctx, _lib.rbsog_observe_start(ctx, int(n_lags), int(origin_every)))
+
+
+def rbsog_observe_sample(ctx):
+    _check(ctx, _lib.rbsog_observe_sample(ctx))
+
+
+def rbsog_observe_result(ctx, n_lags: int):
+    """(msd[n_lags], vacf[n_lags], count[n_lags]) accumulated since rbsog_observe_start."""
+    msd, vacf = np.zeros(n_lags), np.zeros(n_lags)
+    cnt = np.zeros(n_lags, dtype=np.int64)
+    _check(ctx, _lib.rbsog_observe_result(ctx, _ptr(msd), _ptr(vacf), _ptr(cnt)))
+    return msd, vacf, cnt
+
+
+def rbsog_green_kubo(P_series, dt: float, V: float, T: float, max_lag: int, stream=None):
+    """(acf[max_lag], C) of a pressure-tensor series [n, 3, 3] (host array or device tensor)."""
+    if not hasattr(P_series, "data_ptr"):
+        P_series = np.ascontiguousarray(np.asarray(P_series, dtype=np.float64).reshape(-1, 9))
+    n = P_series.shape[0]
+    acf = np.zeros(int(max_lag))
+    Cv = C.c_double()
+    st = _lib.rbsog_green_kubo(_ptr(P_series), int(n), float(dt), float(V), float(T), int(max_lag), _ptr(acf),
+                               C.byref(Cv), C.c_void_p(stream))
+    if st != 0:
+        raise RBSOGError(st, "rbsog_green_kubo failed")
+    return acf, Cv.value
 
 
 def rbsog_get_energies(ctx):

@@ -132,6 +132,13 @@ struct rbsog_ctx {
     float4 *d_cstab = nullptr;           // its shell table [cs.n_tab]
     std::vector<float4> h_ltab;
     int32_t *nbr_list = nullptr, *nbr_cnt = nullptr, *list_perm = nullptr, *d_rebuild = nullptr;
+    // observables of Appendix A (rbsog_observe_*), single system
+    int32_t obs_lags = 0, obs_every = 0, obs_slots = 0;
+    int64_t obs_frame = 0;
+    double4_32a *obs_xprev = nullptr, *obs_u = nullptr, *obs_ring_u = nullptr, *obs_ring_v = nullptr;
+    double2 *obs_part = nullptr;
+    double *obs_acc = nullptr;        // [4 n_lags]: MSD sums, VACF sums, then the result
+    int64_t *obs_count = nullptr;     // [n_lags]
     // pinned host mirrors
     double *h_energy = nullptr;
     int32_t *h_err = nullptr;
@@ -1764,26 +1771,24 @@ rbsog_status rbsog_rho(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *rho_
     return leave(ctx);
 }
 
-rbsog_status rbsog_compute_virial(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *W_out) {
-    if (!ctx || !m || !W_out || P < 1) return RBSOG_EINVAL;
-    if (ctx->n_sys != 1) return fail(ctx, RBSOG_EINVAL, "rbsog_compute_virial needs a single system");
-    if (!ctx->have_params || !all_state(ctx)) return fail(ctx, RBSOG_ESTATE, "params and state required");
-    rbsog_status es = enter(ctx);
-    if (es != RBSOG_OK) return es;
+namespace {
+
+// Enqueues the virial of system 0 on the k-set m[P][3] (host or device)
+// into the device array dW[9]; its scratch is stream-ordered.
+rbsog_status virial_device(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *dW) {
     const int64_t n = ctx->n_per[0];
     const int M = ctx->p[0].M;
     int32_t *m3 = nullptr;
     int4 *m4 = nullptr;
     double2 *part = nullptr, *rho = nullptr;
     void *kt = nullptr;
-    double *vpart = nullptr, *dW = nullptr, *dom = nullptr, *dsl = nullptr;
+    double *vpart = nullptr, *dom = nullptr, *dsl = nullptr;
     CK(cudaMallocAsync((void **)&m3, sizeof(int32_t) * 3 * P, ctx->st));
     CK(cudaMallocAsync((void **)&m4, sizeof(int4) * P, ctx->st));
     CK(cudaMallocAsync((void **)&part, sizeof(double2) * (size_t)P * ctx->desc[0].n_ptiles, ctx->st));
     CK(cudaMallocAsync((void **)&rho, sizeof(double2) * P, ctx->st));
     CK(cudaMallocAsync(&kt, ktab_bytes(ctx->precision, P), ctx->st));
     CK(cudaMallocAsync((void **)&vpart, sizeof(double) * 6 * (size_t)virial_blocks(n), ctx->st));
-    CK(cudaMallocAsync((void **)&dW, sizeof(double) * 9, ctx->st));
     CK(cudaMallocAsync((void **)&dom, sizeof(double) * (M + 1), ctx->st));
     CK(cudaMallocAsync((void **)&dsl, sizeof(double) * (M + 1), ctx->st));
     CK(cudaMemcpyAsync(m3, m, sizeof(int32_t) * 3 * P, cudaMemcpyDefault, ctx->st));
@@ -1796,12 +1801,143 @@ rbsog_status rbsog_compute_virial(rbsog_ctx *ctx, const int32_t *m, int32_t P, d
     CK(launch_rho_combine(ctx->precision, bv, part, rho, kt, ctx->st, prof_of(ctx)));
     CK(launch_virial(ctx->d_desc, n, ctx->nsog, ctx->cb.start, ctx->cb.perm, ctx->cb.cell_of, ctx->posq, vpart, rho,
                      m3, P, dom, dsl, M, ctx->S[0], dW, ctx->st));
-    CK(cudaMemcpyAsync(W_out, dW, sizeof(double) * 9, cudaMemcpyDefault, ctx->st));
-    for (void *ptr : {(void *)m3, (void *)m4, (void *)part, (void *)rho, kt, (void *)vpart, (void *)dW, (void *)dom,
+    for (void *ptr : {(void *)m3, (void *)m4, (void *)part, (void *)rho, kt, (void *)vpart, (void *)dom,
                       (void *)dsl})
         CK(cudaFreeAsync(ptr, ctx->st));
+    return RBSOG_OK;
+}
+
+rbsog_status single_system_ready(rbsog_ctx *ctx, const char *what) {
+    if (ctx->n_sys != 1) return fail(ctx, RBSOG_EINVAL, "%s needs a single system", what);
+    if (!ctx->have_params || !all_state(ctx)) return fail(ctx, RBSOG_ESTATE, "params and state required");
+    return RBSOG_OK;
+}
+
+}  // namespace
+
+rbsog_status rbsog_compute_virial(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *W_out) {
+    if (!ctx || !m || !W_out || P < 1) return RBSOG_EINVAL;
+    rbsog_status es = single_system_ready(ctx, "rbsog_compute_virial");
+    if (es != RBSOG_OK) return es;
+    es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    double *dW = nullptr;
+    CK(cudaMallocAsync((void **)&dW, sizeof(double) * 9, ctx->st));
+    es = virial_device(ctx, m, P, dW);
+    if (es != RBSOG_OK) return es;
+    CK(cudaMemcpyAsync(W_out, dW, sizeof(double) * 9, cudaMemcpyDefault, ctx->st));
+    CK(cudaFreeAsync(dW, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return leave(ctx);
+}
+
+rbsog_status rbsog_compute_pressure(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *P_out) {
+    if (!ctx || !m || !P_out || P < 1) return RBSOG_EINVAL;
+    rbsog_status es = single_system_ready(ctx, "rbsog_compute_pressure");
+    if (es != RBSOG_OK) return es;
+    es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    const int64_t n = ctx->n_per[0];
+    double *dW = nullptr, *kpart = nullptr, *dP = nullptr;
+    CK(cudaMallocAsync((void **)&dW, sizeof(double) * 9, ctx->st));
+    CK(cudaMallocAsync((void **)&dP, sizeof(double) * 9, ctx->st));
+    CK(cudaMallocAsync((void **)&kpart, sizeof(double) * 6 * (size_t)obs_blocks(n), ctx->st));
+    es = virial_device(ctx, m, P, dW);
+    if (es != RBSOG_OK) return es;
+    const double V = ctx->p[0].L[0] * ctx->p[0].L[1] * ctx->p[0].L[2];
+    CK(launch_pressure(n, ctx->vel, ctx->p[0].mass, dW, V, kpart, dP, ctx->st));
+    CK(cudaMemcpyAsync(P_out, dP, sizeof(double) * 9, cudaMemcpyDefault, ctx->st));
+    for (void *ptr : {(void *)dW, (void *)dP, (void *)kpart}) CK(cudaFreeAsync(ptr, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return leave(ctx);
+}
+
+rbsog_status rbsog_observe_start(rbsog_ctx *ctx, int32_t n_lags, int32_t origin_every) {
+    if (!ctx) return RBSOG_EINVAL;
+    if (n_lags < 1 || origin_every < 1)
+        return fail(ctx, RBSOG_EINVAL, "n_lags and origin_every must be >= 1");
+    const int64_t slots = ((int64_t)n_lags + origin_every - 1) / origin_every;
+    if (slots > kObsMaxPairs)
+        return fail(ctx, RBSOG_EINVAL, "n_lags / origin_every may keep at most %d origins (asked %lld)", kObsMaxPairs,
+                    (long long)slots);
+    rbsog_status es = single_system_ready(ctx, "rbsog_observe_start");
+    if (es != RBSOG_OK) return es;
+    es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    const int64_t n = ctx->n_per[0];
+    CK(cudaStreamSynchronize(ctx->st));   // earlier samples may still read the buffers being replaced
+    CK(dalloc(&ctx->obs_xprev, n));
+    CK(dalloc(&ctx->obs_u, n));
+    CK(dalloc(&ctx->obs_ring_u, (size_t)slots * n));
+    CK(dalloc(&ctx->obs_ring_v, (size_t)slots * n));
+    CK(dalloc(&ctx->obs_part, (size_t)obs_blocks(n) * kObsMaxPairs));
+    CK(dalloc(&ctx->obs_acc, 4 * (size_t)n_lags));
+    CK(dalloc(&ctx->obs_count, n_lags));
+    CK(cudaMemsetAsync(ctx->obs_acc, 0, sizeof(double) * 4 * n_lags, ctx->st));
+    CK(cudaMemsetAsync(ctx->obs_count, 0, sizeof(int64_t) * n_lags, ctx->st));
+    ctx->obs_lags = n_lags;
+    ctx->obs_every = origin_every;
+    ctx->obs_slots = (int32_t)slots;
+    ctx->obs_frame = 0;
+    return leave(ctx);
+}
+
+rbsog_status rbsog_observe_sample(rbsog_ctx *ctx) {
+    if (!ctx) return RBSOG_EINVAL;
+    if (ctx->obs_lags == 0) return fail(ctx, RBSOG_ESTATE, "rbsog_observe_start must come first");
+    rbsog_status es = single_system_ready(ctx, "rbsog_observe_sample");
+    if (es != RBSOG_OK) return es;
+    es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    const int64_t j = ctx->obs_frame, every = ctx->obs_every;
+    const int store = j % every == 0 ? (int)((j / every) % ctx->obs_slots) : -1;
+    // the origins c * every <= j still within n_lags of frame j, newest first
+    ObsPairs pr{};
+    for (int64_t c = j / every; c >= 0 && j - c * every < ctx->obs_lags; --c) {
+        pr.slot[pr.n] = (int32_t)(c % ctx->obs_slots);
+        pr.lag[pr.n] = (int32_t)(j - c * every);
+        ++pr.n;
+    }
+    CK(launch_obs_sample(ctx->n_per[0], ctx->posq, ctx->vel, ctx->obs_xprev, ctx->obs_u, ctx->obs_ring_u,
+                         ctx->obs_ring_v, ctx->p[0].L, j == 0, store, pr, ctx->obs_part, ctx->obs_acc,
+                         ctx->obs_acc + ctx->obs_lags, ctx->obs_count, ctx->st));
+    ctx->obs_frame = j + 1;
+    return leave(ctx);
+}
+
+rbsog_status rbsog_observe_result(rbsog_ctx *ctx, double *msd, double *vacf, int64_t *count) {
+    if (!ctx) return RBSOG_EINVAL;
+    if (ctx->obs_lags == 0) return fail(ctx, RBSOG_ESTATE, "rbsog_observe_start must come first");
+    rbsog_status es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    const int32_t L = ctx->obs_lags;
+    double *res = ctx->obs_acc + 2 * L;
+    CK(launch_obs_result(L, ctx->n_per[0], ctx->obs_acc, ctx->obs_acc + L, ctx->obs_count, res, ctx->st));
+    if (msd) CK(cudaMemcpyAsync(msd, res, sizeof(double) * L, cudaMemcpyDefault, ctx->st));
+    if (vacf) CK(cudaMemcpyAsync(vacf, res + L, sizeof(double) * L, cudaMemcpyDefault, ctx->st));
+    if (count) CK(cudaMemcpyAsync(count, ctx->obs_count, sizeof(int64_t) * L, cudaMemcpyDefault, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return leave(ctx);
+}
+
+rbsog_status rbsog_green_kubo(const double *P_series, int64_t n_samples, double dt, double V, double T,
+                              int32_t max_lag, double *acf_out, double *C_out, void *stream) {
+    rbsog_ctx *ctx = nullptr;   // context-free: CK reports the status only
+    if (!P_series || !C_out || n_samples < 2 || max_lag < 2 || max_lag > n_samples || !(T > 0.0) || !(V > 0.0) ||
+        !(dt > 0.0))
+        return RBSOG_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double *ser = nullptr, *scr = nullptr;
+    CK(cudaMallocAsync((void **)&ser, sizeof(double) * 9 * (size_t)n_samples, st));
+    CK(cudaMallocAsync((void **)&scr, sizeof(double) * (7 + (size_t)max_lag), st));
+    CK(cudaMemcpyAsync(ser, P_series, sizeof(double) * 9 * (size_t)n_samples, cudaMemcpyDefault, st));
+    CK(launch_green_kubo(ser, n_samples, max_lag, V * dt / (6.0 * T), scr, scr + 7, scr + 6, st));
+    if (acf_out) CK(cudaMemcpyAsync(acf_out, scr + 7, sizeof(double) * max_lag, cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(C_out, scr + 6, sizeof(double), cudaMemcpyDefault, st));
+    CK(cudaFreeAsync(ser, st));
+    CK(cudaFreeAsync(scr, st));
+    CK(cudaStreamSynchronize(st));
+    return RBSOG_OK;
 }
 
 rbsog_status rbsog_get_cells(rbsog_ctx *ctx, int32_t *cell_start, int32_t *perm, int32_t *nbr) {
@@ -1973,6 +2109,13 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->dpart);
     dfree(&ctx->dip);
     dfree(&ctx->fin_count);
+    dfree(&ctx->obs_xprev);
+    dfree(&ctx->obs_u);
+    dfree(&ctx->obs_ring_u);
+    dfree(&ctx->obs_ring_v);
+    dfree(&ctx->obs_part);
+    dfree(&ctx->obs_acc);
+    dfree(&ctx->obs_count);
     dfree(&ctx->d_remaining);
     if (ctx->h_energy) cudaFreeHost(ctx->h_energy);
     if (ctx->h_err) cudaFreeHost(ctx->h_err);

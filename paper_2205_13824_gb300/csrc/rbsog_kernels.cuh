@@ -366,6 +366,36 @@ cudaError_t launch_virial(const SysDesc *sysd, int64_t n, const NearSog &sog, co
                           const double2 *rho, const int32_t *m3, int32_t P, const double *omega, const double *sl,
                           int32_t M, double S, double *W, cudaStream_t st);
 
+// ---- observables (k_observe.cu) --------------------------------------------------
+// MSD/VACF sampling of system 0 (n particles, caller order): per sample the
+// unwrapped positions u (from xprev, the folded positions of the previous
+// sample; first != 0 starts them), the origin ring (ring_u, ring_v: slots of
+// n entries; store_slot < 0 stores none) and, for each active origin p
+// (ring slot pr.slot[p] at lag pr.lag[p]), the sums of |u - u0|^2 and v . v0
+// added to msd_sum, vacf_sum and count at that lag.  part: obs_blocks(n) *
+// kObsMaxPairs double2 of scratch.
+constexpr int kObsMaxPairs = 64;
+struct ObsPairs {
+    int32_t n;
+    int32_t slot[kObsMaxPairs];
+    int32_t lag[kObsMaxPairs];
+};
+int32_t obs_blocks(int64_t n);
+cudaError_t launch_obs_sample(int64_t n, const double4_32a *posq, const double4_32a *vel, double4_32a *xprev,
+                              double4_32a *u, double4_32a *ring_u, double4_32a *ring_v, const double L[3],
+                              int first, int store_slot, const ObsPairs &pr, double2 *part, double *msd_sum,
+                              double *vacf_sum, int64_t *count, cudaStream_t st);
+// out[0 .. n_lags) = MSD, out[n_lags .. 2 n_lags) = VACF (0 where count = 0).
+cudaError_t launch_obs_result(int32_t n_lags, int64_t n, const double *msd_sum, const double *vacf_sum,
+                              const int64_t *count, double *out, cudaStream_t st);
+// Pt[9] = (sum_i m v_i v_i^T + W) / V; part: obs_blocks(n) * 6 doubles.
+cudaError_t launch_pressure(int64_t n, const double4_32a *vel, double mass, const double *W, double V,
+                            double *part, double *Pt, cudaStream_t st);
+// Green-Kubo: mean[6] scratch, acf[max_lag], *C = scale * trapezoid(acf)
+// with scale = V dt / (6 T); series[ns][9] on the device.
+cudaError_t launch_green_kubo(const double *series, int64_t ns, int32_t max_lag, double scale, double *mean,
+                              double *acf, double *C, cudaStream_t st);
+
 // ---- boundary terms (k_boundary.cu) ---------------------------------------------
 // Zero-frequency term of systems with a non-tinfoil boundary: dipole moment
 // from the caller-order positions, U0 into energy[sys * kNumEnergy + 7], the

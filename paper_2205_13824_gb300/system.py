@@ -85,6 +85,22 @@ class RBSOG:
         """(counts[3, nbins], g[3, nbins]) by sign pair ++, +-, -- on [0, L/2)."""
         return B.rbsog_rdf(self.ctx, nbins)
 
+    def pressure(self, m):
+        """Pressure tensor [3, 3] of Appendix A, the far virial on k-set m[P][3]."""
+        return B.rbsog_compute_pressure(self.ctx, m)
+
+    def observe_start(self, n_lags: int, origin_every: int = 1):
+        """Start MSD/VACF accumulation; the current state is frame 0 of the next sample."""
+        self._obs_lags = int(n_lags)
+        B.rbsog_observe_start(self.ctx, n_lags, origin_every)
+
+    def observe_sample(self):
+        B.rbsog_observe_sample(self.ctx)
+
+    def observe_result(self):
+        """(msd, vacf, count) per lag in samples."""
+        return B.rbsog_observe_result(self.ctx, self._obs_lags)
+
     def kseq(self, set0: int, nsets: int):
         import numpy as np
         out = np.zeros((nsets * self.params.P, 3), dtype=np.int32)
