@@ -139,6 +139,11 @@ def lib():
             L.orc_pressure.restype = C.c_int
             L.orc_green_kubo.argtypes = [_i64, _pd, _d, _d, _d, _i32, _pd, C.POINTER(_d)]
             L.orc_green_kubo.restype = C.c_int
+            L.orc_pg_plan.argtypes = [_pd, _pd, _i32, _pd, _i32, _pi32, _pd]
+            L.orc_pg_plan.restype = _i32
+            L.orc_pg_kseq.argtypes = [_pd, _pd, _i32, _pd, _i32, _u64, _i64, _i64, _pi32, _pi32]
+            L.orc_pg_kseq.restype = C.c_int
+            L.orc_far_rb_w.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), _i32, _pi32, _pd, _pd, C.POINTER(_d)]
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -377,6 +382,47 @@ def virial(sys_: System, q, x, S=0.0, m=None):
         m = _i32a(m)
         lib().orc_virial(x.shape[0], _p(q), _p(x), C.byref(sys_.c), float(S), m.shape[0], _p(m, _pi32), _p(W))
     return W.reshape(3, 3)
+
+
+def pg_plan(sog: SOG, L, P: int):
+    """Per-Gaussian sampling plan: (P_eff, P_l[M + 1], S_l[M + 1])."""
+    Lv = _f64(np.broadcast_to(np.asarray(L, float), (3,)).copy())
+    P_l = np.zeros(sog.M + 1, dtype=np.int32)
+    S_l = np.zeros(sog.M + 1)
+    pe = lib().orc_pg_plan(_p(sog.omega), _p(sog.s), sog.M, _p(Lv), int(P), _p(P_l, _pi32), _p(S_l))
+    if pe < 0:
+        raise ValueError("sampling table too long")
+    return int(pe), P_l, S_l
+
+
+def pg_kseq(sog: SOG, L, P: int, seed: int, set0: int, n_sets: int):
+    """Per-Gaussian k-sets: (m[n_sets * P_eff, 3], stratum[n_sets * P_eff])."""
+    pe, _, _ = pg_plan(sog, L, P)
+    Lv = _f64(np.broadcast_to(np.asarray(L, float), (3,)).copy())
+    m = np.zeros((n_sets * pe, 3), dtype=np.int32)
+    st = np.zeros(n_sets * pe, dtype=np.int32)
+    if lib().orc_pg_kseq(_p(sog.omega), _p(sog.s), sog.M, _p(Lv), int(P), int(seed), int(set0), int(n_sets),
+                         _p(m, _pi32), _p(st, _pi32)):
+        raise ValueError("sampling table too long")
+    return m, st
+
+
+def pg_weights(sog: SOG, L, P: int):
+    """Weight S_l / P_l of every frequency of one per-Gaussian set (length P_eff)."""
+    pe, P_l, S_l = pg_plan(sog, L, P)
+    return np.concatenate([np.full(P_l[l], S_l[l] / P_l[l]) for l in range(sog.M + 1) if P_l[l] > 0])
+
+
+def far_rb_w(sys_: System, q, x, m, c):
+    """Eq. 3.24 with per-frequency weights c (c = S / P everywhere is far_rb); returns (f, U)."""
+    q, x = _f64(q), _f64(x)
+    m = _i32a(m)
+    c = _f64(c)
+    f = np.zeros_like(x)
+    U = _d(0.0)
+    lib().orc_far_rb_w(x.shape[0], _p(q), _p(x), C.byref(sys_.c), m.shape[0], _p(m, _pi32), _p(c), _p(f),
+                       C.byref(U))
+    return f, U.value
 
 
 def msd_vacf(x_frames, v_frames, L, n_lags: int, origin_every: int = 1):

@@ -1288,3 +1288,137 @@ int orc_green_kubo(int64_t n_samples, const double *Pt, double dt, double V, dou
     *C = V / (6.0 * T) * integral;
     return 0;
 }
+
+/* ---- per-Gaussian independent sampling (Sec. 3.3, closing remark) ------- */
+
+#define PG_MAX_JMAX (1 << 20)
+
+/* Cumulative table of one coordinate: T[0] = 1, T[j] = T[j-1] + 2 e^{-x j^2};
+ * z = sum_{j>=1} 2 e^{-x j^2} summed on its own (no cancellation when tiny). */
+static int pg_table(double s, double L, double **T_out, int32_t *jmax_out, double *z_out) {
+    const double a = M_PI * s / L;
+    const double x = a * a;
+    const double jm = ceil(sqrt(50.0 / x));
+    if (!(jm <= (double)PG_MAX_JMAX)) return -1;
+    const int32_t jmax = jm < 1.0 ? 1 : (int32_t)jm;
+    double *T = (double *)malloc(sizeof(double) * ((size_t)jmax + 1));
+    if (!T) return -1;
+    T[0] = 1.0;
+    double z = 0.0;
+    for (int32_t j = 1; j <= jmax; ++j) {
+        const double w = 2.0 * exp(-x * (double)j * (double)j);
+        T[j] = T[j - 1] + w;
+        z = z + w;
+    }
+    *T_out = T;
+    *jmax_out = jmax;
+    *z_out = z;
+    return 0;
+}
+
+/* prod_d (1 + z_d) - 1 expanded, so that tiny z keep their digits. */
+static double pg_G(const double z[3]) {
+    return (((((z[0] + z[1]) + z[2]) + z[0] * z[1]) + z[0] * z[2]) + z[1] * z[2]) + (z[0] * z[1]) * z[2];
+}
+
+int32_t orc_pg_plan(const double *omega, const double *s, int32_t M, const double L[3], int32_t P,
+                    int32_t *P_l, double *S_l) {
+    double tot = 0.0;
+    for (int32_t l = 0; l <= M; ++l) {
+        double z[3];
+        for (int d = 0; d < 3; ++d) {
+            double *T;
+            int32_t jm;
+            if (pg_table(s[l], L[d], &T, &jm, &z[d])) return -1;
+            free(T);
+        }
+        S_l[l] = omega[l] * s[l] * s[l] * s[l] * pg_G(z);
+        tot += S_l[l];
+    }
+    int32_t P_eff = 0;
+    for (int32_t l = 0; l <= M; ++l) {
+        P_l[l] = S_l[l] > 1e-16 * tot ? (int32_t)ceil((double)P * S_l[l] / tot) : 0;
+        P_eff += P_l[l];
+    }
+    return P_eff;
+}
+
+/* Smallest j in [j0, jmax] with t < T[j]; jmax when rounding put t at the end. */
+static int32_t pg_search(const double *T, int32_t j0, int32_t jmax, double t) {
+    for (int32_t j = j0; j <= jmax; ++j)
+        if (t < T[j]) return j;
+    return jmax;
+}
+
+int orc_pg_kseq(const double *omega, const double *s, int32_t M, const double L[3], int32_t P, uint64_t seed,
+                int64_t set0, int64_t n_sets, int32_t *m_out, int32_t *stratum_out) {
+    int32_t P_l[256];
+    double S_l[256];
+    if (M < 0 || M > 255) return -1;
+    const int32_t P_eff = orc_pg_plan(omega, s, M, L, P, P_l, S_l);
+    if (P_eff < 0) return -1;
+    const uint64_t key[2] = {seed, 0x8000000000000002ull};
+    for (int32_t l = 0, eta0 = 0; l <= M; eta0 += P_l[l], ++l) {
+        if (P_l[l] == 0) continue;
+        double *T[3], z[3];
+        int32_t jmax[3];
+        for (int d = 0; d < 3; ++d)
+            if (pg_table(s[l], L[d], &T[d], &jmax[d], &z[d])) return -1;
+        /* P(first non-zero coordinate is x | m != 0), and y given m_x = 0 */
+        const double thr1 = ((z[0] * (1.0 + z[1])) * (1.0 + z[2])) / pg_G(z);
+        const double den2 = (z[1] + z[2]) + z[1] * z[2];
+        const double thr2 = den2 > 0.0 ? (z[1] * (1.0 + z[2])) / den2 : 1.0;
+        for (int64_t t = 0; t < n_sets; ++t)
+            for (int32_t e = 0; e < P_l[l]; ++e) {
+                const int64_t eta = eta0 + e;
+                const uint64_t ca[4] = {(uint64_t)(set0 + t), (uint64_t)eta, 0, 0};
+                const uint64_t cb[4] = {(uint64_t)(set0 + t), (uint64_t)eta, 1, 0};
+                uint64_t ra[4], rb[4];
+                orc_philox4x64_10(ca, key, ra);
+                orc_philox4x64_10(cb, key, rb);
+                const int first = u01(ra[0]) < thr1 ? 0 : (u01(ra[1]) < thr2 ? 1 : 2);
+                int32_t *m = m_out + 3 * (t * P_eff + eta);
+                for (int d = 0; d < 3; ++d) {
+                    const double u = u01(rb[d]);
+                    const double Tn = T[d][jmax[d]];
+                    int32_t j;
+                    if (d < first) j = 0;
+                    else if (d == first) j = pg_search(T[d], 1, jmax[d], T[d][0] + u * (Tn - T[d][0]));
+                    else j = pg_search(T[d], 0, jmax[d], u * Tn);
+                    m[d] = ((ra[2] >> d) & 1u) ? -j : j;
+                }
+                if (stratum_out) stratum_out[t * P_eff + eta] = l;
+            }
+        for (int d = 0; d < 3; ++d) free(T[d]);
+    }
+    return 0;
+}
+
+void orc_far_rb_w(int64_t n, const double *q, const double *x, const orc_sys *sys, int32_t P, const int32_t *m,
+                  const double *c, double *f, double *U_rb) {
+    const double V = sys->L[0] * sys->L[1] * sys->L[2];
+    const double pre = pow(M_PI, 1.5) / V;
+    double *rho = (double *)malloc(sizeof(double) * 2 * (size_t)(P > 0 ? P : 1));
+    orc_rho(n, q, x, sys->L, P, m, rho);
+    double U = 0.0;
+    for (int32_t e = 0; e < P; ++e) U += c[e] * (rho[2 * e] * rho[2 * e] + rho[2 * e + 1] * rho[2 * e + 1]);
+    *U_rb = sys->lB * 0.5 * pre * U;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double fi[3] = {0.0, 0.0, 0.0};
+        for (int32_t e = 0; e < P; ++e) {
+            double k[3];
+            for (int d = 0; d < 3; ++d) k[d] = 2.0 * M_PI * (double)m[3 * e + d] / sys->L[d];
+            const double th = k[0] * x[3 * i] + k[1] * x[3 * i + 1] + k[2] * x[3 * i + 2];
+            const double im = c[e] * (cos(th) * rho[2 * e + 1] - sin(th) * rho[2 * e]);
+            fi[0] += k[0] * im;
+            fi[1] += k[1] * im;
+            fi[2] += k[2] * im;
+        }
+        const double g = -sys->lB * q[i] * pre;
+        f[3 * i + 0] = g * fi[0];
+        f[3 * i + 1] = g * fi[1];
+        f[3 * i + 2] = g * fi[2];
+    }
+    free(rho);
+}

@@ -80,6 +80,38 @@ int64_t orc_mh_chain(const double *omega, const double *s, int32_t M, const doub
 int64_t orc_kseq(const double *omega, const double *s, int32_t M, const double L[3],
                  uint64_t seed, int64_t n_chains, int64_t chain_len, int32_t *m_out);
 
+/* ---- per-Gaussian independent sampling (Sec. 3.3, closing remark) ------- */
+/* Gaussian l alone, normalised over k != 0, is the distribution
+ * p_l(k) = e^{-s_l^2 k^2 / 4} / (prod_d H_l^d - 1); its share of the far sum
+ * is S_l = w_l s_l^3 (prod_d H_l^d - 1) (S = sum_l S_l, Eq. 3.16).  Batch
+ * sizes adapt to the shares: P_l = ceil(P S_l / S) for S_l > 1e-16 S, else 0
+ * (that Gaussian is dropped).  Each set holds the strata in order of l, P_l
+ * frequencies each, P_eff = sum_l P_l in all; the estimator weighs a
+ * frequency of stratum l by S_l / P_l where the mixture sampler uses S / P.
+ * orc_pg_plan fills P_l[M + 1] and S_l[M + 1] and returns P_eff (-1 on a
+ * table longer than 2^20 entries).
+ *
+ * Frequency eta of set t: the coordinates are independent discrete Gaussians
+ * p(m_d) proportional to e^{-x_d m_d^2}, x_d = (pi s_l / L_d)^2, conditioned
+ * on m != 0 by choosing the first non-zero coordinate d* with its exact
+ * conditional probability; coordinates before d* are 0, d* is drawn given
+ * m_d* != 0, the ones after it unconditioned.  Each coordinate is drawn by
+ * inverting the cumulative table T_d[j] = 1 + sum_{i=1..j} 2 e^{-x_d i^2}
+ * (|m| = j, j <= jmax = ceil(sqrt(50 / x_d))), its sign from a random bit.
+ * Random numbers: Philox4x64-10, key (seed, 2^63 + 2), counters (t, eta, 0, 0)
+ * (two decision uniforms, the sign bits in the third word) and
+ * (t, eta, 1, 0) (one uniform per coordinate).  m_out[n_sets][P_eff][3],
+ * stratum_out[n_sets][P_eff] (may be NULL). */
+int32_t orc_pg_plan(const double *omega, const double *s, int32_t M, const double L[3], int32_t P,
+                    int32_t *P_l, double *S_l);
+int orc_pg_kseq(const double *omega, const double *s, int32_t M, const double L[3], int32_t P, uint64_t seed,
+                int64_t set0, int64_t n_sets, int32_t *m_out, int32_t *stratum_out);
+/* Eq. 3.24 with a weight per frequency: U = (lB pi^{3/2} / (2V)) sum_eta
+ * c_eta |rho(k_eta)|^2 and its force (c_eta = S / P for every eta is
+ * orc_far_rb). */
+void orc_far_rb_w(int64_t n, const double *q, const double *x, const orc_sys *sys, int32_t P, const int32_t *m,
+                  const double *c, double *f, double *U_rb);
+
 /* ---- cell list and near field (Sec. 3.1, Eq. 3.9 first line) ------------ */
 void orc_wrap(int64_t n, double *x, const double L[3]);
 int  orc_cell_list(int64_t n, const double *x, const double L[3], double rc,
