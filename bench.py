@@ -429,8 +429,67 @@ def run_extras(args, q, x, v, dev):
     out["fp32c_coreshell_near"] = {"value": N / (ms_c / 1e3), "ms_per_step": ms_c,
                                    "near_ms": near_c[1] / near_c[0]}
     g.close()
+    out.update(run_dynamics_extras(args, tq, tx, tv, dev))
     out["batched_replicas"] = run_replicas(args, dev)
     out["serving"] = run_serving(dev)
+    return out
+
+
+def run_dynamics_extras(args, tq, tx, tv, dev):
+    """Step time with the Langevin and Nose-Hoover thermostats and with the
+    per-Gaussian sampler on the same workload; the cost of the Appendix A
+    observables beside the step (one MSD/VACF sample with 8 origins, one
+    pressure tensor, one Green-Kubo integral of a 10^4-sample series)."""
+    import torch
+
+    import paper_2205_13824_gb300 as Pk
+    B = Pk.binding
+    N, L, P = args.N, args.L, args.P
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    out = {}
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for name, kw in (("fp32c_langevin", {"tau_T": 0.1, "thermostat": "langevin"}),
+                     ("fp32c_nose_hoover", {"tau_T": 0.1, "thermostat": "nose-hoover"}),
+                     ("fp32c_per_gaussian_sampler", {"sampler": "per-gaussian"})):
+        g = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=args.steps + 8, seed=19, precision="fp32c", **kw),
+                     device=dev.index)
+        g.set_state(tq, tx, tv)
+        g.step(2)
+        ms_t = timed(lambda: g.step(args.steps), 1) / args.steps
+        out[name] = {"value": N / (ms_t / 1e3), "unit": "particle-steps/s", "ms_per_step": ms_t}
+        if "sampler" in kw:
+            out[name]["P_set"] = int(g.info()[0].P_set)
+        g.close()
+    g = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=args.steps + 8, seed=19, precision="fp32c"), device=dev.index)
+    g.set_state(tq, tx, tv)
+    g.observe_start(64, 8)
+    for _ in range(64):
+        g.observe_sample()
+    ms_obs = timed(g.observe_sample, 20)
+    m = g.kseq(0, 1)
+    g.pressure(m)
+    t0 = time.perf_counter()
+    g.pressure(m)
+    ms_p = (time.perf_counter() - t0) * 1e3
+    g.close()
+    ser = torch.randn((10000, 9), dtype=torch.float64, device=dev)
+    B.rbsog_green_kubo(ser, 0.01, 1.0, 1.0, 1000)
+    t0 = time.perf_counter()
+    B.rbsog_green_kubo(ser, 0.01, 1.0, 1.0, 1000)
+    ms_gk = (time.perf_counter() - t0) * 1e3
+    out["observables"] = {"msd_vacf_sample_ms": ms_obs, "msd_vacf_origins": 8,
+                          "pressure_tensor_ms": ms_p, "green_kubo_ms": ms_gk,
+                          "green_kubo_series": "10000 samples x 1000 lags"}
     return out
 
 

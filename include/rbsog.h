@@ -108,6 +108,25 @@ typedef struct {
                                  xi += dt/4 G; v *= e^{-xi dt/2}; eta += dt/2 xi;
                                  xi += dt/4 G with G = (2K - g T_target)/Q; set_state
                                  starts xi = eta = 0; U + K + U_th is conserved            */
+    int32_t sampler;          /* frequency sampler (Sec. 3.3): 0 the mixture distribution by
+                                 Metropolis-Hastings chains (default); 1 per-Gaussian
+                                 independent sampling: Gaussian l, normalised over k != 0, is
+                                 sampled exactly P_l = ceil(P S_l / S) times per set, S_l =
+                                 w_l s_l^3 (prod_d H_l^d - 1) its share of S (Gaussians with
+                                 S_l <= 1e-16 S dropped), each frequency weighted by S_l/P_l;
+                                 a set then holds P_eff = sum_l P_l frequencies (the largest
+                                 over a batch, shorter sets padded with weight-0 entries;
+                                 rbsog_info.P_set).  The same for every system of a batch;
+                                 chain_len is unused.  Frequency eta of set t draws the
+                                 Philox4x64-10 blocks A, B with key (seed, 2^63 + 2) and
+                                 counters (t, eta, 0, 0), (t, eta, 1, 0); its first non-zero
+                                 coordinate is x if u(A0) < P(m_x != 0 | m != 0), else y if
+                                 u(A1) < P(m_y != 0 | m_x = 0, m != 0), else z; earlier
+                                 coordinates are 0, that one is drawn given |m_d| >= 1 and
+                                 later ones unconditioned, |m_d| by inverting with u(B_d) the
+                                 sums 1 + sum_{i=1..j} 2 e^{-x i^2}, x = (pi s_l / L_d)^2,
+                                 j <= ceil(sqrt(50 / x)), the sign from bit d of A2
+                                 (u(r) = (r >> 11) 2^-53)                                     */
 } rbsog_params;
 
 /* Energies of the last force evaluation (Eqs. 3.1, 3.6-3.8) and kinetic state. */
@@ -130,6 +149,7 @@ typedef struct {
     int64_t n_chains;         /* sampler chains; chain c fills sequence entries
                                  [c * chain_len, (c + 1) * chain_len)                       */
     int32_t chain_len;
+    int32_t P_set;            /* frequencies per k-set: P, or P_eff with sampler 1          */
 } rbsog_info;
 
 /* Create a context for n >= 2 particles on CUDA device `device`; `stream`
@@ -160,8 +180,10 @@ rbsog_status rbsog_set_state(rbsog_ctx *ctx, const double *q, const double *x, c
 
 /* One force evaluation F = F_N + F*_F (+ WCA) at the current positions
  * (Eq. 3.9 first line, Eq. 3.24).  m_kset: P integer frequency vectors
- * m[P][3] (k = 2 pi m / L) in host or device memory, or NULL to take the
- * next k-set of the pre-sampled sequence (advancing the cursor).  f_out
+ * m[P][3] (k = 2 pi m / L; P_set of rbsog_info with the per-Gaussian
+ * sampler) in host or device memory, each weighted S / P as mixture samples,
+ * or NULL to take the next k-set of the pre-sampled sequence with its own
+ * weights (advancing the cursor).  f_out
  * ([n][3], host or device) and e_out (host) may be NULL.  The forces are
  * also kept as the context's current forces. */
 rbsog_status rbsog_compute_forces(rbsog_ctx *ctx, const int32_t *m_kset, double *f_out,

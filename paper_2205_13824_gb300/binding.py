@@ -49,7 +49,7 @@ class rbsog_params(C.Structure):
                 ("T_target", C.c_double), ("tau_T", C.c_double), ("seed", C.c_uint64),
                 ("n_ksets", C.c_int64), ("chain_len", C.c_int32), ("precision", C.c_int32),
                 ("boundary", C.c_int32), ("near_kernel", C.c_int32), ("r_in", C.c_double),
-                ("thermostat", C.c_int32)]
+                ("thermostat", C.c_int32), ("sampler", C.c_int32)]
 
 
 class rbsog_energies(C.Structure):
@@ -64,7 +64,7 @@ class rbsog_energies(C.Structure):
 class rbsog_info(C.Structure):
     _fields_ = [("sigma", C.c_double), ("omega0", C.c_double), ("S", C.c_double),
                 ("M", C.c_int32), ("ncell", C.c_int32 * 3), ("n_chains", C.c_int64),
-                ("chain_len", C.c_int32)]
+                ("chain_len", C.c_int32), ("P_set", C.c_int32)]
 
 
 def _load():

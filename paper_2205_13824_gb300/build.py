@@ -17,10 +17,12 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librbsog.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# Per-file extra flags.  The sampler must round every FP64 operation
-# separately (no fused multiply-add) so its accept/reject decisions are the
-# IEEE evaluation of the written expressions.
-EXTRA = {"k_sampler.cu": ["-fmad=false"]}
+# Per-file extra flags.  The samplers must round every FP64 operation
+# separately (no fused multiply-add, on the device and, for the per-Gaussian
+# sampler's tables, on the host) so that their decisions are the IEEE
+# evaluation of the written expressions.
+EXTRA = {"k_sampler.cu": ["-fmad=false"],
+         "k_pgsample.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]}
 
 
 def nvcc() -> str:

@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(kCombineThreads) k_rho_combine(BatchView bv, c
         const int4 m = load_m(bv, d, sy, k);
         // 2 pi / L from the host: FP64 divisions are slow on this GPU
         const double kx = d.box.kfac[0] * m.x, ky = d.box.kfac[1] * m.y, kz = d.box.kfac[2] * m.z;
-        const double coef = d.coef;
+        // per-Gaussian sampling: each frequency weighted by its stratum
+        const double coef = bv.kw ? d.coef * bv.kw[(int64_t)sy * kKwStride + m.w] : d.coef;
         if (PREC == 1) {
             KEntry32 e;
             e.mx = m.x;

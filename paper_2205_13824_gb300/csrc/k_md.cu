@@ -178,9 +178,17 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BatchView bv, const do
         uw += e.y;
     }
     chunk(bv.P, lo, hi);
-    for (int j = lo + tid; j < hi; j += kFinThreads) {
-        const double2 r = rho[(int64_t)sy * bv.P + j];
-        r2 += r.x * r.x + r.y * r.y;
+    if (bv.kw) {   // per-Gaussian sampling: |rho|^2 weighted by the frequency's stratum
+        const int4 *ks = bv.kseq + a.k_off + bv.cursor[sy] * (int64_t)bv.P;
+        for (int j = lo + tid; j < hi; j += kFinThreads) {
+            const double2 r = rho[(int64_t)sy * bv.P + j];
+            r2 += bv.kw[(int64_t)sy * kKwStride + ks[j].w] * (r.x * r.x + r.y * r.y);
+        }
+    } else {
+        for (int j = lo + tid; j < hi; j += kFinThreads) {
+            const double2 r = rho[(int64_t)sy * bv.P + j];
+            r2 += r.x * r.x + r.y * r.y;
+        }
     }
     if (with_kinetic) {
         chunk(a.n_kpart, lo, hi);

@@ -132,6 +132,9 @@ struct rbsog_ctx {
     float4 *d_cstab = nullptr;           // its shell table [cs.n_tab]
     std::vector<float4> h_ltab;
     int32_t *nbr_list = nullptr, *nbr_cnt = nullptr, *list_perm = nullptr, *d_rebuild = nullptr;
+    // per-Gaussian independent sampling (rbsog_params.sampler = 1)
+    bool pg_sampler = false;
+    double *d_kw = nullptr;           // [n_sys * kKwStride] per-stratum estimator weights
     // observables of Appendix A (rbsog_observe_*), single system
     int32_t obs_lags = 0, obs_every = 0, obs_slots = 0;
     int64_t obs_frame = 0;
@@ -598,6 +601,7 @@ BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
     v.precision = c->precision;
     v.fin_part = c->fin_part;
     v.fin_count = c->fin_count;
+    v.kw = (c->pg_sampler && !m_explicit) ? c->d_kw : nullptr;
     v.lpos = c->use_list ? c->lpos : nullptr;
     v.linv = c->use_list ? c->linv : nullptr;
     return v;
@@ -1013,6 +1017,10 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         if (q.thermostat < 0 || q.thermostat > 2)
             return fail(ctx, RBSOG_EINVAL,
                         "system %d: thermostat must be 0 (Berendsen), 1 (Langevin) or 2 (Nose-Hoover)", s);
+        if (q.sampler < 0 || q.sampler > 1)
+            return fail(ctx, RBSOG_EINVAL, "system %d: sampler must be 0 (mixture) or 1 (per-Gaussian)", s);
+        if (s > 0 && q.sampler != p[0].sampler)
+            return fail(ctx, RBSOG_EINVAL, "system %d: sampler must be the same for every system", s);
         if (q.near_kernel < 0 || q.near_kernel > 1)
             return fail(ctx, RBSOG_EINVAL, "system %d: near_kernel must be 0 (table) or 1 (core-shell)", s);
         if (s > 0 && (q.near_kernel != p[0].near_kernel || q.r_in != p[0].r_in))
@@ -1086,6 +1094,20 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
             return fail(ctx, RBSOG_EINVAL, "the core-shell table cannot reach r_c^2 from r_in^2 in 8 octaves");
     }
 
+    // per-Gaussian sampling: plans per system (box-dependent); every set of the
+    // batch holds the largest P_eff frequencies, shorter ones padded
+    std::vector<PgPlan> plans;
+    int32_t P_batch = p[0].P;
+    if (p[0].sampler == 1) {
+        plans.resize(ns);
+        P_batch = 0;
+        for (int s = 0; s < ns; ++s) {
+            if (!pg_plan(w.data(), sv.data(), p[0].M, p[s].L, p[0].P, plans[s]))
+                return fail(ctx, RBSOG_EINVAL, "system %d: per-Gaussian sampling table longer than 2^20", s);
+            P_batch = std::max(P_batch, plans[s].P_eff);
+        }
+    }
+
     drop_graph(ctx);
     ctx->p = p;
     ctx->any_boundary = false;
@@ -1094,7 +1116,8 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
     ctx->s = sv;
     ctx->sigma = sigma;
     ctx->omega0 = w0;
-    ctx->P = p[0].P;
+    ctx->P = P_batch;
+    ctx->pg_sampler = p[0].sampler == 1;
     ctx->precision = p[0].precision;
     build_near_sog(ctx->nsog, w, sv, p[0].M, p[0].r_c);
     build_sog_tables(ctx->nsog, w, sv, p[0].M, p[0].r_c);
@@ -1148,7 +1171,8 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         d.nh_Q = d.thermostat == 2 ? (3.0 * (double)d.n - 3.0) * q.T_target * q.tau_T * q.tau_T : 0.0;
         d.T0 = q.T_target;
         d.tau = q.tau_T;
-        ctx->chain_len[s] = q.chain_len > 0 ? q.chain_len : 256;
+        // per-Gaussian sampling writes one set per "chain"
+        ctx->chain_len[s] = ctx->pg_sampler ? ctx->P : (q.chain_len > 0 ? q.chain_len : 256);
         const int64_t total = q.n_ksets * (int64_t)ctx->P;
         ctx->n_chains[s] = (total + ctx->chain_len[s] - 1) / ctx->chain_len[s];
         for (int64_t b = 0; b < d.n_kpart; ++b) ctx->pblk.push_back(make_int2(s, (int)b));
@@ -1171,6 +1195,17 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
     CK(dalloc(&ctx->cb.start, (size_t)c_off + 1));
     CK(dalloc(&ctx->cb.tile_sum, (size_t)cell_scan_tiles(c_off)));
     CK(dalloc(&ctx->m_tmp, (size_t)ctx->P));
+    if (ctx->pg_sampler) {
+        std::vector<double> kw((size_t)ns * kKwStride, 0.0);
+        for (int s = 0; s < ns; ++s)
+            for (const PgStratum &st : plans[s].strata)
+                kw[(size_t)s * kKwStride + st.l] =
+                    (plans[s].S_l[st.l] / plans[s].P_l[st.l]) / (ctx->S[s] / (double)ctx->P);
+        CK(dalloc(&ctx->d_kw, kw.size()));
+        CK(cudaMemcpy(ctx->d_kw, kw.data(), sizeof(double) * kw.size(), cudaMemcpyHostToDevice));
+    } else {
+        dfree(&ctx->d_kw);
+    }
     CK(dalloc(&ctx->m3_tmp, (size_t)ctx->P * 3));
     CK(dalloc(&ctx->d_pblk, ctx->pblk.size()));
     CK(dalloc(&ctx->d_cell_sys, cell_sys.size()));
@@ -1240,7 +1275,30 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
             coff += ctx->n_chains[s];
             ss.push_back(y);
         }
-        if (!ss.empty()) {
+        if (ctx->pg_sampler) {
+            for (int s = 0; s < ns; ++s) {
+                if (sample_mask && !(*sample_mask)[s]) continue;
+                const PgPlan &pl = plans[s];
+                PgStratum *d_st = nullptr;
+                int32_t *d_slot = nullptr;
+                double *d_tab = nullptr;
+                CK(cudaMallocAsync((void **)&d_st, sizeof(PgStratum) * std::max<size_t>(pl.strata.size(), 1), ctx->st));
+                CK(cudaMallocAsync((void **)&d_slot, sizeof(int32_t) * std::max<size_t>(pl.slot_stratum.size(), 1),
+                                   ctx->st));
+                CK(cudaMallocAsync((void **)&d_tab, sizeof(double) * std::max<size_t>(pl.tables.size(), 1), ctx->st));
+                CK(cudaMemcpyAsync(d_st, pl.strata.data(), sizeof(PgStratum) * pl.strata.size(), cudaMemcpyHostToDevice,
+                                   ctx->st));
+                CK(cudaMemcpyAsync(d_slot, pl.slot_stratum.data(), sizeof(int32_t) * pl.slot_stratum.size(),
+                                   cudaMemcpyHostToDevice, ctx->st));
+                CK(cudaMemcpyAsync(d_tab, pl.tables.data(), sizeof(double) * pl.tables.size(), cudaMemcpyHostToDevice,
+                                   ctx->st));
+                CK(launch_pg_sampler(d_st, d_slot, pl.P_eff, ctx->P, d_tab, p[s].seed, p[s].n_ksets,
+                                     ctx->kseq + ctx->desc[s].k_off, ctx->st, prof_of(ctx)));
+                // the host vectors stay alive until the copies have run
+                CK(cudaStreamSynchronize(ctx->st));
+                for (void *ptr : {(void *)d_st, (void *)d_slot, (void *)d_tab}) CK(cudaFreeAsync(ptr, ctx->st));
+            }
+        } else if (!ss.empty()) {
             SamplerSys *d_ss = nullptr;
             CK(cudaMallocAsync((void **)&d_ss, sizeof(SamplerSys) * ss.size(), ctx->st));
             CK(cudaMemcpyAsync(d_ss, ss.data(), sizeof(SamplerSys) * ss.size(), cudaMemcpyHostToDevice, ctx->st));
@@ -1354,6 +1412,7 @@ rbsog_status rbsog_get_info(const rbsog_ctx *ctx, rbsog_info *info, double *omeg
     for (int d = 0; d < 3; ++d) info->ncell[d] = ctx->desc[0].box.nc[d];
     info->n_chains = ctx->n_chains[0];
     info->chain_len = ctx->chain_len[0];
+    info->P_set = ctx->P;
     if (omega) std::memcpy(omega, ctx->omega.data(), sizeof(double) * (ctx->p[0].M + 1));
     if (s) std::memcpy(s, ctx->s.data(), sizeof(double) * (ctx->p[0].M + 1));
     return RBSOG_OK;
@@ -2109,6 +2168,7 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->dpart);
     dfree(&ctx->dip);
     dfree(&ctx->fin_count);
+    dfree(&ctx->d_kw);
     dfree(&ctx->obs_xprev);
     dfree(&ctx->obs_u);
     dfree(&ctx->obs_ring_u);

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
 namespace rbsog {
 
@@ -111,6 +112,38 @@ struct ProfScope {
 cudaError_t launch_mh_sampler(const SamplerDev &sp, const SamplerSys *sys, int n_sys, int64_t total_chains,
                               int4 *kseq, int32_t *err_flag, cudaStream_t st, const Prof *prof);
 
+// ---- per-Gaussian independent sampling (k_pgsample.cu) -------------------------
+// The variant sampler of Sec. 3.3: Gaussian l alone, normalised over k != 0,
+// is sampled P_l = ceil(P S_l / S) times per set (S_l its share of Eq. 3.16;
+// Gaussians with S_l <= 1e-16 S are dropped); a set holds the strata in order
+// of l, P_eff = sum_l P_l frequencies, padded to the batch's frequencies per
+// set with (1, 0, 0) entries of stratum kPgPad and weight 0.  The k-sequence
+// entry's w holds the stratum; the estimator weighs it by
+// kw[sys * kKwStride + w] = (S_l / P_l) / (S / P_batch).
+constexpr int kPgPad = kMaxGauss;
+constexpr int kKwStride = kMaxGauss + 1;
+struct PgStratum {
+    double thr1;          // P(first non-zero coordinate is x | m != 0)
+    double thr2;          // P(it is y | m_x = 0, m != 0)
+    int64_t tab_off[3];   // cumulative table of each coordinate in the table array
+    int32_t jmax[3];      // its last index
+    int32_t l;            // Gaussian index
+};
+struct PgPlan {
+    int32_t P_eff = 0;
+    std::vector<int32_t> P_l;             // [M + 1]
+    std::vector<double> S_l;              // [M + 1]
+    std::vector<PgStratum> strata;        // active Gaussians in order of l
+    std::vector<int32_t> slot_stratum;    // [P_eff]: index into strata
+    std::vector<double> tables;           // cumulative tables, concatenated
+};
+// false when a coordinate table would exceed 2^20 entries.
+bool pg_plan(const double *omega, const double *s, int M, const double L[3], int P, PgPlan &plan);
+// Fills kseq[set * P_batch + eta] for sets [0, n_sets) of one system.
+cudaError_t launch_pg_sampler(const PgStratum *strata, const int32_t *slot_stratum, int32_t P_eff, int32_t P_batch,
+                              const double *tables, uint64_t seed, int64_t n_sets, int4 *kseq, cudaStream_t st,
+                              const Prof *prof);
+
 // ---- batch layout -------------------------------------------------------------
 // Every kernel works on a batch of independent systems laid out back to back
 // (particles, cells, k-sequences, partial sums).  A single system is a batch
@@ -170,6 +203,8 @@ struct BatchView {
     uint4 *lpos;               // [n_total] fixed-point positions in the cell order of the
                                // last list build (neighbour-list path; null otherwise)
     int32_t *linv;             // [n_total] cell-order slot of caller particle i at that build
+    const double *kw;          // [n_sys * kKwStride] per-stratum weights of per-Gaussian
+                               // sampling (null: the mixture sampler, or an explicit k-set)
     double4_32a *fin_part;     // [n_sys * kFinChunks] finalize: per-chunk energy sums
     unsigned int *fin_count;   // [n_sys] finalize: chunks done (reset by the last one)
 };

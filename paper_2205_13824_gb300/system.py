@@ -15,7 +15,7 @@ DEFAULT_M = 36
 def make_params(L, P, r_c=3.0, b=DEFAULT_B, sigma=0.0, omega0=0.0, M=DEFAULT_M, lB=1.0,
                 wca_sigma=1.0, wca_eps=1.0, dt=0.001, mass=1.0, T_target=1.0, tau_T=0.0,
                 seed=1, n_ksets=1, chain_len=0, precision="fp64", boundary=0, near_kernel=0,
-                r_in=0.0, thermostat=0) -> B.rbsog_params:
+                r_in=0.0, thermostat=0, sampler=0) -> B.rbsog_params:
     if isinstance(L, (int, float)):
         L = (float(L),) * 3
     p = B.rbsog_params()
@@ -35,6 +35,7 @@ def make_params(L, P, r_c=3.0, b=DEFAULT_B, sigma=0.0, omega0=0.0, M=DEFAULT_M, 
     p.r_in = float(r_in)
     p.thermostat = {"berendsen": 0, "langevin": 1, "nose-hoover": 2}[thermostat] \
         if isinstance(thermostat, str) else int(thermostat)
+    p.sampler = {"mixture": 0, "per-gaussian": 1}[sampler] if isinstance(sampler, str) else int(sampler)
     return p
 
 
@@ -103,7 +104,7 @@ class RBSOG:
 
     def kseq(self, set0: int, nsets: int):
         import numpy as np
-        out = np.zeros((nsets * self.params.P, 3), dtype=np.int32)
+        out = np.zeros((nsets * self.info()[0].P_set, 3), dtype=np.int32)
         B.rbsog_get_kseq(self.ctx, set0, nsets, out)
         return out
 
