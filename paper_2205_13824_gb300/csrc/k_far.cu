@@ -249,13 +249,29 @@ __global__ void __launch_bounds__(kCombineThreads) k_rho_combine(BatchView bv, c
 }
 
 // Particle l of a scatter block: far force (already multiplied by q) plus the
-// near-field force, checked and stored in caller order.
-__device__ __forceinline__ void store_total(int64_t s, double fx, double fy, double fz, const double4_32a &fn,
-                                            const int32_t *__restrict__ perm, double4_32a *__restrict__ force,
-                                            int32_t *__restrict__ err_flag) {
+// near-field force, checked and stored in caller order (returned as well).
+__device__ __forceinline__ double4_32a store_total(int64_t s, double fx, double fy, double fz,
+                                                   const double4_32a &fn, const int32_t *__restrict__ perm,
+                                                   double4_32a *__restrict__ force, int32_t *__restrict__ err_flag) {
     const double tx = fx + fn.x, ty = fy + fn.y, tz = fz + fn.z;
     if (!(isfinite(tx) && isfinite(ty) && isfinite(tz))) atomicOr(err_flag, 1);
-    force[perm ? perm[s] : s] = make_double4_32a(tx, ty, tz, 0.0);
+    const double4_32a t = make_double4_32a(tx, ty, tz, 0.0);
+    force[perm ? perm[s] : s] = t;
+    return t;
+}
+
+// The step's second half kick of one particle, v += dt/2 F/m, and its FP32C
+// kinetic-energy term: the same expressions as the kick kernel, so that the
+// fused and the separate kick give the same bits.
+__device__ __forceinline__ float kick_one(double4_32a *__restrict__ vel, int64_t i, const double4_32a &f,
+                                          const SysDesc &a) {
+    double4_32a v = vel[i];
+    const double h = a.half_dt_inv_mass;
+    v.x += h * f.x;
+    v.y += h * f.y;
+    v.z += h * f.z;
+    vel[i] = v;
+    return (float)fma(v.z, v.z, fma(v.y, v.y, v.x * v.x)) * a.half_mass_f;
 }
 
 // The two near energies of a particle packed in fn.w (neighbour-list path),
@@ -341,9 +357,11 @@ __global__ void __launch_bounds__(kScatterThreads)
 __global__ void __launch_bounds__(kScatter32Threads, 9)
     k_far_scatter32(BatchView bv, const uint4 *__restrict__ sp32, const float4 *__restrict__ ktab_all,
                     const double4_32a *__restrict__ fnear, const int32_t *__restrict__ perm,
-                    double4_32a *__restrict__ force, int32_t *__restrict__ err_flag, double2 *__restrict__ epart) {
+                    double4_32a *__restrict__ force, int32_t *__restrict__ err_flag, double2 *__restrict__ epart,
+                    double4_32a *__restrict__ vel, double *__restrict__ kpart) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ double2 s_e[kParticleBlock / 32];
+    __shared__ double s_k[kParticleBlock / 32];
     float4 *sk = reinterpret_cast<float4 *>(smem_raw);
     const int tid = threadIdx.x;
     const int2 work = bv.pblk[blockIdx.x];
@@ -406,8 +424,36 @@ __global__ void __launch_bounds__(kScatter32Threads, 9)
         }
     }
     const float qa = __uint_as_float(pa.w), qb = __uint_as_float(pb.w);
-    if (act_a) store_total(sa, (double)(qa * gx.x), (double)(qa * gy.x), (double)(qa * gz.x), fa, perm, force, err_flag);
-    if (act_b) store_total(sb, (double)(qb * gx.y), (double)(qb * gy.y), (double)(qb * gz.y), fb, perm, force, err_flag);
+    double4_32a ta = fa, tb = fb;
+    if (act_a)
+        ta = store_total(sa, (double)(qa * gx.x), (double)(qa * gy.x), (double)(qa * gz.x), fa, perm, force, err_flag);
+    if (act_b)
+        tb = store_total(sb, (double)(qb * gx.y), (double)(qb * gy.y), (double)(qb * gz.y), fb, perm, force, err_flag);
+    if (vel) {
+        // the step's second half kick with the force just formed, and the
+        // block's kinetic energy summed as the kick kernel sums it: an FP32
+        // tree per 32 particles (warp w holds 32w.. and 128 + 32w..), then
+        // the eight trees in FP64 in particle order
+        float ka = 0.f, kb = 0.f;
+        if (act_a) ka = kick_one(vel, perm ? perm[sa] : sa, ta, d);
+        if (act_b) kb = kick_one(vel, perm ? perm[sb] : sb, tb, d);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ka += __shfl_down_sync(0xffffffffu, ka, o);
+            kb += __shfl_down_sync(0xffffffffu, kb, o);
+        }
+        const int w = tid >> 5;
+        if ((tid & 31) == 0) {
+            s_k[w] = (double)ka;
+            s_k[w + kScatter32Threads / 32] = (double)kb;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < kParticleBlock / 32; ++q) t += s_k[q];
+            kpart[d.kp_off + work.y] = t;
+        }
+    }
 }
 
 }  // namespace
@@ -458,12 +504,13 @@ cudaError_t launch_rho_combine(int precision, const BatchView &bv, const double2
 cudaError_t launch_far_scatter(int precision, const BatchView &bv, const double4_32a *sp64, const uint4 *sp32,
                                const void *ktab, const double4_32a *fnear, const int32_t *perm,
                                double4_32a *force, int32_t *err_flag, cudaStream_t st, const Prof *prof,
-                               double2 *epart) {
+                               double2 *epart, double4_32a *kick_vel, double *kick_kpart) {
     ProfScope ps(prof, precision == 1 ? "far_scatter_fp32c" : "far_scatter_fp64");
     if (precision == 1) {
         const size_t sm = sizeof(KEntry32) * kKChunk32;
         k_far_scatter32<<<bv.n_pblk, kScatter32Threads, sm, st>>>(bv, sp32, static_cast<const float4 *>(ktab),
-                                                                   fnear, perm, force, err_flag, epart);
+                                                                   fnear, perm, force, err_flag, epart, kick_vel,
+                                                                   kick_kpart);
     } else {
         const size_t sm = sizeof(KEntry64) * kKChunk64;
         k_far_scatter64<<<bv.n_pblk, kScatterThreads, sm, st>>>(bv, sp64, ktab, fnear, perm, force, err_flag,

@@ -610,10 +610,15 @@ BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
 // Cell list + near field + far field for the current positions; total force
 // into c->force (caller order).  With a mask, only masked systems take the
 // new forces, energies and k-set.
+// fuse_kick: the FP32C scatter also runs the step's second half kick (the
+// caller then launches no kick); valid only without a boundary term, which
+// adds to the force after the scatter.
 rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_sorted,
-                            double4_32a *force_out = nullptr, bool packed = false) {
+                            double4_32a *force_out = nullptr, bool packed = false, bool fuse_kick = false) {
     const Prof *pf = prof_of(ctx);
     const int prec = ctx->precision;
+    double4_32a *kv = fuse_kick ? ctx->vel : nullptr;
+    double *kp = fuse_kick ? ctx->kpart : nullptr;
     if (ctx->use_list && !nbr_sorted) {
         // neighbour lists: caller-order fixed-point positions (written by the
         // kick-drift in a step), cell list and lists of the flagged systems,
@@ -662,7 +667,7 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
         CK(launch_rho_sweep(prec, bv, ctx->sp64, ctx->sp32c, ctx->rho_part, ctx->st, pf));
         CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
         CK(launch_far_scatter(prec, bv, ctx->sp64, ctx->sp32c, ctx->ktab, ctx->fnear, nullptr,
-                              force_out ? force_out : ctx->force, ctx->err_flag, ctx->st, pf, ctx->epart));
+                              force_out ? force_out : ctx->force, ctx->err_flag, ctx->st, pf, ctx->epart, kv, kp));
         if (ctx->any_boundary)
             CK(launch_boundary(bv, ctx->posq, ctx->dpart, ctx->dip, ctx->energy, force_out ? force_out : ctx->force,
                                ctx->st, pf));
@@ -674,7 +679,7 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
     CK(launch_rho_sweep(prec, bv, ctx->sp64, ctx->sp32, ctx->rho_part, ctx->st, pf));
     CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
     CK(launch_far_scatter(prec, bv, ctx->sp64, ctx->sp32, ctx->ktab, ctx->fnear, ctx->cb.perm,
-                          force_out ? force_out : ctx->force, ctx->err_flag, ctx->st, pf));
+                          force_out ? force_out : ctx->force, ctx->err_flag, ctx->st, pf, nullptr, kv, kp));
     if (ctx->any_boundary)
         CK(launch_boundary(bv, ctx->posq, ctx->dpart, ctx->dip, ctx->energy, force_out ? force_out : ctx->force,
                            ctx->st, pf));
@@ -698,9 +703,10 @@ rbsog_status enqueue_kick_drift(rbsog_ctx *ctx) {
 rbsog_status enqueue_step_tail(rbsog_ctx *ctx) {
     const Prof *pf = prof_of(ctx);
     const BatchView bv = view(ctx);
-    rbsog_status s = enqueue_forces(ctx, bv, nullptr, nullptr, ctx->use_list);
+    const bool fused = ctx->precision == RBSOG_FP32C && !ctx->any_boundary;
+    rbsog_status s = enqueue_forces(ctx, bv, nullptr, nullptr, ctx->use_list, fused);
     if (s != RBSOG_OK) return s;
-    CK(launch_kick(bv, ctx->vel, ctx->force, ctx->kpart, ctx->st, pf));
+    if (!fused) CK(launch_kick(bv, ctx->vel, ctx->force, ctx->kpart, ctx->st, pf));
     CK(launch_finalize(bv, ctx->epart, ctx->rho, ctx->kpart, 1, ctx->energy, 1, ctx->st, pf));
     bool thermo = false;
     for (auto &pp : ctx->p) thermo = thermo || (pp.tau_T > 0.0 && pp.thermostat != 1);

@@ -364,10 +364,15 @@ cudaError_t launch_rho_combine(int precision, const BatchView &bv, const double2
 // perm null the particles are already in caller order (neighbour-list path):
 // force[s] = fnear[s] + far, and the per-particle energies packed in
 // fnear[s].w are summed per particle block into epart[e_off + block].
+// FP32C with kick_vel non-null: the step's second half kick is fused into
+// the kernel (v += dt/2 F/m in caller order and the kinetic-energy partial
+// of each particle block into kick_kpart, the bits of launch_kick); only
+// when nothing else adds to the force afterwards.
 cudaError_t launch_far_scatter(int precision, const BatchView &bv, const double4_32a *sp64,
                                const uint4 *sp32, const void *ktab, const double4_32a *fnear,
                                const int32_t *perm, double4_32a *force, int32_t *err_flag, cudaStream_t st,
-                               const Prof *prof, double2 *epart = nullptr);
+                               const Prof *prof, double2 *epart = nullptr, double4_32a *kick_vel = nullptr,
+                               double *kick_kpart = nullptr);
 size_t ktab_bytes(int precision, int64_t nk);
 
 // ---- integrator and reductions (k_md.cu) --------------------------------------
