@@ -147,3 +147,33 @@ def test_server_cancel_waiting_and_running():
     for jid in ids:
         srv.release(jid)
     srv.close()
+
+
+@pytest.mark.parametrize("thermostat", ["langevin", "nose-hoover"])
+def test_served_thermostatted_jobs_equal_alone(thermostat):
+    """Langevin noise (keyed by the step counter) and the Nose-Hoover
+    variables (kept with the energies) move with a job when the server
+    re-batches it: each job still ends with its alone trajectory."""
+    Pk, dev = _setup()
+    jobs = [JOBS[0], JOBS[2], JOBS[4], JOBS[5]]
+    states = [I.electrolyte(j[0], j[1], seed=800 + i) for i, j in enumerate(jobs)]
+    params = []
+    for j in jobs:
+        p = _params(Pk, j[1], j[2], j[3], "fp32c", j[4], tau=0.05)
+        p.thermostat = {"langevin": 1, "nose-hoover": 2}[thermostat]
+        params.append(p)
+    srv = Pk.Server(max_jobs=2, mem_budget_bytes=8 << 30, quantum=3, device=0)
+    ids = [srv.submit(params[i], *states[i], nsteps=jobs[i][4]) for i in range(len(jobs))]
+    for _ in range(100):
+        act, wait, _ = srv.advance()
+        if act == 0 and wait == 0:
+            break
+    for i, jid in enumerate(ids):
+        st, x, v, f, e, steps = srv.result(jid)
+        assert st == 2 and steps == jobs[i][4]
+        xa, va, fa, ea, sa = _alone(Pk, dev, jobs[i], params[i], states[i])
+        for a, b in ((xa, x), (va, v), (fa, f)):
+            assert np.array_equal(a, b), (thermostat, i)
+        assert ea == e, (thermostat, i)
+        srv.release(jid)
+    srv.close()
