@@ -145,6 +145,8 @@ def lib():
             L.orc_pg_kseq.restype = C.c_int
             L.orc_far_rb_w.argtypes = [_i64, _pd, _pd, C.POINTER(OrcSys), _i32, _pi32, _pd, _pd, C.POINTER(_d)]
             L.orc_num_threads.restype = C.c_int
+            L.orc_set_num_threads.argtypes = [C.c_int]
+            L.orc_set_num_threads.restype = C.c_int
             _lib = L
     return _lib
 
@@ -539,3 +541,8 @@ def rdf(q, x, L, nbins):
 
 def num_threads():
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> int:
+    """Threads for the oracle's parallel loops; returns the previous count."""
+    return int(lib().orc_set_num_threads(int(n)))

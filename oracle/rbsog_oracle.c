@@ -51,6 +51,17 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the later parallel loops (n >= 1); the previous count is returned. */
+int orc_set_num_threads(int n) {
+    const int old = orc_num_threads();
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return old;
+}
+
 /* ------------------------------------------------------------------------
  * Sum-of-Gaussians decomposition (Sec. 2, Eqs. 2.5-2.11).
  * ------------------------------------------------------------------------ */

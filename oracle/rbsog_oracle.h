@@ -203,6 +203,7 @@ int orc_green_kubo(int64_t n_samples, const double *Pt, double dt, double V, dou
                    double *acf, double *C);
 
 int  orc_num_threads(void);
+int  orc_set_num_threads(int n);
 
 #ifdef __cplusplus
 }
