@@ -39,6 +39,8 @@ def test_full_size_forces(big, P, full, prec, tol):
     g = Pk.RBSOG(N, p, device=0)
     d = torch.device("cuda:0")
     g.set_state(torch.tensor(q, device=d), torch.tensor(x, device=d), torch.tensor(v, device=d))
+    if prec == "fp32c" and P == 500:
+        Pk.binding.rbsog_batch_autotune(g.ctx, 2)   # the benchmark's launch shapes for this workload
     m = O.kseq(sog, s.L, seed=77, n_chains=8, chain_len=(P + 7) // 8)[:P]
     f = torch.zeros((N, 3), dtype=torch.float64, device=d)
     e = Pk.binding.rbsog_compute_forces(g.ctx, m, f)
