@@ -175,26 +175,22 @@ __global__ void __launch_bounds__(kThreads) k_gk_mean(const double *__restrict__
         for (int c = 0; c < 6; ++c) mean[c] = t[c] / (double)ns;
 }
 
-// Block t: acf[t] = sum over the six components of the origin-averaged
-// product of fluctuations at lag t.
+// Block t: acf[t] = the products of fluctuations at lag t summed over the
+// six components and the origins, divided by the n - t origins.
 __global__ void __launch_bounds__(kThreads) k_gk_acf(const double *__restrict__ series, int64_t ns,
                                                      const double *__restrict__ mean, double *__restrict__ acf) {
     const int64_t t = blockIdx.x;
     double m[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) m[c] = mean[c];
-    double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, r[6];
-    for (int64_t o = threadIdx.x; o + t < ns; o += kThreads)
+    double s[1] = {0.0}, r[1];
+    for (int64_t o = threadIdx.x; o + t < ns; o += kThreads) {
+        const double *a = series + 9 * o, *b = series + 9 * (o + t);
 #pragma unroll
-        for (int c = 0; c < 6; ++c)
-            s[c] += (series[9 * o + gk_comp(c)] - m[c]) * (series[9 * (o + t) + gk_comp(c)] - m[c]);
-    block_sum<6>(s, r);
-    if (threadIdx.x == 0) {
-        double a = 0.0;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) a += r[c];
-        acf[t] = a / (double)(ns - t);
+        for (int c = 0; c < 6; ++c) s[0] += (a[gk_comp(c)] - m[c]) * (b[gk_comp(c)] - m[c]);
     }
+    block_sum<1>(s, r);
+    if (threadIdx.x == 0) acf[t] = r[0] / (double)(ns - t);
 }
 
 __global__ void __launch_bounds__(kThreads) k_gk_integral(const double *__restrict__ acf, int32_t max_lag,
