@@ -275,6 +275,8 @@ def run_ours(args, rank, world, local, dist):
     # (every ~22 steps here), so they are not counted
     gated = ("cell_bin", "cell_scan", "cell_scatter", "cell_order_gather", "list_build")
     launches_per_step = sum(c for k, (c, _) in prof.items() if not k.startswith(gated)) / K
+    if "list_build" in prof:
+        launches_per_step += 1   # the one-thread kernel that sets the rebuild node's condition
 
     # end to end through the C ABI from pinned host buffers: per step the
     # state (q, x, v, f) goes host->device, one step runs, (x, v, f) comes
