@@ -428,7 +428,8 @@ rbsog_status rbsog_rdf(rbsog_ctx *ctx, int32_t nbins, uint64_t *counts, double *
  * retirements rebuild the batch at the next quantum, moving the running
  * jobs' state device to device.  Each job's trajectory is the one it would
  * follow alone (same parameters and seed).  All jobs of a server share b,
- * sigma, omega0, M, r_c, P and precision.  Host memory for inputs is copied
+ * sigma, omega0, M, r_c, P, precision, sampler, near_kernel and r_in (those
+ * of the first job submitted).  Host memory for inputs is copied
  * at submit; results stay on the host until released. */
 typedef struct rbsog_server rbsog_server;
 /* max_jobs >= 1 slots, mem_budget_bytes > 0, quantum >= 1 steps per advance. */
@@ -436,7 +437,8 @@ rbsog_status rbsog_server_create(rbsog_server **out, int32_t max_jobs, int64_t m
                                  int32_t quantum, int device, void *stream);
 /* Queue a job: q[n], x[n][3], v[n][3] (NULL: zero) in host memory; the
  * sequence length is set to nsteps + 1.  RBSOG_ENOMEM if the job alone
- * exceeds the budget. */
+ * exceeds the budget; RBSOG_EINVAL if a shared parameter differs from the
+ * first job's. */
 rbsog_status rbsog_server_submit(rbsog_server *s, int64_t n, const rbsog_params *p, const double *q,
                                  const double *x, const double *v, int64_t nsteps, int64_t *job_id);
 /* Admit what fits, rebuild the batch if its membership changed, advance it

@@ -2233,6 +2233,8 @@ struct rbsog_server {
     rbsog_ctx *batch = nullptr;
     int64_t frozen_n = 0;             // particles of retired jobs still in the batch
     int64_t next_id = 1;
+    bool have_shape = false;          // the parameters every job must share (set by the first submit)
+    rbsog_params shape{};
     std::string err;
 };
 
@@ -2395,6 +2397,17 @@ rbsog_status rbsog_server_submit(rbsog_server *s, int64_t n, const rbsog_params 
     else j.v.assign(3 * n, 0.0);
     j.footprint = footprint_bytes(j);
     if (j.footprint > s->budget) return srv_fail(s, RBSOG_ENOMEM, "job larger than the memory budget");
+    // jobs run together in one batch, which shares these parameters
+    const rbsog_params &h = s->shape;
+    if (s->have_shape && (p->b != h.b || p->sigma != h.sigma || p->omega0 != h.omega0 || p->M != h.M ||
+                          p->r_c != h.r_c || p->P != h.P || p->precision != h.precision ||
+                          p->sampler != h.sampler || p->near_kernel != h.near_kernel || p->r_in != h.r_in))
+        return srv_fail(s, RBSOG_EINVAL, "b, sigma, omega0, M, r_c, P, precision, sampler, near_kernel and r_in "
+                                         "must match the server's first job");
+    if (!s->have_shape) {
+        s->shape = *p;
+        s->have_shape = true;
+    }
     if (job_id) *job_id = j.id;
     s->waiting.push_back(j.id);
     s->jobs[j.id] = std::move(j);

@@ -106,7 +106,11 @@ def test_server_rejects_invalid_jobs():
     big = I.electrolyte(64000, 50.4, seed=2)
     with pytest.raises(B.RBSOGError):
         srv.submit(_params(Pk, 50.4, 1.0, 1, "fp32c", 5), *big, nsteps=5)
+    p_other = _params(Pk, 12.6, 1.0, 1, "fp32c", 5)
+    p_other.P = 32                                 # the server's jobs share P (set by the first job)
     jid = srv.submit(p, q, x, v, nsteps=5)
+    with pytest.raises(B.RBSOGError):
+        srv.submit(p_other, q, x, v, nsteps=5)
     assert srv.result(jid)[0] == 0
     with pytest.raises(B.RBSOGError):
         srv.release(jid)           # not finished
