@@ -136,3 +136,18 @@ def test_observer_argument_checks():
     g.close()
     with pytest.raises(B.RBSOGError):
         B.rbsog_green_kubo(np.zeros((10, 9)), 0.1, 1.0, 1.0, 11)
+
+
+def test_observables_need_a_single_system():
+    Pk, dev = _setup()
+    B = Pk.binding
+    systems = [(1000, 12.6), (2000, 15.874)]
+    params = [Pk.make_params(L, 16, n_ksets=3, seed=5 + i) for i, (_, L) in enumerate(systems)]
+    b = Pk.Batch([N for N, _ in systems], params, device=0)
+    for i, (N, L) in enumerate(systems):
+        b.set_state(i, *(torch.tensor(a, device=dev) for a in I.electrolyte(N, L, seed=90 + i)))
+    with pytest.raises(B.RBSOGError):
+        B.rbsog_observe_start(b.ctx, 8, 1)
+    with pytest.raises(B.RBSOGError):
+        B.rbsog_compute_pressure(b.ctx, np.ones((16, 3), dtype=np.int32))
+    b.close()
