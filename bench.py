@@ -710,6 +710,7 @@ def run_reference(args, rank, world, sample=65536):
     x, v, f, _ = O.md(s, q, x, v, S, P, ks[used * P:], K, 0.001, f=f)
     el = time.perf_counter() - t0
     val = ns * K / el
+    smalls = oracle_small_configs(O, sog)
     return {"metric": METRIC, "value": val, "unit": "particle-steps/s", "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": el / K * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
@@ -719,7 +720,42 @@ def run_reference(args, rank, world, sample=65536):
                              "sample": f"{K} full FP64 oracle steps of the same electrolyte at density 0.5 "
                                        f"with {ns} particles (L={Ls:.3f}), P={P}, on the host cores"},
             "e2e": {"value": val, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+                    "d2h_bytes_per_step": 0},
+            "oracle_configs": smalls}
+
+
+def oracle_small_configs(O, sog):
+    """The oracle on the smaller workloads, timed on the host cores: the
+    1000-ion electrolyte (L = 12.6, P = 100) for one force evaluation and 10
+    velocity-Verlet steps, the 64,000-ion one (L = 50.4, P = 200) for one
+    force evaluation and 10 steps, and one force evaluation per P in
+    {100, 500, 2000} on a 65,536-ion sample of the 1,048,576-ion workload
+    (L scaled to density 0.5; per particle-step, so it extrapolates to the
+    full size)."""
+    out = {}
+    for name, n, L, P in (("N1000_L12.6_P100", 1000, 12.6, 100), ("N64000_L50.4_P200", 64000, 50.4, 200)):
+        q, x, v = electrolyte_state(n, L, seed=7)
+        s = O.System((L, L, L), sog, 3.0, 1.0, 1.0, 1.0)
+        ks = O.kseq(sog, s.L, seed=5, n_chains=8, chain_len=(P * 11 + 7) // 8)
+        t0 = time.perf_counter()
+        x, v, f, _ = O.md(s, q, x, v, s.S(), P, ks, 0, 0.001)
+        t1 = time.perf_counter()
+        O.md(s, q, x, v, s.S(), P, ks[P:], 10, 0.001, f=f)
+        t2 = time.perf_counter()
+        out[name] = {"force_eval_s": t1 - t0, "steps": 10, "particle_steps_per_s": n * 10 / (t2 - t1)}
+    ns = 65536
+    Ls = 128.0 * (ns / 1048576) ** (1.0 / 3.0)
+    q, x, v = electrolyte_state(ns, Ls, seed=9)
+    s = O.System((Ls, Ls, Ls), sog, 3.0, 1.0, 1.0, 1.0)
+    for P in (100, 500, 2000):
+        ks = O.kseq(sog, s.L, seed=5, n_chains=8, chain_len=(P + 7) // 8)
+        t0 = time.perf_counter()
+        O.md(s, q, x, v, s.S(), P, ks, 0, 0.001)
+        el = time.perf_counter() - t0
+        out[f"N1048576_P{P}_sample65536"] = {"force_eval_s": el, "particle_steps_per_s": ns / el,
+                                             "extrapolated_full_step_s": el * 1048576 / ns}
+    out["cores"] = O.num_threads()
+    return out
 
 
 def main():
