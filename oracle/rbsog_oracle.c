@@ -368,33 +368,25 @@ void orc_wrap(int64_t n, double *x, const double L[3]) {
         }
 }
 
-/* Cells of side h_d = L_d / n_d with n_d = floor(L_d / r_c) >= 3.  A particle
- * at wrapped x goes to c_d = floor(x_d * (n_d / L_d)) (clamped to [0, n_d - 1]), cell id
- * (c_z n_y + c_y) n_x + c_x.  Members of a cell are listed by increasing
- * fixed-point x coordinate X = trunc(x (2^32 / L_x)) (clamped to [0, 2^32 - 1]),
- * ties by increasing particle index: the order along an x-row of cells is
- * then the order in x.  Returns -1 if some n_d < 3. */
-static uint32_t cell_key_x(double x, double Lx) {
-    double t = x * (4294967296.0 / Lx);
-    if (t < 0.0) t = 0.0;
-    if (t > 4294967295.0) t = 4294967295.0;
-    return (uint32_t)t;
-}
-
+/* Cells of side h_d = L_d / n_d with n_d = floor(L_d / r_c) >= 3 (the cell
+ * list that makes the near-field sum of Eq. 3.9 O(N), Sec. 3.4).  A particle
+ * at wrapped x goes to c_d = floor(x_d / h_d) (clamped to [0, n_d - 1]), cell
+ * id (c_z n_y + c_y) n_x + c_x.  Members of a cell are listed in increasing
+ * particle index.  Returns -1 if some n_d < 3. */
 int orc_cell_list(int64_t n, const double *x, const double L[3], double rc,
                   int32_t *ncell, int32_t *cell_of, int32_t *cell_start, int32_t *perm) {
-    double inv_h[3];
+    double h[3];
     for (int d = 0; d < 3; ++d) {
         ncell[d] = (int32_t)floor(L[d] / rc);
         if (ncell[d] < 3) return -1;
-        inv_h[d] = (double)ncell[d] / L[d];
+        h[d] = L[d] / (double)ncell[d];
     }
     int64_t nc = (int64_t)ncell[0] * ncell[1] * ncell[2];
     for (int64_t c = 0; c <= nc; ++c) cell_start[c] = 0;
     for (int64_t i = 0; i < n; ++i) {
         int32_t c3[3];
         for (int d = 0; d < 3; ++d) {
-            int32_t c = (int32_t)floor(x[3 * i + d] * inv_h[d]);
+            int32_t c = (int32_t)floor(x[3 * i + d] / h[d]);
             if (c >= ncell[d]) c = ncell[d] - 1;
             if (c < 0) c = 0;
             c3[d] = c;
@@ -404,24 +396,12 @@ int orc_cell_list(int64_t n, const double *x, const double L[3], double rc,
     }
     for (int64_t c = 0; c < nc; ++c) cell_start[c + 1] += cell_start[c];
     int32_t *fill = (int32_t *)calloc((size_t)(nc > 0 ? nc : 1), sizeof(int32_t));
-    for (int64_t i = 0; i < n; ++i) {          /* members in index order */
+    for (int64_t i = 0; i < n; ++i) {
         int32_t c = cell_of[i];
         perm[cell_start[c] + fill[c]] = (int32_t)i;
         fill[c] += 1;
     }
     free(fill);
-    for (int64_t c = 0; c < nc; ++c) {         /* stable insertion sort by X */
-        for (int32_t a = cell_start[c] + 1; a < cell_start[c + 1]; ++a) {
-            const int32_t v = perm[a];
-            const uint32_t kv = cell_key_x(x[3 * (int64_t)v], L[0]);
-            int32_t b = a - 1;
-            while (b >= cell_start[c] && cell_key_x(x[3 * (int64_t)perm[b]], L[0]) > kv) {
-                perm[b + 1] = perm[b];
-                --b;
-            }
-            perm[b + 1] = v;
-        }
-    }
     return 0;
 }
 

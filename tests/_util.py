@@ -95,3 +95,25 @@ def nacl(n_side: int, a: float):
     idx = np.array([[i, j, k] for i in range(n_side) for j in range(n_side) for k in range(n_side)])
     q = np.where(idx.sum(1) % 2 == 0, 1.0, -1.0)
     return q, (idx + 0.5) * a
+
+
+def rms_rel(a, b):
+    """Global RMS relative error sqrt(sum |a_i - b_i|^2 / sum |b_i|^2)."""
+    return math.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2))
+
+
+def per_particle_rel(a, b):
+    """Per-particle relative force errors |a_i - b_i| / (|b_i| + median_j |b_j|):
+    the median in the denominator keeps particles whose force nearly cancels
+    from reading as large relative errors, while one particle off by a
+    fraction of a typical force still shows.  Returns (median, max)."""
+    nb = np.linalg.norm(b, axis=1)
+    e = np.linalg.norm(a - b, axis=1) / (nb + np.median(nb))
+    return float(np.median(e)), float(e.max())
+
+
+# per-particle bars: FP64 within 1e-9 of a typical force at every particle;
+# FP32C within 1e-4 (the combined near table's worst case is 6.1e-7 of G(0),
+# the far field's 24-bit angles and hardware sin/cos about 1e-6 per term)
+PP_FP64 = 1e-9
+PP_FP32C = 1e-4

@@ -157,20 +157,30 @@ def test_self_energy_closed_form():
 
 
 def test_cell_list_matches_binning():
+    """Cells of side h = L / floor(L / r_c): particle i goes to floor(x / h)
+    per axis, members of a cell in increasing index (a stable sort of the
+    cell ids), cell_start the prefix sum of the counts."""
     L = 12.6
     q, x, _ = I.electrolyte(1000, L, seed=3)
     nc, cell_of, start, perm = O.cell_list(x, (L, L, L), 3.0)
     assert list(nc) == [4, 4, 4]
-    c = np.minimum(np.floor(x * (4 / L)).astype(int), 3)
+    h = L / 4
+    c = np.minimum(np.floor(x / h).astype(int), 3)
     ref = (c[:, 2] * 4 + c[:, 1]) * 4 + c[:, 0]
     assert np.array_equal(cell_of, ref)
-    # within a cell: increasing fixed-point x, ties by index
-    X = np.clip(x[:, 0] * (4294967296.0 / L), 0.0, 4294967295.0).astype(np.uint64)
-    assert np.array_equal(perm, np.lexsort((np.arange(len(x)), X, ref)))
-    xs = x[perm]
-    for c in range(64):   # x increases along each cell's member list
-        assert np.all(np.diff(xs[start[c]:start[c + 1], 0]) >= 0)
+    assert np.array_equal(perm, np.argsort(ref, kind="stable"))
     assert np.array_equal(start, np.r_[0, np.cumsum(np.bincount(ref, minlength=64))])
+    # a cuboid box with unequal cell counts per axis
+    Lv = (9.3, 12.0, 15.1)
+    rng = np.random.default_rng(8)
+    x = rng.uniform(0, 1, size=(500, 3)) * np.array(Lv)
+    nc, cell_of, start, perm = O.cell_list(x, Lv, 3.0)
+    n3 = np.floor(np.array(Lv) / 3.0).astype(int)
+    assert list(nc) == list(n3)
+    c = np.minimum(np.floor(x / (np.array(Lv) / n3)).astype(int), n3 - 1)
+    ref = (c[:, 2] * n3[1] + c[:, 1]) * n3[0] + c[:, 0]
+    assert np.array_equal(cell_of, ref)
+    assert np.array_equal(perm, np.argsort(ref, kind="stable"))
 
 
 def test_neighbour_counts_match_bruteforce():
