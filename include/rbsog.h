@@ -268,18 +268,18 @@ rbsog_status rbsog_get_profile(rbsog_ctx *ctx, int32_t cap, char (*names)[32], i
  * example work being recorded into a stream capture) or an embedding host
  * whose allocator must not be re-entered or has a fixed budget.
  *
- * Computes rho(k) = sum_j q_j e^{i k . r_j}, k = 2 pi m / L (Eq. 3.4), in
- * FP64, exactly like rbsog_rho but without a context: q[n], x[n][3] (any
- * real positions), m[P][3] and rho_out[P][2] (Re, Im) are caller-owned
- * DEVICE buffers on the current device; L[3] is host memory.  Work is
- * enqueued on `stream` (cudaStream_t, NULL = legacy default stream); the
- * call does not synchronise.
+ * Computes the same structure factors as rbsog_rho, in FP64, but without a
+ * context: q[n], x[n][3] (any real positions), m[P][3] and rho_out[P][2]
+ * (Re, Im) are caller-owned DEVICE buffers on the current device; L[3] is
+ * host memory.  Work is enqueued on `stream` (cudaStream_t, NULL = legacy
+ * default stream); the call does not synchronise.
  *
  * It allocates nothing: its partial sums live in a file-scope device array
  * of RBSOG_NOALLOC_MAX_P * 64 complex FP64 values (2 MiB) that every GPU
- * which loads the library holds until the process exits.  The first call on
- * a device looks up that array's device address (cudaGetSymbolAddress, with
- * the device current); make that first call before any stream capture.  All
+ * which loads the library holds until the process exits.  The first call in
+ * a CUDA context (per device; again after that device's context was reset)
+ * looks up the array's device address with cudaGetSymbolAddress, with the
+ * device current; make that first call before any stream capture.  All
  * calls share the array: calls whose work overlaps on the GPU (different
  * streams, or host threads) race and must be ordered by the caller.  Each
  * call overwrites every partial it reads, so no clearing is needed.

@@ -64,7 +64,7 @@ class rbsog_energies(C.Structure):
 class rbsog_info(C.Structure):
     _fields_ = [("sigma", C.c_double), ("omega0", C.c_double), ("S", C.c_double),
                 ("M", C.c_int32), ("ncell", C.c_int32 * 3), ("n_chains", C.c_int64),
-                ("chain_len", C.c_int32), ("P_set", C.c_int32)]
+                ("chain_len", C.c_int32), ("P_set", C.c_int32), ("list_builds", C.c_int64)]
 
 
 def _load():
@@ -307,16 +307,48 @@ def rbsog_get_profile(ctx, cap: int = 64):
 RBSOG_NOALLOC_MAX_P = 2048
 
 
+def _device_tensor(t, name, dtype, shape):
+    """t must be a contiguous torch CUDA tensor on the current device with the
+    given dtype and shape: the allocation-free entry point reads and writes
+    raw device addresses, so a host array or a short buffer must not reach it."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name}: a torch CUDA tensor is required")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: tensor on cuda:{t.device.index}, current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: tensor must be contiguous")
+    return t.data_ptr()
+
+
 def rbsog_rho_noalloc(q, x, L, m, rho_out, stream=None):
     """rho(k) from caller-owned device buffers with no device allocation
-    (see include/rbsog.h); P = m.shape[0] must not exceed RBSOG_NOALLOC_MAX_P."""
-    P = int(m.shape[0])
+    (see include/rbsog.h).  q[n] and x[n, 3] float64, m[P, 3] int32 and
+    rho_out[P, 2] float64 must be contiguous CUDA tensors on the current
+    device; P must not exceed RBSOG_NOALLOC_MAX_P."""
+    import torch
+    if not hasattr(x, "shape") or len(x.shape) != 2:
+        raise ValueError("x: expected shape (n, 3)")
+    n = int(x.shape[0])
+    P = int(m.shape[0]) if hasattr(m, "shape") else -1
+    if n < 1 or P < 1:
+        raise ValueError("need n >= 1 particles and P >= 1 frequencies")
+    if P > RBSOG_NOALLOC_MAX_P:
+        raise RBSOGError(1, f"rbsog_rho_noalloc: P={P} exceeds the allocation-free maximum of "
+                            f"{RBSOG_NOALLOC_MAX_P}")
+    pq = _device_tensor(q, "q", torch.float64, (n,))
+    px = _device_tensor(x, "x", torch.float64, (n, 3))
+    pm = _device_tensor(m, "m", torch.int32, (P, 3))
+    po = _device_tensor(rho_out, "rho_out", torch.float64, (P, 2))
     Lc = (C.c_double * 3)(*[float(v) for v in L])
-    s = _lib.rbsog_rho_noalloc(int(x.shape[0]), _ptr(q), _ptr(x), Lc, _ptr(m), P, _ptr(rho_out), stream)
+    s = _lib.rbsog_rho_noalloc(n, pq, px, Lc, pm, P, po, stream)
     if s != 0:
-        why = (f"P={P} exceeds the allocation-free maximum of {RBSOG_NOALLOC_MAX_P}"
-               if P > RBSOG_NOALLOC_MAX_P else "invalid argument or CUDA failure")
-        raise RBSOGError(s, f"rbsog_rho_noalloc: {why}")
+        raise RBSOGError(s, "rbsog_rho_noalloc: invalid argument or CUDA failure")
 
 
 def rbsog_measure_peaks(device: int = 0):

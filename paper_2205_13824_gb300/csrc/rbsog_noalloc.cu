@@ -9,6 +9,7 @@
 // part of the loaded library.  It computes the same quantity as rbsog_rho
 // (FP64), with a sweep kernel whose blocks each loop over a fixed number of
 // particle tiles so that the number of partials does not grow with n.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -110,11 +111,42 @@ __global__ void __launch_bounds__(256) k_rho_groups_combine(int32_t P, const dou
     }
 }
 
-// Device address of the scratch array, looked up once per device (with that
-// device current) the first time the entry point runs on it.
+// Device address of the scratch array, looked up once per CUDA context
+// (with that context's device current) the first time the entry point runs
+// in it.  The address belongs to the module loaded into that context: after
+// a cudaDeviceReset the device gets a new primary context and the array a
+// new address, so the cache is keyed on the context's unique id.
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
-double2 *g_scratch_ptr[kMaxDevices] = {};
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    double2 *ptr;
+};
+ScratchSlot g_scratch[kMaxDevices] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique id of the current context (0 when none is current or on failure),
+// through the driver entry points the runtime exposes.
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return 0;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 }  // namespace
 
@@ -125,15 +157,23 @@ extern "C" rbsog_status rbsog_rho_noalloc(int64_t n, const double *q, const doub
     if (!(L[0] > 0.0) || !(L[1] > 0.0) || !(L[2] > 0.0)) return RBSOG_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RBSOG_ECUDA;
+    unsigned long long ctx_id = current_ctx_id();
+    if (ctx_id == 0) {   // no context current yet: make the device's primary context current
+        if (cudaSetDevice(dev) != cudaSuccess) return RBSOG_ECUDA;
+        ctx_id = current_ctx_id();
+        if (ctx_id == 0) return RBSOG_ECUDA;
+    }
     double2 *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_scratch_mu);
-        if (!g_scratch_ptr[dev]) {
+        ScratchSlot &sl = g_scratch[dev];
+        if (!sl.ptr || sl.ctx_id != ctx_id) {
             void *ptr = nullptr;
             if (cudaGetSymbolAddress(&ptr, g_rho_scratch) != cudaSuccess || !ptr) return RBSOG_ECUDA;
-            g_scratch_ptr[dev] = static_cast<double2 *>(ptr);
+            sl.ptr = static_cast<double2 *>(ptr);
+            sl.ctx_id = ctx_id;
         }
-        scratch = g_scratch_ptr[dev];
+        scratch = sl.ptr;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     dim3 grid(kGroups, (unsigned)((P + kKTile - 1) / kKTile));
