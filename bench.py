@@ -215,6 +215,33 @@ def load_peaks():
         return {}
 
 
+def rel_errors(f, fo, e=None, eo=None):
+    """RMS relative force error, per-particle median and max of
+    |F_i - F_ref,i| / (|F_ref,i| + median_j |F_ref,j|), and the relative
+    error of the total potential energy U_near + U_far - U_self + U_wca."""
+    import numpy as np
+    nb = np.linalg.norm(fo, axis=1)
+    pp = np.linalg.norm(f - fo, axis=1) / (nb + np.median(nb))
+    out = {"rms_rel_force": float(np.sqrt(np.sum((f - fo) ** 2) / np.sum(fo ** 2))),
+           "per_particle_median": float(np.median(pp)), "per_particle_max": float(pp.max())}
+    if e is not None and eo is not None:
+        U = e["U_near"] + e["U_far"] - e["U_self"] + e["U_wca"]
+        Uo = eo["U_near"] + eo["U_far"] - eo["U_self"] + eo["U_wca"]
+        out["rel_energy"] = abs(U - Uo) / abs(Uo)
+    return out
+
+
+def sig(v, digits=4):
+    """Round floats (recursively) to a few significant digits for the JSON line."""
+    if isinstance(v, float):
+        return float(f"{v:.{digits}g}")
+    if isinstance(v, dict):
+        return {k: sig(x, digits) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [sig(x, digits) for x in v]
+    return v
+
+
 def run_ours(args, rank, world, local, dist):
     import numpy as np
     import torch
@@ -226,7 +253,8 @@ def run_ours(args, rank, world, local, dist):
     N, L, P, K, W = args.N, args.L, args.P, args.steps, args.warmup
     q, x, v = electrolyte_state(N, L, seed=2024 + rank)
     n_e2e = max(3, min(K, 10))
-    need = W + 2 * K + n_e2e + 8
+    n_long = 0 if args.quick else 220
+    need = W + 2 * K + n_e2e + n_long + 8
     p32 = Pk.make_params(L, P, n_ksets=need, seed=17 + rank, precision="fp32c")
     g = Pk.RBSOG(N, p32, device=local)
     tq, tx, tv = (torch.tensor(a, device=dev) for a in (q, x, v))
@@ -246,19 +274,33 @@ def run_ours(args, rank, world, local, dist):
     barrier()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    builds0 = g.info()[0].list_builds
     clk = Clocks(local)
     with clk:
         barrier()
-        t_wall = time.perf_counter()
         e0.record(stream)
         g.step(K)
         e1.record(stream)
         torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall
         barrier()
     ms = e0.elapsed_time(e1) / K
     clocks = clk.summary()
     ms = max_over_ranks([ms], dist, dev)[0]
+    rebuilds_in_window = g.info()[0].list_builds - builds0
+
+    # a longer graph-replayed window: the neighbour-list rebuild interval and
+    # the per-step time with rebuilds in their long-run proportion
+    amort = None
+    if n_long:
+        b0 = g.info()[0].list_builds
+        e0.record(stream)
+        g.step(n_long)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        nb = g.info()[0].list_builds - b0
+        ms_long = e0.elapsed_time(e1) / n_long
+        amort = {"steps": n_long, "rebuilds": nb, "steps_per_rebuild": (n_long / nb) if nb else None,
+                 "ms_per_step": ms_long, "value": whole_job_value(N, world, ms_long / 1e3)}
 
     # per-kernel CUDA-event timing over K more steps (eager launches)
     B.rbsog_set_profiling(g.ctx, True)
@@ -277,6 +319,11 @@ def run_ours(args, rank, world, local, dist):
     launches_per_step = sum(c for k, (c, _) in prof.items() if not k.startswith(gated)) / K
     if "list_build" in prof:
         launches_per_step += 1   # the one-thread kernel that sets the rebuild node's condition
+    gpu_launches = int(round(launches_per_step * K))
+    if rebuilds_in_window:
+        per_build = sum(c for k, (c, _) in prof.items() if k.startswith(gated)) / max(1, prof.get(
+            "list_build", (1, 0))[0])
+        gpu_launches += int(round(per_build * rebuilds_in_window))
 
     # end to end through the C ABI from pinned host buffers: per step the
     # state (q, x, v, f) goes host->device, one step runs, (x, v, f) comes
@@ -295,10 +342,6 @@ def run_ours(args, rank, world, local, dist):
     t_e2e = max_over_ranks([t_e2e], dist, dev)[0]
     g.close()
 
-    extras = {}
-    if not args.quick and rank == 0:
-        extras = run_extras(args, q, x, v, dev)
-
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6686.1)
     lists = "list_build" in prof
@@ -308,7 +351,10 @@ def run_ours(args, rank, world, local, dist):
                 if k.startswith(("rho_sweep", "far_scatter"))]
     roof_near = [roofline_for(k, c, t, N, L, P, 3.0, meas, hbm, lists) for k, (c, t) in prof.items()
                  if k.startswith("near")]
-    kernels = {k: {"launches": c, "ms_per_launch": t / c, "share": t / sum(tt for _, tt in prof.values())}
+    roof_build = [roofline_for(k, c, t, N, L, P, 3.0, meas, hbm, lists) for k, (c, t) in prof.items()
+                  if k.startswith("list_build")]
+    tot = sum(tt for _, tt in prof.values())
+    kernels = {k: {"launches": c, "ms_per_launch": t / c, "share": t / tot}
                for k, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     value = whole_job_value(N, world, ms / 1e3)
     line = {
@@ -322,29 +368,47 @@ def run_ours(args, rank, world, local, dist):
                    "autotuned": tuned},
         "e2e": {"value": whole_job_value(N, world, t_e2e), "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(round(launches_per_step * K)),
-        "gpu_launches_note": "per step: the kernels outside the conditional rebuild node; rebuild steps "
-                             "add the cell-list and list-build kernels",
+        "gpu_launches": gpu_launches,
         "roofline": roof,
-        "roofline_far_field": roof_far,
-        "roofline_near_field": roof_near,
+        "clocks": clocks,
+    }
+    head = {"fp32c": {"value": value, "ms_per_step": ms, "rebuilds_in_window": rebuilds_in_window}}
+    if amort:
+        head["fp32c"]["long_window"] = amort
+    extras = {}
+    if not args.quick and rank == 0:
+        extras = run_extras(args, q, x, v, dev)
+        line["cpu_baseline"] = extras.pop("cpu_baseline")
+    line.update({
+        "gpu_launches_note": "graph-replayed steps: the kernels outside the conditional rebuild node, plus the "
+                             "cell-list and list-build kernels of the rebuilds inside the window",
+        "roofline_far_field": sig(roof_far),
+        "roofline_near_field": sig(roof_near),
+        "roofline_list_build": sig(roof_build),
         "near_field_method": "neighbour lists, skin r_c/10, rebuilt on a displacement test" if lists
                              else "cell stencil",
-        "measured_peaks": {"mufu_per_s": meas["mufu_per_s"], "fma32_per_s": meas["fma32_per_s"],
-                           "fma64_per_s": meas["fma64_per_s"], "sm_mhz": meas["sm_mhz"]},
-        "clocks": clocks,
-        "kernels": kernels,
+        "measured_peaks": sig({"mufu_per_s": meas["mufu_per_s"], "fma32_per_s": meas["fma32_per_s"],
+                               "fma64_per_s": meas["fma64_per_s"], "sm_mhz": meas["sm_mhz"],
+                               "sm_count": meas.get("sm_count")}),
+        "kernels": sig(kernels, 3),
         "ms_per_step_eager_profiled": ms_prof,
-    }
-    line.update(extras)
-    if rank == 0 and not args.quick:
-        line["cpu_baseline"] = cpu_baseline(N, L, P, q, x, v)
+    })
+    hl = extras.pop("headline", {})
+    line.update(sig(extras))
+    head.update(hl)
+    head["far_field_frac"] = {r["kernel"]: sig(r["frac"], 3) for r in roof_far}
+    head["near_field_frac"] = {r["kernel"]: sig(r["frac"], 3) for r in roof_near}
+    head["list_build_frac"] = {r["kernel"]: sig(r.get("frac"), 3) for r in roof_build}
+    # the compact summary goes last, so that it survives when only the end
+    # of a long line is kept
+    line["headline"] = sig(head)
     return line, rank
 
 
 def run_extras(args, q, x, v, dev):
-    """FP64 comparator path at the same workload, the FP32C-vs-FP64 force
-    error on one shared k-set, and the P sweep of the FP32C path."""
+    """FP64 comparator path at the same workload; the FP32C and FP64 forces
+    and energies on one k-set against the FP64 oracle (timed on the host
+    cores: the CPU baseline); the P sweep of the FP32C path; the options."""
     import numpy as np
     import torch
 
@@ -355,17 +419,21 @@ def run_extras(args, q, x, v, dev):
     tq, tx, tv = (torch.tensor(a, device=dev) for a in (q, x, v))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     st = torch.cuda.current_stream()
+    base, m, f_o, e_o = cpu_baseline(N, L, P, q, x, v)
+    out["cpu_baseline"] = base
     K64 = max(2, min(args.steps, 5))
     g64 = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=K64 + 4, seed=17, precision="fp64"), device=dev.index)
     g32 = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=4, seed=17, precision="fp32c"), device=dev.index)
     g64.set_state(tq, tx, tv)
     g32.set_state(tq, tx, tv)
-    m = g64.kseq(0, 1)
     f64 = torch.zeros((N, 3), dtype=torch.float64, device=dev)
     f32 = torch.zeros_like(f64)
-    B.rbsog_compute_forces(g64.ctx, m, f64)
-    B.rbsog_compute_forces(g32.ctx, m, f32)
-    err = float(torch.sqrt(((f32 - f64) ** 2).sum() / (f64 ** 2).sum()))
+    e64 = B.rbsog_compute_forces(g64.ctx, m, f64)
+    e32 = B.rbsog_compute_forces(g32.ctx, m, f32)
+    f64n, f32n = f64.cpu().numpy(), f32.cpu().numpy()
+    err32 = rel_errors(f32n, f_o, e32, e_o)
+    err64 = rel_errors(f64n, f_o, e64, e_o)
+    err32_64 = rel_errors(f32n, f64n, e32, e64)
     g32.close()
     g64.step(1)
     torch.cuda.synchronize()
@@ -377,7 +445,13 @@ def run_extras(args, q, x, v, dev):
     g64.close()
     out["fp64_path"] = {"value": N / (ms64 / 1e3), "unit": "particle-steps/s", "ms_per_step": ms64,
                         "steps": K64, "dtype": "f64"}
-    out["fp32c_vs_fp64_rms_rel_force_err"] = err
+    acc = {"k_set": f"one k-set of P={P} from the oracle's sampler, initial state of the workload",
+           "particles": N, "fp32c_vs_oracle": err32, "fp64_vs_oracle": err64, "fp32c_vs_fp64_gpu": err32_64}
+    out["accuracy"] = acc
+    out["headline"] = {"fp64": {"value": N / (ms64 / 1e3), "ms_per_step": ms64},
+                       "fp32c_vs_oracle": err32, "fp64_vs_oracle": {k: err64[k] for k in ("rms_rel_force",
+                                                                                         "per_particle_max",
+                                                                                         "rel_energy")}}
     sweep = {}
     for Ps in (100, 500, 2000):
         if Ps == P:
@@ -438,8 +512,16 @@ def run_extras(args, q, x, v, dev):
                                    "near_ms": near_c[1] / near_c[0]}
     g.close()
     out.update(run_dynamics_extras(args, tq, tx, tv, dev))
-    out["batched_replicas"] = run_replicas(args, dev)
-    out["serving"] = run_serving(dev)
+    rep = run_replicas(dev)
+    out["batched_replicas"] = rep
+    srv = run_serving(dev)
+    out["serving"] = srv
+    cb = srv["continuous_batching"]
+    out["headline"]["replicas"] = {"value": rep["value"], "ms_per_step": rep["ms_per_step"], "steps": rep["steps"]}
+    out["headline"]["serving"] = {"jobs": srv["jobs"], "p50_s": cb["latency_p50_s"], "p99_s": cb["latency_p99_s"],
+                                  "served_particle_steps_per_s": cb["served_particle_steps_per_s"],
+                                  "fp64_one_at_a_time_p50_s": srv["one_at_a_time_fp64"]["latency_p50_s"],
+                                  "fp64_one_at_a_time_p99_s": srv["one_at_a_time_fp64"]["latency_p99_s"]}
     return out
 
 
@@ -501,11 +583,11 @@ def run_dynamics_extras(args, tq, tx, tv, dev):
     return out
 
 
-def serve_trace(Pk, trace, states, P, max_jobs, quantum):
+def serve_trace(Pk, trace, states, P, max_jobs, quantum, budget):
     """Replay a job trace in real time through one server: jobs are
     submitted when their arrival time has passed; latency = completion -
     arrival (wall clock)."""
-    srv = Pk.Server(max_jobs=max_jobs, mem_budget_bytes=64 << 30, quantum=quantum)
+    srv = Pk.Server(max_jobs=max_jobs, mem_budget_bytes=budget, quantum=quantum)
     lat, pending = [], {}
     nxt = 0
     t0 = time.perf_counter()
@@ -541,90 +623,81 @@ def fifo_latencies(arrivals, service):
     return lat
 
 
-def run_serving(dev, n_jobs=64, P=200):
-    """Continuous batching under Poisson job traces (rbsog_inputs.job_trace):
-    N log-uniform in [500, 200000] at density 0.5, 100-1000 steps, P = 200,
-    FP32C -- the serving workload's size and length mix with the step counts
-    cut tenfold so that a trace replays in seconds.  Two arrival rates: 50
-    jobs/s (offered load above capacity) and 10 jobs/s.  Against it: the same
-    50/s trace served one job at a time (FP32C, measured), and one job at a
-    time in FP64 (estimated: FIFO queue over the measured FP64 step times of
-    each job size class)."""
+SERVE_JOBS, SERVE_RATE, SERVE_BUDGET = 200, 50.0, 150 * 10 ** 9
+
+
+def run_serving(dev, n_jobs=SERVE_JOBS, P=200):
+    """The serving workload as specified: Poisson arrivals at 50 jobs/s, N
+    log-uniform in [500, 200000] at density 0.5, steps uniform in [100,
+    10000], P = 200, FP32C, device-memory budget 150 GB; a seeded trace of
+    n_jobs jobs replayed in real time through continuous batching.  Against
+    it: the same jobs one at a time in FP64, FIFO in arrival order, with each
+    job's service time = its step count x its own FP64 step time measured on
+    the device (the job's state, 5 graph-replayed steps after one warm-up);
+    the full FP64 runs would take hours, so this part is extrapolated per job
+    and labelled so."""
     import numpy as np
     import torch
 
     import paper_2205_13824_gb300 as Pk
     import rbsog_inputs as I
-    out = {"jobs": n_jobs, "P": P, "N_range": [500, 200000], "steps_range": [100, 1000],
-           "precision": "fp32c", "quantum_steps": 25}
-    states_cache = {}
-
-    def states_for(trace):
-        res = []
-        for j in trace:
-            key = (j["N"], j["seed"])
-            if key not in states_cache:
-                states_cache[key] = I.electrolyte(j["N"], j["L"], seed=j["seed"] % 100000)
-            res.append(states_cache[key])
-        return res
-
+    trace = I.job_trace(n_jobs, seed=11, rate=SERVE_RATE, n_min=500, n_max=200000, steps_min=100,
+                        steps_max=10000)
+    out = {"jobs": n_jobs, "arrival_rate_per_s": SERVE_RATE, "P": P, "N_range": [500, 200000],
+           "steps_range": [100, 10000], "mem_budget_bytes": SERVE_BUDGET, "precision": "fp32c",
+           "trace": "rbsog_inputs.job_trace(seed=11)", "quantum_steps": 50}
+    states = [I.electrolyte(j["N"], j["L"], seed=j["seed"] % 100000) for j in trace]
+    work = sum(j["N"] * j["steps"] for j in trace)
+    out["offered_particle_steps_per_s"] = work / trace[-1]["t"]
     warm = I.job_trace(1, seed=5, rate=50.0, n_min=500, n_max=2000, steps_min=5, steps_max=5)
-    serve_trace(Pk, [dict(warm[0], t=0.0)], states_for(warm), P, 4, 5)
-    for label, rate in (("rate_50_per_s", 50.0), ("rate_10_per_s", 10.0)):
-        trace = I.job_trace(n_jobs, seed=11, rate=rate, n_min=500, n_max=200000, steps_min=100, steps_max=1000)
-        states = states_for(trace)
-        work = sum(j["N"] * j["steps"] for j in trace)
-        res = {"arrival_rate_per_s": rate, "offered_particle_steps_per_s": work / trace[-1]["t"]}
-        modes = (("continuous_batching", 64),) + ((("one_at_a_time_fp32c", 1),) if rate == 50.0 else ())
-        for name, mj in modes:
-            lat, span = serve_trace(Pk, trace, states, P, mj, 25)
-            lat = np.sort(np.array(lat))
-            res[name] = {"max_jobs": mj, "makespan_s": span, "served_particle_steps_per_s": work / span,
-                         "latency_p50_s": float(np.percentile(lat, 50)),
-                         "latency_p99_s": float(np.percentile(lat, 99)), "completed": int(lat.size)}
-        if rate == 50.0:
-            # FP64, one job at a time: step time measured per size class (N
-            # at 1k, 10k, 100k, 200k), interpolated in log N; FIFO queue
-            sizes = [1000, 10000, 100000, 200000]
-            ms = []
-            for n in sizes:
-                L = (n / 0.5) ** (1.0 / 3.0)
-                q, x, v = I.electrolyte(n, L, seed=3)
-                g = Pk.RBSOG(n, Pk.make_params(L, P, n_ksets=8, precision="fp64"))
-                g.set_state(*(torch.tensor(a, device=dev) for a in (q, x, v)))
-                g.step(1)
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                g.step(5)
-                torch.cuda.synchronize()
-                ms.append((time.perf_counter() - t0) / 5 * 1e3)
-                g.close()
-            step_ms = np.interp(np.log([j["N"] for j in trace]), np.log(sizes), ms)
-            service = [s * j["steps"] / 1e3 for s, j in zip(step_ms, trace)]
-            lat = np.sort(np.array(fifo_latencies([j["t"] for j in trace], service)))
-            free = 0.0
-            for a, s in zip([j["t"] for j in trace], service):
-                free = max(a, free) + s
-            res["one_at_a_time_fp64_estimate"] = {
-                "basis": "FIFO queue over measured FP64 step times at N = 1k, 10k, 100k, 200k (log-interpolated)",
-                "fp64_ms_per_step_at": dict(zip([str(s) for s in sizes], ms)),
-                "makespan_s": free, "served_particle_steps_per_s": work / free,
-                "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99))}
-        out[label] = res
+    serve_trace(Pk, [dict(warm[0], t=0.0)], [I.electrolyte(warm[0]["N"], warm[0]["L"], seed=1)], P, 4, 5,
+                SERVE_BUDGET)
+    lat, span = serve_trace(Pk, trace, states, P, 128, 50, SERVE_BUDGET)
+    lat = np.sort(np.array(lat))
+    out["continuous_batching"] = {"max_jobs": 128, "makespan_s": span, "served_particle_steps_per_s": work / span,
+                                  "latency_p50_s": float(np.percentile(lat, 50)),
+                                  "latency_p99_s": float(np.percentile(lat, 99)), "completed": int(lat.size)}
+    # FP64 one job at a time: every job's own FP64 step time on the device
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    t_meas = time.perf_counter()
+    for j, (q, x, v) in zip(trace, states):
+        g = Pk.RBSOG(j["N"], Pk.make_params(j["L"], P, seed=j["seed"], n_ksets=8, precision="fp64"))
+        g.set_state(*(torch.tensor(a, device=dev) for a in (q, x, v)))
+        g.step(1)
+        e0.record(st)
+        g.step(5)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1) / 5)
+        g.close()
+    t_meas = time.perf_counter() - t_meas
+    service = [m * j["steps"] / 1e3 for m, j in zip(ms, trace)]
+    lat64 = np.sort(np.array(fifo_latencies([j["t"] for j in trace], service)))
+    free = 0.0
+    for a_, s_ in zip([j["t"] for j in trace], service):
+        free = max(a_, free) + s_
+    out["one_at_a_time_fp64"] = {
+        "basis": "FIFO in arrival order; service = steps x the job's own FP64 step time, measured on the "
+                 "device over 5 steps of each job (extrapolated to its step count)",
+        "measure_s": t_meas, "makespan_s": free, "served_particle_steps_per_s": work / free,
+        "latency_p50_s": float(np.percentile(lat64, 50)), "latency_p99_s": float(np.percentile(lat64, 99)),
+        "fp64_ms_per_step_median": float(np.median(ms))}
     return out
 
 
-def run_replicas(args, dev, n_sys=256, P=200):
-    """Batched replicas: n_sys independent electrolytes, N log-uniform in
-    [1000, 100000], density 0.5, Bjerrum length uniform in [0.7, 1.5], P = 200,
-    FP32C, all advanced by one graph launch per step (autotuned shapes)."""
+def run_replicas(dev, n_sys=256, P=200, K=500, W=5):
+    """Batched replicas as specified: n_sys independent electrolytes, N
+    log-uniform in [1000, 100000], density 0.5, Bjerrum length uniform in
+    [0.7, 1.5], P = 200, FP32C, all advanced by one graph launch per step
+    (autotuned shapes), timed over 500 steps."""
     import torch
 
     import paper_2205_13824_gb300 as Pk
     import rbsog_inputs as I
     B = Pk.binding
     Ns, Ls, lBs = I.replica_sizes(n_sys, seed=4)
-    K, W = args.steps, max(2, min(args.warmup, 5))
     params = [Pk.make_params(float(Ls[i]), P, lB=float(lBs[i]), seed=1000 + i, n_ksets=W + K + 4,
                              precision="fp32c") for i in range(n_sys)]
     b = Pk.Batch([int(n) for n in Ns], params, device=dev.index)
@@ -648,9 +721,13 @@ def run_replicas(args, dev, n_sys=256, P=200):
             "autotuned": tuned}
 
 
-def cpu_baseline(N, L, P, q, x, v, sample_steps=1):
-    """The FP64 oracle, as it stands, on the host cores: one full
-    velocity-Verlet step (one force evaluation) of the same workload."""
+def cpu_baseline(N, L, P, q, x, v):
+    """The FP64 oracle, as it stands, on the host cores: one full force
+    evaluation (near field over its cell list + random-batch far field with
+    rho(k) over all particles; the cost of one velocity-Verlet step) of the
+    whole workload on a k-set from the oracle's own sampler.  Returns the
+    baseline record, that k-set and the oracle's forces and energies (the
+    reference the GPU paths' errors are measured against)."""
     import numpy as np
 
     import oracle as O
@@ -658,10 +735,10 @@ def cpu_baseline(N, L, P, q, x, v, sample_steps=1):
     sog = O.SOG(sog.b, sog.sigma, sog.omega0, 36)
     s = O.System((L, L, L), sog, 3.0, 1.0, 1.0, 1.0)
     S = s.S()
-    ks = O.kseq(sog, s.L, seed=5, n_chains=8, chain_len=(P * sample_steps + 7) // 8)
-    f0 = np.zeros_like(x)
+    m = O.kseq(sog, s.L, seed=5, n_chains=8, chain_len=(P + 7) // 8)[:P]
+    xw = O.wrap(x, s.L)
     t0 = time.perf_counter()
-    O.md(s, q, x, v, S, P, ks, sample_steps, 0.001, f=f0)
+    f_o, e_o = O.forces(s, q, xw, S=S, m=m)
     dt = time.perf_counter() - t0
     # one host core on a 65,536-particle sample of the same electrolyte (the
     # oracle's cost per particle-step does not depend on N)
@@ -675,12 +752,13 @@ def cpu_baseline(N, L, P, q, x, v, sample_steps=1):
     O.md(s1, q1, x1, v1, s1.S(), P, ks1, 1, 0.001, f=np.zeros_like(x1))
     dt1 = time.perf_counter() - t1
     O.set_num_threads(old)
-    return {"value": N * sample_steps / dt, "unit": "particle-steps/s", "cores": O.num_threads(),
-            "kind": "oracle", "sample": f"{sample_steps} full step(s) (one FP64 force evaluation each: "
-                                        f"near cells + random-batch far, P={P}) of the N={N} workload",
+    base = {"value": N / dt, "unit": "particle-steps/s", "cores": O.num_threads(),
+            "kind": "oracle", "sample": f"one full FP64 force evaluation (near cells + random-batch far, "
+                                        f"P={P}) of the N={N} workload",
             "seconds": dt,
             "one_core": {"value": ns / dt1, "unit": "particle-steps/s", "cores": 1, "seconds": dt1,
                          "sample": f"1 full step of a {ns}-particle sample at the same density and P={P}"}}
+    return base, m, f_o, e_o
 
 
 def run_reference(args, rank, world, sample=65536):

@@ -150,6 +150,9 @@ typedef struct {
                                  [c * chain_len, (c + 1) * chain_len)                       */
     int32_t chain_len;
     int32_t P_set;            /* frequencies per k-set: P, or P_eff with sampler 1          */
+    int64_t list_builds;      /* FP32C neighbour-list path: builds run since set_params (any
+                                 system of the context); 0 off that path.  Reading it waits
+                                 for the context's queued work                              */
 } rbsog_info;
 
 /* Create a context for n >= 2 particles on CUDA device `device`; `stream`

@@ -399,8 +399,13 @@ __global__ void k_rebuild_condition(cudaGraphConditionalHandle h, const int32_t 
     cudaGraphSetConditional(h, *any ? 1u : 0u);
 }
 
+// Clears the per-system flags and the 'any system' flag after a build and
+// counts the builds that ran (rebuild[n_sys + 1]).
 __global__ void k_list_clear(int n_sys, int32_t *__restrict__ rebuild) {
+    const int any = threadIdx.x == 0 ? rebuild[n_sys] : 0;
+    __syncthreads();
     for (int s = threadIdx.x; s <= n_sys; s += blockDim.x) rebuild[s] = 0;
+    if (threadIdx.x == 0 && any) rebuild[n_sys + 1] += 1;
 }
 
 }  // namespace

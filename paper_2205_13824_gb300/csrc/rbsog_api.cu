@@ -1233,7 +1233,9 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
             CK(cudaMemcpy(ctx->d_cstab, cstab.data(), sizeof(float4) * cstab.size(), cudaMemcpyHostToDevice));
         }
         CK(dalloc(&ctx->nbr_list, (n + 31) / 32 * 32 * (size_t)ctx->list_cap));
-        CK(dalloc(&ctx->d_rebuild, (size_t)ns + 1));
+        // flags of the ns systems, the 'any system' flag, and a count of the
+        // list builds run since set_params (read by rbsog_get_info)
+        CK(dalloc(&ctx->d_rebuild, (size_t)ns + 2));
         CK(cudaMemset(ctx->xref, 0, sizeof(uint4) * n));
         CK(cudaMemset(ctx->nbr_cnt, 0, sizeof(int32_t) * n));
         CK(cudaMemset(ctx->list_perm, 0, sizeof(int32_t) * n));
@@ -1242,8 +1244,9 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         std::vector<int32_t> ident(n);
         for (size_t q = 0; q < n; ++q) ident[q] = (int32_t)q;
         CK(cudaMemcpy(ctx->linv, ident.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
-        std::vector<int32_t> ones((size_t)ns + 1, 1);
-        CK(cudaMemcpy(ctx->d_rebuild, ones.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice));
+        std::vector<int32_t> ones((size_t)ns + 2, 1);
+        ones[(size_t)ns + 1] = 0;
+        CK(cudaMemcpy(ctx->d_rebuild, ones.data(), sizeof(int32_t) * (ns + 2), cudaMemcpyHostToDevice));
     }
     rbsog_status es = enter(ctx);
     if (es != RBSOG_OK) return es;
@@ -1419,6 +1422,16 @@ rbsog_status rbsog_get_info(const rbsog_ctx *ctx, rbsog_info *info, double *omeg
     info->n_chains = ctx->n_chains[0];
     info->chain_len = ctx->chain_len[0];
     info->P_set = ctx->P;
+    info->list_builds = 0;
+    if (ctx->use_list && ctx->d_rebuild) {
+        int32_t nb = 0;
+        if (cudaSetDevice(ctx->device) != cudaSuccess ||
+            cudaMemcpyAsync(&nb, ctx->d_rebuild + ctx->n_sys + 1, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            ctx->st) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->st) != cudaSuccess)
+            return RBSOG_ECUDA;
+        info->list_builds = nb;
+    }
     if (omega) std::memcpy(omega, ctx->omega.data(), sizeof(double) * (ctx->p[0].M + 1));
     if (s) std::memcpy(s, ctx->s.data(), sizeof(double) * (ctx->p[0].M + 1));
     return RBSOG_OK;
