@@ -139,6 +139,11 @@ def lib():
             L.orc_pressure.restype = C.c_int
             L.orc_green_kubo.argtypes = [_i64, _pd, _d, _d, _d, _i32, _pd, C.POINTER(_d)]
             L.orc_green_kubo.restype = C.c_int
+            L.orc_heat_flux.argtypes = [_i64, _pd, _pd, _pd, _d, C.POINTER(OrcSys), _d, _i32, _pi32, _pd, _pd,
+                                        _pd]
+            L.orc_heat_flux.restype = C.c_int
+            L.orc_green_kubo_heat.argtypes = [_i64, _pd, _d, _d, _d, _i32, _pd, C.POINTER(_d)]
+            L.orc_green_kubo_heat.restype = C.c_int
             L.orc_pg_plan.argtypes = [_pd, _pd, _i32, _pd, _i32, _pi32, _pd]
             L.orc_pg_plan.restype = _i32
             L.orc_pg_kseq.argtypes = [_pd, _pd, _i32, _pd, _i32, _u64, _i64, _i64, _pi32, _pi32]
@@ -466,6 +471,39 @@ def green_kubo(P_series, dt, V, T, max_lag):
     Cv = _d(0.0)
     if lib().orc_green_kubo(Pt.shape[0], _p(Pt), float(dt), float(V), float(T), int(max_lag), _p(acf),
                             C.byref(Cv)):
+        raise ValueError("bad sizes")
+    return acf, Cv.value
+
+
+def heat_flux(sys_: System, q, x, v, mass, S=0.0, m=None):
+    """Heat flux of Appendix A (orc_heat_flux in the C source): returns
+    (J[3], per-atom energies e[n], per-atom virials W[n, 3, 3]); m None: no
+    far term (near field, WCA, kinetic and self terms only)."""
+    q, x, v = _f64(q), _f64(x), _f64(v)
+    n = x.shape[0]
+    J = np.zeros(3)
+    e = np.zeros(n)
+    W = np.zeros((n, 9))
+    if m is None:
+        rc_ = lib().orc_heat_flux(n, _p(q), _p(x), _p(v), float(mass), C.byref(sys_.c), 0.0, 0, None, _p(J),
+                                  _p(e), _p(W))
+    else:
+        m = _i32a(m)
+        rc_ = lib().orc_heat_flux(n, _p(q), _p(x), _p(v), float(mass), C.byref(sys_.c), float(S), m.shape[0],
+                                  _p(m, _pi32), _p(J), _p(e), _p(W))
+    if rc_:
+        raise ValueError("fewer than 3 cells per side")
+    return J, e, W.reshape(n, 3, 3)
+
+
+def green_kubo_heat(J_series, dt, V, T, max_lag):
+    """Green-Kubo heat conductivity of Appendix A from a heat-flux series
+    [n, 3]; returns (acf[max_lag], C)."""
+    J = _f64(np.asarray(J_series, float).reshape(-1, 3))
+    acf = np.zeros(int(max_lag))
+    Cv = _d(0.0)
+    if lib().orc_green_kubo_heat(J.shape[0], _p(J), float(dt), float(V), float(T), int(max_lag), _p(acf),
+                                 C.byref(Cv)):
         raise ValueError("bad sizes")
     return acf, Cv.value
 

@@ -1280,6 +1280,145 @@ int orc_green_kubo(int64_t n_samples, const double *Pt, double dt, double V, dou
     return 0;
 }
 
+/* ---- heat flux and heat conductivity (Appendix A) ------------------------
+ * J = (1/V) [ sum_i e_i v_i + (1/2) sum_{i<j} (f_ij . (v_i + v_j)) r_ij ],
+ * e_i the per-atom energy (kinetic and potential).  The pair sum equals
+ * sum_i W_i v_i with the per-atom virial W_i,ab = (1/2) sum_{j != i} r_ij,a
+ * f_ij,b (r_ij = r_i - r_j minimum image, f_ij the force on i from j): each
+ * ordered pair gives r_ij (f_ij . v_i) / 2 and the two orders of a pair give
+ * the printed term.  Per-atom energies: (1/2) m |v_i|^2, half of every pair
+ * energy (Coulomb near part and WCA), minus the self term (1/2) F_M(0) q_i^2,
+ * and the far part.  The random-batch far energy pi^{3/2} S/(2PV) sum_eta
+ * |rho(k_eta)|^2 splits over atoms as e_i = (c/2) q_i sum_eta
+ * Re(e^{-i k_eta . r_i} rho(k_eta)), c = pi^{3/2} S/(P V), since
+ * sum_i q_i e^{-i k . r_i} = conj(rho(k)); the far virial of orc_virial
+ * splits the same way, W_i,ab = (c/2) q_i sum_eta Re(e^{-i k.r_i} rho)
+ * (delta_ab - (1/2) k_a k_b T1/T0).  Summed over atoms these give U*_RB and
+ * the random-batch far virial exactly.  P = 0: no far term.  Coulomb terms
+ * times lB.  e_atom[n] and W_atom[n][9] are returned when non-NULL. */
+int orc_heat_flux(int64_t n, const double *q, const double *x, const double *v, double mass,
+                  const orc_sys *sys, double S, int32_t P, const int32_t *m, double J[3], double *e_atom,
+                  double *W_atom) {
+    int32_t nc3[3];
+    int32_t *cell_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t ncmax = 1;
+    for (int d = 0; d < 3; ++d) ncmax *= (int64_t)floor(sys->L[d] / sys->rc) > 0 ? (int64_t)floor(sys->L[d] / sys->rc) : 1;
+    int32_t *start = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ncmax + 1));
+    if (orc_cell_list(n, x, sys->L, sys->rc, nc3, cell_of, start, perm) != 0) {
+        free(cell_of); free(perm); free(start);
+        return -1;
+    }
+    double *e = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *W = (double *)calloc(9 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    const double rc2 = sys->rc * sys->rc;
+    const double V = sys->L[0] * sys->L[1] * sys->L[2];
+    double FM0 = 0.0;
+    for (int32_t l = 0; l <= sys->M; ++l) FM0 += sys->omega[l];
+    /* near field and WCA: every ordered pair from its first atom */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t c = cell_of[i];
+        int32_t cx = c % nc3[0], cy = (c / nc3[0]) % nc3[1], cz = c / (nc3[0] * nc3[1]);
+        double ei = 0.0, Wi[9] = {0};
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int32_t ox = (cx + dx + nc3[0]) % nc3[0];
+                    int32_t oy = (cy + dy + nc3[1]) % nc3[1];
+                    int32_t oz = (cz + dz + nc3[2]) % nc3[2];
+                    int32_t o = (oz * nc3[1] + oy) * nc3[0] + ox;
+                    for (int32_t t = start[o]; t < start[o + 1]; ++t) {
+                        int32_t j = perm[t];
+                        if (j == i) continue;
+                        double d[3];
+                        double r2 = min_image(x + 3 * i, x + 3 * j, sys->L, d);
+                        if (!(r2 < rc2)) continue;
+                        double fij[3] = {0.0, 0.0, 0.0}, un = 0.0, uw = 0.0;
+                        near_pair(sys, q[i], q[j], d, r2, fij, &un, &uw);   /* halves of the pair energy */
+                        ei += un + uw;
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = 0; b < 3; ++b) Wi[3 * a + b] += 0.5 * d[a] * fij[b];
+                    }
+                }
+        const double v2 = v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2];
+        e[i] = ei + 0.5 * mass * v2 - sys->lB * 0.5 * FM0 * q[i] * q[i];
+        for (int c9 = 0; c9 < 9; ++c9) W[9 * i + c9] = Wi[c9];
+    }
+    if (P > 0) {
+        const double c = sys->lB * pow(M_PI, 1.5) * S / ((double)P * V);
+        double *rho = (double *)malloc(sizeof(double) * 2 * (size_t)P);
+        double *kv = (double *)malloc(sizeof(double) * 4 * (size_t)P);   /* k, T1/T0 */
+        orc_rho(n, q, x, sys->L, P, m, rho);
+        for (int32_t h = 0; h < P; ++h) {
+            double k2 = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                kv[4 * h + d] = 2.0 * M_PI * (double)m[3 * h + d] / sys->L[d];
+                k2 += kv[4 * h + d] * kv[4 * h + d];
+            }
+            double T0 = 0.0, T1 = 0.0;
+            for (int32_t l = 0; l <= sys->M; ++l) {
+                const double s2 = sys->s[l] * sys->s[l];
+                const double t = sys->omega[l] * s2 * sys->s[l] * exp(-s2 * k2 / 4.0);
+                T0 += t;
+                T1 += t * s2;
+            }
+            kv[4 * h + 3] = T0 > 0.0 ? T1 / T0 : 0.0;
+        }
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            double ei = 0.0, Wi[9] = {0};
+            for (int32_t h = 0; h < P; ++h) {
+                const double *k = kv + 4 * h;
+                const double th = k[0] * x[3 * i] + k[1] * x[3 * i + 1] + k[2] * x[3 * i + 2];
+                /* Re(e^{-i th} (A + iB)) = cos(th) A + sin(th) B */
+                const double re = cos(th) * rho[2 * h] + sin(th) * rho[2 * h + 1];
+                const double w = 0.5 * c * q[i] * re;
+                ei += w;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) Wi[3 * a + b] += w * ((a == b ? 1.0 : 0.0) - 0.5 * k[3] * k[a] * k[b]);
+            }
+            e[i] += ei;
+            for (int c9 = 0; c9 < 9; ++c9) W[9 * i + c9] += Wi[c9];
+        }
+        free(rho);
+        free(kv);
+    }
+    double Js[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            double t = e[i] * v[3 * i + a];
+            for (int b = 0; b < 3; ++b) t += W[9 * i + 3 * a + b] * v[3 * i + b];
+            Js[a] += t;
+        }
+    for (int a = 0; a < 3; ++a) J[a] = Js[a] / V;
+    if (e_atom) memcpy(e_atom, e, sizeof(double) * (size_t)n);
+    if (W_atom) memcpy(W_atom, W, sizeof(double) * 9 * (size_t)n);
+    free(e); free(W); free(cell_of); free(perm); free(start);
+    return 0;
+}
+
+/* Heat conductivity by the Green-Kubo relation of Appendix A:
+ * C = V / (3 k_B T^2) * integral over t of <J(0) . J(t)>, the average over
+ * all origins t0 with t0 + t < n_samples of J(t0) . J(t0 + t) (the flux as
+ * sampled, no mean removed: its equilibrium mean is zero), integrated by the
+ * trapezoid rule over the lags 0 .. max_lag - 1 spaced dt.  J[n_samples][3];
+ * acf[max_lag] receives the autocorrelation per lag. */
+int orc_green_kubo_heat(int64_t n_samples, const double *J, double dt, double V, double T, int32_t max_lag,
+                        double *acf, double *C) {
+    if (n_samples < 2 || max_lag < 2 || max_lag > n_samples || T <= 0.0) return -1;
+    for (int32_t t = 0; t < max_lag; ++t) {
+        double a = 0.0;
+        for (int64_t o = 0; o + t < n_samples; ++o)
+            for (int c = 0; c < 3; ++c) a += J[3 * o + c] * J[3 * (o + t) + c];
+        acf[t] = a / (double)(n_samples - t);
+    }
+    double integral = 0.0;
+    for (int32_t t = 0; t + 1 < max_lag; ++t) integral += 0.5 * dt * (acf[t] + acf[t + 1]);
+    *C = V / (3.0 * T * T) * integral;
+    return 0;
+}
+
 /* ---- per-Gaussian independent sampling (Sec. 3.3, closing remark) ------- */
 
 #define PG_MAX_JMAX (1 << 20)

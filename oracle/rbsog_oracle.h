@@ -202,6 +202,20 @@ int orc_pressure(int64_t n, const double *q, const double *x, const double *v, d
 int orc_green_kubo(int64_t n_samples, const double *Pt, double dt, double V, double T, int32_t max_lag,
                    double *acf, double *C);
 
+/* Heat flux J[3] of Appendix A for the current state: per-atom energies
+ * (kinetic, half of each near and WCA pair energy, minus the self term, the
+ * far energy split over atoms) times velocities plus the per-atom virials
+ * (half of r_ij f_ij per ordered pair; the random-batch far virial split over
+ * atoms) contracted with the velocities, over V.  P = 0: no far term.
+ * e_atom[n], W_atom[n][9] returned when non-NULL.  -1 if fewer than 3 cells
+ * per side. */
+int orc_heat_flux(int64_t n, const double *q, const double *x, const double *v, double mass,
+                  const orc_sys *sys, double S, int32_t P, const int32_t *m, double J[3], double *e_atom,
+                  double *W_atom);
+/* Green-Kubo heat conductivity V/(3 k_B T^2) * integral <J(0).J(t)> dt. */
+int orc_green_kubo_heat(int64_t n_samples, const double *J, double dt, double V, double T, int32_t max_lag,
+                        double *acf, double *C);
+
 int  orc_num_threads(void);
 int  orc_set_num_threads(int n);
 
