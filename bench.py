@@ -571,6 +571,10 @@ def run_dynamics_extras(args, tq, tx, tv, dev):
     t0 = time.perf_counter()
     g.pressure(m)
     ms_p = (time.perf_counter() - t0) * 1e3
+    g.heat_flux(m)
+    t0 = time.perf_counter()
+    g.heat_flux(m)
+    ms_h = (time.perf_counter() - t0) * 1e3
     g.close()
     ser = torch.randn((10000, 9), dtype=torch.float64, device=dev)
     B.rbsog_green_kubo(ser, 0.01, 1.0, 1.0, 1000)
@@ -578,7 +582,7 @@ def run_dynamics_extras(args, tq, tx, tv, dev):
     B.rbsog_green_kubo(ser, 0.01, 1.0, 1.0, 1000)
     ms_gk = (time.perf_counter() - t0) * 1e3
     out["observables"] = {"msd_vacf_sample_ms": ms_obs, "msd_vacf_origins": 8,
-                          "pressure_tensor_ms": ms_p, "green_kubo_ms": ms_gk,
+                          "pressure_tensor_ms": ms_p, "heat_flux_ms": ms_h, "green_kubo_ms": ms_gk,
                           "green_kubo_series": "10000 samples x 1000 lags"}
     return out
 

@@ -356,6 +356,32 @@ rbsog_status rbsog_observe_result(rbsog_ctx *ctx, double *msd, double *vacf, int
 rbsog_status rbsog_green_kubo(const double *P_series, int64_t n_samples, double dt, double V, double T,
                               int32_t max_lag, double *acf_out, double *C_out, void *stream);
 
+/* Heat flux J (Appendix A) of the current state of a single tinfoil system:
+ *   J = (1/V) [ sum_i e_i v_i + (1/2) sum_{i<j} (f_ij . (v_i + v_j)) r_ij ],
+ * e_i the per-atom energy: m |v_i|^2 / 2, half of each near-field (Coulomb
+ * near part, Eq. 2.7, and WCA) pair energy, minus lB F_M(0) q_i^2 / 2, plus
+ * the random-batch far energy split over atoms,
+ * (c/2) q_i sum_eta Re(e^{-i k_eta . r_i} rho(k_eta)), c = lB pi^{3/2} S/(P V)
+ * (Eq. 3.24), whose sum is the far energy.  The far field has no pair
+ * forces; its share of the pair term is the random-batch far virial of
+ * rbsog_compute_virial split over atoms the same way and contracted with
+ * v_i.  k-set m[P][3] (host or device); P = 0 (m may be NULL): no far term.
+ * FP64 for both precisions, from the FP64 state.  J_out[3] host or device.
+ * RBSOG_EINVAL for a batch of several systems or a non-tinfoil boundary. */
+rbsog_status rbsog_compute_heat_flux(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *J_out);
+
+/* Heat conductivity by the Green-Kubo relation of Appendix A from a series
+ * J_series[n_samples][3] (spaced dt apart, host or device; e.g. from
+ * rbsog_compute_heat_flux): C = V / (3 k_B T^2) times the integral over t of
+ * <J(t0) . J(t0 + t)>, the flux as sampled (no mean removed), averaged over
+ * all origins t0 with t0 + t < n_samples and integrated by the trapezoid rule
+ * over the lags 0 .. max_lag - 1.  acf_out[max_lag] (host or device, NULL to
+ * skip), *C_out (host).  Context-free; work on `stream`, which the call
+ * synchronises.  RBSOG_EINVAL for n_samples < 2, max_lag outside
+ * [2, n_samples], non-positive dt, V or T, or a NULL J_series or C_out. */
+rbsog_status rbsog_green_kubo_heat(const double *J_series, int64_t n_samples, double dt, double V, double T,
+                                   int32_t max_lag, double *acf_out, double *C_out, void *stream);
+
 /* Roofline denominators measured on `device` by short microbenchmarks (not
  * part of the method): out[0] MUFU sin/cos results per second (each of sin
  * and cos counts one), out[1] FP32 FMA per second, out[2] FP64 FMA per

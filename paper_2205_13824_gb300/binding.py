@@ -26,7 +26,7 @@ EXPORTS = ("rbsog_create", "rbsog_set_params", "rbsog_get_info", "rbsog_set_stat
            "rbsog_get_kseq", "rbsog_rho", "rbsog_get_cells", "rbsog_set_profiling",
            "rbsog_get_cursor", "rbsog_restore", "rbsog_step_io", "rbsog_compute_virial", "rbsog_rho_noalloc", "rbsog_measure_peaks",
            "rbsog_compute_pressure", "rbsog_observe_start", "rbsog_observe_sample", "rbsog_observe_result",
-           "rbsog_green_kubo",
+           "rbsog_green_kubo", "rbsog_compute_heat_flux", "rbsog_green_kubo_heat",
            "rbsog_batch_create", "rbsog_batch_set_params", "rbsog_batch_set_state", "rbsog_batch_restore",
            "rbsog_batch_get_state", "rbsog_batch_get_energies", "rbsog_batch_get_kseq", "rbsog_batch_step",
            "rbsog_batch_autotune", "rbsog_batch_rdf", "rbsog_rdf",
@@ -93,6 +93,9 @@ def _load():
         "rbsog_observe_result": [P, P, P, P],
         "rbsog_green_kubo": [P, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int32, P,
                              C.POINTER(C.c_double), P],
+        "rbsog_compute_heat_flux": [P, P, C.c_int32, P],
+        "rbsog_green_kubo_heat": [P, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int32, P,
+                                  C.POINTER(C.c_double), P],
         "rbsog_get_kseq": [P, C.c_int64, C.c_int64, P],
         "rbsog_rho": [P, P, C.c_int32, P],
         "rbsog_get_cells": [P, P, P, P],
@@ -236,6 +239,17 @@ def rbsog_compute_pressure(ctx, m):
     Pt = np.zeros(9)
     _check(ctx, _lib.rbsog_compute_pressure(ctx, _ptr(m), int(m.shape[0]), _ptr(Pt)))
     return Pt.reshape(3, 3)
+
+
+def rbsog_compute_heat_flux(ctx, m=None):
+    """Heat flux J[3] of Appendix A; the far term on k-set m[P][3], none for m None."""
+    J = np.zeros(3)
+    if m is None:
+        _check(ctx, _lib.rbsog_compute_heat_flux(ctx, None, 0, _ptr(J)))
+    else:
+        m = np.ascontiguousarray(m, dtype=np.int32)
+        _check(ctx, _lib.rbsog_compute_heat_flux(ctx, _ptr(m), int(m.shape[0]), _ptr(J)))
+    return J
 
 
 def rbsog_observe_start(ctx, n_lags: int, origin_every: int = 1):
@@ -495,3 +509,17 @@ def rbsog_last_error(ctx) -> str:
 
 def rbsog_destroy(ctx):
     _check(None, _lib.rbsog_destroy(ctx))
+
+
+def rbsog_green_kubo_heat(J_series, dt: float, V: float, T: float, max_lag: int, stream=None):
+    """(acf[max_lag], C) of a heat-flux series [n, 3] (host array or device tensor)."""
+    if not hasattr(J_series, "data_ptr"):
+        J_series = np.ascontiguousarray(np.asarray(J_series, dtype=np.float64).reshape(-1, 3))
+    n = J_series.shape[0]
+    acf = np.zeros(int(max_lag))
+    Cv = C.c_double()
+    st = _lib.rbsog_green_kubo_heat(_ptr(J_series), int(n), float(dt), float(V), float(T), int(max_lag),
+                                    _ptr(acf), C.byref(Cv), C.c_void_p(stream))
+    if st != 0:
+        raise RBSOGError(st, "rbsog_green_kubo_heat failed")
+    return acf, Cv.value

@@ -201,6 +201,20 @@ __global__ void __launch_bounds__(kThreads) k_gk_integral(const double *__restri
     if (threadIdx.x == 0) *C = scale * 0.5 * t[0];
 }
 
+// Block t: acf[t] = sum over the origins of J(t0) . J(t0 + t) (the flux as
+// sampled, no mean removed), divided by the n - t origins.
+__global__ void __launch_bounds__(kThreads) k_gkh_acf(const double *__restrict__ series, int64_t ns,
+                                                      double *__restrict__ acf) {
+    const int64_t t = blockIdx.x;
+    double s[1] = {0.0}, r[1];
+    for (int64_t o = threadIdx.x; o + t < ns; o += kThreads) {
+        const double *a = series + 3 * o, *b = series + 3 * (o + t);
+        s[0] += a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+    }
+    block_sum<1>(s, r);
+    if (threadIdx.x == 0) acf[t] = r[0] / (double)(ns - t);
+}
+
 }  // namespace
 
 int32_t obs_blocks(int64_t n) { return (int32_t)((n + kThreads - 1) / kThreads); }
@@ -241,6 +255,15 @@ cudaError_t launch_green_kubo(const double *series, int64_t ns, int32_t max_lag,
     if (e != cudaSuccess) return e;
     k_gk_acf<<<max_lag, kThreads, 0, st>>>(series, ns, mean, acf);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_gk_integral<<<1, kThreads, 0, st>>>(acf, max_lag, scale, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_green_kubo_heat(const double *series, int64_t ns, int32_t max_lag, double scale, double *acf,
+                                   double *C, cudaStream_t st) {
+    k_gkh_acf<<<max_lag, kThreads, 0, st>>>(series, ns, acf);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_gk_integral<<<1, kThreads, 0, st>>>(acf, max_lag, scale, C);
     return cudaGetLastError();

@@ -1885,6 +1885,43 @@ rbsog_status virial_device(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *
     return RBSOG_OK;
 }
 
+// Heat flux J[3] of system 0 (Appendix A) into device memory dJ; the far
+// term on the k-set m (host or device, P >= 1), none for P == 0.
+rbsog_status heat_flux_device(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *dJ) {
+    const int64_t n = ctx->n_per[0];
+    const int M = ctx->p[0].M;
+    const int32_t nb = heat_blocks(n);
+    const int32_t Pa = P > 0 ? P : 1;
+    int32_t *m3 = nullptr;
+    double2 *rpart = nullptr, *rho = nullptr;
+    double4_32a *ktab = nullptr;
+    double *part = nullptr, *dom = nullptr, *dsl = nullptr;
+    CK(cudaMallocAsync((void **)&m3, sizeof(int32_t) * 3 * Pa, ctx->st));
+    CK(cudaMallocAsync((void **)&rpart, sizeof(double2) * heat_rho_partials(Pa), ctx->st));
+    CK(cudaMallocAsync((void **)&rho, sizeof(double2) * Pa, ctx->st));
+    CK(cudaMallocAsync((void **)&ktab, sizeof(double4_32a) * 2 * Pa, ctx->st));
+    CK(cudaMallocAsync((void **)&part, sizeof(double) * 6 * (size_t)nb, ctx->st));
+    CK(cudaMallocAsync((void **)&dom, sizeof(double) * (M + 1), ctx->st));
+    CK(cudaMallocAsync((void **)&dsl, sizeof(double) * (M + 1), ctx->st));
+    if (P > 0) CK(cudaMemcpyAsync(m3, m, sizeof(int32_t) * 3 * P, cudaMemcpyDefault, ctx->st));
+    CK(cudaMemcpyAsync(dom, ctx->omega.data(), sizeof(double) * (M + 1), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(dsl, ctx->s.data(), sizeof(double) * (M + 1), cudaMemcpyHostToDevice, ctx->st));
+    const BatchView bv = view(ctx);
+    CK(launch_build_cells(bv, ctx->posq, ctx->cb, ctx->precision, ctx->sp64, ctx->sp32, ctx->st, prof_of(ctx)));
+    double FM0 = 0.0;
+    for (int l = 0; l <= M; ++l) FM0 += ctx->omega[l];
+    const BoxDev &box = ctx->desc[0].box;
+    const double lB = ctx->p[0].coulomb_prefactor;
+    const double V = box.L[0] * box.L[1] * box.L[2];
+    const double half_c = P > 0 ? lB * std::pow(kPi, 1.5) * ctx->S[0] / (2.0 * P * V) : 0.0;
+    CK(launch_heat_flux(ctx->d_desc, box, n, ctx->nsog, ctx->cb.start, ctx->cb.perm, ctx->cb.cell_of, ctx->posq,
+                        ctx->vel, ctx->p[0].mass, 0.5 * lB * FM0, m3, P, dom, dsl, M, half_c, rpart, rho, ktab, part,
+                        part + 3 * (size_t)nb, dJ, ctx->st));
+    for (void *ptr : {(void *)m3, (void *)rpart, (void *)rho, (void *)ktab, (void *)part, (void *)dom, (void *)dsl})
+        CK(cudaFreeAsync(ptr, ctx->st));
+    return RBSOG_OK;
+}
+
 rbsog_status single_system_ready(rbsog_ctx *ctx, const char *what) {
     if (ctx->n_sys != 1) return fail(ctx, RBSOG_EINVAL, "%s needs a single system", what);
     if (!ctx->have_params || !all_state(ctx)) return fail(ctx, RBSOG_ESTATE, "params and state required");
@@ -1905,6 +1942,24 @@ rbsog_status rbsog_compute_virial(rbsog_ctx *ctx, const int32_t *m, int32_t P, d
     if (es != RBSOG_OK) return es;
     CK(cudaMemcpyAsync(W_out, dW, sizeof(double) * 9, cudaMemcpyDefault, ctx->st));
     CK(cudaFreeAsync(dW, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return leave(ctx);
+}
+
+rbsog_status rbsog_compute_heat_flux(rbsog_ctx *ctx, const int32_t *m, int32_t P, double *J_out) {
+    if (!ctx || !J_out || P < 0 || (P > 0 && !m)) return RBSOG_EINVAL;
+    rbsog_status es = single_system_ready(ctx, "rbsog_compute_heat_flux");
+    if (es != RBSOG_OK) return es;
+    if (ctx->p[0].boundary != 0)
+        return fail(ctx, RBSOG_EINVAL, "rbsog_compute_heat_flux covers tinfoil systems (boundary 0)");
+    es = enter(ctx);
+    if (es != RBSOG_OK) return es;
+    double *dJ = nullptr;
+    CK(cudaMallocAsync((void **)&dJ, sizeof(double) * 3, ctx->st));
+    es = heat_flux_device(ctx, m, P, dJ);
+    if (es != RBSOG_OK) return es;
+    CK(cudaMemcpyAsync(J_out, dJ, sizeof(double) * 3, cudaMemcpyDefault, ctx->st));
+    CK(cudaFreeAsync(dJ, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return leave(ctx);
 }
@@ -2012,6 +2067,26 @@ rbsog_status rbsog_green_kubo(const double *P_series, int64_t n_samples, double 
     CK(launch_green_kubo(ser, n_samples, max_lag, V * dt / (6.0 * T), scr, scr + 7, scr + 6, st));
     if (acf_out) CK(cudaMemcpyAsync(acf_out, scr + 7, sizeof(double) * max_lag, cudaMemcpyDefault, st));
     CK(cudaMemcpyAsync(C_out, scr + 6, sizeof(double), cudaMemcpyDefault, st));
+    CK(cudaFreeAsync(ser, st));
+    CK(cudaFreeAsync(scr, st));
+    CK(cudaStreamSynchronize(st));
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_green_kubo_heat(const double *J_series, int64_t n_samples, double dt, double V, double T,
+                                   int32_t max_lag, double *acf_out, double *C_out, void *stream) {
+    rbsog_ctx *ctx = nullptr;   // context-free: CK reports the status only
+    if (!J_series || !C_out || n_samples < 2 || max_lag < 2 || max_lag > n_samples || !(T > 0.0) || !(V > 0.0) ||
+        !(dt > 0.0))
+        return RBSOG_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double *ser = nullptr, *scr = nullptr;
+    CK(cudaMallocAsync((void **)&ser, sizeof(double) * 3 * (size_t)n_samples, st));
+    CK(cudaMallocAsync((void **)&scr, sizeof(double) * (1 + (size_t)max_lag), st));
+    CK(cudaMemcpyAsync(ser, J_series, sizeof(double) * 3 * (size_t)n_samples, cudaMemcpyDefault, st));
+    CK(launch_green_kubo_heat(ser, n_samples, max_lag, V * dt / (3.0 * T * T), scr + 1, scr, st));
+    if (acf_out) CK(cudaMemcpyAsync(acf_out, scr + 1, sizeof(double) * max_lag, cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(C_out, scr, sizeof(double), cudaMemcpyDefault, st));
     CK(cudaFreeAsync(ser, st));
     CK(cudaFreeAsync(scr, st));
     CK(cudaStreamSynchronize(st));

@@ -406,6 +406,23 @@ cudaError_t launch_virial(const SysDesc *sysd, int64_t n, const NearSog &sog, co
                           const double2 *rho, const int32_t *m3, int32_t P, const double *omega, const double *sl,
                           int32_t M, double S, double *W, cudaStream_t st);
 
+// ---- heat flux (k_heat.cu) -----------------------------------------------------
+// Heat flux J[3] (Appendix A) of system 0 from the FP64 caller-order state:
+// near field (+ WCA) over the cell list (start, perm, cell_of), kinetic and
+// self terms (half_lB_FM0 = lB F_M(0) / 2), and for P > 0 the random-batch far
+// energy and virial split over atoms on the k-set m3[P][3] (half_c = lB
+// pi^{3/2} S / (2 P V); SOG omega, sl of M + 1 terms).  Scratch: rpart
+// heat_rho_partials(P) double2, rho[P], ktab[2P], part_near and part_far
+// 3 * heat_blocks(n) doubles each.
+int32_t heat_blocks(int64_t n);
+size_t heat_rho_partials(int32_t P);
+cudaError_t launch_heat_flux(const SysDesc *sysd, const BoxDev &box, int64_t n, const NearSog &sog,
+                             const int32_t *start, const int32_t *perm, const int32_t *cell_of,
+                             const double4_32a *posq, const double4_32a *vel, double mass, double half_lB_FM0,
+                             const int32_t *m3, int32_t P, const double *omega, const double *sl, int32_t M,
+                             double half_c, double2 *rpart, double2 *rho, double4_32a *ktab, double *part_near,
+                             double *part_far, double *J, cudaStream_t st);
+
 // ---- observables (k_observe.cu) --------------------------------------------------
 // MSD/VACF sampling of system 0 (n particles, caller order): per sample the
 // unwrapped positions u (from xprev, the folded positions of the previous
@@ -435,6 +452,11 @@ cudaError_t launch_pressure(int64_t n, const double4_32a *vel, double mass, cons
 // with scale = V dt / (6 T); series[ns][9] on the device.
 cudaError_t launch_green_kubo(const double *series, int64_t ns, int32_t max_lag, double scale, double *mean,
                               double *acf, double *C, cudaStream_t st);
+// Green-Kubo heat conductivity: acf[t] = sum over the three components and
+// the ns - t origins of J(t0) . J(t0 + t) / (ns - t), *C = scale *
+// trapezoid(acf), scale = V dt / (3 T^2); series[ns][3] on the device.
+cudaError_t launch_green_kubo_heat(const double *series, int64_t ns, int32_t max_lag, double scale, double *acf,
+                                   double *C, cudaStream_t st);
 
 // ---- boundary terms (k_boundary.cu) ---------------------------------------------
 // Zero-frequency term of systems with a non-tinfoil boundary: dipole moment

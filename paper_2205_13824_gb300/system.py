@@ -90,6 +90,10 @@ class RBSOG:
         """Pressure tensor [3, 3] of Appendix A, the far virial on k-set m[P][3]."""
         return B.rbsog_compute_pressure(self.ctx, m)
 
+    def heat_flux(self, m=None):
+        """Heat flux J[3] of Appendix A, the far term on k-set m[P][3]."""
+        return B.rbsog_compute_heat_flux(self.ctx, m)
+
     def observe_start(self, n_lags: int, origin_every: int = 1):
         """Start MSD/VACF accumulation; the current state is frame 0 of the next sample."""
         self._obs_lags = int(n_lags)
