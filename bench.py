@@ -171,17 +171,30 @@ def profiled_traffic(kernel, N, P):
     return None
 
 
-def roofline_for(name, launches, ms_total, N, L, P, rc, meas, hbm_gbs, lists=False):
+def distinct_per_set(ks, P):
+    """Mean number of runs of equal consecutive frequencies per k-set: the
+    frequencies the far-field kernels evaluate once the sets are folded."""
+    import numpy as np
+    m = np.asarray(ks).reshape(-1, P, 3)
+    starts = np.any(m[:, 1:] != m[:, :-1], axis=2).sum(axis=1) + 1
+    return float(starts.mean())
+
+
+def roofline_for(name, launches, ms_total, N, L, P, rc, meas, hbm_gbs, lists=False, P_eval=None):
     """Algorithmic work of one launch over its average CUDA-event duration,
-    against the rate measured on this GPU by rbsog_measure_peaks."""
+    against the rate measured on this GPU by rbsog_measure_peaks.  P_eval:
+    frequencies per set the far-field kernels evaluate (the distinct runs of
+    a folded set), P when None."""
     t = ms_total / launches / 1e3
     out = {"kernel": name, "ms_per_launch": t * 1e3, "traffic": profiled_traffic(name, N, P)}
     if name.startswith(("rho_sweep", "far_scatter")):
-        # one (particle, frequency) term = one sin + one cos on the MUFU pipe
-        achieved = N * P / t / 1e9
+        # one (particle, evaluated frequency) term = one sin + one cos on the MUFU pipe
+        Pe = P if P_eval is None else P_eval
+        achieved = N * Pe / t / 1e9
         peak = meas["mufu_per_s"] / 2 / 1e9
         out.update(bound="alu", achieved=achieved, peak=peak, unit="Gsincos/s", frac=achieved / peak,
-                   peak_basis="measured MUFU sin+cos rate / 2 (rbsog_measure_peaks)")
+                   peak_basis="measured MUFU sin+cos rate / 2 (rbsog_measure_peaks)",
+                   work=f"N x {Pe:.1f} evaluated frequencies per set (P = {P} sampled)")
         return out
     if name.startswith("near"):
         # FP32 instruction-equivalents: 8 per candidate distance test, 50 per
@@ -259,6 +272,7 @@ def run_ours(args, rank, world, local, dist):
     g = Pk.RBSOG(N, p32, device=local)
     tq, tx, tv = (torch.tensor(a, device=dev) for a in (q, x, v))
     g.set_state(tq, tx, tv)
+    P_eval = distinct_per_set(g.kseq(0, need), P)
 
     def barrier():
         if dist is not None:
@@ -346,8 +360,8 @@ def run_ours(args, rank, world, local, dist):
     hbm = peaks.get("hbm_gbs", 6686.1)
     lists = "list_build" in prof
     top = max(prof.items(), key=lambda kv: kv[1][1])
-    roof = roofline_for(top[0], top[1][0], top[1][1], N, L, P, 3.0, meas, hbm, lists)
-    roof_far = [roofline_for(k, c, t, N, L, P, 3.0, meas, hbm) for k, (c, t) in prof.items()
+    roof = roofline_for(top[0], top[1][0], top[1][1], N, L, P, 3.0, meas, hbm, lists, P_eval)
+    roof_far = [roofline_for(k, c, t, N, L, P, 3.0, meas, hbm, P_eval=P_eval) for k, (c, t) in prof.items()
                 if k.startswith(("rho_sweep", "far_scatter"))]
     roof_near = [roofline_for(k, c, t, N, L, P, 3.0, meas, hbm, lists) for k, (c, t) in prof.items()
                  if k.startswith("near")]
@@ -372,7 +386,8 @@ def run_ours(args, rank, world, local, dist):
         "roofline": roof,
         "clocks": clocks,
     }
-    head = {"fp32c": {"value": value, "ms_per_step": ms, "rebuilds_in_window": rebuilds_in_window}}
+    head = {"fp32c": {"value": value, "ms_per_step": ms, "rebuilds_in_window": rebuilds_in_window,
+                      "P": P, "P_evaluated_per_set": P_eval}}
     if amort:
         head["fp32c"]["long_window"] = amort
     extras = {}

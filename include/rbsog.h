@@ -126,7 +126,14 @@ typedef struct {
                                  later ones unconditioned, |m_d| by inverting with u(B_d) the
                                  sums 1 + sum_{i=1..j} 2 e^{-x i^2}, x = (pi s_l / L_d)^2,
                                  j <= ceil(sqrt(50 / x)), the sign from bit d of A2
-                                 (u(r) = (r >> 11) 2^-53)                                     */
+                                 (u(r) = (r >> 11) 2^-53).
+                                 With sampler 0 each set of the sequence is folded on the
+                                 device after sampling: a Metropolis-Hastings chain repeats
+                                 its state on every rejection (about half of the draws), and
+                                 each run of equal consecutive frequencies is evaluated once
+                                 and weighted by its length in rho(k), the far force and the
+                                 energy -- the same sums up to rounding.  An explicit k-set
+                                 (rbsog_compute_forces) is evaluated entry by entry.         */
 } rbsog_params;
 
 /* Energies of the last force evaluation (Eqs. 3.1, 3.6-3.8) and kinetic state. */

@@ -56,10 +56,18 @@ struct KEntry64 {       // 64 bytes
     double cim, mx, my, mz;
 };
 
-// Frequency k of system s's current k-set (explicit set for a batch of one).
+// Entry k of system s's current k-set (explicit set for a batch of one; the
+// folded set, whose .w is the run length, when the sequence was folded).
 __device__ __forceinline__ int4 load_m(const BatchView &bv, const SysDesc &d, int s, int k) {
     if (bv.m_explicit) return bv.m_explicit[k];
-    return bv.kseq[d.k_off + bv.cursor[s] * (int64_t)bv.P + k];
+    const int4 *seq = bv.kfold ? bv.kfold : bv.kseq;
+    return seq[d.k_off + bv.cursor[s] * (int64_t)bv.P + k];
+}
+
+// Entries of system s's current k-set the far-field kernels evaluate: the
+// distinct runs of a folded set, otherwise all P.
+__device__ __forceinline__ int set_len(const BatchView &bv, const SysDesc &d, int s) {
+    return bv.kcount ? bv.kcount[d.kc_off + bv.cursor[s]] : bv.P;
 }
 
 // 1 + t in [1, 2) for a phase given as t = ph 2^-32 turns, t rounded to 23
@@ -94,6 +102,8 @@ __global__ void __launch_bounds__(kSweepThreads)
     const int ptile = work.y;
     const int ktile = PREC == 1 ? kKTile32 : kKTile;
     const int k0 = blockIdx.y * ktile;
+    const int nk = set_len(bv, d, work.x);
+    if (k0 >= nk) return;                                     // beyond the folded set: whole block
     const int64_t p0 = d.p_off + (int64_t)ptile * d.tile_p;
     const int np = (int)min((int64_t)d.tile_p, d.p_off + d.n - p0);
 
@@ -101,33 +111,55 @@ __global__ void __launch_bounds__(kSweepThreads)
     const int jb = wid * per_warp, je = min(jb + per_warp, np);
     if (PREC == 1) {
         int4 ma = make_int4(0, 0, 0, 0), mb = ma;
-        if (k0 + lane < bv.P) ma = load_m(bv, d, work.x, k0 + lane);
-        if (k0 + lane + 32 < bv.P) mb = load_m(bv, d, work.x, k0 + lane + 32);
+        if (k0 + lane < nk) ma = load_m(bv, d, work.x, k0 + lane);
+        if (k0 + lane + 32 < nk) mb = load_m(bv, d, work.x, k0 + lane + 32);
         uint4 *sp = reinterpret_cast<uint4 *>(smem_raw);
         for (int j = tid; j < np; j += kSweepThreads) sp[j] = sp32[p0 + j];
         __syncthreads();
         const float2 two_pi = f2(kTwoPiF, kTwoPiF), m_two_pi = f2(-kTwoPiF, -kTwoPiF);
         float2 re_hi = f2(0.f, 0.f), re_lo = re_hi, im_hi = re_hi, im_lo = re_hi;
-        for (int j0 = jb; j0 < je; j0 += 32) {
-            const int j1 = min(j0 + 32, je);
-            float2 cr = f2(0.f, 0.f), ci = cr;
+        if (k0 + 32 < nk) {
+            for (int j0 = jb; j0 < je; j0 += 32) {
+                const int j1 = min(j0 + 32, je);
+                float2 cr = f2(0.f, 0.f), ci = cr;
 #pragma unroll 4
-            for (int j = j0; j < j1; ++j) {
-                const uint4 p = sp[j];
-                const uint32_t ph_a = (uint32_t)ma.x * p.x + (uint32_t)ma.y * p.y + (uint32_t)ma.z * p.z;
-                const uint32_t ph_b = (uint32_t)mb.x * p.x + (uint32_t)mb.y * p.y + (uint32_t)mb.z * p.z;
-                const float2 ang = __ffma2_rn(f2(one_plus_turns(ph_a), one_plus_turns(ph_b)), two_pi, m_two_pi);
-                float s_a, c_a, s_b, c_b;
-                __sincosf(ang.x, &s_a, &c_a);
-                __sincosf(ang.y, &s_b, &c_b);
-                const float q = __uint_as_float(p.w);
-                cr = __ffma2_rn(f2(q, q), f2(c_a, c_b), cr);
-                ci = __ffma2_rn(f2(q, q), f2(s_a, s_b), ci);
+                for (int j = j0; j < j1; ++j) {
+                    const uint4 p = sp[j];
+                    const uint32_t ph_a = (uint32_t)ma.x * p.x + (uint32_t)ma.y * p.y + (uint32_t)ma.z * p.z;
+                    const uint32_t ph_b = (uint32_t)mb.x * p.x + (uint32_t)mb.y * p.y + (uint32_t)mb.z * p.z;
+                    const float2 ang = __ffma2_rn(f2(one_plus_turns(ph_a), one_plus_turns(ph_b)), two_pi, m_two_pi);
+                    float s_a, c_a, s_b, c_b;
+                    __sincosf(ang.x, &s_a, &c_a);
+                    __sincosf(ang.y, &s_b, &c_b);
+                    const float q = __uint_as_float(p.w);
+                    cr = __ffma2_rn(f2(q, q), f2(c_a, c_b), cr);
+                    ci = __ffma2_rn(f2(q, q), f2(s_a, s_b), ci);
+                }
+                two_sum(re_hi.x, re_lo.x, cr.x);
+                two_sum(re_hi.y, re_lo.y, cr.y);
+                two_sum(im_hi.x, im_lo.x, ci.x);
+                two_sum(im_hi.y, im_lo.y, ci.y);
             }
-            two_sum(re_hi.x, re_lo.x, cr.x);
-            two_sum(re_hi.y, re_lo.y, cr.y);
-            two_sum(im_hi.x, im_lo.x, ci.x);
-            two_sum(im_hi.y, im_lo.y, ci.y);
+        } else {
+            // the set's last tile holds at most 32 frequencies: one per lane
+            // (the same expressions, so a frequency's partial is the same bits)
+            for (int j0 = jb; j0 < je; j0 += 32) {
+                const int j1 = min(j0 + 32, je);
+                float cr = 0.f, ci = 0.f;
+#pragma unroll 4
+                for (int j = j0; j < j1; ++j) {
+                    const uint4 p = sp[j];
+                    const uint32_t ph_a = (uint32_t)ma.x * p.x + (uint32_t)ma.y * p.y + (uint32_t)ma.z * p.z;
+                    const float ang = fmaf(one_plus_turns(ph_a), kTwoPiF, -kTwoPiF);
+                    float s_a, c_a;
+                    __sincosf(ang, &s_a, &c_a);
+                    const float q = __uint_as_float(p.w);
+                    cr = fmaf(q, c_a, cr);
+                    ci = fmaf(q, s_a, ci);
+                }
+                two_sum(re_hi.x, re_lo.x, cr);
+                two_sum(im_hi.x, im_lo.x, ci);
+            }
         }
         s_re[wid][lane] = (double)re_hi.x + (double)re_lo.x;
         s_im[wid][lane] = (double)im_hi.x + (double)im_lo.x;
@@ -135,7 +167,7 @@ __global__ void __launch_bounds__(kSweepThreads)
         s_im[wid][lane + 32] = (double)im_hi.y + (double)im_lo.y;
     } else {
         int4 m = make_int4(0, 0, 0, 0);
-        if (k0 + lane < bv.P) m = load_m(bv, d, work.x, k0 + lane);
+        if (k0 + lane < nk) m = load_m(bv, d, work.x, k0 + lane);
         double4_32a *sp = reinterpret_cast<double4_32a *>(smem_raw);
         const double ilx = 1.0 / d.box.L[0], ily = 1.0 / d.box.L[1], ilz = 1.0 / d.box.L[2];
         for (int j = tid; j < np; j += kSweepThreads) {
@@ -161,7 +193,7 @@ __global__ void __launch_bounds__(kSweepThreads)
     // warp c sums column c (frequency k0 + c) over the 8 warps, in order
     if (tid < ktile) {
         const int k = k0 + tid;
-        if (k < bv.P) {
+        if (k < nk) {
             double re = 0.0, im = 0.0;
 #pragma unroll
             for (int w = 0; w < kSweepThreads / 32; ++w) {
@@ -182,6 +214,10 @@ __global__ void __launch_bounds__(kCombineThreads) k_rho_combine(BatchView bv, c
     const int sy = (int)(gk / bv.P), k = (int)(gk % bv.P);
     if (bv.remaining && bv.remaining[sy] == 0) return;
     const SysDesc &d = bv.sys[sy];
+    if (k >= set_len(bv, d, sy)) {   // past the folded set: weight 0 in the energy
+        if (threadIdx.x == 0) rho[gk] = make_double2(0.0, 0.0);
+        return;
+    }
     const double2 *row = rho_part + d.rp_off + (int64_t)k * d.n_ptiles;
     // thread t sums tiles t, t + 128, ... in order; then the warps' trees,
     // then the 4 warps in order
@@ -220,8 +256,10 @@ __global__ void __launch_bounds__(kCombineThreads) k_rho_combine(BatchView bv, c
         const int4 m = load_m(bv, d, sy, k);
         // 2 pi / L from the host: FP64 divisions are slow on this GPU
         const double kx = d.box.kfac[0] * m.x, ky = d.box.kfac[1] * m.y, kz = d.box.kfac[2] * m.z;
-        // per-Gaussian sampling: each frequency weighted by its stratum
-        const double coef = bv.kw ? d.coef * bv.kw[(int64_t)sy * kKwStride + m.w] : d.coef;
+        // per-Gaussian sampling: each frequency weighted by its stratum; a
+        // folded set: each distinct frequency by the length of its run
+        const double coef = bv.kw ? d.coef * bv.kw[(int64_t)sy * kKwStride + m.w]
+                                  : (bv.kfold ? d.coef * (double)m.w : d.coef);
         if (PREC == 1) {
             KEntry32 e;
             e.mx = m.x;
@@ -303,9 +341,9 @@ __global__ void __launch_bounds__(kScatterThreads)
     const int64_t sl = (int64_t)work.y * kScatterThreads + tid;
     const int64_t s = d.p_off + sl;
     const bool active = sl < d.n;
-    const int P = bv.P;
+    const int P = set_len(bv, d, work.x);
     double4_32a *sk = reinterpret_cast<double4_32a *>(smem_raw);
-    const double4_32a *kt = reinterpret_cast<const double4_32a *>(ktab_all) + 2 * (int64_t)work.x * P;
+    const double4_32a *kt = reinterpret_cast<const double4_32a *>(ktab_all) + 2 * (int64_t)work.x * bv.P;
     double4_32a p = make_double4_32a(0, 0, 0, 0);
     if (active) p = sp64[s];
     const double ux = p.x / d.box.L[0], uy = p.y / d.box.L[1], uz = p.z / d.box.L[2];
@@ -367,14 +405,14 @@ __global__ void __launch_bounds__(kScatter32Threads, 9)
     const int2 work = bv.pblk[blockIdx.x];
     if (bv.remaining && bv.remaining[work.x] == 0) return;   // frozen system: whole block leaves
     const SysDesc &d = bv.sys[work.x];
-    const int P = bv.P;
+    const int P = set_len(bv, d, work.x);
     const int64_t la = (int64_t)work.y * kParticleBlock + tid, lb = la + kScatter32Threads;
     const bool act_a = la < d.n, act_b = lb < d.n;
     const int64_t sa = d.p_off + la, sb = d.p_off + lb;
     uint4 pa = make_uint4(0, 0, 0, 0), pb = pa;
     if (act_a) pa = sp32[sa];
     if (act_b) pb = sp32[sb];
-    const float4 *kt = ktab_all + 2 * (int64_t)work.x * P;
+    const float4 *kt = ktab_all + 2 * (int64_t)work.x * bv.P;
     const float2 two_pi = f2(kTwoPiF, kTwoPiF), m_two_pi = f2(-kTwoPiF, -kTwoPiF);
     float2 gx = f2(0.f, 0.f), gy = gx, gz = gx;
     for (int c0 = 0; c0 < P; c0 += kKChunk32) {

@@ -184,6 +184,12 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BatchView bv, const do
             const double2 r = rho[(int64_t)sy * bv.P + j];
             r2 += bv.kw[(int64_t)sy * kKwStride + ks[j].w] * (r.x * r.x + r.y * r.y);
         }
+    } else if (bv.kfold) {   // a folded set: |rho|^2 of each distinct frequency times its run length
+        const int4 *ks = bv.kfold + a.k_off + bv.cursor[sy] * (int64_t)bv.P;
+        for (int j = lo + tid; j < hi; j += kFinThreads) {
+            const double2 r = rho[(int64_t)sy * bv.P + j];
+            r2 += (double)ks[j].w * (r.x * r.x + r.y * r.y);
+        }
     } else {
         for (int j = lo + tid; j < hi; j += kFinThreads) {
             const double2 r = rho[(int64_t)sy * bv.P + j];

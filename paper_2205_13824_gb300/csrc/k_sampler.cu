@@ -163,7 +163,62 @@ __global__ void __launch_bounds__(kRound) k_mh_chain(const __grid_constant__ Sam
     }
 }
 
+// One warp per set: the starts of the runs of equal consecutive frequencies
+// by ballot (in order), then each run's length from the next start.
+__global__ void __launch_bounds__(256) k_fold_sets(const FoldSys *__restrict__ sys, int n_sys, int64_t total_sets,
+                                                   int32_t P, const int4 *__restrict__ kseq, int4 *__restrict__ kfold,
+                                                   int32_t *__restrict__ kcount) {
+    const int lane = threadIdx.x & 31;
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // global set
+    if (g >= total_sets) return;
+    int lo = 0, hi = n_sys;   // system of set g: largest lo with set_off <= g
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sys[mid].set_off <= g) lo = mid; else hi = mid;
+    }
+    const FoldSys &y = sys[lo];
+    const int64_t s = g - y.set_off;
+    const int4 *in = kseq + y.k_off + s * P;
+    int4 *out = kfold + y.k_off + s * P;
+    int nrun = 0;
+    for (int j0 = 0; j0 < P; j0 += 32) {
+        const int j = j0 + lane;
+        bool start = false;
+        int4 m = make_int4(0, 0, 0, 0);
+        if (j < P) {
+            m = in[j];
+            if (j == 0) {
+                start = true;
+            } else {
+                const int4 pr = in[j - 1];
+                start = m.x != pr.x || m.y != pr.y || m.z != pr.z;
+            }
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, start);
+        if (start) out[nrun + __popc(b & ((1u << lane) - 1u))] = make_int4(m.x, m.y, m.z, j);
+        nrun += __popc(b);
+    }
+    __syncwarp();
+    for (int t0 = 0; t0 < nrun; t0 += 32) {
+        const int t = t0 + lane;
+        int len = 0;
+        if (t < nrun) len = (t + 1 < nrun ? out[t + 1].w : P) - out[t].w;
+        __syncwarp();
+        if (t < nrun) out[t].w = len;
+        __syncwarp();
+    }
+    for (int t = nrun + lane; t < P; t += 32) out[t] = make_int4(0, 0, 0, 0);
+    if (lane == 0) kcount[y.kc_off + s] = nrun;
+}
+
 }  // namespace
+
+cudaError_t launch_fold_kseq(const FoldSys *sys, int n_sys, int64_t total_sets, int32_t P, const int4 *kseq,
+                             int4 *kfold, int32_t *kcount, cudaStream_t st) {
+    if (total_sets <= 0) return cudaSuccess;
+    k_fold_sets<<<(unsigned)((total_sets + 7) / 8), 256, 0, st>>>(sys, n_sys, total_sets, P, kseq, kfold, kcount);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mh_sampler(const SamplerDev &sp, const SamplerSys *sys, int n_sys, int64_t total_chains,
                               int4 *kseq, int32_t *err_flag, cudaStream_t st, const Prof *prof) {

@@ -98,6 +98,8 @@ struct rbsog_ctx {
     CellBuffers cb{};
     double *kpart = nullptr;
     int4 *kseq = nullptr;
+    int4 *kfold = nullptr;       // folded k-sets (mixture sampler); see FoldSys
+    int32_t *kcount = nullptr;   // distinct runs per k-set
     int64_t *cursor = nullptr, *step_ctr = nullptr;
     double2 *rho_part = nullptr, *rho = nullptr, *epart = nullptr;
     void *ktab = nullptr;
@@ -592,6 +594,8 @@ BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
     v.cursor = c->cursor;
     v.step = c->step_ctr;
     v.kseq = c->kseq;
+    v.kfold = m_explicit ? nullptr : c->kfold;
+    v.kcount = m_explicit ? nullptr : c->kcount;
     v.m_explicit = m_explicit;
     v.max_cap = c->max_cap;
     v.max_tile_p = c->max_tile_p;
@@ -1140,7 +1144,7 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
     ctx->nblk.clear();
     ctx->sblk.clear();
     std::vector<int32_t> cell_sys;
-    int64_t c_off = 0, k_off = 0, kp_off = 0;
+    int64_t c_off = 0, k_off = 0, kp_off = 0, kc_off = 0;
     ctx->tune.assign(ns, Tune{});
     for (int s = 0; s < ns; ++s) {
         const rbsog_params &q = p[s];
@@ -1151,6 +1155,8 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
         d.c_off = c_off;
         d.k_off = k_off;
         d.n_sets = q.n_ksets;
+        d.kc_off = kc_off;
+        kc_off += q.n_ksets;
         d.n_kpart = (int32_t)((d.n + kParticleBlock - 1) / kParticleBlock);
         d.kp_off = (int32_t)kp_off;
         double Ssum = 0.0;
@@ -1193,6 +1199,13 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
 
     CK(cudaSetDevice(ctx->device));
     CK(dalloc(&ctx->kseq, (size_t)k_off));
+    if (!ctx->pg_sampler) {
+        CK(dalloc(&ctx->kfold, (size_t)k_off));
+        CK(dalloc(&ctx->kcount, (size_t)kc_off));
+    } else {   // per-Gaussian draws are independent: no runs to fold
+        dfree(&ctx->kfold);
+        dfree(&ctx->kcount);
+    }
     CK(dalloc(&ctx->rho, (size_t)ns * ctx->P));
     CK(dalloc((unsigned char **)&ctx->ktab, ktab_bytes(ctx->precision, (int64_t)ns * ctx->P)));
     CK(dalloc(&ctx->kpart, (size_t)kp_off));
@@ -1313,6 +1326,21 @@ rbsog_status set_params_impl(rbsog_ctx *ctx, const rbsog_params *pp, const std::
             CK(cudaMemcpyAsync(d_ss, ss.data(), sizeof(SamplerSys) * ss.size(), cudaMemcpyHostToDevice, ctx->st));
             CK(launch_mh_sampler(sp, d_ss, (int)ss.size(), coff, ctx->kseq, ctx->err_flag, ctx->st, prof_of(ctx)));
             CK(cudaFreeAsync(d_ss, ctx->st));
+            // fold each sampled set's runs of repeated frequencies
+            std::vector<FoldSys> fs;
+            int64_t set_off = 0;
+            for (int s = 0; s < ns; ++s) {
+                if (sample_mask && !(*sample_mask)[s]) continue;
+                fs.push_back(FoldSys{ctx->desc[s].k_off, ctx->desc[s].kc_off, set_off});
+                set_off += ctx->desc[s].n_sets;
+            }
+            FoldSys *d_fs = nullptr;
+            CK(cudaMallocAsync((void **)&d_fs, sizeof(FoldSys) * fs.size(), ctx->st));
+            CK(cudaMemcpyAsync(d_fs, fs.data(), sizeof(FoldSys) * fs.size(), cudaMemcpyHostToDevice, ctx->st));
+            CK(launch_fold_kseq(d_fs, (int)fs.size(), set_off, ctx->P, ctx->kseq, ctx->kfold, ctx->kcount, ctx->st));
+            // the host vector stays alive until the copy has run
+            CK(cudaStreamSynchronize(ctx->st));
+            CK(cudaFreeAsync(d_fs, ctx->st));
         }
     }
     rbsog_status fs = check_flags(ctx);
@@ -2242,6 +2270,8 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     dfree(&ctx->cb.pack);
     dfree(&ctx->kpart);
     dfree(&ctx->kseq);
+    dfree(&ctx->kfold);
+    dfree(&ctx->kcount);
     dfree(&ctx->cursor);
     dfree(&ctx->step_ctr);
     dfree(&ctx->rho_part);
@@ -2330,10 +2360,10 @@ namespace {
 
 int64_t footprint_bytes(const Job &j) {
     // state, cell-ordered copies, cell arrays and staging per particle; the
-    // k-sequence; cells and partial sums
+    // k-sequence and its folded copy; cells and partial sums
     int64_t ncell = 1;
     for (int d = 0; d < 3; ++d) ncell *= (int64_t)std::floor(j.p.L[d] / j.p.r_c);
-    return j.n * 256 + (j.nsteps + 1) * (int64_t)j.p.P * 16 + ncell * 16 + (int64_t)j.p.P * 4096;
+    return j.n * 256 + (j.nsteps + 1) * ((int64_t)j.p.P * 32 + 4) + ncell * 16 + (int64_t)j.p.P * 4096;
 }
 
 rbsog_status srv_fail(rbsog_server *s, rbsog_status st, const std::string &m) {
@@ -2394,6 +2424,12 @@ rbsog_status rebuild(rbsog_server *sv, const std::vector<int64_t> &keep, const s
         const int64_t n = od.n;
         CK(cudaMemcpyAsync(nb->kseq + ndsc.k_off, old->kseq + od.k_off,
                            sizeof(int4) * old->n_chains[o] * old->chain_len[o], cudaMemcpyDeviceToDevice, nb->st));
+        if (nb->kfold && old->kfold) {
+            CK(cudaMemcpyAsync(nb->kfold + ndsc.k_off, old->kfold + od.k_off,
+                               sizeof(int4) * old->n_chains[o] * old->chain_len[o], cudaMemcpyDeviceToDevice, nb->st));
+            CK(cudaMemcpyAsync(nb->kcount + ndsc.kc_off, old->kcount + od.kc_off, sizeof(int32_t) * od.n_sets,
+                               cudaMemcpyDeviceToDevice, nb->st));
+        }
         CK(cudaMemcpyAsync(nb->posq + ndsc.p_off, old->posq + od.p_off, sizeof(double4_32a) * n,
                            cudaMemcpyDeviceToDevice, nb->st));
         CK(cudaMemcpyAsync(nb->vel + ndsc.p_off, old->vel + od.p_off, sizeof(double4_32a) * n,

@@ -112,6 +112,21 @@ struct ProfScope {
 cudaError_t launch_mh_sampler(const SamplerDev &sp, const SamplerSys *sys, int n_sys, int64_t total_chains,
                               int4 *kseq, int32_t *err_flag, cudaStream_t st, const Prof *prof);
 
+// Folded k-sets.  A Metropolis-Hastings chain repeats its state on every
+// rejected proposal, so about half of a set's P frequencies equal their
+// predecessor.  Every term of the random-batch sums (rho(k), the force, the
+// energy) depends only on the frequency, so each run of equal consecutive
+// frequencies is evaluated once and weighted by its length: the sums are the
+// same up to rounding.  Set s of a system becomes kfold[k_off + s P + t] =
+// (m, run length) for t < kcount[kc_off + s], zero entries (weight 0) after.
+struct FoldSys {
+    int64_t k_off;            // first int4 of the system's sequence
+    int64_t kc_off;           // first set count of the system
+    int64_t set_off;          // first global set (prefix over the listed systems)
+};
+cudaError_t launch_fold_kseq(const FoldSys *sys, int n_sys, int64_t total_sets, int32_t P, const int4 *kseq,
+                             int4 *kfold, int32_t *kcount, cudaStream_t st);
+
 // ---- per-Gaussian independent sampling (k_pgsample.cu) -------------------------
 // The variant sampler of Sec. 3.3: Gaussian l alone, normalised over k != 0,
 // is sampled P_l = ceil(P S_l / S) times per set (S_l its share of Eq. 3.16;
@@ -160,6 +175,7 @@ struct SysDesc {
     int64_t rp_off;            // first rho partial (double2 units)
     int64_t k_off;             // first int4 of this system's k-sequence
     int64_t n_sets;            // k-sets sampled
+    int64_t kc_off;            // first entry of this system's folded-set counts
     int32_t kp_off, n_kpart;   // kinetic partials (one per particle block)
     double coef;               // -lB pi^{3/2} S / (P V): multiplies q_i k Im(...)
     double half_coef_U;        // lB pi^{3/2} S / (2 P V)
@@ -191,6 +207,8 @@ struct BatchView {
     int64_t *cursor;           // [n_sys] k-sets consumed
     int64_t *step;             // [n_sys] completed steps
     const int4 *kseq;          // concatenated k-sequences
+    const int4 *kfold;         // folded k-sets (same layout; .w = run length), or null:
+    const int32_t *kcount;     //   far-field kernels then read kseq and all P entries
     const int4 *m_explicit;    // explicit k-set for a batch of one, or null
     const int32_t *force_mask; // [n_sys]: only systems with a non-zero entry take the new
                                // forces, energies and k-set (null: all systems)

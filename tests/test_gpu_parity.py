@@ -248,6 +248,36 @@ def test_forces_fp32c_within_target(N, L, P):
     g.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32c", 1e-5)])
+def test_folded_sets_equal_the_full_sum(prec, tol):
+    """A sampled set is folded into its runs of repeated frequencies, each
+    evaluated once and weighted by its length; the forces and energies equal
+    those of the same P frequencies given explicitly (no folding), and both
+    match the oracle on that set."""
+    _dev()
+    N, L, P = 4998, 21.5, 200
+    q, x, v = I.electrolyte(N, L, seed=77)
+    g, sog = make(N, L, P, prec=prec, n_ksets=3, seed=123)
+    g.set_state(*to_dev(q, x, v))
+    m = g.kseq(0, 1)
+    runs = 1 + int(np.sum(np.any(m[1:] != m[:-1], axis=1)))
+    assert runs < 0.75 * P                    # the chain repeats states: the set folds
+    B = _lib().binding
+    f_fold = torch.zeros((N, 3), dtype=torch.float64, device=_dev())
+    e_fold = B.rbsog_compute_forces(g.ctx, None, f_fold)      # next set of the sequence: folded
+    f_full = torch.zeros_like(f_fold)
+    e_full = B.rbsog_compute_forces(g.ctx, m, f_full)         # the same P frequencies, explicit
+    a, b = f_fold.cpu().numpy(), f_full.cpu().numpy()
+    assert rms_rel(a, b) < tol
+    for k in ("U_near", "U_far", "U_wca"):
+        assert e_fold[k] == pytest.approx(e_full[k], rel=tol)
+    s = osys(L, sog)
+    f_o, e_o = O.forces(s, q, O.wrap(x, s.L), S=s.S(), m=m)
+    assert rms_rel(a, f_o) < (1e-10 if prec == "fp64" else 1e-4)
+    assert e_fold["U_far"] == pytest.approx(e_o["U_far"], rel=(1e-10 if prec == "fp64" else 1e-5))
+    g.close()
+
+
 def test_far_force_sums_to_zero_and_no_nan():
     """Per k-set the random-batch force has zero sum (Im rho* rho = 0) and
     the near force obeys Newton 3, so the total force sums to ~0."""
