@@ -88,20 +88,22 @@ __device__ __forceinline__ void two_sum(float &hi, float &lo, float x) {
     lo += err;
 }
 
+// One sweep item: particle tile sblk[item_x] against frequency tile item_y.
+// Every early return is uniform over the block.
 template <int PREC>
-__global__ void __launch_bounds__(kSweepThreads)
-    k_rho_sweep(BatchView bv, const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
-                double2 *__restrict__ rho_part) {
+__device__ __forceinline__ void sweep_item(const BatchView &bv, const double4_32a *__restrict__ sp64,
+                                           const uint4 *__restrict__ sp32, double2 *__restrict__ rho_part,
+                                           int item_x, int item_y) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ double s_re[kSweepThreads / 32][kKTile32];
     __shared__ double s_im[kSweepThreads / 32][kKTile32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int2 work = bv.sblk[blockIdx.x];
-    if (bv.remaining && bv.remaining[work.x] == 0) return;   // frozen system: whole block leaves
+    const int2 work = bv.sblk[item_x];
+    if (bv.remaining && bv.remaining[work.x] == 0) return;   // frozen system: whole item skipped
     const SysDesc &d = bv.sys[work.x];
     const int ptile = work.y;
     const int ktile = PREC == 1 ? kKTile32 : kKTile;
-    const int k0 = blockIdx.y * ktile;
+    const int k0 = item_y * ktile;
     const int nk = set_len(bv, d, work.x);
     if (k0 >= nk) return;                                     // beyond the folded set: whole block
     const int64_t p0 = d.p_off + (int64_t)ptile * d.tile_p;
@@ -202,6 +204,20 @@ __global__ void __launch_bounds__(kSweepThreads)
             }
             rho_part[d.rp_off + (int64_t)k * d.n_ptiles + ptile] = make_double2(re, im);
         }
+    }
+}
+
+// Items = (particle tile, frequency tile) pairs, n_x particle tiles per
+// frequency tile; a block takes items blockIdx.x, blockIdx.x + gridDim.x, ...
+// (one item per block on a full grid; several on a persistent grid that
+// leaves room on each SM for a kernel running beside it).
+template <int PREC>
+__global__ void __launch_bounds__(kSweepThreads)
+    k_rho_sweep(BatchView bv, const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
+                double2 *__restrict__ rho_part, int n_x, int n_items) {
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        sweep_item<PREC>(bv, sp64, sp32, rho_part, it % n_x, it / n_x);
+        __syncthreads();   // the next item restages the shared tile
     }
 }
 
@@ -512,18 +528,26 @@ size_t ktab_bytes(int precision, int64_t nk) {
 }
 
 cudaError_t launch_rho_sweep(int precision, const BatchView &bv, const double4_32a *sp64, const uint4 *sp32,
-                             double2 *rho_part, cudaStream_t st, const Prof *prof) {
+                             double2 *rho_part, cudaStream_t st, const Prof *prof, int blocks_per_sm) {
     const int kt = precision == 1 ? kKTile32 : kKTile;
-    dim3 grid((unsigned)bv.n_sblk, (unsigned)((bv.P + kt - 1) / kt));
+    const int n_items = bv.n_sblk * ((bv.P + kt - 1) / kt);
+    int grid = n_items;
+    if (blocks_per_sm > 0) {
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        grid = std::min(n_items, std::max(1, blocks_per_sm * sms));
+    }
     ProfScope ps(prof, precision == 1 ? "rho_sweep_fp32c" : "rho_sweep_fp64");
     if (precision == 1) {
         const size_t sm = sizeof(uint4) * (size_t)bv.max_tile_p;
         cudaFuncSetAttribute(k_rho_sweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_rho_sweep<1><<<grid, kSweepThreads, sm, st>>>(bv, sp64, sp32, rho_part);
+        k_rho_sweep<1><<<grid, kSweepThreads, sm, st>>>(bv, sp64, sp32, rho_part, bv.n_sblk, n_items);
     } else {
         const size_t sm = sizeof(double4_32a) * (size_t)bv.max_tile_p;
         cudaFuncSetAttribute(k_rho_sweep<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_rho_sweep<0><<<grid, kSweepThreads, sm, st>>>(bv, sp64, sp32, rho_part);
+        k_rho_sweep<0><<<grid, kSweepThreads, sm, st>>>(bv, sp64, sp32, rho_part, bv.n_sblk, n_items);
     }
     return cudaGetLastError();
 }

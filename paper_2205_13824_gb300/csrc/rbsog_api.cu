@@ -27,6 +27,8 @@ using namespace rbsog;
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
+// resident rho-sweep blocks per SM when the sweep runs beside the list force
+constexpr int kSweepBesideNear = 4;
 
 struct ProfRec {
     const char *name;
@@ -152,6 +154,8 @@ struct rbsog_ctx {
     cudaGraphExec_t graph = nullptr;
     bool capturing = false;           // enqueue_step is being captured into the step graph
     cudaStream_t side = nullptr;      // captures the bodies of conditional graph nodes
+    cudaStream_t far = nullptr;       // the rho(k) sweep and combine, beside the near field
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     bool profiling = false;
     std::vector<ProfRec> prof_open, prof_done;
@@ -628,6 +632,19 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
         // kick-drift in a step), cell list and lists of the flagged systems,
         // listed pairs, far field in caller order
         if (!packed) CK(launch_fix_pack(bv, ctx->posq, ctx->sp32c, ctx->xref, ctx->d_rebuild, ctx->st, pf));
+        // The rho(k) sweep and combine need only the caller-order positions:
+        // they run on a second stream beside the list rebuild and the list
+        // force (MUFU-bound next to an L1-bound kernel), joined before the
+        // scatter.  Profiled launches stay on one stream, so that each
+        // kernel's event pair times that kernel alone.
+        const bool fork = pf == nullptr;
+        if (fork) {
+            CK(cudaEventRecord(ctx->ev_fork, ctx->st));
+            CK(cudaStreamWaitEvent(ctx->far, ctx->ev_fork, 0));
+            CK(launch_rho_sweep(prec, bv, ctx->sp64, ctx->sp32c, ctx->rho_part, ctx->far, pf, kSweepBesideNear));
+            CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->far, pf));
+            CK(cudaEventRecord(ctx->ev_join, ctx->far));
+        }
         auto rebuild = [&](cudaStream_t s2) -> rbsog_status {
             CK(launch_build_cells(bv, ctx->posq, ctx->cb, prec, ctx->sp64, ctx->sp32, s2, pf,
                                   ctx->d_rebuild + ctx->n_sys));
@@ -668,8 +685,12 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
         }
         CK(launch_near_list(bv, ctx->nsog, ctx->d_ltab, ctx->nbr_list, ctx->nbr_cnt, ctx->list_perm, ctx->fnear,
                             ctx->st, pf, ctx->use_cs ? &ctx->cs : nullptr, ctx->d_cstab));
-        CK(launch_rho_sweep(prec, bv, ctx->sp64, ctx->sp32c, ctx->rho_part, ctx->st, pf));
-        CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
+        if (fork) {
+            CK(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
+        } else {
+            CK(launch_rho_sweep(prec, bv, ctx->sp64, ctx->sp32c, ctx->rho_part, ctx->st, pf));
+            CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
+        }
         CK(launch_far_scatter(prec, bv, ctx->sp64, ctx->sp32c, ctx->ktab, ctx->fnear, nullptr,
                               force_out ? force_out : ctx->force, ctx->err_flag, ctx->st, pf, ctx->epart, kv, kp));
         if (ctx->any_boundary)
@@ -914,6 +935,10 @@ rbsog_status rbsog_batch_create(rbsog_batch **out, int32_t n_sys, const int64_t 
     if (cudaSetDevice(device) != cudaSuccess) return bail(RBSOG_ECUDA);
     if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess) return bail(RBSOG_ECUDA);
     if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess) return bail(RBSOG_ECUDA);
+    if (cudaStreamCreateWithFlags(&ctx->far, cudaStreamNonBlocking) != cudaSuccess) return bail(RBSOG_ECUDA);
+    if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return bail(RBSOG_ECUDA);
     if (cudaStreamCreateWithFlags(&ctx->io, cudaStreamNonBlocking) != cudaSuccess) return bail(RBSOG_ECUDA);
     if (cudaEventCreateWithFlags(&ctx->ev_q, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_x, cudaEventDisableTiming) != cudaSuccess ||
@@ -2311,6 +2336,9 @@ rbsog_status rbsog_destroy(rbsog_ctx *ctx) {
     if (ctx->ev_io) cudaEventDestroy(ctx->ev_io);
     if (ctx->st) cudaStreamDestroy(ctx->st);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->far) cudaStreamDestroy(ctx->far);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->io) cudaStreamDestroy(ctx->io);
     delete ctx;
     return RBSOG_OK;

@@ -372,8 +372,12 @@ cudaError_t launch_near_list(const BatchView &bv, const NearSog &sog, const floa
 // ---- far field (k_far.cu) -----------------------------------------------------
 // tile_override > 0 replaces the default particles-per-tile rule (tunable)
 void far_layout(int64_t n, int32_t P, int precision, int tile_override, int &tile_p, int &n_ptiles);
+// blocks_per_sm > 0: a persistent grid of that many blocks per SM, each
+// taking several (particle tile, frequency tile) items, which leaves room on
+// every SM for a kernel running beside it on another stream.
 cudaError_t launch_rho_sweep(int precision, const BatchView &bv, const double4_32a *sp64,
-                             const uint4 *sp32, double2 *rho_part, cudaStream_t st, const Prof *prof);
+                             const uint4 *sp32, double2 *rho_part, cudaStream_t st, const Prof *prof,
+                             int blocks_per_sm = 0);
 // Combines partials in FP64 (fixed order) into rho[n_sys * P] and the per-k
 // scatter table (k vector, prescaled Re/Im rho, integer m).
 cudaError_t launch_rho_combine(int precision, const BatchView &bv, const double2 *rho_part, double2 *rho,
