@@ -207,14 +207,23 @@ __device__ __forceinline__ void sweep_item(const BatchView &bv, const double4_32
     }
 }
 
-// Items = (particle tile, frequency tile) pairs, n_x particle tiles per
-// frequency tile; a block takes items blockIdx.x, blockIdx.x + gridDim.x, ...
-// (one item per block on a full grid; several on a persistent grid that
-// leaves room on each SM for a kernel running beside it).
+// Full grid: block (x, y) sweeps particle tile sblk[x] against frequency
+// tile y.
 template <int PREC>
 __global__ void __launch_bounds__(kSweepThreads)
     k_rho_sweep(BatchView bv, const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
-                double2 *__restrict__ rho_part, int n_x, int n_items) {
+                double2 *__restrict__ rho_part) {
+    sweep_item<PREC>(bv, sp64, sp32, rho_part, blockIdx.x, blockIdx.y);
+}
+
+// Persistent grid: items = (particle tile, frequency tile) pairs, n_x
+// particle tiles per frequency tile; a block takes items blockIdx.x,
+// blockIdx.x + gridDim.x, ..., which leaves room on each SM for a kernel
+// running beside it.
+template <int PREC>
+__global__ void __launch_bounds__(kSweepThreads)
+    k_rho_sweep_resident(BatchView bv, const double4_32a *__restrict__ sp64, const uint4 *__restrict__ sp32,
+                         double2 *__restrict__ rho_part, int n_x, int n_items) {
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         sweep_item<PREC>(bv, sp64, sp32, rho_part, it % n_x, it / n_x);
         __syncthreads();   // the next item restages the shared tile
@@ -530,24 +539,33 @@ size_t ktab_bytes(int precision, int64_t nk) {
 cudaError_t launch_rho_sweep(int precision, const BatchView &bv, const double4_32a *sp64, const uint4 *sp32,
                              double2 *rho_part, cudaStream_t st, const Prof *prof, int blocks_per_sm) {
     const int kt = precision == 1 ? kKTile32 : kKTile;
-    const int n_items = bv.n_sblk * ((bv.P + kt - 1) / kt);
-    int grid = n_items;
+    const int nkt = (bv.P + kt - 1) / kt;
+    const size_t sm = precision == 1 ? sizeof(uint4) * (size_t)bv.max_tile_p
+                                     : sizeof(double4_32a) * (size_t)bv.max_tile_p;
+    ProfScope ps(prof, precision == 1 ? "rho_sweep_fp32c" : "rho_sweep_fp64");
     if (blocks_per_sm > 0) {
         int dev = 0, sms = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        grid = std::min(n_items, std::max(1, blocks_per_sm * sms));
+        const int n_items = bv.n_sblk * nkt;
+        const int grid = std::min(n_items, std::max(1, blocks_per_sm * sms));
+        if (precision == 1) {
+            cudaFuncSetAttribute(k_rho_sweep_resident<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_rho_sweep_resident<1><<<grid, kSweepThreads, sm, st>>>(bv, sp64, sp32, rho_part, bv.n_sblk, n_items);
+        } else {
+            cudaFuncSetAttribute(k_rho_sweep_resident<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_rho_sweep_resident<0><<<grid, kSweepThreads, sm, st>>>(bv, sp64, sp32, rho_part, bv.n_sblk, n_items);
+        }
+        return cudaGetLastError();
     }
-    ProfScope ps(prof, precision == 1 ? "rho_sweep_fp32c" : "rho_sweep_fp64");
+    const dim3 grid((unsigned)bv.n_sblk, (unsigned)nkt);
     if (precision == 1) {
-        const size_t sm = sizeof(uint4) * (size_t)bv.max_tile_p;
         cudaFuncSetAttribute(k_rho_sweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_rho_sweep<1><<<grid, kSweepThreads, sm, st>>>(bv, sp64, sp32, rho_part, bv.n_sblk, n_items);
+        k_rho_sweep<1><<<grid, kSweepThreads, sm, st>>>(bv, sp64, sp32, rho_part);
     } else {
-        const size_t sm = sizeof(double4_32a) * (size_t)bv.max_tile_p;
         cudaFuncSetAttribute(k_rho_sweep<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_rho_sweep<0><<<grid, kSweepThreads, sm, st>>>(bv, sp64, sp32, rho_part, bv.n_sblk, n_items);
+        k_rho_sweep<0><<<grid, kSweepThreads, sm, st>>>(bv, sp64, sp32, rho_part);
     }
     return cudaGetLastError();
 }
