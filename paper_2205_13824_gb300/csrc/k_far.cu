@@ -337,6 +337,34 @@ __device__ __forceinline__ float kick_one(double4_32a *__restrict__ vel, int64_t
     return (float)fma(v.z, v.z, fma(v.y, v.y, v.x * v.x)) * a.half_mass_f;
 }
 
+// The second half kick of this step (as kick_one, returning its kinetic
+// term), then the next step's half kick and drift with the force just formed
+// (the expressions of the kick-drift kernel, so the same bits as launching
+// it): positions folded into the box, the fixed-point pack and displacement
+// test for the next step's neighbour lists.
+__device__ __forceinline__ float kick_drift_one(double4_32a *__restrict__ vel, int64_t i, const double4_32a &f,
+                                                const SysDesc &a, int sys, const BatchView &bv,
+                                                const DriftOut &dr) {
+    double4_32a v = vel[i];
+    const double h = a.half_dt_inv_mass;
+    v.x += h * f.x;
+    v.y += h * f.y;
+    v.z += h * f.z;
+    const float ke = (float)fma(v.z, v.z, fma(v.y, v.y, v.x * v.x)) * a.half_mass_f;
+    v.x += h * f.x;
+    v.y += h * f.y;
+    v.z += h * f.z;
+    double4_32a p = dr.posq[i];
+    p.x += a.dt * v.x;
+    p.y += a.dt * v.y;
+    p.z += a.dt * v.z;
+    fold_into_box(p, a.box);
+    vel[i] = v;
+    dr.posq[i] = p;
+    fixed_pack_check(a, sys, bv.n_sys, p, i, dr.sp32c, dr.xref, dr.rebuild, bv.lpos, bv.linv);
+    return ke;
+}
+
 // The two near energies of a particle packed in fn.w (neighbour-list path),
 // summed over a warp's 32 particles by an FP32 tree.
 __device__ __forceinline__ float2 warp_energy(bool active, const double4_32a &fn) {
@@ -421,7 +449,7 @@ __global__ void __launch_bounds__(kScatter32Threads, 9)
     k_far_scatter32(BatchView bv, const uint4 *__restrict__ sp32, const float4 *__restrict__ ktab_all,
                     const double4_32a *__restrict__ fnear, const int32_t *__restrict__ perm,
                     double4_32a *__restrict__ force, int32_t *__restrict__ err_flag, double2 *__restrict__ epart,
-                    double4_32a *__restrict__ vel, double *__restrict__ kpart) {
+                    double4_32a *__restrict__ vel, double *__restrict__ kpart, const DriftOut drift) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ double2 s_e[kParticleBlock / 32];
     __shared__ double s_k[kParticleBlock / 32];
@@ -498,8 +526,13 @@ __global__ void __launch_bounds__(kScatter32Threads, 9)
         // tree per 32 particles (warp w holds 32w.. and 128 + 32w..), then
         // the eight trees in FP64 in particle order
         float ka = 0.f, kb = 0.f;
-        if (act_a) ka = kick_one(vel, perm ? perm[sa] : sa, ta, d);
-        if (act_b) kb = kick_one(vel, perm ? perm[sb] : sb, tb, d);
+        if (drift.posq) {   // caller order (neighbour-list path): perm is null
+            if (act_a) ka = kick_drift_one(vel, sa, ta, d, work.x, bv, drift);
+            if (act_b) kb = kick_drift_one(vel, sb, tb, d, work.x, bv, drift);
+        } else {
+            if (act_a) ka = kick_one(vel, perm ? perm[sa] : sa, ta, d);
+            if (act_b) kb = kick_one(vel, perm ? perm[sb] : sb, tb, d);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             ka += __shfl_down_sync(0xffffffffu, ka, o);
@@ -584,13 +617,14 @@ cudaError_t launch_rho_combine(int precision, const BatchView &bv, const double2
 cudaError_t launch_far_scatter(int precision, const BatchView &bv, const double4_32a *sp64, const uint4 *sp32,
                                const void *ktab, const double4_32a *fnear, const int32_t *perm,
                                double4_32a *force, int32_t *err_flag, cudaStream_t st, const Prof *prof,
-                               double2 *epart, double4_32a *kick_vel, double *kick_kpart) {
+                               double2 *epart, double4_32a *kick_vel, double *kick_kpart, const DriftOut *drift) {
     ProfScope ps(prof, precision == 1 ? "far_scatter_fp32c" : "far_scatter_fp64");
     if (precision == 1) {
         const size_t sm = sizeof(KEntry32) * kKChunk32;
+        const DriftOut dr = (drift && kick_vel && !perm) ? *drift : DriftOut{nullptr, nullptr, nullptr, nullptr};
         k_far_scatter32<<<bv.n_pblk, kScatter32Threads, sm, st>>>(bv, sp32, static_cast<const float4 *>(ktab),
                                                                    fnear, perm, force, err_flag, epart, kick_vel,
-                                                                   kick_kpart);
+                                                                   kick_kpart, dr);
     } else {
         const size_t sm = sizeof(KEntry64) * kKChunk64;
         k_far_scatter64<<<bv.n_pblk, kScatterThreads, sm, st>>>(bv, sp64, ktab, fnear, perm, force, err_flag,

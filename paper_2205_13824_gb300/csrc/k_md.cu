@@ -11,11 +11,6 @@ namespace {
 constexpr int kThreads = kParticleBlock;
 constexpr int kFinThreads = 256;
 
-__device__ __forceinline__ double fold(double x, double L) {
-    double v = x - L * floor(x / L);
-    return v >= L ? 0.0 : v;
-}
-
 // Three standard normals for the Langevin step of particle il in the step
 // with step counter t: Philox4x64-10, key (seed, 2^63 + 1) (the sampler's
 // chain keys stay below 2^63), counter (t, il, 0, 0); Box-Muller
@@ -45,15 +40,6 @@ __device__ __forceinline__ void langevin_noise(uint64_t seed, int64_t t, int64_t
         z[2] = r23 * c3;
         (void)s3;
     }
-}
-
-// x < 0 or x >= L (L > 0) decided on the bit patterns with integer compares
-// (the order of non-negative doubles is that of their bits): the same
-// outcome as the FP64 compares, which are scarce on this GPU; -0.0 stays,
-// NaN folds to NaN either way.
-__device__ __forceinline__ bool outside(double x, long long Lbits) {
-    const long long b = __double_as_longlong(x);
-    return b >= Lbits || (b < 0 && b != (long long)0x8000000000000000ull);
 }
 
 // v += dt/2 F/m ; x += dt v ; x folded into [0, L).
@@ -95,10 +81,7 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift(BatchView bv, double4_3
         p.y += a.dt * v.y;
         p.z += a.dt * v.z;
     }
-    // fold only coordinates that left the box (the division is FP64-pipe bound)
-    if (outside(p.x, __double_as_longlong(a.box.L[0]))) p.x = fold(p.x, a.box.L[0]);
-    if (outside(p.y, __double_as_longlong(a.box.L[1]))) p.y = fold(p.y, a.box.L[1]);
-    if (outside(p.z, __double_as_longlong(a.box.L[2]))) p.z = fold(p.z, a.box.L[2]);
+    fold_into_box(p, a.box);
     vel[i] = v;
     posq[i] = p;
     if (sp32c) fixed_pack_check(a, w.x, bv.n_sys, p, i, sp32c, xref, rebuild, bv.lpos, bv.linv);

@@ -71,6 +71,8 @@ struct rbsog_ctx {
     cudaEvent_t ev_q = nullptr, ev_x = nullptr, ev_io = nullptr;   // rbsog_step_io
     cudaStream_t io = nullptr;                                     // rbsog_step_io downloads
     cudaGraphExec_t graph_tail = nullptr;   // a step without its kick-drift (rbsog_step_io)
+    cudaGraphExec_t graph_fused = nullptr;  // a step without its kick-drift whose scatter runs
+                                            // the next step's kick-drift (rbsog_batch_step)
     std::string err;
 
     bool have_params = false;
@@ -621,8 +623,11 @@ BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
 // fuse_kick: the FP32C scatter also runs the step's second half kick (the
 // caller then launches no kick); valid only without a boundary term, which
 // adds to the force after the scatter.
+// fuse_drift (with fuse_kick, neighbour lists): the scatter also runs the
+// next step's half kick and drift.
 rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_sorted,
-                            double4_32a *force_out = nullptr, bool packed = false, bool fuse_kick = false) {
+                            double4_32a *force_out = nullptr, bool packed = false, bool fuse_kick = false,
+                            bool fuse_drift = false) {
     const Prof *pf = prof_of(ctx);
     const int prec = ctx->precision;
     double4_32a *kv = fuse_kick ? ctx->vel : nullptr;
@@ -691,8 +696,10 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
             CK(launch_rho_sweep(prec, bv, ctx->sp64, ctx->sp32c, ctx->rho_part, ctx->st, pf));
             CK(launch_rho_combine(prec, bv, ctx->rho_part, ctx->rho, ctx->ktab, ctx->st, pf));
         }
+        const DriftOut dr{ctx->posq, ctx->sp32c, ctx->xref, ctx->d_rebuild};
         CK(launch_far_scatter(prec, bv, ctx->sp64, ctx->sp32c, ctx->ktab, ctx->fnear, nullptr,
-                              force_out ? force_out : ctx->force, ctx->err_flag, ctx->st, pf, ctx->epart, kv, kp));
+                              force_out ? force_out : ctx->force, ctx->err_flag, ctx->st, pf, ctx->epart, kv, kp,
+                              fuse_kick && fuse_drift ? &dr : nullptr));
         if (ctx->any_boundary)
             CK(launch_boundary(bv, ctx->posq, ctx->dpart, ctx->dip, ctx->energy, force_out ? force_out : ctx->force,
                                ctx->st, pf));
@@ -725,11 +732,13 @@ rbsog_status enqueue_kick_drift(rbsog_ctx *ctx) {
     return RBSOG_OK;
 }
 
-rbsog_status enqueue_step_tail(rbsog_ctx *ctx) {
+// drift_next: the step's scatter also runs the next step's kick-drift
+// (drift_fusable only).
+rbsog_status enqueue_step_tail(rbsog_ctx *ctx, bool drift_next = false) {
     const Prof *pf = prof_of(ctx);
     const BatchView bv = view(ctx);
     const bool fused = ctx->precision == RBSOG_FP32C && !ctx->any_boundary;
-    rbsog_status s = enqueue_forces(ctx, bv, nullptr, nullptr, ctx->use_list, fused);
+    rbsog_status s = enqueue_forces(ctx, bv, nullptr, nullptr, ctx->use_list, fused, drift_next && fused);
     if (s != RBSOG_OK) return s;
     if (!fused) CK(launch_kick(bv, ctx->vel, ctx->force, ctx->kpart, ctx->st, pf));
     CK(launch_finalize(bv, ctx->epart, ctx->rho, ctx->kpart, 1, ctx->energy, 1, ctx->st, pf));
@@ -746,20 +755,38 @@ rbsog_status enqueue_step(rbsog_ctx *ctx) {
     return enqueue_step_tail(ctx);
 }
 
+// The scatter can run the next step's kick-drift when nothing happens to the
+// velocities between this step's second half kick and the next step's first
+// one: FP32C on neighbour lists (the scatter writes the total force in
+// caller order), no boundary term after the scatter, no thermostat, no step
+// budgets (a system could stop after this step).
+bool drift_fusable(const rbsog_ctx *ctx) {
+    if (ctx->precision != RBSOG_FP32C || !ctx->use_list || ctx->any_boundary || ctx->use_budget) return false;
+    for (const auto &pp : ctx->p)
+        if (pp.tau_T > 0.0) return false;
+    return true;
+}
+
 void drop_graph(rbsog_ctx *c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->graph_tail) cudaGraphExecDestroy(c->graph_tail);
+    if (c->graph_fused) cudaGraphExecDestroy(c->graph_fused);
     c->graph = nullptr;
     c->graph_tail = nullptr;
+    c->graph_fused = nullptr;
 }
 
-// Captures a whole step (tail = false) or its tail into *out (once).
-rbsog_status capture_step(rbsog_ctx *ctx, bool tail, cudaGraphExec_t *out) {
+enum class StepPart { whole, tail, tail_drift };
+
+// Captures a whole step, its tail, or its tail with the next step's
+// kick-drift into *out (once).
+rbsog_status capture_step(rbsog_ctx *ctx, StepPart part, cudaGraphExec_t *out) {
     if (*out) return RBSOG_OK;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
     ctx->capturing = true;
-    rbsog_status es = tail ? enqueue_step_tail(ctx) : enqueue_step(ctx);
+    rbsog_status es = part == StepPart::whole ? enqueue_step(ctx)
+                                              : enqueue_step_tail(ctx, part == StepPart::tail_drift);
     ctx->capturing = false;
     cudaError_t ce = cudaStreamEndCapture(ctx->st, &g);
     if (es != RBSOG_OK) {
@@ -1621,8 +1648,19 @@ rbsog_status rbsog_batch_step(rbsog_batch *ctx, int64_t nsteps) {
             es = enqueue_step(ctx);
             if (es != RBSOG_OK) return es;
         }
+    } else if (nsteps >= 2 && drift_fusable(ctx)) {
+        // one kick-drift, then steps whose scatter runs the next step's
+        // kick-drift, then a last step that leaves the state at its end
+        es = enqueue_kick_drift(ctx);
+        if (es != RBSOG_OK) return es;
+        es = capture_step(ctx, StepPart::tail_drift, &ctx->graph_fused);
+        if (es != RBSOG_OK) return es;
+        es = capture_step(ctx, StepPart::tail, &ctx->graph_tail);
+        if (es != RBSOG_OK) return es;
+        for (int64_t t = 0; t + 1 < nsteps; ++t) CK(cudaGraphLaunch(ctx->graph_fused, ctx->st));
+        CK(cudaGraphLaunch(ctx->graph_tail, ctx->st));
     } else if (nsteps > 0) {
-        es = capture_step(ctx, false, &ctx->graph);
+        es = capture_step(ctx, StepPart::whole, &ctx->graph);
         if (es != RBSOG_OK) return es;
         for (int64_t t = 0; t < nsteps; ++t) CK(cudaGraphLaunch(ctx->graph, ctx->st));
     }
@@ -1710,7 +1748,7 @@ rbsog_status rbsog_step_io(rbsog_ctx *ctx, const double *q, const double *x, con
             if (es != RBSOG_OK) return es;
         }
     } else if (nsteps > 1) {
-        es = capture_step(ctx, false, &ctx->graph);
+        es = capture_step(ctx, StepPart::whole, &ctx->graph);
         if (es != RBSOG_OK) return es;
         for (int64_t t = 0; t + 1 < nsteps; ++t) CK(cudaGraphLaunch(ctx->graph, ctx->st));
     }
@@ -1730,7 +1768,7 @@ rbsog_status rbsog_step_io(rbsog_ctx *ctx, const double *q, const double *x, con
         es = enqueue_step_tail(ctx);
         if (es != RBSOG_OK) return es;
     } else {
-        es = capture_step(ctx, true, &ctx->graph_tail);
+        es = capture_step(ctx, StepPart::tail, &ctx->graph_tail);
         if (es != RBSOG_OK) return es;
         CK(cudaGraphLaunch(ctx->graph_tail, ctx->st));
     }

@@ -266,6 +266,29 @@ __device__ __forceinline__ uint32_t fixed32(double x, double inv) {
     return __double2uint_rz(x * inv);
 }
 
+// x folded into [0, L); L mapped to 0.
+__device__ __forceinline__ double fold(double x, double L) {
+    double v = x - L * floor(x / L);
+    return v >= L ? 0.0 : v;
+}
+
+// x < 0 or x >= L (L > 0) decided on the bit patterns with integer compares
+// (the order of non-negative doubles is that of their bits): the same
+// outcome as the FP64 compares, which are scarce on this GPU; -0.0 stays,
+// NaN folds to NaN either way.
+__device__ __forceinline__ bool outside(double x, long long Lbits) {
+    const long long b = __double_as_longlong(x);
+    return b >= Lbits || (b < 0 && b != (long long)0x8000000000000000ull);
+}
+
+// Folds only the coordinates that left the box (the division is FP64-pipe
+// bound).
+__device__ __forceinline__ void fold_into_box(double4_32a &p, const BoxDev &box) {
+    if (outside(p.x, __double_as_longlong(box.L[0]))) p.x = fold(p.x, box.L[0]);
+    if (outside(p.y, __double_as_longlong(box.L[1]))) p.y = fold(p.y, box.L[1]);
+    if (outside(p.z, __double_as_longlong(box.L[2]))) p.z = fold(p.z, box.L[2]);
+}
+
 // Caller-order fixed-point position (x, y, z, FP32 charge) of particle i for
 // the neighbour-list path, and the test of its displacement since the last
 // list build: a particle of system `sys` that moved more than skin / 2 sets
@@ -390,11 +413,22 @@ cudaError_t launch_rho_combine(int precision, const BatchView &bv, const double2
 // the kernel (v += dt/2 F/m in caller order and the kinetic-energy partial
 // of each particle block into kick_kpart, the bits of launch_kick); only
 // when nothing else adds to the force afterwards.
+// With drift non-null as well (FP32C, neighbour lists, no thermostat): the
+// next step's half kick and drift follow in the same pass, with the
+// expressions of launch_kick_drift (drift.posq, and the fixed-point pack and
+// displacement test into drift.sp32c / xref / rebuild), so that the next
+// step starts at its force evaluation.
+struct DriftOut {
+    double4_32a *posq;
+    uint4 *sp32c;
+    const uint4 *xref;
+    int32_t *rebuild;
+};
 cudaError_t launch_far_scatter(int precision, const BatchView &bv, const double4_32a *sp64,
                                const uint4 *sp32, const void *ktab, const double4_32a *fnear,
                                const int32_t *perm, double4_32a *force, int32_t *err_flag, cudaStream_t st,
                                const Prof *prof, double2 *epart = nullptr, double4_32a *kick_vel = nullptr,
-                               double *kick_kpart = nullptr);
+                               double *kick_kpart = nullptr, const DriftOut *drift = nullptr);
 size_t ktab_bytes(int precision, int64_t nk);
 
 // ---- integrator and reductions (k_md.cu) --------------------------------------

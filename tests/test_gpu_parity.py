@@ -465,6 +465,35 @@ def test_checkpoint_resume_is_bit_exact():
         g.close()
 
 
+def test_fused_kick_drift_equals_separate_steps():
+    """In NVE on neighbour lists a call of several steps lets each step's
+    scatter run the next step's kick-drift; the state and energies equal,
+    bit for bit, those of one-step calls (each a whole step) and of the
+    eager launches, including steps with list rebuilds."""
+    _dev()
+    N, L, P, steps = 4998, 21.5, 64, 30
+    q, x, v = I.electrolyte(N, L, seed=18, T=4.0)
+    out = []
+    for mode in ("fused", "single", "eager"):
+        g, _ = make(N, L, P, prec="fp32c", n_ksets=steps + 2, seed=6)
+        _lib().binding.rbsog_set_profiling(g.ctx, mode == "eager")
+        g.set_state(*to_dev(q, x, v))
+        if mode == "single":
+            for _ in range(steps):
+                g.step(1)
+        else:
+            g.step(steps)
+        st = [a.cpu().numpy() for a in g.state()[:3]]
+        out.append((st, g.energies(), g.info()[0].list_builds))
+        g.close()
+    assert out[0][2] > 1                      # lists were rebuilt during the run
+    for st, e, nb in out[1:]:
+        for a, b in zip(out[0][0], st):
+            assert np.array_equal(a, b)
+        assert e == out[0][1]
+        assert nb == out[0][2]
+
+
 def test_runs_are_deterministic():
     _dev()
     N, L, P = 4998, 21.5, 64
