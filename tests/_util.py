@@ -117,3 +117,16 @@ def per_particle_rel(a, b):
 # the far field's 24-bit angles and hardware sin/cos about 1e-6 per term)
 PP_FP64 = 1e-9
 PP_FP32C = 1e-4
+
+
+def oracle_kseq(O, g, sog, L, seed, nsets):
+    """The oracle's own sampling of the first nsets k-sets for a device
+    context's chain layout (seed, chains of chain_len); it is the input the
+    oracle's trajectory takes, and it equals the device's sequence bit for
+    bit (checked here as well)."""
+    info = g.info()[0]
+    Lv = (L,) * 3 if isinstance(L, (int, float)) else tuple(L)
+    ks = O.kseq(sog, Lv, seed=seed, n_chains=info.n_chains, chain_len=info.chain_len)
+    P = info.P_set
+    assert np.array_equal(g.kseq(0, nsets), ks[: nsets * P])
+    return ks

@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 import rbsog_inputs as I
-from tests._util import prod_sog
+from tests._util import oracle_kseq, prod_sog
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -34,7 +34,7 @@ def test_nose_hoover_trajectory_matches_oracle(prec, tol):
     p, sog = _params(Pk, L, P, prec, steps + 1)
     g = Pk.RBSOG(N, p, device=0)
     g.set_state(*(torch.tensor(a, device=dev) for a in (q, x, v)))
-    ks = g.kseq(0, steps + 1)
+    ks = oracle_kseq(O, g, sog, L, p.seed, steps + 1)
     g.step(steps)
     xg, vg, _, st = g.state()
     e = g.energies()

@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 import rbsog_inputs as I
-from tests._util import prod_sog
+from tests._util import oracle_kseq, prod_sog
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -31,7 +31,7 @@ def test_msd_vacf_match_oracle_trajectory():
                        precision="fp64")
     g = Pk.RBSOG(N, p, device=0)
     g.set_state(*(torch.tensor(a, device=dev) for a in (q, x, v)))
-    ks = g.kseq(0, steps + 1)
+    ks = oracle_kseq(O, g, sog, L, 4, steps + 1)
     g.observe_start(n_lags, every_o)
     g.observe_sample()
     for _ in range(n_samp - 1):

