@@ -351,22 +351,25 @@ def run_ours(args, rank, world, local, dist):
     prof = B.rbsog_get_profile(g.ctx)
     B.rbsog_set_profiling(g.ctx, False)
     rebuilds_prof = g.info()[0].list_builds - b_prof
+    # the near field runs on neighbour lists (built at least once so far)
+    lists = g.info()[0].list_builds > 0
     # kernels every graph-replayed step launches; the cell-list and list-build
     # kernels sit in a conditional graph node and run only on rebuild steps
     # (every ~22 steps here), so they are not counted
     gated = ("cell_bin", "cell_scan", "cell_scatter", "cell_order_gather", "list_build")
     launches_per_step = sum(c for k, (c, _) in prof.items() if not k.startswith(gated)) / K
-    if "list_build" in prof:
+    if lists:
         launches_per_step += 1   # the one-thread kernel that sets the rebuild node's condition
     gpu_launches = int(round(launches_per_step * K))
-    if "kick_drift" in prof and "list_build" in prof:
+    if "kick_drift" in prof and lists:
         # NVE on neighbour lists: in the graph-replayed call each step's
         # scatter runs the next step's kick-drift, so the call launches one
         # kick-drift kernel instead of one per step
         gpu_launches -= K - 1
     if rebuilds_in_window:
-        per_build = sum(c for k, (c, _) in prof.items() if k.startswith(gated)) / max(1, prof.get(
-            "list_build", (1, 0))[0])
+        # kernels of one rebuild: the cell-list and list-build launches of the
+        # profiled rebuilds per rebuild (one launch each, the scan two)
+        per_build = sum(c for k, (c, _) in prof.items() if k.startswith(gated)) / max(1, rebuilds_prof)
         gpu_launches += int(round(per_build * rebuilds_in_window))
 
     # end to end through the C ABI from pinned host buffers: per step the
@@ -388,16 +391,15 @@ def run_ours(args, rank, world, local, dist):
 
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6686.1)
-    lists = "list_build" in prof
     top = max(prof.items(), key=lambda kv: kv[1][1])
     roof = roofline_for(top[0], top[1][0], top[1][1], N, L, P, 3.0, meas, hbm, lists, P_eval)
     roof_far = [roofline_for(k, c, t, N, L, P, 3.0, meas, hbm, P_eval=P_eval) for k, (c, t) in prof.items()
                 if k.startswith(("rho_sweep", "far_scatter"))]
     roof_near = [roofline_for(k, c, t, N, L, P, 3.0, meas, hbm, lists) for k, (c, t) in prof.items()
                  if k.startswith("near")]
-    # the gated build kernel returns at once on steps without a rebuild: its
-    # profiled time over the rebuilds that ran is the time per rebuild
-    roof_build = [roofline_for(k, max(1, rebuilds_prof), t, N, L, P, 3.0, meas, hbm, lists)
+    # profiled steps launch the build kernels only on a rebuild: the profiled
+    # time over those launches is the time per rebuild
+    roof_build = [roofline_for(k, c, t, N, L, P, 3.0, meas, hbm, lists)
                   for k, (c, t) in prof.items() if k.startswith("list_build")]
     tot = sum(tt for _, tt in prof.values())
     kernels = {k: {"launches": c, "ms_per_launch": t / c, "share": t / tot}

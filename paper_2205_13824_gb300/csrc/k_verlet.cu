@@ -95,8 +95,9 @@ __global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv
     const BoxDev &box = desc.box;
     const int group = desc.group, nseg_x = desc.nseg_x, cap = desc.near_cap;
     const int lcap = bv.list_cap;
-    float4 *__restrict__ st = reinterpret_cast<float4 *>(smem_raw);                       // [cap]
-    int *__restrict__ st_id = reinterpret_cast<int *>(smem_raw + sizeof(float4) * cap);   // [cap]
+    // [cap] staged partners: offsets from the block centre and, in w, the
+    // particle's cell-order index (as bits)
+    float4 *__restrict__ st = reinterpret_cast<float4 *>(smem_raw);
     const int64_t coff = desc.c_off;
     const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
     const int sx = work.y % nseg_x, row = work.y / nseg_x;
@@ -168,8 +169,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv
                         const int src = psrc[pp] + (t - plo[pp]);
                         const uint4 u = sp32[src];
                         st[t - c0] = make_float4(offset_f(u.x, ox, fsx), offset_f(u.y, oy, fsy),
-                                                 offset_f(u.z, oz, fsz), 0.f);
-                        st_id[t - c0] = src;
+                                                 offset_f(u.z, oz, fsz), __int_as_float(src));
                     }
                 }
             }
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv
                     const float dx = ix - pj.x, dy = iy - pj.y, dz = iz - pj.z;
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     if (r2 < rl2 && r2 > 0.f) {
-                        if (cnt < lcap) nbr_list[slot_index(hi, cnt, lcap)] = st_id[t - c0];
+                        if (cnt < lcap) nbr_list[slot_index(hi, cnt, lcap)] = __float_as_int(pj.w);
                         else over = true;
                         ++cnt;
                     }
@@ -417,7 +417,7 @@ cudaError_t launch_rebuild_condition(cudaGraphConditionalHandle h, const int32_t
 
 size_t list_build_smem(int cap, int list_cap) {
     (void)list_cap;
-    return (sizeof(float4) + sizeof(int)) * (size_t)cap;
+    return sizeof(float4) * (size_t)cap;
 }
 
 cudaError_t launch_fix_pack(const BatchView &bv, const double4_32a *posq, uint4 *sp32c, const uint4 *xref,

@@ -685,8 +685,20 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
             CK(ce);
             CK(cudaStreamUpdateCaptureDependencies(ctx->st, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
         } else {
-            rbsog_status rs = rebuild(ctx->st);
-            if (rs != RBSOG_OK) return rs;
+            // eager launches: the rebuild kernels are gated on the device;
+            // profiled steps read the flag first and launch them only on a
+            // rebuild, so that their timings are those of real rebuilds
+            bool run = true;
+            if (pf) {
+                int32_t *hf = reinterpret_cast<int32_t *>(ctx->h_i64 + 3);
+                CK(cudaMemcpyAsync(hf, ctx->d_rebuild + ctx->n_sys, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->st));
+                CK(cudaStreamSynchronize(ctx->st));
+                run = *hf != 0;
+            }
+            if (run) {
+                rbsog_status rs = rebuild(ctx->st);
+                if (rs != RBSOG_OK) return rs;
+            }
         }
         CK(launch_near_list(bv, ctx->nsog, ctx->d_ltab, ctx->nbr_list, ctx->nbr_cnt, ctx->list_perm, ctx->fnear,
                             ctx->st, pf, ctx->use_cs ? &ctx->cs : nullptr, ctx->d_cstab));
