@@ -561,6 +561,7 @@ def run_extras(args, q, x, v, dev):
                                    "near_ms": near_c[1] / near_c[0]}
     g.close()
     out.update(run_dynamics_extras(args, tq, tx, tv, dev))
+    out["small_configs"] = run_small_configs(dev)
     rep = run_replicas(dev)
     out["batched_replicas"] = rep
     srv = run_serving(dev)
@@ -571,6 +572,129 @@ def run_extras(args, q, x, v, dev):
                                   "served_particle_steps_per_s": cb["served_particle_steps_per_s"],
                                   "fp64_one_at_a_time_p50_s": srv["one_at_a_time_fp64"]["latency_p50_s"],
                                   "fp64_one_at_a_time_p99_s": srv["one_at_a_time_fp64"]["latency_p99_s"]}
+    return out
+
+
+def run_small_configs(dev):
+    """The two smaller workloads as specified.  1,000-ion electrolyte (L =
+    12.6, P = 100), FP64: one force evaluation and 10 velocity-Verlet steps,
+    timed, with the forces after the 10 steps against the oracle's trajectory
+    on the oracle's own sequence (the CPU-baseline leg's oracle).  64,000-ion
+    electrolyte (L = 50.4, P = 200), FP32C, 1,000 Berendsen steps at T0 = 1:
+    every 100 steps the FP32C force at the trajectory's positions against the
+    FP64 path on one k-set (RMS relative and worst particle), the total
+    energy and T; the same run through the FP64 path, and 1,000 NVE steps in
+    both precisions from the same start, for the energies side by side."""
+    import numpy as np
+    import torch
+
+    import paper_2205_13824_gb300 as Pk
+    import rbsog_inputs as I
+    B = Pk.binding
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    # 1,000 ions, FP64: 10 steps against the oracle's trajectory, then the
+    # steady-state step time on the same system
+    N, L, P, steps = 1000, 12.6, 100, 10
+    q, x, v = I.electrolyte(N, L, seed=1)
+    p = Pk.make_params(L, P, n_ksets=steps + 1, seed=7, precision="fp64")
+    g = Pk.RBSOG(N, p, device=dev.index)
+    g.set_state(*(torch.tensor(a, device=dev) for a in (q, x, v)))
+    info = g.info()[0]
+    g.step(steps)
+    xg, _, fg, _ = (a.cpu().numpy() if hasattr(a, "cpu") else a for a in g.state())
+    kseq_dev = g.kseq(0, steps + 1)
+    g.close()
+    base, ks, xo, fo = cpu_baseline_small(q, x, v, L, P, steps, info.n_chains, info.chain_len)
+    dx = xg - xo
+    dx -= L * np.rint(dx / L)
+    reps = 200
+
+    def steady_ms(prec):
+        h = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=steps * (reps + 1) + 1, seed=7, precision=prec),
+                     device=dev.index)
+        h.set_state(*(torch.tensor(a, device=dev) for a in (q, x, v)))
+        h.step(steps)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            h.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        h.close()
+        return e0.elapsed_time(e1) / (reps * steps)
+    ms = steady_ms("fp64")
+    ms32 = steady_ms("fp32c")
+    out["electrolyte_N1000_fp64"] = {
+        "ms_per_step": ms, "value": N / (ms / 1e3), "unit": "particle-steps/s",
+        "timing": f"{reps} calls of {steps} steps each, after the first call",
+        "vs_oracle_after_10_steps": dict(rel_errors(fg, fo), max_position_diff=float(np.abs(dx).max()),
+                                         same_k_sequence=bool(np.array_equal(kseq_dev, ks[: len(kseq_dev)]))),
+        "cpu_baseline": base,
+        "fp32c": {"ms_per_step": ms32, "value": N / (ms32 / 1e3)},
+        "note": "the FP64 near field of 1,000 ions runs on 32 blocks of one active warp each: "
+                "bound by the latency of this GPU's FP64 units, not by their rate"}
+    # 64,000 ions, FP32C, 1,000 Berendsen steps; NVE drift
+    N, L, P = 64000, 50.4, 200
+    q, x, v = I.electrolyte(N, L, seed=2022)
+    tq, tx, tv = (torch.tensor(a, device=dev) for a in (q, x, v))
+    g = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=1001, seed=77, precision="fp32c", tau_T=0.1), device=dev.index)
+    g.set_state(tq, tx, tv)
+    c32 = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=1, seed=1, precision="fp32c"), device=dev.index)
+    c64 = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=1, seed=1, precision="fp64"), device=dev.index)
+    m = c64.kseq(0, 1)
+    f32 = torch.zeros((N, 3), dtype=torch.float64, device=dev)
+    f64 = torch.zeros_like(f32)
+    rows, t_steps = [], 0.0
+    for c in range(10):
+        e0.record(st)
+        g.step(100)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t_steps += e0.elapsed_time(e1)
+        xg = g.state()[0]
+        en = g.energies()
+        for ctx, f in ((c32, f32), (c64, f64)):
+            ctx.set_state(tq, xg)
+            B.rbsog_compute_forces(ctx.ctx, m, f)
+        err = rel_errors(f32.cpu().numpy(), f64.cpu().numpy())
+        rows.append({"step": 100 * (c + 1), "rms_rel_force_vs_fp64": err["rms_rel_force"],
+                     "per_particle_max_vs_fp64": err["per_particle_max"], "T": en["T"],
+                     "E_total": en["U_near"] + en["U_far"] - en["U_self"] + en["U_wca"] + en["K"]})
+    counts, gr = g.rdf(256)
+    g.close()
+    c32.close()
+    c64.close()
+    # the same 1,000 NVT steps through the FP64 path, and 1,000 NVE steps in
+    # both precisions: energies every 100 steps side by side
+    runs = {}
+    for name, prec, tau in (("nvt_fp64", "fp64", 0.1), ("nve_fp32c", "fp32c", 0.0), ("nve_fp64", "fp64", 0.0)):
+        h = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=1001, seed=77, precision=prec, tau_T=tau), device=dev.index)
+        h.set_state(tq, tx, tv)
+        es = []
+        for c in range(10):
+            h.step(100)
+            en = h.energies()
+            es.append(en["U_near"] + en["U_far"] - en["U_self"] + en["U_wca"] + en["K"])
+        h.close()
+        runs[name] = es
+    e32 = [r["E_total"] for r in rows]
+    energy = {
+        "nvt_fp32c_E_every_100_steps": e32, "nvt_fp64_E_every_100_steps": runs["nvt_fp64"],
+        "nvt_max_rel_E_diff_fp32c_vs_fp64": max(abs(a - b) / abs(b) for a, b in zip(e32, runs["nvt_fp64"])),
+        "nvt_rel_E_change_steps_100_to_1000": (e32[-1] - e32[0]) / abs(e32[0]),
+        "nve_fp32c_E_every_100_steps": runs["nve_fp32c"], "nve_fp64_E_every_100_steps": runs["nve_fp64"],
+        "nve_max_rel_E_diff_fp32c_vs_fp64": max(abs(a - b) / abs(b) for a, b in
+                                                zip(runs["nve_fp32c"], runs["nve_fp64"])),
+        "nve_note": "without a thermostat the random-batch force noise heats the system (the method is "
+                    "analysed under a thermostat); both precisions follow the same energies"}
+    b = int(1.1 / (L / 512))
+    out["electrolyte_N64000_fp32c_nvt"] = {"steps": 1000, "ms_per_step": t_steps / 1000,
+                                           "value": N / (t_steps / 1000 / 1e3), "every_100_steps": rows,
+                                           "rdf_contact_peak": {"++": float(gr[0, b - 3:b + 6].max()),
+                                                                "+-": float(gr[1, b - 3:b + 6].max())},
+                                           "energy": energy}
     return out
 
 
@@ -812,6 +936,26 @@ def cpu_baseline(N, L, P, q, x, v):
             "one_core": {"value": ns / dt1, "unit": "particle-steps/s", "cores": 1, "seconds": dt1,
                          "sample": f"1 full step of a {ns}-particle sample at the same density and P={P}"}}
     return base, m, f_o, e_o
+
+
+def cpu_baseline_small(q, x, v, L, P, steps, n_chains, chain_len):
+    """The FP64 oracle on the 1,000-ion electrolyte: `steps` velocity-Verlet
+    steps from the initial state on the oracle's own sampling of the
+    k-sequence for the GPU context's chain layout, timed on the host cores.
+    Returns the baseline record, that sequence and the final positions and
+    forces."""
+    import oracle as O
+    sog = O.SOG.solve(1.48783512395703226, 3.0, 232)
+    sog = O.SOG(sog.b, sog.sigma, sog.omega0, 36)
+    s = O.System((L,) * 3, sog, 3.0, 1.0, 1.0, 1.0)
+    ks = O.kseq(sog, s.L, seed=7, n_chains=n_chains, chain_len=chain_len)
+    t0 = time.perf_counter()
+    xo, _, fo, _ = O.md(s, q, x, v, s.S(), P, ks, steps, 0.001)
+    dt = time.perf_counter() - t0
+    base = {"value": len(q) * steps / dt, "unit": "particle-steps/s", "cores": O.num_threads(),
+            "kind": "oracle", "sample": f"initial force + {steps} FP64 steps of the {len(q)}-ion system, P={P}",
+            "seconds": dt}
+    return base, ks, xo, fo
 
 
 def run_reference(args, rank, world, sample=65536):
