@@ -221,9 +221,11 @@ def roofline_for(name, launches, ms_total, N, L, P, rc, meas, hbm_gbs, lists=Fal
         return out
     if name.startswith("near"):
         # FP32 instruction-equivalents: 8 per candidate distance test, 50 per
-        # pair inside r_c (MUFU ops counted once).  Candidates: the particles
-        # within r_c + skin of the neighbour-list method (skin = r_c / 10), or
-        # the 27-cell stencil when the step runs without lists
+        # pair inside r_c with the pair energies, 36 without them (the list
+        # force leaves them out on every step but the last of a call; MUFU
+        # ops counted once).  Candidates: the particles within r_c + skin of
+        # the neighbour-list method (skin = r_c / 10), or the 27-cell stencil
+        # when the step runs without lists
         pairs = 4.0 / 3.0 * math.pi * rc ** 3 * N / L ** 3
         if lists:
             cand = 4.0 / 3.0 * math.pi * (1.1 * rc) ** 3 * N / L ** 3
@@ -231,12 +233,15 @@ def roofline_for(name, launches, ms_total, N, L, P, rc, meas, hbm_gbs, lists=Fal
         else:
             cand = 27.0 * N / math.floor(L / rc) ** 3
             basis = "candidate test over the 27-cell stencil"
-        ops = N * (8.0 * cand + 50.0 * pairs)
+        per_pair = 36.0 if lists else 50.0
+        ops = N * (8.0 * cand + per_pair * pairs)
         achieved = ops / t / 1e12
         peak = meas["fma32_per_s"] / 1e12
         out.update(bound="alu", achieved=achieved, peak=peak, unit="Top/s", frac=achieved / peak,
                    peak_basis="measured FP32 FMA issue rate (rbsog_measure_peaks); work = 8 FP32 ops per "
-                              + basis + " + 50 per pair within r_c")
+                              + basis + f" + {per_pair:.0f} per pair within r_c"
+                              + (" (forces only: the pair energies are left out on all steps but the last "
+                                 "of a call)" if lists else ""))
         return out
     achieved = N * 64 / t / 1e9
     out.update(bound="hbm", achieved=achieved, peak=hbm_gbs, unit="GB/s", frac=achieved / hbm_gbs)

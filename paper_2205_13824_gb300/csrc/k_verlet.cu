@@ -33,6 +33,7 @@
 //               combined FP32 table; force and the two energies per particle;
 //   list_clear  resets the rebuild flags after a build.
 #include <cmath>
+#include <type_traits>
 
 #include "rbsog_kernels.cuh"
 
@@ -246,6 +247,10 @@ __global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv
 // energy) from a table indexed by the low exponent bits and 8 high mantissa
 // bits of the FP32 r^2, linearly interpolated by the remaining 15 mantissa
 // bits (entries: value at the bin start and change over the bin).
+//
+// energy = 0: the two pair energies are left out (written as zero) except in
+// systems taking their last budgeted step; the force arithmetic is the same
+// instructions either way, so the forces do not depend on the flag.
 template <bool CORESHELL>
 __global__ void __launch_bounds__(kNearThreads, CORESHELL ? 4 : 5) k_near_list(const BatchView bv, const float ltab_scale,
                                                             const float ltab_h, const float4 *__restrict__ ltab,
@@ -253,10 +258,11 @@ __global__ void __launch_bounds__(kNearThreads, CORESHELL ? 4 : 5) k_near_list(c
                                                             const int32_t *__restrict__ nbr_list,
                                                             const int32_t *__restrict__ nbr_cnt,
                                                             const int32_t *__restrict__ list_perm,
-                                                            double4_32a *__restrict__ fnear) {
+                                                            double4_32a *__restrict__ fnear, const int energy) {
     extern __shared__ __align__(16) float4 s_tab[];
     const int2 w = bv.pblk[blockIdx.x];
     if (bv.remaining && bv.remaining[w.x] == 0) return;
+    const bool want_e = energy != 0 || (bv.remaining && bv.remaining[w.x] == 1);
     // consecutive threads fill consecutive 16-byte slots (no bank conflicts)
     if (CORESHELL) {
         for (int t = threadIdx.x; t < cs.n_tab; t += kNearThreads) s_tab[t] = ltab[t];
@@ -278,88 +284,99 @@ __global__ void __launch_bounds__(kNearThreads, CORESHELL ? 4 : 5) k_near_list(c
     const float tscale = ltab_scale, mh = -ltab_h;
     const int cnt = min(nbr_cnt[s], bv.list_cap);
     constexpr int64_t stride = 32;
-    float fx = 0.f, fy = 0.f, fz = 0.f, un = 0.f, uw = 0.f;
-    // candidates in groups of four: four list words, then four positions,
-    // are in flight together (the loads, not the arithmetic, set the pace)
-    auto pair = [&](const uint4 &pj) {
-        const float dx = offset_f(pi.x, pj.x, fsx), dy = offset_f(pi.y, pj.y, fsy), dz = offset_f(pi.z, pj.z, fsz);
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        if (r2 < rc2) {
-            const float qq = qi * __uint_as_float(pj.w);
-            float g, inv_r2;
-            if (CORESHELL) {
-                if (r2 < cs.rin2) {
-                    float gs = cs.a[kCsQ - 1], fs = cs.b[kCsQ];
-#pragma unroll
-                    for (int i = kCsQ - 2; i >= 0; --i) gs = fmaf(gs, r2, cs.a[i]);
-#pragma unroll
-                    for (int i = kCsQ - 1; i >= 0; --i) fs = fmaf(fs, r2, cs.b[i]);
+    // the step without energies and the step with them: one instantiation of
+    // the loop each, chosen per block
+    auto run = [&](auto e_tag) {
+        constexpr bool E = decltype(e_tag)::value;
+        float fx = 0.f, fy = 0.f, fz = 0.f, un = 0.f, uw = 0.f;
+        // candidates in groups of four: four list words, then four positions,
+        // are in flight together (the loads, not the arithmetic, set the pace)
+        auto pair = [&](const uint4 &pj) {
+            const float dx = offset_f(pi.x, pj.x, fsx), dy = offset_f(pi.y, pj.y, fsy), dz = offset_f(pi.z, pj.z, fsz);
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (r2 < rc2) {
+                const float qq = qi * __uint_as_float(pj.w);
+                float g, inv_r2;
+                if (CORESHELL) {
+                    if (r2 < cs.rin2) {
+                        float gs = cs.a[kCsQ - 1], fs = cs.b[kCsQ];
+    #pragma unroll
+                        for (int i = kCsQ - 2; i >= 0; --i) gs = fmaf(gs, r2, cs.a[i]);
+                        if constexpr (E) {
+    #pragma unroll
+                            for (int i = kCsQ - 1; i >= 0; --i) fs = fmaf(fs, r2, cs.b[i]);
+                        }
+                        const float inv_r = rsqrtf(r2);
+                        inv_r2 = inv_r * inv_r;
+                        g = qq * (inv_r2 * inv_r - 2.0f * gs);
+                        if constexpr (E) un += 0.5f * qq * (inv_r - fs);
+                    } else {
+                        const uint32_t bits = __float_as_uint(r2);
+                        const int idx = (int)((((bits >> 23) & cs.emask) << kCsManBits) |
+                                              ((bits >> (23 - kCsManBits)) & ((1u << kCsManBits) - 1u)));
+                        const float fr = (float)(bits & ((1u << (23 - kCsManBits)) - 1u)) *
+                                         (1.0f / (float)(1u << (23 - kCsManBits)));
+                        const float4 e = tab[idx];                 // (g0, dg, n0, dn) of the bin
+                        g = qq * fmaf(fr, e.y, e.x);
+                        if constexpr (E) un += 0.5f * qq * fmaf(fr, e.w, e.z);
+                        inv_r2 = r2 < wrc2 ? __frcp_rn(r2) : 0.f;
+                    }
+                } else {
+                    const float x = r2 * tscale;
+                    const int kt = min((int)x, kLTabN - 1);
+                    const float sx = x - (float)kt;
+                    const float4 e = tab[kt * kTabCopies];      // (g0, g1, g2, F at the interval start)
+                    const float gs = fmaf(fmaf(e.z, sx, e.y), sx, e.x);
                     const float inv_r = rsqrtf(r2);
                     inv_r2 = inv_r * inv_r;
                     g = qq * (inv_r2 * inv_r - 2.0f * gs);
-                    un += 0.5f * qq * (inv_r - fs);
-                } else {
-                    const uint32_t bits = __float_as_uint(r2);
-                    const int idx = (int)((((bits >> 23) & cs.emask) << kCsManBits) |
-                                          ((bits >> (23 - kCsManBits)) & ((1u << kCsManBits) - 1u)));
-                    const float fr = (float)(bits & ((1u << (23 - kCsManBits)) - 1u)) *
-                                     (1.0f / (float)(1u << (23 - kCsManBits)));
-                    const float4 e = tab[idx];                 // (g0, dg, n0, dn) of the bin
-                    g = qq * fmaf(fr, e.y, e.x);
-                    un += 0.5f * qq * fmaf(fr, e.w, e.z);
-                    inv_r2 = r2 < wrc2 ? __frcp_rn(r2) : 0.f;
+                    if constexpr (E) {
+                        const float gi = fmaf(fmaf(e.z * (1.0f / 3.0f), sx, 0.5f * e.y), sx, e.x);   // (1/s) int_0^s G
+                        const float fs = fmaf(mh * sx, gi, e.w);
+                        un += 0.5f * qq * (inv_r - fs);
+                    }
                 }
-            } else {
-                const float x = r2 * tscale;
-                const int kt = min((int)x, kLTabN - 1);
-                const float sx = x - (float)kt;
-                const float4 e = tab[kt * kTabCopies];      // (g0, g1, g2, F at the interval start)
-                const float gs = fmaf(fmaf(e.z, sx, e.y), sx, e.x);
-                const float gi = fmaf(fmaf(e.z * (1.0f / 3.0f), sx, 0.5f * e.y), sx, e.x);   // (1/s) int_0^s G
-                const float fs = fmaf(mh * sx, gi, e.w);
-                const float inv_r = rsqrtf(r2);
-                inv_r2 = inv_r * inv_r;
-                g = qq * (inv_r2 * inv_r - 2.0f * gs);
-                un += 0.5f * qq * (inv_r - fs);
+                if (r2 < wrc2) {
+                    // WCA from 1/r^2 (no divisions: this branch runs for some
+                    // lane of most warps, so its length is paid by all lanes)
+                    const float sr2 = ws2 * inv_r2;
+                    const float sr6 = sr2 * sr2 * sr2;
+                    g += 24.0f * weps * (2.0f * sr6 * sr6 - sr6) * inv_r2;
+                    if constexpr (E) uw += 0.5f * (4.0f * weps * (sr6 * sr6 - sr6) + weps);
+                }
+                fx = fmaf(g, dx, fx);
+                fy = fmaf(g, dy, fy);
+                fz = fmaf(g, dz, fz);
             }
-            if (r2 < wrc2) {
-                // WCA from 1/r^2 (no divisions: this branch runs for some
-                // lane of most warps, so its length is paid by all lanes)
-                const float sr2 = ws2 * inv_r2;
-                const float sr6 = sr2 * sr2 * sr2;
-                g += 24.0f * weps * (2.0f * sr6 * sr6 - sr6) * inv_r2;
-                uw += 0.5f * (4.0f * weps * (sr6 * sr6 - sr6) + weps);
+        };
+        const int32_t *lp = nbr_list + slot_index(s, 0, bv.list_cap);
+        int k = 0;
+        if (cnt >= 4) {
+            // the next group's four list words (streamed from DRAM) are loaded
+            // before this group's pairs are evaluated, so their latency overlaps
+            // the arithmetic; only the position gathers (L1/L2) stay exposed
+            int j0 = lp[0], j1 = lp[stride], j2 = lp[2 * stride], j3 = lp[3 * stride];
+            for (; k + 4 <= cnt; k += 4) {
+                const uint4 p0 = lpos[j0], p1 = lpos[j1], p2 = lpos[j2], p3 = lpos[j3];
+                if (k + 8 <= cnt) {
+                    j0 = lp[(int64_t)(k + 4) * stride];
+                    j1 = lp[(int64_t)(k + 5) * stride];
+                    j2 = lp[(int64_t)(k + 6) * stride];
+                    j3 = lp[(int64_t)(k + 7) * stride];
+                }
+                pair(p0);
+                pair(p1);
+                pair(p2);
+                pair(p3);
             }
-            fx = fmaf(g, dx, fx);
-            fy = fmaf(g, dy, fy);
-            fz = fmaf(g, dz, fz);
         }
+        for (; k < cnt; ++k) pair(lpos[lp[(int64_t)k * stride]]);
+        // the two energies travel in the w slot as a pair of floats
+        fnear[list_perm[s]] = make_double4_32a((double)fx, (double)fy, (double)fz,
+                                               __hiloint2double(__float_as_int(un), __float_as_int(uw)));
     };
-    const int32_t *lp = nbr_list + slot_index(s, 0, bv.list_cap);
-    int k = 0;
-    if (cnt >= 4) {
-        // the next group's four list words (streamed from DRAM) are loaded
-        // before this group's pairs are evaluated, so their latency overlaps
-        // the arithmetic; only the position gathers (L1/L2) stay exposed
-        int j0 = lp[0], j1 = lp[stride], j2 = lp[2 * stride], j3 = lp[3 * stride];
-        for (; k + 4 <= cnt; k += 4) {
-            const uint4 p0 = lpos[j0], p1 = lpos[j1], p2 = lpos[j2], p3 = lpos[j3];
-            if (k + 8 <= cnt) {
-                j0 = lp[(int64_t)(k + 4) * stride];
-                j1 = lp[(int64_t)(k + 5) * stride];
-                j2 = lp[(int64_t)(k + 6) * stride];
-                j3 = lp[(int64_t)(k + 7) * stride];
-            }
-            pair(p0);
-            pair(p1);
-            pair(p2);
-            pair(p3);
-        }
-    }
-    for (; k < cnt; ++k) pair(lpos[lp[(int64_t)k * stride]]);
-    // the two energies travel in the w slot as a pair of floats
-    fnear[list_perm[s]] = make_double4_32a((double)fx, (double)fy, (double)fz,
-                                           __hiloint2double(__float_as_int(un), __float_as_int(uw)));
+    if (want_e) run(std::true_type{});
+    else run(std::false_type{});
 }
 
 // One running system's lists, reference positions and flag moved from one
@@ -456,20 +473,20 @@ cudaError_t launch_list_move(int64_t n, int64_t old_off, int64_t new_off, int ol
 
 cudaError_t launch_near_list(const BatchView &bv, const NearSog &sog, const float4 *ltab, const int32_t *nbr_list,
                              const int32_t *nbr_cnt, const int32_t *list_perm, double4_32a *fnear, cudaStream_t st,
-                             const Prof *prof, const CoreShellDev *cs, const float4 *cstab) {
+                             const Prof *prof, const CoreShellDev *cs, const float4 *cstab, bool energy) {
     if (cs) {
         ProfScope ps(prof, "near_fp32c_coreshell");
         const size_t sm = sizeof(float4) * (size_t)cs->n_tab;
         cudaError_t e = cudaFuncSetAttribute(k_near_list<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         k_near_list<true><<<bv.n_pblk, kNearThreads, sm, st>>>(bv, 0.f, 0.f, cstab, *cs, nbr_list, nbr_cnt,
-                                                               list_perm, fnear);
+                                                               list_perm, fnear, energy ? 1 : 0);
         return cudaGetLastError();
     }
     ProfScope ps(prof, "near_fp32c");
     const CoreShellDev none{};
     k_near_list<false><<<bv.n_pblk, kNearThreads, sizeof(float4) * kLTabN * kTabCopies, st>>>(
-        bv, sog.ltab_scale, sog.ltab_h, ltab, none, nbr_list, nbr_cnt, list_perm, fnear);
+        bv, sog.ltab_scale, sog.ltab_h, ltab, none, nbr_list, nbr_cnt, list_perm, fnear, energy ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -71,6 +71,7 @@ struct rbsog_ctx {
     cudaEvent_t ev_q = nullptr, ev_x = nullptr, ev_io = nullptr;   // rbsog_step_io
     cudaStream_t io = nullptr;                                     // rbsog_step_io downloads
     cudaGraphExec_t graph_tail = nullptr;   // a step without its kick-drift (rbsog_step_io)
+    cudaGraphExec_t graph_e = nullptr;      // a whole step with energies (the last of a call)
     cudaGraphExec_t graph_fused = nullptr;  // a step without its kick-drift whose scatter runs
                                             // the next step's kick-drift (rbsog_batch_step)
     std::string err;
@@ -153,7 +154,7 @@ struct rbsog_ctx {
     int32_t *h_err = nullptr;
     int64_t *h_i64 = nullptr;
 
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;  // a whole step without energies
     bool capturing = false;           // enqueue_step is being captured into the step graph
     cudaStream_t side = nullptr;      // captures the bodies of conditional graph nodes
     cudaStream_t far = nullptr;       // the rho(k) sweep and combine, beside the near field
@@ -625,9 +626,12 @@ BatchView view(rbsog_ctx *c, const int4 *m_explicit = nullptr, int32_t P = -1) {
 // adds to the force after the scatter.
 // fuse_drift (with fuse_kick, neighbour lists): the scatter also runs the
 // next step's half kick and drift.
+// energy = false (neighbour lists): the list force leaves the pair energies
+// out, for steps whose energies nobody reads (not the last step of a call;
+// a system on its last budgeted step still gets them).
 rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_sorted,
                             double4_32a *force_out = nullptr, bool packed = false, bool fuse_kick = false,
-                            bool fuse_drift = false) {
+                            bool fuse_drift = false, bool energy = true) {
     const Prof *pf = prof_of(ctx);
     const int prec = ctx->precision;
     double4_32a *kv = fuse_kick ? ctx->vel : nullptr;
@@ -701,7 +705,7 @@ rbsog_status enqueue_forces(rbsog_ctx *ctx, const BatchView &bv, int32_t *nbr_so
             }
         }
         CK(launch_near_list(bv, ctx->nsog, ctx->d_ltab, ctx->nbr_list, ctx->nbr_cnt, ctx->list_perm, ctx->fnear,
-                            ctx->st, pf, ctx->use_cs ? &ctx->cs : nullptr, ctx->d_cstab));
+                            ctx->st, pf, ctx->use_cs ? &ctx->cs : nullptr, ctx->d_cstab, energy));
         if (fork) {
             CK(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
         } else {
@@ -745,12 +749,13 @@ rbsog_status enqueue_kick_drift(rbsog_ctx *ctx) {
 }
 
 // drift_next: the step's scatter also runs the next step's kick-drift
-// (drift_fusable only).
-rbsog_status enqueue_step_tail(rbsog_ctx *ctx, bool drift_next = false) {
+// (drift_fusable only).  energy: the step's energies are computed (the last
+// step of a call); other steps may leave the pair energies out.
+rbsog_status enqueue_step_tail(rbsog_ctx *ctx, bool drift_next = false, bool energy = true) {
     const Prof *pf = prof_of(ctx);
     const BatchView bv = view(ctx);
     const bool fused = ctx->precision == RBSOG_FP32C && !ctx->any_boundary;
-    rbsog_status s = enqueue_forces(ctx, bv, nullptr, nullptr, ctx->use_list, fused, drift_next && fused);
+    rbsog_status s = enqueue_forces(ctx, bv, nullptr, nullptr, ctx->use_list, fused, drift_next && fused, energy);
     if (s != RBSOG_OK) return s;
     if (!fused) CK(launch_kick(bv, ctx->vel, ctx->force, ctx->kpart, ctx->st, pf));
     CK(launch_finalize(bv, ctx->epart, ctx->rho, ctx->kpart, 1, ctx->energy, 1, ctx->st, pf));
@@ -761,10 +766,10 @@ rbsog_status enqueue_step_tail(rbsog_ctx *ctx, bool drift_next = false) {
     return RBSOG_OK;
 }
 
-rbsog_status enqueue_step(rbsog_ctx *ctx) {
+rbsog_status enqueue_step(rbsog_ctx *ctx, bool energy = true) {
     rbsog_status s = enqueue_kick_drift(ctx);
     if (s != RBSOG_OK) return s;
-    return enqueue_step_tail(ctx);
+    return enqueue_step_tail(ctx, false, energy);
 }
 
 // The scatter can run the next step's kick-drift when nothing happens to the
@@ -781,14 +786,19 @@ bool drift_fusable(const rbsog_ctx *ctx) {
 
 void drop_graph(rbsog_ctx *c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph_e) cudaGraphExecDestroy(c->graph_e);
     if (c->graph_tail) cudaGraphExecDestroy(c->graph_tail);
     if (c->graph_fused) cudaGraphExecDestroy(c->graph_fused);
     c->graph = nullptr;
+    c->graph_e = nullptr;
     c->graph_tail = nullptr;
     c->graph_fused = nullptr;
 }
 
-enum class StepPart { whole, tail, tail_drift };
+// whole: a step without energies; whole_e: a step with them; tail: a step
+// without its kick-drift, with energies; tail_drift: a step without its
+// kick-drift whose scatter runs the next one's, without energies.
+enum class StepPart { whole, whole_e, tail, tail_drift };
 
 // Captures a whole step, its tail, or its tail with the next step's
 // kick-drift into *out (once).
@@ -797,8 +807,10 @@ rbsog_status capture_step(rbsog_ctx *ctx, StepPart part, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
     ctx->capturing = true;
-    rbsog_status es = part == StepPart::whole ? enqueue_step(ctx)
-                                              : enqueue_step_tail(ctx, part == StepPart::tail_drift);
+    rbsog_status es = part == StepPart::whole     ? enqueue_step(ctx, false)
+                      : part == StepPart::whole_e ? enqueue_step(ctx, true)
+                                                  : enqueue_step_tail(ctx, part == StepPart::tail_drift,
+                                                                      part == StepPart::tail);
     ctx->capturing = false;
     cudaError_t ce = cudaStreamEndCapture(ctx->st, &g);
     if (es != RBSOG_OK) {
@@ -1657,7 +1669,7 @@ rbsog_status rbsog_batch_step(rbsog_batch *ctx, int64_t nsteps) {
     if (es != RBSOG_OK) return es;
     if (ctx->profiling) {
         for (int64_t t = 0; t < nsteps; ++t) {
-            es = enqueue_step(ctx);
+            es = enqueue_step(ctx, t + 1 == nsteps);
             if (es != RBSOG_OK) return es;
         }
     } else if (nsteps >= 2 && drift_fusable(ctx)) {
@@ -1672,9 +1684,15 @@ rbsog_status rbsog_batch_step(rbsog_batch *ctx, int64_t nsteps) {
         for (int64_t t = 0; t + 1 < nsteps; ++t) CK(cudaGraphLaunch(ctx->graph_fused, ctx->st));
         CK(cudaGraphLaunch(ctx->graph_tail, ctx->st));
     } else if (nsteps > 0) {
-        es = capture_step(ctx, StepPart::whole, &ctx->graph);
+        // steps without energies, then the last one with them
+        if (nsteps > 1) {
+            es = capture_step(ctx, StepPart::whole, &ctx->graph);
+            if (es != RBSOG_OK) return es;
+        }
+        es = capture_step(ctx, StepPart::whole_e, &ctx->graph_e);
         if (es != RBSOG_OK) return es;
-        for (int64_t t = 0; t < nsteps; ++t) CK(cudaGraphLaunch(ctx->graph, ctx->st));
+        for (int64_t t = 0; t + 1 < nsteps; ++t) CK(cudaGraphLaunch(ctx->graph, ctx->st));
+        CK(cudaGraphLaunch(ctx->graph_e, ctx->st));
     }
     for (int s = 0; s < ctx->n_sys; ++s) {
         const int64_t run = ctx->use_budget ? std::min(nsteps, ctx->remaining_host[s]) : nsteps;
@@ -1756,7 +1774,7 @@ rbsog_status rbsog_step_io(rbsog_ctx *ctx, const double *q, const double *x, con
     // tail while the new positions are copied out on the io stream
     if (ctx->profiling) {
         for (int64_t t = 0; t + 1 < nsteps; ++t) {
-            es = enqueue_step(ctx);
+            es = enqueue_step(ctx, false);
             if (es != RBSOG_OK) return es;
         }
     } else if (nsteps > 1) {

@@ -387,10 +387,12 @@ struct CoreShellDev {
     int32_t n_tab;               // 2^(b_exp + kCsManBits)
 };
 // cs == nullptr: the combined table (ltab); else the core-shell kernel with
-// its table cstab.
+// its table cstab.  energy = false leaves the pair energies out (zero) except
+// in systems on their last budgeted step.
 cudaError_t launch_near_list(const BatchView &bv, const NearSog &sog, const float4 *ltab, const int32_t *nbr_list,
                              const int32_t *nbr_cnt, const int32_t *list_perm, double4_32a *fnear, cudaStream_t st,
-                             const Prof *prof, const CoreShellDev *cs = nullptr, const float4 *cstab = nullptr);
+                             const Prof *prof, const CoreShellDev *cs = nullptr, const float4 *cstab = nullptr,
+                             bool energy = true);
 
 // ---- far field (k_far.cu) -----------------------------------------------------
 // tile_override > 0 replaces the default particles-per-tile rule (tunable)
