@@ -45,6 +45,7 @@ constexpr int kMaxGroupB = 16;
 constexpr int kMaxStagedB = 9 * (kMaxGroupB + 2);
 constexpr int kNearThreads = kParticleBlock;
 constexpr int kTabCopies = 8;                  // shared-memory copies of the tables (bank groups)
+constexpr int kNearGroup = 4;                  // list candidates whose loads are in flight together
 
 __device__ __forceinline__ int wrap_cell_b(int c, int n) {
     return c < 0 ? c + n : (c >= n ? c - n : c);
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv
 // systems taking their last budgeted step; the force arithmetic is the same
 // instructions either way, so the forces do not depend on the flag.
 template <bool CORESHELL>
-__global__ void __launch_bounds__(kNearThreads, CORESHELL ? 4 : 5) k_near_list(const BatchView bv, const float ltab_scale,
+__global__ void __launch_bounds__(kNearThreads, 4) k_near_list(const BatchView bv, const float ltab_scale,
                                                             const float ltab_h, const float4 *__restrict__ ltab,
                                                             const __grid_constant__ CoreShellDev cs,
                                                             const int32_t *__restrict__ nbr_list,
@@ -289,8 +290,9 @@ __global__ void __launch_bounds__(kNearThreads, CORESHELL ? 4 : 5) k_near_list(c
     auto run = [&](auto e_tag) {
         constexpr bool E = decltype(e_tag)::value;
         float fx = 0.f, fy = 0.f, fz = 0.f, un = 0.f, uw = 0.f;
-        // candidates in groups of four: four list words, then four positions,
-        // are in flight together (the loads, not the arithmetic, set the pace)
+        // candidates in groups of kNearGroup: their list words, then their
+        // positions, are in flight together (the loads, not the arithmetic,
+        // set the pace)
         auto pair = [&](const uint4 &pj) {
             const float dx = offset_f(pi.x, pj.x, fsx), dy = offset_f(pi.y, pj.y, fsy), dz = offset_f(pi.z, pj.z, fsz);
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -300,10 +302,10 @@ __global__ void __launch_bounds__(kNearThreads, CORESHELL ? 4 : 5) k_near_list(c
                 if (CORESHELL) {
                     if (r2 < cs.rin2) {
                         float gs = cs.a[kCsQ - 1], fs = cs.b[kCsQ];
-    #pragma unroll
+#pragma unroll
                         for (int i = kCsQ - 2; i >= 0; --i) gs = fmaf(gs, r2, cs.a[i]);
                         if constexpr (E) {
-    #pragma unroll
+#pragma unroll
                             for (int i = kCsQ - 1; i >= 0; --i) fs = fmaf(fs, r2, cs.b[i]);
                         }
                         const float inv_r = rsqrtf(r2);
@@ -351,23 +353,24 @@ __global__ void __launch_bounds__(kNearThreads, CORESHELL ? 4 : 5) k_near_list(c
         };
         const int32_t *lp = nbr_list + slot_index(s, 0, bv.list_cap);
         int k = 0;
-        if (cnt >= 4) {
-            // the next group's four list words (streamed from DRAM) are loaded
-            // before this group's pairs are evaluated, so their latency overlaps
-            // the arithmetic; only the position gathers (L1/L2) stay exposed
-            int j0 = lp[0], j1 = lp[stride], j2 = lp[2 * stride], j3 = lp[3 * stride];
-            for (; k + 4 <= cnt; k += 4) {
-                const uint4 p0 = lpos[j0], p1 = lpos[j1], p2 = lpos[j2], p3 = lpos[j3];
-                if (k + 8 <= cnt) {
-                    j0 = lp[(int64_t)(k + 4) * stride];
-                    j1 = lp[(int64_t)(k + 5) * stride];
-                    j2 = lp[(int64_t)(k + 6) * stride];
-                    j3 = lp[(int64_t)(k + 7) * stride];
+        if (cnt >= kNearGroup) {
+            // the next group's list words (streamed from DRAM) are loaded
+            // before this group's pairs are evaluated, so their latency
+            // overlaps the arithmetic; only the position gathers (L1/L2) stay
+            // exposed
+            int j[kNearGroup];
+#pragma unroll
+            for (int u = 0; u < kNearGroup; ++u) j[u] = lp[u * stride];
+            for (; k + kNearGroup <= cnt; k += kNearGroup) {
+                uint4 p[kNearGroup];
+#pragma unroll
+                for (int u = 0; u < kNearGroup; ++u) p[u] = lpos[j[u]];
+                if (k + 2 * kNearGroup <= cnt) {
+#pragma unroll
+                    for (int u = 0; u < kNearGroup; ++u) j[u] = lp[(int64_t)(k + kNearGroup + u) * stride];
                 }
-                pair(p0);
-                pair(p1);
-                pair(p2);
-                pair(p3);
+#pragma unroll
+                for (int u = 0; u < kNearGroup; ++u) pair(p[u]);
             }
         }
         for (; k < cnt; ++k) pair(lpos[lp[(int64_t)k * stride]]);
