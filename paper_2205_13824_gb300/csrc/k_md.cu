@@ -310,6 +310,15 @@ __global__ void __launch_bounds__(kThreads) k_unsort(int64_t n, int64_t off, con
     out[perm[off + s] - off] = sorted[off + s];
 }
 
+__global__ void k_finalize_counters(BatchView bv, int64_t advance) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= bv.n_sys) return;
+    if (bv.force_mask && !bv.force_mask[s]) return;
+    if (bv.remaining && bv.remaining[s] == 0) return;
+    bv.step[s] += 1;
+    bv.cursor[s] += advance;
+}
+
 __global__ void k_step_done(int32_t n_sys, int64_t *__restrict__ remaining) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < n_sys && remaining[s] > 0) remaining[s] -= 1;
@@ -344,6 +353,12 @@ cudaError_t launch_finalize(const BatchView &bv, const double2 *epart, const dou
     ProfScope ps(prof, "finalize");
     k_finalize<<<bv.n_sys * kFinChunks, kFinThreads, 0, st>>>(bv, epart, rho, kpart, with_kinetic, energy,
                                                                advance);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_counters(const BatchView &bv, int64_t advance, cudaStream_t st, const Prof *prof) {
+    ProfScope ps(prof, "finalize");
+    k_finalize_counters<<<(unsigned)((bv.n_sys + 127) / 128), 128, 0, st>>>(bv, advance);
     return cudaGetLastError();
 }
 

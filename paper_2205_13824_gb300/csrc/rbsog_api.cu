@@ -759,9 +759,14 @@ rbsog_status enqueue_step_tail(rbsog_ctx *ctx, bool drift_next = false, bool ene
     rbsog_status s = enqueue_forces(ctx, bv, nullptr, nullptr, ctx->use_list, fused, drift_next && fused, energy);
     if (s != RBSOG_OK) return s;
     if (!fused) CK(launch_kick(bv, ctx->vel, ctx->force, ctx->kpart, ctx->st, pf));
-    CK(launch_finalize(bv, ctx->epart, ctx->rho, ctx->kpart, 1, ctx->energy, 1, ctx->st, pf));
     bool thermo = false;
     for (auto &pp : ctx->p) thermo = thermo || (pp.tau_T > 0.0 && pp.thermostat != 1);
+    // the sums of finalize feed the thermostats and the reported energies;
+    // a step with neither only advances the counters
+    if (energy || thermo || ctx->use_budget)
+        CK(launch_finalize(bv, ctx->epart, ctx->rho, ctx->kpart, 1, ctx->energy, 1, ctx->st, pf));
+    else
+        CK(launch_finalize_counters(bv, 1, ctx->st, pf));
     if (thermo) CK(launch_rescale(bv, ctx->vel, ctx->energy, ctx->st, pf));
     CK(launch_step_done(bv, ctx->st, pf));
     return RBSOG_OK;

@@ -453,6 +453,10 @@ cudaError_t launch_kick(const BatchView &bv, double4_32a *vel, const double4_32a
 cudaError_t launch_finalize(const BatchView &bv, const double2 *epart, const double2 *rho, const double *kpart,
                             int with_kinetic, double *energy, int64_t advance, cudaStream_t st,
                             const Prof *prof);
+// A step whose energies and temperature nobody reads (no thermostat, no step
+// budgets, not the last step of a call): only the cursor advance and the
+// step count of finalize, one thread per system.
+cudaError_t launch_finalize_counters(const BatchView &bv, int64_t advance, cudaStream_t st, const Prof *prof);
 // ---- virial (k_virial.cu) ------------------------------------------------------
 // Configurational virial W[9] (row-major, symmetric) of system 0: near field
 // (+ WCA) from the cell list (start, perm, cell_of) and the FP64 positions,
