@@ -144,7 +144,8 @@ def electrolyte_state(N, L, seed):
 # workload, with the hash of the kernel source they were taken from
 PROFILE_OF = {"near": ("near_fp32c_lists_electrolyte_N1048576.md", "k_verlet.cu"),
               "rho_sweep": ("rho_sweep_fp32c_electrolyte_N1048576_P500.md", "k_far.cu"),
-              "far_scatter": ("far_scatter_fp32c_electrolyte_N1048576_P500.md", "k_far.cu")}
+              "far_scatter": ("far_scatter_fp32c_electrolyte_N1048576_P500.md", "k_far.cu"),
+              "list_build": ("list_build_fp32c_electrolyte_N1048576.md", "k_verlet.cu")}
 
 
 def profiled_traffic(kernel, N, P):
@@ -155,7 +156,7 @@ def profiled_traffic(kernel, N, P):
     for key, (fname, src) in PROFILE_OF.items():
         if not kernel.startswith(key):
             continue
-        if N != N_DEF or (key != "near" and P != P_DEF):
+        if N != N_DEF or (key not in ("near", "list_build") and P != P_DEF):
             return None
         try:
             txt = open(os.path.join(ROOT, "profiles", fname)).read()
