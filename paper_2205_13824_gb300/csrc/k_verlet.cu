@@ -46,6 +46,7 @@ constexpr int kMaxStagedB = 9 * (kMaxGroupB + 2);
 constexpr int kNearThreads = kParticleBlock;
 constexpr int kTabCopies = 8;                  // shared-memory copies of the tables (bank groups)
 constexpr int kNearGroup = 4;                  // list candidates whose loads are in flight together
+constexpr int kBuildGroup = 4;                 // list build: window candidates tested together
 
 __device__ __forceinline__ int wrap_cell_b(int c, int n) {
     return c < 0 ? c + n : (c >= n ? c - n : c);
@@ -157,6 +158,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv
         }
         int cnt = 0;
         bool over = false;
+        // slot k of this particle's list is lrow[32 k] (sliced layout)
+        int32_t *__restrict__ lrow = nbr_list + slot_index(active ? hi : hb, 0, lcap);
         for (int c0 = 0; c0 < total; c0 += cap) {
             const int c1 = min(c0 + cap, total);
             __syncthreads();
@@ -203,16 +206,26 @@ __global__ void __launch_bounds__(kBuildThreads) k_list_build(const BatchView bv
                     if (st[m - c0].x <= xr) a = m + 1; else e = m;
                 }
                 a = min(a, c1);
-                for (int t = lo; t < a; ++t) {
-                    const float4 pj = st[t - c0];
+                // candidates kBuildGroup at a time (independent loads and
+                // distance tests in flight), appended in window order
+                auto append = [&](const float4 &pj) {
                     const float dx = ix - pj.x, dy = iy - pj.y, dz = iz - pj.z;
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     if (r2 < rl2 && r2 > 0.f) {
-                        if (cnt < lcap) nbr_list[slot_index(hi, cnt, lcap)] = __float_as_int(pj.w);
+                        if (cnt < lcap) lrow[(int64_t)cnt * 32] = __float_as_int(pj.w);
                         else over = true;
                         ++cnt;
                     }
+                };
+                int t = lo;
+                for (; t + kBuildGroup <= a; t += kBuildGroup) {
+                    float4 p[kBuildGroup];
+#pragma unroll
+                    for (int u = 0; u < kBuildGroup; ++u) p[u] = st[t + u - c0];
+#pragma unroll
+                    for (int u = 0; u < kBuildGroup; ++u) append(p[u]);
                 }
+                for (; t < a; ++t) append(st[t - c0]);
             }
         }
         if (active) {

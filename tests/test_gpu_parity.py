@@ -355,8 +355,12 @@ def test_fp32c_neighbour_lists_over_rebuilds():
         assert rms_rel(fg.cpu().numpy(), fo) < 1e-4
         moved = np.abs(((xo - x) + L / 2) % L - L / 2).max()
         assert moved > 0.15 or N == 216        # beyond half the skin (0.15 at r_c = 3)
+        # the last step of a call computes the energies (the others leave the
+        # pair energies out): all of them match the oracle's last step
         e = g.energies()
-        assert e["U_near"] == pytest.approx(es[-1]["U_near"], rel=1e-4, abs=1e-3)
+        for k in ("U_near", "U_far", "U_wca", "K"):
+            assert e[k] == pytest.approx(es[-1][k], rel=1e-4, abs=1e-3), k
+        assert e["U_wca"] > 0.0
         g.close()
 
 
