@@ -1474,7 +1474,7 @@ rbsog_status rbsog_batch_autotune(rbsog_batch *ctx, int32_t reps, int32_t *chose
         }
         return RBSOG_OK;
     };
-    const int homes[] = {64, 96, 120, 160, 224};
+    const int homes[] = {64, 16, 32, 96, 120, 160, 224};
     const int tiles[] = {0, 256, 512, 1024, 2048};
     Tune best_t;
     float best_ms = 1e30f;
