@@ -621,6 +621,7 @@ def run_small_configs(dev):
         h = Pk.RBSOG(N, Pk.make_params(L, P, n_ksets=steps * (reps + 1) + 1, seed=7, precision=prec),
                      device=dev.index)
         h.set_state(*(torch.tensor(a, device=dev) for a in (q, x, v)))
+        B.rbsog_batch_autotune(h.ctx, 3)   # launch shapes for this size (state untouched)
         h.step(steps)
         torch.cuda.synchronize()
         e0.record(st)
@@ -634,12 +635,12 @@ def run_small_configs(dev):
     ms32 = steady_ms("fp32c")
     out["electrolyte_N1000_fp64"] = {
         "ms_per_step": ms, "value": N / (ms / 1e3), "unit": "particle-steps/s",
-        "timing": f"{reps} calls of {steps} steps each, after the first call",
+        "timing": f"{reps} calls of {steps} steps each, after autotuning and a first call",
         "vs_oracle_after_10_steps": dict(rel_errors(fg, fo), max_position_diff=float(np.abs(dx).max()),
                                          same_k_sequence=bool(np.array_equal(kseq_dev, ks[: len(kseq_dev)]))),
         "cpu_baseline": base,
         "fp32c": {"ms_per_step": ms32, "value": N / (ms32 / 1e3)},
-        "note": "the FP64 near field of 1,000 ions runs on 32 blocks of one active warp each: "
+        "note": "the FP64 near field of 1,000 ions runs on at most 64 blocks of one active warp each: "
                 "bound by the latency of this GPU's FP64 units, not by their rate"}
     # 64,000 ions, FP32C, 1,000 Berendsen steps; NVE drift
     N, L, P = 64000, 50.4, 200
