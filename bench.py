@@ -148,28 +148,30 @@ PROFILE_OF = {"near": ("near_fp32c_lists_electrolyte_N1048576.md", "k_verlet.cu"
               "list_build": ("list_build_fp32c_electrolyte_N1048576.md", "k_verlet.cu")}
 
 
-def profiled_traffic(kernel, N, P):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    summary is for another workload or the kernel source changed since."""
+def profiled_fields(kernel, N, P):
+    """(DRAM bytes per launch, limiter) from the committed ncu summary, or
+    (None, None) when the summary is for another workload or the kernel
+    source changed since."""
     import hashlib
     import re
     for key, (fname, src) in PROFILE_OF.items():
         if not kernel.startswith(key):
             continue
         if N != N_DEF or (key not in ("near", "list_build") and P != P_DEF):
-            return None
+            return None, None
         try:
             txt = open(os.path.join(ROOT, "profiles", fname)).read()
             cur = hashlib.sha256(open(os.path.join(ROOT, "paper_2205_13824_gb300", "csrc", src), "rb")
                                  .read()).hexdigest()[:16]
         except OSError:
-            return None
+            return None, None
         m = re.search(r"traffic_bytes_per_launch: (\d+)", txt)
         h = re.search(r"sha256 prefix `([0-9a-f]+)`", txt)
-        if m and h and h.group(1) == cur:
-            return int(m.group(1))
-        return None
-    return None
+        lim = re.search(r"`limiter: ([^`]+)`", txt)
+        if h and h.group(1) == cur:
+            return (int(m.group(1)) if m else None), (lim.group(1) + " (ncu)" if lim else None)
+        return None, None
+    return None, None
 
 
 def distinct_per_set(ks, P):
@@ -187,7 +189,10 @@ def roofline_for(name, launches, ms_total, N, L, P, rc, meas, hbm_gbs, lists=Fal
     frequencies per set the far-field kernels evaluate (the distinct runs of
     a folded set), P when None."""
     t = ms_total / launches / 1e3
-    out = {"kernel": name, "ms_per_launch": t * 1e3, "traffic": profiled_traffic(name, N, P)}
+    traffic, limiter = profiled_fields(name, N, P)
+    out = {"kernel": name, "ms_per_launch": t * 1e3, "traffic": traffic}
+    if limiter:
+        out["limiter"] = limiter
     if name.startswith(("rho_sweep", "far_scatter")):
         # one (particle, evaluated frequency) term = one sin + one cos on the MUFU pipe
         Pe = P if P_eval is None else P_eval
