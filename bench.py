@@ -645,8 +645,8 @@ def run_small_configs(dev):
                                          same_k_sequence=bool(np.array_equal(kseq_dev, ks[: len(kseq_dev)]))),
         "cpu_baseline": base,
         "fp32c": {"ms_per_step": ms32, "value": N / (ms32 / 1e3)},
-        "note": "the FP64 near field of 1,000 ions runs on at most 64 blocks of one active warp each: "
-                "bound by the latency of this GPU's FP64 units, not by their rate"}
+        "note": "the FP64 near field of 1,000 ions splits each block's cell-stencil rows over its four warps; "
+                "it stays bound by the latency of this GPU's FP64 units (64 blocks), not by their rate"}
     # 64,000 ions, FP32C, 1,000 Berendsen steps; NVE drift
     N, L, P = 64000, 50.4, 200
     q, x, v = I.electrolyte(N, L, seed=2022)

@@ -173,6 +173,9 @@ __global__ void __launch_bounds__(kThreads, PREC == 1 ? 6 : 4)
     __shared__ int s_hstart[kMaxGroup + 1];
     __shared__ float4 s_tab[ND < 0 ? 2 * kTabN : 1];   // Gaussian-sum tables (ND < 0)
     __shared__ uint16_t s_hord[WIN ? kMaxHome : 1];    // home particles in quadrant order (WIN)
+    // split (FP64, small systems): the row partials of the four warps
+    __shared__ double s_pf[PREC == 0 ? 3 * kThreads : 1];
+    __shared__ int s_pc[PREC == 0 ? kThreads : 1];
     extern __shared__ __align__(32) unsigned char smem_raw[];
     // disjoint regions: restrict lets the compiler move staged loads across
     // list stores
@@ -282,6 +285,13 @@ __global__ void __launch_bounds__(kThreads, PREC == 1 ? 6 : 4)
     }
 
     double e_near = 0.0, e_wca = 0.0;
+    // split (FP64 systems below kNearSplitMaxN particles, whose blocks hold
+    // too few home particles to keep four warps busy): every warp takes every
+    // run of 32 home particles, but only the rows r = wid, wid + 4, ...; the
+    // four row partials of a particle are added in warp order.  The order
+    // depends on the system alone (not on the block size), so a system's
+    // forces are the same bits alone or in a batch.
+    const bool split = PREC == 0 && desc.near_split != 0;
     // Staging: one chunk [c0, c1) of the staged region at a time (normally the
     // whole region fits); every warp then works through the home particles in
     // runs of 32 consecutive particles (one per lane).
@@ -309,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 1 ? 6 : 4)
             }
         }
         __syncthreads();
-        for (int rb = hb + 32 * wid; rb < he; rb += kThreads) {
+        for (int rb = hb + (split ? 0 : 32 * wid); rb < he; rb += split ? 32 : kThreads) {
             const int pidx = rb - hb + lane;
             const bool active = pidx < nhome;
             const int hi = active ? hb + (reord ? (int)s_hord[pidx] : pidx) : he;
@@ -464,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 1 ? 6 : 4)
                     }
                 }
             } else
-            for (int r = 0; r < 9; ++r) {
+            for (int r = split ? wid : 0; r < 9; r += split ? kThreads / 32 : 1) {
                 const int kb = r * w + cx_lo, ke = r * w + cx_hi + 3;   // staged cells [kb, ke)
                 const int lo = max(s_off[kb], c0), hi3 = min(s_off[ke], c1);
                 for (int tb = lo; tb < hi3; tb += kList) {
@@ -502,7 +512,25 @@ __global__ void __launch_bounds__(kThreads, PREC == 1 ? 6 : 4)
                 }
             }
             compute();
-            if (active) {
+            if (split) {
+                // the warps' row partials of the run's 32 particles, added in
+                // warp order by warp 0
+                s_pf[(wid * 3 + 0) * 32 + lane] = fx;
+                s_pf[(wid * 3 + 1) * 32 + lane] = fy;
+                s_pf[(wid * 3 + 2) * 32 + lane] = fz;
+                s_pc[wid * 32 + lane] = cnt;
+                __syncthreads();
+                if (wid == 0) {
+                    for (int w2 = 1; w2 < kThreads / 32; ++w2) {
+                        fx += s_pf[(w2 * 3 + 0) * 32 + lane];
+                        fy += s_pf[(w2 * 3 + 1) * 32 + lane];
+                        fz += s_pf[(w2 * 3 + 2) * 32 + lane];
+                        cnt += s_pc[w2 * 32 + lane];
+                    }
+                }
+                __syncthreads();   // the partials are read before the next run writes them
+            }
+            if (active && (!split || wid == 0)) {
                 if (c0 == 0) {
                     fnear[hi] = make_double4_32a((double)fx, (double)fy, (double)fz, 0.0);
                     if (nbr) nbr[hi] = cnt;

@@ -917,6 +917,7 @@ rbsog_status apply_layout(rbsog_ctx *ctx) {
         // 112 home particles fill the builder's 128 threads in one round
         const int home = ctx->use_list ? 112 : ctx->tune[s].home;
         near_layout(d.box, d.n, ctx->precision, home, d.group, d.nseg_x, d.near_cap, nblocks, npart);
+        d.near_split = ctx->precision == RBSOG_FP64 && d.n < kNearSplitMaxN ? 1 : 0;
         d.e_off = (int32_t)e_off;
         d.n_epart = npart;
         if (ctx->use_list) {

@@ -170,6 +170,7 @@ struct SysDesc {
     int64_t c_off;             // first cell (global index)
     int32_t group, nseg_x;     // near field: home cells per block, segments per x-row
     int32_t near_cap;          // near field: staged particles per shared-memory chunk
+    int32_t near_split;        // near field (FP64 cell stencil): the warps of a block split the rows
     int32_t e_off, n_epart;    // near-energy partials (one per near-field block)
     int32_t tile_p, n_ptiles;  // rho sweep: particles per tile, tiles
     int64_t rp_off;            // first rho partial (double2 units)
@@ -228,6 +229,9 @@ struct BatchView {
 };
 constexpr int kFinChunks = 16;    // blocks per system in the finalize reduction
 constexpr int kParticleBlock = 256;
+// FP64 systems below this many particles split the cell-stencil rows over
+// the warps of a near-field block (their blocks hold few home particles)
+constexpr int64_t kNearSplitMaxN = 131072;
 
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
 // 64x64->128-bit products with the published multipliers, key bumped by the
