@@ -56,7 +56,12 @@ std::tuple<int, int, int> tune_key(int64_t n, int P, int prec) {
 Tune tune_for(int64_t n, int P, int prec) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(tune_key(n, P, prec));
-    return it == g_tune.end() ? Tune{} : it->second;
+    if (it != g_tune.end()) return it->second;
+    Tune t;
+    // FP64 systems whose stencil rows are split over the warps: about one
+    // run of 32 home particles per block keeps the four warps' shares even
+    if (prec == RBSOG_FP64 && n < kNearSplitMaxN) t.home = 32;
+    return t;
 }
 
 }  // namespace
