@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, PREC == 1 ? 6 : 4)
     __shared__ int s_shift[kMaxStaged];
     __shared__ int s_hstart[kMaxGroup + 1];
     __shared__ float4 s_tab[ND < 0 ? 2 * kTabN : 1];   // Gaussian-sum tables (ND < 0)
-    __shared__ uint16_t s_hord[WIN ? kMaxHome : 1];    // home particles in quadrant order (WIN)
+    __shared__ uint16_t s_hord[WIN && PREC == 1 ? kMaxHome : 1];    // home particles in quadrant order (WIN, FP32C)
     // split (FP64, small systems): the row partials of the four warps
     __shared__ double s_pf[PREC == 0 ? 3 * kThreads : 1];
     __shared__ int s_pc[PREC == 0 ? kThreads : 1];
@@ -245,8 +245,10 @@ __global__ void __launch_bounds__(kThreads, PREC == 1 ? 6 : 4)
     // so that a warp's lanes see similar row gaps and similar window lengths.
     // The grouping is a deterministic stable counting sort done by warp 0.
     const int nhome = he - hb;
-    const bool reord = WIN && nhome <= kMaxHome;
-    if constexpr (WIN) {
+    // (FP32C only: FP64 keeps the cell order, so that its per-block energy
+    // sums keep their order)
+    const bool reord = WIN && PREC == 1 && nhome <= kMaxHome;
+    if constexpr (WIN && PREC == 1) {
         if (reord && wid == 0) {
             auto quad = [&](int p) {
                 if (p >= nhome) return 4;
@@ -405,7 +407,76 @@ __global__ void __launch_bounds__(kThreads, PREC == 1 ? 6 : 4)
                 cnt += n;
                 n = 0;
             };
-            if constexpr (WIN) {
+            if constexpr (WIN && PREC == 0) {
+                // FP64 per-lane windows: the same x-windows as below, found
+                // on FP32 offsets from the block centre (a staged particle's
+                // offset is its FP64 x plus its cell's image shift, minus the
+                // centre), with a margin far above the FP32 rounding; the
+                // FP64 distance test decides, with the expressions of the
+                // full stencil.  The windows hold every partner in the same
+                // staged order, so the lists, and so the forces and energies,
+                // are those of the full stencil bit for bit.
+                constexpr float kMargin = 1e-3f;
+                const float hy = box.h_f[1], hz = box.h_f[2];
+                const float inv_hx = 1.0f / box.h_f[0], xbase = 1.0f + 0.5f * (float)nh;
+                const double cxa = ((double)x0 + 0.5 * (double)nh) * box.h[0];
+                const double cya = ((double)cy + 0.5) * box.h[1], cza = ((double)cz + 0.5) * box.h[2];
+                const float fxi = (float)(ix - cxa), fyi = (float)(iy - cya), fzi = (float)(iz - cza);
+#pragma unroll 1
+                for (int r = split ? wid : 0; r < 9; r += split ? kThreads / 32 : 1) {
+                    const int dyr = r % 3 - 1, dzr = r / 3 - 1;
+                    const int k0 = r * w;
+                    int lo = 0, len = 0, cl = 0;
+                    if (active) {
+                        const float gy = dyr == 0 ? 0.f
+                                                  : fmaxf((dyr < 0 ? fyi + 0.5f * hy : 0.5f * hy - fyi) - kMargin, 0.f);
+                        const float gz = dzr == 0 ? 0.f
+                                                  : fmaxf((dzr < 0 ? fzi + 0.5f * hz : 0.5f * hz - fzi) - kMargin, 0.f);
+                        const float b2 = box.rc2_f - gy * gy - gz * gz;
+                        if (b2 > 0.f) {
+                            const float bb = sqrtf(b2) + kMargin;
+                            const float xl = fxi - bb, xr = fxi + bb;
+                            cl = min(max((int)floorf(fmaf(xl, inv_hx, xbase)), 0), w - 1);
+                            const int ch = min(max((int)floorf(fmaf(xr, inv_hx, xbase)), 0), w - 1);
+                            const double ol = box.L[0] * (double)((s_shift[k0 + cl] & 3) - 1) - cxa;
+                            int a = max(s_off[k0 + cl], c0), e = min(s_off[k0 + cl + 1], c1);
+                            while (a < e) {   // first x >= xl
+                                const int m = (a + e) >> 1;
+                                if ((float)(st[m - c0].x + ol) < xl) a = m + 1; else e = m;
+                            }
+                            lo = a;
+                            const double oh = box.L[0] * (double)((s_shift[k0 + ch] & 3) - 1) - cxa;
+                            a = max(s_off[k0 + ch], c0);
+                            e = min(s_off[k0 + ch + 1], c1);
+                            while (a < e) {   // first x > xr
+                                const int m = (a + e) >> 1;
+                                if ((float)(st[m - c0].x + oh) <= xr) a = m + 1; else e = m;
+                            }
+                            len = max(min(a, c1) - min(lo, c1), 0);
+                        }
+                    }
+                    const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+                    int kc = k0 + cl;   // staged cell of the next candidate
+                    for (int it = 0; it < maxlen; it += kList) {
+                        const int m = min(max(len - it, 0), kList);
+                        if (__any_sync(0xffffffffu, n + m > kList)) compute();
+                        for (int uu = 0; uu < m; ++uu) {
+                            const int t = lo + it + uu;
+                            while (s_off[kc + 1] <= t) ++kc;
+                            const int code = s_shift[kc];
+                            const double4_32a pj = st[t - c0];
+                            const double dx = __dsub_rn(__dsub_rn(ix, pj.x), box.L[0] * (double)((code & 3) - 1));
+                            const double dy = __dsub_rn(__dsub_rn(iy, pj.y), box.L[1] * (double)(((code >> 2) & 3) - 1));
+                            const double dz = __dsub_rn(__dsub_rn(iz, pj.z), box.L[2] * (double)(((code >> 4) & 3) - 1));
+                            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                            if (r2 < pc.rc2 && t != t_self) {
+                                list[n * kThreads + tid] = (entry)((t - c0) | (code << 20));
+                                ++n;
+                            }
+                        }
+                    }
+                }
+            } else if constexpr (WIN) {
                 // Per-lane windows.  Every staged row is sorted in x (cells
                 // in x order, members by x), so the candidates of lane i in
                 // row (dy, dz) are the contiguous run with |x_j - x_i| <= b,
@@ -616,8 +687,8 @@ cudaError_t launch_near(int precision, const BatchView &bv, const NearSog &sog, 
         else if (spec) go(k_near<1, 5, 8, false>);
         else go(k_near<1, 0, 0, false>);
     } else {
-        if (spec) go(k_near<0, 5, 12, false>);
-        else go(k_near<0, 0, 0, false>);
+        if (spec) go(k_near<0, 5, 12, true>);
+        else go(k_near<0, 0, 0, true>);
     }
     return cudaGetLastError();
 }
