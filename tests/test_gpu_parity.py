@@ -223,6 +223,39 @@ def test_forces_fp64_match_oracle(N, L, P):
     g.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_forces_in_a_cuboid_box_match_oracle(prec):
+    """A cuboid box (three different sides): per-dimension cell sides,
+    fixed-point scales, image shifts and stencil windows, against the
+    oracle on the same k-set."""
+    _dev()
+    B = _lib().binding
+    a = 1.26
+    n = (8, 10, 16)
+    L = tuple(float(k * a) for k in n)
+    rng = np.random.default_rng(42)
+    grid = np.stack(np.meshgrid(*[np.arange(k) for k in n], indexing="ij"), -1).reshape(-1, 3)
+    x = (grid + 0.5) * a + rng.uniform(-0.2, 0.2, size=grid.shape)
+    N = x.shape[0]
+    q = np.where(rng.permutation(N) % 2 == 0, 1.0, -1.0)
+    P = 48
+    g, sog = make(N, L, P, prec=prec, n_ksets=2, seed=5)
+    g.set_state(*to_dev(q, x))
+    s = osys(L, sog)
+    m = O.kseq(sog, s.L, seed=9, n_chains=4, chain_len=P // 4)[:P]
+    f = torch.zeros((N, 3), dtype=torch.float64, device=_dev())
+    B.rbsog_compute_forces(g.ctx, m, f)
+    fo, _ = O.forces(s, q, O.wrap(x, s.L), S=s.S(), m=m)
+    fg = f.cpu().numpy()
+    g.close()
+    if prec == "fp64":
+        assert rms_rel(fg, fo) < 1e-10
+        assert per_particle_rel(fg, fo)[1] < PP_FP64
+    else:
+        assert rms_rel(fg, fo) < 1e-4
+        assert per_particle_rel(fg, fo)[1] < PP_FP32C
+
+
 @pytest.mark.parametrize("N,L,P", CASES)
 def test_forces_fp32c_within_target(N, L, P):
     _dev()
