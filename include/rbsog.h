@@ -205,7 +205,9 @@ rbsog_status rbsog_compute_forces(rbsog_ctx *ctx, const int32_t *m_kset, double 
  * rescaled by
  * sqrt(1 + dt/tau_T (T_target/T - 1)) after the second half kick.  Enqueued
  * asynchronously (replayed from a CUDA graph of one step when profiling is
- * off).  Returns RBSOG_EINVAL if the sequence would run out of k-sets. */
+ * off).  The energies rbsog_get_energies reads afterwards are those of the
+ * last step; the steps before it may leave the pair energies out.  Returns
+ * RBSOG_EINVAL if the sequence would run out of k-sets. */
 rbsog_status rbsog_step(rbsog_ctx *ctx, int64_t nsteps);
 
 /* Copy the current state out (any pointer may be NULL; host or device):
