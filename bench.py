@@ -529,6 +529,23 @@ def run_extras(args, q, x, v, dev):
         sweep[str(Ps)] = {"value": N / (ms_s / 1e3), "ms_per_step": ms_s}
         g.close()
     out["fp32c_P_sweep"] = sweep
+    # the FP64 path at the other two batch sizes (a few steps: about 0.1 s each)
+    sweep64 = {}
+    for Ps in (100, 2000):
+        if Ps == P:
+            continue
+        g = Pk.RBSOG(N, Pk.make_params(L, Ps, n_ksets=K64 + 4, seed=19, precision="fp64"), device=dev.index)
+        g.set_state(tq, tx, tv)
+        g.step(1)
+        torch.cuda.synchronize()
+        e0.record(st)
+        g.step(K64)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1) / K64
+        sweep64[str(Ps)] = {"value": N / (ms_s / 1e3), "ms_per_step": ms_s, "steps": K64}
+        g.close()
+    out["fp64_P_sweep"] = sweep64
     # the zero-frequency term of a spherical or planar boundary (Sec. 3.2) on
     # the same workload: step time with it, and its own kernels' time
     bnd = {}
